@@ -1,0 +1,197 @@
+"""Seeded synthetic read sets shaped like the workloads of arXiv 1410.0562.
+
+This module holds no part of the BWT method: it only draws reads.  Both the
+oracle (in the tests and the CPU baseline) and the GPU library consume what it
+returns, and neither is imported here.
+
+The paper measures on two real sequencing sets that are not available here
+(NA12878, 1.2 G x 101 bp Illumina reads; Venter, 32 M x 875 bp Sanger reads;
+Section 7).  The generators below stand in for them with the same shapes:
+short reads at ~10x coverage of a genome, ragged mid-length reads, and long
+reads with indels.  All randomness comes from numpy's PCG64 generator seeded
+with the values listed in ``CONFIGS``; the same seed gives the same reads on
+any machine with the same numpy version.
+
+A read set is returned as ``(reads, offsets)``: ``reads`` is a uint8 array of
+ASCII bases (the concatenation of all reads) and ``offsets`` a uint64 array of
+``m + 1`` non-decreasing entries, read ``j`` being
+``reads[offsets[j]:offsets[j+1]]``.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+DNA = b"ACGT"
+_LUT = np.frombuffer(DNA, dtype=np.uint8)
+
+
+def _rng(seed: int) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+def offsets_from_lengths(lengths) -> np.ndarray:
+    lengths = np.asarray(lengths, dtype=np.uint64)
+    off = np.zeros(len(lengths) + 1, dtype=np.uint64)
+    np.cumsum(lengths, out=off[1:])
+    return off
+
+
+def genome(size: int, seed: int) -> np.ndarray:
+    """An i.i.d. uniform genome over {0,1,2,3} (codes of A,C,G,T)."""
+    return _rng(seed).integers(0, 4, size=size, dtype=np.uint8)
+
+
+def uniform_reads(n_reads: int, length: int, seed: int, alphabet: bytes = DNA):
+    """n_reads reads of equal length, every base i.i.d. uniform over the alphabet."""
+    rng = _rng(seed)
+    lut = np.frombuffer(alphabet, dtype=np.uint8)
+    codes = rng.integers(0, len(lut), size=n_reads * length, dtype=np.uint8)
+    return lut[codes], offsets_from_lengths(np.full(n_reads, length))
+
+
+def ragged_reads(n_reads: int, min_len: int, max_len: int, seed: int, alphabet: bytes = DNA,
+                 p_empty: float = 0.0, p_repeat: float = 0.0):
+    """Reads of uniform random length in [min_len, max_len], i.i.d. bases.
+
+    ``p_empty`` makes that fraction of reads empty; ``p_repeat`` makes that
+    fraction of reads a single repeated base (long common prefixes).
+    """
+    rng = _rng(seed)
+    lut = np.frombuffer(alphabet, dtype=np.uint8)
+    lengths = rng.integers(min_len, max_len + 1, size=n_reads)
+    if p_empty > 0:
+        lengths[rng.random(n_reads) < p_empty] = 0
+    off = offsets_from_lengths(lengths)
+    codes = rng.integers(0, len(lut), size=int(off[-1]), dtype=np.uint8)
+    if p_repeat > 0:
+        rep = np.nonzero(rng.random(n_reads) < p_repeat)[0]
+        for j in rep:
+            codes[off[j]:off[j + 1]] = codes[off[j]] if off[j + 1] > off[j] else 0
+    return lut[codes], off
+
+
+def _revcomp(codes: np.ndarray) -> np.ndarray:
+    return (3 - codes)[..., ::-1]
+
+
+def sampled_reads(g: np.ndarray, n_reads: int, lengths, sub_rate: float, seed: int):
+    """Reads sampled from genome g at uniform offsets and strands, with
+    uniform substitutions (the new base is one of the other three).
+
+    ``lengths`` is an int (all reads that long) or an array of n_reads lengths.
+    """
+    rng = _rng(seed)
+    G = len(g)
+    if np.isscalar(lengths):
+        lengths = np.full(n_reads, int(lengths), dtype=np.int64)
+    lengths = np.asarray(lengths, dtype=np.int64)
+    off = offsets_from_lengths(lengths)
+    out = np.empty(int(off[-1]), dtype=np.uint8)
+    starts = rng.integers(0, G - lengths + 1)
+    minus = rng.random(n_reads) < 0.5
+    # group by length so each group is one vectorised gather
+    for L in np.unique(lengths):
+        idx = np.nonzero(lengths == L)[0]
+        if L == 0:
+            continue
+        win = np.lib.stride_tricks.sliding_window_view(g, int(L))[starts[idx]].copy()
+        mi = minus[idx]
+        win[mi] = _revcomp(win[mi])
+        sub = rng.random(win.shape) < sub_rate
+        shift = rng.integers(1, 4, size=win.shape, dtype=np.uint8)
+        win = np.where(sub, (win + shift) & 3, win).astype(np.uint8)
+        pos = off[idx][:, None].astype(np.int64) + np.arange(int(L))[None, :]
+        out[pos.ravel()] = win.ravel()
+    return _LUT[out], off
+
+
+def long_reads(g: np.ndarray, n_reads: int, mean_len: float, sigma: float, clip: tuple, p_del: float,
+               p_ins: float, p_sub: float, seed: int):
+    """Long reads with indels: log-normal lengths with the given mean and
+    sigma, clipped to ``clip``; each emitted step is a deletion (skip a genome
+    base) with probability p_del, an insertion (emit a random base) with
+    p_ins, a substitution with p_sub, else a copy; a read stops after its
+    drawn number of emitted bases.  Strands are 50/50.
+    """
+    rng = _rng(seed)
+    mu = np.log(mean_len) - sigma * sigma / 2
+    lengths = np.clip(np.round(rng.lognormal(mu, sigma, size=n_reads)), clip[0], clip[1]).astype(np.int64)
+    off = offsets_from_lengths(lengths)
+    out = np.empty(int(off[-1]), dtype=np.uint8)
+    G = len(g)
+    for j in range(n_reads):
+        L = int(lengths[j])
+        steps = int(L * 1.25) + 64
+        u = rng.random(steps)
+        rand_base = rng.integers(0, 4, size=steps, dtype=np.uint8)
+        shift = rng.integers(1, 4, size=steps, dtype=np.uint8)
+        is_del = u < p_del
+        is_ins = (u >= p_del) & (u < p_del + p_ins)
+        is_sub = (u >= p_del + p_ins) & (u < p_del + p_ins + p_sub)
+        emit = ~is_del
+        consume = ~is_ins  # copies, substitutions and deletions advance the genome
+        gpos = np.cumsum(consume) - consume  # genome offset consumed before each step
+        span = int(gpos[-1]) + 2
+        start = int(rng.integers(0, max(G - span, 1)))
+        src = g[(start + np.minimum(gpos, G - 1 - start))]
+        base = np.where(is_ins, rand_base, np.where(is_sub, (src + shift) & 3, src)).astype(np.uint8)
+        seq = base[emit][:L]
+        if len(seq) < L:  # never expected with the 25% slack, but stay exact
+            seq = np.concatenate([seq, rng.integers(0, 4, size=L - len(seq), dtype=np.uint8)])
+        if rng.random() < 0.5:
+            seq = _revcomp(seq)
+        out[off[j]:off[j + 1]] = seq
+    return _LUT[out], off
+
+
+@dataclass(frozen=True)
+class Workload:
+    name: str
+    reads: np.ndarray
+    offsets: np.ndarray
+    block_suffixes: int
+    index_bits: int
+    appends: tuple  # read-count boundaries of the sbwt_append calls
+
+    @property
+    def m(self) -> int:
+        return len(self.offsets) - 1
+
+    @property
+    def bases(self) -> int:
+        return int(self.offsets[-1])
+
+
+def tiny(seed: int = 0x05621410 + 1) -> Workload:
+    """1,000 reads x 100 bp, i.i.d. uniform bases, appended as 2 x 500 reads."""
+    reads, off = uniform_reads(1000, 100, seed)
+    return Workload("tiny-1000x100-iid", reads, off, 1 << 24, 32, (0, 500, 1000))
+
+
+def short(n_reads: int = 1_000_000, genome_size: int = 10_000_000, seed_genome: int = 0x14100562 + 2,
+          seed_reads: int = 0x05621410 + 2) -> Workload:
+    """1M x 100 bp reads from a 10 Mbp i.i.d. genome, uniform offsets and
+    strands, 1% substitutions; blocks of 16,777,216 suffixes; 32-bit indices."""
+    g = genome(genome_size, seed_genome)
+    reads, off = sampled_reads(g, n_reads, 100, 0.01, seed_reads)
+    return Workload(f"short-{n_reads}x100-g{genome_size}", reads, off, 1 << 24, 32, (0, n_reads))
+
+
+def batched(n_reads: int = 2_000_000, genome_size: int = 50_000_000, seed_genome: int = 0x14100562 + 3,
+            seed_reads: int = 0x05621410 + 3) -> Workload:
+    """2M reads of length uniform in [50, 250] from a 50 Mbp i.i.d. genome, 1% substitutions; 64-bit indices."""
+    g = genome(genome_size, seed_genome)
+    lengths = _rng(seed_reads ^ 0x5A5A).integers(50, 251, size=n_reads)
+    reads, off = sampled_reads(g, n_reads, lengths, 0.01, seed_reads)
+    return Workload(f"batched-{n_reads}xU[50,250]-g{genome_size}", reads, off, 0, 64, (0, n_reads))
+
+
+def long(n_reads: int = 20_000, genome_size: int = 100_000_000, seed_genome: int = 0x14100562 + 4,
+         seed_reads: int = 0x05621410 + 4) -> Workload:
+    """20k log-normal reads (mean 10 kbp, sigma 0.5, clipped to [1k, 50k]) with
+    6% substitutions, 2% insertions, 2% deletions; 64-bit indices."""
+    g = genome(genome_size, seed_genome)
+    reads, off = long_reads(g, n_reads, 10_000.0, 0.5, (1_000, 50_000), 0.02, 0.02, 0.06, seed_reads)
+    return Workload(f"long-{n_reads}xlognormal10k-g{genome_size}", reads, off, 0, 64, (0, n_reads))
