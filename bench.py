@@ -1,0 +1,362 @@
+"""Benchmark: set-bwte BWT build throughput (Mbp/s) on synthetic reads.
+
+A step builds the BWT of the whole workload from an empty index: one
+``sbwt_append`` of every read, which runs Algorithm 1 of arXiv 1410.0562 over
+all its blocks (ConstructSA, B_int, ComputeRanks, the g[SA_int] gather,
+Insert) in the library's CUDA kernels.  Default workload: 1M x 100 bp reads
+from a seeded 10 Mbp i.i.d. genome with 1% substitutions (uniform offsets and
+strands), blocks of 2^24 suffixes, 32-bit indices -- a synthetic stand-in
+shaped like the paper's short-read set.
+
+``value`` is timed with CUDA events on the library's stream, inputs already in
+HBM; between timed steps a 256 MB buffer is written to flush L2 (outside the
+timed region).  ``e2e`` times the host-buffer C-ABI call: H2D of the reads
+from pinned memory, the build, and the D2H of B.  ``--impl reference`` times
+the CPU oracle (a plain single-threaded suffix sort by direct comparison) on a
+bounded sample of the same workload.
+
+Under torchrun (N > 1) each rank builds an independent index of its own read
+set (replicas: the path has no exchange step), so per-GPU work is fixed.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import readgen  # noqa: E402
+
+METRIC = "BWT build Mbp/s"
+UNIT = "Mbp/s"
+DOMINANT = "radix_downsweep"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="short", choices=["short", "tiny"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--profile-steps", type=int, default=None,
+                    help="steps run under per-kernel event timing (default: the timed steps)")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def make_workload(name: str, rank: int):
+    if name == "tiny":
+        w = readgen.tiny()
+    else:
+        # every rank indexes its own read set (same shape, its own seeds)
+        w = readgen.short(seed_genome=0x14100562 + 2 + 1000 * rank, seed_reads=0x05621410 + 2 + 1000 * rank)
+    return w
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def load_traffic(kernel: str):
+    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, if it
+    was taken on the current kernel sources; else None."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        with open(path) as f:
+            t = json.load(f)
+        from paper_1410_0562_gb300 import _build
+        if t.get("sources_sha") != _build.sources_sha():
+            return None
+        k = t["kernels"].get(kernel)
+        if not k:
+            return None
+        return k
+    except Exception:
+        return None
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = f"/tmp/sbwt_clocks_{os.getpid()}.csv"
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index),
+                 "--query-gpu=clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+                 "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if not self.proc:
+            return None
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 6:
+                    continue
+                try:
+                    sm.append(float(parts[0]))
+                    mx.append(float(parts[1]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[2:6]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        except OSError:
+            return None
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(w, n_reads: int):
+    """The oracle as it stands on a bounded sample: the first n_reads reads."""
+    import oracle
+    n_reads = min(n_reads, w.m)
+    off = w.offsets[: n_reads + 1]
+    reads = w.reads[: int(off[-1])]
+    t = time.perf_counter()
+    oracle.bwt(reads, off)
+    dt = time.perf_counter() - t
+    return {"value": float(off[-1]) / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {n_reads} reads ({int(off[-1])} bp) of the workload, full BWT by the oracle, "
+                      f"{dt:.1f} s single-threaded"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    w = make_workload(args.workload, 0)
+    n_reads = min(50_000, w.m)
+    off = w.offsets[: n_reads + 1]
+    reads = w.reads[: int(off[-1])]
+    import oracle
+    oracle.build()
+    for _ in range(args.warmup):
+        oracle.bwt(reads, off)
+    times = []
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        oracle.bwt(reads, off)
+        times.append(time.perf_counter() - t)
+    total = sum(times)
+    value = float(off[-1]) * args.steps / total / 1e6
+    sample = (f"each step: the oracle's full BWT of the first {n_reads} reads ({int(off[-1])} bp) of the "
+              f"workload, single-threaded")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": w.name, "sample_reads": n_reads, "block_suffixes": w.block_suffixes,
+                   "index_bits": w.index_bits, "parallelism": "none (host cores)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gb300(args):
+    import torch
+
+    import paper_1410_0562_gb300 as sb
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_mod
+        dist_mod.init_process_group("nccl", device_id=torch.device("cuda", local))
+        dist = dist_mod
+    if rank == 0:
+        sb.build()
+    if dist:
+        dist.barrier()
+    sb.load()
+
+    w = make_workload(args.workload, rank)
+    bases = w.bases
+    stream = torch.cuda.Stream()
+    idx = sb.SetBWT(b"ACGT", index_bits=w.index_bits, block_suffixes=w.block_suffixes,
+                    stream=stream.cuda_stream, device=local)
+    d_reads = torch.from_numpy(w.reads).to("cuda")
+    d_off = torch.from_numpy(w.offsets.astype(np.int64)).to("cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    torch.cuda.synchronize()
+
+    def step():
+        idx.reset()
+        idx.append_device(d_reads.data_ptr(), d_off.data_ptr(), w.m)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    # timed region: K steps, each bracketed by events on the library stream
+    sb.sbwt_reset_kernel_stats(idx.handle)
+    sb.sbwt_set_profiling(idx.handle, True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        for k in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(k & 0xFF)  # L2 flush, outside the events
+                ev[k][0].record(stream)
+            step()
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    ms_steps = [a.elapsed_time(b) for a, b in ev]
+    stats = sb.sbwt_get_kernel_stats(idx.handle)
+    sb.sbwt_set_profiling(idx.handle, False)
+    total_ms = float(sum(ms_steps))
+    if dist:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+
+    # the result is the one the oracle pins: spot-check it on this rank
+    B = idx.bwt()
+    assert len(B) == bases + w.m
+    assert int(np.count_nonzero(B == ord("$"))) == w.m
+
+    # end to end through the host-buffer C ABI: pinned H2D, build, D2H of B
+    e2e = None
+    if not args.no_e2e:
+        h_reads = torch.from_numpy(w.reads).pin_memory()
+        h_off = torch.from_numpy(w.offsets.astype(np.int64)).pin_memory()
+        h_out = torch.empty(bases + w.m, dtype=torch.uint8).pin_memory()
+        out_ptr = h_out.data_ptr()
+        import ctypes
+
+        def e2e_step():
+            idx.reset()
+            sb.sbwt_append(idx.handle, h_reads.data_ptr(), h_off.data_ptr(), w.m)
+            got = ctypes.c_uint64()
+            rc = sb.load().sbwt_get_bwt(idx.handle, ctypes.c_void_p(out_ptr), bases + w.m, ctypes.byref(got))
+            assert rc == 0
+
+        for _ in range(max(1, args.warmup)):
+            e2e_step()
+        torch.cuda.synchronize()
+        e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                for _ in range(args.steps)]
+        for k in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(k & 0xFF)
+                e_ev[k][0].record(stream)
+            e2e_step()
+            e_ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        e_ms = float(sum(a.elapsed_time(b) for a, b in e_ev))
+        if dist:
+            t = torch.tensor([e_ms], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e_ms = float(t.item())
+        e2e = {"value": bases * world * args.steps / (e_ms / 1e3) / 1e6, "unit": UNIT,
+               "h2d_bytes_per_step": int(w.reads.nbytes + w.offsets.nbytes),
+               "d2h_bytes_per_step": int(bases + w.m)}
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+
+    value = bases * world * args.steps / (total_ms / 1e3) / 1e6
+    by_ms = sorted(stats, key=lambda s: -s["ms"])
+    dom = next((s for s in stats if s["name"] == DOMINANT), by_ms[0])
+    dom = by_ms[0] if by_ms and by_ms[0]["ms"] > 0 else dom
+    peak, peak_kind = load_peaks()
+    achieved = dom["bytes"] / (dom["ms"] / 1e3) / 1e9 if dom["ms"] > 0 else 0.0
+    traffic = load_traffic(dom["name"])
+    roofline = {"bound": "hbm", "kernel": dom["name"], "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": peak_kind,
+                "traffic": traffic["dram_bytes_per_launch"] if traffic else None,
+                "algorithmic_bytes_per_launch": dom["bytes"] / max(dom["launches"], 1),
+                "avg_launch_us": 1e3 * dom["ms"] / max(dom["launches"], 1)}
+    kernels = {s["name"]: {"launches": s["launches"] // args.steps, "ms_per_step": s["ms"] / args.steps,
+                           "GBps": (s["bytes"] / (s["ms"] / 1e3) / 1e9) if s["ms"] > 0 else None}
+               for s in by_ms}
+    launches = int(sum(s["launches"] for s in stats))
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": w.name, "reads": w.m, "bases": bases, "block_suffixes": w.block_suffixes,
+                   "index_bits": w.index_bits, "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "l2": "flushed between timed steps (256 MB write, outside the timed region)",
+                   "step": "reset + one append of every read (all blocks of Algorithm 1)"},
+        "roofline": roofline,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "kernels": kernels,
+    }
+    clocks = clk.summary()
+    if clocks:
+        line["clocks"] = clocks
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline(w, 200_000 if args.workload == "short" else w.m)
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gb300(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,164 @@
+/*
+ * sbwt.h -- C ABI of the GB300 set-bwte library (libsbwt.so).
+ *
+ * The library builds and incrementally extends the Burrows-Wheeler transform
+ * of a set of strings (DNA reads) on one GPU, following set-bwte
+ * (Pantaleoni, arXiv 1410.0562):
+ *
+ *   - The BWT of a string set S_0..S_{m-1} is the BWT of
+ *     T = S_0 $_0 ... S_{m-1} $_{m-1} with $_0 < ... < $_{m-1} < c_1
+ *     (Section 2, Eq. 1): B[i] = T[(SA[i]-1) mod n].  Terminators are
+ *     ordered by global read index, which is the order reads were appended.
+ *   - rank(c,k,B) = |{i<k : B[i]=c}| (Section 2, Eq. 2).
+ *   - Each sbwt_append splits its reads into blocks of at most M suffixes
+ *     (a read longer than M forms its own block) and adds each block in turn
+ *     (Algorithm 1): ConstructSA of the block, B_int, ComputeRanks against
+ *     the current index (Lemma 1 and Algorithm 2 of Section 4), the g[SA_int]
+ *     reordering and Insert (Section 5).  All of these run as CUDA kernels;
+ *     there is no CPU fallback.
+ *
+ * Conventions shared by every call:
+ *   - Return value: SBWT_OK (0) or a negative SBWT_E* code; sbwt_strerror
+ *     turns it into text.  On any error the index is left exactly as it was
+ *     before the call.
+ *   - A handle is not thread-safe: one call at a time per handle.
+ *   - Host pointers are owned by the caller and only read (or written) during
+ *     the call.  Device pointers must be device memory of the index's GPU.
+ *   - Alphabet: 1 to 4 distinct bytes in strictly increasing byte order
+ *     (c_1 < ... < c_sigma, Section 2), none of them '$' or 0.
+ *   - Read set: `reads` holds the concatenated bytes of m reads and `offsets`
+ *     m+1 non-decreasing uint64 values with offsets[0] = 0; read j is
+ *     reads[offsets[j] .. offsets[j+1]).  Empty reads are allowed.
+ *   - B is returned one byte per row: the alphabet byte, or '$' (0x24) for
+ *     every terminator (all $_k share one output byte).
+ */
+#ifndef SBWT_H
+#define SBWT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define SBWT_OK 0
+#define SBWT_EINVAL (-1)   /* bad argument, byte outside the alphabet, bad offsets */
+#define SBWT_ENOMEM (-2)   /* the HBM budget (or the device) cannot hold the result */
+#define SBWT_ERANGE (-3)   /* output buffer too small; the needed size is reported */
+#define SBWT_EDEVICE (-4)  /* a CUDA error, or a device-side wait that gave up */
+#define SBWT_ENOTSUP (-5)  /* option not supported by this build */
+
+typedef struct sbwt_index sbwt_index; /* opaque, owned by the library */
+
+/* Options for sbwt_create_ex.  Zero-initialise and set what you need. */
+typedef struct {
+    uint32_t index_bits;     /* width of the g / g_sa row indices: 32 or 64; 0 =
+                                32 while the index stays below 2^32 - 1 rows, 64
+                                beyond.  With 32, an append that would reach
+                                2^32 - 1 rows returns SBWT_EINVAL. */
+    uint64_t block_suffixes; /* M of Algorithm 1 (suffixes per block), at most
+                                2^31; 0 = 2^24 */
+    void *stream;            /* cudaStream_t every kernel is launched on; NULL =
+                                a stream the library creates and owns */
+    int32_t device;          /* CUDA device ordinal; -1 = the current device */
+    uint32_t reserved[8];    /* must be zero */
+} sbwt_options;
+
+/* Creates an empty index over `alphabet` (a NUL-terminated string of 1..4
+ * bytes in strictly increasing order).  hbm_budget_bytes caps the device
+ * memory the index may hold, its working buffers included (0 = no cap beyond
+ * the device's free memory).  Device state is created lazily by the first
+ * call that needs the GPU, so this call does not touch the GPU.
+ * Errors: SBWT_EINVAL (bad alphabet, NULL out), SBWT_ENOMEM (host). */
+int sbwt_create(const char *alphabet, size_t hbm_budget_bytes, sbwt_index **out);
+
+/* sbwt_create with options; opt may be NULL (all defaults).
+ * Errors: as sbwt_create, plus SBWT_EINVAL for an invalid option. */
+int sbwt_create_ex(const char *alphabet, size_t hbm_budget_bytes, const sbwt_options *opt,
+                   sbwt_index **out);
+
+/* Appends m reads from HOST memory (Algorithm 1 over the new reads; Section 3
+ * notes that new strings can be added at any time because suffixes never
+ * cross a read).  The reads get the global ids n_reads .. n_reads+m-1, in
+ * order.  Inputs are validated before the index changes: a byte outside the
+ * alphabet or bad offsets give SBWT_EINVAL and leave the index unchanged.
+ * Blocks until the index holds the new reads. */
+int sbwt_append(sbwt_index *idx, const uint8_t *reads, const uint64_t *offsets, uint64_t m);
+
+/* As sbwt_append, but `d_reads` (offsets[m] bytes) and `d_offsets` (m+1
+ * values) are DEVICE pointers on the index's GPU.  The offsets are copied to
+ * the host once to plan the blocks.  Blocks until done. */
+int sbwt_append_device(sbwt_index *idx, const uint8_t *d_reads, const uint64_t *d_offsets, uint64_t m);
+
+/* Writes B (n bytes, see conventions) into host buffer `out` of `cap` bytes
+ * and sets *n_out = n.  If cap < n returns SBWT_ERANGE with *n_out = n and
+ * nothing written; out may be NULL when cap is 0. */
+int sbwt_get_bwt(sbwt_index *idx, uint8_t *out, uint64_t cap, uint64_t *n_out);
+
+/* rank(c, k, B) (Eq. 2) for c an alphabet byte or '$', 0 <= k <= n.
+ * Errors: SBWT_EINVAL for another c or k > n. */
+int sbwt_rank(sbwt_index *idx, uint8_t c, uint64_t k, uint64_t *out);
+
+/* q rank queries at once: out[i] = rank(cs[i], ks[i], B); host arrays.
+ * Errors: SBWT_EINVAL if any query is invalid (nothing written). */
+int sbwt_rank_batch(sbwt_index *idx, const uint8_t *cs, const uint64_t *ks, uint64_t q, uint64_t *out);
+
+/* Number of rows n (symbols, terminators included) and reads m. */
+int sbwt_size(const sbwt_index *idx, uint64_t *n, uint64_t *m);
+
+/* Empties the index (n = m = 0) and keeps its device buffers for reuse. */
+int sbwt_reset(sbwt_index *idx);
+
+/* Frees everything the index holds.  NULL is a no-op. */
+void sbwt_destroy(sbwt_index *idx);
+
+/* Static text for a status code. */
+const char *sbwt_strerror(int code);
+
+/* The cudaStream_t the index launches on (creating device state if needed). */
+int sbwt_get_stream(sbwt_index *idx, void **stream);
+
+/* ---- intermediates of the last block (for checking each step) ----------
+ * With capture on, every append keeps the arrays of its LAST block:
+ *   SBWT_STAGE_SA   : SA_int, block-local text positions (uint32 each);
+ *                     position of read j's symbol k is
+ *                     sum_{l<j}(|P_l|+1) + k over the block's reads, its
+ *                     terminator at k = |P_j| (Algorithm 1, ConstructSA)
+ *   SBWT_STAGE_BINT : B_int, one byte per suffix in SA order: 0..sigma-1
+ *                     for c_1..c_sigma, 255 for a terminator
+ *   SBWT_STAGE_G    : g, per block text position, number of rows of the
+ *                     index before the block that are smaller (Algorithm 2),
+ *                     uint64 each
+ *   SBWT_STAGE_GSA  : g_sa = g[SA_int], uint64 each
+ * sbwt_get_stage copies one of them to host memory `out` (cap bytes),
+ * *count_out = number of elements; SBWT_ERANGE if it does not fit. */
+#define SBWT_STAGE_SA 0
+#define SBWT_STAGE_BINT 1
+#define SBWT_STAGE_G 2
+#define SBWT_STAGE_GSA 3
+int sbwt_set_capture(sbwt_index *idx, int on);
+int sbwt_get_stage(sbwt_index *idx, int stage, void *out, uint64_t cap, uint64_t *count_out);
+
+/* ---- per-kernel timing ---------------------------------------------------
+ * With profiling on, every kernel launch is bracketed by CUDA events on the
+ * index's stream.  sbwt_get_kernel_stats fills up to `cap` records (one per
+ * kernel name, accumulated since the last sbwt_reset_kernel_stats) and sets
+ * *n_out to the number of distinct kernels.  `bytes` is the algorithmic HBM
+ * traffic the launches were sized for (reads + writes of their inputs and
+ * outputs, counted once).  Launch counts are kept even with profiling off. */
+typedef struct {
+    char name[48];
+    uint64_t launches;
+    double ms;      /* summed event time; 0 with profiling off */
+    double bytes;   /* summed algorithmic bytes */
+} sbwt_kernel_stat;
+int sbwt_set_profiling(sbwt_index *idx, int on);
+int sbwt_get_kernel_stats(sbwt_index *idx, sbwt_kernel_stat *out, int cap, int *n_out);
+int sbwt_reset_kernel_stats(sbwt_index *idx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SBWT_H */

@@ -1,0 +1,674 @@
+// capi.cu -- the index runtime behind include/sbwt.h: device state, the
+// memory plan under the HBM budget, block planning and the per-block
+// pipeline of Algorithm 1 (arXiv 1410.0562):
+//   ConstructSA -> B_int -> ComputeRanks -> g[SA_int] -> Insert.
+// Host code only orchestrates; every step of the path is a CUDA kernel.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "sbwt.h"
+#include "sbwt_kernels.cuh"
+
+using namespace sbwt;
+
+namespace {
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+struct Dict {
+    DevBuf blocks, super, C;
+};
+
+struct BlockPlan {
+    uint64_t j0, j1;    // reads [j0, j1) of the append
+    uint64_t n_int;     // suffixes (symbols + terminators)
+    uint64_t base;      // text position of the block's first suffix
+    uint64_t max_len;   // longest read
+};
+
+constexpr uint64_t kDefaultBlock = 1ull << 24;
+constexpr uint64_t kMaxBlock = 1ull << 31;
+
+}  // namespace
+
+struct sbwt_index {
+    uint8_t alphabet[4] = {0, 0, 0, 0};
+    int sigma = 0;
+    uint32_t alpha4 = 0;
+    size_t budget = 0;
+    uint32_t index_bits = 0;
+    uint64_t M = kDefaultBlock;
+    int device = -1;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    bool dev_ready = false;
+
+    uint64_t n = 0, m = 0;
+    Dict dict[3];
+    int cur = 0;
+
+    DevBuf reads, offsets, text, term, err;
+    DevBuf keys, keys_alt, vals, vals_alt, sa, rank, tmp_a, tmp_b, act_pos0, act_pos1, act_suf0, act_suf1;
+    DevBuf radix_temp, scan_temp, count_log, g, gsa, bint, sb_tot;
+    DevBuf out_bytes, q_codes, q_ks, q_out;
+
+    uint32_t* h_err = nullptr;      // pinned
+    uint64_t* h_offsets = nullptr;  // pinned staging for device-side offsets
+    size_t h_offsets_cap = 0;
+
+    Launcher L;
+    bool capture = false;
+    bool last_valid = false;
+    uint64_t last_n = 0;
+    bool last_idx64 = false;
+
+    std::vector<DevBuf*> all_bufs() {
+        std::vector<DevBuf*> v = {&reads,  &offsets,  &text,     &term,     &err,        &keys,      &keys_alt,
+                                  &vals,   &vals_alt, &sa,       &rank,     &tmp_a,      &tmp_b,     &act_pos0,
+                                  &act_pos1, &act_suf0, &act_suf1, &radix_temp, &scan_temp, &count_log, &g,
+                                  &gsa,    &bint,     &sb_tot,   &out_bytes, &q_codes,   &q_ks,      &q_out};
+        for (auto& d : dict) {
+            v.push_back(&d.blocks);
+            v.push_back(&d.super);
+            v.push_back(&d.C);
+        }
+        return v;
+    }
+    size_t held_bytes() {
+        size_t s = 0;
+        for (DevBuf* b : all_bufs()) s += b->bytes;
+        return s;
+    }
+};
+
+namespace {
+
+int set_device(sbwt_index* idx) {
+    if (idx->device >= 0 && cudaSetDevice(idx->device) != cudaSuccess) return SBWT_EDEVICE;
+    return SBWT_OK;
+}
+
+void free_buf(DevBuf& b) {
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+// Makes b hold at least `bytes` (contents are not kept when it grows).
+int grow(DevBuf& b, size_t bytes) {
+    if (bytes == 0) bytes = 256;
+    bytes = (bytes + 255) & ~(size_t)255;
+    if (b.bytes >= bytes) return SBWT_OK;
+    free_buf(b);
+    if (cudaMalloc(&b.p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        b.p = nullptr;
+        return SBWT_ENOMEM;
+    }
+    b.bytes = bytes;
+    return SBWT_OK;
+}
+
+int device_init(sbwt_index* idx) {
+    if (idx->dev_ready) return set_device(idx);
+    if (idx->device < 0) {
+        if (cudaGetDevice(&idx->device) != cudaSuccess) return SBWT_EDEVICE;
+    }
+    if (set_device(idx)) return SBWT_EDEVICE;
+    if (!idx->stream) {
+        if (cudaStreamCreateWithFlags(&idx->stream, cudaStreamNonBlocking) != cudaSuccess) return SBWT_EDEVICE;
+        idx->own_stream = true;
+    }
+    idx->L.stream = idx->stream;
+    radix_init();
+    if (cudaMallocHost(&idx->h_err, sizeof(uint32_t)) != cudaSuccess) return SBWT_EDEVICE;
+    // the committed dictionary starts empty: one zero block, one zero superblock, C = 0
+    Dict& d = idx->dict[idx->cur];
+    if (grow(d.blocks, sizeof(OccBlock)) || grow(d.super, 32) || grow(d.C, 32)) return SBWT_ENOMEM;
+    cudaMemsetAsync(d.blocks.p, 0, sizeof(OccBlock), idx->stream);
+    cudaMemsetAsync(d.super.p, 0, 32, idx->stream);
+    cudaMemsetAsync(d.C.p, 0, 32, idx->stream);
+    if (grow(idx->err, 4)) return SBWT_ENOMEM;
+    if (cudaStreamSynchronize(idx->stream) != cudaSuccess) return SBWT_EDEVICE;
+    idx->dev_ready = true;
+    return SBWT_OK;
+}
+
+int validate_offsets(const uint64_t* off, uint64_t m) {
+    if (off[0] != 0) return SBWT_EINVAL;
+    for (uint64_t j = 0; j < m; ++j) {
+        if (off[j + 1] < off[j]) return SBWT_EINVAL;
+        if (off[j + 1] - off[j] + 1 > kMaxBlock) return SBWT_EINVAL;  // block-local indices are 32-bit
+    }
+    return SBWT_OK;
+}
+
+// Greedy partition (Algorithm 1: blocks of roughly M suffixes): whole reads
+// while the block stays within M suffixes; a longer read is a block alone.
+std::vector<BlockPlan> plan_blocks(const uint64_t* off, uint64_t m, uint64_t M) {
+    std::vector<BlockPlan> v;
+    uint64_t j = 0;
+    while (j < m) {
+        BlockPlan b{j, j, 0, off[j] + j, 0};
+        while (j < m) {
+            const uint64_t len = off[j + 1] - off[j];
+            if (b.n_int > 0 && b.n_int + len + 1 > M) break;
+            b.n_int += len + 1;
+            b.max_len = std::max(b.max_len, len);
+            ++j;
+        }
+        b.j1 = j;
+        v.push_back(b);
+    }
+    return v;
+}
+
+struct Plan {
+    std::vector<BlockPlan> blocks;
+    uint64_t npos = 0, nbytes = 0, cap = 0, max_len = 0;
+    size_t slots = 0;
+    bool idx64 = false;
+};
+
+struct Need {
+    DevBuf* buf;
+    size_t bytes;
+};
+
+std::vector<Need> buffer_needs(sbwt_index* idx, const Plan& p, bool host_input, uint64_t m_new) {
+    const uint64_t cap = std::max<uint64_t>(p.cap, 1);
+    const size_t w = p.idx64 ? 8 : 4;
+    const uint64_t n_final = idx->n + p.npos;
+    std::vector<Need> v;
+    if (host_input) {
+        v.push_back({&idx->reads, (size_t)p.nbytes});
+        v.push_back({&idx->offsets, (size_t)(m_new + 1) * 8});
+    }
+    v.push_back({&idx->text, (size_t)((p.npos + 31) / 32 * 2 + kTextPadWords) * 4});
+    v.push_back({&idx->term, (size_t)((p.npos + 31) / 32 + kTermPadWords) * 4});
+    for (DevBuf* b : {&idx->keys, &idx->keys_alt}) v.push_back({b, (size_t)cap * 8});
+    for (DevBuf* b : {&idx->vals, &idx->vals_alt, &idx->sa, &idx->rank, &idx->tmp_a, &idx->tmp_b, &idx->act_pos0,
+                      &idx->act_pos1, &idx->act_suf0, &idx->act_suf1})
+        v.push_back({b, (size_t)cap * 4});
+    v.push_back({&idx->radix_temp, radix_temp_words(cap) * 4});
+    v.push_back({&idx->scan_temp, scan_temp_words(cap) * 4});
+    v.push_back({&idx->count_log, p.slots * p.blocks.size() * 4});
+    v.push_back({&idx->g, (size_t)cap * w});
+    v.push_back({&idx->gsa, (size_t)cap * w});
+    v.push_back({&idx->bint, (size_t)cap});
+    v.push_back({&idx->sb_tot, (size_t)dict_supers(n_final) * 16});
+    for (int k = 0; k < 3; ++k) {
+        if (k == idx->cur) continue;
+        v.push_back({&idx->dict[k].blocks, (size_t)dict_blocks(n_final) * sizeof(OccBlock)});
+        v.push_back({&idx->dict[k].super, (size_t)dict_supers(n_final) * 32});
+        v.push_back({&idx->dict[k].C, 32});
+    }
+    return v;
+}
+
+// Budget check first (nothing changes on failure), then growth.
+int reserve(sbwt_index* idx, const std::vector<Need>& needs) {
+    size_t total = idx->held_bytes();
+    for (const Need& n : needs) {
+        size_t want = (n.bytes + 255) & ~(size_t)255;
+        if (want > n.buf->bytes) total += want - n.buf->bytes;
+    }
+    if (idx->budget && total > idx->budget) return SBWT_ENOMEM;
+    for (const Need& n : needs)
+        if (int rc = grow(*n.buf, n.bytes)) return rc;
+    return SBWT_OK;
+}
+
+template <class IdxT>
+void run_block(sbwt_index* idx, const BlockPlan& bp, const uint64_t* d_offsets, const Dict& src, Dict& dst,
+               uint64_t n_ext, uint64_t m_ext, size_t slots, size_t k) {
+    Launcher& L = idx->L;
+    const uint32_t n = (uint32_t)bp.n_int;
+    SuffixSortBuffers b;
+    b.keys = (unsigned long long*)idx->keys.p;
+    b.keys_alt = (unsigned long long*)idx->keys_alt.p;
+    b.vals = (uint32_t*)idx->vals.p;
+    b.vals_alt = (uint32_t*)idx->vals_alt.p;
+    b.sa = (uint32_t*)idx->sa.p;
+    b.rank = (uint32_t*)idx->rank.p;
+    b.tmp_a = (uint32_t*)idx->tmp_a.p;
+    b.tmp_b = (uint32_t*)idx->tmp_b.p;
+    b.act_pos[0] = (uint32_t*)idx->act_pos0.p;
+    b.act_pos[1] = (uint32_t*)idx->act_pos1.p;
+    b.act_suf[0] = (uint32_t*)idx->act_suf0.p;
+    b.act_suf[1] = (uint32_t*)idx->act_suf1.p;
+    b.radix_temp = (uint32_t*)idx->radix_temp.p;
+    b.scan_temp = (uint32_t*)idx->scan_temp.p;
+    b.count_log = (uint32_t*)idx->count_log.p + slots * k;
+    b.err = (uint32_t*)idx->err.p;
+    const uint32_t* text = (const uint32_t*)idx->text.p;
+    const uint32_t* term = (const uint32_t*)idx->term.p;
+
+    suffix_sort_block(L, text, term, bp.base, n, (uint32_t)bp.max_len, b);
+    launch_bint(L, text, term, bp.base, b.sa, n, (uint8_t*)idx->bint.p);
+    launch_compute_ranks<IdxT>(L, text, d_offsets, bp.j0, bp.j1 - bp.j0, bp.n_int, (const OccBlock*)src.blocks.p,
+                               (const unsigned long long*)src.super.p, (const unsigned long long*)src.C.p, n_ext,
+                               m_ext, (IdxT*)idx->g.p, (uint32_t*)idx->err.p);
+    launch_gather<IdxT>(L, b.sa, (const IdxT*)idx->g.p, n, (IdxT*)idx->gsa.p);
+    launch_insert<IdxT>(L, (const OccBlock*)src.blocks.p, n_ext, (const uint8_t*)idx->bint.p,
+                        (const IdxT*)idx->gsa.p, bp.n_int, (OccBlock*)dst.blocks.p,
+                        (unsigned long long*)dst.super.p, (unsigned long long*)dst.C.p, m_ext + (bp.j1 - bp.j0),
+                        (uint32_t*)idx->sb_tot.p);
+}
+
+int append_impl(sbwt_index* idx, const uint8_t* d_reads, const uint64_t* d_offsets, const uint64_t* h_off,
+                uint64_t m_new, bool host_input, const uint8_t* h_reads) {
+    Plan p;
+    p.nbytes = h_off[m_new];
+    p.npos = p.nbytes + m_new;
+    p.blocks = plan_blocks(h_off, m_new, idx->M);
+    for (const BlockPlan& b : p.blocks) {
+        p.cap = std::max(p.cap, b.n_int);
+        p.max_len = std::max(p.max_len, b.max_len);
+    }
+    p.slots = suffix_sort_log_slots((uint32_t)p.max_len);
+    const uint64_t n_final = idx->n + p.npos;
+    if (idx->index_bits == 32 && n_final >= 0xFFFFFFFFull) return SBWT_EINVAL;
+    p.idx64 = idx->index_bits == 64 || n_final >= 0xFFFFFFFFull;
+
+    if (int rc = device_init(idx)) return rc;
+    if (int rc = reserve(idx, buffer_needs(idx, p, host_input, m_new))) return rc;
+    cudaStream_t s = idx->stream;
+    Launcher& L = idx->L;
+    L.unit_log = (const uint32_t*)idx->count_log.p;
+    L.unit_log_len = p.slots * p.blocks.size();
+
+    if (host_input) {
+        if (p.nbytes) cudaMemcpyAsync(idx->reads.p, h_reads, p.nbytes, cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(idx->offsets.p, h_off, (m_new + 1) * 8, cudaMemcpyHostToDevice, s);
+        d_reads = (const uint8_t*)idx->reads.p;
+        d_offsets = (const uint64_t*)idx->offsets.p;
+    }
+    // pack + validate before anything of the index changes
+    const uint64_t text_words = (p.npos + 31) / 32 * 2, term_words = (p.npos + 31) / 32;
+    cudaMemsetAsync((uint32_t*)idx->text.p + text_words, 0, kTextPadWords * 4, s);
+    cudaMemsetAsync((uint32_t*)idx->term.p + term_words, 0, kTermPadWords * 4, s);
+    cudaMemsetAsync(idx->err.p, 0, 4, s);
+    launch_pack(L, d_reads, d_offsets, m_new, p.npos, idx->alpha4, idx->sigma, (uint32_t*)idx->text.p,
+                (uint32_t*)idx->term.p, (uint32_t*)idx->err.p);
+    cudaMemcpyAsync(idx->h_err, idx->err.p, 4, cudaMemcpyDeviceToHost, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) return SBWT_EDEVICE;
+    if (*idx->h_err) {
+        L.resolve();
+        return SBWT_EINVAL;
+    }
+
+    int other[2], o = 0;
+    for (int k = 0; k < 3; ++k)
+        if (k != idx->cur) other[o++] = k;
+    int src = idx->cur;
+    uint64_t n_ext = idx->n, m_ext = idx->m;
+    for (size_t k = 0; k < p.blocks.size(); ++k) {
+        const BlockPlan& bp = p.blocks[k];
+        const int dst = other[k & 1];
+        if (p.idx64)
+            run_block<unsigned long long>(idx, bp, d_offsets, idx->dict[src], idx->dict[dst], n_ext, m_ext, p.slots,
+                                          k);
+        else
+            run_block<uint32_t>(idx, bp, d_offsets, idx->dict[src], idx->dict[dst], n_ext, m_ext, p.slots, k);
+        n_ext += bp.n_int;
+        m_ext += bp.j1 - bp.j0;
+        src = dst;
+    }
+    cudaMemcpyAsync(idx->h_err, idx->err.p, 4, cudaMemcpyDeviceToHost, s);
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) return SBWT_EDEVICE;
+    if (*idx->h_err) {  // a kernel caught an inconsistent index; keep the old one
+        L.resolve();
+        return SBWT_EDEVICE;
+    }
+    idx->cur = src;
+    idx->n = n_ext;
+    idx->m = m_ext;
+    idx->last_valid = !p.blocks.empty();
+    idx->last_n = p.blocks.empty() ? 0 : p.blocks.back().n_int;
+    idx->last_idx64 = p.idx64;
+    if (L.resolve() != cudaSuccess) return SBWT_EDEVICE;
+    return SBWT_OK;
+}
+
+int parse_alphabet(const char* alphabet, sbwt_index* idx) {
+    if (!alphabet) return SBWT_EINVAL;
+    size_t len = strlen(alphabet);
+    if (len < 1 || len > 4) return SBWT_EINVAL;
+    for (size_t a = 0; a < len; ++a) {
+        uint8_t c = (uint8_t)alphabet[a];
+        if (c == '$') return SBWT_EINVAL;
+        if (a > 0 && c <= (uint8_t)alphabet[a - 1]) return SBWT_EINVAL;
+        idx->alphabet[a] = c;
+    }
+    idx->sigma = (int)len;
+    idx->alpha4 = 0;
+    for (int a = 0; a < 4; ++a) idx->alpha4 |= (uint32_t)idx->alphabet[a < (int)len ? a : 0] << (8 * a);
+    return SBWT_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Launcher
+// ---------------------------------------------------------------------------
+namespace sbwt {
+
+cudaEvent_t Launcher::take_event() {
+    if (!free_events_.empty()) {
+        cudaEvent_t e = free_events_.back();
+        free_events_.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+int Launcher::stat_index(const char* name) {
+    for (size_t i = 0; i < stats.size(); ++i)
+        if (stats[i].name == name) return (int)i;
+    KernelStat k;
+    k.name = name;
+    stats.push_back(k);
+    return (int)stats.size() - 1;
+}
+
+int Launcher::before(const char* name, double fixed, double per_unit, const uint32_t* d_units) {
+    const int s = stat_index(name);
+    stats[s].launches++;
+    if (!profiling) return -1;
+    Pending p{s, take_event(), take_event(), fixed, per_unit, d_units};
+    cudaEventRecord(p.a, stream);
+    pending_.push_back(p);
+    return (int)pending_.size() - 1;
+}
+
+void Launcher::after(int token) {
+    if (token >= 0) cudaEventRecord(pending_[token].b, stream);
+}
+
+cudaError_t Launcher::resolve() {
+    if (pending_.empty()) return cudaSuccess;
+    std::vector<uint32_t> log(unit_log_len);
+    cudaError_t err = cudaSuccess;
+    if (unit_log_len) err = cudaMemcpy(log.data(), unit_log, unit_log_len * 4, cudaMemcpyDeviceToHost);
+    for (const Pending& p : pending_) {
+        float ms = 0;
+        if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) stats[p.stat].ms += ms;
+        double units = 0;
+        if (p.units) {
+            if (p.units >= unit_log && p.units < unit_log + unit_log_len) {
+                units = log[p.units - unit_log];
+            } else {
+                uint32_t u = 0;
+                cudaMemcpy(&u, p.units, 4, cudaMemcpyDeviceToHost);
+                units = u;
+            }
+        }
+        stats[p.stat].bytes += p.fixed + p.per_unit * units;
+        free_events_.push_back(p.a);
+        free_events_.push_back(p.b);
+    }
+    pending_.clear();
+    cudaGetLastError();
+    return err;
+}
+
+void Launcher::reset() {
+    for (KernelStat& k : stats) {
+        k.launches = 0;
+        k.ms = 0;
+        k.bytes = 0;
+    }
+}
+
+void Launcher::release() {
+    for (const Pending& p : pending_) {
+        cudaEventDestroy(p.a);
+        cudaEventDestroy(p.b);
+    }
+    pending_.clear();
+    for (cudaEvent_t e : free_events_) cudaEventDestroy(e);
+    free_events_.clear();
+}
+
+}  // namespace sbwt
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char* sbwt_strerror(int code) {
+    switch (code) {
+        case SBWT_OK: return "ok";
+        case SBWT_EINVAL: return "invalid argument or input";
+        case SBWT_ENOMEM: return "out of device memory or over the HBM budget";
+        case SBWT_ERANGE: return "output buffer too small";
+        case SBWT_EDEVICE: return "CUDA device error";
+        case SBWT_ENOTSUP: return "not supported";
+        default: return "unknown error";
+    }
+}
+
+int sbwt_create_ex(const char* alphabet, size_t hbm_budget_bytes, const sbwt_options* opt, sbwt_index** out) {
+    if (!out) return SBWT_EINVAL;
+    *out = nullptr;
+    sbwt_index* idx = new (std::nothrow) sbwt_index();
+    if (!idx) return SBWT_ENOMEM;
+    if (parse_alphabet(alphabet, idx)) {
+        delete idx;
+        return SBWT_EINVAL;
+    }
+    idx->budget = hbm_budget_bytes;
+    if (opt) {
+        bool bad = opt->index_bits != 0 && opt->index_bits != 32 && opt->index_bits != 64;
+        bad |= opt->block_suffixes > kMaxBlock;
+        for (uint32_t r : opt->reserved) bad |= r != 0;
+        if (bad) {
+            delete idx;
+            return SBWT_EINVAL;
+        }
+        idx->index_bits = opt->index_bits;
+        if (opt->block_suffixes) idx->M = opt->block_suffixes;
+        idx->stream = (cudaStream_t)opt->stream;
+        idx->device = opt->device;
+    }
+    *out = idx;
+    return SBWT_OK;
+}
+
+int sbwt_create(const char* alphabet, size_t hbm_budget_bytes, sbwt_index** out) {
+    return sbwt_create_ex(alphabet, hbm_budget_bytes, nullptr, out);
+}
+
+int sbwt_append(sbwt_index* idx, const uint8_t* reads, const uint64_t* offsets, uint64_t m) {
+    if (!idx || !offsets) return SBWT_EINVAL;
+    if (validate_offsets(offsets, m)) return SBWT_EINVAL;
+    if (m == 0) return SBWT_OK;
+    if (offsets[m] > 0 && !reads) return SBWT_EINVAL;
+    return append_impl(idx, nullptr, nullptr, offsets, m, true, reads);
+}
+
+int sbwt_append_device(sbwt_index* idx, const uint8_t* d_reads, const uint64_t* d_offsets, uint64_t m) {
+    if (!idx || !d_offsets) return SBWT_EINVAL;
+    if (int rc = device_init(idx)) return rc;
+    if (m + 1 > idx->h_offsets_cap) {
+        if (idx->h_offsets) cudaFreeHost(idx->h_offsets);
+        idx->h_offsets = nullptr;
+        idx->h_offsets_cap = 0;
+        if (cudaMallocHost(&idx->h_offsets, (m + 1) * 8) != cudaSuccess) return SBWT_ENOMEM;
+        idx->h_offsets_cap = m + 1;
+    }
+    if (cudaMemcpyAsync(idx->h_offsets, d_offsets, (m + 1) * 8, cudaMemcpyDeviceToHost, idx->stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(idx->stream) != cudaSuccess)
+        return SBWT_EDEVICE;
+    if (validate_offsets(idx->h_offsets, m)) return SBWT_EINVAL;
+    if (m == 0) return SBWT_OK;
+    if (idx->h_offsets[m] > 0 && !d_reads) return SBWT_EINVAL;
+    return append_impl(idx, d_reads, d_offsets, idx->h_offsets, m, false, nullptr);
+}
+
+int sbwt_get_bwt(sbwt_index* idx, uint8_t* out, uint64_t cap, uint64_t* n_out) {
+    if (!idx || !n_out) return SBWT_EINVAL;
+    *n_out = idx->n;
+    if (cap < idx->n) return SBWT_ERANGE;
+    if (idx->n == 0) return SBWT_OK;
+    if (!out) return SBWT_EINVAL;
+    if (int rc = device_init(idx)) return rc;
+    if (int rc = reserve(idx, {{&idx->out_bytes, (size_t)idx->n}})) return rc;
+    launch_unpack(idx->L, (const OccBlock*)idx->dict[idx->cur].blocks.p, idx->n, idx->alpha4,
+                  (uint8_t*)idx->out_bytes.p);
+    cudaMemcpyAsync(out, idx->out_bytes.p, idx->n, cudaMemcpyDeviceToHost, idx->stream);
+    if (cudaStreamSynchronize(idx->stream) != cudaSuccess || cudaGetLastError() != cudaSuccess) return SBWT_EDEVICE;
+    idx->L.resolve();
+    return SBWT_OK;
+}
+
+int sbwt_rank_batch(sbwt_index* idx, const uint8_t* cs, const uint64_t* ks, uint64_t q, uint64_t* out) {
+    if (!idx || (q && (!cs || !ks || !out))) return SBWT_EINVAL;
+    std::vector<uint8_t> codes(q);
+    for (uint64_t i = 0; i < q; ++i) {
+        if (ks[i] > idx->n) return SBWT_EINVAL;
+        int code = -1;
+        if (cs[i] == '$') code = 4;
+        for (int a = 0; a < idx->sigma; ++a)
+            if (cs[i] == idx->alphabet[a]) code = a;
+        if (code < 0) return SBWT_EINVAL;
+        codes[i] = (uint8_t)code;
+    }
+    if (q == 0) return SBWT_OK;
+    if (int rc = device_init(idx)) return rc;
+    if (int rc = reserve(idx, {{&idx->q_codes, (size_t)q}, {&idx->q_ks, (size_t)q * 8}, {&idx->q_out, (size_t)q * 8}}))
+        return rc;
+    cudaStream_t s = idx->stream;
+    cudaMemcpyAsync(idx->q_codes.p, codes.data(), q, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(idx->q_ks.p, ks, q * 8, cudaMemcpyHostToDevice, s);
+    const Dict& d = idx->dict[idx->cur];
+    launch_rank_batch(idx->L, (const OccBlock*)d.blocks.p, (const unsigned long long*)d.super.p,
+                      (const uint8_t*)idx->q_codes.p, (const unsigned long long*)idx->q_ks.p, q,
+                      (unsigned long long*)idx->q_out.p);
+    cudaMemcpyAsync(out, idx->q_out.p, q * 8, cudaMemcpyDeviceToHost, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) return SBWT_EDEVICE;
+    idx->L.resolve();
+    return SBWT_OK;
+}
+
+int sbwt_rank(sbwt_index* idx, uint8_t c, uint64_t k, uint64_t* out) {
+    if (!out) return SBWT_EINVAL;
+    return sbwt_rank_batch(idx, &c, &k, 1, out);
+}
+
+int sbwt_size(const sbwt_index* idx, uint64_t* n, uint64_t* m) {
+    if (!idx) return SBWT_EINVAL;
+    if (n) *n = idx->n;
+    if (m) *m = idx->m;
+    return SBWT_OK;
+}
+
+int sbwt_reset(sbwt_index* idx) {
+    if (!idx) return SBWT_EINVAL;
+    idx->n = idx->m = 0;
+    idx->last_valid = false;
+    if (!idx->dev_ready) return SBWT_OK;
+    if (set_device(idx)) return SBWT_EDEVICE;
+    Dict& d = idx->dict[idx->cur];
+    cudaMemsetAsync(d.blocks.p, 0, sizeof(OccBlock), idx->stream);
+    cudaMemsetAsync(d.super.p, 0, 32, idx->stream);
+    cudaMemsetAsync(d.C.p, 0, 32, idx->stream);
+    if (cudaStreamSynchronize(idx->stream) != cudaSuccess) return SBWT_EDEVICE;
+    return SBWT_OK;
+}
+
+void sbwt_destroy(sbwt_index* idx) {
+    if (!idx) return;
+    if (idx->dev_ready) {
+        set_device(idx);
+        cudaStreamSynchronize(idx->stream);
+        idx->L.release();
+        for (DevBuf* b : idx->all_bufs()) free_buf(*b);
+        if (idx->h_err) cudaFreeHost(idx->h_err);
+        if (idx->h_offsets) cudaFreeHost(idx->h_offsets);
+        if (idx->own_stream) cudaStreamDestroy(idx->stream);
+    }
+    delete idx;
+}
+
+int sbwt_get_stream(sbwt_index* idx, void** stream) {
+    if (!idx || !stream) return SBWT_EINVAL;
+    if (int rc = device_init(idx)) return rc;
+    *stream = (void*)idx->stream;
+    return SBWT_OK;
+}
+
+int sbwt_set_capture(sbwt_index* idx, int on) {
+    if (!idx) return SBWT_EINVAL;
+    idx->capture = on != 0;
+    idx->last_valid = false;
+    return SBWT_OK;
+}
+
+int sbwt_get_stage(sbwt_index* idx, int stage, void* out, uint64_t cap, uint64_t* count_out) {
+    if (!idx || !count_out) return SBWT_EINVAL;
+    if (!idx->capture || !idx->last_valid) return SBWT_EINVAL;
+    const uint64_t n = idx->last_n;
+    *count_out = n;
+    size_t elem = 0;
+    const void* src = nullptr;
+    switch (stage) {
+        case SBWT_STAGE_SA: elem = 4; src = idx->sa.p; break;
+        case SBWT_STAGE_BINT: elem = 1; src = idx->bint.p; break;
+        case SBWT_STAGE_G: elem = 8; src = idx->g.p; break;
+        case SBWT_STAGE_GSA: elem = 8; src = idx->gsa.p; break;
+        default: return SBWT_EINVAL;
+    }
+    if (cap < n * elem) return SBWT_ERANGE;
+    if (n == 0) return SBWT_OK;
+    if (!out) return SBWT_EINVAL;
+    if (set_device(idx)) return SBWT_EDEVICE;
+    if ((stage == SBWT_STAGE_G || stage == SBWT_STAGE_GSA) && !idx->last_idx64) {
+        std::vector<uint32_t> tmp(n);
+        if (cudaMemcpy(tmp.data(), src, n * 4, cudaMemcpyDeviceToHost) != cudaSuccess) return SBWT_EDEVICE;
+        uint64_t* o = (uint64_t*)out;
+        for (uint64_t i = 0; i < n; ++i) o[i] = tmp[i];
+        return SBWT_OK;
+    }
+    if (cudaMemcpy(out, src, n * elem, cudaMemcpyDeviceToHost) != cudaSuccess) return SBWT_EDEVICE;
+    return SBWT_OK;
+}
+
+int sbwt_set_profiling(sbwt_index* idx, int on) {
+    if (!idx) return SBWT_EINVAL;
+    idx->L.profiling = on != 0;
+    return SBWT_OK;
+}
+
+int sbwt_get_kernel_stats(sbwt_index* idx, sbwt_kernel_stat* out, int cap, int* n_out) {
+    if (!idx || !n_out) return SBWT_EINVAL;
+    const auto& st = idx->L.stats;
+    *n_out = (int)st.size();
+    for (int i = 0; i < cap && i < (int)st.size(); ++i) {
+        memset(&out[i], 0, sizeof(out[i]));
+        strncpy(out[i].name, st[i].name.c_str(), sizeof(out[i].name) - 1);
+        out[i].launches = st[i].launches;
+        out[i].ms = st[i].ms;
+        out[i].bytes = st[i].bytes;
+    }
+    return SBWT_OK;
+}
+
+int sbwt_reset_kernel_stats(sbwt_index* idx) {
+    if (!idx) return SBWT_EINVAL;
+    idx->L.reset();
+    return SBWT_OK;
+}
+
+}  // extern "C"

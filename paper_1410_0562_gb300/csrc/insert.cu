@@ -1,0 +1,220 @@
+// insert.cu -- Insert (arXiv 1410.0562, Algorithm 1 and Section 5) as one
+// stable parallel merge that writes the next rank dictionary.
+//
+// New symbol i (in SA_int order) lands on row g_sa[i] + i of the result: the
+// g_sa[i] old rows below it plus the i new symbols before it.  New symbols
+// with equal g_sa keep their SA_int order and go before old row g_sa (they
+// are smaller: Lemma 1's g counts the old suffixes below the new one, and old
+// and new suffixes never tie because their terminators differ).  Old rows
+// keep their relative order.
+//
+// One CTA builds one superblock (1024 occurrence blocks of 64 rows), four
+// consecutive blocks per thread.  For output block b (rows [o, o+64)) a binary
+// search finds i0 = |{i : g_sa[i] + i < o}|; the block then holds the old rows
+// starting at o - i0, into which the new symbols with final rows in [o, o+64)
+// are spliced in ascending order.  Per-block counts are scanned across the
+// CTA for the 16-bit block counters; a one-CTA pass scans the superblock
+// totals into the 64-bit superblock counters and C[] (Lemma 1's C[c] counts
+// every smaller symbol, the terminators included).
+#include "sbwt_kernels.cuh"
+
+namespace sbwt {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kPerThread = kBlocksPerSuper / kThreads;  // 4
+static_assert(kPerThread == 4, "four output blocks per thread");
+
+struct Window {
+    unsigned long long w0, w1, dm;
+};
+
+// 64 old rows starting at row s (rows past the old end read as zero).
+__device__ __forceinline__ Window old_window(const OccBlock* __restrict__ old_blocks, uint64_t nb_old, uint64_t s) {
+    const uint64_t bs = s >> kOccShift;
+    const uint32_t off = (uint32_t)(s & (kOccSpan - 1));
+    const OccBlock& A = old_blocks[bs];
+    const unsigned long long a0 = A.sym[0], a1 = A.sym[1], da = A.dmask;
+    unsigned long long a2 = 0, a3 = 0, db = 0;
+    if (bs + 1 < nb_old) {
+        const OccBlock& B = old_blocks[bs + 1];
+        a2 = B.sym[0];
+        a3 = B.sym[1];
+        db = B.dmask;
+    }
+    Window w;
+    const uint32_t sh = 2 * off;  // 0 .. 126 bits
+    if (sh == 0) {
+        w.w0 = a0;
+        w.w1 = a1;
+    } else if (sh < 64) {
+        w.w0 = (a0 >> sh) | (a1 << (64 - sh));
+        w.w1 = (a1 >> sh) | (a2 << (64 - sh));
+    } else if (sh == 64) {
+        w.w0 = a1;
+        w.w1 = a2;
+    } else {
+        const uint32_t s2 = sh - 64;
+        w.w0 = (a1 >> s2) | (a2 << (64 - s2));
+        w.w1 = (a2 >> s2) | (a3 << (64 - s2));
+    }
+    w.dm = off == 0 ? da : ((da >> off) | (db << (64 - off)));
+    return w;
+}
+
+// Splice one row holding `code` (terminator when dollar) in at position p of
+// the 64-row window; rows p.. move up by one and row 63 falls off.
+__device__ __forceinline__ void splice(Window& w, uint32_t p, uint32_t code, uint32_t dollar) {
+    if (p < 32) {
+        w.w1 = (w.w1 << 2) | (w.w0 >> 62);
+        const unsigned long long keep = low_bits(2 * p);
+        w.w0 = (w.w0 & keep) | ((unsigned long long)code << (2 * p)) | ((w.w0 & ~keep) << 2);
+    } else {
+        const uint32_t q = p - 32;
+        const unsigned long long keep = low_bits(2 * q);
+        w.w1 = (w.w1 & keep) | ((unsigned long long)code << (2 * q)) | ((w.w1 & ~keep) << 2);
+    }
+    const unsigned long long keepd = low_bits(p);
+    w.dm = (w.dm & keepd) | ((unsigned long long)dollar << p) | ((w.dm & ~keepd) << 1);
+}
+
+template <class IdxT>
+__global__ void __launch_bounds__(kThreads) insert_kernel(const OccBlock* __restrict__ old_blocks,
+                                                          unsigned long long n_ext, const uint8_t* __restrict__ bint,
+                                                          const IdxT* __restrict__ gsa, unsigned long long n_int,
+                                                          OccBlock* __restrict__ new_blocks,
+                                                          unsigned long long n_new, uint32_t* __restrict__ sb_tot) {
+    const uint64_t nb_new = (n_new >> kOccShift) + 1;
+    const uint64_t nb_old = (n_ext >> kOccShift) + 1;
+    const uint64_t b0 = (uint64_t)blockIdx.x * kBlocksPerSuper + (uint64_t)threadIdx.x * kPerThread;
+    Window win[kPerThread];
+    uint32_t cnt[kPerThread][4];
+#pragma unroll
+    for (int bb = 0; bb < kPerThread; ++bb) {
+        win[bb].w0 = win[bb].w1 = win[bb].dm = 0;
+        cnt[bb][0] = cnt[bb][1] = cnt[bb][2] = cnt[bb][3] = 0;
+    }
+    if (b0 < nb_new) {
+        uint64_t lo = 0, hi = n_int;  // first i with g_sa[i] + i >= o
+        const uint64_t o0 = b0 << kOccShift;
+        while (lo < hi) {
+            const uint64_t mid = lo + ((hi - lo) >> 1);
+            if ((uint64_t)gsa[mid] + mid < o0) lo = mid + 1; else hi = mid;
+        }
+        uint64_t i = lo;
+#pragma unroll
+        for (int bb = 0; bb < kPerThread; ++bb) {
+            const uint64_t b = b0 + bb;
+            if (b >= nb_new) break;
+            const uint64_t o = b << kOccShift;
+            // o - i old rows precede this block; clamped so a bad g_sa can
+            // never send the window past the old dictionary
+            const uint64_t s_old = o >= i ? min((unsigned long long)(o - i), n_ext) : 0ull;
+            Window w = old_window(old_blocks, nb_old, s_old);
+            while (i < n_int) {
+                const uint64_t row = (uint64_t)gsa[i] + i;
+                if (row >= o + kOccSpan) break;
+                const uint8_t x = bint[i];
+                splice(w, (uint32_t)(row - o), x == kBintDollar ? 0u : x, x == kBintDollar ? 1u : 0u);
+                ++i;
+            }
+            const uint32_t valid = n_new > o ? (uint32_t)min((unsigned long long)kOccSpan, n_new - o) : 0u;
+            const unsigned long long v0 = low_bits(2 * min(valid, 32u));
+            const unsigned long long v1 = valid > 32 ? low_bits(2 * (valid - 32)) : 0ull;
+            w.w0 &= v0;
+            w.w1 &= v1;
+            w.dm &= low_bits(valid);
+#pragma unroll
+            for (uint32_t c = 0; c < 4; ++c)
+                cnt[bb][c] = __popcll(match_code(w.w0, c) & v0) + __popcll(match_code(w.w1, c) & v1);
+            cnt[bb][0] -= __popcll(w.dm);
+            win[bb] = w;
+        }
+    }
+    // 16-bit block counters: exclusive scan of the per-thread totals.
+    unsigned long long t01 = 0, t23 = 0;
+#pragma unroll
+    for (int bb = 0; bb < kPerThread; ++bb) {
+        t01 += (unsigned long long)cnt[bb][0] | ((unsigned long long)cnt[bb][1] << 32);
+        t23 += (unsigned long long)cnt[bb][2] | ((unsigned long long)cnt[bb][3] << 32);
+    }
+    unsigned long long tot01, tot23;
+    const unsigned long long e01 = cta_exclusive_scan<SumOp, kThreads>(t01, tot01);
+    const unsigned long long e23 = cta_exclusive_scan<SumOp, kThreads>(t23, tot23);
+    uint32_t pref[4] = {(uint32_t)e01, (uint32_t)(e01 >> 32), (uint32_t)e23, (uint32_t)(e23 >> 32)};
+#pragma unroll
+    for (int bb = 0; bb < kPerThread; ++bb) {
+        const uint64_t b = b0 + bb;
+        if (b >= nb_new) break;
+        OccBlock out;
+        out.sym[0] = win[bb].w0;
+        out.sym[1] = win[bb].w1;
+        out.dmask = win[bb].dm;
+        out.cnt = (unsigned long long)pref[0] | ((unsigned long long)pref[1] << 16) |
+                  ((unsigned long long)pref[2] << 32) | ((unsigned long long)pref[3] << 48);
+        ulonglong2* dst = reinterpret_cast<ulonglong2*>(new_blocks + b);
+        dst[0] = make_ulonglong2(out.sym[0], out.sym[1]);
+        dst[1] = make_ulonglong2(out.dmask, out.cnt);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) pref[c] += cnt[bb][c];
+    }
+    if (threadIdx.x == 0) {
+        uint32_t* t = sb_tot + 4ull * blockIdx.x;
+        t[0] = (uint32_t)tot01;
+        t[1] = (uint32_t)(tot01 >> 32);
+        t[2] = (uint32_t)tot23;
+        t[3] = (uint32_t)(tot23 >> 32);
+    }
+}
+
+constexpr int kScanThreads = 1024;
+
+__global__ void __launch_bounds__(kScanThreads) super_scan_kernel(const uint32_t* __restrict__ sb_tot,
+                                                                  unsigned long long nsb,
+                                                                  unsigned long long* __restrict__ super,
+                                                                  unsigned long long* __restrict__ C,
+                                                                  unsigned long long m) {
+    unsigned long long carry[4] = {0, 0, 0, 0};
+    for (unsigned long long base = 0; base < nsb; base += kScanThreads) {
+        const unsigned long long s = base + threadIdx.x;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const unsigned long long v = s < nsb ? sb_tot[4 * s + c] : 0ull;
+            unsigned long long tot;
+            const unsigned long long ex = cta_exclusive_scan<SumOp, kScanThreads>(v, tot);
+            if (s < nsb) super[4 * s + c] = carry[c] + ex;
+            carry[c] += tot;
+        }
+    }
+    if (threadIdx.x == 0) {
+        C[0] = m;
+        C[1] = m + carry[0];
+        C[2] = C[1] + carry[1];
+        C[3] = C[2] + carry[2];
+    }
+}
+
+}  // namespace
+
+template <class IdxT>
+void launch_insert(Launcher& L, const OccBlock* old_blocks, uint64_t n_ext, const uint8_t* bint, const IdxT* gsa,
+                   uint64_t n_int, OccBlock* new_blocks, unsigned long long* new_super, unsigned long long* new_C,
+                   uint64_t m_new, uint32_t* sb_tot) {
+    const uint64_t n_new = n_ext + n_int;
+    const uint64_t nsb = dict_supers(n_new);
+    const double bytes = 32.0 * dict_blocks(n_ext) + (1.0 + sizeof(IdxT)) * n_int + 32.0 * dict_blocks(n_new);
+    SBWT_LAUNCH(L, "insert_merge", bytes, 0, nullptr, insert_kernel<IdxT>, (unsigned)nsb, kThreads, 0, old_blocks,
+                (unsigned long long)n_ext, bint, gsa, (unsigned long long)n_int, new_blocks,
+                (unsigned long long)n_new, sb_tot);
+    SBWT_LAUNCH(L, "super_scan", 48.0 * nsb, 0, nullptr, super_scan_kernel, 1, kScanThreads, 0, sb_tot,
+                (unsigned long long)nsb, new_super, new_C, (unsigned long long)m_new);
+}
+
+template void launch_insert<uint32_t>(Launcher&, const OccBlock*, uint64_t, const uint8_t*, const uint32_t*,
+                                      uint64_t, OccBlock*, unsigned long long*, unsigned long long*, uint64_t,
+                                      uint32_t*);
+template void launch_insert<unsigned long long>(Launcher&, const OccBlock*, uint64_t, const uint8_t*,
+                                                const unsigned long long*, uint64_t, OccBlock*,
+                                                unsigned long long*, unsigned long long*, uint64_t, uint32_t*);
+
+}  // namespace sbwt

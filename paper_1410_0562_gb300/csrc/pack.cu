@@ -1,0 +1,72 @@
+// pack.cu -- validates an append's reads against the alphabet and packs them
+// into the 2-bit text + terminator bitmap every later kernel reads.
+//
+// Position rule: read j's symbol k sits at offsets[j] + j + k and its
+// terminator at offsets[j+1] + j, i.e. every read is followed by one
+// terminator slot (T = S_0 $_0 S_1 $_1 ..., Section 2 of arXiv 1410.0562).
+// The byte behind position t of read j is therefore reads[t - j].
+#include "sbwt_internal.cuh"
+
+namespace sbwt {
+namespace {
+
+constexpr int kThreads = 256;
+
+// One thread per 32 positions: two MSB-first text words and one bitmap word.
+__global__ void __launch_bounds__(kThreads) pack_kernel(const uint8_t* __restrict__ reads,
+                                                        const unsigned long long* __restrict__ offsets,
+                                                        unsigned long long m, unsigned long long npos,
+                                                        uint32_t alpha4, int sigma, uint32_t* __restrict__ text,
+                                                        uint32_t* __restrict__ term,
+                                                        uint32_t* __restrict__ d_err) {
+    const uint64_t w = (uint64_t)blockIdx.x * kThreads + threadIdx.x;
+    const uint64_t t0 = w * 32;
+    if (t0 >= npos) return;
+    // read holding t0: the last j with offsets[j] + j <= t0
+    uint64_t lo = 0, hi = m;  // invariant: offsets[lo] + lo <= t0 < offsets[hi] + hi
+    while (hi - lo > 1) {
+        uint64_t mid = lo + (hi - lo) / 2;
+        if (offsets[mid] + mid <= t0) lo = mid; else hi = mid;
+    }
+    uint64_t j = lo;
+    uint64_t end_j = offsets[j + 1] + j;  // terminator position of read j
+    uint32_t tw[2] = {0u, 0u}, bw = 0u;
+    bool bad = false;
+    const uint32_t a0 = alpha4 & 0xFF, a1 = (alpha4 >> 8) & 0xFF, a2 = (alpha4 >> 16) & 0xFF, a3 = alpha4 >> 24;
+    for (int q = 0; q < 32; ++q) {
+        const uint64_t t = t0 + q;
+        if (t >= npos) break;
+        uint32_t code = 0;
+        if (t == end_j) {
+            bw |= 1u << q;
+            ++j;
+            if (j < m) end_j = offsets[j + 1] + j;
+        } else {
+            const uint32_t b = reads[t - j];
+            if (b == a0) code = 0;
+            else if (sigma > 1 && b == a1) code = 1;
+            else if (sigma > 2 && b == a2) code = 2;
+            else if (sigma > 3 && b == a3) code = 3;
+            else bad = true;
+        }
+        tw[q >> 4] |= code << (30 - 2 * (q & 15));
+    }
+    text[2 * w] = tw[0];
+    text[2 * w + 1] = tw[1];
+    term[w] = bw;
+    if (bad) atomicOr(d_err, 1u);
+}
+
+}  // namespace
+
+void launch_pack(Launcher& L, const uint8_t* d_reads, const uint64_t* d_offsets, uint64_t m, uint64_t npos,
+                 uint32_t alpha4, int sigma, uint32_t* text, uint32_t* term, uint32_t* d_err) {
+    const uint64_t words = (npos + 31) / 32;
+    if (words == 0) return;
+    const unsigned grid = ceil_div_u(words, kThreads);
+    SBWT_LAUNCH(L, "pack_reads", (double)(npos - m) + 8.0 * (m + 1) + npos / 4.0 + npos / 8.0, 0, nullptr,
+                pack_kernel, grid, kThreads, 0, d_reads, reinterpret_cast<const unsigned long long*>(d_offsets),
+                (unsigned long long)m, (unsigned long long)npos, alpha4, sigma, text, term, d_err);
+}
+
+}  // namespace sbwt

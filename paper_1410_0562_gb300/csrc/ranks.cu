@@ -1,0 +1,168 @@
+// ranks.cu -- B_int extraction, ComputeRanks, the g[SA_int] gather, rank
+// queries and the unpacking of B (arXiv 1410.0562, Algorithm 1 and
+// Algorithm 2 with Lemma 1).
+#include "sbwt_kernels.cuh"
+
+namespace sbwt {
+namespace {
+
+constexpr int kThreads = 256;
+
+// B_int[i]: the symbol before block suffix SA[i] inside its read, or a
+// terminator when the suffix starts its read (Eq. 1 restricted to the block).
+__global__ void __launch_bounds__(kThreads) bint_kernel(const uint32_t* __restrict__ text,
+                                                        const uint32_t* __restrict__ term, unsigned long long base,
+                                                        const uint32_t* __restrict__ sa, uint32_t n,
+                                                        uint8_t* __restrict__ bint) {
+    const uint32_t i = blockIdx.x * kThreads + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t t = sa[i] < n ? sa[i] : 0u;
+    const uint64_t P = base + t;
+    bint[i] = (t == 0 || is_term(term, P - 1)) ? kBintDollar : (uint8_t)text_code(text, P - 1);
+}
+
+// Algorithm 2, one thread per read: start at i = m_ext on the read's
+// terminator (it is larger than exactly the m_ext old terminators and smaller
+// than every old suffix that starts with a symbol), then walk the read
+// backwards with Lemma 1: i := C[c] + rank(c, i, B_ext), c = P[k-1].
+template <class IdxT>
+__global__ void __launch_bounds__(kThreads) compute_ranks_kernel(const uint32_t* __restrict__ text,
+                                                                 const unsigned long long* __restrict__ offsets,
+                                                                 unsigned long long j_begin,
+                                                                 unsigned long long nreads,
+                                                                 const OccBlock* __restrict__ blocks,
+                                                                 const unsigned long long* __restrict__ super,
+                                                                 const unsigned long long* __restrict__ d_C,
+                                                                 unsigned long long n_ext,
+                                                                 unsigned long long m_ext, IdxT* __restrict__ g,
+                                                                 uint32_t* __restrict__ d_err) {
+    const uint64_t j = (uint64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (j >= nreads) return;
+    const uint64_t jj = j_begin + j;
+    const uint64_t o0 = offsets[j_begin];
+    const uint64_t oj = offsets[jj];
+    const uint64_t len = offsets[jj + 1] - oj;
+    const uint64_t rs = oj - o0 + j;  // block-local position of the read's first symbol
+    const uint64_t P = oj + jj;       // the same position in the append's text
+    const unsigned long long C0 = d_C[0], C1 = d_C[1], C2 = d_C[2], C3 = d_C[3];
+    unsigned long long i = m_ext;
+    g[rs + len] = (IdxT)i;
+    uint64_t wcur = ~0ull;
+    uint32_t word = 0;
+    for (uint64_t k = len; k > 0; --k) {
+        const uint64_t t = P + k - 1;
+        if ((t >> 4) != wcur) {
+            wcur = t >> 4;
+            word = __ldg(text + wcur);
+        }
+        const uint32_t c = (word >> (30u - 2u * (uint32_t)(t & 15))) & 3u;
+        const unsigned long long Cc = c == 0 ? C0 : c == 1 ? C1 : c == 2 ? C2 : C3;
+        i = Cc + occ_rank(blocks, super, c, i);
+        if (i > n_ext) {
+            atomicOr(d_err, 8u);
+            i = n_ext;
+        }
+        g[rs + k - 1] = (IdxT)i;
+    }
+}
+
+template <class IdxT>
+__global__ void __launch_bounds__(kThreads) gather_kernel(const uint32_t* __restrict__ sa,
+                                                          const IdxT* __restrict__ g, uint32_t n,
+                                                          IdxT* __restrict__ gsa) {
+    const uint32_t i = blockIdx.x * kThreads + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t t = sa[i];
+    gsa[i] = t < n ? g[t] : (IdxT)0;
+}
+
+__global__ void __launch_bounds__(kThreads) rank_batch_kernel(const OccBlock* __restrict__ blocks,
+                                                              const unsigned long long* __restrict__ super,
+                                                              const uint8_t* __restrict__ codes,
+                                                              const unsigned long long* __restrict__ ks,
+                                                              unsigned long long q,
+                                                              unsigned long long* __restrict__ out) {
+    const uint64_t i = (uint64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (i >= q) return;
+    const uint32_t c = codes[i];
+    const unsigned long long k = ks[i];
+    if (c < 4) {
+        out[i] = occ_rank(blocks, super, c, k);
+    } else {  // terminators: every row before k that holds no symbol
+        unsigned long long s = 0;
+        for (uint32_t x = 0; x < 4; ++x) s += occ_rank(blocks, super, x, k);
+        out[i] = k - s;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) unpack_kernel(const OccBlock* __restrict__ blocks,
+                                                          unsigned long long n, uint32_t alpha4,
+                                                          uint8_t* __restrict__ out) {
+    const uint64_t r = (uint64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (r >= n) return;
+    const OccBlock& b = blocks[r >> kOccShift];
+    const uint32_t q = (uint32_t)(r & (kOccSpan - 1));
+    if ((b.dmask >> q) & 1ull) {
+        out[r] = (uint8_t)'$';
+    } else {
+        const uint32_t c = (uint32_t)(b.sym[q >> 5] >> (2 * (q & 31))) & 3u;
+        out[r] = (uint8_t)(alpha4 >> (8 * c));
+    }
+}
+
+}  // namespace
+
+void launch_bint(Launcher& L, const uint32_t* text, const uint32_t* term, uint64_t base, const uint32_t* sa,
+                 uint32_t n, uint8_t* bint) {
+    if (n == 0) return;
+    SBWT_LAUNCH(L, "extract_bint", (double)n * (4 + 1 + 4 + 4), 0, nullptr, bint_kernel, ceil_div_u(n, kThreads),
+                kThreads, 0, text, term, (unsigned long long)base, sa, n, bint);
+}
+
+template <class IdxT>
+void launch_compute_ranks(Launcher& L, const uint32_t* text, const uint64_t* d_offsets, uint64_t j_begin,
+                          uint64_t nreads, uint64_t n_int, const OccBlock* blocks, const unsigned long long* super,
+                          const unsigned long long* d_C, uint64_t n_ext, uint64_t m_ext, IdxT* g,
+                          uint32_t* d_err) {
+    if (nreads == 0) return;
+    // per suffix: one 32-byte occurrence block, a g write, a quarter byte of text
+    const double bytes = (double)(n_int - nreads) * (32.0 + 8.0) + (double)n_int * sizeof(IdxT) + n_int / 4.0 +
+                         16.0 * nreads;
+    SBWT_LAUNCH(L, "compute_ranks", bytes, 0, nullptr, compute_ranks_kernel<IdxT>, ceil_div_u(nreads, kThreads),
+                kThreads, 0, text, reinterpret_cast<const unsigned long long*>(d_offsets),
+                (unsigned long long)j_begin, (unsigned long long)nreads, blocks, super, d_C,
+                (unsigned long long)n_ext, (unsigned long long)m_ext, g, d_err);
+}
+
+template <class IdxT>
+void launch_gather(Launcher& L, const uint32_t* sa, const IdxT* g, uint32_t n, IdxT* gsa) {
+    if (n == 0) return;
+    SBWT_LAUNCH(L, "gather_gsa", (double)n * (4 + 2 * sizeof(IdxT)), 0, nullptr, gather_kernel<IdxT>,
+                ceil_div_u(n, kThreads), kThreads, 0, sa, g, n, gsa);
+}
+
+void launch_rank_batch(Launcher& L, const OccBlock* blocks, const unsigned long long* super, const uint8_t* codes,
+                       const unsigned long long* ks, uint64_t q, unsigned long long* out) {
+    if (q == 0) return;
+    SBWT_LAUNCH(L, "rank_query", (double)q * (1 + 8 + 32 + 8 + 8), 0, nullptr, rank_batch_kernel,
+                ceil_div_u(q, kThreads), kThreads, 0, blocks, super, codes, ks, (unsigned long long)q, out);
+}
+
+void launch_unpack(Launcher& L, const OccBlock* blocks, uint64_t n, uint32_t alpha4, uint8_t* out) {
+    if (n == 0) return;
+    SBWT_LAUNCH(L, "unpack_bwt", (double)n * (1 + 0.5), 0, nullptr, unpack_kernel, ceil_div_u(n, kThreads),
+                kThreads, 0, blocks, (unsigned long long)n, alpha4, out);
+}
+
+template void launch_compute_ranks<uint32_t>(Launcher&, const uint32_t*, const uint64_t*, uint64_t, uint64_t,
+                                             uint64_t, const OccBlock*, const unsigned long long*,
+                                             const unsigned long long*, uint64_t, uint64_t, uint32_t*, uint32_t*);
+template void launch_compute_ranks<unsigned long long>(Launcher&, const uint32_t*, const uint64_t*, uint64_t,
+                                                       uint64_t, uint64_t, const OccBlock*,
+                                                       const unsigned long long*, const unsigned long long*,
+                                                       uint64_t, uint64_t, unsigned long long*, uint32_t*);
+template void launch_gather<uint32_t>(Launcher&, const uint32_t*, const uint32_t*, uint32_t, uint32_t*);
+template void launch_gather<unsigned long long>(Launcher&, const uint32_t*, const unsigned long long*, uint32_t,
+                                                unsigned long long*);
+
+}  // namespace sbwt

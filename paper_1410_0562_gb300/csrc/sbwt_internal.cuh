@@ -1,0 +1,229 @@
+// sbwt_internal.cuh -- device data layouts and helpers shared by the kernels
+// of the GB300 set-bwte library (arXiv 1410.0562).  Nothing here is exported.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+namespace sbwt {
+
+// ---------------------------------------------------------------------------
+// Text of an append (all its blocks): one 2-bit code per position, terminator
+// positions hold code 0 and are flagged in a separate bitmap.  Position of
+// read j's symbol k is offsets[j] + j + k; its terminator sits at
+// offsets[j+1] + j (the block-local form of the same rule is the reading of
+// Algorithm 2's text index: the exclusive prefix sum of |P_l|+1, plus k).
+//   text[t >> 4] holds positions 16w .. 16w+15, MSB first: the code of t is
+//   at bits 30 - 2*(t & 15), so concatenated words compare like strings.
+//   term[t >> 5] bit (t & 31) is set iff t is a terminator.
+// Both arrays carry zeroed padding words past the end (kTextPadWords,
+// kTermPadWords) so fixed-width windows never read out of bounds.
+// ---------------------------------------------------------------------------
+constexpr int kTextPadWords = 4;
+constexpr int kTermPadWords = 2;
+
+__device__ __forceinline__ uint32_t text_code(const uint32_t* __restrict__ text, uint64_t t) {
+    return (text[t >> 4] >> (30u - 2u * (uint32_t)(t & 15))) & 3u;
+}
+__device__ __forceinline__ uint32_t is_term(const uint32_t* __restrict__ term, uint64_t t) {
+    return (term[t >> 5] >> (t & 31)) & 1u;
+}
+
+// ---------------------------------------------------------------------------
+// Rank dictionary over B (Section 5's occurrence counters, re-laid out for
+// one 32-byte sector per rank query).  Row r of B lives in occurrence block
+// r >> 6 (64 rows per block):
+//   sym[2]  : 2-bit codes, row q of the block at bits 2*(q & 31) of
+//             sym[q >> 5] (LSB first); a terminator is stored as code 0
+//   dmask   : bit q set iff row q holds a terminator
+//   cnt     : four 16-bit counts, count of code c (terminators excluded) in
+//             [superblock start, block start), at bits 16c
+// Superblocks span 2^16 rows; super[4*s + c] counts code c in [0, 2^16 s).
+// A dictionary of n rows has (n >> 6) + 1 blocks and (n >> 16) + 1
+// superblocks, so rank(c, n) needs no special case; rows >= n are zero.
+// rank(c, i) = super[4*(i>>16)+c] + cnt_c(block i>>6) + matches of c among
+// the first (i & 63) rows of the block, minus terminators when c == 0.
+// ---------------------------------------------------------------------------
+constexpr int kOccShift = 6;
+constexpr int kOccSpan = 1 << kOccShift;
+constexpr int kSuperShift = 16;
+constexpr int kBlocksPerSuper = 1 << (kSuperShift - kOccShift);  // 1024
+constexpr uint8_t kBintDollar = 255;                              // B_int code of a terminator
+
+struct __align__(32) OccBlock {
+    unsigned long long sym[2];
+    unsigned long long dmask;
+    unsigned long long cnt;
+};
+static_assert(sizeof(OccBlock) == 32, "one sector per occurrence block");
+
+__device__ __forceinline__ unsigned long long low_bits(uint32_t nbits) {
+    return nbits >= 64 ? ~0ull : ((1ull << nbits) - 1ull);
+}
+
+// Mask with bit 2q set for every 2-bit field q of x equal to code c.
+__device__ __forceinline__ unsigned long long match_code(unsigned long long x, uint32_t c) {
+    unsigned long long y = x ^ (0x5555555555555555ull * c);
+    return ~(y | (y >> 1)) & 0x5555555555555555ull;
+}
+
+// rank(c, i, B) for a symbol code c (Eq. 2), from one 32-byte block load.
+__device__ __forceinline__ unsigned long long occ_rank(const OccBlock* __restrict__ blocks,
+                                                       const unsigned long long* __restrict__ super,
+                                                       uint32_t c, unsigned long long i) {
+    const ulonglong2* p = reinterpret_cast<const ulonglong2*>(blocks + (i >> kOccShift));
+    ulonglong2 s = __ldg(p);
+    ulonglong2 d = __ldg(p + 1);
+    uint32_t r = (uint32_t)(i & (kOccSpan - 1));
+    unsigned long long m0 = match_code(s.x, c), m1 = match_code(s.y, c);
+    uint32_t in_block;
+    if (r <= 32) {
+        in_block = __popcll(m0 & low_bits(2 * r));
+    } else {
+        in_block = __popcll(m0) + __popcll(m1 & low_bits(2 * (r - 32)));
+    }
+    if (c == 0) in_block -= __popcll(d.x & low_bits(r));
+    uint32_t cnt = (uint32_t)(d.y >> (16 * c)) & 0xFFFFu;
+    return __ldg(super + ((i >> kSuperShift) << 2) + c) + cnt + in_block;
+}
+
+// ---------------------------------------------------------------------------
+// CTA-wide scans (warp shuffles + one shared array of warp totals).
+// ---------------------------------------------------------------------------
+struct SumOp {
+    template <class T>
+    __device__ __forceinline__ static T id() { return T(0); }
+    template <class T>
+    __device__ __forceinline__ static T f(T a, T b) { return a + b; }
+};
+struct MaxOp {  // identity 0: every scanned value is unsigned
+    template <class T>
+    __device__ __forceinline__ static T id() { return T(0); }
+    template <class T>
+    __device__ __forceinline__ static T f(T a, T b) { return a > b ? a : b; }
+};
+
+// Exclusive scan of one value per thread over a CTA of NT threads (NT a
+// multiple of 32, at most 1024).  Every thread must call it.  Returns the
+// exclusive prefix and sets `total` to the CTA-wide result.
+template <class Op, int NT, class T>
+__device__ __forceinline__ T cta_exclusive_scan(T v, T& total) {
+    constexpr int kW = NT / 32;
+    __shared__ T warp_tot[kW];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    T x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        T y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x = Op::f(y, x);
+    }
+    if (lane == 31) warp_tot[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        T w = lane < kW ? warp_tot[lane] : Op::template id<T>();
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            T y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w = Op::f(y, w);
+        }
+        if (lane < kW) warp_tot[lane] = w;
+    }
+    __syncthreads();
+    T excl = __shfl_up_sync(0xffffffffu, x, 1);
+    if (lane == 0) excl = Op::template id<T>();
+    T before = warp > 0 ? warp_tot[warp - 1] : Op::template id<T>();
+    total = warp_tot[kW - 1];
+    __syncthreads();
+    return Op::f(before, excl);
+}
+
+// ---------------------------------------------------------------------------
+// Launch bookkeeping: every kernel launch goes through a Launcher, which
+// counts it and (with profiling on) brackets it with CUDA events.  The
+// algorithmic bytes of a launch are `fixed` plus `per_unit` times a count
+// that may live in device memory (the number of elements a launch with a
+// device-side count actually processed); such counts must sit in the
+// Launcher's unit log so one copy resolves them all after the stream drains.
+// ---------------------------------------------------------------------------
+struct KernelStat {
+    std::string name;
+    uint64_t launches = 0;
+    double ms = 0;
+    double bytes = 0;
+};
+
+class Launcher {
+  public:
+    cudaStream_t stream = nullptr;
+    bool profiling = false;
+    std::vector<KernelStat> stats;
+    const uint32_t* unit_log = nullptr;  // device array of element counts
+    size_t unit_log_len = 0;
+
+    int before(const char* name, double fixed, double per_unit = 0, const uint32_t* d_units = nullptr);
+    void after(int token);
+    // Folds pending event pairs into stats; call with the stream idle.
+    cudaError_t resolve();
+    void reset();
+    void release();
+
+  private:
+    struct Pending {
+        int stat;
+        cudaEvent_t a, b;
+        double fixed, per_unit;
+        const uint32_t* units;
+    };
+    std::vector<Pending> pending_;
+    std::vector<cudaEvent_t> free_events_;
+    cudaEvent_t take_event();
+    int stat_index(const char* name);
+};
+
+// SBWT_LAUNCH(L, "name", fixed_bytes, per_unit_bytes, d_units, kernel, grid, block, smem, args...)
+#define SBWT_LAUNCH(L, NAME, FIXED, PER_UNIT, UNITS, KERNEL, GRID, BLOCK, SMEM, ...)            \
+    do {                                                                                       \
+        int _tok = (L).before(NAME, (double)(FIXED), (double)(PER_UNIT), (UNITS));             \
+        KERNEL<<<(GRID), (BLOCK), (SMEM), (L).stream>>>(__VA_ARGS__);                          \
+        (L).after(_tok);                                                                       \
+    } while (0)
+
+inline unsigned int ceil_div_u(uint64_t a, uint64_t b) { return (unsigned int)((a + b - 1) / b); }
+
+// ---------------------------------------------------------------------------
+// Device-wide primitives (scan.cu, radix.cu).  Every count is read from
+// device memory so a sequence of launches needs no host round trip; `cap`
+// bounds the count and sizes the grids.
+// ---------------------------------------------------------------------------
+constexpr int kScanTile = 4096;  // elements per scan CTA (256 threads x 16)
+
+// Temporary storage of a scan over at most `cap` elements.
+size_t scan_temp_words(uint64_t cap);
+
+// out[i] = sum of in[0..i) (exclusive) over *d_len elements; *d_total gets
+// the sum of all of them when d_total != nullptr.  in == out allowed.
+void scan_exclusive_sum(Launcher& L, const uint32_t* in, uint32_t* out, const uint32_t* d_len,
+                        uint64_t cap, uint32_t* temp, uint32_t* d_total);
+// out[i] = max of in[0..i] (inclusive) over *d_len elements.  in == out allowed.
+void scan_inclusive_max(Launcher& L, const uint32_t* in, uint32_t* out, const uint32_t* d_len,
+                        uint64_t cap, uint32_t* temp);
+
+constexpr int kRadixBits = 8;
+constexpr int kRadixTile = 4096;  // keys per radix CTA (256 threads x 16)
+
+size_t radix_temp_words(uint64_t cap);
+void radix_init();  // once per device, before the first sort
+
+// Stable LSD radix sort of (*d_n) 64-bit keys with 32-bit values on bits
+// [begin_bit, end_bit); key bits at and above end_bit must be zero.  Sorts
+// between (keys, vals) and (keys_alt, vals_alt); returns true when the
+// result ended in the *_alt buffers.  A scatter index out of range (an
+// inconsistent histogram) is skipped and flagged in *d_err (bit 4).
+bool radix_sort_pairs(Launcher& L, unsigned long long* keys, uint32_t* vals, unsigned long long* keys_alt,
+                      uint32_t* vals_alt, const uint32_t* d_n, uint64_t cap, int begin_bit, int end_bit,
+                      uint32_t* temp, uint32_t* d_err);
+
+}  // namespace sbwt

@@ -1,0 +1,65 @@
+// sbwt_kernels.cuh -- host-side launchers of the set-bwte kernels (one .cu
+// file each); the runtime in capi.cu strings them together per block.
+#pragma once
+
+#include "sbwt_internal.cuh"
+
+namespace sbwt {
+
+// pack.cu: reads + offsets (device) -> 2-bit text and terminator bitmap of
+// the whole append; sets *d_err != 0 when a byte is outside the alphabet.
+void launch_pack(Launcher& L, const uint8_t* d_reads, const uint64_t* d_offsets, uint64_t m, uint64_t npos,
+                 uint32_t alpha4, int sigma, uint32_t* text, uint32_t* term, uint32_t* d_err);
+
+// suffix_sort.cu: ConstructSA of one block of n suffixes starting at text
+// position `base`.  Results: sa (SA_int), rank (its inverse).
+struct SuffixSortBuffers {
+    unsigned long long *keys, *keys_alt;  // n each
+    uint32_t *vals, *vals_alt;            // n each
+    uint32_t *sa, *rank, *tmp_a, *tmp_b;  // n each
+    uint32_t *act_pos[2], *act_suf[2];    // n each
+    uint32_t* radix_temp;                 // radix_temp_words(n)
+    uint32_t* scan_temp;                  // scan_temp_words(n)
+    uint32_t* count_log;                  // suffix_sort_log_slots(max_len) words
+    uint32_t* err;                        // error flags (bit 2: a doubling offset left its block)
+};
+uint32_t suffix_sort_rounds(uint32_t max_len);
+size_t suffix_sort_log_slots(uint32_t max_len);
+void suffix_sort_block(Launcher& L, const uint32_t* text, const uint32_t* term, uint64_t base, uint32_t n,
+                       uint32_t max_len, const SuffixSortBuffers& b);
+
+// ranks.cu
+// B_int[i] = code of the symbol before block suffix SA[i], kBintDollar at a
+// read start (Algorithm 1, B(S_jk, SA_int)).
+void launch_bint(Launcher& L, const uint32_t* text, const uint32_t* term, uint64_t base, const uint32_t* sa,
+                 uint32_t n, uint8_t* bint);
+// ComputeRanks (Algorithm 2 with Lemma 1): g[t] for every block position.
+// A row index past n_ext (impossible for a consistent dictionary) is clamped
+// and flagged in *d_err (bit 3) instead of being dereferenced.
+template <class IdxT>
+void launch_compute_ranks(Launcher& L, const uint32_t* text, const uint64_t* d_offsets, uint64_t j_begin,
+                          uint64_t nreads, uint64_t n_int, const OccBlock* blocks, const unsigned long long* super,
+                          const unsigned long long* d_C, uint64_t n_ext, uint64_t m_ext, IdxT* g, uint32_t* d_err);
+// g_sa[i] = g[SA_int[i]].
+template <class IdxT>
+void launch_gather(Launcher& L, const uint32_t* sa, const IdxT* g, uint32_t n, IdxT* gsa);
+// rank queries: codes 0..3, or 4 for the terminator.
+void launch_rank_batch(Launcher& L, const OccBlock* blocks, const unsigned long long* super, const uint8_t* codes,
+                       const unsigned long long* ks, uint64_t q, unsigned long long* out);
+// B as bytes: alphabet byte per code, '$' for a terminator row.
+void launch_unpack(Launcher& L, const OccBlock* blocks, uint64_t n, uint32_t alpha4, uint8_t* out);
+
+// insert.cu: Insert (Section 5) as a stable merge of the old dictionary
+// (n_ext rows) with n_int new symbols at rows g_sa[i] + i; writes the new
+// dictionary's symbols, terminator masks and block counters, then the
+// superblock counters and C[] (m = terminators in the new dictionary).
+template <class IdxT>
+void launch_insert(Launcher& L, const OccBlock* old_blocks, uint64_t n_ext, const uint8_t* bint, const IdxT* gsa,
+                   uint64_t n_int, OccBlock* new_blocks, unsigned long long* new_super, unsigned long long* new_C,
+                   uint64_t m_new, uint32_t* sb_tot);
+
+// Sizes of a dictionary of n rows.
+inline uint64_t dict_blocks(uint64_t n) { return (n >> kOccShift) + 1; }
+inline uint64_t dict_supers(uint64_t n) { return (dict_blocks(n) + kBlocksPerSuper - 1) / kBlocksPerSuper; }
+
+}  // namespace sbwt

@@ -1,0 +1,108 @@
+"""The C ABI without a GPU: libsbwt.so builds, loads, exports every entry
+point include/sbwt.h declares, and rejects bad arguments on the host before
+touching a device."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_1410_0562_gb300 as sb
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "sbwt.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    sb.build()
+    return sb.load()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(sbwt_[a-z_]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("sbwt_create", "sbwt_append", "sbwt_get_bwt", "sbwt_rank"):
+        assert required in names
+    assert sorted(sb.EXPORTS) == names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+        assert ctypes.cast(getattr(lib, name), ctypes.c_void_p).value
+
+
+def test_strerror(lib):
+    for code in (0, -1, -2, -3, -4, -5, -99):
+        assert isinstance(sb.strerror(code), str) and sb.strerror(code)
+
+
+@pytest.mark.parametrize("alpha", [b"", b"ACGTN", b"CA", b"AAC", b"A$", b"ACC"])
+def test_create_rejects_bad_alphabet(lib, alpha):
+    h = ctypes.c_void_p()
+    assert lib.sbwt_create(alpha, 0, ctypes.byref(h)) == sb.SBWT_EINVAL
+    assert not h.value
+
+
+def test_create_does_not_touch_the_gpu(lib):
+    # works on a machine without a GPU: device state is created lazily
+    for alpha in (b"A", b"AC", b"ACG", b"ACGT", b"abn", b"imps"):
+        h = sb.sbwt_create(alpha)
+        assert sb.sbwt_size(h) == (0, 0)
+        sb.sbwt_reset(h)
+        sb.sbwt_destroy(h)
+    sb.sbwt_destroy(None)
+
+
+def test_create_ex_rejects_bad_options(lib):
+    for kw in ({"index_bits": 16}, {"block_suffixes": (1 << 31) + 1}):
+        with pytest.raises(sb.SbwtError) as e:
+            sb.sbwt_create_ex(b"ACGT", **kw)
+        assert e.value.code == sb.SBWT_EINVAL
+
+
+def test_append_rejects_bad_offsets_on_the_host(lib):
+    h = sb.sbwt_create(b"ACGT")
+    reads = np.frombuffer(b"ACGTACGT", np.uint8)
+    for off in ([1, 4, 8], [0, 5, 4, 8], [0, 9, 8]):
+        with pytest.raises(sb.SbwtError) as e:
+            sb.sbwt_append(h, reads, np.array(off, np.uint64))
+        assert e.value.code == sb.SBWT_EINVAL
+    assert sb.sbwt_size(h) == (0, 0)
+    # m = 0 is a no-op that needs no device
+    sb.sbwt_append(h, reads, np.array([0], np.uint64))
+    assert sb.sbwt_size(h) == (0, 0)
+    sb.sbwt_destroy(h)
+
+
+def test_queries_validate_on_the_host(lib):
+    h = sb.sbwt_create(b"ACGT")
+    with pytest.raises(sb.SbwtError):
+        sb.sbwt_rank(h, ord("N"), 0)
+    with pytest.raises(sb.SbwtError):
+        sb.sbwt_rank(h, ord("A"), 1)  # k > n = 0
+    assert len(sb.sbwt_get_bwt(h)) == 0
+    with pytest.raises(sb.SbwtError):
+        sb.sbwt_get_stage(h, sb.SBWT_STAGE_SA)  # capture is off
+    sb.sbwt_destroy(h)
+
+
+def test_no_cpu_fallback_without_a_device(lib):
+    """On a machine without a GPU a valid append must fail loudly with
+    SBWT_EDEVICE; it must never compute the BWT on the host."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    h = sb.sbwt_create(b"ACGT")
+    with pytest.raises(sb.SbwtError) as e:
+        sb.sbwt_append(h, np.frombuffer(b"ACGT", np.uint8), np.array([0, 4], np.uint64))
+    assert e.value.code == sb.SBWT_EDEVICE
+    assert sb.sbwt_size(h) == (0, 0)
+    sb.sbwt_destroy(h)

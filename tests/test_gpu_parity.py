@@ -1,0 +1,263 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Everything here is exact integer work, so every comparison is bit-exact:
+the BWT, each block's intermediates (SA_int, B_int, g, g_sa), and rank
+queries.  Inputs are seeded and synthetic (readgen) or hand-made edge cases.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1410_0562_gb300 as sb
+import readgen
+from test_oracle import load_golden, pack
+
+pytestmark = pytest.mark.gpu
+
+CODE_BYTES = {255: ord("$")}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    sb.build()
+    sb.load()
+
+
+def gpu_bwt(reads, offsets, alphabet=b"ACGT", M=0, cuts=None, index_bits=0, capture=False):
+    """Build through the C ABI, appending reads [cuts[k], cuts[k+1]) per call."""
+    m = len(offsets) - 1
+    cuts = list(cuts) if cuts else [0, m]
+    idx = sb.SetBWT(alphabet, index_bits=index_bits, block_suffixes=M)
+    if capture:
+        sb.sbwt_set_capture(idx.handle, True)
+    offsets = np.asarray(offsets, np.uint64)
+    for a, b in zip(cuts[:-1], cuts[1:]):
+        o = offsets[a:b + 1] - offsets[a]
+        idx.append(np.ascontiguousarray(reads[int(offsets[a]):int(offsets[b])]), o)
+    return idx
+
+
+def bint_bytes(bint_codes, alphabet=b"ACGT"):
+    lut = np.zeros(256, np.uint8)
+    for i, c in enumerate(alphabet):
+        lut[i] = c
+    lut[255] = ord("$")
+    return lut[bint_codes]
+
+
+@pytest.mark.parametrize("alpha,reads,expect", load_golden())
+def test_golden_examples(alpha, reads, expect):
+    data, off = pack(reads)
+    assert bytes(gpu_bwt(data, off, alpha).bwt()) == expect
+    # one read per append gives the same B (Algorithm 1, forward order)
+    assert bytes(gpu_bwt(data, off, alpha, cuts=range(len(reads) + 1)).bwt()) == expect
+
+
+def test_tiny_workload_and_intermediates():
+    """1,000 x 100 bp i.i.d. reads appended as 2 x 500: B and every
+    intermediate of the second block against the oracle."""
+    w = readgen.tiny()
+    idx = gpu_bwt(w.reads, w.offsets, M=w.block_suffixes, cuts=w.appends, capture=True)
+    B = idx.bwt()
+    expect = oracle.bwt(w.reads, w.offsets)
+    assert np.array_equal(B, expect)
+    j0, j1 = 500, 1000
+    sa = sb.sbwt_get_stage(idx.handle, sb.SBWT_STAGE_SA)
+    assert np.array_equal(sa.astype(np.uint64), oracle.block_sa(w.reads, w.offsets, j0, j1))
+    bint = sb.sbwt_get_stage(idx.handle, sb.SBWT_STAGE_BINT)
+    assert np.array_equal(bint_bytes(bint), oracle.block_bint(w.reads, w.offsets, j0, j1, sa))
+    g = sb.sbwt_get_stage(idx.handle, sb.SBWT_STAGE_G)
+    assert np.array_equal(g, oracle.block_g_direct(w.reads, w.offsets, j0, j1))
+    gsa = sb.sbwt_get_stage(idx.handle, sb.SBWT_STAGE_GSA)
+    assert np.array_equal(gsa, g[sa.astype(np.int64)])
+    assert np.all(np.diff(gsa.astype(np.int64)) >= 0)
+    assert idx.size() == (len(expect), w.m)
+
+
+def test_first_block_intermediates():
+    """The first block ranks against an empty index: g = 0 everywhere."""
+    w = readgen.tiny()
+    idx = gpu_bwt(w.reads, w.offsets, cuts=[0, 500], capture=True)
+    sa = sb.sbwt_get_stage(idx.handle, sb.SBWT_STAGE_SA)
+    assert np.array_equal(sa.astype(np.uint64), oracle.block_sa(w.reads, w.offsets, 0, 500))
+    assert not np.any(sb.sbwt_get_stage(idx.handle, sb.SBWT_STAGE_G))
+
+
+@pytest.mark.parametrize("M", [1, 7, 64, 1000, 4096, 50_500, 1 << 24])
+def test_block_partition_invariance(M):
+    w = readgen.tiny()
+    expect = oracle.bwt(w.reads, w.offsets)
+    assert np.array_equal(gpu_bwt(w.reads, w.offsets, M=M, cuts=w.appends).bwt(), expect)
+
+
+@pytest.mark.parametrize("seed", range(24))
+def test_random_edge_sets(seed):
+    rng = np.random.default_rng(1000 + seed)
+    m = int(rng.integers(1, 300))
+    reads = []
+    for _ in range(m):
+        kind = rng.random()
+        if kind < 0.1:
+            reads.append(b"")
+        elif kind < 0.25:  # a run of one base: long common prefixes
+            reads.append(bytes([b"ACGT"[rng.integers(0, 4)]]) * int(rng.integers(1, 200)))
+        elif kind < 0.35:  # a short tandem repeat
+            unit = bytes(rng.choice(np.frombuffer(b"ACGT", np.uint8), size=int(rng.integers(1, 4))))
+            reads.append((unit * 200)[: int(rng.integers(1, 300))])
+        elif kind < 0.45 and reads:  # an exact duplicate
+            reads.append(reads[int(rng.integers(0, len(reads)))])
+        else:
+            reads.append(bytes(rng.choice(np.frombuffer(b"ACGT", np.uint8), size=int(rng.integers(1, 150)))))
+    data, off = pack(reads)
+    expect = oracle.bwt(data, off)
+    M = int(rng.choice([1, 50, 500, 5000, 1 << 20]))
+    cuts = sorted(set([0, m] + [int(x) for x in rng.integers(0, m, size=int(rng.integers(0, 4)))]))
+    idx = gpu_bwt(data, off, M=M, cuts=cuts, index_bits=int(rng.choice([0, 32, 64])))
+    assert np.array_equal(idx.bwt(), expect)
+
+
+@pytest.mark.parametrize("alphabet", [b"A", b"AC", b"ACG", b"abn", b"imps"])
+def test_small_alphabets(alphabet):
+    rng = np.random.default_rng(len(alphabet))
+    reads = [bytes(rng.choice(np.frombuffer(alphabet, np.uint8), size=int(rng.integers(0, 80))))
+             for _ in range(200)]
+    data, off = pack(reads)
+    expect = oracle.bwt(data, off, alphabet)
+    assert np.array_equal(gpu_bwt(data, off, alphabet, M=777, cuts=[0, 60, 200]).bwt(), expect)
+
+
+def test_long_reads_many_doubling_rounds():
+    """Reads up to 3 kbp sharing long prefixes need several doubling rounds."""
+    rng = np.random.default_rng(5)
+    base = bytes(rng.choice(np.frombuffer(b"ACGT", np.uint8), size=3000))
+    reads = [base[int(rng.integers(0, 50)):][: int(rng.integers(500, 2950))] for _ in range(40)]
+    reads += [b"A" * 2500, b"A" * 2499, b"AC" * 1200, b"A" * 2500]
+    data, off = pack(reads)
+    expect = oracle.bwt(data, off)
+    assert np.array_equal(gpu_bwt(data, off, M=30_000, cuts=[0, 20, 44]).bwt(), expect)
+
+
+@pytest.mark.parametrize("n_int", [4095, 4096, 4097, 8193, 65535, 65536, 65537])
+def test_ragged_tile_and_superblock_sizes(n_int):
+    """Blocks whose suffix count straddles a radix tile (4096) and B sizes
+    that straddle a superblock (65536 rows)."""
+    rng = np.random.default_rng(n_int)
+    lengths = []
+    left = n_int
+    while left > 0:
+        L = min(int(rng.integers(0, 120)), left - 1)
+        lengths.append(L)
+        left -= L + 1
+    off = readgen.offsets_from_lengths(lengths)
+    data = rng.choice(np.frombuffer(b"ACGT", np.uint8), size=int(off[-1]))
+    assert oracle.num_suffixes(off) == n_int
+    expect = oracle.bwt(data, off)
+    idx = gpu_bwt(data, off, capture=True)
+    assert np.array_equal(idx.bwt(), expect)
+    sa = sb.sbwt_get_stage(idx.handle, sb.SBWT_STAGE_SA)
+    assert len(sa) == n_int
+    # and appended in two halves
+    h = len(lengths) // 2
+    assert np.array_equal(gpu_bwt(data, off, cuts=[0, h, len(lengths)]).bwt(), expect)
+
+
+def test_rank_queries_match_counts():
+    w = readgen.tiny()
+    idx = gpu_bwt(w.reads, w.offsets, cuts=w.appends)
+    B = oracle.bwt(w.reads, w.offsets)
+    n = len(B)
+    rng = np.random.default_rng(3)
+    ks = np.concatenate([[0, 1, 63, 64, 65, 65535, 65536, 65537, n - 1, n], rng.integers(0, n + 1, size=200)])
+    for c in b"$ACGT":
+        cum = np.concatenate([[0], np.cumsum(B == c)])
+        got = idx.rank_batch(np.full(len(ks), c, np.uint8), ks.astype(np.uint64))
+        assert np.array_equal(got, cum[ks])
+    assert idx.rank("G", n) == int(np.count_nonzero(B == ord("G")))
+    with pytest.raises(sb.SbwtError):
+        idx.rank("A", n + 1)
+
+
+def test_bad_input_leaves_index_unchanged():
+    w = readgen.tiny()
+    idx = gpu_bwt(w.reads, w.offsets, cuts=[0, 500])
+    before = idx.bwt().copy()
+    bad = w.reads[int(w.offsets[500]):].copy()
+    bad[1234] = ord("N")
+    with pytest.raises(sb.SbwtError) as e:
+        idx.append(bad, w.offsets[500:] - w.offsets[500])
+    assert e.value.code == sb.SBWT_EINVAL
+    assert np.array_equal(idx.bwt(), before)
+    assert idx.size() == (len(before), 500)
+    idx.append(w.reads[int(w.offsets[500]):], w.offsets[500:] - w.offsets[500])
+    assert np.array_equal(idx.bwt(), oracle.bwt(w.reads, w.offsets))
+
+
+def test_budget_too_small_is_enomem_and_harmless():
+    w = readgen.tiny()
+    idx = sb.SetBWT(b"ACGT", hbm_budget=1 << 16)
+    with pytest.raises(sb.SbwtError) as e:
+        idx.append(w.reads, w.offsets)
+    assert e.value.code == sb.SBWT_ENOMEM
+    assert idx.size() == (0, 0)
+
+
+def test_index_bits_64_matches_32():
+    w = readgen.tiny()
+    a = gpu_bwt(w.reads, w.offsets, cuts=w.appends, index_bits=32, capture=True)
+    b = gpu_bwt(w.reads, w.offsets, cuts=w.appends, index_bits=64, capture=True)
+    assert np.array_equal(a.bwt(), b.bwt())
+    assert np.array_equal(sb.sbwt_get_stage(a.handle, sb.SBWT_STAGE_GSA), sb.sbwt_get_stage(b.handle, sb.SBWT_STAGE_GSA))
+
+
+def test_device_append_matches_host_append():
+    import torch
+    w = readgen.tiny()
+    d_reads = torch.from_numpy(w.reads).cuda()
+    d_off = torch.from_numpy(w.offsets.astype(np.int64)).cuda()
+    idx = sb.SetBWT(b"ACGT")
+    idx.append_device(d_reads.data_ptr(), d_off.data_ptr(), w.m)
+    assert np.array_equal(idx.bwt(), oracle.bwt(w.reads, w.offsets))
+    idx.reset()
+    assert idx.size() == (0, 0)
+    idx.append_device(d_reads.data_ptr(), d_off.data_ptr(), w.m)
+    assert np.array_equal(idx.bwt(), oracle.bwt(w.reads, w.offsets))
+
+
+def test_repeated_appends_reuse_buffers():
+    """Many small appends into one index equal the one-shot BWT."""
+    w = readgen.tiny()
+    cuts = list(range(0, 1001, 37)) + [1000]
+    cuts = sorted(set(cuts))
+    assert np.array_equal(gpu_bwt(w.reads, w.offsets, cuts=cuts).bwt(), oracle.bwt(w.reads, w.offsets))
+
+
+def test_short_read_workload_full_size():
+    """The 1M x 100 bp short-read workload (10 Mbp genome, 1% substitutions,
+    blocks of 2^24 suffixes, 32-bit indices) in the launch configuration the
+    benchmark times.  The oracle cannot sort 101M suffixes in test time, so:
+    sampled rows computed one by one by the oracle, the terminator rows, the
+    symbol multiset, and LF inversion of the whole B back to every read."""
+    w = readgen.short()
+    idx = gpu_bwt(w.reads, w.offsets, M=w.block_suffixes, index_bits=w.index_bits)
+    B = idx.bwt()
+    n = oracle.num_suffixes(w.offsets)
+    assert len(B) == n and idx.size() == (n, w.m)
+    # multiset: same symbols as the reads, exactly m terminators
+    counts = np.bincount(B, minlength=256)
+    expect_counts = np.bincount(w.reads, minlength=256)
+    expect_counts[ord("$")] += w.m
+    assert np.array_equal(counts, expect_counts)
+    # rows 0..m-1 are $_0..$_{m-1}: the last symbol of each read
+    last = w.reads[(w.offsets[1:] - 1).astype(np.int64)]
+    assert np.array_equal(B[: w.m], last)
+    # sampled suffixes: their rows by direct counting, and B there
+    rng = np.random.default_rng(17)
+    for _ in range(6):
+        r = int(rng.integers(0, w.m))
+        L = int(w.offsets[r + 1] - w.offsets[r])
+        p = int(rng.integers(0, L + 1))
+        row = oracle.row_of_suffix(w.reads, w.offsets, r, p)
+        assert B[row] == oracle.bwt_symbol_of_suffix(w.reads, w.offsets, r, p)
+    # LF inversion recovers every read
+    rec, roff = oracle.lf_invert(B, w.m)
+    assert np.array_equal(roff, w.offsets) and np.array_equal(rec, w.reads)
