@@ -79,7 +79,7 @@ int sbwt_create(const char *alphabet, size_t hbm_budget_bytes, sbwt_index **out)
 int sbwt_create_ex(const char *alphabet, size_t hbm_budget_bytes, const sbwt_options *opt,
                    sbwt_index **out);
 
-/* Appends m reads from HOST memory (Algorithm 1 over the new reads; Section 3
+/* Appends m reads from HOST memory (Algorithm 1 over the new reads; Section 2
  * notes that new strings can be added at any time because suffixes never
  * cross a read).  The reads get the global ids n_reads .. n_reads+m-1, in
  * order.  Inputs are validated before the index changes: a byte outside the
