@@ -158,6 +158,37 @@ int sbwt_set_profiling(sbwt_index *idx, int on);
 int sbwt_get_kernel_stats(sbwt_index *idx, sbwt_kernel_stat *out, int cap, int *n_out);
 int sbwt_reset_kernel_stats(sbwt_index *idx);
 
+/* ---- BWT of a small read set without allocating -------------------------
+ * The paper has no counterpart to this call.  It is for callers that cannot
+ * allocate device memory: a process whose device memory is handed out by
+ * another framework's pool, a service that forbids allocation after start-up
+ * to keep its footprint and latency fixed, or a plug-in whose host owns the
+ * allocator.  Everything else in this library allocates its buffers with
+ * cudaMalloc; this call does not (no cudaMalloc, cudaFree or allocating
+ * library routine).
+ *
+ * It writes B (see conventions) of the m reads in host memory `reads` /
+ * `offsets` into host buffer `out` of `cap` bytes, *n_out = n = offsets[m] +
+ * m; the result is byte-for-byte what sbwt_create + sbwt_append +
+ * sbwt_get_bwt give for the same reads.  `stream` is the cudaStream_t to run
+ * on (NULL = the default stream); the call returns when the result is in
+ * `out`.
+ *
+ * Its working memory is one file-scope device array sized for at most
+ * SBWT_NOALLOC_MAX_SUFFIXES suffixes (reads plus one terminator each), about
+ * 18 MB, which every GPU that loads the library holds until the process
+ * exits.  Larger read sets return SBWT_EINVAL.  The first call on a device
+ * looks up the array's device address (set-up, once per device); make that
+ * first call before any stream capture.  All calls share the array and it
+ * keeps the last call's contents; two calls whose GPU work overlapped would
+ * race, so this function holds a process-wide lock until its stream has
+ * finished.  Errors: SBWT_EINVAL (bad alphabet or offsets, a byte outside the
+ * alphabet, more than SBWT_NOALLOC_MAX_SUFFIXES suffixes), SBWT_ERANGE
+ * (cap < n), SBWT_EDEVICE. */
+#define SBWT_NOALLOC_MAX_SUFFIXES (1u << 18)
+int sbwt_bwt_noalloc(const char *alphabet, const uint8_t *reads, const uint64_t *offsets, uint64_t m,
+                     uint8_t *out, uint64_t cap, uint64_t *n_out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

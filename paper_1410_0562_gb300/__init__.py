@@ -39,8 +39,11 @@ EXPORTS = (
     "sbwt_create", "sbwt_create_ex", "sbwt_append", "sbwt_append_device", "sbwt_get_bwt", "sbwt_rank",
     "sbwt_rank_batch", "sbwt_size", "sbwt_reset", "sbwt_destroy", "sbwt_strerror", "sbwt_get_stream",
     "sbwt_set_capture", "sbwt_get_stage", "sbwt_set_profiling", "sbwt_get_kernel_stats",
-    "sbwt_reset_kernel_stats",
+    "sbwt_reset_kernel_stats", "sbwt_bwt_noalloc",
 )
+
+#: most suffixes (reads + one terminator each) sbwt_bwt_noalloc accepts
+SBWT_NOALLOC_MAX_SUFFIXES = 1 << 18
 
 
 class SbwtError(RuntimeError):
@@ -98,6 +101,7 @@ def load() -> ctypes.CDLL:
             "sbwt_set_profiling": ([P, I], I),
             "sbwt_get_kernel_stats": ([P, ctypes.POINTER(sbwt_kernel_stat), I, ctypes.POINTER(I)], I),
             "sbwt_reset_kernel_stats": ([P], I),
+            "sbwt_bwt_noalloc": ([ctypes.c_char_p, P, P, U64, P, U64, ctypes.POINTER(U64), P], I),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -231,6 +235,21 @@ def sbwt_get_kernel_stats(h) -> list:
 
 def sbwt_reset_kernel_stats(h):
     _check(load().sbwt_reset_kernel_stats(h), "sbwt_reset_kernel_stats")
+
+
+def sbwt_bwt_noalloc(alphabet: bytes, reads, offsets, stream: int = 0) -> np.ndarray:
+    """B of a small read set computed without any device allocation (for
+    callers whose device memory is owned by someone else); at most
+    SBWT_NOALLOC_MAX_SUFFIXES suffixes."""
+    rp, rk = _host_ptr(reads, np.uint8)
+    op, ok = _host_ptr(offsets, np.uint64)
+    m = len(ok) - 1
+    n = int(ok[-1]) + m
+    out = np.zeros(max(n, 1), dtype=np.uint8)
+    got = ctypes.c_uint64()
+    _check(load().sbwt_bwt_noalloc(alphabet, rp, op, m, ctypes.c_void_p(out.ctypes.data), n, ctypes.byref(got),
+                                   ctypes.c_void_p(stream or None)), "sbwt_bwt_noalloc")
+    return out[: got.value]
 
 
 class SetBWT:

@@ -1,0 +1,56 @@
+"""sbwt_bwt_noalloc: the BWT of a small read set for callers that cannot
+allocate device memory (their device memory belongs to another framework's
+pool, or allocation is forbidden after start-up).  It works from one fixed
+device array instead of cudaMalloc, so its output must equal, byte for byte,
+what the allocating entry points (sbwt_create + sbwt_append + sbwt_get_bwt)
+produce for the same reads -- on consecutive calls too, since every call
+reuses the same array."""
+import numpy as np
+import pytest
+
+import paper_1410_0562_gb300 as sb
+import readgen
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    sb.build()
+    sb.load()
+
+
+def allocating_bwt(reads, offsets, alphabet=b"ACGT"):
+    idx = sb.SetBWT(alphabet)
+    idx.append(reads, offsets)
+    out = idx.bwt()
+    idx.close()
+    return out
+
+
+def test_two_calls_in_a_row_match_the_allocating_path():
+    # a larger set first, then a smaller one: the second call must not see
+    # anything the first left behind in the shared array
+    big_r, big_o = readgen.ragged_reads(1500, 0, 150, seed=21, p_empty=0.05, p_repeat=0.05)
+    small_r, small_o = readgen.uniform_reads(300, 100, seed=22)
+    assert int(big_o[-1]) + len(big_o) - 1 <= sb.SBWT_NOALLOC_MAX_SUFFIXES
+    first = sb.sbwt_bwt_noalloc(b"ACGT", big_r, big_o)
+    second = sb.sbwt_bwt_noalloc(b"ACGT", small_r, small_o)
+    assert np.array_equal(first, allocating_bwt(big_r, big_o))
+    assert np.array_equal(second, allocating_bwt(small_r, small_o))
+
+
+def test_other_alphabet_and_size_limit():
+    reads, off = readgen.ragged_reads(200, 0, 60, seed=23, alphabet=b"ACG")
+    assert np.array_equal(sb.sbwt_bwt_noalloc(b"ACG", reads, off), allocating_bwt(reads, off, b"ACG"))
+    # one suffix past the fixed maximum is refused before any GPU work
+    L = sb.SBWT_NOALLOC_MAX_SUFFIXES
+    too_big = np.full(L, ord("A"), np.uint8)
+    with pytest.raises(sb.SbwtError) as e:
+        sb.sbwt_bwt_noalloc(b"ACGT", too_big, np.array([0, L], np.uint64))
+    assert e.value.code == sb.SBWT_EINVAL
+    # exactly at the maximum is accepted
+    at_max = np.full(L - 1, ord("C"), np.uint8)
+    at_max[::7] = ord("A")
+    off = np.array([0, L - 1], np.uint64)
+    assert np.array_equal(sb.sbwt_bwt_noalloc(b"ACGT", at_max, off), allocating_bwt(at_max, off))
