@@ -251,11 +251,11 @@ void run_block(sbwt_index* idx, const BlockPlan& bp, const uint64_t* d_offsets, 
     const uint32_t* term = (const uint32_t*)idx->term.p;
 
     suffix_sort_block(L, text, term, bp.base, n, (uint32_t)bp.max_len, b);
-    launch_bint(L, text, term, bp.base, b.sa, n, (uint8_t*)idx->bint.p);
     launch_compute_ranks<IdxT>(L, text, d_offsets, bp.j0, bp.j1 - bp.j0, bp.n_int, (const OccBlock*)src.blocks.p,
                                (const unsigned long long*)src.super.p, (const unsigned long long*)src.C.p, n_ext,
                                m_ext, (IdxT*)idx->g.p, (uint32_t*)idx->err.p);
-    launch_gather<IdxT>(L, b.sa, (const IdxT*)idx->g.p, n, (IdxT*)idx->gsa.p);
+    launch_bint_gather<IdxT>(L, text, term, bp.base, b.sa, (const IdxT*)idx->g.p, n, (uint8_t*)idx->bint.p,
+                             (IdxT*)idx->gsa.p);
     launch_insert<IdxT>(L, (const OccBlock*)src.blocks.p, n_ext, (const uint8_t*)idx->bint.p,
                         (const IdxT*)idx->gsa.p, bp.n_int, (OccBlock*)dst.blocks.p,
                         (unsigned long long*)dst.super.p, (unsigned long long*)dst.C.p, m_ext + (bp.j1 - bp.j0),

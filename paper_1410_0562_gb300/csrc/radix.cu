@@ -1,11 +1,24 @@
 // radix.cu -- stable LSD radix sort of (64-bit key, 32-bit value) pairs,
-// 8-bit digits, element count in device memory.  Each digit pass is an
-// upsweep (per-tile digit histograms), a device-wide scan of the
-// digit-major histogram matrix, and a downsweep that ranks every key inside
-// its tile with warp match/ballot, stages the tile in shared memory in digit
-// order and writes it out in coalesced runs.  This is the sort under the
-// suffix sorting of a block (Section 3 of arXiv 1410.0562 sorts suffixes by
+// 8-bit digits, element count in device memory.  This is the sort under the
+// suffix sorting of a block (Section 3 of arXiv 1410.0562 sorts suffixes as
 // long integer keys of packed symbols, refined over iterations).
+//
+// One read of the keys builds the digit histograms of every pass at once;
+// each digit pass is then a single persistent kernel (the single-pass
+// "onesweep" scheme of Adinets and Merrill): a CTA takes the next tile in
+// order, ranks its keys per digit (8 warp ballots give each lane the mask of
+// lanes with the same digit), publishes its per-digit counts, finds the
+// counts of all earlier tiles by decoupled look-back, stages the tile in
+// shared memory in digit order and writes it out in coalesced runs.
+//
+// The look-back waits only on tiles taken earlier, by CTAs already running,
+// so it always ends; every wait is still bounded, and a CTA that gives up
+// flags *d_err (bit 6) and goes on with a wrong count whose writes the bounds
+// checks drop.  Look-back words carry an epoch so the buffer never needs
+// clearing: a word from an earlier pass reads as "not ready".
+#include <algorithm>
+#include <atomic>
+
 #include "sbwt_internal.cuh"
 
 namespace sbwt {
@@ -16,114 +29,162 @@ constexpr int kWarps = kThreads / 32;
 constexpr int kItems = kRadixTile / kThreads;      // 16 keys per thread
 constexpr int kWarpItems = kRadixTile / kWarps;    // 512 consecutive keys per warp
 constexpr int kBins = 1 << kRadixBits;             // 256
-static_assert(kBins == kThreads, "one thread per digit in the downsweep");
+constexpr int kMaxPasses = 8;
+static_assert(kBins == kThreads, "one thread per digit");
 
 constexpr size_t kScatterSmem = (size_t)kRadixTile * 8 + (size_t)kRadixTile * 4 + (size_t)kWarps * kBins * 4 +
-                                (size_t)kBins * 4 * 2;
+                                (size_t)kBins * 4 * 3 + 16;
 
-__global__ void __launch_bounds__(kThreads) radix_hist_kernel(const unsigned long long* __restrict__ keys,
-                                                              const uint32_t* __restrict__ d_n, int shift,
-                                                              uint32_t* __restrict__ hist,
-                                                              uint32_t* __restrict__ d_hist_len) {
-    __shared__ uint32_t h[kWarps * kBins];
-    const uint32_t n = *d_n;
-    const uint32_t ntiles = (uint32_t)(((uint64_t)n + kRadixTile - 1) / kRadixTile);
-    if (blockIdx.x == 0 && threadIdx.x == 0) *d_hist_len = ntiles * kBins;
-    const uint32_t tile = blockIdx.x;
-    if (tile >= ntiles) return;
-    for (int i = threadIdx.x; i < kWarps * kBins; i += kThreads) h[i] = 0;
-    __syncthreads();
-    const int warp = threadIdx.x >> 5;
-    const uint64_t base = (uint64_t)tile * kRadixTile;
-    const uint32_t cnt = (uint32_t)min((uint64_t)kRadixTile, (uint64_t)n - base);
-#pragma unroll 4
-    for (int q = 0; q < kItems; ++q) {
-        uint32_t i = q * kThreads + threadIdx.x;
-        if (i < cnt) {
-            uint32_t d = (uint32_t)(keys[base + i] >> shift) & (kBins - 1);
-            atomicAdd(&h[warp * kBins + d], 1u);
-        }
-    }
-    __syncthreads();
-    const int d = threadIdx.x;
-    uint32_t s = 0;
-#pragma unroll
-    for (int w = 0; w < kWarps; ++w) s += h[w * kBins + d];
-    hist[(uint64_t)d * ntiles + tile] = s;
+// look-back word: [63:34] epoch, [33:32] state, [31:0] count
+constexpr unsigned long long kAggregate = 1ull << 32;
+constexpr unsigned long long kPrefix = 2ull << 32;
+constexpr uint32_t kSpinLimit = 1u << 22;
+
+// Temp layout (32-bit words): [0, 8) tile counters, [8, 8 + 8*256) digit
+// starts of every pass, then the look-back words (8-byte aligned).
+constexpr size_t kCounters = 0;
+constexpr size_t kDigitStart = 8;
+constexpr size_t kLookback = kDigitStart + (size_t)kMaxPasses * kBins + 8;
+
+__device__ __forceinline__ void store_volatile(unsigned long long* p, unsigned long long v) {
+    *reinterpret_cast<volatile unsigned long long*>(p) = v;
+}
+__device__ __forceinline__ unsigned long long load_volatile(const unsigned long long* p) {
+    return *reinterpret_cast<const volatile unsigned long long*>(p);
 }
 
-__global__ void __launch_bounds__(kThreads) radix_scatter_kernel(const unsigned long long* __restrict__ kin,
-                                                                 const uint32_t* __restrict__ vin,
-                                                                 unsigned long long* __restrict__ kout,
-                                                                 uint32_t* __restrict__ vout,
-                                                                 const uint32_t* __restrict__ d_n, int shift,
-                                                                 const uint32_t* __restrict__ hist,
-                                                                 uint32_t* __restrict__ d_err) {
+// Digit histograms of every pass in one read of the keys.
+__global__ void __launch_bounds__(kThreads) radix_hist_kernel(const unsigned long long* __restrict__ keys,
+                                                              const uint32_t* __restrict__ d_n, int begin_bit,
+                                                              int passes, uint32_t* __restrict__ ghist) {
+    __shared__ uint32_t h[kMaxPasses * kBins];
+    for (int i = threadIdx.x; i < passes * kBins; i += kThreads) h[i] = 0;
+    __syncthreads();
+    const uint32_t n = *d_n;
+    for (uint64_t i = (uint64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (uint64_t)gridDim.x * kThreads) {
+        const unsigned long long k = keys[i] >> begin_bit;
+        for (int p = 0; p < passes; ++p) atomicAdd(&h[p * kBins + ((k >> (kRadixBits * p)) & (kBins - 1))], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < passes * kBins; i += kThreads)
+        if (h[i]) atomicAdd(&ghist[i], h[i]);
+}
+
+// Exclusive scan of each pass's histogram into digit start offsets.
+__global__ void __launch_bounds__(kThreads) radix_digit_scan_kernel(uint32_t* __restrict__ ghist, int passes) {
+    for (int p = 0; p < passes; ++p) {
+        uint32_t tot;
+        const uint32_t ex = cta_exclusive_scan<SumOp, kThreads>(ghist[p * kBins + threadIdx.x], tot);
+        ghist[p * kBins + threadIdx.x] = ex;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads, 2) radix_onesweep_kernel(
+    const unsigned long long* __restrict__ kin, const uint32_t* __restrict__ vin, unsigned long long* __restrict__ kout,
+    uint32_t* __restrict__ vout, const uint32_t* __restrict__ d_n, int shift, const uint32_t* __restrict__ dstart_g,
+    unsigned long long* __restrict__ lookback, uint32_t* __restrict__ tile_counter, unsigned long long epoch,
+    uint32_t* __restrict__ d_err) {
     extern __shared__ __align__(16) unsigned char smem[];
     unsigned long long* skeys = reinterpret_cast<unsigned long long*>(smem);
     uint32_t* svals = reinterpret_cast<uint32_t*>(skeys + kRadixTile);
-    uint32_t* wcnt = svals + kRadixTile;     // [kWarps][kBins]
+    uint32_t* wcnt = svals + kRadixTile;       // [kWarps][kBins]
     uint32_t* dstart = wcnt + kWarps * kBins;  // tile-local start of each digit
     uint32_t* gstart = dstart + kBins;         // global start of each digit for this tile
+    uint32_t* misc = gstart + kBins;
 
     const uint32_t n = *d_n;
     const uint32_t ntiles = (uint32_t)(((uint64_t)n + kRadixTile - 1) / kRadixTile);
-    const uint32_t tile = blockIdx.x;
-    if (tile >= ntiles) return;
-    const uint64_t base = (uint64_t)tile * kRadixTile;
-    const uint32_t cnt = (uint32_t)min((uint64_t)kRadixTile, (uint64_t)n - base);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-
-    for (int i = threadIdx.x; i < kWarps * kBins; i += kThreads) wcnt[i] = 0;
-
-    unsigned long long k[kItems];
-    uint32_t v[kItems];
-#pragma unroll
-    for (int it = 0; it < kItems; ++it) {
-        uint32_t i = warp * kWarpItems + it * 32 + lane;
-        bool valid = i < cnt;
-        k[it] = valid ? kin[base + i] : 0ull;
-        v[it] = valid ? vin[base + i] : 0u;
-    }
-    __syncthreads();
-
-    // Rank each key among the equal digits of its warp, in index order.
     const uint32_t lt = (1u << lane) - 1u;
-    uint32_t dr[kItems];
-    uint32_t* my = wcnt + warp * kBins;
-#pragma unroll
-    for (int it = 0; it < kItems; ++it) {
-        uint32_t i = warp * kWarpItems + it * 32 + lane;
-        uint32_t d = i < cnt ? (uint32_t)(k[it] >> shift) & (kBins - 1) : (uint32_t)kBins;
-        uint32_t peers = __match_any_sync(0xffffffffu, d);
-        uint32_t prior = d < kBins ? my[d] : 0u;
-        __syncwarp();
-        if (d < kBins && lane == __ffs(peers) - 1) my[d] = prior + __popc(peers);
-        __syncwarp();
-        dr[it] = (d << 16) | (prior + __popc(peers & lt));
-    }
-    __syncthreads();
+    const int d = threadIdx.x;  // the digit this thread publishes and looks back for
+    const unsigned long long tag = epoch << 34;
 
-    // Per digit: exclusive offsets across warps, then across digits.
-    const int d = threadIdx.x;
-    uint32_t tot_d = 0;
+    for (;;) {
+        if (threadIdx.x == 0) misc[0] = atomicAdd(tile_counter, 1u);
+        for (int i = threadIdx.x; i < kWarps * kBins; i += kThreads) wcnt[i] = 0;
+        __syncthreads();
+        const uint32_t tile = misc[0];
+        if (tile >= ntiles) break;
+        const uint64_t base = (uint64_t)tile * kRadixTile;
+        const uint32_t cnt = (uint32_t)min((uint64_t)kRadixTile, (uint64_t)n - base);
+
+        unsigned long long k[kItems];
+        uint32_t v[kItems];
 #pragma unroll
-    for (int w = 0; w < kWarps; ++w) {
-        uint32_t t = wcnt[w * kBins + d];
-        wcnt[w * kBins + d] = tot_d;
-        tot_d += t;
-    }
-    uint32_t tile_total;
-    uint32_t start = cta_exclusive_scan<SumOp, kThreads>(tot_d, tile_total);
-    dstart[d] = start;
-    gstart[d] = hist[(uint64_t)d * ntiles + tile];
-    __syncthreads();
+        for (int it = 0; it < kItems; ++it) {
+            const uint32_t i = warp * kWarpItems + it * 32 + lane;
+            const bool valid = i < cnt;
+            k[it] = valid ? kin[base + i] : 0ull;
+            v[it] = valid ? vin[base + i] : 0u;
+        }
+
+        // rank among equal digits of the warp, in index order
+        uint32_t* my = wcnt + warp * kBins;
+        uint32_t dr[kItems];
+#pragma unroll
+        for (int it = 0; it < kItems; ++it) {
+            const uint32_t i = warp * kWarpItems + it * 32 + lane;
+            const bool valid = i < cnt;
+            const uint32_t dg = (uint32_t)(k[it] >> shift) & (kBins - 1);
+            uint32_t peers = __ballot_sync(0xffffffffu, valid);
+            if (!valid) peers = ~peers;
+#pragma unroll
+            for (int b = 0; b < kRadixBits; ++b) {
+                const uint32_t bal = __ballot_sync(0xffffffffu, (dg >> b) & 1u);
+                peers &= ((dg >> b) & 1u) ? bal : ~bal;
+            }
+            const uint32_t prior = valid ? my[dg] : 0u;
+            __syncwarp();
+            if (valid && lane == __ffs(peers) - 1) my[dg] = prior + __popc(peers);
+            __syncwarp();
+            dr[it] = valid ? ((dg << 16) | (prior + __popc(peers & lt))) : 0xFFFFFFFFu;
+        }
+        __syncthreads();
+
+        // tile counts per digit; exclusive offsets across warps
+        uint32_t cnt_d = 0;
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) {
+            const uint32_t t = wcnt[w * kBins + d];
+            wcnt[w * kBins + d] = cnt_d;
+            cnt_d += t;
+        }
+        // publish this tile's count, then look back for the earlier tiles'
+        unsigned long long* lb = lookback + (uint64_t)tile * kBins + d;
+        uint32_t excl = 0;
+        if (tile == 0) {
+            store_volatile(lb, tag | kPrefix | cnt_d);
+        } else {
+            store_volatile(lb, tag | kAggregate | cnt_d);
+            int64_t kt = (int64_t)tile - 1;
+            uint32_t spins = 0;
+            while (kt >= 0) {
+                const unsigned long long w = load_volatile(lookback + (uint64_t)kt * kBins + d);
+                const unsigned long long state = (w >> 32) & 3ull;
+                if ((w & ~0x3FFFFFFFFull) != tag || state == 0) {
+                    if (++spins > kSpinLimit) {
+                        atomicOr(d_err, 64u);
+                        break;
+                    }
+                    if (spins > 64) __nanosleep(64);
+                    continue;
+                }
+                excl += (uint32_t)w;
+                if (state == 2) break;
+                --kt;
+            }
+            store_volatile(lb, tag | kPrefix | (excl + cnt_d));
+        }
+        uint32_t tile_total;
+        dstart[d] = cta_exclusive_scan<SumOp, kThreads>(cnt_d, tile_total);
+        gstart[d] = dstart_g[d] + excl;
+        __syncthreads();
 
 #pragma unroll
-    for (int it = 0; it < kItems; ++it) {
-        uint32_t dd = dr[it] >> 16;
-        if (dd < kBins) {
-            uint32_t pos = dstart[dd] + wcnt[warp * kBins + dd] + (dr[it] & 0xFFFFu);
+        for (int it = 0; it < kItems; ++it) {
+            if (dr[it] == 0xFFFFFFFFu) continue;
+            const uint32_t dd = dr[it] >> 16;
+            const uint32_t pos = dstart[dd] + wcnt[warp * kBins + dd] + (dr[it] & 0xFFFFu);
             if (pos < kRadixTile) {
                 skeys[pos] = k[it];
                 svals[pos] = v[it];
@@ -131,52 +192,76 @@ __global__ void __launch_bounds__(kThreads) radix_scatter_kernel(const unsigned 
                 atomicOr(d_err, 16u);
             }
         }
-    }
-    __syncthreads();
+        __syncthreads();
 
-    for (uint32_t s = threadIdx.x; s < cnt; s += kThreads) {
-        unsigned long long key = skeys[s];
-        uint32_t dd = (uint32_t)(key >> shift) & (kBins - 1);
-        uint64_t o = (uint64_t)gstart[dd] + (s - dstart[dd]);
-        if (o < n) {
-            kout[o] = key;
-            vout[o] = svals[s];
-        } else {
-            atomicOr(d_err, 16u);
+        for (uint32_t s = threadIdx.x; s < cnt; s += kThreads) {
+            const unsigned long long key = skeys[s];
+            const uint32_t dd = (uint32_t)(key >> shift) & (kBins - 1);
+            const uint64_t o = (uint64_t)gstart[dd] + (s - dstart[dd]);
+            if (o < n) {
+                kout[o] = key;
+                vout[o] = svals[s];
+            } else {
+                atomicOr(d_err, 16u);
+            }
         }
+        __syncthreads();
     }
+}
+
+int g_grid_cache[64] = {0};
+
+unsigned persistent_grid(uint64_t cap) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int& cached = g_grid_cache[dev & 63];
+    if (cached == 0) {
+        int sms = 0, per_sm = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, radix_onesweep_kernel, kThreads, kScatterSmem);
+        cached = std::max(1, sms) * std::max(1, per_sm);
+    }
+    const uint64_t tiles = cap / kRadixTile + 1;
+    return (unsigned)std::min<uint64_t>((uint64_t)cached, tiles);
 }
 
 }  // namespace
 
 size_t radix_temp_words(uint64_t cap) {
-    uint64_t tiles = cap / kRadixTile + 1;
-    return 64 + (size_t)(tiles * kBins) + scan_temp_words(tiles * kBins) + 64;
+    const uint64_t tiles = cap / kRadixTile + 1;
+    return kLookback + 2 * (size_t)tiles * kBins + 64;
 }
 
 void radix_init() {
-    cudaFuncSetAttribute(radix_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScatterSmem);
+    cudaFuncSetAttribute(radix_onesweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScatterSmem);
+    persistent_grid(0);
 }
 
 bool radix_sort_pairs(Launcher& L, unsigned long long* keys, uint32_t* vals, unsigned long long* keys_alt,
                       uint32_t* vals_alt, const uint32_t* d_n, uint64_t cap, int begin_bit, int end_bit,
                       uint32_t* temp, uint32_t* d_err) {
-    const uint64_t max_tiles = cap / kRadixTile + 1;
-    uint32_t* d_hist_len = temp;
-    uint32_t* hist = temp + 64;
-    uint32_t* stemp = hist + max_tiles * kBins;
-    const unsigned grid = (unsigned)(cap ? ceil_div_u(cap, kRadixTile) : 1);
+    const int passes = (end_bit - begin_bit + kRadixBits - 1) / kRadixBits;
+    if (passes <= 0) return false;
+    uint32_t* counters = temp + kCounters;
+    uint32_t* ghist = temp + kDigitStart;
+    unsigned long long* lookback = reinterpret_cast<unsigned long long*>(temp + kLookback);
+    static std::atomic<unsigned long long> epoch_counter{0};  // unique per pass across all sorts of the process
+    cudaMemsetAsync(temp, 0, (kDigitStart + (size_t)kMaxPasses * kBins) * 4, L.stream);
+    const unsigned grid = persistent_grid(cap);
+    SBWT_LAUNCH(L, "radix_histogram", 0, 8, d_n, radix_hist_kernel, grid, kThreads, 0, keys, d_n, begin_bit, passes,
+                ghist);
+    SBWT_LAUNCH(L, "radix_digit_scan", 8.0 * kBins * passes, 0, nullptr, radix_digit_scan_kernel, 1, kThreads, 0,
+                ghist, passes);
     bool alt = false;
-    for (int shift = begin_bit; shift < end_bit; shift += kRadixBits) {
-        unsigned long long* kin = alt ? keys_alt : keys;
-        uint32_t* vin = alt ? vals_alt : vals;
+    for (int p = 0; p < passes; ++p) {
+        const unsigned long long* kin = alt ? keys_alt : keys;
+        const uint32_t* vin = alt ? vals_alt : vals;
         unsigned long long* ko = alt ? keys : keys_alt;
         uint32_t* vo = alt ? vals : vals_alt;
-        SBWT_LAUNCH(L, "radix_upsweep", 0, 8, d_n, radix_hist_kernel, grid, kThreads, 0, kin, d_n, shift, hist,
-                    d_hist_len);
-        scan_exclusive_sum(L, hist, hist, d_hist_len, max_tiles * kBins, stemp, nullptr);
-        SBWT_LAUNCH(L, "radix_downsweep", 0, 24, d_n, radix_scatter_kernel, grid, kThreads, kScatterSmem, kin,
-                    vin, ko, vo, d_n, shift, hist, d_err);
+        const unsigned long long epoch = ++epoch_counter;
+        SBWT_LAUNCH(L, "radix_onesweep", 0, 24, d_n, radix_onesweep_kernel, grid, kThreads, kScatterSmem, kin, vin,
+                    ko, vo, d_n, begin_bit + kRadixBits * p, ghist + p * kBins, lookback, counters + p,
+                    epoch & 0x3FFFFFFFull, d_err);
         alt = !alt;
     }
     return alt;

@@ -76,6 +76,23 @@ __global__ void __launch_bounds__(kThreads) gather_kernel(const uint32_t* __rest
     gsa[i] = t < n ? g[t] : (IdxT)0;
 }
 
+// B_int and g_sa in one pass over SA_int (both index by SA_int[i]).
+template <class IdxT>
+__global__ void __launch_bounds__(kThreads) bint_gather_kernel(const uint32_t* __restrict__ text,
+                                                               const uint32_t* __restrict__ term,
+                                                               unsigned long long base,
+                                                               const uint32_t* __restrict__ sa,
+                                                               const IdxT* __restrict__ g, uint32_t n,
+                                                               uint8_t* __restrict__ bint,
+                                                               IdxT* __restrict__ gsa) {
+    const uint32_t i = blockIdx.x * kThreads + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t t = sa[i] < n ? sa[i] : 0u;
+    const uint64_t P = base + t;
+    bint[i] = (t == 0 || is_term(term, P - 1)) ? kBintDollar : (uint8_t)text_code(text, P - 1);
+    gsa[i] = g[t];
+}
+
 __global__ void __launch_bounds__(kThreads) rank_batch_kernel(const OccBlock* __restrict__ blocks,
                                                               const unsigned long long* __restrict__ super,
                                                               const uint8_t* __restrict__ codes,
@@ -141,6 +158,17 @@ void launch_gather(Launcher& L, const uint32_t* sa, const IdxT* g, uint32_t n, I
                 ceil_div_u(n, kThreads), kThreads, 0, sa, g, n, gsa);
 }
 
+template <class IdxT>
+void launch_bint_gather(Launcher& L, const uint32_t* text, const uint32_t* term, uint64_t base, const uint32_t* sa,
+                        const IdxT* g, uint32_t n, uint8_t* bint, IdxT* gsa) {
+    if (n == 0) return;
+    // per suffix: SA_int read, one text word and one bitmap word (random), a
+    // random g sector, B_int and g_sa writes
+    SBWT_LAUNCH(L, "bint_gather", (double)n * (4 + 4 + 4 + 32 + 1 + sizeof(IdxT)), 0, nullptr,
+                bint_gather_kernel<IdxT>, ceil_div_u(n, kThreads), kThreads, 0, text, term,
+                (unsigned long long)base, sa, g, n, bint, gsa);
+}
+
 void launch_rank_batch(Launcher& L, const OccBlock* blocks, const unsigned long long* super, const uint8_t* codes,
                        const unsigned long long* ks, uint64_t q, unsigned long long* out) {
     if (q == 0) return;
@@ -161,6 +189,11 @@ template void launch_compute_ranks<unsigned long long>(Launcher&, const uint32_t
                                                        uint64_t, uint64_t, const OccBlock*,
                                                        const unsigned long long*, const unsigned long long*,
                                                        uint64_t, uint64_t, unsigned long long*, uint32_t*);
+template void launch_bint_gather<uint32_t>(Launcher&, const uint32_t*, const uint32_t*, uint64_t, const uint32_t*,
+                                           const uint32_t*, uint32_t, uint8_t*, uint32_t*);
+template void launch_bint_gather<unsigned long long>(Launcher&, const uint32_t*, const uint32_t*, uint64_t,
+                                                     const uint32_t*, const unsigned long long*, uint32_t, uint8_t*,
+                                                     unsigned long long*);
 template void launch_gather<uint32_t>(Launcher&, const uint32_t*, const uint32_t*, uint32_t, uint32_t*);
 template void launch_gather<unsigned long long>(Launcher&, const uint32_t*, const unsigned long long*, uint32_t,
                                                 unsigned long long*);

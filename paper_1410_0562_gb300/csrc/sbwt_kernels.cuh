@@ -43,6 +43,10 @@ void launch_compute_ranks(Launcher& L, const uint32_t* text, const uint64_t* d_o
 // g_sa[i] = g[SA_int[i]].
 template <class IdxT>
 void launch_gather(Launcher& L, const uint32_t* sa, const IdxT* g, uint32_t n, IdxT* gsa);
+// B_int and g_sa fused: one pass over SA_int after ComputeRanks.
+template <class IdxT>
+void launch_bint_gather(Launcher& L, const uint32_t* text, const uint32_t* term, uint64_t base, const uint32_t* sa,
+                        const IdxT* g, uint32_t n, uint8_t* bint, IdxT* gsa);
 // rank queries: codes 0..3, or 4 for the terminator.
 void launch_rank_batch(Launcher& L, const OccBlock* blocks, const unsigned long long* super, const uint8_t* codes,
                        const unsigned long long* ks, uint64_t q, unsigned long long* out);
