@@ -255,7 +255,9 @@ def run_gb300(args):
             ev[k][1].record(stream)
         torch.cuda.synchronize()
     ms_steps = [a.elapsed_time(b) for a, b in ev]
-    stats = sb.sbwt_get_kernel_stats(idx.handle)
+    all_stats = sb.sbwt_get_kernel_stats(idx.handle)
+    stats = [s for s in all_stats if not s["name"].startswith("host:")]
+    host_phases = {s["name"][5:]: s["ms"] / args.steps for s in all_stats if s["name"].startswith("host:")}
     sb.sbwt_set_profiling(idx.handle, False)
     total_ms = float(sum(ms_steps))
     if dist:
@@ -339,6 +341,7 @@ def run_gb300(args):
         "e2e": e2e,
         "gpu_launches": launches,
         "kernels": kernels,
+        "host_ms_per_step": host_phases,
     }
     clocks = clk.summary()
     if clocks:

@@ -4,6 +4,7 @@
 //   ConstructSA -> B_int -> ComputeRanks -> g[SA_int] -> Insert.
 // Host code only orchestrates; every step of the path is a CUDA kernel.
 #include <algorithm>
+#include <chrono>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -54,8 +55,8 @@ struct sbwt_index {
     int cur = 0;
 
     DevBuf reads, offsets, text, term, err;
-    DevBuf keys, keys_alt, vals, vals_alt, sa, rank, tmp_a, tmp_b, act_pos0, act_pos1, act_suf0, act_suf1;
-    DevBuf radix_temp, scan_temp, count_log, g, gsa, bint, sb_tot;
+    DevBuf keys, keys_alt, vals, vals_alt, sa, rank, act_pos0, act_pos1, act_suf0, act_suf1;
+    DevBuf radix_temp, lookback, counters, count_log, g, gsa, bint, sb_tot;
     DevBuf out_bytes, q_codes, q_ks, q_out;
 
     uint32_t* h_err = nullptr;      // pinned
@@ -69,10 +70,11 @@ struct sbwt_index {
     bool last_idx64 = false;
 
     std::vector<DevBuf*> all_bufs() {
-        std::vector<DevBuf*> v = {&reads,  &offsets,  &text,     &term,     &err,        &keys,      &keys_alt,
-                                  &vals,   &vals_alt, &sa,       &rank,     &tmp_a,      &tmp_b,     &act_pos0,
-                                  &act_pos1, &act_suf0, &act_suf1, &radix_temp, &scan_temp, &count_log, &g,
-                                  &gsa,    &bint,     &sb_tot,   &out_bytes, &q_codes,   &q_ks,      &q_out};
+        std::vector<DevBuf*> v = {&reads,      &offsets,  &text,      &term,     &err,      &keys,
+                                  &keys_alt,   &vals,     &vals_alt,  &sa,       &rank,     &act_pos0,
+                                  &act_pos1,   &act_suf0, &act_suf1,  &radix_temp, &lookback, &counters,
+                                  &count_log,  &g,        &gsa,       &bint,     &sb_tot,   &out_bytes,
+                                  &q_codes,    &q_ks,     &q_out};
         for (auto& d : dict) {
             v.push_back(&d.blocks);
             v.push_back(&d.super);
@@ -126,7 +128,7 @@ int device_init(sbwt_index* idx) {
         idx->own_stream = true;
     }
     idx->L.stream = idx->stream;
-    radix_init();
+    suffix_sort_init();
     if (cudaMallocHost(&idx->h_err, sizeof(uint32_t)) != cudaSuccess) return SBWT_EDEVICE;
     // the committed dictionary starts empty: one zero block, one zero superblock, C = 0
     Dict& d = idx->dict[idx->cur];
@@ -193,11 +195,12 @@ std::vector<Need> buffer_needs(sbwt_index* idx, const Plan& p, bool host_input, 
     v.push_back({&idx->text, (size_t)((p.npos + 31) / 32 * 2 + kTextPadWords) * 4});
     v.push_back({&idx->term, (size_t)((p.npos + 31) / 32 + kTermPadWords) * 4});
     for (DevBuf* b : {&idx->keys, &idx->keys_alt}) v.push_back({b, (size_t)cap * 8});
-    for (DevBuf* b : {&idx->vals, &idx->vals_alt, &idx->sa, &idx->rank, &idx->tmp_a, &idx->tmp_b, &idx->act_pos0,
-                      &idx->act_pos1, &idx->act_suf0, &idx->act_suf1})
+    for (DevBuf* b : {&idx->vals, &idx->vals_alt, &idx->sa, &idx->rank, &idx->act_pos0, &idx->act_pos1,
+                      &idx->act_suf0, &idx->act_suf1})
         v.push_back({b, (size_t)cap * 4});
     v.push_back({&idx->radix_temp, radix_temp_words(cap) * 4});
-    v.push_back({&idx->scan_temp, scan_temp_words(cap) * 4});
+    v.push_back({&idx->lookback, suffix_sort_lookback_words(cap) * 8});
+    v.push_back({&idx->counters, p.slots * 4});
     v.push_back({&idx->count_log, p.slots * p.blocks.size() * 4});
     v.push_back({&idx->g, (size_t)cap * w});
     v.push_back({&idx->gsa, (size_t)cap * w});
@@ -237,14 +240,13 @@ void run_block(sbwt_index* idx, const BlockPlan& bp, const uint64_t* d_offsets, 
     b.vals_alt = (uint32_t*)idx->vals_alt.p;
     b.sa = (uint32_t*)idx->sa.p;
     b.rank = (uint32_t*)idx->rank.p;
-    b.tmp_a = (uint32_t*)idx->tmp_a.p;
-    b.tmp_b = (uint32_t*)idx->tmp_b.p;
     b.act_pos[0] = (uint32_t*)idx->act_pos0.p;
     b.act_pos[1] = (uint32_t*)idx->act_pos1.p;
     b.act_suf[0] = (uint32_t*)idx->act_suf0.p;
     b.act_suf[1] = (uint32_t*)idx->act_suf1.p;
     b.radix_temp = (uint32_t*)idx->radix_temp.p;
-    b.scan_temp = (uint32_t*)idx->scan_temp.p;
+    b.lookback = (unsigned long long*)idx->lookback.p;
+    b.counters = (uint32_t*)idx->counters.p;
     b.count_log = (uint32_t*)idx->count_log.p + slots * k;
     b.err = (uint32_t*)idx->err.p;
     const uint32_t* text = (const uint32_t*)idx->text.p;
@@ -263,7 +265,8 @@ void run_block(sbwt_index* idx, const BlockPlan& bp, const uint64_t* d_offsets, 
 }
 
 int append_impl(sbwt_index* idx, const uint8_t* d_reads, const uint64_t* d_offsets, const uint64_t* h_off,
-                uint64_t m_new, bool host_input, const uint8_t* h_reads) {
+                uint64_t m_new, bool host_input, const uint8_t* h_reads,
+                std::chrono::steady_clock::time_point t_start) {
     Plan p;
     p.nbytes = h_off[m_new];
     p.npos = p.nbytes + m_new;
@@ -281,8 +284,12 @@ int append_impl(sbwt_index* idx, const uint8_t* d_reads, const uint64_t* d_offse
     if (int rc = reserve(idx, buffer_needs(idx, p, host_input, m_new))) return rc;
     cudaStream_t s = idx->stream;
     Launcher& L = idx->L;
+    if (L.settle_units() != cudaSuccess) return SBWT_EDEVICE;  // the count log is about to be reused
+    idx->last_valid = false;  // the scratch arrays are about to be overwritten
     L.unit_log = (const uint32_t*)idx->count_log.p;
     L.unit_log_len = p.slots * p.blocks.size();
+    const auto t_plan = std::chrono::steady_clock::now();
+    L.add_host("host:plan", std::chrono::duration<double, std::milli>(t_plan - t_start).count());
 
     if (host_input) {
         if (p.nbytes) cudaMemcpyAsync(idx->reads.p, h_reads, p.nbytes, cudaMemcpyHostToDevice, s);
@@ -295,14 +302,11 @@ int append_impl(sbwt_index* idx, const uint8_t* d_reads, const uint64_t* d_offse
     cudaMemsetAsync((uint32_t*)idx->text.p + text_words, 0, kTextPadWords * 4, s);
     cudaMemsetAsync((uint32_t*)idx->term.p + term_words, 0, kTermPadWords * 4, s);
     cudaMemsetAsync(idx->err.p, 0, 4, s);
+    // A byte outside the alphabet sets bit 0 of the error word; the blocks
+    // still run (into scratch dictionaries) and the check at the end refuses
+    // the result, which saves a round trip on every valid append.
     launch_pack(L, d_reads, d_offsets, m_new, p.npos, idx->alpha4, idx->sigma, (uint32_t*)idx->text.p,
                 (uint32_t*)idx->term.p, (uint32_t*)idx->err.p);
-    cudaMemcpyAsync(idx->h_err, idx->err.p, 4, cudaMemcpyDeviceToHost, s);
-    if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) return SBWT_EDEVICE;
-    if (*idx->h_err) {
-        L.resolve();
-        return SBWT_EINVAL;
-    }
 
     int other[2], o = 0;
     for (int k = 0; k < 3; ++k)
@@ -322,18 +326,20 @@ int append_impl(sbwt_index* idx, const uint8_t* d_reads, const uint64_t* d_offse
         src = dst;
     }
     cudaMemcpyAsync(idx->h_err, idx->err.p, 4, cudaMemcpyDeviceToHost, s);
+    const auto t_launch = std::chrono::steady_clock::now();
+    L.add_host("host:launch", std::chrono::duration<double, std::milli>(t_launch - t_plan).count());
     if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) return SBWT_EDEVICE;
-    if (*idx->h_err) {  // a kernel caught an inconsistent index; keep the old one
-        L.resolve();
-        return SBWT_EDEVICE;
-    }
+    L.add_host("host:wait",
+               std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_launch).count());
+    if (L.settle_units() != cudaSuccess) return SBWT_EDEVICE;
+    if (*idx->h_err & 1u) return SBWT_EINVAL;  // a byte outside the alphabet; the index is unchanged
+    if (*idx->h_err) return SBWT_EDEVICE;      // a kernel caught an inconsistent index; keep the old one
     idx->cur = src;
     idx->n = n_ext;
     idx->m = m_ext;
     idx->last_valid = !p.blocks.empty();
     idx->last_n = p.blocks.empty() ? 0 : p.blocks.back().n_int;
     idx->last_idx64 = p.idx64;
-    if (L.resolve() != cudaSuccess) return SBWT_EDEVICE;
     return SBWT_OK;
 }
 
@@ -384,7 +390,7 @@ int Launcher::before(const char* name, double fixed, double per_unit, const uint
     const int s = stat_index(name);
     stats[s].launches++;
     if (!profiling) return -1;
-    Pending p{s, take_event(), take_event(), fixed, per_unit, d_units};
+    Pending p{s, take_event(), take_event(), fixed, per_unit, d_units, d_units == nullptr};
     cudaEventRecord(p.a, stream);
     pending_.push_back(p);
     return (int)pending_.size() - 1;
@@ -394,31 +400,45 @@ void Launcher::after(int token) {
     if (token >= 0) cudaEventRecord(pending_[token].b, stream);
 }
 
-cudaError_t Launcher::resolve() {
-    if (pending_.empty()) return cudaSuccess;
+cudaError_t Launcher::settle_units() {
+    bool any = false;
+    for (const Pending& p : pending_) any |= !p.settled;
+    if (!any) return cudaSuccess;
     std::vector<uint32_t> log(unit_log_len);
     cudaError_t err = cudaSuccess;
     if (unit_log_len) err = cudaMemcpy(log.data(), unit_log, unit_log_len * 4, cudaMemcpyDeviceToHost);
+    for (Pending& p : pending_) {
+        if (p.settled) continue;
+        uint32_t u = 0;
+        if (p.units >= unit_log && p.units < unit_log + unit_log_len)
+            u = log[p.units - unit_log];
+        else
+            cudaMemcpy(&u, p.units, 4, cudaMemcpyDeviceToHost);
+        p.fixed += p.per_unit * u;
+        p.per_unit = 0;
+        p.settled = true;
+    }
+    return err;
+}
+
+cudaError_t Launcher::resolve() {
+    cudaError_t err = settle_units();
     for (const Pending& p : pending_) {
         float ms = 0;
         if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) stats[p.stat].ms += ms;
-        double units = 0;
-        if (p.units) {
-            if (p.units >= unit_log && p.units < unit_log + unit_log_len) {
-                units = log[p.units - unit_log];
-            } else {
-                uint32_t u = 0;
-                cudaMemcpy(&u, p.units, 4, cudaMemcpyDeviceToHost);
-                units = u;
-            }
-        }
-        stats[p.stat].bytes += p.fixed + p.per_unit * units;
+        stats[p.stat].bytes += p.fixed;
         free_events_.push_back(p.a);
         free_events_.push_back(p.b);
     }
     pending_.clear();
     cudaGetLastError();
     return err;
+}
+
+void Launcher::add_host(const char* name, double ms) {
+    const int s = stat_index(name);
+    stats[s].launches++;
+    stats[s].ms += ms;
 }
 
 void Launcher::reset() {
@@ -491,14 +511,16 @@ int sbwt_create(const char* alphabet, size_t hbm_budget_bytes, sbwt_index** out)
 
 int sbwt_append(sbwt_index* idx, const uint8_t* reads, const uint64_t* offsets, uint64_t m) {
     if (!idx || !offsets) return SBWT_EINVAL;
+    const auto t0 = std::chrono::steady_clock::now();
     if (validate_offsets(offsets, m)) return SBWT_EINVAL;
     if (m == 0) return SBWT_OK;
     if (offsets[m] > 0 && !reads) return SBWT_EINVAL;
-    return append_impl(idx, nullptr, nullptr, offsets, m, true, reads);
+    return append_impl(idx, nullptr, nullptr, offsets, m, true, reads, t0);
 }
 
 int sbwt_append_device(sbwt_index* idx, const uint8_t* d_reads, const uint64_t* d_offsets, uint64_t m) {
     if (!idx || !d_offsets) return SBWT_EINVAL;
+    const auto t0 = std::chrono::steady_clock::now();
     if (int rc = device_init(idx)) return rc;
     if (m + 1 > idx->h_offsets_cap) {
         if (idx->h_offsets) cudaFreeHost(idx->h_offsets);
@@ -514,7 +536,7 @@ int sbwt_append_device(sbwt_index* idx, const uint8_t* d_reads, const uint64_t* 
     if (validate_offsets(idx->h_offsets, m)) return SBWT_EINVAL;
     if (m == 0) return SBWT_OK;
     if (idx->h_offsets[m] > 0 && !d_reads) return SBWT_EINVAL;
-    return append_impl(idx, d_reads, d_offsets, idx->h_offsets, m, false, nullptr);
+    return append_impl(idx, d_reads, d_offsets, idx->h_offsets, m, false, nullptr, t0);
 }
 
 int sbwt_get_bwt(sbwt_index* idx, uint8_t* out, uint64_t cap, uint64_t* n_out) {
@@ -529,7 +551,6 @@ int sbwt_get_bwt(sbwt_index* idx, uint8_t* out, uint64_t cap, uint64_t* n_out) {
                   (uint8_t*)idx->out_bytes.p);
     cudaMemcpyAsync(out, idx->out_bytes.p, idx->n, cudaMemcpyDeviceToHost, idx->stream);
     if (cudaStreamSynchronize(idx->stream) != cudaSuccess || cudaGetLastError() != cudaSuccess) return SBWT_EDEVICE;
-    idx->L.resolve();
     return SBWT_OK;
 }
 
@@ -558,7 +579,6 @@ int sbwt_rank_batch(sbwt_index* idx, const uint8_t* cs, const uint64_t* ks, uint
                       (unsigned long long*)idx->q_out.p);
     cudaMemcpyAsync(out, idx->q_out.p, q * 8, cudaMemcpyDeviceToHost, s);
     if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) return SBWT_EDEVICE;
-    idx->L.resolve();
     return SBWT_OK;
 }
 
@@ -653,6 +673,10 @@ int sbwt_set_profiling(sbwt_index* idx, int on) {
 
 int sbwt_get_kernel_stats(sbwt_index* idx, sbwt_kernel_stat* out, int cap, int* n_out) {
     if (!idx || !n_out) return SBWT_EINVAL;
+    if (idx->dev_ready) {
+        if (set_device(idx) || cudaStreamSynchronize(idx->stream) != cudaSuccess) return SBWT_EDEVICE;
+        if (idx->L.resolve() != cudaSuccess) return SBWT_EDEVICE;
+    }
     const auto& st = idx->L.stats;
     *n_out = (int)st.size();
     for (int i = 0; i < cap && i < (int)st.size(); ++i) {

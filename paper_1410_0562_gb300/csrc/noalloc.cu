@@ -33,12 +33,13 @@ constexpr size_t kText = kOffsets + up256((kMax + 1) * 8);
 constexpr size_t kTerm = kText + up256(((kMax + 31) / 32 * 2 + kTextPadWords) * 4);
 constexpr size_t kKeys = kTerm + up256(((kMax + 31) / 32 + kTermPadWords) * 4);
 constexpr size_t kKeysAlt = kKeys + up256(kMax * 8);
-constexpr size_t kU32 = kKeysAlt + up256(kMax * 8);  // ten arrays of kMax uint32
-constexpr size_t kRadixTemp = kU32 + 10 * up256(kMax * 4);
-constexpr size_t kRadixTempBytes = 128 * 1024;  // radix_temp_words(kMax) * 4 must fit (checked at set-up)
-constexpr size_t kScanTemp = kRadixTemp + kRadixTempBytes;
-constexpr size_t kScanTempBytes = 4096;
-constexpr size_t kCountLog = kScanTemp + kScanTempBytes;
+constexpr size_t kU32 = kKeysAlt + up256(kMax * 8);  // eight arrays of kMax uint32
+constexpr size_t kRadixTemp = kU32 + 8 * up256(kMax * 4);
+constexpr size_t kRadixTempBytes = 256 * 1024;  // radix_temp_words(kMax) * 4 must fit (checked at set-up)
+constexpr size_t kLookback = kRadixTemp + kRadixTempBytes;
+constexpr size_t kLookbackBytes = 4096;  // suffix_sort_lookback_words(kMax) * 8 must fit (checked at set-up)
+constexpr size_t kCounters = kLookback + kLookbackBytes;
+constexpr size_t kCountLog = kCounters + 256;
 constexpr size_t kCountLogBytes = 256;
 constexpr size_t kBint = kCountLog + kCountLogBytes;
 constexpr size_t kOut = kBint + up256(kMax);
@@ -71,10 +72,10 @@ int setup(int dev, DeviceState** out) {
             cudaGetLastError();
             return SBWT_EDEVICE;
         }
-        if (radix_temp_words(kMax) * 4 > kRadixTempBytes || scan_temp_words(kMax) * 4 > kScanTempBytes ||
+        if (radix_temp_words(kMax) * 4 > kRadixTempBytes || suffix_sort_lookback_words(kMax) * 8 > kLookbackBytes ||
             suffix_sort_log_slots((uint32_t)kMax) * 4 > kCountLogBytes)
             return SBWT_EDEVICE;
-        radix_init();
+        suffix_sort_init();
         st.base = static_cast<unsigned char*>(p);
         st.ready = true;
     }
@@ -161,14 +162,13 @@ extern "C" int sbwt_bwt_noalloc(const char* alphabet, const uint8_t* reads, cons
     sb.vals_alt = u32 + stride;
     sb.sa = u32 + 2 * stride;
     sb.rank = u32 + 3 * stride;
-    sb.tmp_a = u32 + 4 * stride;
-    sb.tmp_b = u32 + 5 * stride;
-    sb.act_pos[0] = u32 + 6 * stride;
-    sb.act_pos[1] = u32 + 7 * stride;
-    sb.act_suf[0] = u32 + 8 * stride;
-    sb.act_suf[1] = u32 + 9 * stride;
+    sb.act_pos[0] = u32 + 4 * stride;
+    sb.act_pos[1] = u32 + 5 * stride;
+    sb.act_suf[0] = u32 + 6 * stride;
+    sb.act_suf[1] = u32 + 7 * stride;
     sb.radix_temp = reinterpret_cast<uint32_t*>(b + kRadixTemp);
-    sb.scan_temp = reinterpret_cast<uint32_t*>(b + kScanTemp);
+    sb.lookback = reinterpret_cast<unsigned long long*>(b + kLookback);
+    sb.counters = reinterpret_cast<uint32_t*>(b + kCounters);
     sb.count_log = reinterpret_cast<uint32_t*>(b + kCountLog);
     sb.err = err;
     uint8_t* bint = b + kBint;

@@ -3,19 +3,14 @@
 // suffix sorting of a block (Section 3 of arXiv 1410.0562 sorts suffixes as
 // long integer keys of packed symbols, refined over iterations).
 //
-// One read of the keys builds the digit histograms of every pass at once;
-// each digit pass is then a single persistent kernel (the single-pass
-// "onesweep" scheme of Adinets and Merrill): a CTA takes the next tile in
-// order, ranks its keys per digit (8 warp ballots give each lane the mask of
-// lanes with the same digit), publishes its per-digit counts, finds the
-// counts of all earlier tiles by decoupled look-back, stages the tile in
-// shared memory in digit order and writes it out in coalesced runs.
-//
-// The look-back waits only on tiles taken earlier, by CTAs already running,
-// so it always ends; every wait is still bounded, and a CTA that gives up
-// flags *d_err (bit 6) and goes on with a wrong count whose writes the bounds
-// checks drop.  Look-back words carry an epoch so the buffer never needs
-// clearing: a word from an earlier pass reads as "not ready".
+// The digit histograms of every pass come from one read of the keys (or
+// from the kernel that wrote them); each digit pass is then one persistent
+// kernel (the single-pass "onesweep" scheme of Adinets and Merrill): a CTA
+// takes the next tile in order, ranks its keys per digit (8 warp ballots give
+// each lane the mask of lanes with the same digit), publishes its per-digit
+// counts, finds the counts of all earlier tiles by decoupled look-back,
+// stages the tile in shared memory in digit order and writes it out in
+// coalesced runs.
 #include <algorithm>
 #include <atomic>
 
@@ -28,46 +23,29 @@ constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kItems = kRadixTile / kThreads;      // 16 keys per thread
 constexpr int kWarpItems = kRadixTile / kWarps;    // 512 consecutive keys per warp
-constexpr int kBins = 1 << kRadixBits;             // 256
-constexpr int kMaxPasses = 8;
+constexpr int kBins = kRadixBins;
 static_assert(kBins == kThreads, "one thread per digit");
 
 constexpr size_t kScatterSmem = (size_t)kRadixTile * 8 + (size_t)kRadixTile * 4 + (size_t)kWarps * kBins * 4 +
                                 (size_t)kBins * 4 * 3 + 16;
 
-// look-back word: [63:34] epoch, [33:32] state, [31:0] count
-constexpr unsigned long long kAggregate = 1ull << 32;
-constexpr unsigned long long kPrefix = 2ull << 32;
-constexpr uint32_t kSpinLimit = 1u << 22;
-
-// Temp layout (32-bit words): [0, 8) tile counters, [8, 8 + 8*256) digit
-// starts of every pass, then the look-back words (8-byte aligned).
+// Temp layout (32-bit words): [0, 8) tile counters of the passes, [8, 8 +
+// 8*256) digit histograms / starts of every pass, then the look-back words.
 constexpr size_t kCounters = 0;
 constexpr size_t kDigitStart = 8;
-constexpr size_t kLookback = kDigitStart + (size_t)kMaxPasses * kBins + 8;
+constexpr size_t kLookback = kDigitStart + (size_t)kRadixMaxPasses * kBins + 8;
 
-__device__ __forceinline__ void store_volatile(unsigned long long* p, unsigned long long v) {
-    *reinterpret_cast<volatile unsigned long long*>(p) = v;
-}
-__device__ __forceinline__ unsigned long long load_volatile(const unsigned long long* p) {
-    return *reinterpret_cast<const volatile unsigned long long*>(p);
-}
-
-// Digit histograms of every pass in one read of the keys.
 __global__ void __launch_bounds__(kThreads) radix_hist_kernel(const unsigned long long* __restrict__ keys,
                                                               const uint32_t* __restrict__ d_n, int begin_bit,
                                                               int passes, uint32_t* __restrict__ ghist) {
-    __shared__ uint32_t h[kMaxPasses * kBins];
+    __shared__ uint32_t h[kRadixMaxPasses * kBins];
     for (int i = threadIdx.x; i < passes * kBins; i += kThreads) h[i] = 0;
     __syncthreads();
     const uint32_t n = *d_n;
-    for (uint64_t i = (uint64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (uint64_t)gridDim.x * kThreads) {
-        const unsigned long long k = keys[i] >> begin_bit;
-        for (int p = 0; p < passes; ++p) atomicAdd(&h[p * kBins + ((k >> (kRadixBits * p)) & (kBins - 1))], 1u);
-    }
+    for (uint64_t i = (uint64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (uint64_t)gridDim.x * kThreads)
+        radix_hist_add(h, keys[i], begin_bit, passes);
     __syncthreads();
-    for (int i = threadIdx.x; i < passes * kBins; i += kThreads)
-        if (h[i]) atomicAdd(&ghist[i], h[i]);
+    radix_hist_flush<kThreads>(h, ghist, passes);
 }
 
 // Exclusive scan of each pass's histogram into digit start offsets.
@@ -97,7 +75,7 @@ __global__ void __launch_bounds__(kThreads, 2) radix_onesweep_kernel(
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t lt = (1u << lane) - 1u;
     const int d = threadIdx.x;  // the digit this thread publishes and looks back for
-    const unsigned long long tag = epoch << 34;
+    const unsigned long long tag = lb_tag(epoch);
 
     for (;;) {
         if (threadIdx.x == 0) misc[0] = atomicAdd(tile_counter, 1u);
@@ -153,27 +131,11 @@ __global__ void __launch_bounds__(kThreads, 2) radix_onesweep_kernel(
         unsigned long long* lb = lookback + (uint64_t)tile * kBins + d;
         uint32_t excl = 0;
         if (tile == 0) {
-            store_volatile(lb, tag | kPrefix | cnt_d);
+            lb_store(lb, tag | kLbPrefix | cnt_d);
         } else {
-            store_volatile(lb, tag | kAggregate | cnt_d);
-            int64_t kt = (int64_t)tile - 1;
-            uint32_t spins = 0;
-            while (kt >= 0) {
-                const unsigned long long w = load_volatile(lookback + (uint64_t)kt * kBins + d);
-                const unsigned long long state = (w >> 32) & 3ull;
-                if ((w & ~0x3FFFFFFFFull) != tag || state == 0) {
-                    if (++spins > kSpinLimit) {
-                        atomicOr(d_err, 64u);
-                        break;
-                    }
-                    if (spins > 64) __nanosleep(64);
-                    continue;
-                }
-                excl += (uint32_t)w;
-                if (state == 2) break;
-                --kt;
-            }
-            store_volatile(lb, tag | kPrefix | (excl + cnt_d));
+            lb_store(lb, tag | kLbAggregate | cnt_d);
+            excl = lb_lookback<SumOp>(lookback + d, kBins, tile, tag, d_err, 64u);
+            lb_store(lb, tag | kLbPrefix | (excl + cnt_d));
         }
         uint32_t tile_total;
         dstart[d] = cta_exclusive_scan<SumOp, kThreads>(cnt_d, tile_total);
@@ -209,23 +171,34 @@ __global__ void __launch_bounds__(kThreads, 2) radix_onesweep_kernel(
     }
 }
 
-int g_grid_cache[64] = {0};
+std::atomic<unsigned long long> g_epoch{0};
+unsigned g_onesweep_ctas[64] = {0};
+unsigned g_hist_ctas[64] = {0};
 
-unsigned persistent_grid(uint64_t cap) {
+int current_device() {
     int dev = 0;
     cudaGetDevice(&dev);
-    int& cached = g_grid_cache[dev & 63];
-    if (cached == 0) {
-        int sms = 0, per_sm = 0;
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, radix_onesweep_kernel, kThreads, kScatterSmem);
-        cached = std::max(1, sms) * std::max(1, per_sm);
-    }
-    const uint64_t tiles = cap / kRadixTile + 1;
-    return (unsigned)std::min<uint64_t>((uint64_t)cached, tiles);
+    return dev & 63;
 }
 
 }  // namespace
+
+unsigned long long lb_next_epoch() {
+    unsigned long long e;
+    do {
+        e = (++g_epoch) & 0x3FFFFFFFull;
+    } while (e == 0);
+    return e;
+}
+
+unsigned persistent_ctas(const void* kernel, int threads, size_t smem) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
+    cudaGetLastError();
+    return (unsigned)(std::max(1, sms) * std::max(1, per_sm));
+}
 
 size_t radix_temp_words(uint64_t cap) {
     const uint64_t tiles = cap / kRadixTile + 1;
@@ -234,22 +207,34 @@ size_t radix_temp_words(uint64_t cap) {
 
 void radix_init() {
     cudaFuncSetAttribute(radix_onesweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScatterSmem);
-    persistent_grid(0);
+    const int dev = current_device();
+    g_onesweep_ctas[dev] = persistent_ctas((const void*)radix_onesweep_kernel, kThreads, kScatterSmem);
+    g_hist_ctas[dev] = persistent_ctas((const void*)radix_hist_kernel, kThreads, 0);
+}
+
+uint32_t* radix_histograms(uint32_t* temp) { return temp + kDigitStart; }
+
+void radix_hist_clear(Launcher& L, uint32_t* temp) {
+    cudaMemsetAsync(temp, 0, (kDigitStart + (size_t)kRadixMaxPasses * kBins) * 4, L.stream);
 }
 
 bool radix_sort_pairs(Launcher& L, unsigned long long* keys, uint32_t* vals, unsigned long long* keys_alt,
                       uint32_t* vals_alt, const uint32_t* d_n, uint64_t cap, int begin_bit, int end_bit,
-                      uint32_t* temp, uint32_t* d_err) {
-    const int passes = (end_bit - begin_bit + kRadixBits - 1) / kRadixBits;
+                      uint32_t* temp, uint32_t* d_err, bool hist_ready) {
+    const int passes = radix_passes(begin_bit, end_bit);
     if (passes <= 0) return false;
     uint32_t* counters = temp + kCounters;
     uint32_t* ghist = temp + kDigitStart;
     unsigned long long* lookback = reinterpret_cast<unsigned long long*>(temp + kLookback);
-    static std::atomic<unsigned long long> epoch_counter{0};  // unique per pass across all sorts of the process
-    cudaMemsetAsync(temp, 0, (kDigitStart + (size_t)kMaxPasses * kBins) * 4, L.stream);
-    const unsigned grid = persistent_grid(cap);
-    SBWT_LAUNCH(L, "radix_histogram", 0, 8, d_n, radix_hist_kernel, grid, kThreads, 0, keys, d_n, begin_bit, passes,
-                ghist);
+    const int dev = current_device();
+    const uint64_t tiles = cap / kRadixTile + 1;
+    const unsigned grid = (unsigned)std::min<uint64_t>(std::max(1u, g_onesweep_ctas[dev]), tiles);
+    if (!hist_ready) {
+        radix_hist_clear(L, temp);
+        const unsigned hgrid = (unsigned)std::min<uint64_t>(std::max(1u, g_hist_ctas[dev]), cap / kThreads + 1);
+        SBWT_LAUNCH(L, "radix_histogram", 0, 8, d_n, radix_hist_kernel, hgrid, kThreads, 0, keys, d_n, begin_bit,
+                    passes, ghist);
+    }
     SBWT_LAUNCH(L, "radix_digit_scan", 8.0 * kBins * passes, 0, nullptr, radix_digit_scan_kernel, 1, kThreads, 0,
                 ghist, passes);
     bool alt = false;
@@ -258,10 +243,9 @@ bool radix_sort_pairs(Launcher& L, unsigned long long* keys, uint32_t* vals, uns
         const uint32_t* vin = alt ? vals_alt : vals;
         unsigned long long* ko = alt ? keys : keys_alt;
         uint32_t* vo = alt ? vals : vals_alt;
-        const unsigned long long epoch = ++epoch_counter;
         SBWT_LAUNCH(L, "radix_onesweep", 0, 24, d_n, radix_onesweep_kernel, grid, kThreads, kScatterSmem, kin, vin,
                     ko, vo, d_n, begin_bit + kRadixBits * p, ghist + p * kBins, lookback, counters + p,
-                    epoch & 0x3FFFFFFFull, d_err);
+                    lb_next_epoch(), d_err);
         alt = !alt;
     }
     return alt;

@@ -16,15 +16,18 @@ void launch_pack(Launcher& L, const uint8_t* d_reads, const uint64_t* d_offsets,
 struct SuffixSortBuffers {
     unsigned long long *keys, *keys_alt;  // n each
     uint32_t *vals, *vals_alt;            // n each
-    uint32_t *sa, *rank, *tmp_a, *tmp_b;  // n each
+    uint32_t *sa, *rank;                  // n each
     uint32_t *act_pos[2], *act_suf[2];    // n each
     uint32_t* radix_temp;                 // radix_temp_words(n)
-    uint32_t* scan_temp;                  // scan_temp_words(n)
+    unsigned long long* lookback;         // suffix_sort_lookback_words(n)
+    uint32_t* counters;                   // suffix_sort_log_slots(max_len) words
     uint32_t* count_log;                  // suffix_sort_log_slots(max_len) words
-    uint32_t* err;                        // error flags (bit 2: a doubling offset left its block)
+    uint32_t* err;                        // error flags (bits 2..7)
 };
+void suffix_sort_init();  // once per device (includes radix_init)
 uint32_t suffix_sort_rounds(uint32_t max_len);
 size_t suffix_sort_log_slots(uint32_t max_len);
+size_t suffix_sort_lookback_words(uint64_t cap);
 void suffix_sort_block(Launcher& L, const uint32_t* text, const uint32_t* term, uint64_t base, uint32_t n,
                        uint32_t max_len, const SuffixSortBuffers& b);
 
