@@ -21,7 +21,8 @@ arrays into it.  Every function cites the passage of the paper it follows:
   start value ``i := m_ext``.
 * :func:`insert` -- Insert (Algorithm 1, Section 5) as a stable merge.
 * :func:`setbwte` -- Algorithm 1 over given block boundaries.
-* :func:`lf_invert` -- recovers the reads from B by LF steps.
+* :func:`lf_invert`, :func:`lf_invert_sampled` -- recover the reads from B
+  by LF steps.
 * :func:`row_of_suffix`, :func:`bwt_symbol_of_suffix` -- one suffix's row and
   B symbol, for sampled checks at large sizes.
 
@@ -89,6 +90,8 @@ def _declare(lib):
     lib.oracle_setbwte.restype = I
     lib.oracle_lf_invert.argtypes = [P, U64, U64, P, I, P, U64, P]
     lib.oracle_lf_invert.restype = I
+    lib.oracle_lf_invert_sampled.argtypes = [P, U64, U64, P, I, P, U64, P]
+    lib.oracle_lf_invert_sampled.restype = I
     lib.oracle_row_of_suffix.argtypes = [P, P, U64, U64, U64]
     lib.oracle_row_of_suffix.restype = U64
     lib.oracle_bwt_symbol_of_suffix.argtypes = [P, P, U64, U64]
@@ -226,6 +229,16 @@ def lf_invert(B, m: int, alphabet: bytes = b"ACGT"):
     offsets = np.zeros(m + 1, dtype=np.uint64)
     _check(_load().oracle_lf_invert(_ptr(B), len(B), m, _ptr(alpha), len(alpha), _ptr(reads), len(reads),
                                     _ptr(offsets)), "oracle_lf_invert")
+    return reads[: int(offsets[-1])], offsets
+
+
+def lf_invert_sampled(B, m: int, alphabet: bytes = b"ACGT"):
+    """lf_invert with rank counts every 64 rows (for large B)."""
+    B, alpha = _u8(B), _u8(alphabet)
+    reads = np.zeros(max(len(B), 1), dtype=np.uint8)
+    offsets = np.zeros(m + 1, dtype=np.uint64)
+    _check(_load().oracle_lf_invert_sampled(_ptr(B), len(B), m, _ptr(alpha), len(alpha), _ptr(reads), len(reads),
+                                            _ptr(offsets)), "oracle_lf_invert_sampled")
     return reads[: int(offsets[-1])], offsets
 
 

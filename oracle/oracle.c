@@ -29,8 +29,9 @@
  *     new symbol i lands on row g_sa[i] + i, old rows keep their order.
  *   - oracle_setbwte: Algorithm 1 end to end, block by block, built from the
  *     four functions above.
- *   - oracle_lf_invert: recovers every read from B by LF steps (the FM-index
- *     inversion that Lemma 1 rests on).
+ *   - oracle_lf_invert / oracle_lf_invert_sampled: recover every read from B
+ *     by LF steps (the FM-index inversion that Lemma 1 rests on), with a full
+ *     prefix-count table or with counts every 64 rows.
  *   - oracle_row_of_suffix: row of one suffix in the full sorted order, by
  *     counting the smaller suffixes one comparison at a time (for sampled
  *     checks at sizes where sorting everything is too slow).
@@ -461,6 +462,73 @@ int oracle_lf_invert(const uint8_t *B, uint64_t n, uint64_t m,
         offsets_out[r + 1] = w;
     }
     free(occ);
+    free(tmp);
+    return rc;
+}
+
+/* The same inversion with a lighter rank: counts of every code at each 64th
+ * row, plus a plain count of the rows in between (for sets too large for
+ * the full prefix-count table above).  Same contract as oracle_lf_invert. */
+int oracle_lf_invert_sampled(const uint8_t *B, uint64_t n, uint64_t m, const uint8_t *alphabet, int sigma,
+                             uint8_t *reads_out, uint64_t cap, uint64_t *offsets_out) {
+    const uint64_t nck = n / 64 + 1;
+    uint64_t *ck = (uint64_t *)calloc(nck * (size_t)(sigma + 1), sizeof(uint64_t));
+    int8_t *code = (int8_t *)malloc(n + 1);
+    uint8_t *tmp = (uint8_t *)malloc(n + 1);
+    if (!ck || !code || !tmp) {
+        free(ck);
+        free(code);
+        free(tmp);
+        return ORACLE_ENOMEM;
+    }
+    int rc = ORACLE_OK;
+    uint64_t tot[5] = {0, 0, 0, 0, 0};
+    for (uint64_t k = 0; k < n && !rc; ++k) {
+        if (k % 64 == 0)
+            for (int y = 0; y <= sigma; ++y) ck[(k / 64) * (sigma + 1) + y] = tot[y];
+        int x = bcode(B[k], alphabet, sigma);
+        if (x < 0) rc = ORACLE_EINVAL;
+        else {
+            code[k] = (int8_t)x;
+            ++tot[x];
+        }
+    }
+    if (!rc && n % 64 == 0)
+        for (int y = 0; y <= sigma; ++y) ck[(n / 64) * (sigma + 1) + y] = tot[y];
+    if (!rc && tot[0] != m) rc = ORACLE_EINVAL;
+    uint64_t C[5] = {0, 0, 0, 0, 0};
+    for (int x = 1; x <= sigma && !rc; ++x) C[x] = C[x - 1] + tot[x - 1];
+    uint64_t w = 0;
+    if (!rc) offsets_out[0] = 0;
+    for (uint64_t r = 0; r < m && !rc; ++r) {
+        uint64_t i = r, len = 0;
+        for (;;) {
+            int x = code[i];
+            if (x == 0) break;
+            if (len >= n) {
+                rc = ORACLE_EINVAL;
+                break;
+            }
+            tmp[len++] = B[i];
+            uint64_t rank = ck[(i / 64) * (sigma + 1) + x];
+            for (uint64_t q = i - i % 64; q < i; ++q) rank += code[q] == x;
+            i = C[x] + rank;
+            if (i >= n) {
+                rc = ORACLE_EINVAL;
+                break;
+            }
+        }
+        if (rc) break;
+        if (w + len > cap) {
+            rc = ORACLE_EINVAL;
+            break;
+        }
+        for (uint64_t q = 0; q < len; ++q) reads_out[w + q] = tmp[len - 1 - q];
+        w += len;
+        offsets_out[r + 1] = w;
+    }
+    free(ck);
+    free(code);
     free(tmp);
     return rc;
 }

@@ -56,7 +56,7 @@ struct sbwt_index {
 
     DevBuf reads, offsets, text, term, err;
     DevBuf keys, keys_alt, vals, vals_alt, sa, rank, act_pos0, act_pos1, act_suf0, act_suf1;
-    DevBuf radix_temp, lookback, counters, count_log, g, gsa, bint, sb_tot;
+    DevBuf radix_temp, chunks, count_log, g, gsa, bint, sb_tot;
     DevBuf out_bytes, q_codes, q_ks, q_out;
 
     uint32_t* h_err = nullptr;      // pinned
@@ -72,7 +72,7 @@ struct sbwt_index {
     std::vector<DevBuf*> all_bufs() {
         std::vector<DevBuf*> v = {&reads,      &offsets,  &text,      &term,     &err,      &keys,
                                   &keys_alt,   &vals,     &vals_alt,  &sa,       &rank,     &act_pos0,
-                                  &act_pos1,   &act_suf0, &act_suf1,  &radix_temp, &lookback, &counters,
+                                  &act_pos1,   &act_suf0, &act_suf1,  &radix_temp, &chunks,
                                   &count_log,  &g,        &gsa,       &bint,     &sb_tot,   &out_bytes,
                                   &q_codes,    &q_ks,     &q_out};
         for (auto& d : dict) {
@@ -199,8 +199,7 @@ std::vector<Need> buffer_needs(sbwt_index* idx, const Plan& p, bool host_input, 
                       &idx->act_suf0, &idx->act_suf1})
         v.push_back({b, (size_t)cap * 4});
     v.push_back({&idx->radix_temp, radix_temp_words(cap) * 4});
-    v.push_back({&idx->lookback, suffix_sort_lookback_words(cap) * 8});
-    v.push_back({&idx->counters, p.slots * 4});
+    v.push_back({&idx->chunks, suffix_sort_chunk_words(cap) * 8});
     v.push_back({&idx->count_log, p.slots * p.blocks.size() * 4});
     v.push_back({&idx->g, (size_t)cap * w});
     v.push_back({&idx->gsa, (size_t)cap * w});
@@ -245,8 +244,7 @@ void run_block(sbwt_index* idx, const BlockPlan& bp, const uint64_t* d_offsets, 
     b.act_suf[0] = (uint32_t*)idx->act_suf0.p;
     b.act_suf[1] = (uint32_t*)idx->act_suf1.p;
     b.radix_temp = (uint32_t*)idx->radix_temp.p;
-    b.lookback = (unsigned long long*)idx->lookback.p;
-    b.counters = (uint32_t*)idx->counters.p;
+    b.chunks = (unsigned long long*)idx->chunks.p;
     b.count_log = (uint32_t*)idx->count_log.p + slots * k;
     b.err = (uint32_t*)idx->err.p;
     const uint32_t* text = (const uint32_t*)idx->text.p;

@@ -36,10 +36,9 @@ constexpr size_t kKeysAlt = kKeys + up256(kMax * 8);
 constexpr size_t kU32 = kKeysAlt + up256(kMax * 8);  // eight arrays of kMax uint32
 constexpr size_t kRadixTemp = kU32 + 8 * up256(kMax * 4);
 constexpr size_t kRadixTempBytes = 256 * 1024;  // radix_temp_words(kMax) * 4 must fit (checked at set-up)
-constexpr size_t kLookback = kRadixTemp + kRadixTempBytes;
-constexpr size_t kLookbackBytes = 4096;  // suffix_sort_lookback_words(kMax) * 8 must fit (checked at set-up)
-constexpr size_t kCounters = kLookback + kLookbackBytes;
-constexpr size_t kCountLog = kCounters + 256;
+constexpr size_t kChunks = kRadixTemp + kRadixTempBytes;
+constexpr size_t kChunksBytes = 16384;  // suffix_sort_chunk_words(kMax) * 8 must fit (checked at set-up)
+constexpr size_t kCountLog = kChunks + kChunksBytes;
 constexpr size_t kCountLogBytes = 256;
 constexpr size_t kBint = kCountLog + kCountLogBytes;
 constexpr size_t kOut = kBint + up256(kMax);
@@ -72,7 +71,7 @@ int setup(int dev, DeviceState** out) {
             cudaGetLastError();
             return SBWT_EDEVICE;
         }
-        if (radix_temp_words(kMax) * 4 > kRadixTempBytes || suffix_sort_lookback_words(kMax) * 8 > kLookbackBytes ||
+        if (radix_temp_words(kMax) * 4 > kRadixTempBytes || suffix_sort_chunk_words(kMax) * 8 > kChunksBytes ||
             suffix_sort_log_slots((uint32_t)kMax) * 4 > kCountLogBytes)
             return SBWT_EDEVICE;
         suffix_sort_init();
@@ -167,8 +166,7 @@ extern "C" int sbwt_bwt_noalloc(const char* alphabet, const uint8_t* reads, cons
     sb.act_suf[0] = u32 + 6 * stride;
     sb.act_suf[1] = u32 + 7 * stride;
     sb.radix_temp = reinterpret_cast<uint32_t*>(b + kRadixTemp);
-    sb.lookback = reinterpret_cast<unsigned long long*>(b + kLookback);
-    sb.counters = reinterpret_cast<uint32_t*>(b + kCounters);
+    sb.chunks = reinterpret_cast<unsigned long long*>(b + kChunks);
     sb.count_log = reinterpret_cast<uint32_t*>(b + kCountLog);
     sb.err = err;
     uint8_t* bint = b + kBint;

@@ -200,110 +200,28 @@ class Launcher {
 inline unsigned int ceil_div_u(uint64_t a, uint64_t b) { return (unsigned int)((a + b - 1) / b); }
 
 // ---------------------------------------------------------------------------
-// Decoupled look-back (single-pass scans across CTAs).  Every tile publishes
-// a 64-bit word per scanned column: [63:34] epoch, [33:32] state (1 = the
-// tile's own aggregate, 2 = inclusive prefix), [31:0] value.  A tile combines
-// its predecessors' words, newest first, until it meets an inclusive prefix.
-// Tiles are taken in order by CTAs that are already running, so every wait
-// ends; waits are still bounded (kLbSpinLimit), after which the tile flags
-// *d_err and goes on.  A fresh epoch per launch makes stale words read as
-// "not ready", so the words never need clearing.
-// ---------------------------------------------------------------------------
-constexpr unsigned long long kLbAggregate = 1ull << 32;
-constexpr unsigned long long kLbPrefix = 2ull << 32;
-constexpr unsigned long long kLbTagMask = ~0x3FFFFFFFFull;
-constexpr uint32_t kLbSpinLimit = 1u << 22;
-constexpr int kLbWindow = 8;
-
-__device__ __forceinline__ void lb_store(unsigned long long* p, unsigned long long v) {
-    *reinterpret_cast<volatile unsigned long long*>(p) = v;
-}
-__device__ __forceinline__ unsigned long long lb_load(const unsigned long long* p) {
-    return *reinterpret_cast<const volatile unsigned long long*>(p);
-}
-__device__ __forceinline__ unsigned long long lb_tag(unsigned long long epoch) { return epoch << 34; }
-
-// Exclusive prefix (under Op) of the words of tiles 0 .. tile-1 in one column
-// (word of tile k at base[k * stride]), reading kLbWindow tiles per step.
-template <class Op>
-__device__ __forceinline__ uint32_t lb_lookback(const unsigned long long* base, size_t stride, uint32_t tile,
-                                                unsigned long long tag, uint32_t* d_err, uint32_t err_bit) {
-    uint32_t acc = Op::template id<uint32_t>();
-    int64_t kt = (int64_t)tile - 1;
-    uint32_t spins = 0;
-    while (kt >= 0) {
-        unsigned long long w[kLbWindow];
-#pragma unroll
-        for (int i = 0; i < kLbWindow; ++i) w[i] = kt - i >= 0 ? lb_load(base + (uint64_t)(kt - i) * stride) : 0ull;
-        int used = 0;
-        bool done = false, stall = false;
-#pragma unroll
-        for (int i = 0; i < kLbWindow; ++i) {
-            if (done || stall || kt - i < 0) continue;
-            const unsigned long long state = (w[i] >> 32) & 3ull;
-            if ((w[i] & kLbTagMask) != tag || state == 0) {
-                stall = true;
-                continue;
-            }
-            acc = Op::f(acc, (uint32_t)w[i]);
-            ++used;
-            done = state == 2;
-        }
-        if (done) break;
-        kt -= used;
-        if (stall) {
-            if (++spins > kLbSpinLimit) {
-                atomicOr(d_err, err_bit);
-                break;
-            }
-            if (spins > 32) __nanosleep(128);
-        }
-    }
-    return acc;
-}
-
-// A fresh look-back epoch (process-wide, never reused).
-unsigned long long lb_next_epoch();
-
 // CTAs per launch for a persistent kernel: SMs x resident CTAs per SM.
 unsigned persistent_ctas(const void* kernel, int threads, size_t smem);
 
 // ---------------------------------------------------------------------------
 // Radix sort (radix.cu).  Every count is read from device memory so a
 // sequence of launches needs no host round trip; `cap` bounds the count.
-// Digit histograms of all passes are built by whoever writes the keys
-// (radix_hist_add into shared memory, radix_hist_flush into
-// radix_histograms(temp) after radix_hist_clear), or by the sort itself.
 // ---------------------------------------------------------------------------
 constexpr int kRadixBits = 8;
 constexpr int kRadixBins = 1 << kRadixBits;
-constexpr int kRadixTile = 4096;  // keys per radix tile (256 threads x 16)
-constexpr int kRadixMaxPasses = 8;
 
-__device__ __forceinline__ void radix_hist_add(uint32_t* h, unsigned long long key, int begin_bit, int passes) {
-    key >>= begin_bit;
-    for (int p = 0; p < passes; ++p) atomicAdd(&h[p * kRadixBins + ((key >> (kRadixBits * p)) & (kRadixBins - 1))], 1u);
-}
-template <int NT>
-__device__ __forceinline__ void radix_hist_flush(const uint32_t* h, uint32_t* ghist, int passes) {
-    for (int i = threadIdx.x; i < passes * kRadixBins; i += NT)
-        if (h[i]) atomicAdd(&ghist[i], h[i]);
-}
 inline int radix_passes(int begin_bit, int end_bit) { return (end_bit - begin_bit + kRadixBits - 1) / kRadixBits; }
 
 size_t radix_temp_words(uint64_t cap);
 void radix_init();  // once per device, before the first sort
-uint32_t* radix_histograms(uint32_t* temp);
-void radix_hist_clear(Launcher& L, uint32_t* temp);
 
 // Stable LSD radix sort of (*d_n) 64-bit keys with 32-bit values on bits
 // [begin_bit, end_bit); key bits at and above end_bit must be zero.  Sorts
 // between (keys, vals) and (keys_alt, vals_alt); returns true when the
-// result ended in the *_alt buffers.  With hist_ready the histograms were
-// accumulated by the key producer.  A scatter index out of range is skipped
-// and flagged in *d_err (bit 4), a look-back that gave up in bit 6.
+// result ended in the *_alt buffers.  A scatter index out of range is skipped
+// and flagged in *d_err (bit 4).
 bool radix_sort_pairs(Launcher& L, unsigned long long* keys, uint32_t* vals, unsigned long long* keys_alt,
                       uint32_t* vals_alt, const uint32_t* d_n, uint64_t cap, int begin_bit, int end_bit,
-                      uint32_t* temp, uint32_t* d_err, bool hist_ready);
+                      uint32_t* temp, uint32_t* d_err);
 
 }  // namespace sbwt

@@ -25,12 +25,10 @@
 //    resolved prefix exceeds the longest read of the block.
 // At the end rank[] is the inverse suffix array of the block.
 //
-// After each sort one single-pass kernel does the bookkeeping: group heads,
-// the running max of head rows (each element's group head), the active
-// flags and their running count (the compaction offsets), with both scans
-// carried across tiles by decoupled look-back; it writes SA, rank and the
-// compacted list of unsorted members.  The key kernels also build the digit
-// histograms of the sort that follows.
+// After each sort the bookkeeping (group heads, the running max of head rows
+// = each element's group head, the unsorted flags and their running count =
+// the compaction offsets) is reduce-then-scan over chunks of tiles; it writes
+// SA, rank and the compacted list of unsorted members.
 #include <algorithm>
 
 #include "sbwt_internal.cuh"
@@ -44,8 +42,7 @@ constexpr uint32_t kH0 = 29;
 constexpr int kGItems = 16;
 constexpr int kGTile = kThreads * kGItems;  // elements per group-kernel tile
 
-// Counter slots (one tile counter per group launch).
-constexpr int kSlotInit = 0;
+constexpr unsigned kMaxGroupChunks = 2048;
 
 __device__ __forceinline__ unsigned long long initial_key(const uint32_t* __restrict__ text,
                                                           const uint32_t* __restrict__ term, uint64_t P) {
@@ -70,20 +67,12 @@ __global__ void __launch_bounds__(kThreads) sa_init_keys_kernel(const uint32_t* 
                                                                 unsigned long long base, uint32_t n,
                                                                 unsigned long long* __restrict__ keys,
                                                                 uint32_t* __restrict__ vals,
-                                                                uint32_t* __restrict__ d_n,
-                                                                uint32_t* __restrict__ ghist, int passes) {
-    __shared__ uint32_t h[kRadixMaxPasses * kRadixBins];
-    for (int i = threadIdx.x; i < passes * kRadixBins; i += kThreads) h[i] = 0;
+                                                                uint32_t* __restrict__ d_n) {
     if (blockIdx.x == 0 && threadIdx.x == 0) *d_n = n;
-    __syncthreads();
     for (uint32_t t = blockIdx.x * kThreads + threadIdx.x; t < n; t += gridDim.x * kThreads) {
-        const unsigned long long key = initial_key(text, term, base + t);
-        keys[t] = key;
+        keys[t] = initial_key(text, term, base + t);
         vals[t] = t;
-        radix_hist_add(h, key, 0, passes);
     }
-    __syncthreads();
-    radix_hist_flush<kThreads>(h, ghist, passes);
 }
 
 __global__ void __launch_bounds__(kThreads) sa_round_keys_kernel(const uint32_t* __restrict__ act_suf,
@@ -92,11 +81,7 @@ __global__ void __launch_bounds__(kThreads) sa_round_keys_kernel(const uint32_t*
                                                                  uint32_t n, int bits,
                                                                  unsigned long long* __restrict__ keys,
                                                                  uint32_t* __restrict__ vals,
-                                                                 uint32_t* __restrict__ ghist, int passes,
                                                                  uint32_t* __restrict__ d_err) {
-    __shared__ uint32_t hs[kRadixMaxPasses * kRadixBins];
-    for (int i = threadIdx.x; i < passes * kRadixBins; i += kThreads) hs[i] = 0;
-    __syncthreads();
     const uint32_t cnt = *d_cnt;
     for (uint32_t k = blockIdx.x * kThreads + threadIdx.x; k < cnt; k += gridDim.x * kThreads) {
         const uint32_t t = act_suf[k];
@@ -109,118 +94,155 @@ __global__ void __launch_bounds__(kThreads) sa_round_keys_kernel(const uint32_t*
         } else {
             atomicOr(d_err, 4u);
         }
-        const unsigned long long key = ((unsigned long long)here << bits) | next;
-        keys[k] = key;
+        keys[k] = ((unsigned long long)here << bits) | next;
         vals[k] = t;
-        radix_hist_add(hs, key, 0, passes);
     }
-    __syncthreads();
-    radix_hist_flush<kThreads>(hs, ghist, passes);
 }
 
-// Group bookkeeping after a sort, one tile of kGTile elements per step.
-// Element i of the sorted list (keys, vals) sits on row pos(i) of the block
-// SA: pos(i) = i after the initial sort, act_pos[i] after a round.  Writes
-// SA[pos] = t, rank[t] = row of t's group head, and appends the members of
-// groups with two or more elements to (act_pos_out, act_suf_out); the
-// number appended goes to *d_cnt_out.
+// Group bookkeeping after a sort.  Element i of the sorted list (keys, vals)
+// sits on row pos(i) of the block SA: pos(i) = i after the initial sort,
+// act_pos[i] after a round.  It writes SA[pos] = t, rank[t] = row of t's
+// group head, and appends the members of groups with two or more elements to
+// (act_pos_out, act_suf_out).  Like the radix passes it is reduce-then-scan
+// over chunks of whole tiles: groups_reduce gives each chunk's last head row
+// and member count, groups_scan turns them into per-chunk prefixes (and the
+// total into *d_cnt_out), groups_apply walks each chunk with running values.
+struct ElemInfo {
+    unsigned long long k[kGItems];
+    uint32_t pos[kGItems];
+    uint32_t heads;  // bit q: element q starts a group
+    uint32_t ends;   // bit q: element q is the last of its group
+};
+
 template <bool kRound>
-__global__ void __launch_bounds__(kThreads) sa_groups_kernel(
-    const unsigned long long* __restrict__ keys, const uint32_t* __restrict__ vals,
-    const uint32_t* __restrict__ act_pos_in, const uint32_t* __restrict__ d_cnt, uint32_t n_block,
-    uint32_t* __restrict__ sa, uint32_t* __restrict__ rank, uint32_t* __restrict__ act_pos_out,
-    uint32_t* __restrict__ act_suf_out, uint32_t* __restrict__ d_cnt_out, unsigned long long* __restrict__ lookback,
-    uint32_t* __restrict__ tile_counter, unsigned long long epoch, uint32_t* __restrict__ d_err) {
-    __shared__ uint32_t s_tile, s_pmax, s_psum;
+__device__ __forceinline__ void load_tile_info(const unsigned long long* __restrict__ keys,
+                                               const uint32_t* __restrict__ act_pos_in, uint32_t n, uint32_t i0,
+                                               ElemInfo& e) {
+#pragma unroll
+    for (int q = 0; q < kGItems; ++q) {
+        const uint32_t i = i0 + q;
+        e.k[q] = i < n ? keys[i] : 0ull;
+        e.pos[q] = kRound ? (i < n ? act_pos_in[i] : 0u) : i;
+    }
+    const unsigned long long kprev = (i0 > 0 && i0 - 1 < n) ? keys[i0 - 1] : 0ull;
+    // is the element after this thread's last one a group head?
+    bool next_head = true;
+    if ((uint64_t)i0 + kGItems < n) {
+        const unsigned long long kn = keys[i0 + kGItems];
+        next_head = kn != e.k[kGItems - 1] || (!kRound && (uint32_t)(kn & 31) < kH0);
+    }
+    // head: a new key, or (initial sort) a key that contains its terminator
+    e.heads = 0;
+#pragma unroll
+    for (int q = 0; q < kGItems; ++q) {
+        const uint32_t i = i0 + q;
+        const unsigned long long prev = q == 0 ? kprev : e.k[q - 1];
+        const bool h = i < n && (i == 0 || e.k[q] != prev || (!kRound && (uint32_t)(e.k[q] & 31) < kH0));
+        e.heads |= (uint32_t)h << q;
+    }
+    e.ends = 0;
+#pragma unroll
+    for (int q = 0; q < kGItems; ++q) {
+        const uint32_t i = i0 + q;
+        const bool hn = q + 1 < kGItems ? (((e.heads >> (q + 1)) & 1u) || i + 1 >= n) : next_head;
+        e.ends |= (uint32_t)hn << q;
+    }
+}
+
+__device__ __forceinline__ void chunk_tiles(uint32_t ntiles, uint32_t& t0, uint32_t& t1) {
+    const uint32_t per = (ntiles + gridDim.x - 1) / gridDim.x;
+    t0 = min(ntiles, blockIdx.x * per);
+    t1 = min(ntiles, t0 + per);
+}
+
+template <bool kRound>
+__global__ void __launch_bounds__(kThreads) sa_groups_reduce_kernel(const unsigned long long* __restrict__ keys,
+                                                                    const uint32_t* __restrict__ act_pos_in,
+                                                                    const uint32_t* __restrict__ d_cnt,
+                                                                    uint32_t n_block, uint2* __restrict__ chunk_agg) {
     const uint32_t n = kRound ? *d_cnt : n_block;
     const uint32_t ntiles = (uint32_t)(((uint64_t)n + kGTile - 1) / kGTile);
-    const unsigned long long tag = lb_tag(epoch);
-    if (ntiles == 0) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) *d_cnt_out = 0;
-        return;
-    }
-    for (;;) {
-        if (threadIdx.x == 0) s_tile = atomicAdd(tile_counter, 1u);
-        __syncthreads();
-        const uint32_t tile = s_tile;
-        if (tile >= ntiles) break;
+    uint32_t t0, t1;
+    chunk_tiles(ntiles, t0, t1);
+    uint32_t tmax = 0, tsum = 0;
+    for (uint32_t tile = t0; tile < t1; ++tile) {
+        ElemInfo e;
         const uint32_t i0 = tile * kGTile + threadIdx.x * kGItems;
+        load_tile_info<kRound>(keys, act_pos_in, n, i0, e);
+#pragma unroll
+        for (int q = 0; q < kGItems; ++q) {
+            if (i0 + q >= n) continue;
+            const bool h = (e.heads >> q) & 1u, en = (e.ends >> q) & 1u;
+            if (h) tmax = max(tmax, e.pos[q]);
+            tsum += (h && en) ? 0u : 1u;
+        }
+    }
+    uint32_t totmax, totsum;
+    cta_exclusive_scan<MaxOp, kThreads>(tmax, totmax);
+    cta_exclusive_scan<SumOp, kThreads>(tsum, totsum);
+    if (threadIdx.x == 0) chunk_agg[blockIdx.x] = make_uint2(totmax, totsum);
+}
 
-        unsigned long long k[kGItems];
-        uint32_t pos[kGItems];
-#pragma unroll
-        for (int q = 0; q < kGItems; ++q) {
-            const uint32_t i = i0 + q;
-            k[q] = i < n ? keys[i] : 0ull;
-            pos[q] = kRound ? (i < n ? act_pos_in[i] : 0u) : i;
-        }
-        const unsigned long long kprev = (i0 > 0 && i0 - 1 < n) ? keys[i0 - 1] : 0ull;
-        // is the element after this thread's last one a group head?
-        bool next_head = true;
-        if ((uint64_t)i0 + kGItems < n) {
-            const unsigned long long kn = keys[i0 + kGItems];
-            next_head = kn != k[kGItems - 1] || (!kRound && (uint32_t)(kn & 31) < kH0);
-        }
-        // head flags: a new key, or (initial sort) a key that contains its terminator
-        uint32_t heads = 0;
-#pragma unroll
-        for (int q = 0; q < kGItems; ++q) {
-            const uint32_t i = i0 + q;
-            const unsigned long long prev = q == 0 ? kprev : k[q - 1];
-            const bool h = i < n && (i == 0 || k[q] != prev || (!kRound && (uint32_t)(k[q] & 31) < kH0));
-            heads |= (uint32_t)h << q;
-        }
+__global__ void __launch_bounds__(kThreads) sa_groups_scan_kernel(uint2* __restrict__ chunk_agg, int nchunks,
+                                                                  uint32_t* __restrict__ d_cnt_out) {
+    uint32_t cmax = 0, csum = 0;
+    for (int base = 0; base < nchunks; base += kThreads) {
+        const int c = base + threadIdx.x;
+        const uint2 v = c < nchunks ? chunk_agg[c] : make_uint2(0u, 0u);
+        uint32_t tmax, tsum;
+        const uint32_t emax = cta_exclusive_scan<MaxOp, kThreads>(v.x, tmax);
+        const uint32_t esum = cta_exclusive_scan<SumOp, kThreads>(v.y, tsum);
+        if (c < nchunks) chunk_agg[c] = make_uint2(max(cmax, emax), csum + esum);
+        cmax = max(cmax, tmax);
+        csum += tsum;
+    }
+    if (threadIdx.x == 0) *d_cnt_out = csum;
+}
+
+template <bool kRound>
+__global__ void __launch_bounds__(kThreads) sa_groups_apply_kernel(
+    const unsigned long long* __restrict__ keys, const uint32_t* __restrict__ vals,
+    const uint32_t* __restrict__ act_pos_in, const uint32_t* __restrict__ d_cnt, uint32_t n_block,
+    const uint2* __restrict__ chunk_prefix, uint32_t* __restrict__ sa, uint32_t* __restrict__ rank,
+    uint32_t* __restrict__ act_pos_out, uint32_t* __restrict__ act_suf_out, uint32_t* __restrict__ d_err) {
+    const uint32_t n = kRound ? *d_cnt : n_block;
+    const uint32_t ntiles = (uint32_t)(((uint64_t)n + kGTile - 1) / kGTile);
+    uint32_t t0, t1;
+    chunk_tiles(ntiles, t0, t1);
+    uint32_t run_max = chunk_prefix[blockIdx.x].x, run_sum = chunk_prefix[blockIdx.x].y;
+    for (uint32_t tile = t0; tile < t1; ++tile) {
+        ElemInfo e;
+        const uint32_t i0 = tile * kGTile + threadIdx.x * kGItems;
+        load_tile_info<kRound>(keys, act_pos_in, n, i0, e);
         uint32_t tmax = 0, tsum = 0;
 #pragma unroll
         for (int q = 0; q < kGItems; ++q) {
-            const uint32_t i = i0 + q;
-            if (i >= n) continue;
-            const bool h = (heads >> q) & 1u;
-            const bool hn = q + 1 < kGItems ? (((heads >> (q + 1)) & 1u) || i + 1 >= n) : next_head;
-            if (h) tmax = pos[q];
-            tsum += (h && hn) ? 0u : 1u;
+            if (i0 + q >= n) continue;
+            const bool h = (e.heads >> q) & 1u, en = (e.ends >> q) & 1u;
+            if (h) tmax = max(tmax, e.pos[q]);
+            tsum += (h && en) ? 0u : 1u;
         }
         uint32_t totmax, totsum;
         const uint32_t exmax = cta_exclusive_scan<MaxOp, kThreads>(tmax, totmax);
         const uint32_t exsum = cta_exclusive_scan<SumOp, kThreads>(tsum, totsum);
-        if (threadIdx.x == 0) {
-            unsigned long long* w = lookback + 2ull * tile;
-            uint32_t pmax = 0, psum = 0;
-            if (tile == 0) {
-                lb_store(w, tag | kLbPrefix | totmax);
-                lb_store(w + 1, tag | kLbPrefix | totsum);
-            } else {
-                lb_store(w, tag | kLbAggregate | totmax);
-                lb_store(w + 1, tag | kLbAggregate | totsum);
-                pmax = lb_lookback<MaxOp>(lookback, 2, tile, tag, d_err, 128u);
-                psum = lb_lookback<SumOp>(lookback + 1, 2, tile, tag, d_err, 128u);
-                lb_store(w, tag | kLbPrefix | (pmax > totmax ? pmax : totmax));
-                lb_store(w + 1, tag | kLbPrefix | (psum + totsum));
-            }
-            s_pmax = pmax;
-            s_psum = psum;
-            if (tile == ntiles - 1) *d_cnt_out = psum + totsum;
-        }
-        __syncthreads();
-        uint32_t cur = s_pmax > exmax ? s_pmax : exmax;
-        uint32_t out = s_psum + exsum;
+        uint32_t cur = max(run_max, exmax);
+        uint32_t out = run_sum + exsum;
 #pragma unroll
         for (int q = 0; q < kGItems; ++q) {
             const uint32_t i = i0 + q;
             if (i >= n) continue;
-            const bool h = (heads >> q) & 1u;
-            const bool hn = q + 1 < kGItems ? (((heads >> (q + 1)) & 1u) || i + 1 >= n) : next_head;
-            if (h) cur = pos[q];
+            const bool h = (e.heads >> q) & 1u, en = (e.ends >> q) & 1u;
+            if (h) cur = e.pos[q];
             const uint32_t t = vals[i];
-            if (t < n_block && pos[q] < n_block) {
-                sa[pos[q]] = t;
+            if (t < n_block && e.pos[q] < n_block) {
+                sa[e.pos[q]] = t;
                 rank[t] = cur;
             } else {
                 atomicOr(d_err, 32u);
             }
-            if (!(h && hn)) {
+            if (!(h && en)) {
                 if (out < n_block) {
-                    act_pos_out[out] = pos[q];
+                    act_pos_out[out] = e.pos[q];
                     act_suf_out[out] = t;
                 } else {
                     atomicOr(d_err, 32u);
@@ -228,14 +250,14 @@ __global__ void __launch_bounds__(kThreads) sa_groups_kernel(
                 ++out;
             }
         }
-        __syncthreads();
+        run_max = max(run_max, totmax);
+        run_sum += totsum;
     }
 }
 
 unsigned g_keys_ctas[64] = {0};
 unsigned g_round_keys_ctas[64] = {0};
 unsigned g_groups_ctas[64] = {0};
-unsigned g_round_groups_ctas[64] = {0};
 
 int current_device() {
     int dev = 0;
@@ -250,8 +272,8 @@ void suffix_sort_init() {
     const int dev = current_device();
     g_keys_ctas[dev] = persistent_ctas((const void*)sa_init_keys_kernel, kThreads, 0);
     g_round_keys_ctas[dev] = persistent_ctas((const void*)sa_round_keys_kernel, kThreads, 0);
-    g_groups_ctas[dev] = persistent_ctas((const void*)sa_groups_kernel<false>, kThreads, 0);
-    g_round_groups_ctas[dev] = persistent_ctas((const void*)sa_groups_kernel<true>, kThreads, 0);
+    g_groups_ctas[dev] = std::min<unsigned>(kMaxGroupChunks,
+                                            persistent_ctas((const void*)sa_groups_apply_kernel<true>, kThreads, 0));
 }
 
 uint32_t suffix_sort_rounds(uint32_t max_len) {
@@ -266,7 +288,34 @@ uint32_t suffix_sort_rounds(uint32_t max_len) {
 
 size_t suffix_sort_log_slots(uint32_t max_len) { return suffix_sort_rounds(max_len) + 2; }
 
-size_t suffix_sort_lookback_words(uint64_t cap) { return 2 * (size_t)(cap / kGTile + 2); }
+size_t suffix_sort_chunk_words(uint64_t cap) {
+    (void)cap;
+    return kMaxGroupChunks;  // one (max, count) pair per chunk, 8 bytes each
+}
+
+namespace {
+
+template <bool kRound>
+void run_groups(Launcher& L, const SuffixSortBuffers& b, const unsigned long long* keys, const uint32_t* vals,
+                const uint32_t* act_pos_in, const uint32_t* d_cnt, uint32_t n_block, uint32_t* act_pos_out,
+                uint32_t* act_suf_out, uint32_t* d_cnt_out, unsigned grid) {
+    uint2* agg = reinterpret_cast<uint2*>(b.chunks);
+    const char* names[3] = {kRound ? "sa_round_groups_reduce" : "sa_groups_reduce", "sa_groups_scan",
+                            kRound ? "sa_round_groups_apply" : "sa_groups_apply"};
+    const double fixed = kRound ? 0.0 : (double)n_block;
+    const double per = kRound ? 1.0 : 0.0;
+    SBWT_LAUNCH(L, names[0], fixed * (kRound ? 0 : 8), per * 12, kRound ? d_cnt : nullptr,
+                sa_groups_reduce_kernel<kRound>, grid, kThreads, 0, keys, act_pos_in, d_cnt, n_block, agg);
+    SBWT_LAUNCH(L, names[1], 16.0 * grid, 0, nullptr, sa_groups_scan_kernel, 1, kThreads, 0, agg, (int)grid,
+                d_cnt_out);
+    // per element: key (+ neighbours), value, position, SA and rank writes,
+    // and the compacted pair of an unsorted member
+    SBWT_LAUNCH(L, names[2], fixed * 28, per * 36, kRound ? d_cnt : nullptr, sa_groups_apply_kernel<kRound>, grid,
+                kThreads, 0, keys, vals, act_pos_in, d_cnt, n_block, agg, b.sa, b.rank, act_pos_out, act_suf_out,
+                b.err);
+}
+
+}  // namespace
 
 void suffix_sort_block(Launcher& L, const uint32_t* text, const uint32_t* term, uint64_t base, uint32_t n,
                        uint32_t max_len, const SuffixSortBuffers& b) {
@@ -277,37 +326,28 @@ void suffix_sort_block(Launcher& L, const uint32_t* text, const uint32_t* term, 
         return (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(std::max(1u, ctas), need));
     };
     const uint32_t rounds = suffix_sort_rounds(max_len);
-    cudaMemsetAsync(b.counters, 0, (rounds + 2) * sizeof(uint32_t), L.stream);
 
     uint32_t* d_n = b.count_log;  // slot 0: n; slot r + 1: unsorted members after round r (r = 0: initial)
-    const int passes0 = radix_passes(0, 63);
-    radix_hist_clear(L, b.radix_temp);
     SBWT_LAUNCH(L, "sa_init_keys", (double)n * 12 + n / 4.0 + n / 8.0, 0, nullptr, sa_init_keys_kernel,
                 grid_of(g_keys_ctas[dev], (uint64_t)n / kThreads + 1), kThreads, 0, text, term,
-                (unsigned long long)base, n, b.keys, b.vals, d_n, radix_histograms(b.radix_temp), passes0);
-    bool alt = radix_sort_pairs(L, b.keys, b.vals, b.keys_alt, b.vals_alt, d_n, n, 0, 63, b.radix_temp, b.err, true);
-    SBWT_LAUNCH(L, "sa_groups", (double)n * (8 + 4 + 4 + 4), 8, b.count_log + 1, sa_groups_kernel<false>,
-                grid_of(g_groups_ctas[dev], gtiles), kThreads, 0, alt ? b.keys_alt : b.keys,
-                alt ? b.vals_alt : b.vals, nullptr, d_n, n, b.sa, b.rank, b.act_pos[0], b.act_suf[0],
-                b.count_log + 1, b.lookback, b.counters + kSlotInit, lb_next_epoch(), b.err);
+                (unsigned long long)base, n, b.keys, b.vals, d_n);
+    bool alt = radix_sort_pairs(L, b.keys, b.vals, b.keys_alt, b.vals_alt, d_n, n, 0, 63, b.radix_temp, b.err);
+    run_groups<false>(L, b, alt ? b.keys_alt : b.keys, alt ? b.vals_alt : b.vals, nullptr, d_n, n, b.act_pos[0],
+                      b.act_suf[0], b.count_log + 1, grid_of(g_groups_ctas[dev], gtiles));
 
     const int bits = n > 1 ? 32 - __builtin_clz(n - 1) : 1;
-    const int passes = radix_passes(0, 2 * bits);
     uint32_t h = kH0;
     int cur = 0;
     for (uint32_t r = 1; r <= rounds; ++r, h *= 2) {
         const uint32_t* cnt = b.count_log + r;
         uint32_t* next_cnt = b.count_log + r + 1;
-        radix_hist_clear(L, b.radix_temp);
         SBWT_LAUNCH(L, "sa_round_keys", 0, 24, cnt, sa_round_keys_kernel,
                     grid_of(g_round_keys_ctas[dev], (uint64_t)n / kThreads + 1), kThreads, 0, b.act_suf[cur], cnt,
-                    b.rank, h, n, bits, b.keys, b.vals, radix_histograms(b.radix_temp), passes, b.err);
+                    b.rank, h, n, bits, b.keys, b.vals, b.err);
         const bool a =
-            radix_sort_pairs(L, b.keys, b.vals, b.keys_alt, b.vals_alt, cnt, n, 0, 2 * bits, b.radix_temp, b.err, true);
-        SBWT_LAUNCH(L, "sa_round_groups", 0, 28, cnt, sa_groups_kernel<true>, grid_of(g_round_groups_ctas[dev], gtiles),
-                    kThreads, 0, a ? b.keys_alt : b.keys, a ? b.vals_alt : b.vals, b.act_pos[cur], cnt, n, b.sa,
-                    b.rank, b.act_pos[cur ^ 1], b.act_suf[cur ^ 1], next_cnt, b.lookback, b.counters + r,
-                    lb_next_epoch(), b.err);
+            radix_sort_pairs(L, b.keys, b.vals, b.keys_alt, b.vals_alt, cnt, n, 0, 2 * bits, b.radix_temp, b.err);
+        run_groups<true>(L, b, a ? b.keys_alt : b.keys, a ? b.vals_alt : b.vals, b.act_pos[cur], cnt, n,
+                         b.act_pos[cur ^ 1], b.act_suf[cur ^ 1], next_cnt, grid_of(g_groups_ctas[dev], gtiles));
         cur ^= 1;
     }
 }

@@ -261,3 +261,37 @@ def test_short_read_workload_full_size():
     # LF inversion recovers every read
     rec, roff = oracle.lf_invert(B, w.m)
     assert np.array_equal(roff, w.offsets) and np.array_equal(rec, w.reads)
+
+
+def check_full_size(w, B, samples=3, seed=17):
+    """Properties that pin B at any size: the symbol multiset, the terminator
+    rows, rows of sampled suffixes counted one by one by the oracle, and LF
+    inversion of the whole B back to every read."""
+    n = oracle.num_suffixes(w.offsets)
+    assert len(B) == n
+    counts = np.bincount(B, minlength=256)
+    expect_counts = np.bincount(w.reads, minlength=256)
+    expect_counts[ord("$")] += w.m
+    assert np.array_equal(counts, expect_counts)
+    lens = np.diff(w.offsets.astype(np.int64))
+    last = np.where(lens > 0, w.reads[np.maximum(w.offsets[1:].astype(np.int64) - 1, 0)], ord("$"))
+    assert np.array_equal(B[: w.m], last.astype(np.uint8))
+    rng = np.random.default_rng(seed)
+    for _ in range(samples):
+        r = int(rng.integers(0, w.m))
+        p = int(rng.integers(0, int(lens[r]) + 1))
+        row = oracle.row_of_suffix(w.reads, w.offsets, r, p)
+        assert B[row] == oracle.bwt_symbol_of_suffix(w.reads, w.offsets, r, p)
+    rec, roff = oracle.lf_invert_sampled(B, w.m)
+    assert np.array_equal(roff, w.offsets) and np.array_equal(rec, w.reads)
+
+
+@pytest.mark.parametrize("name", ["batched", "long"])
+def test_full_size_batched_and_long_reads(name):
+    """2M reads of U[50,250] bp from a 50 Mbp genome, and 20k log-normal long
+    reads (mean 10 kbp) with 10% errors from a 100 Mbp genome; 64-bit
+    indices, blocks of 2^25 suffixes."""
+    w = readgen.batched() if name == "batched" else readgen.long()
+    idx = gpu_bwt(w.reads, w.offsets, M=1 << 25, index_bits=64)
+    assert idx.size() == (oracle.num_suffixes(w.offsets), w.m)
+    check_full_size(w, idx.bwt(), samples=2)

@@ -85,6 +85,22 @@ def test_invariants(seed):
     assert brute.to_set(rec, roff) == reads
 
 
+@pytest.mark.parametrize("seed", range(6))
+def test_sampled_lf_invert_matches_full(seed):
+    rng = np.random.default_rng(700 + seed)
+    reads = random_set(rng, int(rng.integers(1, 120)), 150)
+    data, off = pack(reads)
+    B = oracle.bwt(data, off)
+    a = oracle.lf_invert(B, len(reads))
+    b = oracle.lf_invert_sampled(B, len(reads))
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    assert brute.to_set(*b) == reads
+    bad = B.copy()
+    bad[len(reads)] = ord("$") if bad[len(reads)] != ord("$") else ord("A")
+    with pytest.raises(oracle.OracleError):
+        oracle.lf_invert_sampled(bad, len(reads))
+
+
 def test_lf_invert_rejects_broken_bwt():
     data, off = pack([b"ACGTTGCA", b"GATTACA"])
     B = oracle.bwt(data, off).copy()
