@@ -35,6 +35,7 @@ struct BlockPlan {
 
 constexpr uint64_t kDefaultBlock = 1ull << 24;
 constexpr uint64_t kMaxBlock = 1ull << 31;
+constexpr unsigned kPlanCap = 4096;  // blocks a device-planned append may have
 
 }  // namespace
 
@@ -60,8 +61,11 @@ struct sbwt_index {
     DevBuf out_bytes, q_codes, q_ks, q_out;
 
     uint32_t* h_err = nullptr;      // pinned
-    uint64_t* h_offsets = nullptr;  // pinned staging for device-side offsets
+    uint64_t* h_offsets = nullptr;  // pinned staging for device-side offsets (fallback planning)
     size_t h_offsets_cap = 0;
+    DevBuf plan;                     // device block table + summary
+    PlanBlock* h_plan = nullptr;     // pinned copy of the table
+    PlanSummary* h_summary = nullptr;
 
     Launcher L;
     bool capture = false;
@@ -74,7 +78,7 @@ struct sbwt_index {
                                   &keys_alt,   &vals,     &vals_alt,  &sa,       &rank,     &act_pos0,
                                   &act_pos1,   &act_suf0, &act_suf1,  &radix_temp, &chunks,
                                   &count_log,  &g,        &gsa,       &bint,     &sb_tot,   &out_bytes,
-                                  &q_codes,    &q_ks,     &q_out};
+                                  &q_codes,    &q_ks,     &q_out,     &plan};
         for (auto& d : dict) {
             v.push_back(&d.blocks);
             v.push_back(&d.super);
@@ -130,6 +134,8 @@ int device_init(sbwt_index* idx) {
     idx->L.stream = idx->stream;
     suffix_sort_init();
     if (cudaMallocHost(&idx->h_err, sizeof(uint32_t)) != cudaSuccess) return SBWT_EDEVICE;
+    if (cudaMallocHost(&idx->h_plan, kPlanCap * sizeof(PlanBlock)) != cudaSuccess) return SBWT_EDEVICE;
+    if (cudaMallocHost(&idx->h_summary, sizeof(PlanSummary)) != cudaSuccess) return SBWT_EDEVICE;
     // the committed dictionary starts empty: one zero block, one zero superblock, C = 0
     Dict& d = idx->dict[idx->cur];
     if (grow(d.blocks, sizeof(OccBlock)) || grow(d.super, 32) || grow(d.C, 32)) return SBWT_ENOMEM;
@@ -262,13 +268,17 @@ void run_block(sbwt_index* idx, const BlockPlan& bp, const uint64_t* d_offsets, 
                         (uint32_t*)idx->sb_tot.p);
 }
 
-int append_impl(sbwt_index* idx, const uint8_t* d_reads, const uint64_t* d_offsets, const uint64_t* h_off,
-                uint64_t m_new, bool host_input, const uint8_t* h_reads,
-                std::chrono::steady_clock::time_point t_start) {
+Plan host_plan(const uint64_t* h_off, uint64_t m_new, uint64_t M) {
     Plan p;
     p.nbytes = h_off[m_new];
     p.npos = p.nbytes + m_new;
-    p.blocks = plan_blocks(h_off, m_new, idx->M);
+    p.blocks = plan_blocks(h_off, m_new, M);
+    return p;
+}
+
+int append_impl(sbwt_index* idx, const uint8_t* d_reads, const uint64_t* d_offsets, const uint64_t* h_off,
+                uint64_t m_new, bool host_input, const uint8_t* h_reads, Plan p,
+                std::chrono::steady_clock::time_point t_start) {
     for (const BlockPlan& b : p.blocks) {
         p.cap = std::max(p.cap, b.n_int);
         p.max_len = std::max(p.max_len, b.max_len);
@@ -513,28 +523,48 @@ int sbwt_append(sbwt_index* idx, const uint8_t* reads, const uint64_t* offsets, 
     if (validate_offsets(offsets, m)) return SBWT_EINVAL;
     if (m == 0) return SBWT_OK;
     if (offsets[m] > 0 && !reads) return SBWT_EINVAL;
-    return append_impl(idx, nullptr, nullptr, offsets, m, true, reads, t0);
+    return append_impl(idx, nullptr, nullptr, offsets, m, true, reads, host_plan(offsets, m, idx->M), t0);
 }
 
 int sbwt_append_device(sbwt_index* idx, const uint8_t* d_reads, const uint64_t* d_offsets, uint64_t m) {
     if (!idx || !d_offsets) return SBWT_EINVAL;
     const auto t0 = std::chrono::steady_clock::now();
     if (int rc = device_init(idx)) return rc;
-    if (m + 1 > idx->h_offsets_cap) {
-        if (idx->h_offsets) cudaFreeHost(idx->h_offsets);
-        idx->h_offsets = nullptr;
-        idx->h_offsets_cap = 0;
-        if (cudaMallocHost(&idx->h_offsets, (m + 1) * 8) != cudaSuccess) return SBWT_ENOMEM;
-        idx->h_offsets_cap = m + 1;
-    }
-    if (cudaMemcpyAsync(idx->h_offsets, d_offsets, (m + 1) * 8, cudaMemcpyDeviceToHost, idx->stream) !=
-            cudaSuccess ||
-        cudaStreamSynchronize(idx->stream) != cudaSuccess)
-        return SBWT_EDEVICE;
-    if (validate_offsets(idx->h_offsets, m)) return SBWT_EINVAL;
     if (m == 0) return SBWT_OK;
-    if (idx->h_offsets[m] > 0 && !d_reads) return SBWT_EINVAL;
-    return append_impl(idx, d_reads, d_offsets, idx->h_offsets, m, false, nullptr, t0);
+    // validate and plan on the device; only the block table comes back
+    if (int rc = reserve(idx, {{&idx->plan, kPlanCap * sizeof(PlanBlock) + sizeof(PlanSummary)}})) return rc;
+    PlanBlock* d_table = (PlanBlock*)idx->plan.p;
+    PlanSummary* d_sum = (PlanSummary*)((char*)idx->plan.p + kPlanCap * sizeof(PlanBlock));
+    launch_plan(idx->L, d_offsets, m, idx->M, kMaxBlock, d_table, kPlanCap, d_sum);
+    cudaMemcpyAsync(idx->h_summary, d_sum, sizeof(PlanSummary), cudaMemcpyDeviceToHost, idx->stream);
+    cudaMemcpyAsync(idx->h_plan, d_table, kPlanCap * sizeof(PlanBlock), cudaMemcpyDeviceToHost, idx->stream);
+    if (cudaStreamSynchronize(idx->stream) != cudaSuccess || cudaGetLastError() != cudaSuccess) return SBWT_EDEVICE;
+    const PlanSummary sum = *idx->h_summary;
+    if (sum.bad) return SBWT_EINVAL;
+    Plan p;
+    if (sum.blocks <= kPlanCap) {
+        p.npos = sum.npos;
+        p.nbytes = sum.npos - m;
+        for (unsigned k = 0; k < sum.blocks; ++k) {
+            const PlanBlock& b = idx->h_plan[k];
+            p.blocks.push_back(BlockPlan{b.j0, b.j1, b.n_int, b.base, sum.max_len});
+        }
+    } else {  // more blocks than the table holds: plan on the host
+        if (m + 1 > idx->h_offsets_cap) {
+            if (idx->h_offsets) cudaFreeHost(idx->h_offsets);
+            idx->h_offsets = nullptr;
+            idx->h_offsets_cap = 0;
+            if (cudaMallocHost(&idx->h_offsets, (m + 1) * 8) != cudaSuccess) return SBWT_ENOMEM;
+            idx->h_offsets_cap = m + 1;
+        }
+        if (cudaMemcpyAsync(idx->h_offsets, d_offsets, (m + 1) * 8, cudaMemcpyDeviceToHost, idx->stream) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(idx->stream) != cudaSuccess)
+            return SBWT_EDEVICE;
+        p = host_plan(idx->h_offsets, m, idx->M);
+    }
+    if (p.nbytes > 0 && !d_reads) return SBWT_EINVAL;
+    return append_impl(idx, d_reads, d_offsets, nullptr, m, false, nullptr, p, t0);
 }
 
 int sbwt_get_bwt(sbwt_index* idx, uint8_t* out, uint64_t cap, uint64_t* n_out) {
@@ -615,6 +645,8 @@ void sbwt_destroy(sbwt_index* idx) {
         for (DevBuf* b : idx->all_bufs()) free_buf(*b);
         if (idx->h_err) cudaFreeHost(idx->h_err);
         if (idx->h_offsets) cudaFreeHost(idx->h_offsets);
+        if (idx->h_plan) cudaFreeHost(idx->h_plan);
+        if (idx->h_summary) cudaFreeHost(idx->h_summary);
         if (idx->own_stream) cudaStreamDestroy(idx->stream);
     }
     delete idx;

@@ -28,9 +28,12 @@ constexpr int kMaxChunks = 2048;
 static_assert(kBins == kThreads, "one thread per digit");
 
 constexpr size_t kDownSmem = (size_t)kTile * 8 + (size_t)kTile * 4 + (size_t)kWarps * kBins * 4 + (size_t)kBins * 4 * 3;
+static_assert(kDownSmem <= 48 * 1024 + 8 * 1024, "four CTAs per SM");
 
-// Temp layout (32-bit words): the chunk x digit offsets of the current pass.
-constexpr size_t kChunkOffsets = 0;
+// Temp layout (32-bit words): the digit totals of the current pass, then the
+// chunk x digit offsets.
+constexpr size_t kTotals = 0;
+constexpr size_t kChunkOffsets = kBins;
 
 __device__ __forceinline__ void chunk_range(uint32_t n, uint32_t& t0, uint32_t& t1) {
     const uint32_t ntiles = (uint32_t)(((uint64_t)n + kTile - 1) / kTile);
@@ -39,10 +42,12 @@ __device__ __forceinline__ void chunk_range(uint32_t n, uint32_t& t0, uint32_t& 
     t1 = min(ntiles, t0 + per);
 }
 
-// Digit counts of this CTA's chunk (per-warp sub-histograms in shared memory).
+// Digit counts of this CTA's chunk (per-warp sub-histograms in shared
+// memory), also added to the digit totals of the whole pass.
 __global__ void __launch_bounds__(kThreads) radix_upsweep_kernel(const unsigned long long* __restrict__ keys,
                                                                  const uint32_t* __restrict__ d_n, int shift,
-                                                                 uint32_t* __restrict__ chunk_counts) {
+                                                                 uint32_t* __restrict__ chunk_counts,
+                                                                 uint32_t* __restrict__ totals) {
     __shared__ uint32_t h[kWarps * kBins];
     for (int i = threadIdx.x; i < kWarps * kBins; i += kThreads) h[i] = 0;
     __syncthreads();
@@ -58,22 +63,41 @@ __global__ void __launch_bounds__(kThreads) radix_upsweep_kernel(const unsigned 
 #pragma unroll
     for (int w = 0; w < kWarps; ++w) s += h[w * kBins + threadIdx.x];
     chunk_counts[(uint64_t)blockIdx.x * kBins + threadIdx.x] = s;
+    if (s) atomicAdd(&totals[threadIdx.x], s);
 }
 
 // Output offset of every (chunk, digit): the digit's start in the sorted
-// output plus the same digit's count in all earlier chunks.
-__global__ void __launch_bounds__(kThreads) radix_chunk_scan_kernel(uint32_t* __restrict__ chunk_counts,
-                                                                    int nchunks) {
-    const int d = threadIdx.x;
-    uint32_t run = 0;
-    for (int c = 0; c < nchunks; ++c) {
+// output (exclusive scan of the totals) plus the same digit's count in all
+// earlier chunks.  CTA x handles digits [32x, 32x + 32); its 1024 threads
+// are 32 digits x 32 groups of consecutive chunks.
+constexpr int kScanThreads = 1024;
+constexpr int kScanGroups = kScanThreads / 32;
+
+__global__ void __launch_bounds__(kScanThreads) radix_chunk_scan_kernel(uint32_t* __restrict__ chunk_counts,
+                                                                        int nchunks,
+                                                                        const uint32_t* __restrict__ totals) {
+    __shared__ uint32_t start[kBins];
+    __shared__ uint32_t part[kScanGroups][33];
+    const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
+    const int d = blockIdx.x * 32 + lane;
+    uint32_t tot;
+    const uint32_t ex = cta_exclusive_scan<SumOp, kScanThreads>(threadIdx.x < kBins ? totals[threadIdx.x] : 0u, tot);
+    if (threadIdx.x < kBins) start[threadIdx.x] = ex;
+    const int per = (nchunks + kScanGroups - 1) / kScanGroups;
+    const int c0 = min(nchunks, g * per), c1 = min(nchunks, c0 + per);
+    uint32_t sum = 0;
+#pragma unroll 8
+    for (int c = c0; c < c1; ++c) sum += chunk_counts[(uint64_t)c * kBins + d];
+    part[g][lane] = sum;
+    __syncthreads();
+    uint32_t run = start[d];
+    for (int q = 0; q < g; ++q) run += part[q][lane];
+#pragma unroll 8
+    for (int c = c0; c < c1; ++c) {
         const uint32_t v = chunk_counts[(uint64_t)c * kBins + d];
         chunk_counts[(uint64_t)c * kBins + d] = run;
         run += v;
     }
-    uint32_t tot;
-    const uint32_t start = cta_exclusive_scan<SumOp, kThreads>(run, tot);
-    for (int c = 0; c < nchunks; ++c) chunk_counts[(uint64_t)c * kBins + d] += start;
 }
 
 __global__ void __launch_bounds__(kThreads, 4) radix_downsweep_kernel(
@@ -86,6 +110,7 @@ __global__ void __launch_bounds__(kThreads, 4) radix_downsweep_kernel(
     uint32_t* wcnt = svals + kTile;             // [kWarps][kBins]
     uint32_t* dstart = wcnt + kWarps * kBins;   // tile-local start of each digit
     uint32_t* gnext = dstart + kBins;           // running output offset of each digit
+    uint32_t* shift_out = gnext + kBins;        // gnext - dstart: tile slot -> output index
 
     const uint32_t n = *d_n;
     uint32_t t0, t1;
@@ -142,7 +167,9 @@ __global__ void __launch_bounds__(kThreads, 4) radix_downsweep_kernel(
             cnt_d += t;
         }
         uint32_t tile_total;
-        dstart[d] = cta_exclusive_scan<SumOp, kThreads>(cnt_d, tile_total);
+        const uint32_t ds = cta_exclusive_scan<SumOp, kThreads>(cnt_d, tile_total);
+        dstart[d] = ds;
+        shift_out[d] = gnext[d] - ds;
         __syncthreads();
 
 #pragma unroll
@@ -162,7 +189,7 @@ __global__ void __launch_bounds__(kThreads, 4) radix_downsweep_kernel(
         for (uint32_t s = threadIdx.x; s < cnt; s += kThreads) {
             const unsigned long long key = skeys[s];
             const uint32_t dd = (uint32_t)(key >> shift) & (kBins - 1);
-            const uint64_t o = (uint64_t)gnext[dd] + (s - dstart[dd]);
+            const uint32_t o = shift_out[dd] + s;
             if (o < n) {
                 kout[o] = key;
                 vout[o] = svals[s];
@@ -195,8 +222,8 @@ unsigned persistent_ctas(const void* kernel, int threads, size_t smem) {
 }
 
 size_t radix_temp_words(uint64_t cap) {
-    (void)cap;
-    return kChunkOffsets + (size_t)kMaxChunks * kBins + 64;
+    const uint64_t chunks = std::min<uint64_t>(kMaxChunks, cap / kTile + 1);
+    return kChunkOffsets + (size_t)chunks * kBins + 64;
 }
 
 void radix_init() {
@@ -212,6 +239,7 @@ bool radix_sort_pairs(Launcher& L, unsigned long long* keys, uint32_t* vals, uns
     const int passes = radix_passes(begin_bit, end_bit);
     if (passes <= 0) return false;
     uint32_t* chunk = temp + kChunkOffsets;
+    uint32_t* totals = temp + kTotals;
     const int dev = current_device();
     const uint64_t tiles = cap / kTile + 1;
     const unsigned grid = (unsigned)std::min<uint64_t>(std::max(1u, g_down_ctas[dev]), tiles);
@@ -222,9 +250,11 @@ bool radix_sort_pairs(Launcher& L, unsigned long long* keys, uint32_t* vals, uns
         unsigned long long* ko = alt ? keys : keys_alt;
         uint32_t* vo = alt ? vals : vals_alt;
         const int shift = begin_bit + kRadixBits * p;
-        SBWT_LAUNCH(L, "radix_upsweep", 0, 8, d_n, radix_upsweep_kernel, grid, kThreads, 0, kin, d_n, shift, chunk);
-        SBWT_LAUNCH(L, "radix_chunk_scan", 8.0 * grid * kBins, 0, nullptr, radix_chunk_scan_kernel, 1, kThreads, 0,
-                    chunk, (int)grid);
+        cudaMemsetAsync(totals, 0, kBins * 4, L.stream);
+        SBWT_LAUNCH(L, "radix_upsweep", 0, 8, d_n, radix_upsweep_kernel, grid, kThreads, 0, kin, d_n, shift, chunk,
+                    totals);
+        SBWT_LAUNCH(L, "radix_chunk_scan", 12.0 * grid * kBins, 0, nullptr, radix_chunk_scan_kernel, kBins / 32,
+                    kScanThreads, 0, chunk, (int)grid, totals);
         SBWT_LAUNCH(L, "radix_downsweep", 0, 24, d_n, radix_downsweep_kernel, grid, kThreads, kDownSmem, kin, vin, ko,
                     vo, d_n, shift, chunk, d_err);
         alt = !alt;

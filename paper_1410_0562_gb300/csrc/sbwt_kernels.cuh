@@ -64,6 +64,25 @@ void launch_insert(Launcher& L, const OccBlock* old_blocks, uint64_t n_ext, cons
                    uint64_t n_int, OccBlock* new_blocks, unsigned long long* new_super, unsigned long long* new_C,
                    uint64_t m_new, uint32_t* sb_tot);
 
+// plan.cu: checks device-resident offsets (offsets[0] = 0, non-decreasing,
+// every read shorter than max_block suffixes; summary->bad != 0 otherwise),
+// finds the longest read and writes the greedy block partition (Algorithm 1:
+// whole reads, at most M suffixes per block unless one read is longer) into
+// table[0 .. min(blocks, cap)); summary->blocks is the number of blocks.
+struct PlanBlock {
+    unsigned long long j0, j1;  // reads [j0, j1)
+    unsigned long long base;    // text position of the block's first suffix
+    unsigned long long n_int;   // suffixes in the block
+};
+struct PlanSummary {
+    unsigned int bad;
+    unsigned int blocks;
+    unsigned long long max_len;
+    unsigned long long npos;  // suffixes in the whole append
+};
+void launch_plan(Launcher& L, const uint64_t* d_offsets, uint64_t m, uint64_t M, uint64_t max_block,
+                 PlanBlock* table, unsigned cap, PlanSummary* summary);
+
 // Sizes of a dictionary of n rows.
 inline uint64_t dict_blocks(uint64_t n) { return (n >> kOccShift) + 1; }
 inline uint64_t dict_supers(uint64_t n) { return (dict_blocks(n) + kBlocksPerSuper - 1) / kBlocksPerSuper; }
