@@ -27,8 +27,11 @@ constexpr int kBins = kRadixBins;
 constexpr int kMaxChunks = 2048;
 static_assert(kBins == kThreads, "one thread per digit");
 
-constexpr size_t kDownSmem = (size_t)kTile * 8 + (size_t)kTile * 4 + (size_t)kWarps * kBins * 4 + (size_t)kBins * 4 * 3;
-static_assert(kDownSmem <= 48 * 1024 + 8 * 1024, "four CTAs per SM");
+// shared memory of the downsweep: TMA input tile, staged output tile, warp
+// counters, three digit tables, the mbarrier
+constexpr size_t kDownSmem =
+    2 * ((size_t)kTile * 8 + (size_t)kTile * 4) + (size_t)kWarps * kBins * 4 + (size_t)kBins * 4 * 3 + 16;
+static_assert(3 * (kDownSmem + 1024) <= 228 * 1024, "three CTAs per SM");
 
 // Temp layout (32-bit words): the digit totals of the current pass, then the
 // chunk x digit offsets.
@@ -100,17 +103,20 @@ __global__ void __launch_bounds__(kScanThreads) radix_chunk_scan_kernel(uint32_t
     }
 }
 
-__global__ void __launch_bounds__(kThreads, 4) radix_downsweep_kernel(
+__global__ void __launch_bounds__(kThreads, 3) radix_downsweep_kernel(
     const unsigned long long* __restrict__ kin, const uint32_t* __restrict__ vin, unsigned long long* __restrict__ kout,
     uint32_t* __restrict__ vout, const uint32_t* __restrict__ d_n, int shift,
     const uint32_t* __restrict__ chunk_offsets, uint32_t* __restrict__ d_err) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    unsigned long long* skeys = reinterpret_cast<unsigned long long*>(smem);
+    extern __shared__ __align__(128) unsigned char smem[];
+    unsigned long long* in_keys = reinterpret_cast<unsigned long long*>(smem);  // next tile, filled by TMA
+    uint32_t* in_vals = reinterpret_cast<uint32_t*>(in_keys + kTile);
+    unsigned long long* skeys = reinterpret_cast<unsigned long long*>(in_vals + kTile);  // tile in digit order
     uint32_t* svals = reinterpret_cast<uint32_t*>(skeys + kTile);
-    uint32_t* wcnt = svals + kTile;             // [kWarps][kBins]
-    uint32_t* dstart = wcnt + kWarps * kBins;   // tile-local start of each digit
-    uint32_t* gnext = dstart + kBins;           // running output offset of each digit
-    uint32_t* shift_out = gnext + kBins;        // gnext - dstart: tile slot -> output index
+    uint32_t* wcnt = svals + kTile;            // [kWarps][kBins]
+    uint32_t* dstart = wcnt + kWarps * kBins;  // tile-local start of each digit
+    uint32_t* gnext = dstart + kBins;          // running output offset of each digit
+    uint32_t* shift_out = gnext + kBins;       // gnext - dstart: tile slot -> output index
+    unsigned long long* bar = reinterpret_cast<unsigned long long*>(shift_out + kBins);
 
     const uint32_t n = *d_n;
     uint32_t t0, t1;
@@ -119,21 +125,55 @@ __global__ void __launch_bounds__(kThreads, 4) radix_downsweep_kernel(
     const uint32_t lt = (1u << lane) - 1u;
     const int d = threadIdx.x;
     gnext[d] = chunk_offsets[(uint64_t)blockIdx.x * kBins + d];
+    if (threadIdx.x == 0) mbar_init(bar, 1);
+    __syncthreads();
+
+    // whole tiles arrive by TMA one tile ahead; a partial tile (only the very
+    // last one) is read with plain loads
+    auto full = [&](uint32_t tile) { return (uint64_t)(tile + 1) * kTile <= n; };
+    auto prefetch = [&](uint32_t tile) {
+        mbar_expect_tx(bar, kTile * 12u);
+        tma_bulk_load(in_keys, kin + (uint64_t)tile * kTile, kTile * 8u, bar);
+        tma_bulk_load(in_vals, vin + (uint64_t)tile * kTile, kTile * 4u, bar);
+    };
+    uint32_t parity = 0;
+    if (threadIdx.x == 0 && t0 < t1 && full(t0)) prefetch(t0);
 
     for (uint32_t tile = t0; tile < t1; ++tile) {
-        for (int i = threadIdx.x; i < kWarps * kBins; i += kThreads) wcnt[i] = 0;
         const uint64_t base = (uint64_t)tile * kTile;
         const uint32_t cnt = (uint32_t)min((uint64_t)kTile, (uint64_t)n - base);
+        const bool whole = full(tile);
+        bool ok = true;
+        if (whole) {
+            ok = mbar_wait(bar, parity, kMbarSpinLimit);
+            parity ^= 1u;
+        } else {
+            for (uint32_t i = threadIdx.x; i < cnt; i += kThreads) {
+                in_keys[i] = kin[base + i];
+                in_vals[i] = vin[base + i];
+            }
+        }
+        for (int i = threadIdx.x; i < kWarps * kBins; i += kThreads) wcnt[i] = 0;
+        if (!__syncthreads_and(ok)) {
+            // gave up on the copy: flag it, give the copy one more bounded
+            // chance to land (it writes this CTA's shared memory), and stop
+            if (threadIdx.x == 0) atomicOr(d_err, 256u);
+            mbar_wait(bar, parity ^ 1u, kMbarSpinLimit);
+            return;
+        }
         unsigned long long k[kItems];
         uint32_t v[kItems];
 #pragma unroll
         for (int it = 0; it < kItems; ++it) {
             const uint32_t i = warp * kWarpItems + it * 32 + lane;
-            const bool valid = i < cnt;
-            k[it] = valid ? kin[base + i] : 0ull;
-            v[it] = valid ? vin[base + i] : 0u;
+            k[it] = i < cnt ? in_keys[i] : 0ull;
+            v[it] = i < cnt ? in_vals[i] : 0u;
         }
-        __syncthreads();
+        __syncthreads();  // the input buffer is free: fetch the next tile
+        if (threadIdx.x == 0 && tile + 1 < t1 && full(tile + 1)) {
+            fence_proxy_async_smem();
+            prefetch(tile + 1);
+        }
 
         // rank among equal digits of the warp, in index order
         uint32_t* my = wcnt + warp * kBins;
