@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--workload", default="short", choices=["short", "tiny"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-form measurement")
     ap.add_argument("--profile-steps", type=int, default=None,
                     help="steps run under per-kernel event timing (default: the timed steps)")
     return ap.parse_args()
@@ -79,22 +80,27 @@ def load_peaks():
     return 6800.0, "fallback"
 
 
-def load_traffic(kernel: str):
-    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, if it
-    was taken on the current kernel sources; else None."""
+def load_traffic(kernel: str, units: float):
+    """DRAM bytes of `units` units of `kernel`, scaled from the committed ncu
+    capture (profiles/ncu_traffic.json), if that capture was taken on the
+    kernel's current source files; else None."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(path):
         return None
     try:
+        import hashlib
         with open(path) as f:
             t = json.load(f)
-        from paper_1410_0562_gb300 import _build
-        if t.get("sources_sha") != _build.sources_sha():
+        if t.get("kernel") != kernel:
             return None
-        k = t["kernels"].get(kernel)
-        if not k:
+        h = hashlib.sha256()
+        for name in t["source_files"]:
+            h.update(name.encode())
+            with open(os.path.join(ROOT, "paper_1410_0562_gb300", "csrc", name), "rb") as fh:
+                h.update(fh.read())
+        if h.hexdigest()[:16] != t["source_sha"]:
             return None
-        return k
+        return units * float(t["dram_bytes_per_unit"])
     except Exception:
         return None
 
@@ -308,6 +314,46 @@ def run_gb300(args):
                "h2d_bytes_per_step": int(w.reads.nbytes + w.offsets.nbytes),
                "d2h_bytes_per_step": int(bases + w.m)}
 
+    # the batched form on the same reads: block size from the autotuner and
+    # the whole append replayed from a captured CUDA graph
+    batched = None
+    if not args.no_batched:
+        idx_b = sb.SetBWT(b"ACGT", index_bits=w.index_bits, stream=stream.cuda_stream, device=local)
+        best_M, tune = sb.sbwt_autotune_block_suffixes(idx_b.handle, d_reads.data_ptr(), d_off.data_ptr(), w.m,
+                                                       [1 << 22, 1 << 23, 1 << 24, 1 << 25, 1 << 26, 1 << 27])
+        sb.sbwt_set_graph_replay(idx_b.handle, True)
+
+        def step_b():
+            idx_b.reset()
+            idx_b.append_device(d_reads.data_ptr(), d_off.data_ptr(), w.m)
+
+        for _ in range(max(3, args.warmup)):  # eager, eager, capture: replays from here on
+            step_b()
+        sb.sbwt_set_profiling(idx_b.handle, True)
+        b_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                for _ in range(args.steps)]
+        torch.cuda.synchronize()
+        for k in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(k & 0xFF)
+                b_ev[k][0].record(stream)
+            step_b()
+            b_ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        b_ms = float(sum(a.elapsed_time(b) for a, b in b_ev))
+        if dist:
+            t = torch.tensor([b_ms], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            b_ms = float(t.item())
+        b_stats = [s for s in sb.sbwt_get_kernel_stats(idx_b.handle) if not s["name"].startswith("host:")]
+        Bb = idx_b.bwt()
+        assert np.array_equal(Bb, B), "batched form differs from the plain pipeline"
+        batched = {"value": bases * world * args.steps / (b_ms / 1e3) / 1e6, "unit": UNIT,
+                   "ms_per_step": b_ms / args.steps, "block_suffixes": int(best_M), "graph_replay": True,
+                   "autotune_ms": {str(k): round(v, 3) for k, v in tune.items()},
+                   "gpu_launches": int(sum(s["launches"] for s in b_stats))}
+        idx_b.close()
+
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -319,10 +365,11 @@ def run_gb300(args):
     dom = by_ms[0] if by_ms and by_ms[0]["ms"] > 0 else dom
     peak, peak_kind = load_peaks()
     achieved = dom["bytes"] / (dom["ms"] / 1e3) / 1e9 if dom["ms"] > 0 else 0.0
-    traffic = load_traffic(dom["name"])
+    per_launch = dom["bytes"] / max(dom["launches"], 1)
+    traffic = load_traffic(dom["name"], per_launch / 24.0) if dom["name"] == "radix_downsweep" else None
     roofline = {"bound": "hbm", "kernel": dom["name"], "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": peak_kind,
-                "traffic": traffic["dram_bytes_per_launch"] if traffic else None,
+                "traffic": traffic,
                 "algorithmic_bytes_per_launch": dom["bytes"] / max(dom["launches"], 1),
                 "avg_launch_us": 1e3 * dom["ms"] / max(dom["launches"], 1)}
     kernels = {s["name"]: {"launches": s["launches"] // args.steps, "ms_per_step": s["ms"] / args.steps,
@@ -340,6 +387,7 @@ def run_gb300(args):
         "roofline": roofline,
         "e2e": e2e,
         "gpu_launches": launches,
+        "batched": batched,
         "kernels": kernels,
         "host_ms_per_step": host_phases,
     }

@@ -141,6 +141,28 @@ int sbwt_get_stream(sbwt_index *idx, void **stream);
 int sbwt_set_capture(sbwt_index *idx, int on);
 int sbwt_get_stage(sbwt_index *idx, int stage, void *out, uint64_t cap, uint64_t *count_out);
 
+/* ---- batched form: CUDA-graph replay --------------------------------------
+ * With replay on, an append whose plan, sizes, index state (rows, reads, the
+ * buffer holding the current dictionary) and buffers repeat an earlier
+ * append's is captured into a CUDA graph the second time it is seen and
+ * replayed from then on, so the whole block pipeline of Algorithm 1 costs
+ * one launch.  Results are identical with replay on or off.  Up to 8 graphs
+ * are kept; they are dropped when a buffer grows and by sbwt_destroy.  Off
+ * by default. */
+int sbwt_set_graph_replay(sbwt_index *idx, int on);
+
+/* Autotunes M (suffixes per block, Algorithm 1) for reads like the given
+ * ones: builds their BWT with each candidate M (three times; the fastest of
+ * the last two counts), keeps the fastest M in the index and reports it in
+ * *best_out; ms_out, if not NULL, gets each candidate's time in ms (-1 when
+ * it did not fit the HBM budget).  d_reads/d_offsets are device arrays as in
+ * sbwt_append_device.  candidates NULL = {2^22 .. 2^27}.  The index is
+ * emptied (sbwt_reset) before returning.  Errors: SBWT_EINVAL (bad
+ * arguments, a candidate 0 or above 2^31), SBWT_ENOMEM (no candidate fits),
+ * or the error of a failing append. */
+int sbwt_autotune_block_suffixes(sbwt_index *idx, const uint8_t *d_reads, const uint64_t *d_offsets, uint64_t m,
+                                 const uint64_t *candidates, int ncand, uint64_t *best_out, double *ms_out);
+
 /* ---- per-kernel timing ---------------------------------------------------
  * With profiling on, every kernel launch is bracketed by CUDA events on the
  * index's stream.  sbwt_get_kernel_stats fills up to `cap` records (one per

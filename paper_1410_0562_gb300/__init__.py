@@ -39,7 +39,7 @@ EXPORTS = (
     "sbwt_create", "sbwt_create_ex", "sbwt_append", "sbwt_append_device", "sbwt_get_bwt", "sbwt_rank",
     "sbwt_rank_batch", "sbwt_size", "sbwt_reset", "sbwt_destroy", "sbwt_strerror", "sbwt_get_stream",
     "sbwt_set_capture", "sbwt_get_stage", "sbwt_set_profiling", "sbwt_get_kernel_stats",
-    "sbwt_reset_kernel_stats", "sbwt_bwt_noalloc",
+    "sbwt_reset_kernel_stats", "sbwt_set_graph_replay", "sbwt_autotune_block_suffixes", "sbwt_bwt_noalloc",
 )
 
 #: most suffixes (reads + one terminator each) sbwt_bwt_noalloc accepts
@@ -101,6 +101,8 @@ def load() -> ctypes.CDLL:
             "sbwt_set_profiling": ([P, I], I),
             "sbwt_get_kernel_stats": ([P, ctypes.POINTER(sbwt_kernel_stat), I, ctypes.POINTER(I)], I),
             "sbwt_reset_kernel_stats": ([P], I),
+            "sbwt_set_graph_replay": ([P, I], I),
+            "sbwt_autotune_block_suffixes": ([P, P, P, U64, P, I, ctypes.POINTER(U64), P], I),
             "sbwt_bwt_noalloc": ([ctypes.c_char_p, P, P, U64, P, U64, ctypes.POINTER(U64), P], I),
         }
         for name, (args, res) in sig.items():
@@ -235,6 +237,22 @@ def sbwt_get_kernel_stats(h) -> list:
 
 def sbwt_reset_kernel_stats(h):
     _check(load().sbwt_reset_kernel_stats(h), "sbwt_reset_kernel_stats")
+
+
+def sbwt_set_graph_replay(h, on: bool):
+    _check(load().sbwt_set_graph_replay(h, int(on)), "sbwt_set_graph_replay")
+
+
+def sbwt_autotune_block_suffixes(h, d_reads: int, d_offsets: int, m: int, candidates=None):
+    """Returns (best M, {M: ms}) after timing each candidate block size."""
+    cands = np.ascontiguousarray(candidates if candidates is not None else
+                                 [1 << 22, 1 << 23, 1 << 24, 1 << 25, 1 << 26, 1 << 27], dtype=np.uint64)
+    ms = np.zeros(len(cands), dtype=np.float64)
+    best = ctypes.c_uint64()
+    _check(load().sbwt_autotune_block_suffixes(h, ctypes.c_void_p(d_reads), ctypes.c_void_p(d_offsets), m,
+                                               ctypes.c_void_p(cands.ctypes.data), len(cands), ctypes.byref(best),
+                                               ctypes.c_void_p(ms.ctypes.data)), "sbwt_autotune_block_suffixes")
+    return best.value, {int(c): float(t) for c, t in zip(cands, ms)}
 
 
 def sbwt_bwt_noalloc(alphabet: bytes, reads, offsets, stream: int = 0) -> np.ndarray:

@@ -68,6 +68,15 @@ struct sbwt_index {
     PlanSummary* h_summary = nullptr;
 
     Launcher L;
+    // CUDA graphs of whole appends, keyed by everything a launch depends on
+    struct GraphEntry {
+        std::vector<unsigned long long> sig;
+        cudaGraphExec_t exec = nullptr;
+        Launcher::GraphLog log;
+    };
+    bool graph_replay = false;
+    std::vector<GraphEntry> graphs;                    // most recent last
+    std::vector<std::vector<unsigned long long>> seen;  // signatures run once, eagerly
     bool capture = false;
     bool last_valid = false;
     uint64_t last_n = 0;
@@ -220,6 +229,13 @@ std::vector<Need> buffer_needs(sbwt_index* idx, const Plan& p, bool host_input, 
     return v;
 }
 
+void drop_graphs(sbwt_index* idx) {
+    for (auto& g : idx->graphs)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+    idx->graphs.clear();
+    idx->seen.clear();
+}
+
 // Budget check first (nothing changes on failure), then growth.
 int reserve(sbwt_index* idx, const std::vector<Need>& needs) {
     size_t total = idx->held_bytes();
@@ -228,8 +244,10 @@ int reserve(sbwt_index* idx, const std::vector<Need>& needs) {
         if (want > n.buf->bytes) total += want - n.buf->bytes;
     }
     if (idx->budget && total > idx->budget) return SBWT_ENOMEM;
-    for (const Need& n : needs)
+    for (const Need& n : needs) {
+        if (n.buf->bytes < ((n.bytes + 255) & ~(size_t)255) && !idx->graphs.empty()) drop_graphs(idx);
         if (int rc = grow(*n.buf, n.bytes)) return rc;
+    }
     return SBWT_OK;
 }
 
@@ -305,46 +323,104 @@ int append_impl(sbwt_index* idx, const uint8_t* d_reads, const uint64_t* d_offse
         d_reads = (const uint8_t*)idx->reads.p;
         d_offsets = (const uint64_t*)idx->offsets.p;
     }
-    // pack + validate before anything of the index changes
-    const uint64_t text_words = (p.npos + 31) / 32 * 2, term_words = (p.npos + 31) / 32;
-    cudaMemsetAsync((uint32_t*)idx->text.p + text_words, 0, kTextPadWords * 4, s);
-    cudaMemsetAsync((uint32_t*)idx->term.p + term_words, 0, kTermPadWords * 4, s);
-    cudaMemsetAsync(idx->err.p, 0, 4, s);
-    // A byte outside the alphabet sets bit 0 of the error word; the blocks
-    // still run (into scratch dictionaries) and the check at the end refuses
-    // the result, which saves a round trip on every valid append.
-    launch_pack(L, d_reads, d_offsets, m_new, p.npos, idx->alpha4, idx->sigma, (uint32_t*)idx->text.p,
-                (uint32_t*)idx->term.p, (uint32_t*)idx->err.p);
-
+    // where each block reads and writes its dictionary, and the final state
     int other[2], o = 0;
     for (int k = 0; k < 3; ++k)
         if (k != idx->cur) other[o++] = k;
-    int src = idx->cur;
-    uint64_t n_ext = idx->n, m_ext = idx->m;
+    int final_cur = idx->cur;
+    uint64_t final_n = idx->n, final_m = idx->m;
     for (size_t k = 0; k < p.blocks.size(); ++k) {
-        const BlockPlan& bp = p.blocks[k];
-        const int dst = other[k & 1];
-        if (p.idx64)
-            run_block<unsigned long long>(idx, bp, d_offsets, idx->dict[src], idx->dict[dst], n_ext, m_ext, p.slots,
-                                          k);
-        else
-            run_block<uint32_t>(idx, bp, d_offsets, idx->dict[src], idx->dict[dst], n_ext, m_ext, p.slots, k);
-        n_ext += bp.n_int;
-        m_ext += bp.j1 - bp.j0;
-        src = dst;
+        final_cur = other[k & 1];
+        final_n += p.blocks[k].n_int;
+        final_m += p.blocks[k].j1 - p.blocks[k].j0;
     }
-    cudaMemcpyAsync(idx->h_err, idx->err.p, 4, cudaMemcpyDeviceToHost, s);
+
+    // Everything the device does for this append, after the input copies.
+    auto enqueue = [&]() {
+        const uint64_t text_words = (p.npos + 31) / 32 * 2, term_words = (p.npos + 31) / 32;
+        cudaMemsetAsync((uint32_t*)idx->text.p + text_words, 0, kTextPadWords * 4, s);
+        cudaMemsetAsync((uint32_t*)idx->term.p + term_words, 0, kTermPadWords * 4, s);
+        cudaMemsetAsync(idx->err.p, 0, 4, s);
+        // A byte outside the alphabet sets bit 0 of the error word; the blocks
+        // still run (into scratch dictionaries) and the check at the end
+        // refuses the result, which saves a round trip on every valid append.
+        launch_pack(L, d_reads, d_offsets, m_new, p.npos, idx->alpha4, idx->sigma, (uint32_t*)idx->text.p,
+                    (uint32_t*)idx->term.p, (uint32_t*)idx->err.p);
+        int src = idx->cur;
+        uint64_t n_ext = idx->n, m_ext = idx->m;
+        for (size_t k = 0; k < p.blocks.size(); ++k) {
+            const BlockPlan& bp = p.blocks[k];
+            const int dst = other[k & 1];
+            if (p.idx64)
+                run_block<unsigned long long>(idx, bp, d_offsets, idx->dict[src], idx->dict[dst], n_ext, m_ext,
+                                              p.slots, k);
+            else
+                run_block<uint32_t>(idx, bp, d_offsets, idx->dict[src], idx->dict[dst], n_ext, m_ext, p.slots, k);
+            n_ext += bp.n_int;
+            m_ext += bp.j1 - bp.j0;
+            src = dst;
+        }
+        cudaMemcpyAsync(idx->h_err, idx->err.p, 4, cudaMemcpyDeviceToHost, s);
+    };
+
+    const Launcher::GraphLog* replayed = nullptr;
+    if (idx->graph_replay) {
+        // replay a captured graph of an identical append (same plan, sizes,
+        // index state and buffers); capture one on the second sighting
+        std::vector<unsigned long long> sig = {m_new, p.npos, p.nbytes, idx->n, idx->m, (unsigned long long)idx->cur,
+                                               p.idx64, L.profiling, (unsigned long long)(uintptr_t)d_reads,
+                                               (unsigned long long)(uintptr_t)d_offsets, p.blocks.size()};
+        for (const BlockPlan& b : p.blocks) sig.insert(sig.end(), {b.j0, b.j1, b.n_int, b.base, b.max_len});
+        for (DevBuf* b : idx->all_bufs()) sig.push_back((unsigned long long)(uintptr_t)b->p);
+        auto it = std::find_if(idx->graphs.begin(), idx->graphs.end(),
+                               [&](const sbwt_index::GraphEntry& g) { return g.sig == sig; });
+        if (it == idx->graphs.end() && std::find(idx->seen.begin(), idx->seen.end(), sig) != idx->seen.end()) {
+            sbwt_index::GraphEntry g;
+            g.sig = sig;
+            cudaGraph_t graph = nullptr;
+            L.capture = &g.log;
+            cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                enqueue();
+                e = cudaStreamEndCapture(s, &graph);
+            }
+            L.capture = nullptr;
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&g.exec, graph, 0);
+            if (graph) cudaGraphDestroy(graph);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                return SBWT_EDEVICE;
+            }
+            if (idx->graphs.size() >= 8) {
+                cudaGraphExecDestroy(idx->graphs.front().exec);
+                idx->graphs.erase(idx->graphs.begin());
+            }
+            idx->graphs.push_back(std::move(g));
+            it = idx->graphs.end() - 1;
+        }
+        if (it != idx->graphs.end()) {
+            if (cudaGraphLaunch(it->exec, s) != cudaSuccess) return SBWT_EDEVICE;
+            replayed = &it->log;
+        } else {
+            if (idx->seen.size() >= 8) idx->seen.erase(idx->seen.begin());
+            idx->seen.push_back(sig);
+            enqueue();
+        }
+    } else {
+        enqueue();
+    }
     const auto t_launch = std::chrono::steady_clock::now();
     L.add_host("host:launch", std::chrono::duration<double, std::milli>(t_launch - t_plan).count());
     if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) return SBWT_EDEVICE;
     L.add_host("host:wait",
                std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_launch).count());
     if (L.settle_units() != cudaSuccess) return SBWT_EDEVICE;
+    if (replayed && L.account_replay(*replayed) != cudaSuccess) return SBWT_EDEVICE;
     if (*idx->h_err & 1u) return SBWT_EINVAL;  // a byte outside the alphabet; the index is unchanged
     if (*idx->h_err) return SBWT_EDEVICE;      // a kernel caught an inconsistent index; keep the old one
-    idx->cur = src;
-    idx->n = n_ext;
-    idx->m = m_ext;
+    idx->cur = final_cur;
+    idx->n = final_n;
+    idx->m = final_m;
     idx->last_valid = !p.blocks.empty();
     idx->last_n = p.blocks.empty() ? 0 : p.blocks.back().n_int;
     idx->last_idx64 = p.idx64;
@@ -396,6 +472,14 @@ int Launcher::stat_index(const char* name) {
 
 int Launcher::before(const char* name, double fixed, double per_unit, const uint32_t* d_units) {
     const int s = stat_index(name);
+    if (capture) {
+        capture->launches.push_back(s);
+        if (!profiling) return -1;
+        Pending p{s, take_event(), take_event(), fixed, per_unit, d_units, false};
+        cudaEventRecordWithFlags(p.a, stream, cudaEventRecordExternal);
+        capture->timed.push_back(p);
+        return (int)capture->timed.size() - 1;
+    }
     stats[s].launches++;
     if (!profiling) return -1;
     Pending p{s, take_event(), take_event(), fixed, per_unit, d_units, d_units == nullptr};
@@ -405,7 +489,28 @@ int Launcher::before(const char* name, double fixed, double per_unit, const uint
 }
 
 void Launcher::after(int token) {
-    if (token >= 0) cudaEventRecord(pending_[token].b, stream);
+    if (token < 0) return;
+    if (capture)
+        cudaEventRecordWithFlags(capture->timed[token].b, stream, cudaEventRecordExternal);
+    else
+        cudaEventRecord(pending_[token].b, stream);
+}
+
+cudaError_t Launcher::account_replay(const GraphLog& g) {
+    for (int s : g.launches) stats[s].launches++;
+    if (g.timed.empty()) return cudaSuccess;
+    std::vector<uint32_t> log(unit_log_len);
+    cudaError_t err = cudaSuccess;
+    if (unit_log_len) err = cudaMemcpy(log.data(), unit_log, unit_log_len * 4, cudaMemcpyDeviceToHost);
+    for (const Pending& p : g.timed) {
+        float ms = 0;
+        if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) stats[p.stat].ms += ms;
+        uint32_t u = 0;
+        if (p.units && p.units >= unit_log && p.units < unit_log + unit_log_len) u = log[p.units - unit_log];
+        stats[p.stat].bytes += p.fixed + p.per_unit * u;
+    }
+    cudaGetLastError();
+    return err;
 }
 
 cudaError_t Launcher::settle_units() {
@@ -641,6 +746,7 @@ void sbwt_destroy(sbwt_index* idx) {
     if (idx->dev_ready) {
         set_device(idx);
         cudaStreamSynchronize(idx->stream);
+        drop_graphs(idx);
         idx->L.release();
         for (DevBuf* b : idx->all_bufs()) free_buf(*b);
         if (idx->h_err) cudaFreeHost(idx->h_err);
@@ -692,6 +798,72 @@ int sbwt_get_stage(sbwt_index* idx, int stage, void* out, uint64_t cap, uint64_t
         return SBWT_OK;
     }
     if (cudaMemcpy(out, src, n * elem, cudaMemcpyDeviceToHost) != cudaSuccess) return SBWT_EDEVICE;
+    return SBWT_OK;
+}
+
+int sbwt_autotune_block_suffixes(sbwt_index* idx, const uint8_t* d_reads, const uint64_t* d_offsets, uint64_t m,
+                                 const uint64_t* candidates, int ncand, uint64_t* best_out, double* ms_out) {
+    static const uint64_t kDefaults[] = {1ull << 22, 1ull << 23, 1ull << 24, 1ull << 25, 1ull << 26, 1ull << 27};
+    if (!idx || !d_offsets || m == 0) return SBWT_EINVAL;
+    if (!candidates) {
+        candidates = kDefaults;
+        ncand = (int)(sizeof(kDefaults) / sizeof(kDefaults[0]));
+    }
+    if (ncand <= 0) return SBWT_EINVAL;
+    for (int c = 0; c < ncand; ++c)
+        if (candidates[c] == 0 || candidates[c] > kMaxBlock) return SBWT_EINVAL;
+    const uint64_t saved_M = idx->M;
+    const bool saved_replay = idx->graph_replay;
+    idx->graph_replay = false;
+    uint64_t best = 0;
+    double best_ms = 0;
+    int rc = SBWT_OK;
+    for (int c = 0; c < ncand && rc == SBWT_OK; ++c) {
+        idx->M = candidates[c];
+        double t_min = -1;
+        for (int rep = 0; rep < 3; ++rep) {  // the first run sizes the buffers
+            if ((rc = sbwt_reset(idx)) != SBWT_OK) break;
+            const auto t0 = std::chrono::steady_clock::now();
+            const int a = sbwt_append_device(idx, d_reads, d_offsets, m);
+            const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+            if (a == SBWT_ENOMEM) {  // does not fit the budget: skip this candidate
+                t_min = -1;
+                break;
+            }
+            if (a != SBWT_OK) {
+                rc = a;
+                break;
+            }
+            if (rep > 0 && (t_min < 0 || ms < t_min)) t_min = ms;
+        }
+        if (ms_out) ms_out[c] = t_min;
+        if (t_min >= 0 && (best == 0 || t_min < best_ms)) {
+            best = candidates[c];
+            best_ms = t_min;
+        }
+    }
+    idx->graph_replay = saved_replay;
+    const int rr = sbwt_reset(idx);
+    if (rc != SBWT_OK) {
+        idx->M = saved_M;
+        return rc;
+    }
+    if (best == 0) {
+        idx->M = saved_M;
+        return SBWT_ENOMEM;
+    }
+    idx->M = best;
+    if (best_out) *best_out = best;
+    return rr;
+}
+
+int sbwt_set_graph_replay(sbwt_index* idx, int on) {
+    if (!idx) return SBWT_EINVAL;
+    idx->graph_replay = on != 0;
+    if (!idx->graph_replay && idx->dev_ready) {
+        if (set_device(idx) || cudaStreamSynchronize(idx->stream) != cudaSuccess) return SBWT_EDEVICE;
+        drop_graphs(idx);
+    }
     return SBWT_OK;
 }
 

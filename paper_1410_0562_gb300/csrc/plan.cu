@@ -30,8 +30,18 @@ __global__ void __launch_bounds__(kThreads) plan_check_kernel(const unsigned lon
         if (b < a || b - a + 1 > max_block) bad = true;
         else local_max = max(local_max, b - a);
     }
-    if (bad) atomicOr(&out->bad, 1u);
-    if (local_max) atomicMax(&out->max_len, local_max);
+    // one atomic per CTA, not per thread
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&out->bad, 1u);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) local_max = max(local_max, __shfl_xor_sync(0xffffffffu, local_max, o));
+    __shared__ unsigned long long warp_max[kThreads / 32];
+    if ((threadIdx.x & 31) == 0) warp_max[threadIdx.x >> 5] = local_max;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long mx = 0;
+        for (int w = 0; w < kThreads / 32; ++w) mx = max(mx, warp_max[w]);
+        if (mx) atomicMax(&out->max_len, mx);
+    }
 }
 
 __device__ __forceinline__ unsigned long long rpos(const unsigned long long* off, unsigned long long j) {
@@ -73,7 +83,7 @@ void launch_plan(Launcher& L, const uint64_t* d_offsets, uint64_t m, uint64_t M,
                  PlanBlock* table, unsigned cap, PlanSummary* summary) {
     cudaMemsetAsync(summary, 0, sizeof(PlanSummary), L.stream);
     const auto* off = reinterpret_cast<const unsigned long long*>(d_offsets);
-    const unsigned grid = (unsigned)std::min<uint64_t>(4096, (m + kThreads - 1) / kThreads + 1);
+    const unsigned grid = (unsigned)std::min<uint64_t>(1024, (m + kThreads - 1) / kThreads + 1);
     SBWT_LAUNCH(L, "plan_check", 8.0 * (m + 1), 0, nullptr, plan_check_kernel, grid, kThreads, 0, off,
                 (unsigned long long)m, (unsigned long long)max_block, summary);
     SBWT_LAUNCH(L, "plan_blocks", 0, 0, nullptr, plan_blocks_kernel, 1, 1, 0, off, (unsigned long long)m,

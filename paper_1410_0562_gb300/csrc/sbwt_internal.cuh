@@ -157,11 +157,30 @@ struct KernelStat {
 
 class Launcher {
   public:
+    struct Pending {
+        int stat;
+        cudaEvent_t a, b;
+        double fixed, per_unit;
+        const uint32_t* units;
+        bool settled;
+    };
+    // What a captured CUDA graph launches: the stat of every kernel, and
+    // (when captured with profiling on) the event pairs recorded by the graph.
+    struct GraphLog {
+        std::vector<int> launches;
+        std::vector<Pending> timed;
+    };
+
     cudaStream_t stream = nullptr;
     bool profiling = false;
     std::vector<KernelStat> stats;
     const uint32_t* unit_log = nullptr;  // device array of element counts
     size_t unit_log_len = 0;
+    GraphLog* capture = nullptr;  // non-null while a graph is being captured
+
+    // After a replay of a captured graph (stream idle): counts its launches
+    // and, if it was captured with profiling, folds in its event times.
+    cudaError_t account_replay(const GraphLog& g);
 
     int before(const char* name, double fixed, double per_unit = 0, const uint32_t* d_units = nullptr);
     void after(int token);
@@ -176,13 +195,6 @@ class Launcher {
     void release();
 
   private:
-    struct Pending {
-        int stat;
-        cudaEvent_t a, b;
-        double fixed, per_unit;
-        const uint32_t* units;
-        bool settled;
-    };
     std::vector<Pending> pending_;
     std::vector<cudaEvent_t> free_events_;
     cudaEvent_t take_event();

@@ -295,3 +295,63 @@ def test_full_size_batched_and_long_reads(name):
     idx = gpu_bwt(w.reads, w.offsets, M=1 << 25, index_bits=64)
     assert idx.size() == (oracle.num_suffixes(w.offsets), w.m)
     check_full_size(w, idx.bwt(), samples=2)
+
+
+def test_graph_replay_matches_eager():
+    """The batched form: repeated identical appends are captured into a CUDA
+    graph and replayed; every replay gives the oracle's B."""
+    w = readgen.tiny()
+    expect = oracle.bwt(w.reads, w.offsets)
+    idx = sb.SetBWT(b"ACGT", block_suffixes=20_000)  # several blocks per append
+    sb.sbwt_set_graph_replay(idx.handle, True)
+    for _ in range(6):  # eager, eager, capture, capture, replay, replay
+        idx.reset()
+        idx.append(w.reads, w.offsets)
+        assert np.array_equal(idx.bwt(), expect)
+    # incremental appends under replay: same results as one shot
+    for _ in range(3):
+        idx.reset()
+        idx.append(w.reads[: int(w.offsets[500])], w.offsets[:501])
+        idx.append(w.reads[int(w.offsets[500]):], w.offsets[500:] - w.offsets[500])
+        assert np.array_equal(idx.bwt(), expect)
+    stats = {s["name"]: s["launches"] for s in sb.sbwt_get_kernel_stats(idx.handle)}
+    assert stats.get("compute_ranks", 0) > 0 and stats.get("insert_merge", 0) > 0
+    sb.sbwt_set_graph_replay(idx.handle, False)
+    idx.reset()
+    idx.append(w.reads, w.offsets)
+    assert np.array_equal(idx.bwt(), expect)
+
+
+def test_graph_replay_device_input_with_profiling():
+    import torch
+    w = readgen.tiny()
+    expect = oracle.bwt(w.reads, w.offsets)
+    d_reads = torch.from_numpy(w.reads).cuda()
+    d_off = torch.from_numpy(w.offsets.astype(np.int64)).cuda()
+    idx = sb.SetBWT(b"ACGT", block_suffixes=30_000)
+    sb.sbwt_set_graph_replay(idx.handle, True)
+    sb.sbwt_set_profiling(idx.handle, True)
+    for _ in range(5):
+        idx.reset()
+        idx.append_device(d_reads.data_ptr(), d_off.data_ptr(), w.m)
+        assert np.array_equal(idx.bwt(), expect)
+    stats = {s["name"]: s for s in sb.sbwt_get_kernel_stats(idx.handle)}
+    # every append ran the insert kernel of each of its 4 blocks, timed
+    assert stats["insert_merge"]["launches"] == 5 * 4
+    assert stats["insert_merge"]["ms"] > 0 and stats["insert_merge"]["bytes"] > 0
+
+
+def test_autotune_block_suffixes():
+    import torch
+    w = readgen.tiny()
+    d_reads = torch.from_numpy(w.reads).cuda()
+    d_off = torch.from_numpy(w.offsets.astype(np.int64)).cuda()
+    idx = sb.SetBWT(b"ACGT")
+    best, times = sb.sbwt_autotune_block_suffixes(idx.handle, d_reads.data_ptr(), d_off.data_ptr(), w.m,
+                                                  [2048, 30_000, 1 << 20])
+    assert best in (2048, 30_000, 1 << 20) and times[best] == min(t for t in times.values() if t >= 0)
+    assert idx.size() == (0, 0)
+    idx.append_device(d_reads.data_ptr(), d_off.data_ptr(), w.m)
+    assert np.array_equal(idx.bwt(), oracle.bwt(w.reads, w.offsets))
+    with pytest.raises(sb.SbwtError):
+        sb.sbwt_autotune_block_suffixes(idx.handle, d_reads.data_ptr(), d_off.data_ptr(), w.m, [0])
