@@ -63,7 +63,15 @@ typedef struct {
     void *stream;            /* cudaStream_t every kernel is launched on; NULL =
                                 a stream the library creates and owns */
     int32_t device;          /* CUDA device ordinal; -1 = the current device */
-    uint32_t reserved[8];    /* must be zero */
+    uint32_t host_tier;      /* 0 or 1 = allowed, 2 = forbidden, 3 = always (the
+                                dictionaries live in host memory from the first
+                                append on, whatever the budget): when the HBM budget
+                                cannot hold the rank dictionaries (B_ext and its
+                                counters), they move to mapped pinned host memory
+                                and the same kernels reach them over the host link
+                                (Section 5 keeps B_ext in system memory); the
+                                per-block working set stays in HBM */
+    uint32_t reserved[7];    /* must be zero */
 } sbwt_options;
 
 /* Creates an empty index over `alphabet` (a NUL-terminated string of 1..4
@@ -107,6 +115,10 @@ int sbwt_rank_batch(sbwt_index *idx, const uint8_t *cs, const uint64_t *ks, uint
 
 /* Number of rows n (symbols, terminators included) and reads m. */
 int sbwt_size(const sbwt_index *idx, uint64_t *n, uint64_t *m);
+
+/* Memory the index holds: in HBM (counted against the budget) and in the
+ * pinned host tier. */
+int sbwt_memory(const sbwt_index *idx, uint64_t *hbm_bytes, uint64_t *host_bytes);
 
 /* Empties the index (n = m = 0) and keeps its device buffers for reuse. */
 int sbwt_reset(sbwt_index *idx);
@@ -177,6 +189,10 @@ typedef struct {
     double bytes;   /* summed algorithmic bytes */
 } sbwt_kernel_stat;
 int sbwt_set_profiling(sbwt_index *idx, int on);
+/* Profiling on, with events only around launches of the kernel named
+ * `kernel` (one of the names sbwt_get_kernel_stats reports): the least
+ * instrumentation that still times that kernel. */
+int sbwt_set_profiling_only(sbwt_index *idx, const char *kernel);
 int sbwt_get_kernel_stats(sbwt_index *idx, sbwt_kernel_stat *out, int cap, int *n_out);
 int sbwt_reset_kernel_stats(sbwt_index *idx);
 

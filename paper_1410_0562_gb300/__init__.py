@@ -37,8 +37,8 @@ SBWT_STAGE_GSA = 3
 #: every symbol include/sbwt.h declares, in header order
 EXPORTS = (
     "sbwt_create", "sbwt_create_ex", "sbwt_append", "sbwt_append_device", "sbwt_get_bwt", "sbwt_rank",
-    "sbwt_rank_batch", "sbwt_size", "sbwt_reset", "sbwt_destroy", "sbwt_strerror", "sbwt_get_stream",
-    "sbwt_set_capture", "sbwt_get_stage", "sbwt_set_profiling", "sbwt_get_kernel_stats",
+    "sbwt_rank_batch", "sbwt_memory", "sbwt_size", "sbwt_reset", "sbwt_destroy", "sbwt_strerror", "sbwt_get_stream",
+    "sbwt_set_capture", "sbwt_get_stage", "sbwt_set_profiling", "sbwt_set_profiling_only", "sbwt_get_kernel_stats",
     "sbwt_reset_kernel_stats", "sbwt_set_graph_replay", "sbwt_autotune_block_suffixes", "sbwt_bwt_noalloc",
 )
 
@@ -54,7 +54,8 @@ class SbwtError(RuntimeError):
 
 class sbwt_options(ctypes.Structure):
     _fields_ = [("index_bits", ctypes.c_uint32), ("block_suffixes", ctypes.c_uint64),
-                ("stream", ctypes.c_void_p), ("device", ctypes.c_int32), ("reserved", ctypes.c_uint32 * 8)]
+                ("stream", ctypes.c_void_p), ("device", ctypes.c_int32), ("host_tier", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32 * 7)]
 
 
 class sbwt_kernel_stat(ctypes.Structure):
@@ -92,6 +93,7 @@ def load() -> ctypes.CDLL:
             "sbwt_rank": ([P, ctypes.c_uint8, U64, ctypes.POINTER(U64)], I),
             "sbwt_rank_batch": ([P, P, P, U64, P], I),
             "sbwt_size": ([P, ctypes.POINTER(U64), ctypes.POINTER(U64)], I),
+            "sbwt_memory": ([P, ctypes.POINTER(U64), ctypes.POINTER(U64)], I),
             "sbwt_reset": ([P], I),
             "sbwt_destroy": ([P], None),
             "sbwt_strerror": ([I], ctypes.c_char_p),
@@ -99,6 +101,7 @@ def load() -> ctypes.CDLL:
             "sbwt_set_capture": ([P, I], I),
             "sbwt_get_stage": ([P, I, P, U64, ctypes.POINTER(U64)], I),
             "sbwt_set_profiling": ([P, I], I),
+            "sbwt_set_profiling_only": ([P, ctypes.c_char_p], I),
             "sbwt_get_kernel_stats": ([P, ctypes.POINTER(sbwt_kernel_stat), I, ctypes.POINTER(I)], I),
             "sbwt_reset_kernel_stats": ([P], I),
             "sbwt_set_graph_replay": ([P, I], I),
@@ -139,8 +142,8 @@ def sbwt_create(alphabet: bytes = b"ACGT", hbm_budget: int = 0):
 
 
 def sbwt_create_ex(alphabet: bytes = b"ACGT", hbm_budget: int = 0, index_bits: int = 0, block_suffixes: int = 0,
-                   stream: int = 0, device: int = -1):
-    opt = sbwt_options(index_bits, block_suffixes, stream or None, device)
+                   stream: int = 0, device: int = -1, host_tier: int = 0):
+    opt = sbwt_options(index_bits, block_suffixes, stream or None, device, host_tier)
     h = ctypes.c_void_p()
     _check(load().sbwt_create_ex(alphabet, hbm_budget, ctypes.byref(opt), ctypes.byref(h)), "sbwt_create_ex")
     return h
@@ -163,6 +166,13 @@ def sbwt_size(h):
     n, m = ctypes.c_uint64(), ctypes.c_uint64()
     _check(load().sbwt_size(h, ctypes.byref(n), ctypes.byref(m)), "sbwt_size")
     return n.value, m.value
+
+
+def sbwt_memory(h):
+    """(HBM bytes, host-tier bytes) the index holds."""
+    a, b = ctypes.c_uint64(), ctypes.c_uint64()
+    _check(load().sbwt_memory(h, ctypes.byref(a), ctypes.byref(b)), "sbwt_memory")
+    return a.value, b.value
 
 
 def sbwt_get_bwt(h) -> np.ndarray:
@@ -226,6 +236,10 @@ def sbwt_set_profiling(h, on: bool):
     _check(load().sbwt_set_profiling(h, int(on)), "sbwt_set_profiling")
 
 
+def sbwt_set_profiling_only(h, kernel: str):
+    _check(load().sbwt_set_profiling_only(h, kernel.encode()), "sbwt_set_profiling_only")
+
+
 def sbwt_get_kernel_stats(h) -> list:
     n = ctypes.c_int()
     _check(load().sbwt_get_kernel_stats(h, None, 0, ctypes.byref(n)), "sbwt_get_kernel_stats")
@@ -274,9 +288,9 @@ class SetBWT:
     """An index handle: ``SetBWT(b"ACGT").append(reads, offsets).bwt()``."""
 
     def __init__(self, alphabet: bytes = b"ACGT", hbm_budget: int = 0, index_bits: int = 0,
-                 block_suffixes: int = 0, stream: int = 0, device: int = -1):
+                 block_suffixes: int = 0, stream: int = 0, device: int = -1, host_tier: int = 0):
         self.alphabet = alphabet
-        self._h = sbwt_create_ex(alphabet, hbm_budget, index_bits, block_suffixes, stream, device)
+        self._h = sbwt_create_ex(alphabet, hbm_budget, index_bits, block_suffixes, stream, device, host_tier)
 
     @property
     def handle(self):

@@ -5,6 +5,8 @@
 // Host code only orchestrates; every step of the path is a CUDA kernel.
 #include <algorithm>
 #include <chrono>
+#include <functional>
+#include <string>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -17,9 +19,12 @@ using namespace sbwt;
 
 namespace {
 
+// A buffer in HBM, or (host tier) in mapped pinned host memory that kernels
+// reach over the host link through the same unified address.
 struct DevBuf {
     void* p = nullptr;
     size_t bytes = 0;
+    bool host = false;
 };
 
 struct Dict {
@@ -46,6 +51,9 @@ struct sbwt_index {
     size_t budget = 0;
     uint32_t index_bits = 0;
     uint64_t M = kDefaultBlock;
+    bool host_tier_allowed = true;  // dictionaries may move to pinned host memory
+    bool dict_host = false;         // they live there now
+    bool host_tier_forced = false;  // keep them there even when HBM has room
     int device = -1;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
@@ -95,9 +103,10 @@ struct sbwt_index {
         }
         return v;
     }
-    size_t held_bytes() {
+    size_t held_bytes(bool host = false) {
         size_t s = 0;
-        for (DevBuf* b : all_bufs()) s += b->bytes;
+        for (DevBuf* b : all_bufs())
+            if (b->host == host) s += b->bytes;
         return s;
     }
 };
@@ -110,24 +119,53 @@ int set_device(sbwt_index* idx) {
 }
 
 void free_buf(DevBuf& b) {
-    if (b.p) cudaFree(b.p);
+    if (b.p) {
+        if (b.host)
+            cudaFreeHost(b.p);
+        else
+            cudaFree(b.p);
+    }
     b.p = nullptr;
     b.bytes = 0;
+    b.host = false;
 }
 
-// Makes b hold at least `bytes` (contents are not kept when it grows).
-int grow(DevBuf& b, size_t bytes) {
+void* alloc_tier(size_t bytes, bool host) {
+    void* p = nullptr;
+    cudaError_t e = host ? cudaHostAlloc(&p, bytes, cudaHostAllocMapped | cudaHostAllocPortable)
+                         : cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+// Makes b hold at least `bytes` in the given tier (contents are not kept
+// when it grows or moves).
+int grow(DevBuf& b, size_t bytes, bool host = false) {
     if (bytes == 0) bytes = 256;
     bytes = (bytes + 255) & ~(size_t)255;
-    if (b.bytes >= bytes) return SBWT_OK;
+    if (b.bytes >= bytes && b.host == host) return SBWT_OK;
     free_buf(b);
-    if (cudaMalloc(&b.p, bytes) != cudaSuccess) {
-        cudaGetLastError();
-        b.p = nullptr;
-        return SBWT_ENOMEM;
-    }
+    b.p = alloc_tier(bytes, host);
+    if (!b.p) return SBWT_ENOMEM;
     b.bytes = bytes;
+    b.host = host;
     return SBWT_OK;
+}
+
+constexpr int kZeroThreads = 256;
+__global__ void zero_words_kernel(unsigned long long* p, uint64_t words) {
+    const uint64_t i = (uint64_t)blockIdx.x * kZeroThreads + threadIdx.x;
+    if (i < words) p[i] = 0ull;
+}
+
+// Zeroes the first `bytes` (a multiple of 8) of a buffer in either tier.
+void zero_async(const DevBuf& b, size_t bytes, cudaStream_t s) {
+    const uint64_t words = bytes / 8;
+    if (words) zero_words_kernel<<<ceil_div_u(words, kZeroThreads), kZeroThreads, 0, s>>>(
+        (unsigned long long*)b.p, words);
 }
 
 int device_init(sbwt_index* idx) {
@@ -148,9 +186,9 @@ int device_init(sbwt_index* idx) {
     // the committed dictionary starts empty: one zero block, one zero superblock, C = 0
     Dict& d = idx->dict[idx->cur];
     if (grow(d.blocks, sizeof(OccBlock)) || grow(d.super, 32) || grow(d.C, 32)) return SBWT_ENOMEM;
-    cudaMemsetAsync(d.blocks.p, 0, sizeof(OccBlock), idx->stream);
-    cudaMemsetAsync(d.super.p, 0, 32, idx->stream);
-    cudaMemsetAsync(d.C.p, 0, 32, idx->stream);
+    zero_async(d.blocks, sizeof(OccBlock), idx->stream);
+    zero_async(d.super, 32, idx->stream);
+    zero_async(d.C, 32, idx->stream);
     if (grow(idx->err, 4)) return SBWT_ENOMEM;
     if (cudaStreamSynchronize(idx->stream) != cudaSuccess) return SBWT_EDEVICE;
     idx->dev_ready = true;
@@ -196,6 +234,7 @@ struct Plan {
 struct Need {
     DevBuf* buf;
     size_t bytes;
+    bool dict = false;  // a dictionary buffer: may live in the host tier
 };
 
 std::vector<Need> buffer_needs(sbwt_index* idx, const Plan& p, bool host_input, uint64_t m_new) {
@@ -222,9 +261,9 @@ std::vector<Need> buffer_needs(sbwt_index* idx, const Plan& p, bool host_input, 
     v.push_back({&idx->sb_tot, (size_t)dict_supers(n_final) * 16});
     for (int k = 0; k < 3; ++k) {
         if (k == idx->cur) continue;
-        v.push_back({&idx->dict[k].blocks, (size_t)dict_blocks(n_final) * sizeof(OccBlock)});
-        v.push_back({&idx->dict[k].super, (size_t)dict_supers(n_final) * 32});
-        v.push_back({&idx->dict[k].C, 32});
+        v.push_back({&idx->dict[k].blocks, (size_t)dict_blocks(n_final) * sizeof(OccBlock), true});
+        v.push_back({&idx->dict[k].super, (size_t)dict_supers(n_final) * 32, true});
+        v.push_back({&idx->dict[k].C, 32, true});
     }
     return v;
 }
@@ -236,17 +275,72 @@ void drop_graphs(sbwt_index* idx) {
     idx->seen.clear();
 }
 
-// Budget check first (nothing changes on failure), then growth.
-int reserve(sbwt_index* idx, const std::vector<Need>& needs) {
-    size_t total = idx->held_bytes();
-    for (const Need& n : needs) {
-        size_t want = (n.bytes + 255) & ~(size_t)255;
-        if (want > n.buf->bytes) total += want - n.buf->bytes;
+size_t rounded(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// HBM the index would hold after growing to `needs`, with the dictionaries
+// in the host tier or not.
+size_t hbm_after(sbwt_index* idx, const std::vector<Need>& needs, bool dict_host) {
+    size_t total = 0;
+    for (DevBuf* b : idx->all_bufs()) {
+        bool counted = false;
+        for (const Need& n : needs)
+            if (n.buf == b) {
+                counted = true;
+                const bool host = n.dict && dict_host;
+                if (!host) total += std::max(rounded(n.bytes), b->host ? 0 : b->bytes);
+            }
+        if (!counted) {
+            const bool is_dict = b == &idx->dict[0].blocks || b == &idx->dict[0].super || b == &idx->dict[0].C ||
+                                 b == &idx->dict[1].blocks || b == &idx->dict[1].super || b == &idx->dict[1].C ||
+                                 b == &idx->dict[2].blocks || b == &idx->dict[2].super || b == &idx->dict[2].C;
+            if (!b->host && !(is_dict && dict_host)) total += b->bytes;
+        }
     }
-    if (idx->budget && total > idx->budget) return SBWT_ENOMEM;
+    return total;
+}
+
+// Moves the committed dictionary to the host tier (its contents are kept);
+// the scratch dictionaries follow on their next growth.
+int move_dicts_to_host(sbwt_index* idx) {
+    Dict& d = idx->dict[idx->cur];
+    for (DevBuf* b : {&d.blocks, &d.super, &d.C}) {
+        if (b->host || !b->p) continue;
+        void* h = alloc_tier(b->bytes, true);
+        if (!h) return SBWT_ENOMEM;
+        if (cudaMemcpyAsync(h, b->p, b->bytes, cudaMemcpyDeviceToHost, idx->stream) != cudaSuccess ||
+            cudaStreamSynchronize(idx->stream) != cudaSuccess) {
+            cudaFreeHost(h);
+            return SBWT_EDEVICE;
+        }
+        cudaFree(b->p);
+        b->p = h;
+        b->host = true;
+    }
+    for (int k = 0; k < 3; ++k)
+        if (k != idx->cur)
+            for (DevBuf* b : {&idx->dict[k].blocks, &idx->dict[k].super, &idx->dict[k].C})
+                if (!b->host) free_buf(*b);
+    idx->dict_host = true;
+    return SBWT_OK;
+}
+
+// Budget check first (nothing changes on failure), then growth.  When the
+// HBM budget cannot hold the dictionaries, they move to pinned host memory
+// (B_ext "in system memory", Section 5) and only the working set stays in HBM.
+int reserve(sbwt_index* idx, const std::vector<Need>& needs) {
+    bool dict_host = idx->dict_host || idx->host_tier_forced;
+    if (idx->budget && hbm_after(idx, needs, dict_host) > idx->budget) {
+        if (dict_host || !idx->host_tier_allowed || hbm_after(idx, needs, true) > idx->budget) return SBWT_ENOMEM;
+        dict_host = true;
+    }
+    if (dict_host && !idx->dict_host) {
+        if (int rc = move_dicts_to_host(idx)) return rc;
+        if (!idx->graphs.empty()) drop_graphs(idx);
+    }
     for (const Need& n : needs) {
-        if (n.buf->bytes < ((n.bytes + 255) & ~(size_t)255) && !idx->graphs.empty()) drop_graphs(idx);
-        if (int rc = grow(*n.buf, n.bytes)) return rc;
+        const bool host = n.dict && dict_host;
+        if ((n.buf->bytes < rounded(n.bytes) || n.buf->host != host) && !idx->graphs.empty()) drop_graphs(idx);
+        if (int rc = grow(*n.buf, n.bytes, host)) return rc;
     }
     return SBWT_OK;
 }
@@ -368,7 +462,8 @@ int append_impl(sbwt_index* idx, const uint8_t* d_reads, const uint64_t* d_offse
         // replay a captured graph of an identical append (same plan, sizes,
         // index state and buffers); capture one on the second sighting
         std::vector<unsigned long long> sig = {m_new, p.npos, p.nbytes, idx->n, idx->m, (unsigned long long)idx->cur,
-                                               p.idx64, L.profiling, (unsigned long long)(uintptr_t)d_reads,
+                                               p.idx64, L.profiling, std::hash<std::string>{}(L.only),
+                                               (unsigned long long)(uintptr_t)d_reads,
                                                (unsigned long long)(uintptr_t)d_offsets, p.blocks.size()};
         for (const BlockPlan& b : p.blocks) sig.insert(sig.end(), {b.j0, b.j1, b.n_int, b.base, b.max_len});
         for (DevBuf* b : idx->all_bufs()) sig.push_back((unsigned long long)(uintptr_t)b->p);
@@ -472,16 +567,17 @@ int Launcher::stat_index(const char* name) {
 
 int Launcher::before(const char* name, double fixed, double per_unit, const uint32_t* d_units) {
     const int s = stat_index(name);
+    const bool timed = profiling && (only.empty() || only == name);
     if (capture) {
         capture->launches.push_back(s);
-        if (!profiling) return -1;
+        if (!timed) return -1;
         Pending p{s, take_event(), take_event(), fixed, per_unit, d_units, false};
         cudaEventRecordWithFlags(p.a, stream, cudaEventRecordExternal);
         capture->timed.push_back(p);
         return (int)capture->timed.size() - 1;
     }
     stats[s].launches++;
-    if (!profiling) return -1;
+    if (!timed) return -1;
     Pending p{s, take_event(), take_event(), fixed, per_unit, d_units, d_units == nullptr};
     cudaEventRecord(p.a, stream);
     pending_.push_back(p);
@@ -604,6 +700,7 @@ int sbwt_create_ex(const char* alphabet, size_t hbm_budget_bytes, const sbwt_opt
     if (opt) {
         bool bad = opt->index_bits != 0 && opt->index_bits != 32 && opt->index_bits != 64;
         bad |= opt->block_suffixes > kMaxBlock;
+        bad |= opt->host_tier > 3;
         for (uint32_t r : opt->reserved) bad |= r != 0;
         if (bad) {
             delete idx;
@@ -613,6 +710,8 @@ int sbwt_create_ex(const char* alphabet, size_t hbm_budget_bytes, const sbwt_opt
         if (opt->block_suffixes) idx->M = opt->block_suffixes;
         idx->stream = (cudaStream_t)opt->stream;
         idx->device = opt->device;
+        idx->host_tier_allowed = opt->host_tier != 2;
+        idx->host_tier_forced = opt->host_tier == 3;
     }
     *out = idx;
     return SBWT_OK;
@@ -720,6 +819,14 @@ int sbwt_rank(sbwt_index* idx, uint8_t c, uint64_t k, uint64_t* out) {
     return sbwt_rank_batch(idx, &c, &k, 1, out);
 }
 
+int sbwt_memory(const sbwt_index* idx, uint64_t* hbm_bytes, uint64_t* host_bytes) {
+    if (!idx) return SBWT_EINVAL;
+    sbwt_index* mut = const_cast<sbwt_index*>(idx);
+    if (hbm_bytes) *hbm_bytes = mut->held_bytes(false);
+    if (host_bytes) *host_bytes = mut->held_bytes(true);
+    return SBWT_OK;
+}
+
 int sbwt_size(const sbwt_index* idx, uint64_t* n, uint64_t* m) {
     if (!idx) return SBWT_EINVAL;
     if (n) *n = idx->n;
@@ -734,9 +841,9 @@ int sbwt_reset(sbwt_index* idx) {
     if (!idx->dev_ready) return SBWT_OK;
     if (set_device(idx)) return SBWT_EDEVICE;
     Dict& d = idx->dict[idx->cur];
-    cudaMemsetAsync(d.blocks.p, 0, sizeof(OccBlock), idx->stream);
-    cudaMemsetAsync(d.super.p, 0, 32, idx->stream);
-    cudaMemsetAsync(d.C.p, 0, 32, idx->stream);
+    zero_async(d.blocks, sizeof(OccBlock), idx->stream);
+    zero_async(d.super, 32, idx->stream);
+    zero_async(d.C, 32, idx->stream);
     if (cudaStreamSynchronize(idx->stream) != cudaSuccess) return SBWT_EDEVICE;
     return SBWT_OK;
 }
@@ -870,6 +977,14 @@ int sbwt_set_graph_replay(sbwt_index* idx, int on) {
 int sbwt_set_profiling(sbwt_index* idx, int on) {
     if (!idx) return SBWT_EINVAL;
     idx->L.profiling = on != 0;
+    idx->L.only.clear();
+    return SBWT_OK;
+}
+
+int sbwt_set_profiling_only(sbwt_index* idx, const char* kernel) {
+    if (!idx || !kernel) return SBWT_EINVAL;
+    idx->L.profiling = true;
+    idx->L.only = kernel;
     return SBWT_OK;
 }
 

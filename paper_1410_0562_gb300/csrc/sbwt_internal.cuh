@@ -173,6 +173,7 @@ class Launcher {
 
     cudaStream_t stream = nullptr;
     bool profiling = false;
+    std::string only;  // with profiling: time only launches of this name (empty = all)
     std::vector<KernelStat> stats;
     const uint32_t* unit_log = nullptr;  // device array of element counts
     size_t unit_log_len = 0;

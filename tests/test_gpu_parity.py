@@ -355,3 +355,40 @@ def test_autotune_block_suffixes():
     assert np.array_equal(idx.bwt(), oracle.bwt(w.reads, w.offsets))
     with pytest.raises(sb.SbwtError):
         sb.sbwt_autotune_block_suffixes(idx.handle, d_reads.data_ptr(), d_off.data_ptr(), w.m, [0])
+
+
+def test_host_tier_forced():
+    """Rank dictionaries in mapped pinned host memory: same B, same ranks."""
+    w = readgen.tiny()
+    expect = oracle.bwt(w.reads, w.offsets)
+    idx = gpu_bwt(w.reads, w.offsets, M=20_000, cuts=w.appends)
+    ref_ranks = idx.rank_batch(np.full(50, ord("C"), np.uint8), np.arange(0, 101_000, 2020, dtype=np.uint64))
+    h = sb.SetBWT(b"ACGT", block_suffixes=20_000, host_tier=3)
+    h.append(w.reads[: int(w.offsets[500])], w.offsets[:501])
+    h.append(w.reads[int(w.offsets[500]):], w.offsets[500:] - w.offsets[500])
+    assert np.array_equal(h.bwt(), expect)
+    hbm, host = sb.sbwt_memory(h.handle)
+    assert host > 0
+    assert np.array_equal(h.rank_batch(np.full(50, ord("C"), np.uint8), np.arange(0, 101_000, 2020, dtype=np.uint64)),
+                          ref_ranks)
+
+
+def test_host_tier_under_budget():
+    """A budget that holds the working set but not the dictionaries moves
+    them to the host tier instead of failing; B is unchanged."""
+    w = readgen.tiny()
+    expect = oracle.bwt(w.reads, w.offsets)
+    probe = sb.SetBWT(b"ACGT", host_tier=3)
+    probe.append(w.reads, w.offsets)
+    ws_hbm, dict_host = sb.sbwt_memory(probe.handle)
+    assert dict_host > 0
+    budget = ws_hbm + 64 * 1024  # less than the three dictionaries need
+    idx = sb.SetBWT(b"ACGT", hbm_budget=budget)
+    idx.append(w.reads, w.offsets)
+    assert np.array_equal(idx.bwt(), expect)
+    hbm, host = sb.sbwt_memory(idx.handle)
+    assert hbm <= budget and host > 0
+    forbidden = sb.SetBWT(b"ACGT", hbm_budget=budget, host_tier=2)
+    with pytest.raises(sb.SbwtError) as e:
+        forbidden.append(w.reads, w.offsets)
+    assert e.value.code == sb.SBWT_ENOMEM
