@@ -49,6 +49,8 @@ extern "C" {
 #define SBWT_ERANGE (-3)   /* output buffer too small; the needed size is reported */
 #define SBWT_EDEVICE (-4)  /* a CUDA error, or a device-side wait that gave up */
 #define SBWT_ENOTSUP (-5)  /* option not supported by this build */
+#define SBWT_EBUSY (-6)    /* the index is serving: only submit/wait are allowed */
+#define SBWT_ETIMEDOUT (-7) /* sbwt_wait: the request is not done yet */
 
 typedef struct sbwt_index sbwt_index; /* opaque, owned by the library */
 
@@ -195,6 +197,32 @@ int sbwt_set_profiling(sbwt_index *idx, int on);
 int sbwt_set_profiling_only(sbwt_index *idx, const char *kernel);
 int sbwt_get_kernel_stats(sbwt_index *idx, sbwt_kernel_stat *out, int cap, int *n_out);
 int sbwt_reset_kernel_stats(sbwt_index *idx);
+
+/* ---- served form: continuous batching of append requests ---------------
+ * sbwt_serve_start attaches a server to the index: requests submitted with
+ * sbwt_submit are appended in arrival order (their reads get consecutive
+ * global ids in that order, as if appended one by one).  Requests waiting
+ * when a batch starts are coalesced into that batch (one append, so one pass
+ * of Insert over the index for all of them), up to max_batch_bases bases
+ * (0 = no cap); the next batch's copy to the device overlaps the running
+ * batch's kernels.  A request with a byte outside the alphabet fails alone
+ * (SBWT_EINVAL from sbwt_wait).  While serving, the other calls that use the
+ * index return SBWT_EBUSY; sbwt_serve_stop finishes every submitted request
+ * and detaches the server (sbwt_destroy does too). */
+int sbwt_serve_start(sbwt_index *idx, uint64_t max_batch_bases);
+/* Copies the request (host arrays, as in sbwt_append) and queues it;
+ * *ticket names it.  Thread-safe.  Errors: SBWT_EINVAL (not serving, bad
+ * offsets), SBWT_EBUSY (stopping), SBWT_EDEVICE (serving ended on a device
+ * error). */
+int sbwt_submit(sbwt_index *idx, const uint8_t *reads, const uint64_t *offsets, uint64_t m, uint64_t *ticket);
+/* Waits up to timeout_us (0 = do not wait) for a request; returns its
+ * status (SBWT_ETIMEDOUT if not done yet, and the ticket stays valid), the
+ * global id of its first read and its latency from submit to commit in ms.
+ * A finished ticket can be waited for once.  Thread-safe. */
+int sbwt_wait(sbwt_index *idx, uint64_t ticket, uint64_t timeout_us, uint64_t *first_read_id, double *latency_ms);
+/* Finishes the submitted requests and stops serving; returns SBWT_EDEVICE if
+ * a device error ended serving early, else SBWT_OK. */
+int sbwt_serve_stop(sbwt_index *idx);
 
 /* ---- BWT of a small read set without allocating -------------------------
  * The paper has no counterpart to this call.  It is for callers that cannot

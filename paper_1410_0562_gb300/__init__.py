@@ -28,6 +28,8 @@ SBWT_ENOMEM = -2
 SBWT_ERANGE = -3
 SBWT_EDEVICE = -4
 SBWT_ENOTSUP = -5
+SBWT_EBUSY = -6
+SBWT_ETIMEDOUT = -7
 
 SBWT_STAGE_SA = 0
 SBWT_STAGE_BINT = 1
@@ -39,7 +41,8 @@ EXPORTS = (
     "sbwt_create", "sbwt_create_ex", "sbwt_append", "sbwt_append_device", "sbwt_get_bwt", "sbwt_rank",
     "sbwt_rank_batch", "sbwt_memory", "sbwt_size", "sbwt_reset", "sbwt_destroy", "sbwt_strerror", "sbwt_get_stream",
     "sbwt_set_capture", "sbwt_get_stage", "sbwt_set_profiling", "sbwt_set_profiling_only", "sbwt_get_kernel_stats",
-    "sbwt_reset_kernel_stats", "sbwt_set_graph_replay", "sbwt_autotune_block_suffixes", "sbwt_bwt_noalloc",
+    "sbwt_reset_kernel_stats", "sbwt_set_graph_replay", "sbwt_autotune_block_suffixes", "sbwt_serve_start",
+    "sbwt_submit", "sbwt_wait", "sbwt_serve_stop", "sbwt_bwt_noalloc",
 )
 
 #: most suffixes (reads + one terminator each) sbwt_bwt_noalloc accepts
@@ -106,6 +109,10 @@ def load() -> ctypes.CDLL:
             "sbwt_reset_kernel_stats": ([P], I),
             "sbwt_set_graph_replay": ([P, I], I),
             "sbwt_autotune_block_suffixes": ([P, P, P, U64, P, I, ctypes.POINTER(U64), P], I),
+            "sbwt_serve_start": ([P, U64], I),
+            "sbwt_submit": ([P, P, P, U64, ctypes.POINTER(U64)], I),
+            "sbwt_wait": ([P, U64, U64, ctypes.POINTER(U64), ctypes.POINTER(ctypes.c_double)], I),
+            "sbwt_serve_stop": ([P], I),
             "sbwt_bwt_noalloc": ([ctypes.c_char_p, P, P, U64, P, U64, ctypes.POINTER(U64), P], I),
         }
         for name, (args, res) in sig.items():
@@ -282,6 +289,29 @@ def sbwt_bwt_noalloc(alphabet: bytes, reads, offsets, stream: int = 0) -> np.nda
     _check(load().sbwt_bwt_noalloc(alphabet, rp, op, m, ctypes.c_void_p(out.ctypes.data), n, ctypes.byref(got),
                                    ctypes.c_void_p(stream or None)), "sbwt_bwt_noalloc")
     return out[: got.value]
+
+
+def sbwt_serve_start(h, max_batch_bases: int = 0):
+    _check(load().sbwt_serve_start(h, max_batch_bases), "sbwt_serve_start")
+
+
+def sbwt_submit(h, reads, offsets) -> int:
+    rp, rk = _host_ptr(reads, np.uint8)
+    op, ok = _host_ptr(offsets, np.uint64)
+    t = ctypes.c_uint64()
+    _check(load().sbwt_submit(h, rp, op, len(ok) - 1, ctypes.byref(t)), "sbwt_submit")
+    return t.value
+
+
+def sbwt_wait(h, ticket: int, timeout_us: int = 600_000_000):
+    """(status, first read id, latency ms); status is an SBWT_* code."""
+    first, lat = ctypes.c_uint64(), ctypes.c_double()
+    rc = load().sbwt_wait(h, ticket, timeout_us, ctypes.byref(first), ctypes.byref(lat))
+    return rc, first.value, lat.value
+
+
+def sbwt_serve_stop(h):
+    _check(load().sbwt_serve_stop(h), "sbwt_serve_stop")
 
 
 class SetBWT:

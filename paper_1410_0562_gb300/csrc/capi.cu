@@ -7,6 +7,7 @@
 #include <chrono>
 #include <functional>
 #include <string>
+#include <thread>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -14,6 +15,7 @@
 
 #include "sbwt.h"
 #include "sbwt_kernels.cuh"
+#include "sbwt_serve.h"
 
 using namespace sbwt;
 
@@ -85,6 +87,8 @@ struct sbwt_index {
     bool graph_replay = false;
     std::vector<GraphEntry> graphs;                    // most recent last
     std::vector<std::vector<unsigned long long>> seen;  // signatures run once, eagerly
+    void* server = nullptr;           // continuous-batching server, when serving
+    std::thread::id server_worker;    // the only thread that may change the index then
     bool capture = false;
     bool last_valid = false;
     uint64_t last_n = 0;
@@ -112,6 +116,10 @@ struct sbwt_index {
 };
 
 namespace {
+
+// While a server runs, only its worker may use the index (besides
+// submit/wait and the read-only size query).
+bool busy(const sbwt_index* idx) { return idx->server && std::this_thread::get_id() != idx->server_worker; }
 
 int set_device(sbwt_index* idx) {
     if (idx->device >= 0 && cudaSetDevice(idx->device) != cudaSuccess) return SBWT_EDEVICE;
@@ -683,6 +691,8 @@ const char* sbwt_strerror(int code) {
         case SBWT_ERANGE: return "output buffer too small";
         case SBWT_EDEVICE: return "CUDA device error";
         case SBWT_ENOTSUP: return "not supported";
+        case SBWT_EBUSY: return "the index is serving requests";
+        case SBWT_ETIMEDOUT: return "not done yet";
         default: return "unknown error";
     }
 }
@@ -723,6 +733,7 @@ int sbwt_create(const char* alphabet, size_t hbm_budget_bytes, sbwt_index** out)
 
 int sbwt_append(sbwt_index* idx, const uint8_t* reads, const uint64_t* offsets, uint64_t m) {
     if (!idx || !offsets) return SBWT_EINVAL;
+    if (busy(idx)) return SBWT_EBUSY;
     const auto t0 = std::chrono::steady_clock::now();
     if (validate_offsets(offsets, m)) return SBWT_EINVAL;
     if (m == 0) return SBWT_OK;
@@ -732,6 +743,7 @@ int sbwt_append(sbwt_index* idx, const uint8_t* reads, const uint64_t* offsets, 
 
 int sbwt_append_device(sbwt_index* idx, const uint8_t* d_reads, const uint64_t* d_offsets, uint64_t m) {
     if (!idx || !d_offsets) return SBWT_EINVAL;
+    if (busy(idx)) return SBWT_EBUSY;
     const auto t0 = std::chrono::steady_clock::now();
     if (int rc = device_init(idx)) return rc;
     if (m == 0) return SBWT_OK;
@@ -773,12 +785,16 @@ int sbwt_append_device(sbwt_index* idx, const uint8_t* d_reads, const uint64_t* 
 
 int sbwt_get_bwt(sbwt_index* idx, uint8_t* out, uint64_t cap, uint64_t* n_out) {
     if (!idx || !n_out) return SBWT_EINVAL;
+    if (busy(idx)) return SBWT_EBUSY;
     *n_out = idx->n;
     if (cap < idx->n) return SBWT_ERANGE;
     if (idx->n == 0) return SBWT_OK;
     if (!out) return SBWT_EINVAL;
     if (int rc = device_init(idx)) return rc;
-    if (int rc = reserve(idx, {{&idx->out_bytes, (size_t)idx->n}})) return rc;
+    if (reserve(idx, {{&idx->out_bytes, (size_t)idx->n}}) != SBWT_OK) {
+        // over the HBM budget: stage B in pinned host memory instead
+        if (!idx->host_tier_allowed || grow(idx->out_bytes, idx->n, true) != SBWT_OK) return SBWT_ENOMEM;
+    }
     launch_unpack(idx->L, (const OccBlock*)idx->dict[idx->cur].blocks.p, idx->n, idx->alpha4,
                   (uint8_t*)idx->out_bytes.p);
     cudaMemcpyAsync(out, idx->out_bytes.p, idx->n, cudaMemcpyDeviceToHost, idx->stream);
@@ -788,6 +804,7 @@ int sbwt_get_bwt(sbwt_index* idx, uint8_t* out, uint64_t cap, uint64_t* n_out) {
 
 int sbwt_rank_batch(sbwt_index* idx, const uint8_t* cs, const uint64_t* ks, uint64_t q, uint64_t* out) {
     if (!idx || (q && (!cs || !ks || !out))) return SBWT_EINVAL;
+    if (busy(idx)) return SBWT_EBUSY;
     std::vector<uint8_t> codes(q);
     for (uint64_t i = 0; i < q; ++i) {
         if (ks[i] > idx->n) return SBWT_EINVAL;
@@ -800,8 +817,13 @@ int sbwt_rank_batch(sbwt_index* idx, const uint8_t* cs, const uint64_t* ks, uint
     }
     if (q == 0) return SBWT_OK;
     if (int rc = device_init(idx)) return rc;
-    if (int rc = reserve(idx, {{&idx->q_codes, (size_t)q}, {&idx->q_ks, (size_t)q * 8}, {&idx->q_out, (size_t)q * 8}}))
-        return rc;
+    if (reserve(idx, {{&idx->q_codes, (size_t)q}, {&idx->q_ks, (size_t)q * 8}, {&idx->q_out, (size_t)q * 8}}) !=
+        SBWT_OK) {
+        // over the HBM budget: the query arrays go to pinned host memory
+        if (!idx->host_tier_allowed || grow(idx->q_codes, q, true) || grow(idx->q_ks, q * 8, true) ||
+            grow(idx->q_out, q * 8, true))
+            return SBWT_ENOMEM;
+    }
     cudaStream_t s = idx->stream;
     cudaMemcpyAsync(idx->q_codes.p, codes.data(), q, cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(idx->q_ks.p, ks, q * 8, cudaMemcpyHostToDevice, s);
@@ -836,6 +858,7 @@ int sbwt_size(const sbwt_index* idx, uint64_t* n, uint64_t* m) {
 
 int sbwt_reset(sbwt_index* idx) {
     if (!idx) return SBWT_EINVAL;
+    if (busy(idx)) return SBWT_EBUSY;
     idx->n = idx->m = 0;
     idx->last_valid = false;
     if (!idx->dev_ready) return SBWT_OK;
@@ -850,6 +873,7 @@ int sbwt_reset(sbwt_index* idx) {
 
 void sbwt_destroy(sbwt_index* idx) {
     if (!idx) return;
+    if (idx->server) sbwt_serve_stop(idx);
     if (idx->dev_ready) {
         set_device(idx);
         cudaStreamSynchronize(idx->stream);
@@ -1013,3 +1037,16 @@ int sbwt_reset_kernel_stats(sbwt_index* idx) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Server hooks
+// ---------------------------------------------------------------------------
+void* sbwt_serve_attached(sbwt_index* idx) { return idx->server; }
+void sbwt_serve_attach(sbwt_index* idx, void* server) { idx->server = server; }
+void sbwt_serve_set_worker(sbwt_index* idx, std::thread::id id) { idx->server_worker = id; }
+int sbwt_serve_append_device(sbwt_index* idx, const uint8_t* d_reads, const uint64_t* d_offsets, uint64_t m) {
+    return sbwt_append_device(idx, d_reads, d_offsets, m);
+}
+int sbwt_serve_append_host(sbwt_index* idx, const uint8_t* reads, const uint64_t* offsets, uint64_t m) {
+    return sbwt_append(idx, reads, offsets, m);
+}
