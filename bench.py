@@ -46,10 +46,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="short", choices=["short", "tiny"])
+    ap.add_argument("--workload", default="short", choices=["short", "tiny", "serve"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-form measurement")
+    ap.add_argument("--no-serving", action="store_true", help="skip the served-form measurement")
     ap.add_argument("--profile-steps", type=int, default=None,
                     help="steps run under per-kernel event timing (default: the timed steps)")
     return ap.parse_args()
@@ -159,6 +160,54 @@ class Clocks:
             return None
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def measure_serving(sb, idx, requests, rate_rps=None, seed=7):
+    """Serves `requests` (list of (reads, offsets)) against the index: all at
+    once when rate_rps is None (closed loop: the sustained rate), else with
+    Poisson arrivals at rate_rps requests/s.  Returns latency percentiles,
+    throughput over the serving window and the batches' sizes."""
+    import threading
+    rng = np.random.default_rng(seed)
+    gaps = rng.exponential(1.0 / rate_rps, size=len(requests)) if rate_rps else np.zeros(len(requests))
+    tickets = [None] * len(requests)
+    sb.sbwt_serve_start(idx.handle, 0)
+    t0 = time.perf_counter()
+
+    def submitter():
+        t = t0
+        for i, (r, o) in enumerate(requests):
+            t += gaps[i]
+            delay = t - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            tickets[i] = sb.sbwt_submit(idx.handle, r, o)
+
+    th = threading.Thread(target=submitter)
+    th.start()
+    th.join()
+    lat = []
+    for tk in tickets:
+        rc, _, ms = sb.sbwt_wait(idx.handle, tk)
+        assert rc == sb.SBWT_OK, rc
+        lat.append(ms)
+    t1 = time.perf_counter()
+    sb.sbwt_serve_stop(idx.handle)
+    bases = sum(int(o[-1]) for _, o in requests)
+    return {"requests": len(requests), "bases": bases, "Mbps": bases / (t1 - t0) / 1e6,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "offered_rps": rate_rps}
+
+
+def serving_report(sb, idx, requests):
+    """Closed loop for the sustained rate, then Poisson arrivals at 0.5x and
+    0.9x of it (in requests/s); the index keeps growing across the runs."""
+    closed = measure_serving(sb, idx, requests)
+    sustained_rps = closed["requests"] / (closed["bases"] / closed["Mbps"] / 1e6)
+    out = {"sustained": closed}
+    for f in (0.5, 0.9):
+        out[f"load_{f}"] = measure_serving(sb, idx, requests, rate_rps=f * sustained_rps, seed=int(f * 100))
+    return out
 
 
 def cpu_baseline(w, n_reads: int):
@@ -369,6 +418,19 @@ def run_gb300(args):
                                             if b_dom and b_dom["ms"] > 0 else None)}
         idx_b.close()
 
+    # the served form: requests of 10k..200k reads (U[100,150] bp) from the
+    # same genome arriving at an index that holds the whole workload
+    served = None
+    if not args.no_serving and args.workload == "short":
+        g = readgen.genome(10_000_000, 0x14100562 + 2 + 1000 * rank)
+        rs = np.random.default_rng(99 + rank)
+        sizes = np.exp(rs.uniform(np.log(10_000), np.log(200_000), size=24)).astype(np.int64)
+        requests = [readgen.sampled_reads(g, int(mm), rs.integers(100, 151, size=int(mm)), 0.01, 500 + i)
+                    for i, mm in enumerate(sizes)]
+        idx.reset()
+        idx.append_device(d_reads.data_ptr(), d_off.data_ptr(), w.m)
+        served = serving_report(sb, idx, requests)
+
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -401,6 +463,7 @@ def run_gb300(args):
         "e2e": e2e,
         "gpu_launches": launches,
         "batched": batched,
+        "served": served,
         "kernels": kernels,  # one untimed step with every kernel timed
         "host_ms_per_step": host_phases,
     }
@@ -415,10 +478,75 @@ def run_gb300(args):
     return 0
 
 
+def run_serve_workload(args):
+    """The serving workload: a resident index of 20M x 100 bp reads (2 Gbp)
+    under an 8 GB HBM budget, then append requests of 10k..1M reads arriving
+    all at once (sustained rate) and as Poisson streams at 0.5x and 0.9x of
+    it.  A second, smaller index under a 256 MB budget keeps its dictionaries
+    in the pinned host tier and serves the same way."""
+    import torch
+
+    import paper_1410_0562_gb300 as sb
+    rank, world, local = dist_env()
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(local)
+    sb.build()
+    sb.load()
+    t = time.perf_counter()
+    resident, requests = readgen.serving()
+    gen_s = time.perf_counter() - t
+    stream = torch.cuda.Stream()
+    idx = sb.SetBWT(b"ACGT", hbm_budget=8 << 30, index_bits=64, block_suffixes=1 << 25,
+                    stream=stream.cuda_stream, device=local)
+    d_reads = torch.from_numpy(resident.reads).to("cuda")
+    d_off = torch.from_numpy(resident.offsets.astype(np.int64)).to("cuda")
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    idx.append_device(d_reads.data_ptr(), d_off.data_ptr(), resident.m)
+    build_s = time.perf_counter() - t
+    del d_reads, d_off
+    torch.cuda.empty_cache()
+    hbm, host = sb.sbwt_memory(idx.handle)
+    report = serving_report(sb, idx, requests)
+    n, m = idx.size()
+    idx.close()
+
+    # host tier: dictionaries in pinned host memory under a tight budget
+    small = readgen.Workload("resident-2Mx100", resident.reads[: int(resident.offsets[2_000_000])],
+                             resident.offsets[: 2_000_001], 1 << 21, 64, (0, 2_000_000))
+    idx2 = sb.SetBWT(b"ACGT", hbm_budget=256 << 20, index_bits=64, block_suffixes=1 << 21,
+                     stream=stream.cuda_stream, device=local)
+    t = time.perf_counter()
+    idx2.append(small.reads, small.offsets)
+    build2_s = time.perf_counter() - t
+    hbm2, host2 = sb.sbwt_memory(idx2.handle)
+    small_reqs = [r for r in requests if len(r[1]) - 1 <= 100_000][:12]
+    report2 = {"sustained": measure_serving(sb, idx2, small_reqs)}
+    idx2.close()
+    line = {
+        "metric": "append throughput, served (Mbp/s); p50/p99 append latency", "unit": UNIT,
+        "value": report["sustained"]["Mbps"], "higher_is_better": True, "n_gpus": 1, "data": "synthetic",
+        "dtype": "u64",
+        "config": {"workload": resident.name, "requests": len(requests), "hbm_budget": 8 << 30,
+                   "block_suffixes": 1 << 25},
+        "resident_build_s": build_s, "resident_build_Mbps": resident.bases / build_s / 1e6,
+        "generation_s": gen_s, "index_rows_after": n, "index_reads_after": m,
+        "memory_after_build": {"hbm": hbm, "host": host},
+        "serving": report,
+        "host_tier": {"resident": small.name, "hbm_budget": 256 << 20, "build_s": build2_s,
+                      "memory": {"hbm": hbm2, "host": host2}, "serving": report2},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "serve":
+        return run_serve_workload(args)
     return run_gb300(args)
 
 

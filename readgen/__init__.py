@@ -7,10 +7,11 @@ returns, and neither is imported here.
 The paper measures on two real sequencing sets that are not available here
 (NA12878, 1.2 G x 101 bp Illumina reads; Venter, 32 M x 875 bp Sanger reads;
 Section 7).  The generators below stand in for them with the same shapes:
-short reads at ~10x coverage of a genome, ragged mid-length reads, and long
-reads with indels.  All randomness comes from numpy's PCG64 generator seeded
-with the values listed in ``CONFIGS``; the same seed gives the same reads on
-any machine with the same numpy version.
+short reads at ~10x coverage of a genome, ragged mid-length reads, long
+reads with indels, and request streams for the served form.  All randomness
+comes from numpy's PCG64 generator seeded with each workload function's
+default seeds; the same seed gives the same reads on any machine with the
+same numpy version.
 
 A read set is returned as ``(reads, offsets)``: ``reads`` is a uint8 array of
 ASCII bases (the concatenation of all reads) and ``offsets`` a uint64 array of
@@ -91,19 +92,23 @@ def sampled_reads(g: np.ndarray, n_reads: int, lengths, sub_rate: float, seed: i
     out = np.empty(int(off[-1]), dtype=np.uint8)
     starts = rng.integers(0, G - lengths + 1)
     minus = rng.random(n_reads) < 0.5
-    # group by length so each group is one vectorised gather
+    # group by length so each group is one vectorised gather, in chunks of
+    # reads to bound the temporary arrays
+    chunk = 1 << 19
     for L in np.unique(lengths):
-        idx = np.nonzero(lengths == L)[0]
         if L == 0:
             continue
-        win = np.lib.stride_tricks.sliding_window_view(g, int(L))[starts[idx]].copy()
-        mi = minus[idx]
-        win[mi] = _revcomp(win[mi])
-        sub = rng.random(win.shape) < sub_rate
-        shift = rng.integers(1, 4, size=win.shape, dtype=np.uint8)
-        win = np.where(sub, (win + shift) & 3, win).astype(np.uint8)
-        pos = off[idx][:, None].astype(np.int64) + np.arange(int(L))[None, :]
-        out[pos.ravel()] = win.ravel()
+        all_idx = np.nonzero(lengths == L)[0]
+        for c0 in range(0, len(all_idx), chunk):
+            idx = all_idx[c0:c0 + chunk]
+            win = np.lib.stride_tricks.sliding_window_view(g, int(L))[starts[idx]].copy()
+            mi = minus[idx]
+            win[mi] = _revcomp(win[mi])
+            sub = rng.random(win.shape) < sub_rate
+            shift = rng.integers(1, 4, size=win.shape, dtype=np.uint8)
+            win = np.where(sub, (win + shift) & 3, win).astype(np.uint8)
+            pos = off[idx][:, None].astype(np.int64) + np.arange(int(L))[None, :]
+            out[pos.ravel()] = win.ravel()
     return _LUT[out], off
 
 
@@ -195,3 +200,23 @@ def long(n_reads: int = 20_000, genome_size: int = 100_000_000, seed_genome: int
     g = genome(genome_size, seed_genome)
     reads, off = long_reads(g, n_reads, 10_000.0, 0.5, (1_000, 50_000), 0.02, 0.02, 0.06, seed_reads)
     return Workload(f"long-{n_reads}xlognormal10k-g{genome_size}", reads, off, 0, 64, (0, n_reads))
+
+
+def serving(n_resident: int = 20_000_000, genome_size: int = 200_000_000, n_requests: int = 48,
+            seed_genome: int = 0x14100562 + 5, seed_reads: int = 0x05621410 + 5, max_request: int = 1_000_000):
+    """The serving workload: a resident set of n_resident x 100 bp reads (1%
+    substitutions) from a seeded i.i.d. genome, and request read sets whose
+    sizes are log-uniform in [10k, max_request] reads of length U[100, 150]
+    from the same genome.  Returns (resident Workload, list of (reads,
+    offsets))."""
+    g = genome(genome_size, seed_genome)
+    reads, off = sampled_reads(g, n_resident, 100, 0.01, seed_reads)
+    resident = Workload(f"serving-resident-{n_resident}x100-g{genome_size}", reads, off, 1 << 25, 64,
+                        (0, n_resident))
+    rng = _rng(seed_reads ^ 0xA5A5)
+    sizes = np.exp(rng.uniform(np.log(10_000), np.log(max_request), size=n_requests)).astype(np.int64)
+    requests = []
+    for i, m in enumerate(sizes):
+        lengths = rng.integers(100, 151, size=int(m))
+        requests.append(sampled_reads(g, int(m), lengths, 0.01, seed_reads + 1 + i))
+    return resident, requests
