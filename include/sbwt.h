@@ -115,6 +115,15 @@ int sbwt_rank(sbwt_index *idx, uint8_t c, uint64_t k, uint64_t *out);
  * Errors: SBWT_EINVAL if any query is invalid (nothing written). */
 int sbwt_rank_batch(sbwt_index *idx, const uint8_t *cs, const uint64_t *ks, uint64_t q, uint64_t *out);
 
+/* FM-index counting: counts[i] = occurrences of pattern i in the reads
+ * (overlapping ones included), by backward search over B (Lemma 1 applied to
+ * the pattern: the rows of the suffixes that start with P[k..], from [0, n),
+ * one LF step per symbol).  Pattern i is patterns[offsets[i] .. offsets[i+1])
+ * in host memory; offsets has q+1 non-decreasing entries starting at 0.  A
+ * pattern with a byte outside the alphabet occurs 0 times; the empty pattern
+ * counts every suffix (n).  Errors: SBWT_EINVAL for bad offsets. */
+int sbwt_count(sbwt_index *idx, const uint8_t *patterns, const uint64_t *offsets, uint64_t q, uint64_t *counts);
+
 /* Number of rows n (symbols, terminators included) and reads m. */
 int sbwt_size(const sbwt_index *idx, uint64_t *n, uint64_t *m);
 

@@ -23,6 +23,7 @@ arrays into it.  Every function cites the passage of the paper it follows:
 * :func:`setbwte` -- Algorithm 1 over given block boundaries.
 * :func:`lf_invert`, :func:`lf_invert_sampled` -- recover the reads from B
   by LF steps.
+* :func:`count` -- occurrences of a pattern, by direct comparison.
 * :func:`row_of_suffix`, :func:`bwt_symbol_of_suffix` -- one suffix's row and
   B symbol, for sampled checks at large sizes.
 
@@ -92,6 +93,8 @@ def _declare(lib):
     lib.oracle_lf_invert.restype = I
     lib.oracle_lf_invert_sampled.argtypes = [P, U64, U64, P, I, P, U64, P]
     lib.oracle_lf_invert_sampled.restype = I
+    lib.oracle_count.argtypes = [P, P, U64, P, U64]
+    lib.oracle_count.restype = U64
     lib.oracle_row_of_suffix.argtypes = [P, P, U64, U64, U64]
     lib.oracle_row_of_suffix.restype = U64
     lib.oracle_bwt_symbol_of_suffix.argtypes = [P, P, U64, U64]
@@ -240,6 +243,12 @@ def lf_invert_sampled(B, m: int, alphabet: bytes = b"ACGT"):
     _check(_load().oracle_lf_invert_sampled(_ptr(B), len(B), m, _ptr(alpha), len(alpha), _ptr(reads), len(reads),
                                             _ptr(offsets)), "oracle_lf_invert_sampled")
     return reads[: int(offsets[-1])], offsets
+
+
+def count(reads, offsets, pattern: bytes) -> int:
+    """Occurrences of `pattern` in the reads, overlapping ones included."""
+    reads, offsets, pat = _u8(reads), _u64(offsets), _u8(pattern)
+    return int(_load().oracle_count(_ptr(reads), _ptr(offsets), len(offsets) - 1, _ptr(pat), len(pat)))
 
 
 def row_of_suffix(reads, offsets, r: int, p: int) -> int:

@@ -32,6 +32,8 @@
  *   - oracle_lf_invert / oracle_lf_invert_sampled: recover every read from B
  *     by LF steps (the FM-index inversion that Lemma 1 rests on), with a full
  *     prefix-count table or with counts every 64 rows.
+ *   - oracle_count: occurrences of a pattern in the reads, by direct
+ *     comparison (what FM-index backward search counts).
  *   - oracle_row_of_suffix: row of one suffix in the full sorted order, by
  *     counting the smaller suffixes one comparison at a time (for sampled
  *     checks at sizes where sorting everything is too slow).
@@ -531,6 +533,22 @@ int oracle_lf_invert_sampled(const uint8_t *B, uint64_t n, uint64_t m, const uin
     free(code);
     free(tmp);
     return rc;
+}
+
+/* Occurrences of pattern P (bytes, no terminator) in the read set: every
+ * (read, offset) where P starts, overlapping occurrences included, found by
+ * direct comparison.  This is what FM-index backward search counts: the
+ * suffixes of T that start with P (a terminator never matches a symbol, so
+ * an occurrence never spans two reads). */
+uint64_t oracle_count(const uint8_t *reads, const uint64_t *offsets, uint64_t m, const uint8_t *P, uint64_t len) {
+    uint64_t cnt = 0;
+    for (uint64_t r = 0; r < m; ++r) {
+        const uint64_t L = offsets[r + 1] - offsets[r];
+        if (len > L) continue;
+        for (uint64_t p = 0; p + len <= L; ++p)
+            cnt += memcmp(reads + offsets[r] + p, P, len) == 0;
+    }
+    return cnt;
 }
 
 /* Row of suffix (r, p) in the sorted order of all suffixes of the set:

@@ -39,7 +39,7 @@ SBWT_STAGE_GSA = 3
 #: every symbol include/sbwt.h declares, in header order
 EXPORTS = (
     "sbwt_create", "sbwt_create_ex", "sbwt_append", "sbwt_append_device", "sbwt_get_bwt", "sbwt_rank",
-    "sbwt_rank_batch", "sbwt_memory", "sbwt_size", "sbwt_reset", "sbwt_destroy", "sbwt_strerror", "sbwt_get_stream",
+    "sbwt_rank_batch", "sbwt_count", "sbwt_memory", "sbwt_size", "sbwt_reset", "sbwt_destroy", "sbwt_strerror", "sbwt_get_stream",
     "sbwt_set_capture", "sbwt_get_stage", "sbwt_set_profiling", "sbwt_set_profiling_only", "sbwt_get_kernel_stats",
     "sbwt_reset_kernel_stats", "sbwt_set_graph_replay", "sbwt_autotune_block_suffixes", "sbwt_serve_start",
     "sbwt_submit", "sbwt_wait", "sbwt_serve_stop", "sbwt_bwt_noalloc",
@@ -95,6 +95,7 @@ def load() -> ctypes.CDLL:
             "sbwt_get_bwt": ([P, P, U64, ctypes.POINTER(U64)], I),
             "sbwt_rank": ([P, ctypes.c_uint8, U64, ctypes.POINTER(U64)], I),
             "sbwt_rank_batch": ([P, P, P, U64, P], I),
+            "sbwt_count": ([P, P, P, U64, P], I),
             "sbwt_size": ([P, ctypes.POINTER(U64), ctypes.POINTER(U64)], I),
             "sbwt_memory": ([P, ctypes.POINTER(U64), ctypes.POINTER(U64)], I),
             "sbwt_reset": ([P], I),
@@ -203,6 +204,18 @@ def sbwt_rank_batch(h, cs, ks) -> np.ndarray:
     _check(load().sbwt_rank_batch(h, ctypes.c_void_p(cs.ctypes.data), ctypes.c_void_p(ks.ctypes.data), len(ks),
                                   ctypes.c_void_p(out.ctypes.data)), "sbwt_rank_batch")
     return out[: len(ks)]
+
+
+def sbwt_count(h, patterns) -> np.ndarray:
+    """Occurrences of each pattern (a list of bytes) in the indexed reads."""
+    data = b"".join(patterns)
+    offs = np.zeros(len(patterns) + 1, dtype=np.uint64)
+    np.cumsum([len(p) for p in patterns], out=offs[1:])
+    buf = np.frombuffer(data, dtype=np.uint8).copy() if data else np.zeros(1, np.uint8)
+    out = np.zeros(max(len(patterns), 1), dtype=np.uint64)
+    _check(load().sbwt_count(h, ctypes.c_void_p(buf.ctypes.data), ctypes.c_void_p(offs.ctypes.data),
+                             len(patterns), ctypes.c_void_p(out.ctypes.data)), "sbwt_count")
+    return out[: len(patterns)]
 
 
 def sbwt_reset(h):
@@ -342,6 +355,9 @@ class SetBWT:
 
     def rank_batch(self, cs, ks) -> np.ndarray:
         return sbwt_rank_batch(self._h, cs, ks)
+
+    def count(self, patterns) -> np.ndarray:
+        return sbwt_count(self._h, patterns)
 
     def size(self):
         return sbwt_size(self._h)

@@ -68,7 +68,7 @@ struct sbwt_index {
     DevBuf reads, offsets, text, term, err;
     DevBuf keys, keys_alt, vals, vals_alt, sa, rank, act_pos0, act_pos1, act_suf0, act_suf1;
     DevBuf radix_temp, chunks, count_log, g, gsa, bint, sb_tot;
-    DevBuf out_bytes, q_codes, q_ks, q_out;
+    DevBuf out_bytes, q_codes, q_ks, q_out, c_pats, c_offs;
 
     uint32_t* h_err = nullptr;      // pinned
     uint64_t* h_offsets = nullptr;  // pinned staging for device-side offsets (fallback planning)
@@ -99,7 +99,7 @@ struct sbwt_index {
                                   &keys_alt,   &vals,     &vals_alt,  &sa,       &rank,     &act_pos0,
                                   &act_pos1,   &act_suf0, &act_suf1,  &radix_temp, &chunks,
                                   &count_log,  &g,        &gsa,       &bint,     &sb_tot,   &out_bytes,
-                                  &q_codes,    &q_ks,     &q_out,     &plan};
+                                  &q_codes,    &q_ks,     &q_out,     &plan,     &c_pats,   &c_offs};
         for (auto& d : dict) {
             v.push_back(&d.blocks);
             v.push_back(&d.super);
@@ -832,6 +832,34 @@ int sbwt_rank_batch(sbwt_index* idx, const uint8_t* cs, const uint64_t* ks, uint
                       (const uint8_t*)idx->q_codes.p, (const unsigned long long*)idx->q_ks.p, q,
                       (unsigned long long*)idx->q_out.p);
     cudaMemcpyAsync(out, idx->q_out.p, q * 8, cudaMemcpyDeviceToHost, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) return SBWT_EDEVICE;
+    return SBWT_OK;
+}
+
+int sbwt_count(sbwt_index* idx, const uint8_t* patterns, const uint64_t* offsets, uint64_t q, uint64_t* counts) {
+    if (!idx || (q && (!offsets || !counts))) return SBWT_EINVAL;
+    if (busy(idx)) return SBWT_EBUSY;
+    if (q == 0) return SBWT_OK;
+    if (offsets[0] != 0) return SBWT_EINVAL;
+    for (uint64_t i = 0; i < q; ++i)
+        if (offsets[i + 1] < offsets[i]) return SBWT_EINVAL;
+    const uint64_t total = offsets[q];
+    if (total && !patterns) return SBWT_EINVAL;
+    if (int rc = device_init(idx)) return rc;
+    if (reserve(idx, {{&idx->c_pats, (size_t)total + 1}, {&idx->c_offs, (size_t)(q + 1) * 8},
+                      {&idx->q_out, (size_t)q * 8}}) != SBWT_OK) {
+        if (!idx->host_tier_allowed || grow(idx->c_pats, total + 1, true) || grow(idx->c_offs, (q + 1) * 8, true) ||
+            grow(idx->q_out, q * 8, true))
+            return SBWT_ENOMEM;
+    }
+    cudaStream_t s = idx->stream;
+    if (total) cudaMemcpyAsync(idx->c_pats.p, patterns, total, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(idx->c_offs.p, offsets, (q + 1) * 8, cudaMemcpyHostToDevice, s);
+    const Dict& d = idx->dict[idx->cur];
+    launch_count(idx->L, (const OccBlock*)d.blocks.p, (const unsigned long long*)d.super.p,
+                 (const unsigned long long*)d.C.p, idx->n, idx->alpha4, idx->sigma, (const uint8_t*)idx->c_pats.p,
+                 (const uint64_t*)idx->c_offs.p, q, total, (unsigned long long*)idx->q_out.p);
+    cudaMemcpyAsync(counts, idx->q_out.p, q * 8, cudaMemcpyDeviceToHost, s);
     if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) return SBWT_EDEVICE;
     return SBWT_OK;
 }

@@ -112,6 +112,36 @@ __global__ void __launch_bounds__(kThreads) rank_batch_kernel(const OccBlock* __
     }
 }
 
+// FM-index backward search (Lemma 1 applied to a pattern instead of a new
+// read): the rows of the suffixes that start with P[k..] are [lo, hi); one
+// step per symbol, right to left, from [0, n).  hi - lo counts P.
+__global__ void __launch_bounds__(kThreads) count_kernel(const OccBlock* __restrict__ blocks,
+                                                         const unsigned long long* __restrict__ super,
+                                                         const unsigned long long* __restrict__ d_C,
+                                                         unsigned long long n, uint32_t alpha4, int sigma,
+                                                         const uint8_t* __restrict__ pats,
+                                                         const unsigned long long* __restrict__ offs,
+                                                         unsigned long long q, unsigned long long* __restrict__ out) {
+    const uint64_t i = (uint64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (i >= q) return;
+    const unsigned long long C0 = d_C[0], C1 = d_C[1], C2 = d_C[2], C3 = d_C[3];
+    unsigned long long lo = 0, hi = n;
+    for (uint64_t k = offs[i + 1]; k > offs[i] && lo < hi; --k) {
+        const uint32_t b = pats[k - 1];
+        uint32_t c = 4;
+        for (int a = 0; a < sigma; ++a)
+            if (b == ((alpha4 >> (8 * a)) & 0xFFu)) c = (uint32_t)a;
+        if (c == 4) {  // not in the alphabet: no occurrence
+            lo = hi = 0;
+            break;
+        }
+        const unsigned long long Cc = c == 0 ? C0 : c == 1 ? C1 : c == 2 ? C2 : C3;
+        lo = Cc + occ_rank(blocks, super, c, lo);
+        hi = Cc + occ_rank(blocks, super, c, hi);
+    }
+    out[i] = hi > lo ? hi - lo : 0ull;
+}
+
 __global__ void __launch_bounds__(kThreads) unpack_kernel(const OccBlock* __restrict__ blocks,
                                                           unsigned long long n, uint32_t alpha4,
                                                           uint8_t* __restrict__ out) {
@@ -174,6 +204,15 @@ void launch_rank_batch(Launcher& L, const OccBlock* blocks, const unsigned long 
     if (q == 0) return;
     SBWT_LAUNCH(L, "rank_query", (double)q * (1 + 8 + 32 + 8 + 8), 0, nullptr, rank_batch_kernel,
                 ceil_div_u(q, kThreads), kThreads, 0, blocks, super, codes, ks, (unsigned long long)q, out);
+}
+
+void launch_count(Launcher& L, const OccBlock* blocks, const unsigned long long* super,
+                  const unsigned long long* d_C, uint64_t n, uint32_t alpha4, int sigma, const uint8_t* pats,
+                  const uint64_t* offs, uint64_t q, uint64_t total_len, unsigned long long* out) {
+    if (q == 0) return;
+    SBWT_LAUNCH(L, "count_query", (double)total_len * (1 + 2 * 40) + 16.0 * q, 0, nullptr, count_kernel,
+                ceil_div_u(q, kThreads), kThreads, 0, blocks, super, d_C, (unsigned long long)n, alpha4, sigma, pats,
+                reinterpret_cast<const unsigned long long*>(offs), (unsigned long long)q, out);
 }
 
 void launch_unpack(Launcher& L, const OccBlock* blocks, uint64_t n, uint32_t alpha4, uint8_t* out) {

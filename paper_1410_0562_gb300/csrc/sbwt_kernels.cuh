@@ -52,6 +52,10 @@ void launch_bint_gather(Launcher& L, const uint32_t* text, const uint32_t* term,
 // rank queries: codes 0..3, or 4 for the terminator.
 void launch_rank_batch(Launcher& L, const OccBlock* blocks, const unsigned long long* super, const uint8_t* codes,
                        const unsigned long long* ks, uint64_t q, unsigned long long* out);
+// Backward-search counts of q patterns (pattern i = pats[offs[i] .. offs[i+1])).
+void launch_count(Launcher& L, const OccBlock* blocks, const unsigned long long* super,
+                  const unsigned long long* d_C, uint64_t n, uint32_t alpha4, int sigma, const uint8_t* pats,
+                  const uint64_t* offs, uint64_t q, uint64_t total_len, unsigned long long* out);
 // B as bytes: alphabet byte per code, '$' for a terminator row.
 void launch_unpack(Launcher& L, const OccBlock* blocks, uint64_t n, uint32_t alpha4, uint8_t* out);
 

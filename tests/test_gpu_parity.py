@@ -392,3 +392,20 @@ def test_host_tier_under_budget():
     with pytest.raises(sb.SbwtError) as e:
         forbidden.append(w.reads, w.offsets)
     assert e.value.code == sb.SBWT_ENOMEM
+
+
+def test_count_queries_match_oracle():
+    w = readgen.tiny()
+    idx = gpu_bwt(w.reads, w.offsets, M=20_000, cuts=w.appends)
+    rng = np.random.default_rng(21)
+    pats = [b"", b"A", b"ACGT", b"TTTT", b"N", b"ACN"]
+    for L in (1, 2, 3, 5, 8, 12, 20, 100, 101):
+        for _ in range(6):
+            r = int(rng.integers(0, w.m))
+            p0 = int(rng.integers(0, max(1, 101 - L)))
+            pats.append(bytes(w.reads[int(w.offsets[r]) + p0:int(w.offsets[r]) + p0 + L]))  # present
+            pats.append(bytes(rng.choice(np.frombuffer(b"ACGT", np.uint8), size=L)))        # random
+    got = idx.count(pats)
+    expect = [oracle.count(w.reads, w.offsets, p) if all(c in b"ACGT" for c in p) else 0 for p in pats]
+    assert list(got) == expect
+    assert got[0] == oracle.num_suffixes(w.offsets)

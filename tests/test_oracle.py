@@ -230,3 +230,15 @@ def test_rejects_bad_input():
 def test_empty_set():
     assert len(oracle.bwt(np.zeros(0, np.uint8), np.zeros(1, np.uint64))) == 0
     assert bytes(oracle.bwt(*pack([b"", b"", b""]))) == b"$$$"
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_count_is_overlapping_substring_count(seed):
+    rng = np.random.default_rng(900 + seed)
+    reads = random_set(rng, 30, 40, alphabet=b"AC")
+    data, off = pack(reads)
+    for L in (1, 2, 3, 5):
+        for _ in range(5):
+            pat = bytes(rng.choice(np.frombuffer(b"AC", np.uint8), size=L))
+            expect = sum(1 for r in reads for p in range(len(r) - L + 1) if r[p:p + L] == pat)
+            assert oracle.count(data, off, pat) == expect
