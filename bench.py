@@ -63,13 +63,30 @@ def dist_env():
     return rank, world, local
 
 
-def make_workload(name: str, rank: int):
+def make_workload(name: str, rank: int, n_reads: int = 1_000_000):
     if name == "tiny":
         w = readgen.tiny()
     else:
         # every rank indexes its own read set (same shape, its own seeds)
-        w = readgen.short(seed_genome=0x14100562 + 2 + 1000 * rank, seed_reads=0x05621410 + 2 + 1000 * rank)
+        w = readgen.short(n_reads=n_reads, seed_genome=0x14100562 + 2 + 1000 * rank,
+                          seed_reads=0x05621410 + 2 + 1000 * rank)
     return w
+
+
+def max_over_ranks(x: float, dist=None, device="cuda") -> float:
+    """The largest x over all ranks (the job takes as long as its slowest rank)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mbps(bases_per_rank: int, world: int, steps: int, total_ms: float) -> float:
+    """Weak scaling: every rank builds its own index of bases_per_rank bases per
+    step; the job's throughput is all ranks' bases over the slowest rank's time."""
+    return bases_per_rank * world * steps / (total_ms / 1e3) / 1e6
 
 
 def load_peaks():
@@ -323,11 +340,8 @@ def run_gb300(args):
     stats = [s for s in all_stats if not s["name"].startswith("host:")]
     host_phases = {s["name"][5:]: s["ms"] / args.steps for s in all_stats if s["name"].startswith("host:")}
     sb.sbwt_set_profiling(idx.handle, False)
-    total_ms = float(sum(ms_steps))
+    total_ms = max_over_ranks(float(sum(ms_steps)), dist)
     if dist:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
         dist.barrier()
 
     # the result is the one the oracle pins: spot-check it on this rank
@@ -363,12 +377,8 @@ def run_gb300(args):
             e2e_step()
             e_ev[k][1].record(stream)
         torch.cuda.synchronize()
-        e_ms = float(sum(a.elapsed_time(b) for a, b in e_ev))
-        if dist:
-            t = torch.tensor([e_ms], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e_ms = float(t.item())
-        e2e = {"value": bases * world * args.steps / (e_ms / 1e3) / 1e6, "unit": UNIT,
+        e_ms = max_over_ranks(float(sum(a.elapsed_time(b) for a, b in e_ev)), dist)
+        e2e = {"value": whole_job_mbps(bases, world, args.steps, e_ms), "unit": UNIT,
                "h2d_bytes_per_step": int(w.reads.nbytes + w.offsets.nbytes),
                "d2h_bytes_per_step": int(bases + w.m)}
 
@@ -401,16 +411,12 @@ def run_gb300(args):
             step_b()
             b_ev[k][1].record(stream)
         torch.cuda.synchronize()
-        b_ms = float(sum(a.elapsed_time(b) for a, b in b_ev))
-        if dist:
-            t = torch.tensor([b_ms], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            b_ms = float(t.item())
+        b_ms = max_over_ranks(float(sum(a.elapsed_time(b) for a, b in b_ev)), dist)
         b_stats = [s for s in sb.sbwt_get_kernel_stats(idx_b.handle) if not s["name"].startswith("host:")]
         b_dom = next((s for s in b_stats if s["name"] == dominant), None)
         Bb = idx_b.bwt()
         assert np.array_equal(Bb, B), "batched form differs from the plain pipeline"
-        batched = {"value": bases * world * args.steps / (b_ms / 1e3) / 1e6, "unit": UNIT,
+        batched = {"value": whole_job_mbps(bases, world, args.steps, b_ms), "unit": UNIT,
                    "ms_per_step": b_ms / args.steps, "block_suffixes": int(best_M), "graph_replay": True,
                    "autotune_ms": {str(k): round(v, 3) for k, v in tune.items()},
                    "gpu_launches": int(sum(s["launches"] for s in b_stats)),
@@ -436,7 +442,7 @@ def run_gb300(args):
             dist.destroy_process_group()
         return 0
 
-    value = bases * world * args.steps / (total_ms / 1e3) / 1e6
+    value = whole_job_mbps(bases, world, args.steps, total_ms)
     dom = next(s for s in stats if s["name"] == dominant)
     peak, peak_kind = load_peaks()
     achieved = dom["bytes"] / (dom["ms"] / 1e3) / 1e9 if dom["ms"] > 0 else 0.0
@@ -482,7 +488,7 @@ def run_serve_workload(args):
     """The serving workload: a resident index of 20M x 100 bp reads (2 Gbp)
     under an 8 GB HBM budget, then append requests of 10k..1M reads arriving
     all at once (sustained rate) and as Poisson streams at 0.5x and 0.9x of
-    it.  A second, smaller index under a 256 MB budget keeps its dictionaries
+    it.  A second, smaller index under a 512 MB budget keeps its dictionaries
     in the pinned host tier and serves the same way."""
     import torch
 
@@ -515,7 +521,7 @@ def run_serve_workload(args):
     # host tier: dictionaries in pinned host memory under a tight budget
     small = readgen.Workload("resident-2Mx100", resident.reads[: int(resident.offsets[2_000_000])],
                              resident.offsets[: 2_000_001], 1 << 21, 64, (0, 2_000_000))
-    idx2 = sb.SetBWT(b"ACGT", hbm_budget=256 << 20, index_bits=64, block_suffixes=1 << 21,
+    idx2 = sb.SetBWT(b"ACGT", hbm_budget=512 << 20, index_bits=64, block_suffixes=1 << 21,
                      stream=stream.cuda_stream, device=local)
     t = time.perf_counter()
     idx2.append(small.reads, small.offsets)
@@ -534,7 +540,7 @@ def run_serve_workload(args):
         "generation_s": gen_s, "index_rows_after": n, "index_reads_after": m,
         "memory_after_build": {"hbm": hbm, "host": host},
         "serving": report,
-        "host_tier": {"resident": small.name, "hbm_budget": 256 << 20, "build_s": build2_s,
+        "host_tier": {"resident": small.name, "hbm_budget": 512 << 20, "build_s": build2_s,
                       "memory": {"hbm": hbm2, "host": host2}, "serving": report2},
     }
     print(json.dumps(line), flush=True)
