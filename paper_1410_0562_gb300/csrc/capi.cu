@@ -66,7 +66,8 @@ struct sbwt_index {
     int cur = 0;
 
     DevBuf reads, offsets, text, term, err;
-    DevBuf keys, keys_alt, vals, vals_alt, sa, rank, act_pos0, act_pos1, act_suf0, act_suf1;
+    DevBuf keys, keys_alt, vals, vals_alt, sa, rank, act_pos0, act_pos1, act_suf0, act_suf1, loc_act, loc_next;
+    DevBuf units;
     DevBuf radix_temp, chunks, count_log, g, gsa, bint, sb_tot;
     DevBuf out_bytes, q_codes, q_ks, q_out, c_pats, c_offs;
 
@@ -97,7 +98,8 @@ struct sbwt_index {
     std::vector<DevBuf*> all_bufs() {
         std::vector<DevBuf*> v = {&reads,      &offsets,  &text,      &term,     &err,      &keys,
                                   &keys_alt,   &vals,     &vals_alt,  &sa,       &rank,     &act_pos0,
-                                  &act_pos1,   &act_suf0, &act_suf1,  &radix_temp, &chunks,
+                                  &act_pos1,   &act_suf0, &act_suf1,  &loc_act,  &loc_next, &units,
+                                  &radix_temp, &chunks,
                                   &count_log,  &g,        &gsa,       &bint,     &sb_tot,   &out_bytes,
                                   &q_codes,    &q_ks,     &q_out,     &plan,     &c_pats,   &c_offs};
         for (auto& d : dict) {
@@ -258,8 +260,9 @@ std::vector<Need> buffer_needs(sbwt_index* idx, const Plan& p, bool host_input, 
     v.push_back({&idx->term, (size_t)((p.npos + 31) / 32 + kTermPadWords) * 4});
     for (DevBuf* b : {&idx->keys, &idx->keys_alt}) v.push_back({b, (size_t)cap * 8});
     for (DevBuf* b : {&idx->vals, &idx->vals_alt, &idx->sa, &idx->rank, &idx->act_pos0, &idx->act_pos1,
-                      &idx->act_suf0, &idx->act_suf1})
+                      &idx->act_suf0, &idx->act_suf1, &idx->loc_act, &idx->loc_next})
         v.push_back({b, (size_t)cap * 4});
+    v.push_back({&idx->units, suffix_sort_unit_bytes(cap)});
     v.push_back({&idx->radix_temp, radix_temp_words(cap) * 4});
     v.push_back({&idx->chunks, suffix_sort_chunk_words(cap) * 8});
     v.push_back({&idx->count_log, p.slots * p.blocks.size() * 4});
@@ -369,6 +372,9 @@ void run_block(sbwt_index* idx, const BlockPlan& bp, const uint64_t* d_offsets, 
     b.act_pos[1] = (uint32_t*)idx->act_pos1.p;
     b.act_suf[0] = (uint32_t*)idx->act_suf0.p;
     b.act_suf[1] = (uint32_t*)idx->act_suf1.p;
+    b.loc_act = (uint32_t*)idx->loc_act.p;
+    b.loc_next = (uint32_t*)idx->loc_next.p;
+    b.units = idx->units.p;
     b.radix_temp = (uint32_t*)idx->radix_temp.p;
     b.chunks = (unsigned long long*)idx->chunks.p;
     b.count_log = (uint32_t*)idx->count_log.p + slots * k;

@@ -33,8 +33,10 @@ constexpr size_t kText = kOffsets + up256((kMax + 1) * 8);
 constexpr size_t kTerm = kText + up256(((kMax + 31) / 32 * 2 + kTextPadWords) * 4);
 constexpr size_t kKeys = kTerm + up256(((kMax + 31) / 32 + kTermPadWords) * 4);
 constexpr size_t kKeysAlt = kKeys + up256(kMax * 8);
-constexpr size_t kU32 = kKeysAlt + up256(kMax * 8);  // eight arrays of kMax uint32
-constexpr size_t kRadixTemp = kU32 + 8 * up256(kMax * 4);
+constexpr size_t kU32 = kKeysAlt + up256(kMax * 8);  // ten arrays of kMax uint32
+constexpr size_t kUnits = kU32 + 10 * up256(kMax * 4);
+constexpr size_t kUnitsBytes = 8192;  // suffix_sort_unit_bytes(kMax) must fit (checked at set-up)
+constexpr size_t kRadixTemp = kUnits + kUnitsBytes;
 constexpr size_t kRadixTempBytes = 256 * 1024;  // radix_temp_words(kMax) * 4 must fit (checked at set-up)
 constexpr size_t kChunks = kRadixTemp + kRadixTempBytes;
 constexpr size_t kChunksBytes = 16384;  // suffix_sort_chunk_words(kMax) * 8 must fit (checked at set-up)
@@ -72,7 +74,7 @@ int setup(int dev, DeviceState** out) {
             return SBWT_EDEVICE;
         }
         if (radix_temp_words(kMax) * 4 > kRadixTempBytes || suffix_sort_chunk_words(kMax) * 8 > kChunksBytes ||
-            suffix_sort_log_slots((uint32_t)kMax) * 4 > kCountLogBytes)
+            suffix_sort_log_slots((uint32_t)kMax) * 4 > kCountLogBytes || suffix_sort_unit_bytes(kMax) > kUnitsBytes)
             return SBWT_EDEVICE;
         suffix_sort_init();
         st.base = static_cast<unsigned char*>(p);
@@ -165,6 +167,9 @@ extern "C" int sbwt_bwt_noalloc(const char* alphabet, const uint8_t* reads, cons
     sb.act_pos[1] = u32 + 5 * stride;
     sb.act_suf[0] = u32 + 6 * stride;
     sb.act_suf[1] = u32 + 7 * stride;
+    sb.loc_act = u32 + 8 * stride;
+    sb.loc_next = u32 + 9 * stride;
+    sb.units = b + kUnits;
     sb.radix_temp = reinterpret_cast<uint32_t*>(b + kRadixTemp);
     sb.chunks = reinterpret_cast<unsigned long long*>(b + kChunks);
     sb.count_log = reinterpret_cast<uint32_t*>(b + kCountLog);

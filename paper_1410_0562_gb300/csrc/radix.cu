@@ -1,5 +1,5 @@
-// radix.cu -- stable LSD radix sort of (64-bit key, 32-bit value) pairs,
-// 8-bit digits, element count in device memory.  This is the sort under the
+// radix.cu -- stable LSD radix sort of (32- or 64-bit key, 32-bit value)
+// pairs, 8-bit digits, element count in device memory.  This is the sort under the
 // suffix sorting of a block (Section 3 of arXiv 1410.0562 sorts suffixes as
 // long integer keys of packed symbols, refined over iterations).
 //
@@ -29,34 +29,46 @@ static_assert(kBins == kThreads, "one thread per digit");
 
 // shared memory of the downsweep: TMA input tile, staged output tile, warp
 // counters, three digit tables, the mbarrier
-constexpr size_t kDownSmem =
-    2 * ((size_t)kTile * 8 + (size_t)kTile * 4) + (size_t)kWarps * kBins * 4 + (size_t)kBins * 4 * 3 + 16;
-static_assert(3 * (kDownSmem + 1024) <= 228 * 1024, "three CTAs per SM");
+template <class KeyT>
+constexpr size_t down_smem() {
+    return 2 * ((size_t)kTile * sizeof(KeyT) + (size_t)kTile * 4) + (size_t)kWarps * kBins * 4 +
+           (size_t)kBins * 4 * 3 + 16;
+}
+static_assert(3 * (down_smem<unsigned long long>() + 1024) <= 228 * 1024, "three CTAs per SM");
 
-// Temp layout (32-bit words): the digit totals of the current pass, then the
-// chunk x digit offsets.
+// Temp layout (32-bit words): two arrays of digit totals (pass p adds into
+// array p & 1; the chunk scan of pass p clears the other one for pass p + 1),
+// then the chunk x digit offsets.
 constexpr size_t kTotals = 0;
-constexpr size_t kChunkOffsets = kBins;
+constexpr size_t kChunkOffsets = 2 * kBins;
 
+// Chunk c of a grid of `grid` CTAs: tiles [t0, t1).  Only the first
+// ceil(ntiles / per) chunks hold tiles.
+__device__ __forceinline__ uint32_t tiles_per_chunk(uint32_t n, uint32_t grid, uint32_t& ntiles) {
+    ntiles = (uint32_t)(((uint64_t)n + kTile - 1) / kTile);
+    return (ntiles + grid - 1) / grid;
+}
 __device__ __forceinline__ void chunk_range(uint32_t n, uint32_t& t0, uint32_t& t1) {
-    const uint32_t ntiles = (uint32_t)(((uint64_t)n + kTile - 1) / kTile);
-    const uint32_t per = (ntiles + gridDim.x - 1) / gridDim.x;
+    uint32_t ntiles;
+    const uint32_t per = tiles_per_chunk(n, gridDim.x, ntiles);
     t0 = min(ntiles, blockIdx.x * per);
     t1 = min(ntiles, t0 + per);
 }
 
 // Digit counts of this CTA's chunk (per-warp sub-histograms in shared
 // memory), also added to the digit totals of the whole pass.
-__global__ void __launch_bounds__(kThreads) radix_upsweep_kernel(const unsigned long long* __restrict__ keys,
+template <class KeyT>
+__global__ void __launch_bounds__(kThreads) radix_upsweep_kernel(const KeyT* __restrict__ keys,
                                                                  const uint32_t* __restrict__ d_n, int shift,
                                                                  uint32_t* __restrict__ chunk_counts,
                                                                  uint32_t* __restrict__ totals) {
     __shared__ uint32_t h[kWarps * kBins];
-    for (int i = threadIdx.x; i < kWarps * kBins; i += kThreads) h[i] = 0;
-    __syncthreads();
     const uint32_t n = *d_n;
     uint32_t t0, t1;
     chunk_range(n, t0, t1);
+    if (t0 >= t1) return;  // a chunk without tiles: the scan skips it
+    for (int i = threadIdx.x; i < kWarps * kBins; i += kThreads) h[i] = 0;
+    __syncthreads();
     const uint64_t i_end = min((uint64_t)n, (uint64_t)t1 * kTile);
     uint32_t* my = h + (threadIdx.x >> 5) * kBins;
     for (uint64_t i = (uint64_t)t0 * kTile + threadIdx.x; i < i_end; i += kThreads)
@@ -77,15 +89,20 @@ constexpr int kScanThreads = 1024;
 constexpr int kScanGroups = kScanThreads / 32;
 
 __global__ void __launch_bounds__(kScanThreads) radix_chunk_scan_kernel(uint32_t* __restrict__ chunk_counts,
-                                                                        int nchunks,
-                                                                        const uint32_t* __restrict__ totals) {
+                                                                        int grid, const uint32_t* __restrict__ totals,
+                                                                        uint32_t* __restrict__ next_totals,
+                                                                        const uint32_t* __restrict__ d_n) {
     __shared__ uint32_t start[kBins];
     __shared__ uint32_t part[kScanGroups][33];
     const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
     const int d = blockIdx.x * 32 + lane;
+    uint32_t ntiles;
+    const uint32_t tpc = tiles_per_chunk(*d_n, (uint32_t)grid, ntiles);
+    const int nchunks = tpc ? (int)((ntiles + tpc - 1) / tpc) : 0;  // chunks that hold tiles
     uint32_t tot;
     const uint32_t ex = cta_exclusive_scan<SumOp, kScanThreads>(threadIdx.x < kBins ? totals[threadIdx.x] : 0u, tot);
     if (threadIdx.x < kBins) start[threadIdx.x] = ex;
+    if (blockIdx.x == 0 && threadIdx.x < kBins) next_totals[threadIdx.x] = 0;
     const int per = (nchunks + kScanGroups - 1) / kScanGroups;
     const int c0 = min(nchunks, g * per), c1 = min(nchunks, c0 + per);
     uint32_t sum = 0;
@@ -103,14 +120,15 @@ __global__ void __launch_bounds__(kScanThreads) radix_chunk_scan_kernel(uint32_t
     }
 }
 
+template <class KeyT>
 __global__ void __launch_bounds__(kThreads, 3) radix_downsweep_kernel(
-    const unsigned long long* __restrict__ kin, const uint32_t* __restrict__ vin, unsigned long long* __restrict__ kout,
+    const KeyT* __restrict__ kin, const uint32_t* __restrict__ vin, KeyT* __restrict__ kout,
     uint32_t* __restrict__ vout, const uint32_t* __restrict__ d_n, int shift,
     const uint32_t* __restrict__ chunk_offsets, uint32_t* __restrict__ d_err) {
     extern __shared__ __align__(128) unsigned char smem[];
-    unsigned long long* in_keys = reinterpret_cast<unsigned long long*>(smem);  // next tile, filled by TMA
+    KeyT* in_keys = reinterpret_cast<KeyT*>(smem);  // next tile, filled by TMA
     uint32_t* in_vals = reinterpret_cast<uint32_t*>(in_keys + kTile);
-    unsigned long long* skeys = reinterpret_cast<unsigned long long*>(in_vals + kTile);  // tile in digit order
+    KeyT* skeys = reinterpret_cast<KeyT*>(in_vals + kTile);  // tile in digit order
     uint32_t* svals = reinterpret_cast<uint32_t*>(skeys + kTile);
     uint32_t* wcnt = svals + kTile;            // [kWarps][kBins]
     uint32_t* dstart = wcnt + kWarps * kBins;  // tile-local start of each digit
@@ -121,6 +139,7 @@ __global__ void __launch_bounds__(kThreads, 3) radix_downsweep_kernel(
     const uint32_t n = *d_n;
     uint32_t t0, t1;
     chunk_range(n, t0, t1);
+    if (t0 >= t1) return;  // a chunk without tiles
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t lt = (1u << lane) - 1u;
     const int d = threadIdx.x;
@@ -132,8 +151,8 @@ __global__ void __launch_bounds__(kThreads, 3) radix_downsweep_kernel(
     // last one) is read with plain loads
     auto full = [&](uint32_t tile) { return (uint64_t)(tile + 1) * kTile <= n; };
     auto prefetch = [&](uint32_t tile) {
-        mbar_expect_tx(bar, kTile * 12u);
-        tma_bulk_load(in_keys, kin + (uint64_t)tile * kTile, kTile * 8u, bar);
+        mbar_expect_tx(bar, kTile * (uint32_t)(sizeof(KeyT) + 4));
+        tma_bulk_load(in_keys, kin + (uint64_t)tile * kTile, kTile * (uint32_t)sizeof(KeyT), bar);
         tma_bulk_load(in_vals, vin + (uint64_t)tile * kTile, kTile * 4u, bar);
     };
     uint32_t parity = 0;
@@ -161,12 +180,12 @@ __global__ void __launch_bounds__(kThreads, 3) radix_downsweep_kernel(
             mbar_wait(bar, parity ^ 1u, kMbarSpinLimit);
             return;
         }
-        unsigned long long k[kItems];
+        KeyT k[kItems];
         uint32_t v[kItems];
 #pragma unroll
         for (int it = 0; it < kItems; ++it) {
             const uint32_t i = warp * kWarpItems + it * 32 + lane;
-            k[it] = i < cnt ? in_keys[i] : 0ull;
+            k[it] = i < cnt ? in_keys[i] : KeyT(0);
             v[it] = i < cnt ? in_vals[i] : 0u;
         }
         __syncthreads();  // the input buffer is free: fetch the next tile
@@ -227,7 +246,7 @@ __global__ void __launch_bounds__(kThreads, 3) radix_downsweep_kernel(
         __syncthreads();
 
         for (uint32_t s = threadIdx.x; s < cnt; s += kThreads) {
-            const unsigned long long key = skeys[s];
+            const KeyT key = skeys[s];
             const uint32_t dd = (uint32_t)(key >> shift) & (kBins - 1);
             const uint32_t o = shift_out[dd] + s;
             if (o < n) {
@@ -242,7 +261,7 @@ __global__ void __launch_bounds__(kThreads, 3) radix_downsweep_kernel(
     }
 }
 
-unsigned g_down_ctas[64] = {0};
+unsigned g_down_ctas[2][64] = {{0}};  // [key is 64-bit][device]
 
 int current_device() {
     int dev = 0;
@@ -266,40 +285,60 @@ size_t radix_temp_words(uint64_t cap) {
     return kChunkOffsets + (size_t)chunks * kBins + 64;
 }
 
-void radix_init() {
-    cudaFuncSetAttribute(radix_downsweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDownSmem);
-    const int dev = current_device();
-    g_down_ctas[dev] = std::min<unsigned>(kMaxChunks, persistent_ctas((const void*)radix_downsweep_kernel, kThreads,
-                                                                      kDownSmem));
+namespace {
+
+template <class KeyT>
+void radix_init_key() {
+    const size_t smem = down_smem<KeyT>();
+    cudaFuncSetAttribute(radix_downsweep_kernel<KeyT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    g_down_ctas[sizeof(KeyT) == 8][current_device()] =
+        std::min<unsigned>(kMaxChunks, persistent_ctas((const void*)radix_downsweep_kernel<KeyT>, kThreads, smem));
 }
 
-bool radix_sort_pairs(Launcher& L, unsigned long long* keys, uint32_t* vals, unsigned long long* keys_alt,
-                      uint32_t* vals_alt, const uint32_t* d_n, uint64_t cap, int begin_bit, int end_bit,
-                      uint32_t* temp, uint32_t* d_err) {
+}  // namespace
+
+void radix_init() {
+    radix_init_key<uint32_t>();
+    radix_init_key<unsigned long long>();
+}
+
+template <class KeyT>
+bool radix_sort_pairs(Launcher& L, KeyT* keys, uint32_t* vals, KeyT* keys_alt, uint32_t* vals_alt,
+                      const uint32_t* d_n, uint64_t cap, int begin_bit, int end_bit, uint32_t* temp,
+                      uint32_t* d_err) {
     const int passes = radix_passes(begin_bit, end_bit);
     if (passes <= 0) return false;
     uint32_t* chunk = temp + kChunkOffsets;
-    uint32_t* totals = temp + kTotals;
     const int dev = current_device();
     const uint64_t tiles = cap / kTile + 1;
-    const unsigned grid = (unsigned)std::min<uint64_t>(std::max(1u, g_down_ctas[dev]), tiles);
+    const unsigned grid =
+        (unsigned)std::min<uint64_t>(std::max(1u, g_down_ctas[sizeof(KeyT) == 8][dev]), tiles);
+    const double kb = (double)sizeof(KeyT);
     bool alt = false;
     for (int p = 0; p < passes; ++p) {
-        const unsigned long long* kin = alt ? keys_alt : keys;
+        const KeyT* kin = alt ? keys_alt : keys;
         const uint32_t* vin = alt ? vals_alt : vals;
-        unsigned long long* ko = alt ? keys : keys_alt;
+        KeyT* ko = alt ? keys : keys_alt;
         uint32_t* vo = alt ? vals : vals_alt;
         const int shift = begin_bit + kRadixBits * p;
-        cudaMemsetAsync(totals, 0, kBins * 4, L.stream);
-        SBWT_LAUNCH(L, "radix_upsweep", 0, 8, d_n, radix_upsweep_kernel, grid, kThreads, 0, kin, d_n, shift, chunk,
-                    totals);
+        uint32_t* totals = temp + kTotals + (size_t)kBins * (p & 1);
+        uint32_t* next_totals = temp + kTotals + (size_t)kBins * ((p + 1) & 1);
+        if (p == 0) cudaMemsetAsync(totals, 0, kBins * 4, L.stream);
+        SBWT_LAUNCH(L, "radix_upsweep", 0, kb, d_n, radix_upsweep_kernel<KeyT>, grid, kThreads, 0, kin, d_n, shift,
+                    chunk, totals);
         SBWT_LAUNCH(L, "radix_chunk_scan", 12.0 * grid * kBins, 0, nullptr, radix_chunk_scan_kernel, kBins / 32,
-                    kScanThreads, 0, chunk, (int)grid, totals);
-        SBWT_LAUNCH(L, "radix_downsweep", 0, 24, d_n, radix_downsweep_kernel, grid, kThreads, kDownSmem, kin, vin, ko,
-                    vo, d_n, shift, chunk, d_err);
+                    kScanThreads, 0, chunk, (int)grid, totals, next_totals, d_n);
+        SBWT_LAUNCH(L, "radix_downsweep", 0, 2 * (kb + 4), d_n, radix_downsweep_kernel<KeyT>, grid, kThreads,
+                    down_smem<KeyT>(), kin, vin, ko, vo, d_n, shift, chunk, d_err);
         alt = !alt;
     }
     return alt;
 }
+
+template bool radix_sort_pairs<uint32_t>(Launcher&, uint32_t*, uint32_t*, uint32_t*, uint32_t*, const uint32_t*,
+                                         uint64_t, int, int, uint32_t*, uint32_t*);
+template bool radix_sort_pairs<unsigned long long>(Launcher&, unsigned long long*, uint32_t*, unsigned long long*,
+                                                   uint32_t*, const uint32_t*, uint64_t, int, int, uint32_t*,
+                                                   uint32_t*);
 
 }  // namespace sbwt

@@ -105,6 +105,12 @@ struct MaxOp {  // identity 0: every scanned value is unsigned
     template <class T>
     __device__ __forceinline__ static T f(T a, T b) { return a > b ? a : b; }
 };
+struct MinOp {  // identity: all bits set (unsigned values)
+    template <class T>
+    __device__ __forceinline__ static T id() { return ~T(0); }
+    template <class T>
+    __device__ __forceinline__ static T f(T a, T b) { return a < b ? a : b; }
+};
 
 // Exclusive scan of one value per thread over a CTA of NT threads (NT a
 // multiple of 32, at most 1024).  Every thread must call it.  Returns the
@@ -267,13 +273,16 @@ inline int radix_passes(int begin_bit, int end_bit) { return (end_bit - begin_bi
 size_t radix_temp_words(uint64_t cap);
 void radix_init();  // once per device, before the first sort
 
-// Stable LSD radix sort of (*d_n) 64-bit keys with 32-bit values on bits
-// [begin_bit, end_bit); key bits at and above end_bit must be zero.  Sorts
+// Stable LSD radix sort of (*d_n) keys (KeyT: uint32_t or unsigned long
+// long) with 32-bit values on bits [begin_bit, end_bit); key bits outside
+// that range are carried along but do not take part in the order.  Sorts
 // between (keys, vals) and (keys_alt, vals_alt); returns true when the
 // result ended in the *_alt buffers.  A scatter index out of range is skipped
-// and flagged in *d_err (bit 4).
-bool radix_sort_pairs(Launcher& L, unsigned long long* keys, uint32_t* vals, unsigned long long* keys_alt,
-                      uint32_t* vals_alt, const uint32_t* d_n, uint64_t cap, int begin_bit, int end_bit,
-                      uint32_t* temp, uint32_t* d_err);
+// and flagged in *d_err (bit 4).  Every key and value array must start on a
+// 16-byte boundary (whole tiles arrive by TMA bulk copies).
+template <class KeyT>
+bool radix_sort_pairs(Launcher& L, KeyT* keys, uint32_t* vals, KeyT* keys_alt, uint32_t* vals_alt,
+                      const uint32_t* d_n, uint64_t cap, int begin_bit, int end_bit, uint32_t* temp,
+                      uint32_t* d_err);
 
 }  // namespace sbwt

@@ -17,16 +17,19 @@ struct SuffixSortBuffers {
     unsigned long long *keys, *keys_alt;  // n each
     uint32_t *vals, *vals_alt;            // n each
     uint32_t *sa, *rank;                  // n each
-    uint32_t *act_pos[2], *act_suf[2];    // n each
+    uint32_t *act_pos[2], *act_suf[2];    // n each: unsorted members of the device-wide path
+    uint32_t *loc_act, *loc_next;         // n each: unsorted members of the CTA-local units, their next ranks
+    void* units;                          // suffix_sort_unit_bytes(n): one record per window of rows
     uint32_t* radix_temp;                 // radix_temp_words(n)
     unsigned long long* chunks;           // suffix_sort_chunk_words(n): per-chunk (max, count) pairs
-    uint32_t* count_log;                  // suffix_sort_log_slots(max_len) words
+    uint32_t* count_log;                  // suffix_sort_log_slots(max_len) words, 8-byte aligned
     uint32_t* err;                        // error flags (bits 2..7)
 };
 void suffix_sort_init();  // once per device (includes radix_init)
 uint32_t suffix_sort_rounds(uint32_t max_len);
 size_t suffix_sort_log_slots(uint32_t max_len);
 size_t suffix_sort_chunk_words(uint64_t cap);
+size_t suffix_sort_unit_bytes(uint64_t cap);
 void suffix_sort_block(Launcher& L, const uint32_t* text, const uint32_t* term, uint64_t base, uint32_t n,
                        uint32_t max_len, const SuffixSortBuffers& b);
 

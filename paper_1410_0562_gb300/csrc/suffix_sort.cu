@@ -1,34 +1,53 @@
 // suffix_sort.cu -- ConstructSA of one block (Algorithm 1; Section 3 of
 // arXiv 1410.0562 asks for any suffix sort and uses an MSD radix sort over
-// packed symbols that sieves out finished suffixes).  Here: prefix doubling
-// over the hand-written radix sort, with the sieve.
+// packed symbols that sieves out finished suffixes).  Here: an MSD bucket
+// split, CTA-local sorts of the buckets, then prefix doubling whose rounds are
+// again CTA-local wherever a group fits one CTA.
 //
 // Suffix order (Section 2): symbols compare by code; a suffix that reaches
 // its terminator first is smaller; two suffixes that reach their terminators
 // at the same offset compare by read index ($_j order), which inside a block
 // is the order of their text positions.
 //
-// 1. Initial key of the suffix at block position t: its first 29 codes,
-//    MSB first, with codes at and past its terminator zeroed, then
-//    min(len, 29) in the low 5 bits, len = distance to the terminator.
-//    Equal keys with len < 29 end at the same offset, so the stable sort
-//    (values = t in increasing order) already puts them in read order: each
-//    is a finished singleton.  Keys with len >= 29 that are equal form the
-//    unsorted groups.
-// 2. rank[t] = index of the first row of t's group (the Larsson-Sadakane
-//    convention), so ranks stay valid while groups split in later rounds.
-// 3. Round with offset h (29, 58, ...): only members of unsorted groups
-//    (the sieve) are re-sorted, by (rank[t], rank[t + h]); t + h never leaves
-//    the read because an unsorted member has len >= h.  Sorting them as one
-//    list by that composite key keeps groups in place, so the k-th sorted
-//    element goes to the k-th active row.  Rounds continue until the
-//    resolved prefix exceeds the longest read of the block.
-// At the end rank[] is the inverse suffix array of the block.
+// Key of the suffix at block position t: its first 29 codes, MSB first, with
+// codes at and past its terminator zeroed, then min(len, 29) in the low 5
+// bits, len = distance to the terminator.  Equal keys with len < 29 end at
+// the same offset, so ordered by t they are in read order: each is a
+// finished singleton.  Keys with len >= 29 that are equal form the unsorted
+// groups.  rank[t] is the row of the first member of t's group (the
+// Larsson-Sadakane convention), so ranks stay valid while groups split.
 //
-// After each sort the bookkeeping (group heads, the running max of head rows
-// = each element's group head, the unsorted flags and their running count =
-// the compaction offsets) is reduce-then-scan over chunks of tiles; it writes
-// SA, rank and the compacted list of unsorted members.
+// 1. Bucket split.  The bucket of a suffix is (p, l): p its first P codes
+//    (zeroed past the terminator), l = min(len, P).  Ordered by (p, l) the
+//    buckets are ordered like the keys, and the valid pairs are numbered
+//    densely (the digit below): P = 11 fits 24 bits.
+//    A stable LSD sort of (digit, t) on those bits partitions the block into
+//    buckets, each in t order; a bucket's rows are final.  A suffix with
+//    len < P (a "short" one) is alone in a bucket of equal keys: it is
+//    finished where it lands.
+// 2. Units.  The digit-sorted array is cut into windows of kWindow rows; unit
+//    w is every bucket that starts inside window w.  A unit holds whole
+//    buckets, so its rows are final as a set, and as long as its buckets are
+//    at most kWindow long it holds at most 2 kWindow = kLCap rows.
+// 3. Local sort.  One CTA per unit with at most kLCap long suffixes: it
+//    regenerates their keys from the packed text, sorts each bucket in
+//    shared memory by (key, t) (counting, for buckets of at most kSeg; a
+//    merge sort of the unit otherwise), and writes SA, rank and
+//    the unit's still-unsorted members (in row order, in place in the unit's
+//    own range of loc_act).  A unit with more long suffixes goes to the
+//    global path: its suffixes (with their rows) are gathered into one list
+//    that the device-wide radix sort orders by the full key.
+// 4. Round with offset h (29, 58, ...): each unsorted member t is re-sorted
+//    inside its group by rank[t + h]; t + h never leaves the read because an
+//    unsorted member has len >= h.  All next-ranks are read before any rank
+//    of the round is written (a separate gather launch).  Unit-local groups:
+//    one CTA sorts the unit's members by (rank[t], rank[t + h]); a
+//    group whose head row is H keeps rows H .. H + size - 1.  Groups from the
+//    global path: one device-wide radix sort of all of them by the same pair,
+//    as one list, so the k-th sorted element goes to the k-th active row.
+//    Rounds continue until the resolved prefix exceeds the longest read of
+//    the block.
+// At the end rank[] is the inverse suffix array of the block.
 #include <algorithm>
 
 #include "sbwt_internal.cuh"
@@ -41,8 +60,45 @@ constexpr int kThreads = 256;
 constexpr uint32_t kH0 = 29;
 constexpr int kGItems = 16;
 constexpr int kGTile = kThreads * kGItems;  // elements per group-kernel tile
-
 constexpr unsigned kMaxGroupChunks = 2048;
+
+// Local sorts: kLThreads x kLItems pairs per CTA.
+constexpr int kLThreads = 512;
+constexpr int kLItems = 8;
+constexpr uint32_t kLCap = kLThreads * kLItems;  // 4096 long suffixes per unit at most
+constexpr uint32_t kWindow = kLCap / 2;          // rows per window
+constexpr uint32_t kLSlots = kLCap + kLCap / kLItems;
+constexpr uint32_t kNone = 0xFFFFFFFFu;
+constexpr uint32_t kShortFlag = 0x80000000u;  // digit flag: the bucket holds suffixes with len < P
+constexpr int kScanThreads = 1024;
+// Buckets: the first kPc codes and min(len, kPc); their dense numbers need
+// kDigitBits bits (5,592,405 valid pairs for 11 codes).  Two long suffixes
+// share a bucket iff their keys agree above kBucketShift.
+constexpr uint32_t kPc = 11;
+constexpr int kDigitBits = 24;
+constexpr int kBucketShift = 5 + 58 - 2 * (int)kPc;
+
+// Unit table: one entry per window of kWindow rows of the digit-sorted
+// array, stored as one array per field so a scan over windows reads it with
+// vector loads.  Unit w is every bucket that starts inside window w.
+struct Units {
+    uint32_t* beg;    // first bucket start in the window (kNone: no unit starts here)
+    uint32_t* lcb;    // long suffixes in the window before beg
+    uint32_t* lct;    // long suffixes in the window
+    uint32_t* end;    // end of the unit (first row of the next unit)
+    uint32_t* nlong;  // long suffixes in the unit (during the scan: in the block before beg)
+    uint32_t* lofs;   // offset of the unit in the global-path list, kNone for a local unit
+    uint32_t* cnt;    // unsorted members of a local unit: loc_act[beg .. beg + cnt)
+    uint32_t* owner;  // the unit whose rows include the window's first row
+};
+constexpr int kUnitFields = 8;
+// words per field: every field starts on a 32-byte boundary
+inline uint64_t unit_stride(uint64_t cap) { return (cap / kWindow + 2 + 7) & ~7ull; }
+inline Units units_at(void* base, uint64_t cap) {
+    uint32_t* p = static_cast<uint32_t*>(base);
+    const uint64_t s = unit_stride(cap);
+    return Units{p, p + s, p + 2 * s, p + 3 * s, p + 4 * s, p + 5 * s, p + 6 * s, p + 7 * s};
+}
 
 __device__ __forceinline__ unsigned long long initial_key(const uint32_t* __restrict__ text,
                                                           const uint32_t* __restrict__ term, uint64_t P) {
@@ -62,16 +118,748 @@ __device__ __forceinline__ unsigned long long initial_key(const uint32_t* __rest
     return (k58 << 5) | len;
 }
 
-__global__ void __launch_bounds__(kThreads) sa_init_keys_kernel(const uint32_t* __restrict__ text,
-                                                                const uint32_t* __restrict__ term,
-                                                                unsigned long long base, uint32_t n,
-                                                                unsigned long long* __restrict__ keys,
-                                                                uint32_t* __restrict__ vals,
-                                                                uint32_t* __restrict__ d_n) {
+// Dense number of the bucket (p, l) of key K among all valid pairs in (p, l)
+// order, pc = P codes.  A pair is valid when the codes of p at and past l are
+// zero.  Pairs before (p, l): the p pairs (p' < p, l' = P); for each l' < P
+// the multiples of 4^(P - l') below p (short pairs with p' < p); and the
+// short pairs (p, l') with l' < l, i.e. those whose zero tail p has.  Bit 31
+// flags a short bucket.
+__device__ __forceinline__ uint32_t bucket_digit(unsigned long long K, uint32_t pc) {
+    const uint32_t l = min((uint32_t)(K & 31), pc);
+    const uint32_t p = (uint32_t)((K >> 5) >> (58 - 2 * pc));
+    const uint32_t zero_codes = p ? (uint32_t)(__ffs(p) - 1) >> 1 : pc;
+    uint32_t o = p;
+    for (uint32_t k = 1; k <= pc; ++k) o += (p + (1u << (2 * k)) - 1) >> (2 * k);
+    const uint32_t first_valid = pc > zero_codes ? pc - zero_codes : 0;
+    o += l > first_valid ? l - first_valid : 0;
+    return o | (l < pc ? kShortFlag : 0u);
+}
+
+__global__ void __launch_bounds__(kThreads) sa_digit_keys_kernel(const uint32_t* __restrict__ text,
+                                                                 const uint32_t* __restrict__ term,
+                                                                 unsigned long long base, uint32_t n, uint32_t pc,
+                                                                 uint32_t* __restrict__ digits,
+                                                                 uint32_t* __restrict__ vals,
+                                                                 uint32_t* __restrict__ d_n) {
     if (blockIdx.x == 0 && threadIdx.x == 0) *d_n = n;
     for (uint32_t t = blockIdx.x * kThreads + threadIdx.x; t < n; t += gridDim.x * kThreads) {
-        keys[t] = initial_key(text, term, base + t);
+        digits[t] = bucket_digit(initial_key(text, term, base + t), pc);
         vals[t] = t;
+    }
+}
+
+// One warp per window of the digit-sorted array: the first bucket start in
+// the window and the long-suffix counts before it and in the whole window.
+// Short suffixes are finished where they landed: SA and rank are written
+// here.  The k-th long row i of window w is listed as (ll_t, ll_row)[w
+// kWindow + k] = (t, i), so a unit's long rows are a few contiguous runs.
+__global__ void __launch_bounds__(kThreads) sa_unit_begin_kernel(const uint32_t* __restrict__ digits,
+                                                                 const uint32_t* __restrict__ vals, uint32_t n,
+                                                                 uint32_t nwin, Units u, uint32_t* __restrict__ sa,
+                                                                 uint32_t* __restrict__ rank,
+                                                                 uint32_t* __restrict__ ll_t,
+                                                                 uint32_t* __restrict__ ll_row,
+                                                                 uint32_t* __restrict__ d_err) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t warps = gridDim.x * (kThreads / 32);
+    for (uint32_t w = (blockIdx.x * kThreads + threadIdx.x) >> 5; w < nwin; w += warps) {
+        const uint32_t lo = w * kWindow, hi = min(n, lo + kWindow);
+        uint32_t first = kNone, lcb = 0, lct = 0;
+        for (uint32_t b = lo; b < hi; b += 32) {
+            const uint32_t i = b + lane;
+            const bool valid = i < hi;
+            const uint32_t d = valid ? digits[i] : 0u;
+            const uint32_t prev = (valid && i > 0) ? digits[i - 1] : d;
+            const uint32_t t = valid ? vals[i] : 0u;
+            const bool bnd = valid && (i == 0 || d != prev);
+            const bool lng = valid && !(d & kShortFlag);
+            const uint32_t bb = __ballot_sync(0xffffffffu, bnd), bl = __ballot_sync(0xffffffffu, lng);
+            if (valid && t >= n) atomicOr(d_err, 64u);
+            if (valid && !lng && t < n) {
+                sa[i] = t;
+                rank[t] = i;
+            }
+            if (lng) {
+                const uint32_t k = lo + lct + __popc(bl & ((1u << lane) - 1u));
+                ll_t[k] = t;
+                ll_row[k] = i;
+            }
+            if (first == kNone) {
+                if (bb) {
+                    const int fb = __ffs(bb) - 1;
+                    first = b + fb;
+                    lcb += __popc(bl & ((1u << fb) - 1u));
+                } else {
+                    lcb += __popc(bl);
+                }
+            }
+            lct += __popc(bl);
+        }
+        if (lane == 0) {
+            u.beg[w] = first;
+            u.lcb[w] = lcb;
+            u.lct[w] = lct;
+        }
+    }
+}
+
+// kScanPer consecutive windows of one field (vector accesses when whole)
+constexpr int kScanPer = 8;
+__device__ __forceinline__ void load_run(const uint32_t* p, uint32_t w0, uint32_t nwin, uint32_t fill,
+                                         uint32_t (&v)[kScanPer]) {
+    if (w0 + kScanPer <= nwin) {
+        const uint4 a = *reinterpret_cast<const uint4*>(p + w0), b = *reinterpret_cast<const uint4*>(p + w0 + 4);
+        v[0] = a.x, v[1] = a.y, v[2] = a.z, v[3] = a.w, v[4] = b.x, v[5] = b.y, v[6] = b.z, v[7] = b.w;
+    } else {
+#pragma unroll
+        for (int q = 0; q < kScanPer; ++q) v[q] = w0 + q < nwin ? p[w0 + q] : fill;
+    }
+}
+__device__ __forceinline__ void store_run(uint32_t* p, uint32_t w0, uint32_t nwin, const uint32_t (&v)[kScanPer]) {
+    if (w0 + kScanPer <= nwin) {
+        *reinterpret_cast<uint4*>(p + w0) = make_uint4(v[0], v[1], v[2], v[3]);
+        *reinterpret_cast<uint4*>(p + w0 + 4) = make_uint4(v[4], v[5], v[6], v[7]);
+    } else {
+#pragma unroll
+        for (int q = 0; q < kScanPer; ++q)
+            if (w0 + q < nwin) p[w0 + q] = v[q];
+    }
+}
+
+// One CTA over all windows, kScanPer consecutive windows per thread: unit
+// ends, long counts, owners, and the offsets of the units that take the
+// global path.  Also zeroes the per-round counts of local unsorted members
+// (zero_slots[k * zero_stride], k < nzero).
+constexpr uint32_t kScanSpan = kScanThreads * kScanPer;
+
+__global__ void __launch_bounds__(kScanThreads) sa_unit_scan_kernel(Units u, uint32_t nwin, uint32_t n,
+                                                                    uint32_t* __restrict__ d_large_n,
+                                                                    uint32_t* __restrict__ zero_slots, int nzero,
+                                                                    int zero_stride) {
+    __shared__ unsigned long long xch[kScanThreads];
+    if ((int)threadIdx.x < nzero) zero_slots[threadIdx.x * zero_stride] = 0;
+    // forward: long suffixes in the block before each unit start (kept in
+    // nlong until the backward pass), owner of each window's first row
+    uint32_t carry_sum = 0, carry_last = 0;  // carry_last: 1 + index of the last unit so far
+    for (uint32_t base = 0; base < nwin; base += kScanSpan) {
+        const uint32_t w0 = base + threadIdx.x * kScanPer;
+        uint32_t beg[kScanPer], lcb[kScanPer], lct[kScanPer], g[kScanPer], own[kScanPer];
+        load_run(u.beg, w0, nwin, kNone, beg);
+        load_run(u.lcb, w0, nwin, 0u, lcb);
+        load_run(u.lct, w0, nwin, 0u, lct);
+        uint32_t sum = 0, last = 0;
+#pragma unroll
+        for (int q = 0; q < kScanPer; ++q) {
+            sum += lct[q];
+            if (beg[q] != kNone) last = w0 + q + 1;
+        }
+        uint32_t tot, mtot;
+        uint32_t run = carry_sum + cta_exclusive_scan<SumOp, kScanThreads>(sum, tot);
+        uint32_t run_last = max(carry_last, cta_exclusive_scan<MaxOp, kScanThreads>(last, mtot));
+#pragma unroll
+        for (int q = 0; q < kScanPer; ++q) {
+            const uint32_t w = w0 + q;
+            const bool ne = beg[q] != kNone;
+            g[q] = ne ? run + lcb[q] : 0u;
+            own[q] = (ne && beg[q] == w * kWindow) ? w : run_last - 1;  // window 0 always starts a unit
+            run += lct[q];
+            if (ne) run_last = w + 1;
+        }
+        if (w0 < nwin) {
+            store_run(u.nlong, w0, nwin, g);
+            store_run(u.owner, w0, nwin, own);
+        }
+        carry_sum += tot;
+        carry_last = max(carry_last, mtot);
+    }
+    const uint32_t total_long = carry_sum;
+    __syncthreads();
+    // backward, chunks from the last: the next unit's (start, long prefix)
+    // gives each unit's end and long count.  The minimum over later threads
+    // is an exclusive scan in reversed thread order.
+    unsigned long long carry = ~0ull;
+    const uint32_t nchunks = (nwin + kScanSpan - 1) / kScanSpan;
+    for (uint32_t ci = nchunks; ci-- > 0;) {
+        const uint32_t w0 = ci * kScanSpan + threadIdx.x * kScanPer;
+        uint32_t beg[kScanPer], g[kScanPer], end[kScanPer], nl[kScanPer];
+        load_run(u.beg, w0, nwin, kNone, beg);
+        load_run(u.nlong, w0, nwin, 0u, g);
+        unsigned long long mine = ~0ull;
+#pragma unroll
+        for (int q = kScanPer - 1; q >= 0; --q)
+            if (beg[q] != kNone) mine = ((unsigned long long)beg[q] << 32) | g[q];
+        xch[threadIdx.x] = mine;
+        __syncthreads();
+        unsigned long long tot;
+        const unsigned long long rex =
+            cta_exclusive_scan<MinOp, kScanThreads>(xch[kScanThreads - 1 - threadIdx.x], tot);
+        __syncthreads();
+        xch[kScanThreads - 1 - threadIdx.x] = rex;  // min over the threads after that one
+        __syncthreads();
+        unsigned long long nx = min(carry, xch[threadIdx.x]);
+#pragma unroll
+        for (int q = kScanPer - 1; q >= 0; --q) {
+            end[q] = 0;
+            nl[q] = 0;
+            if (beg[q] != kNone) {
+                end[q] = nx == ~0ull ? n : (uint32_t)(nx >> 32);
+                nl[q] = (nx == ~0ull ? total_long : (uint32_t)nx) - g[q];
+                nx = ((unsigned long long)beg[q] << 32) | g[q];
+            }
+        }
+        if (w0 < nwin) {
+            store_run(u.end, w0, nwin, end);
+            store_run(u.nlong, w0, nwin, nl);
+        }
+        carry = min(carry, tot);
+        __syncthreads();
+    }
+    __syncthreads();
+    // forward: offsets of the global-path units
+    uint32_t lcarry = 0;
+    for (uint32_t base = 0; base < nwin; base += kScanSpan) {
+        const uint32_t w0 = base + threadIdx.x * kScanPer;
+        uint32_t beg[kScanPer], end[kScanPer], nl[kScanPer], lofs[kScanPer], zero[kScanPer], sum = 0;
+        load_run(u.beg, w0, nwin, kNone, beg);
+        load_run(u.end, w0, nwin, 0u, end);
+        load_run(u.nlong, w0, nwin, 0u, nl);
+#pragma unroll
+        for (int q = 0; q < kScanPer; ++q) {
+            const bool big = beg[q] != kNone && nl[q] > kLCap;
+            lofs[q] = big ? end[q] - beg[q] : 0u;  // size for now
+            sum += lofs[q];
+            zero[q] = 0;
+        }
+        uint32_t tot;
+        uint32_t run = lcarry + cta_exclusive_scan<SumOp, kScanThreads>(sum, tot);
+#pragma unroll
+        for (int q = 0; q < kScanPer; ++q) {
+            const uint32_t size = lofs[q];
+            lofs[q] = size ? run : kNone;
+            run += size;
+        }
+        if (w0 < nwin) {
+            store_run(u.lofs, w0, nwin, lofs);
+            store_run(u.cnt, w0, nwin, zero);
+        }
+        lcarry += tot;
+    }
+    if (threadIdx.x == 0) *d_large_n = lcarry;
+}
+
+// one spare slot per kLItems: blocked accesses (thread x, item j at
+// kLItems x + j) then fall into distinct banks
+__device__ __forceinline__ uint32_t skew(uint32_t i) { return i + i / kLItems; }
+
+// Stable merge sort of `count` <= kLCap (key, value) pairs held blocked in
+// registers: thread x holds items kLItems x .. kLItems x + kLItems - 1, and
+// every item at or past `count` holds key ~0 (larger than any real key).
+// First each thread sorts its items (odd-even transposition, swapping only
+// strictly larger keys), then runs of kLItems, 2 kLItems, ... are merged
+// pairwise: each thread finds where its kLItems outputs start on the merge
+// path (a binary search between the two runs, ties taken from the left run)
+// and merges them serially.  skey/sval are kLSlots-entry shared arrays,
+// indexed through skew() so blocked accesses do not collide in banks.
+__device__ __forceinline__ void block_merge_sort(unsigned long long (&k)[kLItems], uint32_t (&v)[kLItems],
+                                                 uint32_t count, unsigned long long* skey, uint32_t* sval) {
+#pragma unroll
+    for (int r = 0; r < kLItems; ++r) {
+#pragma unroll
+        for (int j = r & 1; j + 1 < kLItems; j += 2) {
+            const unsigned long long ka = k[j], kb = k[j + 1];
+            const uint32_t va = v[j], vb = v[j + 1];
+            const bool sw = ka > kb;
+            k[j] = sw ? kb : ka;
+            k[j + 1] = sw ? ka : kb;
+            v[j] = sw ? vb : va;
+            v[j + 1] = sw ? va : vb;
+        }
+    }
+    const uint32_t base = threadIdx.x * kLItems;
+    for (uint32_t w = kLItems; w < count; w <<= 1) {
+        __syncthreads();  // the previous pass's readers are done
+#pragma unroll
+        for (int j = 0; j < kLItems; ++j) {
+            skey[skew(base + j)] = k[j];
+            sval[skew(base + j)] = v[j];
+        }
+        __syncthreads();
+        const uint32_t a0 = base & ~(2 * w - 1);  // the pair of runs [a0, a0 + w), [a0 + w, a0 + 2w)
+        if (a0 >= count) continue;                // padding only: already in order
+        const uint32_t a1 = a0 + w, b0 = a1, b1 = a1 + w;
+        const uint32_t d = base - a0;  // this thread's first output within the pair
+        uint32_t lo = d > w ? d - w : 0, hi = d < w ? d : w;
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (skey[skew(a0 + mid)] <= skey[skew(b0 + d - 1 - mid)]) lo = mid + 1;
+            else hi = mid;
+        }
+        uint32_t ai = a0 + lo, bi = b0 + (d - lo);
+        unsigned long long ka = ai < a1 ? skey[skew(ai)] : 0ull;
+        unsigned long long kb = bi < b1 ? skey[skew(bi)] : 0ull;
+#pragma unroll
+        for (int j = 0; j < kLItems; ++j) {
+            const bool take_a = ai < a1 && (bi >= b1 || ka <= kb);
+            if (take_a) {
+                k[j] = ka;
+                v[j] = sval[skew(ai)];
+                ++ai;
+                ka = ai < a1 ? skey[skew(ai)] : 0ull;
+            } else {
+                k[j] = kb;
+                v[j] = sval[skew(bi)];
+                ++bi;
+                kb = bi < b1 ? skey[skew(bi)] : 0ull;
+            }
+        }
+    }
+    __syncthreads();
+}
+
+// Running head positions over a sorted CTA list: heads (bit j: item j of
+// this thread starts a group) -> for each item the index of its group's first
+// item, returned through `first` (the value for item 0; later items update it
+// as they meet heads).
+__device__ __forceinline__ uint32_t carry_in_head(uint32_t heads, uint32_t g0) {
+    const uint32_t last = heads ? g0 + 31 - __clz(heads) : 0u;
+    uint32_t tot;
+    return cta_exclusive_scan<MaxOp, kLThreads>(last, tot);
+}
+
+// Sort of `count` <= kLCap (key, value) pairs held blocked in registers
+// (as for block_merge_sort) when the list is cut into segments of equal
+// key >> shift, contiguous and in segment order, none longer than kSeg: an
+// item's place is its segment's first index plus the number of items of its
+// segment before it in (key, value) order (values are distinct, so the order
+// is total).  Returns false, with the registers untouched, when a segment is
+// longer than kSeg.  On success skey/sval hold the sorted list too.
+constexpr uint32_t kSeg = 64;
+
+__device__ __forceinline__ bool block_segment_sort(unsigned long long (&k)[kLItems], uint32_t (&v)[kLItems],
+                                                   uint32_t count, int shift, unsigned long long* skey,
+                                                   uint32_t* sval, uint32_t* sseg) {
+    const uint32_t g0 = threadIdx.x * kLItems;
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kLItems; ++j) {
+        skey[skew(g0 + j)] = k[j];
+        sval[skew(g0 + j)] = v[j];
+    }
+    __syncthreads();
+    // segment starts, then each segment's end stored at its start
+    const unsigned long long kprev = (g0 > 0 && g0 <= count) ? skey[skew(g0 - 1)] : 0ull;
+    uint32_t starts = 0;
+#pragma unroll
+    for (int j = 0; j < kLItems; ++j) {
+        const uint32_t g = g0 + j;
+        const unsigned long long pk = j ? k[j - 1] : kprev;
+        starts |= (uint32_t)(g < count && (g == 0 || (k[j] >> shift) != (pk >> shift))) << j;
+    }
+    bool next_start = true;
+    if (g0 + kLItems < count) next_start = (skey[skew(g0 + kLItems)] >> shift) != (k[kLItems - 1] >> shift);
+    uint32_t s0 = carry_in_head(starts, g0);
+    uint32_t first[kLItems];
+    bool big = false;
+#pragma unroll
+    for (int j = 0; j < kLItems; ++j) {
+        const uint32_t g = g0 + j;
+        if ((starts >> j) & 1u) s0 = g;
+        first[j] = s0;
+        const bool last = j + 1 < kLItems ? (((starts >> (j + 1)) & 1u) || g + 1 >= count) : next_start;
+        if (g < count && last) {
+            sseg[skew(s0)] = g + 1;
+            big |= g + 1 - s0 > kSeg;
+        }
+    }
+    if (__syncthreads_or(big)) return false;
+    uint32_t pos[kLItems];
+#pragma unroll
+    for (int j = 0; j < kLItems; ++j) {
+        const uint32_t g = g0 + j;
+        pos[j] = g;
+        if (g >= count) continue;
+        const uint32_t s1 = sseg[skew(first[j])];
+        uint32_t r = 0;
+        for (uint32_t x = first[j]; x < s1; ++x) {
+            const unsigned long long kx = skey[skew(x)];
+            r += (kx < k[j] || (kx == k[j] && sval[skew(x)] < v[j])) ? 1u : 0u;
+        }
+        pos[j] = first[j] + r;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kLItems; ++j) {
+        if (g0 + j < count) {
+            skey[skew(pos[j])] = k[j];
+            sval[skew(pos[j])] = v[j];
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kLItems; ++j) {
+        if (g0 + j < count) {
+            k[j] = skey[skew(g0 + j)];
+            v[j] = sval[skew(g0 + j)];
+        }
+    }
+    return true;
+}
+
+// Sorts the blocked items by (key, value) order of whole segments, as
+// above, else by a merge sort of the list; leaves the sorted keys in skey.
+__device__ __forceinline__ void block_sort(unsigned long long (&k)[kLItems], uint32_t (&v)[kLItems],
+                                           uint32_t count, int shift, unsigned long long* skey, uint32_t* sval,
+                                           uint32_t* sseg) {
+    if (block_segment_sort(k, v, count, shift, skey, sval, sseg)) {
+        __syncthreads();
+        return;
+    }
+    block_merge_sort(k, v, count, skey, sval);
+#pragma unroll
+    for (int j = 0; j < kLItems; ++j) skey[skew(threadIdx.x * kLItems + j)] = k[j];
+    __syncthreads();
+}
+
+// Batches: a CTA walks its share of the windows, taking each time the
+// longest run of windows [w, w + k) whose element counts (c, one window per
+// thread; a count above kLCap stops a batch) sum to at most kLCap.  Fills
+// b_pref[i] = elements before window w + i in the batch; returns k (0 when
+// the first window cannot join a batch) and the batch's element total.
+struct Batch {
+    uint32_t pref[kLThreads];  // elements before window w + i
+    uint32_t beg[kLThreads];   // the unit start of window w + i
+    uint32_t abase[kLThreads];  // unsorted members before the window's first slot
+    uint32_t acnt[kLThreads];   // unsorted members of the window's unit
+    uint32_t misc[4];
+};
+
+__device__ __forceinline__ uint32_t form_batch(Batch& b, uint32_t c, uint32_t beg, uint32_t& total) {
+    uint32_t tot;
+    const uint32_t ex = cta_exclusive_scan<SumOp, kLThreads>(c, tot);
+    const uint32_t incl = ex + c;
+    const uint32_t k = (uint32_t)__syncthreads_count(incl <= kLCap);
+    if (threadIdx.x < k) {
+        b.pref[threadIdx.x] = ex;
+        b.beg[threadIdx.x] = beg;
+        b.acnt[threadIdx.x] = 0;
+    }
+    if (k && threadIdx.x == k - 1) b.misc[0] = incl;
+    __syncthreads();
+    total = k ? b.misc[0] : 0u;
+    return k;
+}
+
+// The batch window of slot g: the last i < k with pref[i] <= g (windows
+// with no elements share the next one's prefix, so it is never empty).
+__device__ __forceinline__ uint32_t batch_window(const Batch& b, uint32_t k, uint32_t g) {
+    uint32_t lo = 0, hi = k - 1;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi + 1) >> 1;
+        if (b.pref[mid] <= g) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Writes the unsorted members (act bit j: item j of this thread) of every
+// unit in the batch to its range of loc_act, in sorted order, and sets the
+// units' counts.  Items stay inside their unit's slots when sorted.
+__device__ __forceinline__ void batch_write_unsorted(Batch& b, uint32_t k, uint32_t w, const uint32_t (&v)[kLItems],
+                                                     uint32_t act, uint32_t count, uint32_t* __restrict__ loc_act,
+                                                     uint32_t* __restrict__ unit_cnt, uint32_t* __restrict__ d_cnt) {
+    const uint32_t g0 = threadIdx.x * kLItems;
+    uint32_t atot;
+    uint32_t a = cta_exclusive_scan<SumOp, kLThreads>((uint32_t)__popc(act), atot);
+    uint32_t wi = g0 < count ? batch_window(b, k, g0) : 0u;
+    uint32_t ai = a;
+#pragma unroll
+    for (int j = 0; j < kLItems; ++j) {
+        const uint32_t g = g0 + j;
+        if (g >= count) break;
+        while (wi + 1 < k && b.pref[wi + 1] <= g) ++wi;
+        if (g == b.pref[wi]) b.abase[wi] = ai;
+        if ((act >> j) & 1u) {
+            atomicAdd(&b.acnt[wi], 1u);
+            ++ai;
+        }
+    }
+    __syncthreads();
+    wi = g0 < count ? batch_window(b, k, g0) : 0u;
+    ai = a;
+#pragma unroll
+    for (int j = 0; j < kLItems; ++j) {
+        const uint32_t g = g0 + j;
+        if (g >= count) break;
+        while (wi + 1 < k && b.pref[wi + 1] <= g) ++wi;
+        if ((act >> j) & 1u) loc_act[b.beg[wi] + (ai - b.abase[wi])] = v[j];
+        ai += (act >> j) & 1u;
+    }
+    if (threadIdx.x < k) {
+        const uint32_t before = threadIdx.x + 1 < k ? b.pref[threadIdx.x + 1] : count;
+        if (before > b.pref[threadIdx.x]) unit_cnt[w + threadIdx.x] = b.acnt[threadIdx.x];
+    }
+    if (threadIdx.x == 0 && atot) atomicAdd(d_cnt, atot);
+    __syncthreads();
+}
+
+// Local sort of the units with at most kLCap long suffixes, a batch of
+// consecutive units per CTA step.  A batch's long rows are the runs
+// (ll_t, ll_row)[x kWindow + k0 ...) of the windows x = ws, ws + 1, ... from
+// its first unit start ws (k0 = lcb in window ws, 0 after), in row order;
+// the sorted j-th long suffix takes the j-th of those rows, srow[j].  A
+// global-path unit ends a batch and is skipped.
+__global__ void __launch_bounds__(kLThreads) sa_local_sort_kernel(
+    const uint32_t* __restrict__ text, const uint32_t* __restrict__ term, unsigned long long base, uint32_t n,
+    const uint32_t* __restrict__ ll_t, const uint32_t* __restrict__ ll_row, Units u, uint32_t nwin,
+    uint32_t* __restrict__ sa, uint32_t* __restrict__ rank, uint32_t* __restrict__ loc_act,
+    uint32_t* __restrict__ d_cnt, uint32_t* __restrict__ d_err) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    unsigned long long* skey = reinterpret_cast<unsigned long long*>(smem);
+    uint32_t* sval = reinterpret_cast<uint32_t*>(skey + kLSlots);
+    uint32_t* srow = sval + kLSlots;
+    uint32_t* sseg = srow + kLSlots;
+    __shared__ Batch b;
+    __shared__ uint32_t run_start[kLThreads], run_src[kLThreads];
+
+    const uint32_t per = (nwin + gridDim.x - 1) / gridDim.x;
+    const uint32_t wbeg = min(nwin, blockIdx.x * per), wend = min(nwin, wbeg + per);
+    for (uint32_t w = wbeg; w < wend;) {
+        const uint32_t x = w + threadIdx.x;
+        uint32_t c = kLCap + 1, ub = kNone;
+        if (x < wend) {
+            ub = u.beg[x];
+            c = ub == kNone ? 0u : (u.lofs[x] != kNone ? kLCap + 1 : u.nlong[x]);
+        }
+        uint32_t total;
+        const uint32_t k = form_batch(b, c, ub, total);
+        if (k == 0) {
+            ++w;
+            continue;
+        }
+        if (total == 0) {
+            w += k;
+            continue;
+        }
+        // the batch's first unit start
+        if (threadIdx.x == 0) b.misc[1] = kNone;
+        __syncthreads();
+        if (threadIdx.x < k && ub != kNone) atomicMin(&b.misc[1], x);
+        __syncthreads();
+        const uint32_t ws = b.misc[1];
+        // copy the long rows (with their keys), kLThreads windows at a time
+        uint32_t cc = 0;
+        for (uint32_t x0 = ws; cc < total && x0 < nwin; x0 += kLThreads) {
+            const uint32_t xx = x0 + threadIdx.x;
+            const uint32_t k0 = xx == ws ? u.lcb[ws] : 0u;
+            const uint32_t avail = xx < nwin ? u.lct[xx] - k0 : 0u;
+            uint32_t tot;
+            const uint32_t ex = cta_exclusive_scan<SumOp, kLThreads>(avail, tot);
+            const uint32_t take = min(tot, total - cc);
+            run_start[threadIdx.x] = cc + ex;
+            run_src[threadIdx.x] = xx * kWindow + k0;
+            const uint32_t nruns = (uint32_t)__syncthreads_count(ex < take);
+            for (uint32_t q = threadIdx.x; q < take; q += kLThreads) {
+                uint32_t lo = 0, hi = nruns - 1;  // the last run starting at or before slot cc + q
+                while (lo < hi) {
+                    const uint32_t mid = (lo + hi + 1) >> 1;
+                    if (run_start[mid] <= cc + q) lo = mid;
+                    else hi = mid - 1;
+                }
+                const uint32_t src = run_src[lo] + (cc + q - run_start[lo]);
+                const uint32_t t = ll_t[src];
+                if (t >= n) atomicOr(d_err, 64u);  // an out-of-range t is skipped when written back
+                skey[skew(cc + q)] = initial_key(text, term, base + (t < n ? t : 0u));
+                sval[skew(cc + q)] = t;
+                srow[skew(cc + q)] = ll_row[src];
+            }
+            cc += take;
+            __syncthreads();
+        }
+        const uint32_t cnt = cc;
+        const uint32_t g0 = threadIdx.x * kLItems;
+        unsigned long long kk[kLItems];
+        uint32_t v[kLItems];
+#pragma unroll
+        for (int j = 0; j < kLItems; ++j) {
+            const uint32_t g = g0 + j;
+            kk[j] = g < cnt ? skey[skew(g)] : ~0ull;
+            v[j] = g < cnt ? sval[skew(g)] : 0u;
+        }
+        block_sort(kk, v, cnt, kBucketShift, skey, sval, sseg);  // segments: buckets
+
+        // group heads: a new key, or a key that contains its terminator
+        const unsigned long long kprev = (g0 > 0 && g0 <= cnt) ? skey[skew(g0 - 1)] : 0ull;
+        uint32_t heads = 0;
+#pragma unroll
+        for (int j = 0; j < kLItems; ++j) {
+            const uint32_t g = g0 + j;
+            const unsigned long long pk = j ? kk[j - 1] : kprev;
+            const bool h = g < cnt && (g == 0 || kk[j] != pk || (uint32_t)(kk[j] & 31) < kH0);
+            heads |= (uint32_t)h << j;
+        }
+        bool next_head = true;
+        if (g0 + kLItems < cnt) {
+            const unsigned long long kn = skey[skew(g0 + kLItems)];
+            next_head = kn != kk[kLItems - 1] || (uint32_t)(kn & 31) < kH0;
+        }
+        uint32_t first = carry_in_head(heads, g0);
+        uint32_t act = 0;
+#pragma unroll
+        for (int j = 0; j < kLItems; ++j) {
+            const uint32_t g = g0 + j;
+            if (g >= cnt) break;
+            const bool h = (heads >> j) & 1u;
+            if (h) first = g;
+            const bool e = j + 1 < kLItems ? (((heads >> (j + 1)) & 1u) || g + 1 >= cnt) : next_head;
+            const uint32_t row = srow[skew(g)];
+            if (row < n && v[j] < n) {
+                sa[row] = v[j];
+                rank[v[j]] = srow[skew(first)];
+            }
+            if (!(h && e)) act |= 1u << j;
+        }
+        batch_write_unsorted(b, k, w, v, act, cnt, loc_act, u.cnt, d_cnt);
+        w += k;
+    }
+}
+
+// The global-path list: every row of a unit with more than kLCap long
+// suffixes, in row order, as (key, t, row).  One CTA per window; a window's
+// rows belong to its owner unit up to the window's own unit start.
+__global__ void __launch_bounds__(kThreads) sa_large_gather_kernel(
+    const uint32_t* __restrict__ text, const uint32_t* __restrict__ term, unsigned long long base, uint32_t n,
+    const uint32_t* __restrict__ vals, Units u, uint32_t nwin, unsigned long long* __restrict__ lkeys,
+    uint32_t* __restrict__ lvals, uint32_t* __restrict__ lpos) {
+    for (uint32_t w = blockIdx.x; w < nwin; w += gridDim.x) {
+        const uint32_t lo = w * kWindow, hi = min(n, lo + kWindow);
+        const uint32_t beg = u.beg[w];
+        const uint32_t split = beg == kNone ? hi : beg;
+#pragma unroll
+        for (int part = 0; part < 2; ++part) {
+            const uint32_t q = part == 0 ? u.owner[w] : w;
+            const uint32_t r0 = part == 0 ? lo : split, r1 = part == 0 ? split : hi;
+            if (r0 >= r1 || u.lofs[q] == kNone) continue;
+            const uint32_t lofs = u.lofs[q], qbeg = u.beg[q];
+            for (uint32_t i = r0 + threadIdx.x; i < r1; i += kThreads) {
+                const uint32_t t = vals[i];
+                const uint32_t o = lofs + (i - qbeg);
+                lkeys[o] = initial_key(text, term, base + (t < n ? t : 0u));
+                lvals[o] = t;
+                lpos[o] = i;
+            }
+        }
+    }
+}
+
+// next-ranks of the local unsorted members (one warp per unit), read before
+// any rank of the round changes
+__global__ void __launch_bounds__(kThreads) sa_round_gather_local_kernel(
+    const uint32_t* __restrict__ loc_act, Units u, uint32_t nwin, const uint32_t* __restrict__ rank, uint32_t h,
+    uint32_t n, uint32_t* __restrict__ loc_next, uint32_t* __restrict__ d_err) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t warps = gridDim.x * (kThreads / 32);
+    for (uint32_t w = (blockIdx.x * kThreads + threadIdx.x) >> 5; w < nwin; w += warps) {
+        const uint32_t beg = u.beg[w];
+        if (beg == kNone || u.lofs[w] != kNone) continue;
+        const uint32_t cnt = u.cnt[w];
+        for (uint32_t k = lane; k < cnt; k += 32) {
+            const uint32_t t = loc_act[beg + k];
+            uint32_t nx = 0;
+            if ((uint64_t)t + h < n) nx = rank[t + h];
+            else atomicOr(d_err, 128u);
+            loc_next[beg + k] = nx;
+        }
+    }
+}
+
+// One round for the local units, a batch of units per CTA step: sort the
+// unsorted members by (rank[t], rank[t + h]); a member of the group whose
+// head row is H that lands at offset x of its group takes row H + x.
+__global__ void __launch_bounds__(kLThreads) sa_round_local_kernel(
+    uint32_t* __restrict__ loc_act, const uint32_t* __restrict__ loc_next, Units u, uint32_t nwin, uint32_t n,
+    uint32_t* __restrict__ rank, uint32_t* __restrict__ sa, uint32_t* __restrict__ d_cnt,
+    uint32_t* __restrict__ d_err) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    unsigned long long* skey = reinterpret_cast<unsigned long long*>(smem);
+    uint32_t* sval = reinterpret_cast<uint32_t*>(skey + kLSlots);
+    uint32_t* sseg = sval + kLSlots;
+    __shared__ Batch b;
+
+    const uint32_t per = (nwin + gridDim.x - 1) / gridDim.x;
+    const uint32_t wbeg = min(nwin, blockIdx.x * per), wend = min(nwin, wbeg + per);
+    for (uint32_t w = wbeg; w < wend;) {
+        const uint32_t x = w + threadIdx.x;
+        uint32_t c = kLCap + 1, ub = kNone;
+        if (x < wend) {
+            ub = u.beg[x];
+            c = (ub != kNone && u.lofs[x] == kNone) ? min(u.cnt[x], kLCap) : 0u;
+        }
+        uint32_t total;
+        const uint32_t k = form_batch(b, c, ub, total);
+        if (k == 0) {
+            ++w;
+            continue;
+        }
+        if (total == 0) {
+            w += k;
+            continue;
+        }
+        // key (rank[t], rank[t + h]) of each slot, loaded blocked; a
+        // thread's loads are independent
+        const uint32_t g0 = threadIdx.x * kLItems;
+        unsigned long long kk[kLItems];
+        uint32_t v[kLItems];
+        uint32_t wi = g0 < total ? batch_window(b, k, g0) : 0u;
+#pragma unroll
+        for (int j = 0; j < kLItems; ++j) {
+            const uint32_t g = g0 + j;
+            kk[j] = ~0ull;
+            v[j] = 0;
+            if (g < total) {
+                while (wi + 1 < k && b.pref[wi + 1] <= g) ++wi;
+                const uint32_t src = b.beg[wi] + (g - b.pref[wi]);
+                const uint32_t t = loc_act[src];
+                const uint32_t here = t < n ? rank[t] : 0u;
+                v[j] = t;
+                kk[j] = ((unsigned long long)here << 32) | loc_next[src];
+            }
+        }
+        block_sort(kk, v, total, 32, skey, sval, sseg);  // segments: the old groups (equal rank[t])
+
+        const unsigned long long kprev = (g0 > 0 && g0 <= total) ? skey[skew(g0 - 1)] : 0ull;
+        uint32_t heads = 0, starts = 0;  // new groups; old groups (a new head row)
+#pragma unroll
+        for (int j = 0; j < kLItems; ++j) {
+            const uint32_t g = g0 + j;
+            const unsigned long long pk = j ? kk[j - 1] : kprev;
+            heads |= (uint32_t)(g < total && (g == 0 || kk[j] != pk)) << j;
+            starts |= (uint32_t)(g < total && (g == 0 || (kk[j] >> 32) != (pk >> 32))) << j;
+        }
+        bool next_head = true;
+        if (g0 + kLItems < total) next_head = skey[skew(g0 + kLItems)] != kk[kLItems - 1];
+        uint32_t hfirst = carry_in_head(heads, g0);
+        uint32_t ofirst = carry_in_head(starts, g0);
+        uint32_t act = 0;
+#pragma unroll
+        for (int j = 0; j < kLItems; ++j) {
+            const uint32_t g = g0 + j;
+            if (g >= total) break;
+            const bool h = (heads >> j) & 1u;
+            if (h) hfirst = g;
+            if ((starts >> j) & 1u) ofirst = g;
+            const bool e = j + 1 < kLItems ? (((heads >> (j + 1)) & 1u) || g + 1 >= total) : next_head;
+            const uint32_t here = (uint32_t)(kk[j] >> 32);
+            const uint32_t row = here + (g - ofirst);
+            if (row < n && v[j] < n) {
+                sa[row] = v[j];
+                rank[v[j]] = here + (hfirst - ofirst);
+            } else {
+                atomicOr(d_err, 64u);
+            }
+            if (!(h && e)) act |= 1u << j;
+        }
+        batch_write_unsorted(b, k, w, v, act, total, loc_act, u.cnt, d_cnt);
+        w += k;
     }
 }
 
@@ -99,14 +887,15 @@ __global__ void __launch_bounds__(kThreads) sa_round_keys_kernel(const uint32_t*
     }
 }
 
-// Group bookkeeping after a sort.  Element i of the sorted list (keys, vals)
-// sits on row pos(i) of the block SA: pos(i) = i after the initial sort,
-// act_pos[i] after a round.  It writes SA[pos] = t, rank[t] = row of t's
-// group head, and appends the members of groups with two or more elements to
-// (act_pos_out, act_suf_out).  Like the radix passes it is reduce-then-scan
-// over chunks of whole tiles: groups_reduce gives each chunk's last head row
-// and member count, groups_scan turns them into per-chunk prefixes (and the
-// total into *d_cnt_out), groups_apply walks each chunk with running values.
+// Group bookkeeping of the global path after a device-wide sort.  Element i
+// of the sorted list (keys, vals) sits on row act_pos_in[i] of the block SA.
+// It writes SA[pos] = t, rank[t] = row of t's group head, and appends the
+// members of groups with two or more elements to (act_pos_out, act_suf_out).
+// kInit: the list of the initial keys, where a key that contains its
+// terminator is a group of its own.  Reduce-then-scan over chunks of whole
+// tiles: groups_reduce gives each chunk's last head row and member count,
+// groups_scan turns them into per-chunk prefixes (and the total into
+// *d_cnt_out), groups_apply walks each chunk with running values.
 struct ElemInfo {
     unsigned long long k[kGItems];
     uint32_t pos[kGItems];
@@ -114,7 +903,7 @@ struct ElemInfo {
     uint32_t ends;   // bit q: element q is the last of its group
 };
 
-template <bool kRound>
+template <bool kInit>
 __device__ __forceinline__ void load_tile_info(const unsigned long long* __restrict__ keys,
                                                const uint32_t* __restrict__ act_pos_in, uint32_t n, uint32_t i0,
                                                ElemInfo& e) {
@@ -122,22 +911,21 @@ __device__ __forceinline__ void load_tile_info(const unsigned long long* __restr
     for (int q = 0; q < kGItems; ++q) {
         const uint32_t i = i0 + q;
         e.k[q] = i < n ? keys[i] : 0ull;
-        e.pos[q] = kRound ? (i < n ? act_pos_in[i] : 0u) : i;
+        e.pos[q] = i < n ? act_pos_in[i] : 0u;
     }
     const unsigned long long kprev = (i0 > 0 && i0 - 1 < n) ? keys[i0 - 1] : 0ull;
     // is the element after this thread's last one a group head?
     bool next_head = true;
     if ((uint64_t)i0 + kGItems < n) {
         const unsigned long long kn = keys[i0 + kGItems];
-        next_head = kn != e.k[kGItems - 1] || (!kRound && (uint32_t)(kn & 31) < kH0);
+        next_head = kn != e.k[kGItems - 1] || (kInit && (uint32_t)(kn & 31) < kH0);
     }
-    // head: a new key, or (initial sort) a key that contains its terminator
     e.heads = 0;
 #pragma unroll
     for (int q = 0; q < kGItems; ++q) {
         const uint32_t i = i0 + q;
         const unsigned long long prev = q == 0 ? kprev : e.k[q - 1];
-        const bool h = i < n && (i == 0 || e.k[q] != prev || (!kRound && (uint32_t)(e.k[q] & 31) < kH0));
+        const bool h = i < n && (i == 0 || e.k[q] != prev || (kInit && (uint32_t)(e.k[q] & 31) < kH0));
         e.heads |= (uint32_t)h << q;
     }
     e.ends = 0;
@@ -155,12 +943,12 @@ __device__ __forceinline__ void chunk_tiles(uint32_t ntiles, uint32_t& t0, uint3
     t1 = min(ntiles, t0 + per);
 }
 
-template <bool kRound>
+template <bool kInit>
 __global__ void __launch_bounds__(kThreads) sa_groups_reduce_kernel(const unsigned long long* __restrict__ keys,
                                                                     const uint32_t* __restrict__ act_pos_in,
                                                                     const uint32_t* __restrict__ d_cnt,
-                                                                    uint32_t n_block, uint2* __restrict__ chunk_agg) {
-    const uint32_t n = kRound ? *d_cnt : n_block;
+                                                                    uint2* __restrict__ chunk_agg) {
+    const uint32_t n = *d_cnt;
     const uint32_t ntiles = (uint32_t)(((uint64_t)n + kGTile - 1) / kGTile);
     uint32_t t0, t1;
     chunk_tiles(ntiles, t0, t1);
@@ -168,7 +956,7 @@ __global__ void __launch_bounds__(kThreads) sa_groups_reduce_kernel(const unsign
     for (uint32_t tile = t0; tile < t1; ++tile) {
         ElemInfo e;
         const uint32_t i0 = tile * kGTile + threadIdx.x * kGItems;
-        load_tile_info<kRound>(keys, act_pos_in, n, i0, e);
+        load_tile_info<kInit>(keys, act_pos_in, n, i0, e);
 #pragma unroll
         for (int q = 0; q < kGItems; ++q) {
             if (i0 + q >= n) continue;
@@ -199,13 +987,13 @@ __global__ void __launch_bounds__(kThreads) sa_groups_scan_kernel(uint2* __restr
     if (threadIdx.x == 0) *d_cnt_out = csum;
 }
 
-template <bool kRound>
+template <bool kInit>
 __global__ void __launch_bounds__(kThreads) sa_groups_apply_kernel(
     const unsigned long long* __restrict__ keys, const uint32_t* __restrict__ vals,
     const uint32_t* __restrict__ act_pos_in, const uint32_t* __restrict__ d_cnt, uint32_t n_block,
     const uint2* __restrict__ chunk_prefix, uint32_t* __restrict__ sa, uint32_t* __restrict__ rank,
     uint32_t* __restrict__ act_pos_out, uint32_t* __restrict__ act_suf_out, uint32_t* __restrict__ d_err) {
-    const uint32_t n = kRound ? *d_cnt : n_block;
+    const uint32_t n = *d_cnt;
     const uint32_t ntiles = (uint32_t)(((uint64_t)n + kGTile - 1) / kGTile);
     uint32_t t0, t1;
     chunk_tiles(ntiles, t0, t1);
@@ -213,7 +1001,7 @@ __global__ void __launch_bounds__(kThreads) sa_groups_apply_kernel(
     for (uint32_t tile = t0; tile < t1; ++tile) {
         ElemInfo e;
         const uint32_t i0 = tile * kGTile + threadIdx.x * kGItems;
-        load_tile_info<kRound>(keys, act_pos_in, n, i0, e);
+        load_tile_info<kInit>(keys, act_pos_in, n, i0, e);
         uint32_t tmax = 0, tsum = 0;
 #pragma unroll
         for (int q = 0; q < kGItems; ++q) {
@@ -255,9 +1043,14 @@ __global__ void __launch_bounds__(kThreads) sa_groups_apply_kernel(
     }
 }
 
+constexpr size_t kLocalSortSmem = (size_t)kLSlots * (8 + 4 + 4 + 4);
+constexpr size_t kRoundLocalSmem = (size_t)kLSlots * (8 + 4 + 4);
+
 unsigned g_keys_ctas[64] = {0};
 unsigned g_round_keys_ctas[64] = {0};
 unsigned g_groups_ctas[64] = {0};
+unsigned g_local_ctas[64] = {0};
+unsigned g_round_local_ctas[64] = {0};
 
 int current_device() {
     int dev = 0;
@@ -270,10 +1063,14 @@ int current_device() {
 void suffix_sort_init() {
     radix_init();
     const int dev = current_device();
-    g_keys_ctas[dev] = persistent_ctas((const void*)sa_init_keys_kernel, kThreads, 0);
+    cudaFuncSetAttribute(sa_local_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLocalSortSmem);
+    cudaFuncSetAttribute(sa_round_local_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRoundLocalSmem);
+    g_keys_ctas[dev] = persistent_ctas((const void*)sa_digit_keys_kernel, kThreads, 0);
     g_round_keys_ctas[dev] = persistent_ctas((const void*)sa_round_keys_kernel, kThreads, 0);
     g_groups_ctas[dev] = std::min<unsigned>(kMaxGroupChunks,
-                                            persistent_ctas((const void*)sa_groups_apply_kernel<true>, kThreads, 0));
+                                            persistent_ctas((const void*)sa_groups_apply_kernel<false>, kThreads, 0));
+    g_local_ctas[dev] = persistent_ctas((const void*)sa_local_sort_kernel, kLThreads, kLocalSortSmem);
+    g_round_local_ctas[dev] = persistent_ctas((const void*)sa_round_local_kernel, kLThreads, kRoundLocalSmem);
 }
 
 uint32_t suffix_sort_rounds(uint32_t max_len) {
@@ -286,33 +1083,34 @@ uint32_t suffix_sort_rounds(uint32_t max_len) {
     return r;
 }
 
-size_t suffix_sort_log_slots(uint32_t max_len) { return suffix_sort_rounds(max_len) + 2; }
+// slot 0: n; 1: size of the global-path list; 2 + 2r: global-path unsorted
+// members after round r (r = 0: the initial sort); 3 + 2r: local ones
+size_t suffix_sort_log_slots(uint32_t max_len) { return 4 + 2 * (size_t)suffix_sort_rounds(max_len); }
 
 size_t suffix_sort_chunk_words(uint64_t cap) {
     (void)cap;
     return kMaxGroupChunks;  // one (max, count) pair per chunk, 8 bytes each
 }
 
+size_t suffix_sort_unit_bytes(uint64_t cap) { return (size_t)kUnitFields * unit_stride(cap) * 4; }
+
 namespace {
 
-template <bool kRound>
+template <bool kInit>
 void run_groups(Launcher& L, const SuffixSortBuffers& b, const unsigned long long* keys, const uint32_t* vals,
                 const uint32_t* act_pos_in, const uint32_t* d_cnt, uint32_t n_block, uint32_t* act_pos_out,
                 uint32_t* act_suf_out, uint32_t* d_cnt_out, unsigned grid) {
     uint2* agg = reinterpret_cast<uint2*>(b.chunks);
-    const char* names[3] = {kRound ? "sa_round_groups_reduce" : "sa_groups_reduce", "sa_groups_scan",
-                            kRound ? "sa_round_groups_apply" : "sa_groups_apply"};
-    const double fixed = kRound ? 0.0 : (double)n_block;
-    const double per = kRound ? 1.0 : 0.0;
-    SBWT_LAUNCH(L, names[0], fixed * (kRound ? 0 : 8), per * 12, kRound ? d_cnt : nullptr,
-                sa_groups_reduce_kernel<kRound>, grid, kThreads, 0, keys, act_pos_in, d_cnt, n_block, agg);
+    const char* names[3] = {kInit ? "sa_large_groups_reduce" : "sa_round_groups_reduce", "sa_groups_scan",
+                            kInit ? "sa_large_groups_apply" : "sa_round_groups_apply"};
+    SBWT_LAUNCH(L, names[0], 0, 12, d_cnt, sa_groups_reduce_kernel<kInit>, grid, kThreads, 0, keys, act_pos_in,
+                d_cnt, agg);
     SBWT_LAUNCH(L, names[1], 16.0 * grid, 0, nullptr, sa_groups_scan_kernel, 1, kThreads, 0, agg, (int)grid,
                 d_cnt_out);
     // per element: key (+ neighbours), value, position, SA and rank writes,
     // and the compacted pair of an unsorted member
-    SBWT_LAUNCH(L, names[2], fixed * 28, per * 36, kRound ? d_cnt : nullptr, sa_groups_apply_kernel<kRound>, grid,
-                kThreads, 0, keys, vals, act_pos_in, d_cnt, n_block, agg, b.sa, b.rank, act_pos_out, act_suf_out,
-                b.err);
+    SBWT_LAUNCH(L, names[2], 0, 36, d_cnt, sa_groups_apply_kernel<kInit>, grid, kThreads, 0, keys, vals, act_pos_in,
+                d_cnt, n_block, agg, b.sa, b.rank, act_pos_out, act_suf_out, b.err);
 }
 
 }  // namespace
@@ -326,28 +1124,65 @@ void suffix_sort_block(Launcher& L, const uint32_t* text, const uint32_t* term, 
         return (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(std::max(1u, ctas), need));
     };
     const uint32_t rounds = suffix_sort_rounds(max_len);
+    const uint32_t nwin = (uint32_t)(((uint64_t)n + kWindow - 1) / kWindow);
+    const unsigned warp_grid = grid_of(g_keys_ctas[dev], (uint64_t)nwin / (kThreads / 32) + 1);
+    const Units units = units_at(b.units, n);
+    const uint32_t pc = kPc;
+    const int digit_bits = kDigitBits;
 
-    uint32_t* d_n = b.count_log;  // slot 0: n; slot r + 1: unsorted members after round r (r = 0: initial)
-    SBWT_LAUNCH(L, "sa_init_keys", (double)n * 12 + n / 4.0 + n / 8.0, 0, nullptr, sa_init_keys_kernel,
+    uint32_t* d_n = b.count_log;
+    uint32_t* d_large = b.count_log + 1;
+    uint32_t* dig = reinterpret_cast<uint32_t*>(b.keys);
+    uint32_t* dig_alt = reinterpret_cast<uint32_t*>(b.keys_alt);
+    SBWT_LAUNCH(L, "sa_digit_keys", (double)n * 8 + n / 4.0 + n / 8.0, 0, nullptr, sa_digit_keys_kernel,
                 grid_of(g_keys_ctas[dev], (uint64_t)n / kThreads + 1), kThreads, 0, text, term,
-                (unsigned long long)base, n, b.keys, b.vals, d_n);
-    bool alt = radix_sort_pairs(L, b.keys, b.vals, b.keys_alt, b.vals_alt, d_n, n, 0, 63, b.radix_temp, b.err);
-    run_groups<false>(L, b, alt ? b.keys_alt : b.keys, alt ? b.vals_alt : b.vals, nullptr, d_n, n, b.act_pos[0],
-                      b.act_suf[0], b.count_log + 1, grid_of(g_groups_ctas[dev], gtiles));
+                (unsigned long long)base, n, pc, dig, b.vals, d_n);
+    const bool da = radix_sort_pairs<uint32_t>(L, dig, b.vals, dig_alt, b.vals_alt, d_n, n, 0, digit_bits,
+                                               b.radix_temp, b.err);
+    const uint32_t* digits = da ? dig_alt : dig;
+    uint32_t* tsorted = da ? b.vals_alt : b.vals;
+    uint32_t* tfree = da ? b.vals : b.vals_alt;
+    // the long rows of each window, listed in the block's free arrays (the
+    // next-rank array and the device-wide path's second member list are not
+    // used before the first round)
+    uint32_t* ll_t = b.loc_next;
+    uint32_t* ll_row = b.act_suf[0];
+    SBWT_LAUNCH(L, "sa_unit_begin", (double)n * 16 + 32.0 * nwin, 0, nullptr, sa_unit_begin_kernel, warp_grid,
+                kThreads, 0, digits, tsorted, n, nwin, units, b.sa, b.rank, ll_t, ll_row, b.err);
+    SBWT_LAUNCH(L, "sa_unit_scan", 96.0 * nwin, 0, nullptr, sa_unit_scan_kernel, 1, kScanThreads, 0, units, nwin, n,
+                d_large, b.count_log + 3, (int)rounds + 1, 2);
+    // per long row: its list entry, SA and rank writes (the key words come
+    // from the packed text); per unsorted member the compacted entry
+    SBWT_LAUNCH(L, "sa_local_sort", (double)n * 16, 4, b.count_log + 3, sa_local_sort_kernel,
+                grid_of(g_local_ctas[dev], nwin), kLThreads, kLocalSortSmem, text, term, (unsigned long long)base, n,
+                ll_t, ll_row, units, nwin, b.sa, b.rank, b.loc_act, b.count_log + 3, b.err);
+    SBWT_LAUNCH(L, "sa_large_gather", 32.0 * nwin, 20, d_large, sa_large_gather_kernel, grid_of(g_local_ctas[dev], nwin),
+                kThreads, 0, text, term, (unsigned long long)base, n, tsorted, units, nwin, b.keys, tfree,
+                b.act_pos[0]);
+    const bool la = radix_sort_pairs<unsigned long long>(L, b.keys, tfree, b.keys_alt, tsorted, d_large, n, 0, 63,
+                                                         b.radix_temp, b.err);
+    run_groups<true>(L, b, la ? b.keys_alt : b.keys, la ? tsorted : tfree, b.act_pos[0], d_large, n, b.act_pos[1],
+                     b.act_suf[1], b.count_log + 2, grid_of(g_groups_ctas[dev], gtiles));
 
     const int bits = n > 1 ? 32 - __builtin_clz(n - 1) : 1;
     uint32_t h = kH0;
-    int cur = 0;
+    int cur = 1;
     for (uint32_t r = 1; r <= rounds; ++r, h *= 2) {
-        const uint32_t* cnt = b.count_log + r;
-        uint32_t* next_cnt = b.count_log + r + 1;
+        const uint32_t* cnt = b.count_log + 2 + 2 * (r - 1);
+        uint32_t* next_cnt = b.count_log + 2 + 2 * r;
+        const uint32_t* loc_cnt = b.count_log + 3 + 2 * (r - 1);
+        SBWT_LAUNCH(L, "sa_round_gather", 0, 12, loc_cnt, sa_round_gather_local_kernel, warp_grid, kThreads, 0,
+                    b.loc_act, units, nwin, b.rank, h, n, b.loc_next, b.err);
         SBWT_LAUNCH(L, "sa_round_keys", 0, 24, cnt, sa_round_keys_kernel,
                     grid_of(g_round_keys_ctas[dev], (uint64_t)n / kThreads + 1), kThreads, 0, b.act_suf[cur], cnt,
                     b.rank, h, n, bits, b.keys, b.vals, b.err);
-        const bool a =
-            radix_sort_pairs(L, b.keys, b.vals, b.keys_alt, b.vals_alt, cnt, n, 0, 2 * bits, b.radix_temp, b.err);
-        run_groups<true>(L, b, a ? b.keys_alt : b.keys, a ? b.vals_alt : b.vals, b.act_pos[cur], cnt, n,
-                         b.act_pos[cur ^ 1], b.act_suf[cur ^ 1], next_cnt, grid_of(g_groups_ctas[dev], gtiles));
+        SBWT_LAUNCH(L, "sa_round_local", 0, 24, loc_cnt, sa_round_local_kernel, grid_of(g_round_local_ctas[dev], nwin),
+                    kLThreads, kRoundLocalSmem, b.loc_act, b.loc_next, units, nwin, n, b.rank, b.sa,
+                    b.count_log + 3 + 2 * r, b.err);
+        const bool a = radix_sort_pairs<unsigned long long>(L, b.keys, b.vals, b.keys_alt, b.vals_alt, cnt, n, 0,
+                                                            2 * bits, b.radix_temp, b.err);
+        run_groups<false>(L, b, a ? b.keys_alt : b.keys, a ? b.vals_alt : b.vals, b.act_pos[cur], cnt, n,
+                          b.act_pos[cur ^ 1], b.act_suf[cur ^ 1], next_cnt, grid_of(g_groups_ctas[dev], gtiles));
         cur ^= 1;
     }
 }
