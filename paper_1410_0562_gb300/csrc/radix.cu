@@ -30,7 +30,7 @@ static_assert(kBins == kThreads, "one thread per digit");
 // shared memory of the downsweep: TMA input tile, staged output tile, warp
 // counters, three digit tables, the mbarrier
 template <class KeyT>
-constexpr size_t down_smem() {
+__host__ __device__ constexpr size_t down_smem() {
     return 2 * ((size_t)kTile * sizeof(KeyT) + (size_t)kTile * 4) + (size_t)kWarps * kBins * 4 +
            (size_t)kBins * 4 * 3 + 16;
 }
@@ -38,9 +38,14 @@ static_assert(3 * (down_smem<unsigned long long>() + 1024) <= 228 * 1024, "three
 
 // Temp layout (32-bit words): two arrays of digit totals (pass p adds into
 // array p & 1; the chunk scan of pass p clears the other one for pass p + 1),
-// then the chunk x digit offsets.
+// the fused sort's grid barrier and per-group partial counts, then the chunk
+// x digit offsets.
 constexpr size_t kTotals = 0;
-constexpr size_t kChunkOffsets = 2 * kBins;
+constexpr size_t kGridBar = 2 * kBins;  // grid barrier of the fused sort: arrivals, generation
+constexpr int kFusedGroups = 8;         // chunk groups of the fused sort's offset scan
+constexpr size_t kPartials = kGridBar + 8;
+constexpr size_t kChunkOffsets = kPartials + (size_t)kFusedGroups * kBins;
+constexpr uint32_t kGridSpinLimit = 1u << 22;
 
 // Chunk c of a grid of `grid` CTAs: tiles [t0, t1).  Only the first
 // ceil(ntiles / per) chunks hold tiles.
@@ -56,17 +61,15 @@ __device__ __forceinline__ void chunk_range(uint32_t n, uint32_t& t0, uint32_t& 
 }
 
 // Digit counts of this CTA's chunk (per-warp sub-histograms in shared
-// memory), also added to the digit totals of the whole pass.
+// memory h, kWarps x kBins words), also added to the digit totals of the
+// whole pass.  A chunk without tiles writes nothing: the scans skip it.
 template <class KeyT>
-__global__ void __launch_bounds__(kThreads) radix_upsweep_kernel(const KeyT* __restrict__ keys,
-                                                                 const uint32_t* __restrict__ d_n, int shift,
-                                                                 uint32_t* __restrict__ chunk_counts,
-                                                                 uint32_t* __restrict__ totals) {
-    __shared__ uint32_t h[kWarps * kBins];
-    const uint32_t n = *d_n;
+__device__ __forceinline__ void up_phase(const KeyT* __restrict__ keys, uint32_t n, int shift,
+                                         uint32_t* __restrict__ chunk_counts, uint32_t* __restrict__ totals,
+                                         uint32_t* h) {
     uint32_t t0, t1;
     chunk_range(n, t0, t1);
-    if (t0 >= t1) return;  // a chunk without tiles: the scan skips it
+    if (t0 >= t1) return;
     for (int i = threadIdx.x; i < kWarps * kBins; i += kThreads) h[i] = 0;
     __syncthreads();
     const uint64_t i_end = min((uint64_t)n, (uint64_t)t1 * kTile);
@@ -79,6 +82,15 @@ __global__ void __launch_bounds__(kThreads) radix_upsweep_kernel(const KeyT* __r
     for (int w = 0; w < kWarps; ++w) s += h[w * kBins + threadIdx.x];
     chunk_counts[(uint64_t)blockIdx.x * kBins + threadIdx.x] = s;
     if (s) atomicAdd(&totals[threadIdx.x], s);
+}
+
+template <class KeyT>
+__global__ void __launch_bounds__(kThreads) radix_upsweep_kernel(const KeyT* __restrict__ keys,
+                                                                 const uint32_t* __restrict__ d_n, int shift,
+                                                                 uint32_t* __restrict__ chunk_counts,
+                                                                 uint32_t* __restrict__ totals) {
+    __shared__ uint32_t h[kWarps * kBins];
+    up_phase(keys, *d_n, shift, chunk_counts, totals, h);
 }
 
 // Output offset of every (chunk, digit): the digit's start in the sorted
@@ -120,12 +132,17 @@ __global__ void __launch_bounds__(kScanThreads) radix_chunk_scan_kernel(uint32_t
     }
 }
 
+// The scatter of one pass over this CTA's chunk: whole tiles arrive by TMA
+// one tile ahead (a partial tile, only the very last one, is read with plain
+// loads); each tile is ranked, staged in digit order in shared memory and
+// written out in runs.  smem: down_smem<KeyT>() bytes, its mbarrier already
+// initialised; parity is the mbarrier's phase, carried across calls.
+// Returns false when a copy did not land (flagged in *d_err, bit 8).
 template <class KeyT>
-__global__ void __launch_bounds__(kThreads, 3) radix_downsweep_kernel(
-    const KeyT* __restrict__ kin, const uint32_t* __restrict__ vin, KeyT* __restrict__ kout,
-    uint32_t* __restrict__ vout, const uint32_t* __restrict__ d_n, int shift,
-    const uint32_t* __restrict__ chunk_offsets, uint32_t* __restrict__ d_err) {
-    extern __shared__ __align__(128) unsigned char smem[];
+__device__ __forceinline__ bool down_phase(const KeyT* __restrict__ kin, const uint32_t* __restrict__ vin,
+                                           KeyT* __restrict__ kout, uint32_t* __restrict__ vout, uint32_t n,
+                                           int shift, const uint32_t* __restrict__ chunk_offsets,
+                                           uint32_t* __restrict__ d_err, unsigned char* smem, uint32_t& parity) {
     KeyT* in_keys = reinterpret_cast<KeyT*>(smem);  // next tile, filled by TMA
     uint32_t* in_vals = reinterpret_cast<uint32_t*>(in_keys + kTile);
     KeyT* skeys = reinterpret_cast<KeyT*>(in_vals + kTile);  // tile in digit order
@@ -136,28 +153,25 @@ __global__ void __launch_bounds__(kThreads, 3) radix_downsweep_kernel(
     uint32_t* shift_out = gnext + kBins;       // gnext - dstart: tile slot -> output index
     unsigned long long* bar = reinterpret_cast<unsigned long long*>(shift_out + kBins);
 
-    const uint32_t n = *d_n;
     uint32_t t0, t1;
     chunk_range(n, t0, t1);
-    if (t0 >= t1) return;  // a chunk without tiles
+    if (t0 >= t1) return true;  // a chunk without tiles
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t lt = (1u << lane) - 1u;
     const int d = threadIdx.x;
     gnext[d] = chunk_offsets[(uint64_t)blockIdx.x * kBins + d];
-    if (threadIdx.x == 0) mbar_init(bar, 1);
     __syncthreads();
 
-    // whole tiles arrive by TMA one tile ahead; a partial tile (only the very
-    // last one) is read with plain loads
     auto full = [&](uint32_t tile) { return (uint64_t)(tile + 1) * kTile <= n; };
     auto prefetch = [&](uint32_t tile) {
         mbar_expect_tx(bar, kTile * (uint32_t)(sizeof(KeyT) + 4));
         tma_bulk_load(in_keys, kin + (uint64_t)tile * kTile, kTile * (uint32_t)sizeof(KeyT), bar);
         tma_bulk_load(in_vals, vin + (uint64_t)tile * kTile, kTile * 4u, bar);
     };
-    uint32_t parity = 0;
-    if (threadIdx.x == 0 && t0 < t1 && full(t0)) prefetch(t0);
-
+    if (threadIdx.x == 0 && full(t0)) {
+        fence_proxy_async_smem();
+        prefetch(t0);
+    }
     for (uint32_t tile = t0; tile < t1; ++tile) {
         const uint64_t base = (uint64_t)tile * kTile;
         const uint32_t cnt = (uint32_t)min((uint64_t)kTile, (uint64_t)n - base);
@@ -178,7 +192,7 @@ __global__ void __launch_bounds__(kThreads, 3) radix_downsweep_kernel(
             // chance to land (it writes this CTA's shared memory), and stop
             if (threadIdx.x == 0) atomicOr(d_err, 256u);
             mbar_wait(bar, parity ^ 1u, kMbarSpinLimit);
-            return;
+            return false;
         }
         KeyT k[kItems];
         uint32_t v[kItems];
@@ -259,9 +273,162 @@ __global__ void __launch_bounds__(kThreads, 3) radix_downsweep_kernel(
         __syncthreads();
         gnext[d] += cnt_d;
     }
+    return true;
+}
+
+template <class KeyT>
+__global__ void __launch_bounds__(kThreads, 3) radix_downsweep_kernel(
+    const KeyT* __restrict__ kin, const uint32_t* __restrict__ vin, KeyT* __restrict__ kout,
+    uint32_t* __restrict__ vout, const uint32_t* __restrict__ d_n, int shift,
+    const uint32_t* __restrict__ chunk_offsets, uint32_t* __restrict__ d_err) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem + down_smem<KeyT>() - 16);
+    if (threadIdx.x == 0) mbar_init(bar, 1);
+    uint32_t parity = 0;
+    down_phase(kin, vin, kout, vout, *d_n, shift, chunk_offsets, d_err, smem, parity);
+}
+
+// ---------------------------------------------------------------------------
+// Fused sort: every pass of one sort in a single cooperative launch (all
+// CTAs resident), the phases separated by grid barriers.  It serves lists
+// whose length is only known on the device and is often zero: then every
+// CTA returns at once and the sort costs one launch.
+
+// Grid barrier on two words: arrivals and a generation number.  The last CTA
+// to arrive resets the count and advances the generation; the others wait
+// for the generation to move, for at most kGridSpinLimit polls (then flag
+// *d_err bit 9 and report failure).
+__device__ __forceinline__ bool grid_barrier(unsigned* gbar, unsigned& gen, uint32_t* d_err) {
+    __shared__ int ok_sh;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        __threadfence();
+        const unsigned prev = atomicAdd(&gbar[0], 1u);
+        if (prev == gridDim.x - 1) {
+            atomicExch(&gbar[0], 0u);
+            __threadfence();
+            atomicAdd(&gbar[1], 1u);
+        } else {
+            uint32_t polls = 0;
+            while (*reinterpret_cast<volatile unsigned*>(&gbar[1]) == gen) {
+                if (++polls > kGridSpinLimit) {
+                    ok = 0;
+                    atomicOr(d_err, 512u);
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        __threadfence();
+        ++gen;
+        ok_sh = ok;
+    }
+    __syncthreads();
+    return ok_sh != 0;
+}
+
+// Output offsets of every (chunk, digit) from the chunk counts, in two
+// steps over work items (digit d, group q of consecutive chunks), one warp
+// per item: first the count of each group, then each group's running sum.
+__device__ __forceinline__ void chunk_groups(uint32_t nchunks, uint32_t& per) {
+    per = (nchunks + kFusedGroups - 1) / kFusedGroups;
+}
+__device__ __forceinline__ void scan_a_phase(const uint32_t* __restrict__ chunk_counts, uint32_t nchunks,
+                                             uint32_t* __restrict__ partials) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t warps = gridDim.x * kWarps;
+    uint32_t per;
+    chunk_groups(nchunks, per);
+    for (uint32_t item = blockIdx.x * kWarps + (threadIdx.x >> 5); item < (uint32_t)kBins * kFusedGroups;
+         item += warps) {
+        const uint32_t d = item % kBins, q = item / kBins;
+        const uint32_t c0 = min(nchunks, q * per), c1 = min(nchunks, c0 + per);
+        uint32_t sum = 0;
+        for (uint32_t c = c0 + lane; c < c1; c += 32) sum += chunk_counts[(uint64_t)c * kBins + d];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        if (lane == 0) partials[q * kBins + d] = sum;
+    }
+}
+__device__ __forceinline__ void scan_b_phase(uint32_t* __restrict__ chunk_counts, uint32_t nchunks,
+                                             const uint32_t* __restrict__ partials,
+                                             const uint32_t* __restrict__ totals) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t warps = gridDim.x * kWarps;
+    uint32_t per;
+    chunk_groups(nchunks, per);
+    for (uint32_t item = blockIdx.x * kWarps + (threadIdx.x >> 5); item < (uint32_t)kBins * kFusedGroups;
+         item += warps) {
+        const uint32_t d = item % kBins, q = item / kBins;
+        // start of digit d in the output, plus its count in earlier groups
+        uint32_t run = 0;
+        for (uint32_t e = lane; e < d; e += 32) run += totals[e];
+        for (uint32_t g = lane; g < q; g += 32) run += partials[g * kBins + d];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) run += __shfl_xor_sync(0xffffffffu, run, o);
+        const uint32_t c0 = min(nchunks, q * per), c1 = min(nchunks, c0 + per);
+        for (uint32_t cb = c0; cb < c1; cb += 32) {
+            const uint32_t c = cb + lane;
+            const uint32_t v = c < c1 ? chunk_counts[(uint64_t)c * kBins + d] : 0u;
+            uint32_t x = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            if (c < c1) chunk_counts[(uint64_t)c * kBins + d] = run + x - v;
+            run += __shfl_sync(0xffffffffu, x, 31);
+        }
+    }
+}
+
+template <class KeyT>
+__global__ void __launch_bounds__(kThreads, 3) radix_sort_fused_kernel(KeyT* __restrict__ keys,
+                                                                       uint32_t* __restrict__ vals,
+                                                                       KeyT* __restrict__ keys_alt,
+                                                                       uint32_t* __restrict__ vals_alt,
+                                                                       const uint32_t* __restrict__ d_n,
+                                                                       int begin_bit, int passes,
+                                                                       uint32_t* __restrict__ temp,
+                                                                       uint32_t* __restrict__ d_err) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    const uint32_t n = *d_n;
+    if (n == 0) return;  // the whole grid leaves together
+    unsigned* gbar = temp + kGridBar;
+    unsigned gen = *reinterpret_cast<volatile unsigned*>(&gbar[1]);  // read before this CTA's first arrival
+    unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem + down_smem<KeyT>() - 16);
+    if (threadIdx.x == 0) mbar_init(bar, 1);
+    uint32_t parity = 0;
+    uint32_t ntiles;
+    const uint32_t tpc = tiles_per_chunk(n, gridDim.x, ntiles);
+    const uint32_t nchunks = tpc ? (ntiles + tpc - 1) / tpc : 0;
+    uint32_t* chunk = temp + kChunkOffsets;
+    uint32_t* partials = temp + kPartials;
+    for (int p = 0; p < passes; ++p) {
+        const bool alt = p & 1;
+        const KeyT* kin = alt ? keys_alt : keys;
+        const uint32_t* vin = alt ? vals_alt : vals;
+        KeyT* ko = alt ? keys : keys_alt;
+        uint32_t* vo = alt ? vals : vals_alt;
+        const int shift = begin_bit + kRadixBits * p;
+        uint32_t* totals = temp + kTotals + (size_t)kBins * (p & 1);
+        uint32_t* next_totals = temp + kTotals + (size_t)kBins * ((p + 1) & 1);
+        up_phase(kin, n, shift, chunk, totals, reinterpret_cast<uint32_t*>(smem));
+        if (!grid_barrier(gbar, gen, d_err)) return;
+        scan_a_phase(chunk, nchunks, partials);
+        if (blockIdx.x == 0) next_totals[threadIdx.x] = 0;
+        if (!grid_barrier(gbar, gen, d_err)) return;
+        scan_b_phase(chunk, nchunks, partials, totals);
+        if (!grid_barrier(gbar, gen, d_err)) return;
+        if (!down_phase(kin, vin, ko, vo, n, shift, chunk, d_err, smem, parity)) return;
+        if (!grid_barrier(gbar, gen, d_err)) return;
+    }
 }
 
 unsigned g_down_ctas[2][64] = {{0}};  // [key is 64-bit][device]
+unsigned g_fused_ctas[64] = {0};
+
 
 int current_device() {
     int dev = 0;
@@ -300,6 +467,11 @@ void radix_init_key() {
 void radix_init() {
     radix_init_key<uint32_t>();
     radix_init_key<unsigned long long>();
+    const size_t smem = down_smem<unsigned long long>();
+    cudaFuncSetAttribute(radix_sort_fused_kernel<unsigned long long>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    g_fused_ctas[current_device()] = std::min<unsigned>(
+        kMaxChunks, persistent_ctas((const void*)radix_sort_fused_kernel<unsigned long long>, kThreads, smem));
 }
 
 template <class KeyT>
@@ -323,7 +495,7 @@ bool radix_sort_pairs(Launcher& L, KeyT* keys, uint32_t* vals, KeyT* keys_alt, u
         const int shift = begin_bit + kRadixBits * p;
         uint32_t* totals = temp + kTotals + (size_t)kBins * (p & 1);
         uint32_t* next_totals = temp + kTotals + (size_t)kBins * ((p + 1) & 1);
-        if (p == 0) cudaMemsetAsync(totals, 0, kBins * 4, L.stream);
+        if (p == 0) cudaMemsetAsync(temp, 0, (kGridBar + 2) * 4, L.stream);
         SBWT_LAUNCH(L, "radix_upsweep", 0, kb, d_n, radix_upsweep_kernel<KeyT>, grid, kThreads, 0, kin, d_n, shift,
                     chunk, totals);
         SBWT_LAUNCH(L, "radix_chunk_scan", 12.0 * grid * kBins, 0, nullptr, radix_chunk_scan_kernel, kBins / 32,
@@ -333,6 +505,34 @@ bool radix_sort_pairs(Launcher& L, KeyT* keys, uint32_t* vals, KeyT* keys_alt, u
         alt = !alt;
     }
     return alt;
+}
+
+bool radix_sort_pairs_fused(Launcher& L, unsigned long long* keys, uint32_t* vals, unsigned long long* keys_alt,
+                            uint32_t* vals_alt, const uint32_t* d_n, uint64_t cap, int begin_bit, int end_bit,
+                            uint32_t* temp, uint32_t* d_err) {
+    int passes = radix_passes(begin_bit, end_bit);
+    if (passes <= 0) return false;
+    const int dev = current_device();
+    const uint64_t tiles = cap / kTile + 1;
+    const unsigned grid = (unsigned)std::min<uint64_t>(std::max(1u, g_fused_ctas[dev]), tiles);
+    cudaMemsetAsync(temp, 0, (kGridBar + 2) * 4, L.stream);
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = down_smem<unsigned long long>();
+    cfg.stream = L.stream;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    // per element and pass: the key read by the count, key and value read
+    // and written by the scatter
+    const int tok = L.before("radix_sort_fused", 0, (8.0 + 24.0) * passes, d_n);
+    cudaLaunchKernelEx(&cfg, radix_sort_fused_kernel<unsigned long long>, keys, vals, keys_alt, vals_alt, d_n,
+                       begin_bit, passes, temp, d_err);
+    L.after(tok);
+    return passes & 1;
 }
 
 template bool radix_sort_pairs<uint32_t>(Launcher&, uint32_t*, uint32_t*, uint32_t*, uint32_t*, const uint32_t*,

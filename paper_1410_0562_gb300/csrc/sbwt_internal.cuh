@@ -284,5 +284,12 @@ template <class KeyT>
 bool radix_sort_pairs(Launcher& L, KeyT* keys, uint32_t* vals, KeyT* keys_alt, uint32_t* vals_alt,
                       const uint32_t* d_n, uint64_t cap, int begin_bit, int end_bit, uint32_t* temp,
                       uint32_t* d_err);
+// The same sort of 64-bit keys in one cooperative launch (all passes, the
+// CTAs meeting at bounded grid barriers; a barrier that times out flags
+// *d_err bit 9).  Meant for lists that are often empty: an empty list costs
+// one launch that returns at once.
+bool radix_sort_pairs_fused(Launcher& L, unsigned long long* keys, uint32_t* vals, unsigned long long* keys_alt,
+                            uint32_t* vals_alt, const uint32_t* d_n, uint64_t cap, int begin_bit, int end_bit,
+                            uint32_t* temp, uint32_t* d_err);
 
 }  // namespace sbwt

@@ -121,15 +121,21 @@ __device__ __forceinline__ unsigned long long initial_key(const uint32_t* __rest
 // Dense number of the bucket (p, l) of key K among all valid pairs in (p, l)
 // order, pc = P codes.  A pair is valid when the codes of p at and past l are
 // zero.  Pairs before (p, l): the p pairs (p' < p, l' = P); for each l' < P
-// the multiples of 4^(P - l') below p (short pairs with p' < p); and the
-// short pairs (p, l') with l' < l, i.e. those whose zero tail p has.  Bit 31
-// flags a short bucket.
+// the multiples of 4^(P - l') below p (short pairs with p' < p), in all
+// sum_{k=1..P} ceil(p / 4^k), which for p >= 1 is P + sum_k floor((p-1) /
+// 4^k) = P + ((p-1) - s4(p-1)) / 3 with s4 the base-4 digit sum (Legendre's
+// formula); and the short pairs (p, l') with l' < l, i.e. those whose zero
+// tail p has.  Bit 31 flags a short bucket.
 __device__ __forceinline__ uint32_t bucket_digit(unsigned long long K, uint32_t pc) {
     const uint32_t l = min((uint32_t)(K & 31), pc);
     const uint32_t p = (uint32_t)((K >> 5) >> (58 - 2 * pc));
     const uint32_t zero_codes = p ? (uint32_t)(__ffs(p) - 1) >> 1 : pc;
     uint32_t o = p;
-    for (uint32_t k = 1; k <= pc; ++k) o += (p + (1u << (2 * k)) - 1) >> (2 * k);
+    if (p) {
+        const uint32_t x = p - 1;
+        const uint32_t s4 = (uint32_t)__popc(x & 0x55555555u) + 2u * (uint32_t)__popc(x & 0xAAAAAAAAu);
+        o += pc + (x - s4) / 3;
+    }
     const uint32_t first_valid = pc > zero_codes ? pc - zero_codes : 0;
     o += l > first_valid ? l - first_valid : 0;
     return o | (l < pc ? kShortFlag : 0u);
@@ -428,16 +434,18 @@ __device__ __forceinline__ uint32_t carry_in_head(uint32_t heads, uint32_t g0) {
 
 // Sort of `count` <= kLCap (key, value) pairs held blocked in registers
 // (as for block_merge_sort) when the list is cut into segments of equal
-// key >> shift, contiguous and in segment order, none longer than kSeg: an
+// key >> kShift, contiguous and in segment order, none longer than kSeg: an
 // item's place is its segment's first index plus the number of items of its
 // segment before it in (key, value) order (values are distinct, so the order
 // is total).  Returns false, with the registers untouched, when a segment is
 // longer than kSeg.  On success skey/sval hold the sorted list too.
 constexpr uint32_t kSeg = 64;
 
+template <int kShift>
 __device__ __forceinline__ bool block_segment_sort(unsigned long long (&k)[kLItems], uint32_t (&v)[kLItems],
-                                                   uint32_t count, int shift, unsigned long long* skey,
-                                                   uint32_t* sval, uint32_t* sseg) {
+                                                   uint32_t count, unsigned long long* skey, uint32_t* sval,
+                                                   uint32_t* sseg) {
+    constexpr int shift = kShift;
     const uint32_t g0 = threadIdx.x * kLItems;
     __syncthreads();
 #pragma unroll
@@ -458,13 +466,13 @@ __device__ __forceinline__ bool block_segment_sort(unsigned long long (&k)[kLIte
     bool next_start = true;
     if (g0 + kLItems < count) next_start = (skey[skew(g0 + kLItems)] >> shift) != (k[kLItems - 1] >> shift);
     uint32_t s0 = carry_in_head(starts, g0);
-    uint32_t first[kLItems];
+    uint32_t pos[kLItems];  // first the segment's first index, then the item's place
     bool big = false;
 #pragma unroll
     for (int j = 0; j < kLItems; ++j) {
         const uint32_t g = g0 + j;
         if ((starts >> j) & 1u) s0 = g;
-        first[j] = s0;
+        pos[j] = s0;
         const bool last = j + 1 < kLItems ? (((starts >> (j + 1)) & 1u) || g + 1 >= count) : next_start;
         if (g < count && last) {
             sseg[skew(s0)] = g + 1;
@@ -472,19 +480,17 @@ __device__ __forceinline__ bool block_segment_sort(unsigned long long (&k)[kLIte
         }
     }
     if (__syncthreads_or(big)) return false;
-    uint32_t pos[kLItems];
 #pragma unroll
     for (int j = 0; j < kLItems; ++j) {
         const uint32_t g = g0 + j;
-        pos[j] = g;
         if (g >= count) continue;
-        const uint32_t s1 = sseg[skew(first[j])];
-        uint32_t r = 0;
-        for (uint32_t x = first[j]; x < s1; ++x) {
+        const uint32_t s1 = sseg[skew(pos[j])];
+        uint32_t r = pos[j];
+        for (uint32_t x = pos[j]; x < s1; ++x) {
             const unsigned long long kx = skey[skew(x)];
             r += (kx < k[j] || (kx == k[j] && sval[skew(x)] < v[j])) ? 1u : 0u;
         }
-        pos[j] = first[j] + r;
+        pos[j] = r;
     }
     __syncthreads();
 #pragma unroll
@@ -505,12 +511,13 @@ __device__ __forceinline__ bool block_segment_sort(unsigned long long (&k)[kLIte
     return true;
 }
 
-// Sorts the blocked items by (key, value) order of whole segments, as
-// above, else by a merge sort of the list; leaves the sorted keys in skey.
+// Sorts the blocked items by (key, value): segment by segment as above,
+// else by a merge sort of the list; leaves the sorted keys in skey.
+template <int kShift>
 __device__ __forceinline__ void block_sort(unsigned long long (&k)[kLItems], uint32_t (&v)[kLItems],
-                                           uint32_t count, int shift, unsigned long long* skey, uint32_t* sval,
+                                           uint32_t count, unsigned long long* skey, uint32_t* sval,
                                            uint32_t* sseg) {
-    if (block_segment_sort(k, v, count, shift, skey, sval, sseg)) {
+    if (block_segment_sort<kShift>(k, v, count, skey, sval, sseg)) {
         __syncthreads();
         return;
     }
@@ -608,7 +615,7 @@ __device__ __forceinline__ void batch_write_unsorted(Batch& b, uint32_t k, uint3
 // its first unit start ws (k0 = lcb in window ws, 0 after), in row order;
 // the sorted j-th long suffix takes the j-th of those rows, srow[j].  A
 // global-path unit ends a batch and is skipped.
-__global__ void __launch_bounds__(kLThreads) sa_local_sort_kernel(
+__global__ void __launch_bounds__(kLThreads, 2) sa_local_sort_kernel(
     const uint32_t* __restrict__ text, const uint32_t* __restrict__ term, unsigned long long base, uint32_t n,
     const uint32_t* __restrict__ ll_t, const uint32_t* __restrict__ ll_row, Units u, uint32_t nwin,
     uint32_t* __restrict__ sa, uint32_t* __restrict__ rank, uint32_t* __restrict__ loc_act,
@@ -646,7 +653,13 @@ __global__ void __launch_bounds__(kLThreads) sa_local_sort_kernel(
         if (threadIdx.x < k && ub != kNone) atomicMin(&b.misc[1], x);
         __syncthreads();
         const uint32_t ws = b.misc[1];
-        // copy the long rows (with their keys), kLThreads windows at a time
+        // this thread's slots g0 .. g0 + kLItems - 1 of the batch's long rows:
+        // list positions first (the run table is built kLThreads windows at
+        // a time), then all loads at once
+        const uint32_t g0 = threadIdx.x * kLItems;
+        uint32_t src[kLItems];
+#pragma unroll
+        for (int j = 0; j < kLItems; ++j) src[j] = kNone;
         uint32_t cc = 0;
         for (uint32_t x0 = ws; cc < total && x0 < nwin; x0 += kLThreads) {
             const uint32_t xx = x0 + threadIdx.x;
@@ -658,34 +671,40 @@ __global__ void __launch_bounds__(kLThreads) sa_local_sort_kernel(
             run_start[threadIdx.x] = cc + ex;
             run_src[threadIdx.x] = xx * kWindow + k0;
             const uint32_t nruns = (uint32_t)__syncthreads_count(ex < take);
-            for (uint32_t q = threadIdx.x; q < take; q += kLThreads) {
-                uint32_t lo = 0, hi = nruns - 1;  // the last run starting at or before slot cc + q
+            if (g0 + kLItems > cc && g0 < cc + take) {
+                const uint32_t gs = max(g0, cc);
+                uint32_t lo = 0, hi = nruns - 1;  // the last run starting at or before slot gs
                 while (lo < hi) {
                     const uint32_t mid = (lo + hi + 1) >> 1;
-                    if (run_start[mid] <= cc + q) lo = mid;
+                    if (run_start[mid] <= gs) lo = mid;
                     else hi = mid - 1;
                 }
-                const uint32_t src = run_src[lo] + (cc + q - run_start[lo]);
-                const uint32_t t = ll_t[src];
-                if (t >= n) atomicOr(d_err, 64u);  // an out-of-range t is skipped when written back
-                skey[skew(cc + q)] = initial_key(text, term, base + (t < n ? t : 0u));
-                sval[skew(cc + q)] = t;
-                srow[skew(cc + q)] = ll_row[src];
+#pragma unroll
+                for (int j = 0; j < kLItems; ++j) {
+                    const uint32_t g = g0 + j;
+                    if (g < cc || g >= cc + take) continue;
+                    while (lo + 1 < nruns && run_start[lo + 1] <= g) ++lo;
+                    src[j] = run_src[lo] + (g - run_start[lo]);
+                }
             }
             cc += take;
             __syncthreads();
         }
         const uint32_t cnt = cc;
-        const uint32_t g0 = threadIdx.x * kLItems;
         unsigned long long kk[kLItems];
-        uint32_t v[kLItems];
+        uint32_t v[kLItems], rw[kLItems];
 #pragma unroll
         for (int j = 0; j < kLItems; ++j) {
-            const uint32_t g = g0 + j;
-            kk[j] = g < cnt ? skey[skew(g)] : ~0ull;
-            v[j] = g < cnt ? sval[skew(g)] : 0u;
+            v[j] = src[j] != kNone ? ll_t[src[j]] : 0u;
+            rw[j] = src[j] != kNone ? ll_row[src[j]] : 0u;
         }
-        block_sort(kk, v, cnt, kBucketShift, skey, sval, sseg);  // segments: buckets
+#pragma unroll
+        for (int j = 0; j < kLItems; ++j) {
+            if (v[j] >= n) atomicOr(d_err, 64u);  // an out-of-range t is skipped when written back
+            kk[j] = g0 + j < cnt ? initial_key(text, term, base + (v[j] < n ? v[j] : 0u)) : ~0ull;
+            srow[skew(g0 + j)] = rw[j];
+        }
+        block_sort<kBucketShift>(kk, v, cnt, skey, sval, sseg);  // segments: buckets
 
         // group heads: a new key, or a key that contains its terminator
         const unsigned long long kprev = (g0 > 0 && g0 <= cnt) ? skey[skew(g0 - 1)] : 0ull;
@@ -775,7 +794,7 @@ __global__ void __launch_bounds__(kThreads) sa_round_gather_local_kernel(
 // One round for the local units, a batch of units per CTA step: sort the
 // unsorted members by (rank[t], rank[t + h]); a member of the group whose
 // head row is H that lands at offset x of its group takes row H + x.
-__global__ void __launch_bounds__(kLThreads) sa_round_local_kernel(
+__global__ void __launch_bounds__(kLThreads, 2) sa_round_local_kernel(
     uint32_t* __restrict__ loc_act, const uint32_t* __restrict__ loc_next, Units u, uint32_t nwin, uint32_t n,
     uint32_t* __restrict__ rank, uint32_t* __restrict__ sa, uint32_t* __restrict__ d_cnt,
     uint32_t* __restrict__ d_err) {
@@ -824,7 +843,7 @@ __global__ void __launch_bounds__(kLThreads) sa_round_local_kernel(
                 kk[j] = ((unsigned long long)here << 32) | loc_next[src];
             }
         }
-        block_sort(kk, v, total, 32, skey, sval, sseg);  // segments: the old groups (equal rank[t])
+        block_sort<32>(kk, v, total, skey, sval, sseg);  // segments: the old groups (equal rank[t])
 
         const unsigned long long kprev = (g0 > 0 && g0 <= total) ? skey[skew(g0 - 1)] : 0ull;
         uint32_t heads = 0, starts = 0;  // new groups; old groups (a new head row)
@@ -1159,8 +1178,8 @@ void suffix_sort_block(Launcher& L, const uint32_t* text, const uint32_t* term, 
     SBWT_LAUNCH(L, "sa_large_gather", 32.0 * nwin, 20, d_large, sa_large_gather_kernel, grid_of(g_local_ctas[dev], nwin),
                 kThreads, 0, text, term, (unsigned long long)base, n, tsorted, units, nwin, b.keys, tfree,
                 b.act_pos[0]);
-    const bool la = radix_sort_pairs<unsigned long long>(L, b.keys, tfree, b.keys_alt, tsorted, d_large, n, 0, 63,
-                                                         b.radix_temp, b.err);
+    const bool la = radix_sort_pairs_fused(L, b.keys, tfree, b.keys_alt, tsorted, d_large, n, 0, 63, b.radix_temp,
+                                           b.err);
     run_groups<true>(L, b, la ? b.keys_alt : b.keys, la ? tsorted : tfree, b.act_pos[0], d_large, n, b.act_pos[1],
                      b.act_suf[1], b.count_log + 2, grid_of(g_groups_ctas[dev], gtiles));
 
@@ -1179,8 +1198,8 @@ void suffix_sort_block(Launcher& L, const uint32_t* text, const uint32_t* term, 
         SBWT_LAUNCH(L, "sa_round_local", 0, 24, loc_cnt, sa_round_local_kernel, grid_of(g_round_local_ctas[dev], nwin),
                     kLThreads, kRoundLocalSmem, b.loc_act, b.loc_next, units, nwin, n, b.rank, b.sa,
                     b.count_log + 3 + 2 * r, b.err);
-        const bool a = radix_sort_pairs<unsigned long long>(L, b.keys, b.vals, b.keys_alt, b.vals_alt, cnt, n, 0,
-                                                            2 * bits, b.radix_temp, b.err);
+        const bool a = radix_sort_pairs_fused(L, b.keys, b.vals, b.keys_alt, b.vals_alt, cnt, n, 0, 2 * bits,
+                                              b.radix_temp, b.err);
         run_groups<false>(L, b, a ? b.keys_alt : b.keys, a ? b.vals_alt : b.vals, b.act_pos[cur], cnt, n,
                           b.act_pos[cur ^ 1], b.act_suf[cur ^ 1], next_cnt, grid_of(g_groups_ctas[dev], gtiles));
         cur ^= 1;
