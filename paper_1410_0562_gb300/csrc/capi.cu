@@ -59,6 +59,13 @@ struct sbwt_index {
     int device = -1;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    // The suffix sorts of an append's blocks run on a second stream, ahead of
+    // the ComputeRanks -> B_int/g_sa -> Insert chain on `stream`: a block's
+    // sort reads only the packed text.  Its SA_int goes to one of two buffers
+    // (sa, sa2 by block parity).
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_sorted[2] = {nullptr, nullptr},
+                ev_consumed[2] = {nullptr, nullptr};
     bool dev_ready = false;
 
     uint64_t n = 0, m = 0;
@@ -66,7 +73,7 @@ struct sbwt_index {
     int cur = 0;
 
     DevBuf reads, offsets, text, term, err;
-    DevBuf keys, keys_alt, vals, vals_alt, sa, rank, act_pos0, act_pos1, act_suf0, act_suf1, loc_act, loc_next;
+    DevBuf keys, keys_alt, vals, vals_alt, sa, sa2, rank, act_pos0, act_pos1, act_suf0, act_suf1, loc_act, loc_next;
     DevBuf units;
     DevBuf radix_temp, chunks, count_log, g, gsa, bint, sb_tot;
     DevBuf out_bytes, q_codes, q_ks, q_out, c_pats, c_offs;
@@ -94,11 +101,12 @@ struct sbwt_index {
     bool last_valid = false;
     uint64_t last_n = 0;
     bool last_idx64 = false;
+    const void* last_sa = nullptr;  // the SA_int buffer of the last block
 
     std::vector<DevBuf*> all_bufs() {
         std::vector<DevBuf*> v = {&reads,      &offsets,  &text,      &term,     &err,      &keys,
                                   &keys_alt,   &vals,     &vals_alt,  &sa,       &rank,     &act_pos0,
-                                  &act_pos1,   &act_suf0, &act_suf1,  &loc_act,  &loc_next, &units,
+                                  &act_pos1,   &act_suf0, &act_suf1,  &loc_act,  &loc_next, &units,     &sa2,
                                   &radix_temp, &chunks,
                                   &count_log,  &g,        &gsa,       &bint,     &sb_tot,   &out_bytes,
                                   &q_codes,    &q_ks,     &q_out,     &plan,     &c_pats,   &c_offs};
@@ -189,6 +197,10 @@ int device_init(sbwt_index* idx) {
         idx->own_stream = true;
     }
     idx->L.stream = idx->stream;
+    if (cudaStreamCreateWithFlags(&idx->side, cudaStreamNonBlocking) != cudaSuccess) return SBWT_EDEVICE;
+    for (cudaEvent_t* e : {&idx->ev_fork, &idx->ev_join, &idx->ev_sorted[0], &idx->ev_sorted[1],
+                           &idx->ev_consumed[0], &idx->ev_consumed[1]})
+        if (cudaEventCreateWithFlags(e, cudaEventDisableTiming) != cudaSuccess) return SBWT_EDEVICE;
     suffix_sort_init();
     if (cudaMallocHost(&idx->h_err, sizeof(uint32_t)) != cudaSuccess) return SBWT_EDEVICE;
     if (cudaMallocHost(&idx->h_plan, kPlanCap * sizeof(PlanBlock)) != cudaSuccess) return SBWT_EDEVICE;
@@ -259,7 +271,7 @@ std::vector<Need> buffer_needs(sbwt_index* idx, const Plan& p, bool host_input, 
     v.push_back({&idx->text, (size_t)((p.npos + 31) / 32 * 2 + kTextPadWords) * 4});
     v.push_back({&idx->term, (size_t)((p.npos + 31) / 32 + kTermPadWords) * 4});
     for (DevBuf* b : {&idx->keys, &idx->keys_alt}) v.push_back({b, (size_t)cap * 8});
-    for (DevBuf* b : {&idx->vals, &idx->vals_alt, &idx->sa, &idx->rank, &idx->act_pos0, &idx->act_pos1,
+    for (DevBuf* b : {&idx->vals, &idx->vals_alt, &idx->sa, &idx->sa2, &idx->rank, &idx->act_pos0, &idx->act_pos1,
                       &idx->act_suf0, &idx->act_suf1, &idx->loc_act, &idx->loc_next})
         v.push_back({b, (size_t)cap * 4});
     v.push_back({&idx->units, suffix_sort_unit_bytes(cap)});
@@ -366,7 +378,7 @@ void run_block(sbwt_index* idx, const BlockPlan& bp, const uint64_t* d_offsets, 
     b.keys_alt = (unsigned long long*)idx->keys_alt.p;
     b.vals = (uint32_t*)idx->vals.p;
     b.vals_alt = (uint32_t*)idx->vals_alt.p;
-    b.sa = (uint32_t*)idx->sa.p;
+    b.sa = (uint32_t*)((k & 1) ? idx->sa2.p : idx->sa.p);
     b.rank = (uint32_t*)idx->rank.p;
     b.act_pos[0] = (uint32_t*)idx->act_pos0.p;
     b.act_pos[1] = (uint32_t*)idx->act_pos1.p;
@@ -382,12 +394,22 @@ void run_block(sbwt_index* idx, const BlockPlan& bp, const uint64_t* d_offsets, 
     const uint32_t* text = (const uint32_t*)idx->text.p;
     const uint32_t* term = (const uint32_t*)idx->term.p;
 
+    // the sort, on the side stream; its SA buffer is free once the gather of
+    // block k - 2 has read it
+    const cudaStream_t s = L.stream;
+    if (k >= 2) cudaStreamWaitEvent(idx->side, idx->ev_consumed[k & 1], 0);
+    L.stream = idx->side;
     suffix_sort_block(L, text, term, bp.base, n, (uint32_t)bp.max_len, b);
+    cudaEventRecord(idx->ev_sorted[k & 1], idx->side);
+    L.stream = s;
+    // ComputeRanks needs only the dictionary; the gather waits for the sort
     launch_compute_ranks<IdxT>(L, text, d_offsets, bp.j0, bp.j1 - bp.j0, bp.n_int, (const OccBlock*)src.blocks.p,
                                (const unsigned long long*)src.super.p, (const unsigned long long*)src.C.p, n_ext,
                                m_ext, (IdxT*)idx->g.p, (uint32_t*)idx->err.p);
+    cudaStreamWaitEvent(s, idx->ev_sorted[k & 1], 0);
     launch_bint_gather<IdxT>(L, text, term, bp.base, b.sa, (const IdxT*)idx->g.p, n, (uint8_t*)idx->bint.p,
                              (IdxT*)idx->gsa.p);
+    cudaEventRecord(idx->ev_consumed[k & 1], s);
     launch_insert<IdxT>(L, (const OccBlock*)src.blocks.p, n_ext, (const uint8_t*)idx->bint.p,
                         (const IdxT*)idx->gsa.p, bp.n_int, (OccBlock*)dst.blocks.p,
                         (unsigned long long*)dst.super.p, (unsigned long long*)dst.C.p, m_ext + (bp.j1 - bp.j0),
@@ -456,6 +478,8 @@ int append_impl(sbwt_index* idx, const uint8_t* d_reads, const uint64_t* d_offse
                     (uint32_t*)idx->term.p, (uint32_t*)idx->err.p);
         int src = idx->cur;
         uint64_t n_ext = idx->n, m_ext = idx->m;
+        cudaEventRecord(idx->ev_fork, s);  // the sorts read the packed text
+        cudaStreamWaitEvent(idx->side, idx->ev_fork, 0);
         for (size_t k = 0; k < p.blocks.size(); ++k) {
             const BlockPlan& bp = p.blocks[k];
             const int dst = other[k & 1];
@@ -468,6 +492,8 @@ int append_impl(sbwt_index* idx, const uint8_t* d_reads, const uint64_t* d_offse
             m_ext += bp.j1 - bp.j0;
             src = dst;
         }
+        cudaEventRecord(idx->ev_join, idx->side);
+        cudaStreamWaitEvent(s, idx->ev_join, 0);
         cudaMemcpyAsync(idx->h_err, idx->err.p, 4, cudaMemcpyDeviceToHost, s);
     };
 
@@ -533,6 +559,7 @@ int append_impl(sbwt_index* idx, const uint8_t* d_reads, const uint64_t* d_offse
     idx->last_valid = !p.blocks.empty();
     idx->last_n = p.blocks.empty() ? 0 : p.blocks.back().n_int;
     idx->last_idx64 = p.idx64;
+    idx->last_sa = (p.blocks.size() & 1) ? idx->sa.p : idx->sa2.p;
     return SBWT_OK;
 }
 
@@ -918,6 +945,13 @@ void sbwt_destroy(sbwt_index* idx) {
         if (idx->h_offsets) cudaFreeHost(idx->h_offsets);
         if (idx->h_plan) cudaFreeHost(idx->h_plan);
         if (idx->h_summary) cudaFreeHost(idx->h_summary);
+        if (idx->side) {
+            cudaStreamSynchronize(idx->side);
+            cudaStreamDestroy(idx->side);
+        }
+        for (cudaEvent_t e : {idx->ev_fork, idx->ev_join, idx->ev_sorted[0], idx->ev_sorted[1],
+                              idx->ev_consumed[0], idx->ev_consumed[1]})
+            if (e) cudaEventDestroy(e);
         if (idx->own_stream) cudaStreamDestroy(idx->stream);
     }
     delete idx;
@@ -945,7 +979,7 @@ int sbwt_get_stage(sbwt_index* idx, int stage, void* out, uint64_t cap, uint64_t
     size_t elem = 0;
     const void* src = nullptr;
     switch (stage) {
-        case SBWT_STAGE_SA: elem = 4; src = idx->sa.p; break;
+        case SBWT_STAGE_SA: elem = 4; src = idx->last_sa; break;
         case SBWT_STAGE_BINT: elem = 1; src = idx->bint.p; break;
         case SBWT_STAGE_G: elem = 8; src = idx->g.p; break;
         case SBWT_STAGE_GSA: elem = 8; src = idx->gsa.p; break;
