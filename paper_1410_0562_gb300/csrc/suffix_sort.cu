@@ -157,14 +157,19 @@ __global__ void __launch_bounds__(kThreads) sa_digit_keys_kernel(const uint32_t*
 // One warp per window of the digit-sorted array: the first bucket start in
 // the window and the long-suffix counts before it and in the whole window.
 // Short suffixes are finished where they landed: SA and rank are written
-// here.  The k-th long row i of window w is listed as (ll_t, ll_row)[w
-// kWindow + k] = (t, i), so a unit's long rows are a few contiguous runs.
-__global__ void __launch_bounds__(kThreads) sa_unit_begin_kernel(const uint32_t* __restrict__ digits,
+// here.  The k-th long row i of window w, suffix t, is listed as (ll_t,
+// ll_row, ll_key)[w kWindow + k] = (t, i, its key), so a unit's long rows
+// are a few contiguous runs.
+__global__ void __launch_bounds__(kThreads) sa_unit_begin_kernel(const uint32_t* __restrict__ text,
+                                                                 const uint32_t* __restrict__ term,
+                                                                 unsigned long long base,
+                                                                 const uint32_t* __restrict__ digits,
                                                                  const uint32_t* __restrict__ vals, uint32_t n,
                                                                  uint32_t nwin, Units u, uint32_t* __restrict__ sa,
                                                                  uint32_t* __restrict__ rank,
                                                                  uint32_t* __restrict__ ll_t,
                                                                  uint32_t* __restrict__ ll_row,
+                                                                 unsigned long long* __restrict__ ll_key,
                                                                  uint32_t* __restrict__ d_err) {
     const int lane = threadIdx.x & 31;
     const uint32_t warps = gridDim.x * (kThreads / 32);
@@ -189,6 +194,7 @@ __global__ void __launch_bounds__(kThreads) sa_unit_begin_kernel(const uint32_t*
                 const uint32_t k = lo + lct + __popc(bl & ((1u << lane) - 1u));
                 ll_t[k] = t;
                 ll_row[k] = i;
+                ll_key[k] = initial_key(text, term, base + (t < n ? t : 0u));
             }
             if (first == kNone) {
                 if (bb) {
@@ -611,15 +617,15 @@ __device__ __forceinline__ void batch_write_unsorted(Batch& b, uint32_t k, uint3
 
 // Local sort of the units with at most kLCap long suffixes, a batch of
 // consecutive units per CTA step.  A batch's long rows are the runs
-// (ll_t, ll_row)[x kWindow + k0 ...) of the windows x = ws, ws + 1, ... from
+// (ll_t, ll_row, ll_key)[x kWindow + k0 ...) of the windows x = ws, ws + 1, ... from
 // its first unit start ws (k0 = lcb in window ws, 0 after), in row order;
 // the sorted j-th long suffix takes the j-th of those rows, srow[j].  A
 // global-path unit ends a batch and is skipped.
 __global__ void __launch_bounds__(kLThreads, 2) sa_local_sort_kernel(
-    const uint32_t* __restrict__ text, const uint32_t* __restrict__ term, unsigned long long base, uint32_t n,
-    const uint32_t* __restrict__ ll_t, const uint32_t* __restrict__ ll_row, Units u, uint32_t nwin,
-    uint32_t* __restrict__ sa, uint32_t* __restrict__ rank, uint32_t* __restrict__ loc_act,
-    uint32_t* __restrict__ d_cnt, uint32_t* __restrict__ d_err) {
+    uint32_t n, const uint32_t* __restrict__ ll_t, const uint32_t* __restrict__ ll_row,
+    const unsigned long long* __restrict__ ll_key, Units u, uint32_t nwin, uint32_t* __restrict__ sa,
+    uint32_t* __restrict__ rank, uint32_t* __restrict__ loc_act, uint32_t* __restrict__ d_cnt,
+    uint32_t* __restrict__ d_err) {
     extern __shared__ __align__(16) unsigned char smem[];
     unsigned long long* skey = reinterpret_cast<unsigned long long*>(smem);
     uint32_t* sval = reinterpret_cast<uint32_t*>(skey + kLSlots);
@@ -697,13 +703,10 @@ __global__ void __launch_bounds__(kLThreads, 2) sa_local_sort_kernel(
         for (int j = 0; j < kLItems; ++j) {
             v[j] = src[j] != kNone ? ll_t[src[j]] : 0u;
             rw[j] = src[j] != kNone ? ll_row[src[j]] : 0u;
+            kk[j] = src[j] != kNone ? ll_key[src[j]] : ~0ull;
         }
 #pragma unroll
-        for (int j = 0; j < kLItems; ++j) {
-            if (v[j] >= n) atomicOr(d_err, 64u);  // an out-of-range t is skipped when written back
-            kk[j] = g0 + j < cnt ? initial_key(text, term, base + (v[j] < n ? v[j] : 0u)) : ~0ull;
-            srow[skew(g0 + j)] = rw[j];
-        }
+        for (int j = 0; j < kLItems; ++j) srow[skew(g0 + j)] = rw[j];  // an out-of-range t is skipped when written
         block_sort<kBucketShift>(kk, v, cnt, skey, sval, sseg);  // segments: buckets
 
         // group heads: a new key, or a key that contains its terminator
@@ -1166,15 +1169,17 @@ void suffix_sort_block(Launcher& L, const uint32_t* text, const uint32_t* term, 
     // used before the first round)
     uint32_t* ll_t = b.loc_next;
     uint32_t* ll_row = b.act_suf[0];
-    SBWT_LAUNCH(L, "sa_unit_begin", (double)n * 16 + 32.0 * nwin, 0, nullptr, sa_unit_begin_kernel, warp_grid,
-                kThreads, 0, digits, tsorted, n, nwin, units, b.sa, b.rank, ll_t, ll_row, b.err);
+    // the keys of the long rows go to the 64-bit array the digits are not in
+    unsigned long long* ll_key = da ? b.keys : b.keys_alt;
+    SBWT_LAUNCH(L, "sa_unit_begin", (double)n * 24 + 32.0 * nwin, 0, nullptr, sa_unit_begin_kernel, warp_grid,
+                kThreads, 0, text, term, (unsigned long long)base, digits, tsorted, n, nwin, units, b.sa, b.rank,
+                ll_t, ll_row, ll_key, b.err);
     SBWT_LAUNCH(L, "sa_unit_scan", 96.0 * nwin, 0, nullptr, sa_unit_scan_kernel, 1, kScanThreads, 0, units, nwin, n,
                 d_large, b.count_log + 3, (int)rounds + 1, 2);
-    // per long row: its list entry, SA and rank writes (the key words come
-    // from the packed text); per unsorted member the compacted entry
-    SBWT_LAUNCH(L, "sa_local_sort", (double)n * 16, 4, b.count_log + 3, sa_local_sort_kernel,
-                grid_of(g_local_ctas[dev], nwin), kLThreads, kLocalSortSmem, text, term, (unsigned long long)base, n,
-                ll_t, ll_row, units, nwin, b.sa, b.rank, b.loc_act, b.count_log + 3, b.err);
+    // per long row: its list entry (t, row, key), SA and rank writes; per
+    // unsorted member the compacted entry
+    SBWT_LAUNCH(L, "sa_local_sort", (double)n * 24, 4, b.count_log + 3, sa_local_sort_kernel,
+                grid_of(g_local_ctas[dev], nwin), kLThreads, kLocalSortSmem, n, ll_t, ll_row, ll_key, units, nwin, b.sa, b.rank, b.loc_act, b.count_log + 3, b.err);
     SBWT_LAUNCH(L, "sa_large_gather", 32.0 * nwin, 20, d_large, sa_large_gather_kernel, grid_of(g_local_ctas[dev], nwin),
                 kThreads, 0, text, term, (unsigned long long)base, n, tsorted, units, nwin, b.keys, tfree,
                 b.act_pos[0]);
