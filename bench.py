@@ -216,14 +216,26 @@ def measure_serving(sb, idx, requests, rate_rps=None, seed=7):
             "offered_rps": rate_rps}
 
 
-def serving_report(sb, idx, requests):
+def serving_report(sb, fresh, requests):
     """Closed loop for the sustained rate, then Poisson arrivals at 0.5x and
-    0.9x of it (in requests/s); the index keeps growing across the runs."""
-    closed = measure_serving(sb, idx, requests)
-    sustained_rps = closed["requests"] / (closed["bases"] / closed["Mbps"] / 1e6)
-    out = {"sustained": closed}
-    for f in (0.5, 0.9):
-        out[f"load_{f}"] = measure_serving(sb, idx, requests, rate_rps=f * sustained_rps, seed=int(f * 100))
+    0.9x of it (in requests/s).  Each run serves a freshly built resident
+    index (fresh() builds one), so every run starts from the same index
+    size; each run reports the index's memory when it ends."""
+    out = {}
+    rates = [None, 0.5, 0.9]
+    sustained_rps = None
+    for f in rates:
+        idx = fresh()
+        rate = None if f is None else f * sustained_rps
+        r = measure_serving(sb, idx, requests, rate_rps=rate, seed=7 if f is None else int(f * 100))
+        hbm, host = sb.sbwt_memory(idx.handle)
+        r["memory_after"] = {"hbm": hbm, "host": host}
+        idx.close()
+        if f is None:
+            sustained_rps = r["requests"] / (r["bases"] / r["Mbps"] / 1e6)
+            out["sustained"] = r
+        else:
+            out[f"load_{f}"] = r
     return out
 
 
@@ -433,9 +445,13 @@ def run_gb300(args):
         sizes = np.exp(rs.uniform(np.log(10_000), np.log(200_000), size=24)).astype(np.int64)
         requests = [readgen.sampled_reads(g, int(mm), rs.integers(100, 151, size=int(mm)), 0.01, 500 + i)
                     for i, mm in enumerate(sizes)]
-        idx.reset()
-        idx.append_device(d_reads.data_ptr(), d_off.data_ptr(), w.m)
-        served = serving_report(sb, idx, requests)
+        def fresh():
+            ix = sb.SetBWT(b"ACGT", block_suffixes=w.block_suffixes, index_bits=w.index_bits,
+                           stream=stream.cuda_stream, device=local)
+            ix.append_device(d_reads.data_ptr(), d_off.data_ptr(), w.m)
+            return ix
+
+        served = serving_report(sb, fresh, requests)
 
     if rank != 0:
         if dist:
@@ -511,12 +527,19 @@ def run_serve_workload(args):
     t = time.perf_counter()
     idx.append_device(d_reads.data_ptr(), d_off.data_ptr(), resident.m)
     build_s = time.perf_counter() - t
-    del d_reads, d_off
-    torch.cuda.empty_cache()
     hbm, host = sb.sbwt_memory(idx.handle)
-    report = serving_report(sb, idx, requests)
     n, m = idx.size()
     idx.close()
+
+    def fresh():
+        ix = sb.SetBWT(b"ACGT", hbm_budget=8 << 30, index_bits=64, block_suffixes=1 << 25,
+                       stream=stream.cuda_stream, device=local)
+        ix.append_device(d_reads.data_ptr(), d_off.data_ptr(), resident.m)
+        return ix
+
+    report = serving_report(sb, fresh, requests)
+    del d_reads, d_off
+    torch.cuda.empty_cache()
 
     # host tier: dictionaries in pinned host memory under a tight budget
     small = readgen.Workload("resident-2Mx100", resident.reads[: int(resident.offsets[2_000_000])],
@@ -537,7 +560,7 @@ def run_serve_workload(args):
         "config": {"workload": resident.name, "requests": len(requests), "hbm_budget": 8 << 30,
                    "block_suffixes": 1 << 25},
         "resident_build_s": build_s, "resident_build_Mbps": resident.bases / build_s / 1e6,
-        "generation_s": gen_s, "index_rows_after": n, "index_reads_after": m,
+        "generation_s": gen_s, "resident_rows": n, "resident_reads": m,
         "memory_after_build": {"hbm": hbm, "host": host},
         "serving": report,
         "host_tier": {"resident": small.name, "hbm_budget": 512 << 20, "build_s": build2_s,
