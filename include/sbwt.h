@@ -51,6 +51,7 @@ extern "C" {
 #define SBWT_ENOTSUP (-5)  /* option not supported by this build */
 #define SBWT_EBUSY (-6)    /* the index is serving: only submit/wait are allowed */
 #define SBWT_ETIMEDOUT (-7) /* sbwt_wait: the request is not done yet */
+#define SBWT_EIO (-8)       /* sbwt_save / sbwt_load: the file cannot be written or read */
 
 typedef struct sbwt_index sbwt_index; /* opaque, owned by the library */
 
@@ -232,6 +233,27 @@ int sbwt_wait(sbwt_index *idx, uint64_t ticket, uint64_t timeout_us, uint64_t *f
 /* Finishes the submitted requests and stops serving; returns SBWT_EDEVICE if
  * a device error ended serving early, else SBWT_OK. */
 int sbwt_serve_stop(sbwt_index *idx);
+
+/* ---- Persistence ---------------------------------------------------------
+ * The paper keeps B_ext in memory for the whole construction (Section 5);
+ * persisting it is an addition.  sbwt_save writes the committed index --
+ * the rank dictionary of B (occurrence blocks of 64 rows, 64-bit superblock
+ * counters, C[] as Lemma 1 uses them), n, m, the alphabet and the index
+ * width -- to the file `path` (created or truncated), with a header and a
+ * 64-bit FNV-1a checksum of everything before it.  Little-endian, as laid
+ * out on the device (the same on x86-64 and Arm).  Errors: SBWT_EINVAL (NULL
+ * argument), SBWT_EBUSY (serving), SBWT_EDEVICE, SBWT_EIO.
+ *
+ * sbwt_load creates a new index from such a file, as sbwt_create_ex with the
+ * file's alphabet would (`opt` as there; its index_bits, when 0, is the
+ * file's), and places the dictionary under `hbm_budget_bytes` (in the host
+ * tier if the budget asks for it).  The loaded index answers rank, count and
+ * get_bwt like the saved one, and later appends continue its read ids.  The
+ * file is checked (magic, version, sizes, checksum) before any device work:
+ * SBWT_EIO (cannot open or read), SBWT_EINVAL (not an index file, or damaged;
+ * bad options), SBWT_ENOMEM, SBWT_EDEVICE.  On error *out is NULL. */
+int sbwt_save(sbwt_index *idx, const char *path);
+int sbwt_load(const char *path, size_t hbm_budget_bytes, const sbwt_options *opt, sbwt_index **out);
 
 /* ---- BWT of a small read set without allocating -------------------------
  * The paper has no counterpart to this call.  It is for callers that cannot

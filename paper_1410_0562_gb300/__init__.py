@@ -30,6 +30,7 @@ SBWT_EDEVICE = -4
 SBWT_ENOTSUP = -5
 SBWT_EBUSY = -6
 SBWT_ETIMEDOUT = -7
+SBWT_EIO = -8
 
 SBWT_STAGE_SA = 0
 SBWT_STAGE_BINT = 1
@@ -42,7 +43,7 @@ EXPORTS = (
     "sbwt_rank_batch", "sbwt_count", "sbwt_memory", "sbwt_size", "sbwt_reset", "sbwt_destroy", "sbwt_strerror", "sbwt_get_stream",
     "sbwt_set_capture", "sbwt_get_stage", "sbwt_set_profiling", "sbwt_set_profiling_only", "sbwt_get_kernel_stats",
     "sbwt_reset_kernel_stats", "sbwt_set_graph_replay", "sbwt_autotune_block_suffixes", "sbwt_serve_start",
-    "sbwt_submit", "sbwt_wait", "sbwt_serve_stop", "sbwt_bwt_noalloc",
+    "sbwt_submit", "sbwt_wait", "sbwt_serve_stop", "sbwt_save", "sbwt_load", "sbwt_bwt_noalloc",
 )
 
 #: most suffixes (reads + one terminator each) sbwt_bwt_noalloc accepts
@@ -114,6 +115,8 @@ def load() -> ctypes.CDLL:
             "sbwt_submit": ([P, P, P, U64, ctypes.POINTER(U64)], I),
             "sbwt_wait": ([P, U64, U64, ctypes.POINTER(U64), ctypes.POINTER(ctypes.c_double)], I),
             "sbwt_serve_stop": ([P], I),
+            "sbwt_save": ([P, ctypes.c_char_p], I),
+            "sbwt_load": ([ctypes.c_char_p, SZ, ctypes.POINTER(sbwt_options), ctypes.POINTER(P)], I),
             "sbwt_bwt_noalloc": ([ctypes.c_char_p, P, P, U64, P, U64, ctypes.POINTER(U64), P], I),
         }
         for name, (args, res) in sig.items():
@@ -147,6 +150,20 @@ def sbwt_create(alphabet: bytes = b"ACGT", hbm_budget: int = 0):
     h = ctypes.c_void_p()
     _check(load().sbwt_create(alphabet, hbm_budget, ctypes.byref(h)), "sbwt_create")
     return h
+
+
+def sbwt_save(h, path) -> None:
+    """Writes the committed index to the file `path`."""
+    _check(load().sbwt_save(h, os.fsencode(path)), "sbwt_save")
+
+
+def sbwt_load(path, hbm_budget: int = 0, index_bits: int = 0, block_suffixes: int = 0, stream: int = 0,
+              device: int = -1, host_tier: int = 0):
+    """A new index handle built from a file written by sbwt_save."""
+    opt = sbwt_options(index_bits, block_suffixes, stream or None, device, host_tier)
+    out = ctypes.c_void_p()
+    _check(load().sbwt_load(os.fsencode(path), hbm_budget, ctypes.byref(opt), ctypes.byref(out)), "sbwt_load")
+    return out
 
 
 def sbwt_create_ex(alphabet: bytes = b"ACGT", hbm_budget: int = 0, index_bits: int = 0, block_suffixes: int = 0,
@@ -334,6 +351,19 @@ class SetBWT:
                  block_suffixes: int = 0, stream: int = 0, device: int = -1, host_tier: int = 0):
         self.alphabet = alphabet
         self._h = sbwt_create_ex(alphabet, hbm_budget, index_bits, block_suffixes, stream, device, host_tier)
+
+    @classmethod
+    def load(cls, path, hbm_budget: int = 0, index_bits: int = 0, block_suffixes: int = 0, stream: int = 0,
+             device: int = -1, host_tier: int = 0) -> "SetBWT":
+        """An index read from a file that save() wrote."""
+        self = cls.__new__(cls)
+        self._h = sbwt_load(path, hbm_budget, index_bits, block_suffixes, stream, device, host_tier)
+        self.alphabet = None
+        return self
+
+    def save(self, path) -> "SetBWT":
+        sbwt_save(self._h, path)
+        return self
 
     @property
     def handle(self):

@@ -579,6 +579,41 @@ int parse_alphabet(const char* alphabet, sbwt_index* idx) {
     return SBWT_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Index files (sbwt_save / sbwt_load): a header, the committed dictionary
+// (occurrence blocks, superblock counters, C[]), then a 64-bit FNV-1a
+// checksum of everything before it.
+// ---------------------------------------------------------------------------
+constexpr char kFileMagic[8] = {'S', 'B', 'W', 'T', 'I', 'D', 'X', '1'};
+constexpr uint32_t kFileVersion = 1;
+
+struct FileHeader {
+    char magic[8];
+    uint32_t version;
+    uint32_t sigma;
+    uint8_t alphabet[4];
+    uint32_t index_bits;
+    uint64_t n, m;
+    uint64_t n_blocks, n_supers;  // array lengths: dict_blocks(n), dict_supers(n)
+    uint64_t reserved[4];
+};
+static_assert(sizeof(FileHeader) == 88, "fixed header layout");
+
+struct Fnv1a {
+    uint64_t h = 1469598103934665603ull;
+    void add(const void* p, size_t n) {
+        const uint8_t* b = static_cast<const uint8_t*>(p);
+        for (size_t i = 0; i < n; ++i) h = (h ^ b[i]) * 1099511628211ull;
+    }
+};
+
+struct File {
+    FILE* f = nullptr;
+    ~File() {
+        if (f) fclose(f);
+    }
+};
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -726,6 +761,7 @@ const char* sbwt_strerror(int code) {
         case SBWT_ENOTSUP: return "not supported";
         case SBWT_EBUSY: return "the index is serving requests";
         case SBWT_ETIMEDOUT: return "not done yet";
+        case SBWT_EIO: return "cannot read or write the file";
         default: return "unknown error";
     }
 }
@@ -929,6 +965,115 @@ int sbwt_reset(sbwt_index* idx) {
     zero_async(d.super, 32, idx->stream);
     zero_async(d.C, 32, idx->stream);
     if (cudaStreamSynchronize(idx->stream) != cudaSuccess) return SBWT_EDEVICE;
+    return SBWT_OK;
+}
+
+int sbwt_save(sbwt_index* idx, const char* path) {
+    if (!idx || !path) return SBWT_EINVAL;
+    if (busy(idx)) return SBWT_EBUSY;
+    FileHeader h = {};
+    memcpy(h.magic, kFileMagic, sizeof(h.magic));
+    h.version = kFileVersion;
+    h.sigma = (uint32_t)idx->sigma;
+    memcpy(h.alphabet, idx->alphabet, 4);
+    h.index_bits = idx->index_bits;
+    h.n = idx->n;
+    h.m = idx->m;
+    h.n_blocks = dict_blocks(idx->n);
+    h.n_supers = dict_supers(idx->n);
+    std::vector<OccBlock> blocks(h.n_blocks);
+    std::vector<unsigned long long> super(4 * h.n_supers), C(4, 0ull);
+    if (idx->dev_ready) {  // else the index is empty: all zero
+        if (set_device(idx) || cudaStreamSynchronize(idx->stream) != cudaSuccess) return SBWT_EDEVICE;
+        const Dict& d = idx->dict[idx->cur];
+        if (cudaMemcpy(blocks.data(), d.blocks.p, blocks.size() * sizeof(OccBlock), cudaMemcpyDeviceToHost) !=
+                cudaSuccess ||
+            cudaMemcpy(super.data(), d.super.p, super.size() * 8, cudaMemcpyDeviceToHost) != cudaSuccess ||
+            cudaMemcpy(C.data(), d.C.p, 32, cudaMemcpyDeviceToHost) != cudaSuccess) {
+            cudaGetLastError();
+            return SBWT_EDEVICE;
+        }
+    } else {
+        memset(blocks.data(), 0, blocks.size() * sizeof(OccBlock));
+    }
+    Fnv1a sum;
+    File out;
+    out.f = fopen(path, "wb");
+    if (!out.f) return SBWT_EIO;
+    auto put = [&](const void* p, size_t n) {
+        sum.add(p, n);
+        return fwrite(p, 1, n, out.f) == n;
+    };
+    bool ok = put(&h, sizeof(h)) && put(blocks.data(), blocks.size() * sizeof(OccBlock)) &&
+              put(super.data(), super.size() * 8) && put(C.data(), 32);
+    const uint64_t digest = sum.h;
+    ok = ok && fwrite(&digest, 1, 8, out.f) == 8;
+    ok = fclose(out.f) == 0 && ok;
+    out.f = nullptr;
+    return ok ? SBWT_OK : SBWT_EIO;
+}
+
+int sbwt_load(const char* path, size_t hbm_budget_bytes, const sbwt_options* opt, sbwt_index** out) {
+    if (!out) return SBWT_EINVAL;
+    *out = nullptr;
+    if (!path) return SBWT_EINVAL;
+    File in;
+    in.f = fopen(path, "rb");
+    if (!in.f) return SBWT_EIO;
+    FileHeader h;
+    if (fread(&h, 1, sizeof(h), in.f) != sizeof(h)) return SBWT_EIO;
+    if (memcmp(h.magic, kFileMagic, sizeof(h.magic)) != 0 || h.version != kFileVersion) return SBWT_EINVAL;
+    if (h.sigma < 1 || h.sigma > 4 || (h.index_bits != 0 && h.index_bits != 32 && h.index_bits != 64) ||
+        h.n_blocks != dict_blocks(h.n) || h.n_supers != dict_supers(h.n) || h.m > h.n)
+        return SBWT_EINVAL;
+    // the arrays must be exactly what the rest of the file holds
+    if (fseek(in.f, 0, SEEK_END) != 0) return SBWT_EIO;
+    const long size = ftell(in.f);
+    const uint64_t want = sizeof(h) + h.n_blocks * sizeof(OccBlock) + h.n_supers * 32 + 32 + 8;
+    if (size < 0 || (uint64_t)size != want) return SBWT_EINVAL;
+    if (fseek(in.f, (long)sizeof(h), SEEK_SET) != 0) return SBWT_EIO;
+    std::vector<OccBlock> blocks(h.n_blocks);
+    std::vector<unsigned long long> super(4 * h.n_supers), C(4);
+    uint64_t digest = 0;
+    if (fread(blocks.data(), 1, blocks.size() * sizeof(OccBlock), in.f) != blocks.size() * sizeof(OccBlock) ||
+        fread(super.data(), 1, super.size() * 8, in.f) != super.size() * 8 || fread(C.data(), 1, 32, in.f) != 32 ||
+        fread(&digest, 1, 8, in.f) != 8)
+        return SBWT_EIO;
+    Fnv1a sum;
+    sum.add(&h, sizeof(h));
+    sum.add(blocks.data(), blocks.size() * sizeof(OccBlock));
+    sum.add(super.data(), super.size() * 8);
+    sum.add(C.data(), 32);
+    if (sum.h != digest) return SBWT_EINVAL;
+
+    char alpha[5] = {0, 0, 0, 0, 0};
+    memcpy(alpha, h.alphabet, h.sigma);
+    sbwt_options o = {};
+    if (opt) o = *opt;
+    if (o.index_bits == 0) o.index_bits = h.index_bits;
+    if (h.n >= 0xFFFFFFFFull && o.index_bits == 32) return SBWT_EINVAL;
+    sbwt_index* idx = nullptr;
+    if (int rc = sbwt_create_ex(alpha, hbm_budget_bytes, &o, &idx)) return rc;
+    auto fail = [&](int rc) {
+        sbwt_destroy(idx);
+        return rc;
+    };
+    if (int rc = device_init(idx)) return fail(rc);
+    Dict& d = idx->dict[idx->cur];
+    if (int rc = reserve(idx, {{&d.blocks, blocks.size() * sizeof(OccBlock), true},
+                               {&d.super, super.size() * 8, true},
+                               {&d.C, 32, true}}))
+        return fail(rc);
+    if (cudaMemcpy(d.blocks.p, blocks.data(), blocks.size() * sizeof(OccBlock), cudaMemcpyHostToDevice) !=
+            cudaSuccess ||
+        cudaMemcpy(d.super.p, super.data(), super.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(d.C.p, C.data(), 32, cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(SBWT_EDEVICE);
+    }
+    idx->n = h.n;
+    idx->m = h.m;
+    *out = idx;
     return SBWT_OK;
 }
 

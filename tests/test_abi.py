@@ -106,3 +106,41 @@ def test_no_cpu_fallback_without_a_device(lib):
     assert e.value.code == sb.SBWT_EDEVICE
     assert sb.sbwt_size(h) == (0, 0)
     sb.sbwt_destroy(h)
+
+
+def test_load_checks_the_file_before_any_device_work(lib, tmp_path):
+    """Missing file -> SBWT_EIO; not an index file, a flipped byte or a
+    truncated file -> SBWT_EINVAL; a valid file of an empty index reaches the
+    device step (SBWT_EDEVICE here, without a GPU)."""
+    with pytest.raises(sb.SbwtError) as e:
+        sb.SetBWT.load(tmp_path / "missing.sbwt")
+    assert e.value.code == sb.SBWT_EIO
+    junk = tmp_path / "junk.sbwt"
+    junk.write_bytes(b"not an index" * 20)
+    with pytest.raises(sb.SbwtError) as e:
+        sb.SetBWT.load(junk)
+    assert e.value.code == sb.SBWT_EINVAL
+    good = tmp_path / "empty.sbwt"
+    sb.SetBWT(b"ACGT").save(good)  # never appended: no device work
+    data = bytearray(good.read_bytes())
+    assert data[:8] == b"SBWTIDX1"
+    flipped = tmp_path / "flipped.sbwt"
+    bad = bytearray(data)
+    bad[100] ^= 1
+    flipped.write_bytes(bytes(bad))
+    truncated = tmp_path / "truncated.sbwt"
+    truncated.write_bytes(bytes(data[:-9]))
+    for path in (flipped, truncated):
+        with pytest.raises(sb.SbwtError) as e:
+            sb.SetBWT.load(path)
+        assert e.value.code == sb.SBWT_EINVAL
+    import torch
+    if not torch.cuda.is_available():
+        with pytest.raises(sb.SbwtError) as e:
+            sb.SetBWT.load(good)
+        assert e.value.code == sb.SBWT_EDEVICE
+
+
+def test_save_rejects_null_path(lib):
+    idx = sb.SetBWT(b"ACGT")
+    assert lib.sbwt_save(idx.handle, None) == sb.SBWT_EINVAL
