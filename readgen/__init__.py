@@ -202,6 +202,17 @@ def long(n_reads: int = 20_000, genome_size: int = 100_000_000, seed_genome: int
     return Workload(f"long-{n_reads}xlognormal10k-g{genome_size}", reads, off, 0, 64, (0, n_reads))
 
 
+def repetitive(n_reads: int = 300_000, genome_size: int = 2_000, seed_genome: int = 0x14100562 + 6,
+               seed_reads: int = 0x05621410 + 6) -> Workload:
+    """300k x 100 bp reads from a 2 kbp i.i.d. genome (~15,000x coverage),
+    1% substitutions: every bucket of a few leading symbols and most groups
+    of equal 29-symbol prefixes hold thousands of suffixes.  One block of
+    2^25 suffixes; 64-bit indices."""
+    g = genome(genome_size, seed_genome)
+    reads, off = sampled_reads(g, n_reads, 100, 0.01, seed_reads)
+    return Workload(f"repetitive-{n_reads}x100-g{genome_size}", reads, off, 1 << 25, 64, (0, n_reads))
+
+
 def serving(n_resident: int = 20_000_000, genome_size: int = 200_000_000, n_requests: int = 48,
             seed_genome: int = 0x14100562 + 5, seed_reads: int = 0x05621410 + 5, max_request: int = 1_000_000):
     """The serving workload: a resident set of n_resident x 100 bp reads (1%

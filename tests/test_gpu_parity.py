@@ -297,6 +297,16 @@ def test_full_size_batched_and_long_reads(name):
     check_full_size(w, idx.bwt(), samples=2)
 
 
+def test_full_size_repetitive_reads():
+    """Reads from a 2 kbp genome at ~15,000x coverage: the buckets and most
+    groups overflow the CTA-local sorts, so the device-wide path (one
+    cooperative radix sort per round) does the work at full size."""
+    w = readgen.repetitive()
+    idx = gpu_bwt(w.reads, w.offsets, M=w.block_suffixes, index_bits=w.index_bits)
+    assert idx.size() == (oracle.num_suffixes(w.offsets), w.m)
+    check_full_size(w, idx.bwt(), samples=2)
+
+
 def test_graph_replay_matches_eager():
     """The batched form: repeated identical appends are captured into a CUDA
     graph and replayed; every replay gives the oracle's B."""
