@@ -97,6 +97,15 @@ int sbwt_create_ex(const char *alphabet, size_t hbm_budget_bytes, const sbwt_opt
  * alphabet or bad offsets give SBWT_EINVAL and leave the index unchanged.
  * Blocks until the index holds the new reads. */
 int sbwt_append(sbwt_index *idx, const uint8_t *reads, const uint64_t *offsets, uint64_t m);
+/* Like sbwt_append, but the m reads go BEFORE every read already in the
+ * index: they take ids 0 .. m-1 (in the given order) and the old reads'
+ * ids move up by m.  This is the reverse order Section 2 allows ("reversal
+ * is also possible"): Algorithm 1 runs over the new blocks from the last to
+ * the first, and Algorithm 2 starts every new read at i := 0, since a new
+ * terminator is smaller than every old one.  The result equals one append
+ * of (new reads ++ old reads).  Same arguments, conventions and errors as
+ * sbwt_append. */
+int sbwt_prepend(sbwt_index *idx, const uint8_t *reads, const uint64_t *offsets, uint64_t m);
 
 /* As sbwt_append, but `d_reads` (offsets[m] bytes) and `d_offsets` (m+1
  * values) are DEVICE pointers on the index's GPU.  The offsets are copied to

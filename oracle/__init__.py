@@ -89,6 +89,8 @@ def _declare(lib):
     lib.oracle_insert.restype = I
     lib.oracle_setbwte.argtypes = [P, P, U64, P, I, P, U64, P]
     lib.oracle_setbwte.restype = I
+    lib.oracle_setbwte_reverse.argtypes = [P, P, U64, P, I, P, U64, P]
+    lib.oracle_setbwte_reverse.restype = I
     lib.oracle_lf_invert.argtypes = [P, U64, U64, P, I, P, U64, P]
     lib.oracle_lf_invert.restype = I
     lib.oracle_lf_invert_sampled.argtypes = [P, U64, U64, P, I, P, U64, P]
@@ -214,14 +216,17 @@ def insert(B_ext, bint, g_sa) -> np.ndarray:
     return out[: len(B_ext) + len(bint)]
 
 
-def setbwte(reads, offsets, bounds, alphabet: bytes = b"ACGT") -> np.ndarray:
-    """Algorithm 1 over block boundaries 0 = bounds[0] < ... < bounds[K] = m."""
+def setbwte(reads, offsets, bounds, alphabet: bytes = b"ACGT", reverse: bool = False) -> np.ndarray:
+    """Algorithm 1 over block boundaries 0 = bounds[0] < ... < bounds[K] = m;
+    reverse=True runs the blocks from the last to the first, each going
+    before the reads already inserted (Algorithm 2 then starts at i := 0)."""
     reads, offsets, alpha, bounds = _u8(reads), _u64(offsets), _u8(alphabet), _u64(bounds)
     m = len(offsets) - 1
     n = num_suffixes(offsets)
     out = np.zeros(max(n, 1), dtype=np.uint8)
-    _check(_load().oracle_setbwte(_ptr(reads), _ptr(offsets), m, _ptr(alpha), len(alpha), _ptr(bounds),
-                                  len(bounds) - 1, _ptr(out)), "oracle_setbwte")
+    fn = _load().oracle_setbwte_reverse if reverse else _load().oracle_setbwte
+    _check(fn(_ptr(reads), _ptr(offsets), m, _ptr(alpha), len(alpha), _ptr(bounds), len(bounds) - 1, _ptr(out)),
+           "oracle_setbwte")
     return out[:n]
 
 

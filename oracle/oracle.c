@@ -28,7 +28,9 @@
  *   - oracle_insert: Insert of Algorithm 1 / Section 5 as a stable merge:
  *     new symbol i lands on row g_sa[i] + i, old rows keep their order.
  *   - oracle_setbwte: Algorithm 1 end to end, block by block, built from the
- *     four functions above.
+ *     four functions above; oracle_setbwte_reverse: the same loop over the
+ *     blocks from the last to the first (Section 2 allows the reversal),
+ *     each block going before the reads already inserted.
  *   - oracle_lf_invert / oracle_lf_invert_sampled: recover every read from B
  *     by LF steps (the FM-index inversion that Lemma 1 rests on), with a full
  *     prefix-count table or with counts every 64 rows.
@@ -52,6 +54,9 @@
  *     go before old row g_sa; the final row of new symbol i is g_sa[i]+i.
  *   - Symbols are ordered by byte value (the alphabet is given in strictly
  *     increasing byte order); a byte outside the alphabet is an error.
+ *   - Reverse order: a block added before every read already in B_ext has
+ *     terminators smaller than every old one, so Algorithm 2 starts each of
+ *     its reads at i := 0.
  *
  * Layout conventions (plain, nothing packed):
  *   reads   : the bytes of all reads, concatenated; read r is
@@ -71,7 +76,8 @@
  *   1: Algorithm 2 starts at i := n_ext      2: terminator ties reversed
  *   3: a shorter suffix sorts after a longer one with the same prefix
  *   4: Insert puts new symbols after the old row g_sa (tie order flipped)
- *   5: C[c] leaves out the terminators                                     */
+ *   5: C[c] leaves out the terminators
+ *   6: the reverse order starts Algorithm 2 at i := m_ext, not 0            */
 #ifndef ORACLE_PLANT
 #define ORACLE_PLANT 0
 #endif
@@ -282,10 +288,12 @@ static int bcode(uint8_t b, const uint8_t *alphabet, int sigma) {
  * i := C[c] + rank(c, i, B_ext) with c = P[k].  rank is read from a full
  * prefix-count table, C[c] counts every smaller symbol of B_ext including
  * its m_ext terminators. */
-int oracle_block_g_lemma1(const uint8_t *B_ext, uint64_t n_ext,
+/* Algorithm 2 for the reads [j0, j1); `before` = 1 when the block goes
+ * before every read of B_ext (the start rank is then 0, else m_ext). */
+static int block_g_lemma1(const uint8_t *B_ext, uint64_t n_ext,
                           const uint8_t *reads, const uint64_t *offsets,
                           uint64_t j0, uint64_t j1, const uint8_t *alphabet,
-                          int sigma, uint64_t *g) {
+                          int sigma, int before, uint64_t *g) {
     g_reads = reads;
     g_offsets = offsets;
     uint64_t *occ = (uint64_t *)calloc((n_ext + 1) * (size_t)(sigma + 1), sizeof(uint64_t));
@@ -311,8 +319,11 @@ int oracle_block_g_lemma1(const uint8_t *B_ext, uint64_t n_ext,
         uint64_t k = read_len(j);
 #if ORACLE_PLANT == 1
         uint64_t i = n_ext;
-#else
+#elif ORACLE_PLANT == 6
         uint64_t i = m_ext;
+        (void)before;
+#else
+        uint64_t i = before ? 0 : m_ext;
 #endif
         g[start + k] = i;
         while (k > 0) {
@@ -328,6 +339,13 @@ int oracle_block_g_lemma1(const uint8_t *B_ext, uint64_t n_ext,
     }
     free(occ);
     return ORACLE_OK;
+}
+
+int oracle_block_g_lemma1(const uint8_t *B_ext, uint64_t n_ext,
+                          const uint8_t *reads, const uint64_t *offsets,
+                          uint64_t j0, uint64_t j1, const uint8_t *alphabet,
+                          int sigma, uint64_t *g) {
+    return block_g_lemma1(B_ext, n_ext, reads, offsets, j0, j1, alphabet, sigma, 0, g);
 }
 
 /* Insert (Algorithm 1, Section 5) as a stable merge: new symbol i goes to row
@@ -361,9 +379,9 @@ int oracle_insert(const uint8_t *B_ext, uint64_t n_ext, const uint8_t *bint,
 /* Algorithm 1 end to end over the given block boundaries
  * 0 = bounds[0] < ... < bounds[K] = m: per block ConstructSA, B_int,
  * ComputeRanks (Lemma 1), the g[SA_int] reordering and Insert. */
-int oracle_setbwte(const uint8_t *reads, const uint64_t *offsets, uint64_t m,
+static int setbwte(const uint8_t *reads, const uint64_t *offsets, uint64_t m,
                    const uint8_t *alphabet, int sigma, const uint64_t *bounds,
-                   uint64_t K, uint8_t *B) {
+                   uint64_t K, int reverse, uint8_t *B) {
     int rc = validate(reads, offsets, m, alphabet, sigma);
     if (rc) return rc;
     if (K == 0 || bounds[0] != 0 || bounds[K] != m) return ORACLE_EINVAL;
@@ -376,7 +394,8 @@ int oracle_setbwte(const uint8_t *reads, const uint64_t *offsets, uint64_t m,
         return ORACLE_ENOMEM;
     }
     uint64_t n_ext = 0;
-    for (uint64_t b = 0; b < K; ++b) {
+    for (uint64_t q = 0; q < K; ++q) {
+        uint64_t b = reverse ? K - 1 - q : q;
         uint64_t j0 = bounds[b], j1 = bounds[b + 1];
         if (j1 < j0) rc = ORACLE_EINVAL;
         if (rc) break;
@@ -388,7 +407,7 @@ int oracle_setbwte(const uint8_t *reads, const uint64_t *offsets, uint64_t m,
         if (!sa || !g || !gsa || !bint) rc = ORACLE_ENOMEM;
         if (!rc) rc = oracle_block_sa(reads, offsets, j0, j1, sa);
         if (!rc) rc = oracle_block_bint(reads, offsets, j0, j1, sa, n_int, bint);
-        if (!rc) rc = oracle_block_g_lemma1(ext, n_ext, reads, offsets, j0, j1, alphabet, sigma, g);
+        if (!rc) rc = block_g_lemma1(ext, n_ext, reads, offsets, j0, j1, alphabet, sigma, reverse, g);
         if (!rc) {
             for (uint64_t i = 0; i < n_int; ++i) gsa[i] = g[sa[i]];
             rc = oracle_insert(ext, n_ext, bint, gsa, n_int, nxt);
@@ -407,6 +426,18 @@ int oracle_setbwte(const uint8_t *reads, const uint64_t *offsets, uint64_t m,
     free(ext);
     free(nxt);
     return rc;
+}
+
+int oracle_setbwte(const uint8_t *reads, const uint64_t *offsets, uint64_t m,
+                   const uint8_t *alphabet, int sigma, const uint64_t *bounds,
+                   uint64_t K, uint8_t *B) {
+    return setbwte(reads, offsets, m, alphabet, sigma, bounds, K, 0, B);
+}
+
+int oracle_setbwte_reverse(const uint8_t *reads, const uint64_t *offsets, uint64_t m,
+                           const uint8_t *alphabet, int sigma, const uint64_t *bounds,
+                           uint64_t K, uint8_t *B) {
+    return setbwte(reads, offsets, m, alphabet, sigma, bounds, K, 1, B);
 }
 
 /* Inverts B: for each r < m, start at row r (rows 0..m-1 hold the terminator

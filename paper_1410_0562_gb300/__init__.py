@@ -39,7 +39,7 @@ SBWT_STAGE_GSA = 3
 
 #: every symbol include/sbwt.h declares, in header order
 EXPORTS = (
-    "sbwt_create", "sbwt_create_ex", "sbwt_append", "sbwt_append_device", "sbwt_get_bwt", "sbwt_rank",
+    "sbwt_create", "sbwt_create_ex", "sbwt_append", "sbwt_prepend", "sbwt_append_device", "sbwt_get_bwt", "sbwt_rank",
     "sbwt_rank_batch", "sbwt_count", "sbwt_memory", "sbwt_size", "sbwt_reset", "sbwt_destroy", "sbwt_strerror", "sbwt_get_stream",
     "sbwt_set_capture", "sbwt_get_stage", "sbwt_set_profiling", "sbwt_set_profiling_only", "sbwt_get_kernel_stats",
     "sbwt_reset_kernel_stats", "sbwt_set_graph_replay", "sbwt_autotune_block_suffixes", "sbwt_serve_start",
@@ -92,6 +92,7 @@ def load() -> ctypes.CDLL:
             "sbwt_create": ([ctypes.c_char_p, SZ, ctypes.POINTER(P)], I),
             "sbwt_create_ex": ([ctypes.c_char_p, SZ, ctypes.POINTER(sbwt_options), ctypes.POINTER(P)], I),
             "sbwt_append": ([P, P, P, U64], I),
+            "sbwt_prepend": ([P, P, P, U64], I),
             "sbwt_append_device": ([P, P, P, U64], I),
             "sbwt_get_bwt": ([P, P, U64, ctypes.POINTER(U64)], I),
             "sbwt_rank": ([P, ctypes.c_uint8, U64, ctypes.POINTER(U64)], I),
@@ -180,6 +181,14 @@ def sbwt_append(h, reads, offsets, m: int | None = None):
     if m is None:
         m = len(ok) - 1
     _check(load().sbwt_append(h, rp, op, m), "sbwt_append")
+
+
+def sbwt_prepend(h, reads, offsets, m: int | None = None):
+    rp, rk = _host_ptr(reads, np.uint8)
+    op, ok = _host_ptr(offsets, np.uint64)
+    if m is None:
+        m = len(ok) - 1
+    _check(load().sbwt_prepend(h, rp, op, m), "sbwt_prepend")
 
 
 def sbwt_append_device(h, d_reads: int, d_offsets: int, m: int):
@@ -371,6 +380,11 @@ class SetBWT:
 
     def append(self, reads, offsets, m: int | None = None) -> "SetBWT":
         sbwt_append(self._h, reads, offsets, m)
+        return self
+
+    def prepend(self, reads, offsets, m: int | None = None) -> "SetBWT":
+        """The reads go before every read already in the index."""
+        sbwt_prepend(self._h, reads, offsets, m)
         return self
 
     def append_device(self, d_reads: int, d_offsets: int, m: int) -> "SetBWT":

@@ -251,6 +251,7 @@ struct Plan {
     uint64_t npos = 0, nbytes = 0, cap = 0, max_len = 0;
     size_t slots = 0;
     bool idx64 = false;
+    bool prepend = false;  // the reads go before every read in the index (blocks run last to first)
 };
 
 struct Need {
@@ -368,9 +369,10 @@ int reserve(sbwt_index* idx, const std::vector<Need>& needs) {
     return SBWT_OK;
 }
 
+// Block k of the append, the q-th to run (q = k unless the append prepends).
 template <class IdxT>
 void run_block(sbwt_index* idx, const BlockPlan& bp, const uint64_t* d_offsets, const Dict& src, Dict& dst,
-               uint64_t n_ext, uint64_t m_ext, size_t slots, size_t k) {
+               uint64_t n_ext, uint64_t m_ext, size_t slots, size_t k, size_t q, bool prepend) {
     Launcher& L = idx->L;
     const uint32_t n = (uint32_t)bp.n_int;
     SuffixSortBuffers b;
@@ -378,7 +380,7 @@ void run_block(sbwt_index* idx, const BlockPlan& bp, const uint64_t* d_offsets, 
     b.keys_alt = (unsigned long long*)idx->keys_alt.p;
     b.vals = (uint32_t*)idx->vals.p;
     b.vals_alt = (uint32_t*)idx->vals_alt.p;
-    b.sa = (uint32_t*)((k & 1) ? idx->sa2.p : idx->sa.p);
+    b.sa = (uint32_t*)((q & 1) ? idx->sa2.p : idx->sa.p);
     b.rank = (uint32_t*)idx->rank.p;
     b.act_pos[0] = (uint32_t*)idx->act_pos0.p;
     b.act_pos[1] = (uint32_t*)idx->act_pos1.p;
@@ -397,19 +399,19 @@ void run_block(sbwt_index* idx, const BlockPlan& bp, const uint64_t* d_offsets, 
     // the sort, on the side stream; its SA buffer is free once the gather of
     // block k - 2 has read it
     const cudaStream_t s = L.stream;
-    if (k >= 2) cudaStreamWaitEvent(idx->side, idx->ev_consumed[k & 1], 0);
+    if (q >= 2) cudaStreamWaitEvent(idx->side, idx->ev_consumed[q & 1], 0);
     L.stream = idx->side;
     suffix_sort_block(L, text, term, bp.base, n, (uint32_t)bp.max_len, b);
-    cudaEventRecord(idx->ev_sorted[k & 1], idx->side);
+    cudaEventRecord(idx->ev_sorted[q & 1], idx->side);
     L.stream = s;
     // ComputeRanks needs only the dictionary; the gather waits for the sort
     launch_compute_ranks<IdxT>(L, text, d_offsets, bp.j0, bp.j1 - bp.j0, bp.n_int, (const OccBlock*)src.blocks.p,
                                (const unsigned long long*)src.super.p, (const unsigned long long*)src.C.p, n_ext,
-                               m_ext, (IdxT*)idx->g.p, (uint32_t*)idx->err.p);
-    cudaStreamWaitEvent(s, idx->ev_sorted[k & 1], 0);
+                               prepend ? 0 : m_ext, (IdxT*)idx->g.p, (uint32_t*)idx->err.p);
+    cudaStreamWaitEvent(s, idx->ev_sorted[q & 1], 0);
     launch_bint_gather<IdxT>(L, text, term, bp.base, b.sa, (const IdxT*)idx->g.p, n, (uint8_t*)idx->bint.p,
                              (IdxT*)idx->gsa.p);
-    cudaEventRecord(idx->ev_consumed[k & 1], s);
+    cudaEventRecord(idx->ev_consumed[q & 1], s);
     launch_insert<IdxT>(L, (const OccBlock*)src.blocks.p, n_ext, (const uint8_t*)idx->bint.p,
                         (const IdxT*)idx->gsa.p, bp.n_int, (OccBlock*)dst.blocks.p,
                         (unsigned long long*)dst.super.p, (unsigned long long*)dst.C.p, m_ext + (bp.j1 - bp.j0),
@@ -480,14 +482,19 @@ int append_impl(sbwt_index* idx, const uint8_t* d_reads, const uint64_t* d_offse
         uint64_t n_ext = idx->n, m_ext = idx->m;
         cudaEventRecord(idx->ev_fork, s);  // the sorts read the packed text
         cudaStreamWaitEvent(idx->side, idx->ev_fork, 0);
-        for (size_t k = 0; k < p.blocks.size(); ++k) {
+        const size_t nb = p.blocks.size();
+        for (size_t q = 0; q < nb; ++q) {
+            // prepending runs the blocks last to first, so each one's reads go
+            // before those of the blocks already inserted
+            const size_t k = p.prepend ? nb - 1 - q : q;
             const BlockPlan& bp = p.blocks[k];
-            const int dst = other[k & 1];
+            const int dst = other[q & 1];
             if (p.idx64)
                 run_block<unsigned long long>(idx, bp, d_offsets, idx->dict[src], idx->dict[dst], n_ext, m_ext,
-                                              p.slots, k);
+                                              p.slots, k, q, p.prepend);
             else
-                run_block<uint32_t>(idx, bp, d_offsets, idx->dict[src], idx->dict[dst], n_ext, m_ext, p.slots, k);
+                run_block<uint32_t>(idx, bp, d_offsets, idx->dict[src], idx->dict[dst], n_ext, m_ext, p.slots, k, q,
+                                    p.prepend);
             n_ext += bp.n_int;
             m_ext += bp.j1 - bp.j0;
             src = dst;
@@ -504,7 +511,8 @@ int append_impl(sbwt_index* idx, const uint8_t* d_reads, const uint64_t* d_offse
         std::vector<unsigned long long> sig = {m_new, p.npos, p.nbytes, idx->n, idx->m, (unsigned long long)idx->cur,
                                                p.idx64, L.profiling, std::hash<std::string>{}(L.only),
                                                (unsigned long long)(uintptr_t)d_reads,
-                                               (unsigned long long)(uintptr_t)d_offsets, p.blocks.size()};
+                                               (unsigned long long)(uintptr_t)d_offsets, p.blocks.size(),
+                                               (unsigned long long)p.prepend};
         for (const BlockPlan& b : p.blocks) sig.insert(sig.end(), {b.j0, b.j1, b.n_int, b.base, b.max_len});
         for (DevBuf* b : idx->all_bufs()) sig.push_back((unsigned long long)(uintptr_t)b->p);
         auto it = std::find_if(idx->graphs.begin(), idx->graphs.end(),
@@ -557,7 +565,7 @@ int append_impl(sbwt_index* idx, const uint8_t* d_reads, const uint64_t* d_offse
     idx->n = final_n;
     idx->m = final_m;
     idx->last_valid = !p.blocks.empty();
-    idx->last_n = p.blocks.empty() ? 0 : p.blocks.back().n_int;
+    idx->last_n = p.blocks.empty() ? 0 : (p.prepend ? p.blocks.front().n_int : p.blocks.back().n_int);
     idx->last_idx64 = p.idx64;
     idx->last_sa = (p.blocks.size() & 1) ? idx->sa.p : idx->sa2.p;
     return SBWT_OK;
@@ -808,6 +816,18 @@ int sbwt_append(sbwt_index* idx, const uint8_t* reads, const uint64_t* offsets, 
     if (m == 0) return SBWT_OK;
     if (offsets[m] > 0 && !reads) return SBWT_EINVAL;
     return append_impl(idx, nullptr, nullptr, offsets, m, true, reads, host_plan(offsets, m, idx->M), t0);
+}
+
+int sbwt_prepend(sbwt_index* idx, const uint8_t* reads, const uint64_t* offsets, uint64_t m) {
+    if (!idx || !offsets) return SBWT_EINVAL;
+    if (busy(idx)) return SBWT_EBUSY;
+    const auto t0 = std::chrono::steady_clock::now();
+    if (validate_offsets(offsets, m)) return SBWT_EINVAL;
+    if (m == 0) return SBWT_OK;
+    if (offsets[m] > 0 && !reads) return SBWT_EINVAL;
+    Plan p = host_plan(offsets, m, idx->M);
+    p.prepend = true;
+    return append_impl(idx, nullptr, nullptr, offsets, m, true, reads, p, t0);
 }
 
 int sbwt_append_device(sbwt_index* idx, const uint8_t* d_reads, const uint64_t* d_offsets, uint64_t m) {

@@ -419,3 +419,29 @@ def test_count_queries_match_oracle():
     expect = [oracle.count(w.reads, w.offsets, p) if all(c in b"ACGT" for c in p) else 0 for p in pats]
     assert list(got) == expect
     assert got[0] == oracle.num_suffixes(w.offsets)
+
+
+@pytest.mark.parametrize("M", [0, 7_000])
+def test_prepend_places_reads_first(M):
+    """sbwt_prepend: the reads go before the index's reads (Section 2's
+    reverse order); every mix of appends and prepends equals one append of
+    the reads in their final order (checked by the oracle).  M = 7000 makes
+    the prepended sets span several blocks, run last to first."""
+    a = readgen.ragged_reads(300, 0, 90, seed=81, p_empty=0.03)
+    b = readgen.ragged_reads(250, 1, 120, seed=82, p_repeat=0.05)
+    c = readgen.uniform_reads(200, 60, seed=83)
+    d = readgen.ragged_reads(150, 0, 40, seed=84)
+    idx = sb.SetBWT(b"ACGT", block_suffixes=M)
+    idx.append(*b)
+    idx.prepend(*a)   # a b
+    idx.append(*c)    # a b c
+    idx.prepend(*d)   # d a b c
+    parts = [d, a, b, c]
+    reads = np.concatenate([r for r, _ in parts])
+    lens = np.concatenate([np.diff(o.astype(np.int64)) for _, o in parts])
+    offsets = readgen.offsets_from_lengths(lens)
+    assert idx.size() == (oracle.num_suffixes(offsets), len(offsets) - 1)
+    assert np.array_equal(idx.bwt(), oracle.bwt(reads, offsets))
+    # into an empty index, a prepend is an append
+    e = sb.SetBWT(b"ACGT", block_suffixes=M).prepend(*a)
+    assert np.array_equal(e.bwt(), oracle.bwt(*a))

@@ -186,6 +186,9 @@ def test_block_partition_identity(seed):
     bounds = [0] + [c for c in cuts if 0 < c < m] + [m]
     assert np.array_equal(oracle.setbwte(data, off, bounds), one_shot)
     assert np.array_equal(oracle.setbwte(data, off, list(range(m + 1))), one_shot)  # one read per block
+    # the reverse order (Section 2): the same blocks from last to first
+    assert np.array_equal(oracle.setbwte(data, off, bounds, reverse=True), one_shot)
+    assert np.array_equal(oracle.setbwte(data, off, list(range(m + 1)), reverse=True), one_shot)
 
 
 def test_partition_identity_tiny_workload():
@@ -194,6 +197,8 @@ def test_partition_identity_tiny_workload():
     one_shot = oracle.bwt(w.reads, w.offsets)
     assert np.array_equal(oracle.setbwte(w.reads, w.offsets, list(w.appends)), one_shot)
     assert np.array_equal(oracle.setbwte(w.reads, w.offsets, [0, 1, 13, 200, 499, 500, 877, 1000]), one_shot)
+    assert np.array_equal(oracle.setbwte(w.reads, w.offsets, [0, 1, 13, 200, 499, 500, 877, 1000], reverse=True),
+                          one_shot)
     rec, roff = oracle.lf_invert(one_shot, w.m)
     assert np.array_equal(rec, w.reads) and np.array_equal(roff, w.offsets)
 

@@ -1,7 +1,8 @@
 """Each deliberate mistake planted in a copy of the oracle (ORACLE_PLANT in
 oracle/oracle.c) must make at least one pin fail: the pins are strong enough
 to catch a wrong start rank in Algorithm 2, reversed terminator order, a
-wrong length tie-break, a flipped Insert tie and a C[] without terminators."""
+wrong length tie-break, a flipped Insert tie, a C[] without terminators and
+a reverse-order Algorithm 1 that starts Algorithm 2 at m_ext."""
 import numpy as np
 import pytest
 
@@ -26,12 +27,14 @@ def _pins_hold() -> bool:
                 one = oracle.bwt(data, off)
                 if not np.array_equal(oracle.setbwte(data, off, list(range(m + 1))), one):
                     return False
+                if not np.array_equal(oracle.setbwte(data, off, list(range(m + 1)), reverse=True), one):
+                    return False
         return True
     except oracle.OracleError:
         return False
 
 
-@pytest.mark.parametrize("plant", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("plant", [1, 2, 3, 4, 5, 6])
 def test_planted_mistake_is_caught(plant, tmp_path):
     path = oracle.build_planted(plant, str(tmp_path / f"liboracle_plant{plant}.so"))
     try:
