@@ -757,6 +757,56 @@ void Launcher::release() {
 // ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------
+namespace {
+
+// Appends of at least this many reads are validated and planned on the
+// device (two small kernels and one copy of the block table back) instead of
+// in two host loops over the offsets.
+constexpr uint64_t kDevicePlanMin = 1 << 16;
+
+// Validates device-resident offsets and plans the blocks on the device; the
+// host offsets (h_off, when the caller has them) serve the rare plan with
+// more blocks than the table holds.
+int plan_on_device(sbwt_index* idx, const uint64_t* d_offsets, const uint64_t* h_off, uint64_t m, Plan& p) {
+    if (int rc = reserve(idx, {{&idx->plan, kPlanCap * sizeof(PlanBlock) + sizeof(PlanSummary)}})) return rc;
+    PlanBlock* d_table = (PlanBlock*)idx->plan.p;
+    PlanSummary* d_sum = (PlanSummary*)((char*)idx->plan.p + kPlanCap * sizeof(PlanBlock));
+    launch_plan(idx->L, d_offsets, m, idx->M, kMaxBlock, d_table, kPlanCap, d_sum);
+    cudaMemcpyAsync(idx->h_summary, d_sum, sizeof(PlanSummary), cudaMemcpyDeviceToHost, idx->stream);
+    cudaMemcpyAsync(idx->h_plan, d_table, kPlanCap * sizeof(PlanBlock), cudaMemcpyDeviceToHost, idx->stream);
+    if (cudaStreamSynchronize(idx->stream) != cudaSuccess || cudaGetLastError() != cudaSuccess) return SBWT_EDEVICE;
+    const PlanSummary sum = *idx->h_summary;
+    if (sum.bad) return SBWT_EINVAL;
+    if (sum.blocks <= kPlanCap) {
+        p.npos = sum.npos;
+        p.nbytes = sum.npos - m;
+        for (unsigned k = 0; k < sum.blocks; ++k) {
+            const PlanBlock& b = idx->h_plan[k];
+            p.blocks.push_back(BlockPlan{b.j0, b.j1, b.n_int, b.base, sum.max_len});
+        }
+        return SBWT_OK;
+    }
+    // more blocks than the table holds: plan on the host
+    if (!h_off) {
+        if (m + 1 > idx->h_offsets_cap) {
+            if (idx->h_offsets) cudaFreeHost(idx->h_offsets);
+            idx->h_offsets = nullptr;
+            idx->h_offsets_cap = 0;
+            if (cudaMallocHost(&idx->h_offsets, (m + 1) * 8) != cudaSuccess) return SBWT_ENOMEM;
+            idx->h_offsets_cap = m + 1;
+        }
+        if (cudaMemcpyAsync(idx->h_offsets, d_offsets, (m + 1) * 8, cudaMemcpyDeviceToHost, idx->stream) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(idx->stream) != cudaSuccess)
+            return SBWT_EDEVICE;
+        h_off = idx->h_offsets;
+    }
+    p = host_plan(h_off, m, idx->M);
+    return SBWT_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 const char* sbwt_strerror(int code) {
@@ -812,10 +862,23 @@ int sbwt_append(sbwt_index* idx, const uint8_t* reads, const uint64_t* offsets, 
     if (!idx || !offsets) return SBWT_EINVAL;
     if (busy(idx)) return SBWT_EBUSY;
     const auto t0 = std::chrono::steady_clock::now();
-    if (validate_offsets(offsets, m)) return SBWT_EINVAL;
-    if (m == 0) return SBWT_OK;
-    if (offsets[m] > 0 && !reads) return SBWT_EINVAL;
-    return append_impl(idx, nullptr, nullptr, offsets, m, true, reads, host_plan(offsets, m, idx->M), t0);
+    if (m < kDevicePlanMin) {
+        if (validate_offsets(offsets, m)) return SBWT_EINVAL;
+        if (m == 0) return SBWT_OK;
+        if (offsets[m] > 0 && !reads) return SBWT_EINVAL;
+        return append_impl(idx, nullptr, nullptr, offsets, m, true, reads, host_plan(offsets, m, idx->M), t0);
+    }
+    // a large append: the offsets go to the device first, which validates
+    // them and plans the blocks
+    if (offsets[0] != 0) return SBWT_EINVAL;
+    if (int rc = device_init(idx)) return rc;
+    if (int rc = reserve(idx, {{&idx->offsets, (size_t)(m + 1) * 8}})) return rc;
+    if (cudaMemcpyAsync(idx->offsets.p, offsets, (m + 1) * 8, cudaMemcpyHostToDevice, idx->stream) != cudaSuccess)
+        return SBWT_EDEVICE;
+    Plan p;
+    if (int rc = plan_on_device(idx, (const uint64_t*)idx->offsets.p, offsets, m, p)) return rc;
+    if (p.nbytes > 0 && !reads) return SBWT_EINVAL;
+    return append_impl(idx, nullptr, nullptr, offsets, m, true, reads, p, t0);
 }
 
 int sbwt_prepend(sbwt_index* idx, const uint8_t* reads, const uint64_t* offsets, uint64_t m) {
@@ -837,37 +900,8 @@ int sbwt_append_device(sbwt_index* idx, const uint8_t* d_reads, const uint64_t* 
     if (int rc = device_init(idx)) return rc;
     if (m == 0) return SBWT_OK;
     // validate and plan on the device; only the block table comes back
-    if (int rc = reserve(idx, {{&idx->plan, kPlanCap * sizeof(PlanBlock) + sizeof(PlanSummary)}})) return rc;
-    PlanBlock* d_table = (PlanBlock*)idx->plan.p;
-    PlanSummary* d_sum = (PlanSummary*)((char*)idx->plan.p + kPlanCap * sizeof(PlanBlock));
-    launch_plan(idx->L, d_offsets, m, idx->M, kMaxBlock, d_table, kPlanCap, d_sum);
-    cudaMemcpyAsync(idx->h_summary, d_sum, sizeof(PlanSummary), cudaMemcpyDeviceToHost, idx->stream);
-    cudaMemcpyAsync(idx->h_plan, d_table, kPlanCap * sizeof(PlanBlock), cudaMemcpyDeviceToHost, idx->stream);
-    if (cudaStreamSynchronize(idx->stream) != cudaSuccess || cudaGetLastError() != cudaSuccess) return SBWT_EDEVICE;
-    const PlanSummary sum = *idx->h_summary;
-    if (sum.bad) return SBWT_EINVAL;
     Plan p;
-    if (sum.blocks <= kPlanCap) {
-        p.npos = sum.npos;
-        p.nbytes = sum.npos - m;
-        for (unsigned k = 0; k < sum.blocks; ++k) {
-            const PlanBlock& b = idx->h_plan[k];
-            p.blocks.push_back(BlockPlan{b.j0, b.j1, b.n_int, b.base, sum.max_len});
-        }
-    } else {  // more blocks than the table holds: plan on the host
-        if (m + 1 > idx->h_offsets_cap) {
-            if (idx->h_offsets) cudaFreeHost(idx->h_offsets);
-            idx->h_offsets = nullptr;
-            idx->h_offsets_cap = 0;
-            if (cudaMallocHost(&idx->h_offsets, (m + 1) * 8) != cudaSuccess) return SBWT_ENOMEM;
-            idx->h_offsets_cap = m + 1;
-        }
-        if (cudaMemcpyAsync(idx->h_offsets, d_offsets, (m + 1) * 8, cudaMemcpyDeviceToHost, idx->stream) !=
-                cudaSuccess ||
-            cudaStreamSynchronize(idx->stream) != cudaSuccess)
-            return SBWT_EDEVICE;
-        p = host_plan(idx->h_offsets, m, idx->M);
-    }
+    if (int rc = plan_on_device(idx, d_offsets, nullptr, m, p)) return rc;
     if (p.nbytes > 0 && !d_reads) return SBWT_EINVAL;
     return append_impl(idx, d_reads, d_offsets, nullptr, m, false, nullptr, p, t0);
 }
@@ -884,10 +918,23 @@ int sbwt_get_bwt(sbwt_index* idx, uint8_t* out, uint64_t cap, uint64_t* n_out) {
         // over the HBM budget: stage B in pinned host memory instead
         if (!idx->host_tier_allowed || grow(idx->out_bytes, idx->n, true) != SBWT_OK) return SBWT_ENOMEM;
     }
-    launch_unpack(idx->L, (const OccBlock*)idx->dict[idx->cur].blocks.p, idx->n, idx->alpha4,
-                  (uint8_t*)idx->out_bytes.p);
-    cudaMemcpyAsync(out, idx->out_bytes.p, idx->n, cudaMemcpyDeviceToHost, idx->stream);
-    if (cudaStreamSynchronize(idx->stream) != cudaSuccess || cudaGetLastError() != cudaSuccess) return SBWT_EDEVICE;
+    // unpack in chunks on the index stream while the side stream copies the
+    // chunks already unpacked
+    constexpr uint64_t kChunkRows = 1ull << 24;
+    const cudaStream_t s = idx->stream;
+    const OccBlock* blocks = (const OccBlock*)idx->dict[idx->cur].blocks.p;
+    uint8_t* staged = (uint8_t*)idx->out_bytes.p;
+    int e = 0;
+    for (uint64_t r0 = 0; r0 < idx->n; r0 += kChunkRows, e ^= 1) {
+        const uint64_t r1 = std::min(idx->n, r0 + kChunkRows);
+        launch_unpack(idx->L, blocks, r0, r1, idx->alpha4, staged);
+        cudaEventRecord(idx->ev_sorted[e], s);
+        cudaStreamWaitEvent(idx->side, idx->ev_sorted[e], 0);
+        cudaMemcpyAsync(out + r0, staged + r0, r1 - r0, cudaMemcpyDeviceToHost, idx->side);
+    }
+    cudaEventRecord(idx->ev_join, idx->side);
+    cudaStreamWaitEvent(s, idx->ev_join, 0);
+    if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) return SBWT_EDEVICE;
     return SBWT_OK;
 }
 

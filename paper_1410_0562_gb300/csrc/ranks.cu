@@ -143,17 +143,35 @@ __global__ void __launch_bounds__(kThreads) count_kernel(const OccBlock* __restr
 }
 
 __global__ void __launch_bounds__(kThreads) unpack_kernel(const OccBlock* __restrict__ blocks,
-                                                          unsigned long long n, uint32_t alpha4,
-                                                          uint8_t* __restrict__ out) {
-    const uint64_t r = (uint64_t)blockIdx.x * kThreads + threadIdx.x;
-    if (r >= n) return;
-    const OccBlock& b = blocks[r >> kOccShift];
-    const uint32_t q = (uint32_t)(r & (kOccSpan - 1));
-    if ((b.dmask >> q) & 1ull) {
-        out[r] = (uint8_t)'$';
+                                                          unsigned long long r0, unsigned long long r1,
+                                                          uint32_t alpha4, uint8_t* __restrict__ out) {
+    // one occurrence block (64 rows) per thread, 64 output bytes written as
+    // four 16-byte stores when the block is whole; rows [r0, r1), r0 a
+    // multiple of 64
+    const uint64_t b = (r0 >> kOccShift) + (uint64_t)blockIdx.x * kThreads + threadIdx.x;
+    const uint64_t row0 = b << kOccShift;
+    if (row0 >= r1) return;
+    const OccBlock blk = blocks[b];
+    uint32_t words[16];
+#pragma unroll
+    for (int w = 0; w < 16; ++w) {
+        uint32_t x = 0;
+#pragma unroll
+        for (int q4 = 0; q4 < 4; ++q4) {
+            const uint32_t q = 4 * w + q4;
+            const uint32_t c = (uint32_t)(blk.sym[q >> 5] >> (2 * (q & 31))) & 3u;
+            const uint32_t byte = ((blk.dmask >> q) & 1ull) ? (uint32_t)'$' : ((alpha4 >> (8 * c)) & 0xFFu);
+            x |= byte << (8 * q4);
+        }
+        words[w] = x;
+    }
+    if (row0 + kOccSpan <= r1) {
+        uint4* dst = reinterpret_cast<uint4*>(out + row0);
+#pragma unroll
+        for (int v = 0; v < 4; ++v)
+            dst[v] = make_uint4(words[4 * v], words[4 * v + 1], words[4 * v + 2], words[4 * v + 3]);
     } else {
-        const uint32_t c = (uint32_t)(b.sym[q >> 5] >> (2 * (q & 31))) & 3u;
-        out[r] = (uint8_t)(alpha4 >> (8 * c));
+        for (uint32_t q = 0; q < (uint32_t)(r1 - row0); ++q) out[row0 + q] = (uint8_t)(words[q >> 2] >> (8 * (q & 3)));
     }
 }
 
@@ -215,10 +233,12 @@ void launch_count(Launcher& L, const OccBlock* blocks, const unsigned long long*
                 reinterpret_cast<const unsigned long long*>(offs), (unsigned long long)q, out);
 }
 
-void launch_unpack(Launcher& L, const OccBlock* blocks, uint64_t n, uint32_t alpha4, uint8_t* out) {
-    if (n == 0) return;
-    SBWT_LAUNCH(L, "unpack_bwt", (double)n * (1 + 0.5), 0, nullptr, unpack_kernel, ceil_div_u(n, kThreads),
-                kThreads, 0, blocks, (unsigned long long)n, alpha4, out);
+void launch_unpack(Launcher& L, const OccBlock* blocks, uint64_t r0, uint64_t r1, uint32_t alpha4, uint8_t* out) {
+    if (r1 <= r0) return;
+    const uint64_t nblocks = ((r1 - 1) >> kOccShift) - (r0 >> kOccShift) + 1;
+    SBWT_LAUNCH(L, "unpack_bwt", (double)(r1 - r0) * (1 + 0.5), 0, nullptr, unpack_kernel,
+                ceil_div_u(nblocks, kThreads), kThreads, 0, blocks, (unsigned long long)r0, (unsigned long long)r1,
+                alpha4, out);
 }
 
 template void launch_compute_ranks<uint32_t>(Launcher&, const uint32_t*, const uint64_t*, uint64_t, uint64_t,

@@ -59,8 +59,9 @@ void launch_rank_batch(Launcher& L, const OccBlock* blocks, const unsigned long 
 void launch_count(Launcher& L, const OccBlock* blocks, const unsigned long long* super,
                   const unsigned long long* d_C, uint64_t n, uint32_t alpha4, int sigma, const uint8_t* pats,
                   const uint64_t* offs, uint64_t q, uint64_t total_len, unsigned long long* out);
-// B as bytes: alphabet byte per code, '$' for a terminator row.
-void launch_unpack(Launcher& L, const OccBlock* blocks, uint64_t n, uint32_t alpha4, uint8_t* out);
+// B as bytes, rows [r0, r1) (r0 a multiple of 64): alphabet byte per code,
+// '$' for a terminator row; out[r] for row r.
+void launch_unpack(Launcher& L, const OccBlock* blocks, uint64_t r0, uint64_t r1, uint32_t alpha4, uint8_t* out);
 
 // insert.cu: Insert (Section 5) as a stable merge of the old dictionary
 // (n_ext rows) with n_int new symbols at rows g_sa[i] + i; writes the new
