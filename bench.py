@@ -37,7 +37,6 @@ import readgen  # noqa: E402
 
 METRIC = "BWT build Mbp/s"
 UNIT = "Mbp/s"
-DOMINANT = "radix_downsweep"
 
 
 def parse():
@@ -98,10 +97,11 @@ def load_peaks():
     return 6800.0, "fallback"
 
 
-def load_traffic(kernel: str, units: float):
-    """DRAM bytes of `units` units of `kernel`, scaled from the committed ncu
-    capture (profiles/ncu_traffic.json), if that capture was taken on the
-    kernel's current source files; else None."""
+def load_traffic(kernel: str, alg_bytes: float):
+    """DRAM bytes of a launch of `kernel` that moves `alg_bytes` algorithmic
+    bytes, scaled by units from the committed ncu capture
+    (profiles/ncu_traffic.json), if that capture was taken on the kernel's
+    current source files; else None."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(path):
         return None
@@ -118,7 +118,7 @@ def load_traffic(kernel: str, units: float):
                 h.update(fh.read())
         if h.hexdigest()[:16] != t["source_sha"]:
             return None
-        return units * float(t["dram_bytes_per_unit"])
+        return alg_bytes / float(t["algorithmic_bytes_per_unit"]) * float(t["dram_bytes_per_unit"])
     except Exception:
         return None
 
@@ -463,7 +463,7 @@ def run_gb300(args):
     peak, peak_kind = load_peaks()
     achieved = dom["bytes"] / (dom["ms"] / 1e3) / 1e9 if dom["ms"] > 0 else 0.0
     per_launch = dom["bytes"] / max(dom["launches"], 1)
-    traffic = load_traffic(dom["name"], per_launch / 24.0) if dom["name"] == "radix_downsweep" else None
+    traffic = load_traffic(dom["name"], per_launch)
     roofline = {"bound": "hbm", "kernel": dom["name"], "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": peak_kind,
                 "traffic": traffic,

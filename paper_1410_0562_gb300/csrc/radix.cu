@@ -1,16 +1,19 @@
-// radix.cu -- stable LSD radix sort of (32- or 64-bit key, 32-bit value)
-// pairs, 8-bit digits, element count in device memory.  This is the sort under the
-// suffix sorting of a block (Section 3 of arXiv 1410.0562 sorts suffixes as
-// long integer keys of packed symbols, refined over iterations).
+// radix.cu -- stable LSD radix sort of 64-bit keys, alone or with 32-bit
+// values, 8-bit digits, element count in device memory.  This is the sort
+// under the suffix sorting of a block (Section 3 of arXiv 1410.0562 sorts
+// suffixes as long integer keys of packed symbols, refined over iterations).
 //
 // Each digit pass is reduce-then-scan over chunks: a persistent grid of G
 // CTAs splits the keys into G contiguous chunks of whole tiles; the upsweep
 // counts the digits of every chunk, one CTA turns the G x 256 counts into the
 // output offset of every (chunk, digit), and the downsweep walks each chunk
 // tile by tile with running offsets.  Nothing waits on another CTA.  Inside
-// a tile, eight warp ballots give each lane the mask of lanes with the same
-// digit, which ranks the keys stably; the tile is staged in shared memory in
-// digit order and written out in coalesced runs.
+// a tile, each warp ranks its keys stably: every lane sets its bit in a
+// shared-memory mask word of its digit, so the word it reads back holds the
+// lanes with the same digit; the tile is staged in shared memory in digit
+// order and written out in runs.  A sort of keys alone moves one 8-byte
+// element per key: its runs are twice as long in bytes as those of separate
+// key and value arrays, which is what the scatter's speed depends on.
 #include <algorithm>
 
 #include "sbwt_internal.cuh"
@@ -27,14 +30,15 @@ constexpr int kBins = kRadixBins;
 constexpr int kMaxChunks = 2048;
 static_assert(kBins == kThreads, "one thread per digit");
 
-// shared memory of the downsweep: TMA input tile, staged output tile, warp
-// counters, three digit tables, the mbarrier
-template <class KeyT>
+// shared memory of the downsweep: TMA input tile (keys, then values when
+// kPairs), the staged output tile (same layout), warp digit counters and
+// peer masks, three digit tables, the mbarrier
+template <class KeyT, bool kPairs>
 __host__ __device__ constexpr size_t down_smem() {
-    return 2 * ((size_t)kTile * sizeof(KeyT) + (size_t)kTile * 4) + (size_t)kWarps * kBins * 4 +
+    return 2 * (size_t)kTile * (sizeof(KeyT) + (kPairs ? 4 : 0)) + 2 * (size_t)kWarps * kBins * 4 +
            (size_t)kBins * 4 * 3 + 16;
 }
-static_assert(3 * (down_smem<unsigned long long>() + 1024) <= 228 * 1024, "three CTAs per SM");
+static_assert(3 * (down_smem<unsigned long long, true>() + 1024) <= 228 * 1024, "three CTAs per SM");
 
 // Temp layout (32-bit words): two arrays of digit totals (pass p adds into
 // array p & 1; the chunk scan of pass p clears the other one for pass p + 1),
@@ -135,22 +139,25 @@ __global__ void __launch_bounds__(kScanThreads) radix_chunk_scan_kernel(uint32_t
 // The scatter of one pass over this CTA's chunk: whole tiles arrive by TMA
 // one tile ahead (a partial tile, only the very last one, is read with plain
 // loads); each tile is ranked, staged in digit order in shared memory and
-// written out in runs.  smem: down_smem<KeyT>() bytes, its mbarrier already
+// written out in runs.  Without kPairs there are no values (vin, vout
+// unused).  smem: down_smem<KeyT, kPairs>() bytes, its mbarrier already
 // initialised; parity is the mbarrier's phase, carried across calls.
 // Returns false when a copy did not land (flagged in *d_err, bit 8).
-template <class KeyT>
+template <class KeyT, bool kPairs>
 __device__ __forceinline__ bool down_phase(const KeyT* __restrict__ kin, const uint32_t* __restrict__ vin,
                                            KeyT* __restrict__ kout, uint32_t* __restrict__ vout, uint32_t n,
                                            int shift, const uint32_t* __restrict__ chunk_offsets,
                                            uint32_t* __restrict__ d_err, unsigned char* smem, uint32_t& parity) {
+    constexpr uint32_t kValWords = kPairs ? kTile : 0;
     KeyT* in_keys = reinterpret_cast<KeyT*>(smem);  // next tile, filled by TMA
     uint32_t* in_vals = reinterpret_cast<uint32_t*>(in_keys + kTile);
-    KeyT* skeys = reinterpret_cast<KeyT*>(in_vals + kTile);  // tile in digit order
+    KeyT* skeys = reinterpret_cast<KeyT*>(in_vals + kValWords);  // tile in digit order
     uint32_t* svals = reinterpret_cast<uint32_t*>(skeys + kTile);
-    uint32_t* wcnt = svals + kTile;            // [kWarps][kBins]
-    uint32_t* dstart = wcnt + kWarps * kBins;  // tile-local start of each digit
-    uint32_t* gnext = dstart + kBins;          // running output offset of each digit
-    uint32_t* shift_out = gnext + kBins;       // gnext - dstart: tile slot -> output index
+    uint32_t* wcnt = svals + kValWords;        // [kWarps][kBins] digit counts
+    uint32_t* wmask = wcnt + kWarps * kBins;   // [kWarps][kBins] lanes holding each digit, kept zero
+    uint32_t* dstart = wmask + kWarps * kBins;  // tile-local start of each digit
+    uint32_t* gnext = dstart + kBins;           // running output offset of each digit
+    uint32_t* shift_out = gnext + kBins;        // gnext - dstart: tile slot -> output index
     unsigned long long* bar = reinterpret_cast<unsigned long long*>(shift_out + kBins);
 
     uint32_t t0, t1;
@@ -160,13 +167,14 @@ __device__ __forceinline__ bool down_phase(const KeyT* __restrict__ kin, const u
     const uint32_t lt = (1u << lane) - 1u;
     const int d = threadIdx.x;
     gnext[d] = chunk_offsets[(uint64_t)blockIdx.x * kBins + d];
+    for (int i = threadIdx.x; i < kWarps * kBins; i += kThreads) wmask[i] = 0;
     __syncthreads();
 
     auto full = [&](uint32_t tile) { return (uint64_t)(tile + 1) * kTile <= n; };
     auto prefetch = [&](uint32_t tile) {
-        mbar_expect_tx(bar, kTile * (uint32_t)(sizeof(KeyT) + 4));
+        mbar_expect_tx(bar, kTile * (uint32_t)(sizeof(KeyT) + (kPairs ? 4 : 0)));
         tma_bulk_load(in_keys, kin + (uint64_t)tile * kTile, kTile * (uint32_t)sizeof(KeyT), bar);
-        tma_bulk_load(in_vals, vin + (uint64_t)tile * kTile, kTile * 4u, bar);
+        if (kPairs) tma_bulk_load(in_vals, vin + (uint64_t)tile * kTile, kTile * 4u, bar);
     };
     if (threadIdx.x == 0 && full(t0)) {
         fence_proxy_async_smem();
@@ -183,7 +191,7 @@ __device__ __forceinline__ bool down_phase(const KeyT* __restrict__ kin, const u
         } else {
             for (uint32_t i = threadIdx.x; i < cnt; i += kThreads) {
                 in_keys[i] = kin[base + i];
-                in_vals[i] = vin[base + i];
+                if (kPairs) in_vals[i] = vin[base + i];
             }
         }
         for (int i = threadIdx.x; i < kWarps * kBins; i += kThreads) wcnt[i] = 0;
@@ -200,7 +208,7 @@ __device__ __forceinline__ bool down_phase(const KeyT* __restrict__ kin, const u
         for (int it = 0; it < kItems; ++it) {
             const uint32_t i = warp * kWarpItems + it * 32 + lane;
             k[it] = i < cnt ? in_keys[i] : KeyT(0);
-            v[it] = i < cnt ? in_vals[i] : 0u;
+            v[it] = (kPairs && i < cnt) ? in_vals[i] : 0u;
         }
         __syncthreads();  // the input buffer is free: fetch the next tile
         if (threadIdx.x == 0 && tile + 1 < t1 && full(tile + 1)) {
@@ -208,24 +216,27 @@ __device__ __forceinline__ bool down_phase(const KeyT* __restrict__ kin, const u
             prefetch(tile + 1);
         }
 
-        // rank among equal digits of the warp, in index order
+        // rank among equal digits of the warp, in index order: the lanes
+        // with digit dg are the bits set in wm[dg] once every lane has set
+        // its own; the lowest of them adds their number to the warp's count
+        // and clears the mask word for the next item
         uint32_t* my = wcnt + warp * kBins;
+        uint32_t* wm = wmask + warp * kBins;
         uint32_t dr[kItems];
 #pragma unroll
         for (int it = 0; it < kItems; ++it) {
             const uint32_t i = warp * kWarpItems + it * 32 + lane;
             const bool valid = i < cnt;
             const uint32_t dg = (uint32_t)(k[it] >> shift) & (kBins - 1);
-            uint32_t peers = __ballot_sync(0xffffffffu, valid);
-            if (!valid) peers = ~peers;
-#pragma unroll
-            for (int b = 0; b < kRadixBits; ++b) {
-                const uint32_t bal = __ballot_sync(0xffffffffu, (dg >> b) & 1u);
-                peers &= ((dg >> b) & 1u) ? bal : ~bal;
-            }
+            if (valid) atomicOr(&wm[dg], 1u << lane);
+            __syncwarp();
+            const uint32_t peers = valid ? wm[dg] : 0u;
             const uint32_t prior = valid ? my[dg] : 0u;
             __syncwarp();
-            if (valid && lane == __ffs(peers) - 1) my[dg] = prior + __popc(peers);
+            if (valid && lane == __ffs(peers) - 1) {
+                my[dg] = prior + __popc(peers);
+                wm[dg] = 0;
+            }
             __syncwarp();
             dr[it] = valid ? ((dg << 16) | (prior + __popc(peers & lt))) : 0xFFFFFFFFu;
         }
@@ -252,22 +263,44 @@ __device__ __forceinline__ bool down_phase(const KeyT* __restrict__ kin, const u
             const uint32_t pos = dstart[dd] + wcnt[warp * kBins + dd] + (dr[it] & 0xFFFFu);
             if (pos < kTile) {
                 skeys[pos] = k[it];
-                svals[pos] = v[it];
+                if (kPairs) svals[pos] = v[it];
             } else {
                 atomicOr(d_err, 16u);
             }
         }
         __syncthreads();
 
-        for (uint32_t s = threadIdx.x; s < cnt; s += kThreads) {
-            const KeyT key = skeys[s];
-            const uint32_t dd = (uint32_t)(key >> shift) & (kBins - 1);
-            const uint32_t o = shift_out[dd] + s;
-            if (o < n) {
-                kout[o] = key;
-                vout[o] = svals[s];
-            } else {
-                atomicOr(d_err, 16u);
+        if (whole) {
+            // all loads of the thread's slots first, then all stores
+            uint32_t o[kItems];
+#pragma unroll
+            for (int j = 0; j < kItems; ++j) {
+                const uint32_t s = threadIdx.x + j * kThreads;
+                k[j] = skeys[s];
+                if (kPairs) v[j] = svals[s];
+            }
+#pragma unroll
+            for (int j = 0; j < kItems; ++j)
+                o[j] = shift_out[(uint32_t)(k[j] >> shift) & (kBins - 1)] + threadIdx.x + j * kThreads;
+#pragma unroll
+            for (int j = 0; j < kItems; ++j) {
+                if (o[j] < n) {
+                    kout[o[j]] = k[j];
+                    if (kPairs) vout[o[j]] = v[j];
+                } else {
+                    atomicOr(d_err, 16u);
+                }
+            }
+        } else {
+            for (uint32_t s = threadIdx.x; s < cnt; s += kThreads) {
+                const KeyT key = skeys[s];
+                const uint32_t o = shift_out[(uint32_t)(key >> shift) & (kBins - 1)] + s;
+                if (o < n) {
+                    kout[o] = key;
+                    if (kPairs) vout[o] = svals[s];
+                } else {
+                    atomicOr(d_err, 16u);
+                }
             }
         }
         __syncthreads();
@@ -276,16 +309,16 @@ __device__ __forceinline__ bool down_phase(const KeyT* __restrict__ kin, const u
     return true;
 }
 
-template <class KeyT>
+template <class KeyT, bool kPairs>
 __global__ void __launch_bounds__(kThreads, 3) radix_downsweep_kernel(
     const KeyT* __restrict__ kin, const uint32_t* __restrict__ vin, KeyT* __restrict__ kout,
     uint32_t* __restrict__ vout, const uint32_t* __restrict__ d_n, int shift,
     const uint32_t* __restrict__ chunk_offsets, uint32_t* __restrict__ d_err) {
     extern __shared__ __align__(128) unsigned char smem[];
-    unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem + down_smem<KeyT>() - 16);
+    unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem + down_smem<KeyT, kPairs>() - 16);
     if (threadIdx.x == 0) mbar_init(bar, 1);
     uint32_t parity = 0;
-    down_phase(kin, vin, kout, vout, *d_n, shift, chunk_offsets, d_err, smem, parity);
+    down_phase<KeyT, kPairs>(kin, vin, kout, vout, *d_n, shift, chunk_offsets, d_err, smem, parity);
 }
 
 // ---------------------------------------------------------------------------
@@ -397,7 +430,7 @@ __global__ void __launch_bounds__(kThreads, 3) radix_sort_fused_kernel(KeyT* __r
     if (n == 0) return;  // the whole grid leaves together
     unsigned* gbar = temp + kGridBar;
     unsigned gen = *reinterpret_cast<volatile unsigned*>(&gbar[1]);  // read before this CTA's first arrival
-    unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem + down_smem<KeyT>() - 16);
+    unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem + down_smem<KeyT, true>() - 16);
     if (threadIdx.x == 0) mbar_init(bar, 1);
     uint32_t parity = 0;
     uint32_t ntiles;
@@ -421,12 +454,12 @@ __global__ void __launch_bounds__(kThreads, 3) radix_sort_fused_kernel(KeyT* __r
         if (!grid_barrier(gbar, gen, d_err)) return;
         scan_b_phase(chunk, nchunks, partials, totals);
         if (!grid_barrier(gbar, gen, d_err)) return;
-        if (!down_phase(kin, vin, ko, vo, n, shift, chunk, d_err, smem, parity)) return;
+        if (!down_phase<KeyT, true>(kin, vin, ko, vo, n, shift, chunk, d_err, smem, parity)) return;
         if (!grid_barrier(gbar, gen, d_err)) return;
     }
 }
 
-unsigned g_down_ctas[2][64] = {{0}};  // [key is 64-bit][device]
+unsigned g_keys_ctas[64] = {0};  // downsweep CTAs of the keys-only sort, per device
 unsigned g_fused_ctas[64] = {0};
 
 
@@ -452,56 +485,43 @@ size_t radix_temp_words(uint64_t cap) {
     return kChunkOffsets + (size_t)chunks * kBins + 64;
 }
 
-namespace {
-
-template <class KeyT>
-void radix_init_key() {
-    const size_t smem = down_smem<KeyT>();
-    cudaFuncSetAttribute(radix_downsweep_kernel<KeyT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    g_down_ctas[sizeof(KeyT) == 8][current_device()] =
-        std::min<unsigned>(kMaxChunks, persistent_ctas((const void*)radix_downsweep_kernel<KeyT>, kThreads, smem));
-}
-
-}  // namespace
-
 void radix_init() {
-    radix_init_key<uint32_t>();
-    radix_init_key<unsigned long long>();
-    const size_t smem = down_smem<unsigned long long>();
-    cudaFuncSetAttribute(radix_sort_fused_kernel<unsigned long long>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem);
-    g_fused_ctas[current_device()] = std::min<unsigned>(
-        kMaxChunks, persistent_ctas((const void*)radix_sort_fused_kernel<unsigned long long>, kThreads, smem));
+    using u64 = unsigned long long;
+    const size_t ks = down_smem<u64, false>();
+    cudaFuncSetAttribute(radix_downsweep_kernel<u64, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ks);
+    g_keys_ctas[current_device()] =
+        std::min<unsigned>(kMaxChunks, persistent_ctas((const void*)radix_downsweep_kernel<u64, false>, kThreads, ks));
+    const size_t smem = down_smem<u64, true>();
+    cudaFuncSetAttribute(radix_sort_fused_kernel<u64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    g_fused_ctas[current_device()] =
+        std::min<unsigned>(kMaxChunks, persistent_ctas((const void*)radix_sort_fused_kernel<u64>, kThreads, smem));
 }
 
-template <class KeyT>
-bool radix_sort_pairs(Launcher& L, KeyT* keys, uint32_t* vals, KeyT* keys_alt, uint32_t* vals_alt,
-                      const uint32_t* d_n, uint64_t cap, int begin_bit, int end_bit, uint32_t* temp,
-                      uint32_t* d_err) {
+bool radix_sort_keys(Launcher& L, unsigned long long* keys, unsigned long long* keys_alt, const uint32_t* d_n,
+                     uint64_t cap, int begin_bit, int end_bit, uint32_t* temp, uint32_t* d_err) {
+    using u64 = unsigned long long;
     const int passes = radix_passes(begin_bit, end_bit);
     if (passes <= 0) return false;
     uint32_t* chunk = temp + kChunkOffsets;
-    const int dev = current_device();
     const uint64_t tiles = cap / kTile + 1;
-    const unsigned grid =
-        (unsigned)std::min<uint64_t>(std::max(1u, g_down_ctas[sizeof(KeyT) == 8][dev]), tiles);
-    const double kb = (double)sizeof(KeyT);
+    const unsigned grid = (unsigned)std::min<uint64_t>(std::max(1u, g_keys_ctas[current_device()]), tiles);
+    auto* const down_kernel = radix_downsweep_kernel<u64, false>;
+    const size_t down_bytes = down_smem<u64, false>();
     bool alt = false;
     for (int p = 0; p < passes; ++p) {
-        const KeyT* kin = alt ? keys_alt : keys;
-        const uint32_t* vin = alt ? vals_alt : vals;
-        KeyT* ko = alt ? keys : keys_alt;
-        uint32_t* vo = alt ? vals : vals_alt;
+        const u64* kin = alt ? keys_alt : keys;
+        u64* ko = alt ? keys : keys_alt;
         const int shift = begin_bit + kRadixBits * p;
         uint32_t* totals = temp + kTotals + (size_t)kBins * (p & 1);
         uint32_t* next_totals = temp + kTotals + (size_t)kBins * ((p + 1) & 1);
         if (p == 0) cudaMemsetAsync(temp, 0, (kGridBar + 2) * 4, L.stream);
-        SBWT_LAUNCH(L, "radix_upsweep", 0, kb, d_n, radix_upsweep_kernel<KeyT>, grid, kThreads, 0, kin, d_n, shift,
+        SBWT_LAUNCH(L, "radix_upsweep", 0, 8, d_n, radix_upsweep_kernel<u64>, grid, kThreads, 0, kin, d_n, shift,
                     chunk, totals);
         SBWT_LAUNCH(L, "radix_chunk_scan", 12.0 * grid * kBins, 0, nullptr, radix_chunk_scan_kernel, kBins / 32,
                     kScanThreads, 0, chunk, (int)grid, totals, next_totals, d_n);
-        SBWT_LAUNCH(L, "radix_downsweep", 0, 2 * (kb + 4), d_n, radix_downsweep_kernel<KeyT>, grid, kThreads,
-                    down_smem<KeyT>(), kin, vin, ko, vo, d_n, shift, chunk, d_err);
+        // per key: the 8-byte key read and written once
+        SBWT_LAUNCH(L, "radix_downsweep", 0, 16, d_n, down_kernel, grid, kThreads, down_bytes, kin, nullptr, ko,
+                    nullptr, d_n, shift, chunk, d_err);
         alt = !alt;
     }
     return alt;
@@ -522,7 +542,7 @@ bool radix_sort_pairs_fused(Launcher& L, unsigned long long* keys, uint32_t* val
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(kThreads);
-    cfg.dynamicSmemBytes = down_smem<unsigned long long>();
+    cfg.dynamicSmemBytes = down_smem<unsigned long long, true>();
     cfg.stream = L.stream;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
@@ -534,11 +554,5 @@ bool radix_sort_pairs_fused(Launcher& L, unsigned long long* keys, uint32_t* val
     L.after(tok);
     return passes & 1;
 }
-
-template bool radix_sort_pairs<uint32_t>(Launcher&, uint32_t*, uint32_t*, uint32_t*, uint32_t*, const uint32_t*,
-                                         uint64_t, int, int, uint32_t*, uint32_t*);
-template bool radix_sort_pairs<unsigned long long>(Launcher&, unsigned long long*, uint32_t*, unsigned long long*,
-                                                   uint32_t*, const uint32_t*, uint64_t, int, int, uint32_t*,
-                                                   uint32_t*);
 
 }  // namespace sbwt

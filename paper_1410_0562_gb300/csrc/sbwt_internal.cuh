@@ -273,21 +273,19 @@ inline int radix_passes(int begin_bit, int end_bit) { return (end_bit - begin_bi
 size_t radix_temp_words(uint64_t cap);
 void radix_init();  // once per device, before the first sort
 
-// Stable LSD radix sort of (*d_n) keys (KeyT: uint32_t or unsigned long
-// long) with 32-bit values on bits [begin_bit, end_bit); key bits outside
-// that range are carried along but do not take part in the order.  Sorts
-// between (keys, vals) and (keys_alt, vals_alt); returns true when the
-// result ended in the *_alt buffers.  A scatter index out of range is skipped
-// and flagged in *d_err (bit 4).  Every key and value array must start on a
-// 16-byte boundary (whole tiles arrive by TMA bulk copies).
-template <class KeyT>
-bool radix_sort_pairs(Launcher& L, KeyT* keys, uint32_t* vals, KeyT* keys_alt, uint32_t* vals_alt,
-                      const uint32_t* d_n, uint64_t cap, int begin_bit, int end_bit, uint32_t* temp,
-                      uint32_t* d_err);
-// The same sort of 64-bit keys in one cooperative launch (all passes, the
-// CTAs meeting at bounded grid barriers; a barrier that times out flags
-// *d_err bit 9).  Meant for lists that are often empty: an empty list costs
-// one launch that returns at once.
+// Stable LSD radix sort of (*d_n) 64-bit keys on bits [begin_bit, end_bit);
+// key bits outside that range are carried along but do not take part in the
+// order (a value can ride in them).  Sorts between keys and keys_alt; returns
+// true when the result ended in keys_alt.  A scatter index out of range is
+// skipped and flagged in *d_err (bit 4).  Both arrays must start on a 16-byte
+// boundary (whole tiles arrive by TMA bulk copies).
+bool radix_sort_keys(Launcher& L, unsigned long long* keys, unsigned long long* keys_alt, const uint32_t* d_n,
+                     uint64_t cap, int begin_bit, int end_bit, uint32_t* temp, uint32_t* d_err);
+// A sort of (64-bit key, 32-bit value) pairs, keyed like radix_sort_keys,
+// in one cooperative launch (all passes, the CTAs meeting at bounded grid
+// barriers; a barrier that times out flags *d_err bit 9); the values move in
+// (vals, vals_alt) alongside.  Meant for lists that are often empty: an
+// empty list costs one launch that returns at once.
 bool radix_sort_pairs_fused(Launcher& L, unsigned long long* keys, uint32_t* vals, unsigned long long* keys_alt,
                             uint32_t* vals_alt, const uint32_t* d_n, uint64_t cap, int begin_bit, int end_bit,
                             uint32_t* temp, uint32_t* d_err);

@@ -141,17 +141,17 @@ __device__ __forceinline__ uint32_t bucket_digit(unsigned long long K, uint32_t 
     return o | (l < pc ? kShortFlag : 0u);
 }
 
+// Element of block position t for the bucket split: its bucket digit in the
+// low word, t in the high word (the sort orders by the low kDigitBits bits
+// and carries t).
 __global__ void __launch_bounds__(kThreads) sa_digit_keys_kernel(const uint32_t* __restrict__ text,
                                                                  const uint32_t* __restrict__ term,
                                                                  unsigned long long base, uint32_t n, uint32_t pc,
-                                                                 uint32_t* __restrict__ digits,
-                                                                 uint32_t* __restrict__ vals,
+                                                                 unsigned long long* __restrict__ elems,
                                                                  uint32_t* __restrict__ d_n) {
     if (blockIdx.x == 0 && threadIdx.x == 0) *d_n = n;
-    for (uint32_t t = blockIdx.x * kThreads + threadIdx.x; t < n; t += gridDim.x * kThreads) {
-        digits[t] = bucket_digit(initial_key(text, term, base + t), pc);
-        vals[t] = t;
-    }
+    for (uint32_t t = blockIdx.x * kThreads + threadIdx.x; t < n; t += gridDim.x * kThreads)
+        elems[t] = bucket_digit(initial_key(text, term, base + t), pc) | ((unsigned long long)t << 32);
 }
 
 // One warp per window of the digit-sorted array: the first bucket start in
@@ -163,9 +163,9 @@ __global__ void __launch_bounds__(kThreads) sa_digit_keys_kernel(const uint32_t*
 __global__ void __launch_bounds__(kThreads) sa_unit_begin_kernel(const uint32_t* __restrict__ text,
                                                                  const uint32_t* __restrict__ term,
                                                                  unsigned long long base,
-                                                                 const uint32_t* __restrict__ digits,
-                                                                 const uint32_t* __restrict__ vals, uint32_t n,
-                                                                 uint32_t nwin, Units u, uint32_t* __restrict__ sa,
+                                                                 const unsigned long long* __restrict__ elems,
+                                                                 uint32_t n, uint32_t nwin, Units u,
+                                                                 uint32_t* __restrict__ sa,
                                                                  uint32_t* __restrict__ rank,
                                                                  uint32_t* __restrict__ ll_t,
                                                                  uint32_t* __restrict__ ll_row,
@@ -179,9 +179,10 @@ __global__ void __launch_bounds__(kThreads) sa_unit_begin_kernel(const uint32_t*
         for (uint32_t b = lo; b < hi; b += 32) {
             const uint32_t i = b + lane;
             const bool valid = i < hi;
-            const uint32_t d = valid ? digits[i] : 0u;
-            const uint32_t prev = (valid && i > 0) ? digits[i - 1] : d;
-            const uint32_t t = valid ? vals[i] : 0u;
+            const unsigned long long e = valid ? elems[i] : 0ull;
+            const uint32_t d = (uint32_t)e;
+            const uint32_t prev = (valid && i > 0) ? (uint32_t)elems[i - 1] : d;
+            const uint32_t t = (uint32_t)(e >> 32);
             const bool bnd = valid && (i == 0 || d != prev);
             const bool lng = valid && !(d & kShortFlag);
             const uint32_t bb = __ballot_sync(0xffffffffu, bnd), bl = __ballot_sync(0xffffffffu, lng);
@@ -750,7 +751,7 @@ __global__ void __launch_bounds__(kLThreads, 2) sa_local_sort_kernel(
 // rows belong to its owner unit up to the window's own unit start.
 __global__ void __launch_bounds__(kThreads) sa_large_gather_kernel(
     const uint32_t* __restrict__ text, const uint32_t* __restrict__ term, unsigned long long base, uint32_t n,
-    const uint32_t* __restrict__ vals, Units u, uint32_t nwin, unsigned long long* __restrict__ lkeys,
+    const unsigned long long* __restrict__ elems, Units u, uint32_t nwin, unsigned long long* __restrict__ lkeys,
     uint32_t* __restrict__ lvals, uint32_t* __restrict__ lpos) {
     for (uint32_t w = blockIdx.x; w < nwin; w += gridDim.x) {
         const uint32_t lo = w * kWindow, hi = min(n, lo + kWindow);
@@ -763,7 +764,7 @@ __global__ void __launch_bounds__(kThreads) sa_large_gather_kernel(
             if (r0 >= r1 || u.lofs[q] == kNone) continue;
             const uint32_t lofs = u.lofs[q], qbeg = u.beg[q];
             for (uint32_t i = r0 + threadIdx.x; i < r1; i += kThreads) {
-                const uint32_t t = vals[i];
+                const uint32_t t = (uint32_t)(elems[i] >> 32);
                 const uint32_t o = lofs + (i - qbeg);
                 lkeys[o] = initial_key(text, term, base + (t < n ? t : 0u));
                 lvals[o] = t;
@@ -1154,25 +1155,22 @@ void suffix_sort_block(Launcher& L, const uint32_t* text, const uint32_t* term, 
 
     uint32_t* d_n = b.count_log;
     uint32_t* d_large = b.count_log + 1;
-    uint32_t* dig = reinterpret_cast<uint32_t*>(b.keys);
-    uint32_t* dig_alt = reinterpret_cast<uint32_t*>(b.keys_alt);
     SBWT_LAUNCH(L, "sa_digit_keys", (double)n * 8 + n / 4.0 + n / 8.0, 0, nullptr, sa_digit_keys_kernel,
                 grid_of(g_keys_ctas[dev], (uint64_t)n / kThreads + 1), kThreads, 0, text, term,
-                (unsigned long long)base, n, pc, dig, b.vals, d_n);
-    const bool da = radix_sort_pairs<uint32_t>(L, dig, b.vals, dig_alt, b.vals_alt, d_n, n, 0, digit_bits,
-                                               b.radix_temp, b.err);
-    const uint32_t* digits = da ? dig_alt : dig;
-    uint32_t* tsorted = da ? b.vals_alt : b.vals;
-    uint32_t* tfree = da ? b.vals : b.vals_alt;
+                (unsigned long long)base, n, pc, b.keys, d_n);
+    const bool da = radix_sort_keys(L, b.keys, b.keys_alt, d_n, n, 0, digit_bits, b.radix_temp, b.err);
+    const unsigned long long* elems = da ? b.keys_alt : b.keys;  // (digit, t) in row order
+    // the other 64-bit array holds the keys of the listed long rows, then the
+    // device-wide path's list
+    unsigned long long* other = da ? b.keys : b.keys_alt;
     // the long rows of each window, listed in the block's free arrays (the
     // next-rank array and the device-wide path's second member list are not
     // used before the first round)
     uint32_t* ll_t = b.loc_next;
     uint32_t* ll_row = b.act_suf[0];
-    // the keys of the long rows go to the 64-bit array the digits are not in
-    unsigned long long* ll_key = da ? b.keys : b.keys_alt;
-    SBWT_LAUNCH(L, "sa_unit_begin", (double)n * 24 + 32.0 * nwin, 0, nullptr, sa_unit_begin_kernel, warp_grid,
-                kThreads, 0, text, term, (unsigned long long)base, digits, tsorted, n, nwin, units, b.sa, b.rank,
+    unsigned long long* ll_key = other;
+    SBWT_LAUNCH(L, "sa_unit_begin", (double)n * 24 + 32.0 * nwin, 0, nullptr, sa_unit_begin_kernel,
+                warp_grid, kThreads, 0, text, term, (unsigned long long)base, elems, n, nwin, units, b.sa, b.rank,
                 ll_t, ll_row, ll_key, b.err);
     SBWT_LAUNCH(L, "sa_unit_scan", 96.0 * nwin, 0, nullptr, sa_unit_scan_kernel, 1, kScanThreads, 0, units, nwin, n,
                 d_large, b.count_log + 3, (int)rounds + 1, 2);
@@ -1180,12 +1178,15 @@ void suffix_sort_block(Launcher& L, const uint32_t* text, const uint32_t* term, 
     // unsorted member the compacted entry
     SBWT_LAUNCH(L, "sa_local_sort", (double)n * 24, 4, b.count_log + 3, sa_local_sort_kernel,
                 grid_of(g_local_ctas[dev], nwin), kLThreads, kLocalSortSmem, n, ll_t, ll_row, ll_key, units, nwin, b.sa, b.rank, b.loc_act, b.count_log + 3, b.err);
-    SBWT_LAUNCH(L, "sa_large_gather", 32.0 * nwin, 20, d_large, sa_large_gather_kernel, grid_of(g_local_ctas[dev], nwin),
-                kThreads, 0, text, term, (unsigned long long)base, n, tsorted, units, nwin, b.keys, tfree,
+    // the list of the device-wide path goes to the other array (the long
+    // rows' keys are dead once the local sort has run)
+    SBWT_LAUNCH(L, "sa_large_gather", 32.0 * nwin, 24, d_large, sa_large_gather_kernel, grid_of(g_local_ctas[dev], nwin),
+                kThreads, 0, text, term, (unsigned long long)base, n, elems, units, nwin, other, b.vals,
                 b.act_pos[0]);
-    const bool la = radix_sort_pairs_fused(L, b.keys, tfree, b.keys_alt, tsorted, d_large, n, 0, 63, b.radix_temp,
+    unsigned long long* spare = da ? b.keys_alt : b.keys;  // the elements are dead now
+    const bool la = radix_sort_pairs_fused(L, other, b.vals, spare, b.vals_alt, d_large, n, 0, 63, b.radix_temp,
                                            b.err);
-    run_groups<true>(L, b, la ? b.keys_alt : b.keys, la ? tsorted : tfree, b.act_pos[0], d_large, n, b.act_pos[1],
+    run_groups<true>(L, b, la ? spare : other, la ? b.vals_alt : b.vals, b.act_pos[0], d_large, n, b.act_pos[1],
                      b.act_suf[1], b.count_log + 2, grid_of(g_groups_ctas[dev], gtiles));
 
     const int bits = n > 1 ? 32 - __builtin_clz(n - 1) : 1;
