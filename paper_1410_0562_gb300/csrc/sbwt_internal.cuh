@@ -19,8 +19,9 @@ namespace sbwt {
 //   text[t >> 4] holds positions 16w .. 16w+15, MSB first: the code of t is
 //   at bits 30 - 2*(t & 15), so concatenated words compare like strings.
 //   term[t >> 5] bit (t & 31) is set iff t is a terminator.
-// Both arrays carry zeroed padding words past the end (kTextPadWords,
-// kTermPadWords) so fixed-width windows never read out of bounds.
+// Both arrays start on a 16-byte boundary and carry zeroed padding words past
+// the end (kTextPadWords, kTermPadWords) so fixed-width windows, read as
+// aligned vectors, never leave them.
 // ---------------------------------------------------------------------------
 constexpr int kTextPadWords = 4;
 constexpr int kTermPadWords = 2;

@@ -76,6 +76,7 @@ constexpr int kScanThreads = 1024;
 // share a bucket iff their keys agree above kBucketShift.
 constexpr uint32_t kPc = 11;
 constexpr int kDigitBits = 24;
+constexpr uint32_t kDigitMask = (1u << kDigitBits) - 1;
 constexpr int kBucketShift = 5 + 58 - 2 * (int)kPc;
 
 // Unit table: one entry per window of kWindow rows of the digit-sorted
@@ -118,6 +119,35 @@ __device__ __forceinline__ unsigned long long initial_key(const uint32_t* __rest
     return (k58 << 5) | len;
 }
 
+// The same key when len = min(distance to the terminator, kH0) is known:
+// only the text window is read, as one 16-byte load (plus 8 bytes when the
+// three words cross it; the text array starts on a 16-byte boundary and
+// carries 4 padding words).
+__device__ __forceinline__ unsigned long long key_with_len(const uint32_t* __restrict__ text, uint64_t P,
+                                                           uint32_t len) {
+    const uint64_t wi = P >> 4;
+    const uint32_t q = (uint32_t)(wi & 3);
+    const uint4 a = __ldg(reinterpret_cast<const uint4*>(text + (wi - q)));
+    uint2 b = make_uint2(0u, 0u);
+    if (q >= 2) b = __ldg(reinterpret_cast<const uint2*>(text + (wi - q) + 4));
+    uint32_t w0, w1, w2;
+    if (q == 0) {
+        w0 = a.x, w1 = a.y, w2 = a.z;
+    } else if (q == 1) {
+        w0 = a.y, w1 = a.z, w2 = a.w;
+    } else if (q == 2) {
+        w0 = a.z, w1 = a.w, w2 = b.x;
+    } else {
+        w0 = a.w, w1 = b.x, w2 = b.y;
+    }
+    const uint32_t s = 2u * (uint32_t)(P & 15);
+    const unsigned long long hi = ((unsigned long long)w0 << 32) | w1;
+    const unsigned long long v = (hi << s) | (((unsigned long long)w2 << s) >> 32);
+    unsigned long long k58 = v >> 6;
+    if (len < kH0) k58 &= ~((1ull << (2 * (kH0 - len))) - 1ull);
+    return (k58 << 5) | len;
+}
+
 // Dense number of the bucket (p, l) of key K among all valid pairs in (p, l)
 // order, pc = P codes.  A pair is valid when the codes of p at and past l are
 // zero.  Pairs before (p, l): the p pairs (p' < p, l' = P); for each l' < P
@@ -141,9 +171,10 @@ __device__ __forceinline__ uint32_t bucket_digit(unsigned long long K, uint32_t 
     return o | (l < pc ? kShortFlag : 0u);
 }
 
-// Element of block position t for the bucket split: its bucket digit in the
-// low word, t in the high word (the sort orders by the low kDigitBits bits
-// and carries t).
+// Element of block position t for the bucket split: its bucket digit (bits
+// 0..23, bit 31 the short flag) and min(len, kH0) (bits 24..28) in the low
+// word, t in the high word.  The sort orders by the low kDigitBits bits and
+// carries the rest.
 __global__ void __launch_bounds__(kThreads) sa_digit_keys_kernel(const uint32_t* __restrict__ text,
                                                                  const uint32_t* __restrict__ term,
                                                                  unsigned long long base, uint32_t n, uint32_t pc,
@@ -151,7 +182,10 @@ __global__ void __launch_bounds__(kThreads) sa_digit_keys_kernel(const uint32_t*
                                                                  uint32_t* __restrict__ d_n) {
     if (blockIdx.x == 0 && threadIdx.x == 0) *d_n = n;
     for (uint32_t t = blockIdx.x * kThreads + threadIdx.x; t < n; t += gridDim.x * kThreads)
-        elems[t] = bucket_digit(initial_key(text, term, base + t), pc) | ((unsigned long long)t << 32);
+    {
+        const unsigned long long K = initial_key(text, term, base + t);
+        elems[t] = bucket_digit(K, pc) | ((uint32_t)(K & 31) << 24) | ((unsigned long long)t << 32);
+    }
 }
 
 // One warp per window of the digit-sorted array: the first bucket start in
@@ -161,7 +195,6 @@ __global__ void __launch_bounds__(kThreads) sa_digit_keys_kernel(const uint32_t*
 // ll_row, ll_key)[w kWindow + k] = (t, i, its key), so a unit's long rows
 // are a few contiguous runs.
 __global__ void __launch_bounds__(kThreads) sa_unit_begin_kernel(const uint32_t* __restrict__ text,
-                                                                 const uint32_t* __restrict__ term,
                                                                  unsigned long long base,
                                                                  const unsigned long long* __restrict__ elems,
                                                                  uint32_t n, uint32_t nwin, Units u,
@@ -182,8 +215,9 @@ __global__ void __launch_bounds__(kThreads) sa_unit_begin_kernel(const uint32_t*
             const unsigned long long e = valid ? elems[i] : 0ull;
             const uint32_t d = (uint32_t)e;
             const uint32_t prev = (valid && i > 0) ? (uint32_t)elems[i - 1] : d;
+            const uint32_t len = (d >> 24) & 31u;
             const uint32_t t = (uint32_t)(e >> 32);
-            const bool bnd = valid && (i == 0 || d != prev);
+            const bool bnd = valid && (i == 0 || ((d ^ prev) & kDigitMask) != 0);
             const bool lng = valid && !(d & kShortFlag);
             const uint32_t bb = __ballot_sync(0xffffffffu, bnd), bl = __ballot_sync(0xffffffffu, lng);
             if (valid && t >= n) atomicOr(d_err, 64u);
@@ -195,7 +229,7 @@ __global__ void __launch_bounds__(kThreads) sa_unit_begin_kernel(const uint32_t*
                 const uint32_t k = lo + lct + __popc(bl & ((1u << lane) - 1u));
                 ll_t[k] = t;
                 ll_row[k] = i;
-                ll_key[k] = initial_key(text, term, base + (t < n ? t : 0u));
+                ll_key[k] = key_with_len(text, base + (t < n ? t : 0u), len);
             }
             if (first == kNone) {
                 if (bb) {
@@ -750,7 +784,7 @@ __global__ void __launch_bounds__(kLThreads, 2) sa_local_sort_kernel(
 // suffixes, in row order, as (key, t, row).  One CTA per window; a window's
 // rows belong to its owner unit up to the window's own unit start.
 __global__ void __launch_bounds__(kThreads) sa_large_gather_kernel(
-    const uint32_t* __restrict__ text, const uint32_t* __restrict__ term, unsigned long long base, uint32_t n,
+    const uint32_t* __restrict__ text, unsigned long long base, uint32_t n,
     const unsigned long long* __restrict__ elems, Units u, uint32_t nwin, unsigned long long* __restrict__ lkeys,
     uint32_t* __restrict__ lvals, uint32_t* __restrict__ lpos) {
     for (uint32_t w = blockIdx.x; w < nwin; w += gridDim.x) {
@@ -764,9 +798,10 @@ __global__ void __launch_bounds__(kThreads) sa_large_gather_kernel(
             if (r0 >= r1 || u.lofs[q] == kNone) continue;
             const uint32_t lofs = u.lofs[q], qbeg = u.beg[q];
             for (uint32_t i = r0 + threadIdx.x; i < r1; i += kThreads) {
-                const uint32_t t = (uint32_t)(elems[i] >> 32);
+                const unsigned long long e = elems[i];
+                const uint32_t t = (uint32_t)(e >> 32);
                 const uint32_t o = lofs + (i - qbeg);
-                lkeys[o] = initial_key(text, term, base + (t < n ? t : 0u));
+                lkeys[o] = key_with_len(text, base + (t < n ? t : 0u), ((uint32_t)e >> 24) & 31u);
                 lvals[o] = t;
                 lpos[o] = i;
             }
@@ -1170,7 +1205,7 @@ void suffix_sort_block(Launcher& L, const uint32_t* text, const uint32_t* term, 
     uint32_t* ll_row = b.act_suf[0];
     unsigned long long* ll_key = other;
     SBWT_LAUNCH(L, "sa_unit_begin", (double)n * 24 + 32.0 * nwin, 0, nullptr, sa_unit_begin_kernel,
-                warp_grid, kThreads, 0, text, term, (unsigned long long)base, elems, n, nwin, units, b.sa, b.rank,
+                warp_grid, kThreads, 0, text, (unsigned long long)base, elems, n, nwin, units, b.sa, b.rank,
                 ll_t, ll_row, ll_key, b.err);
     SBWT_LAUNCH(L, "sa_unit_scan", 96.0 * nwin, 0, nullptr, sa_unit_scan_kernel, 1, kScanThreads, 0, units, nwin, n,
                 d_large, b.count_log + 3, (int)rounds + 1, 2);
@@ -1181,7 +1216,7 @@ void suffix_sort_block(Launcher& L, const uint32_t* text, const uint32_t* term, 
     // the list of the device-wide path goes to the other array (the long
     // rows' keys are dead once the local sort has run)
     SBWT_LAUNCH(L, "sa_large_gather", 32.0 * nwin, 24, d_large, sa_large_gather_kernel, grid_of(g_local_ctas[dev], nwin),
-                kThreads, 0, text, term, (unsigned long long)base, n, elems, units, nwin, other, b.vals,
+                kThreads, 0, text, (unsigned long long)base, n, elems, units, nwin, other, b.vals,
                 b.act_pos[0]);
     unsigned long long* spare = da ? b.keys_alt : b.keys;  // the elements are dead now
     const bool la = radix_sort_pairs_fused(L, other, b.vals, spare, b.vals_alt, d_large, n, 0, 63, b.radix_temp,
