@@ -35,7 +35,7 @@ constexpr size_t kKeys = kTerm + up256(((kMax + 31) / 32 + kTermPadWords) * 4);
 constexpr size_t kKeysAlt = kKeys + up256(kMax * 8);
 constexpr size_t kU32 = kKeysAlt + up256(kMax * 8);  // ten arrays of kMax uint32
 constexpr size_t kUnits = kU32 + 10 * up256(kMax * 4);
-constexpr size_t kUnitsBytes = 8192;  // suffix_sort_unit_bytes(kMax) must fit (checked at set-up)
+constexpr size_t kUnitsBytes = 16384;  // suffix_sort_unit_bytes(kMax) must fit (checked at set-up)
 constexpr size_t kRadixTemp = kUnits + kUnitsBytes;
 constexpr size_t kRadixTempBytes = 256 * 1024;  // radix_temp_words(kMax) * 4 must fit (checked at set-up)
 constexpr size_t kChunks = kRadixTemp + kRadixTempBytes;

@@ -25,7 +25,14 @@ __global__ void __launch_bounds__(kThreads) bint_kernel(const uint32_t* __restri
 // terminator (it is larger than exactly the m_ext old terminators and smaller
 // than every old suffix that starts with a symbol), then walk the read
 // backwards with Lemma 1: i := C[c] + rank(c, i, B_ext), c = P[k-1].
-template <class IdxT>
+// With kStage the superblock counters (at most kSuperStageBytes) are first
+// copied to shared memory, so a step reads one occurrence block and nothing
+// else.  The g values of a read are produced at descending positions; they
+// are kept in registers and written 16 bytes at a time wherever a group of
+// 16 / sizeof(IdxT) positions is complete (g starts on a 16-byte boundary).
+constexpr uint32_t kSuperStageBytes = 48 * 1024;
+
+template <class IdxT, bool kStage>
 __global__ void __launch_bounds__(kThreads) compute_ranks_kernel(const uint32_t* __restrict__ text,
                                                                  const unsigned long long* __restrict__ offsets,
                                                                  unsigned long long j_begin,
@@ -36,6 +43,12 @@ __global__ void __launch_bounds__(kThreads) compute_ranks_kernel(const uint32_t*
                                                                  unsigned long long n_ext,
                                                                  unsigned long long m_ext, IdxT* __restrict__ g,
                                                                  uint32_t* __restrict__ d_err) {
+    extern __shared__ unsigned long long s_super[];
+    if (kStage) {
+        const uint32_t words = ((uint32_t)(n_ext >> kSuperShift) + 1) * 4;
+        for (uint32_t x = threadIdx.x; x < words; x += kThreads) s_super[x] = super[x];
+        __syncthreads();
+    }
     const uint64_t j = (uint64_t)blockIdx.x * kThreads + threadIdx.x;
     if (j >= nreads) return;
     const uint64_t jj = j_begin + j;
@@ -45,8 +58,33 @@ __global__ void __launch_bounds__(kThreads) compute_ranks_kernel(const uint32_t*
     const uint64_t rs = oj - o0 + j;  // block-local position of the read's first symbol
     const uint64_t P = oj + jj;       // the same position in the append's text
     const unsigned long long C0 = d_C[0], C1 = d_C[1], C2 = d_C[2], C3 = d_C[3];
+
+    constexpr int G = 16 / (int)sizeof(IdxT);
+    IdxT s[G];  // s[0]: the newest value (lowest position)
+    int held = 0;
+    auto push = [&](uint64_t pos, IdxT v) {
+#pragma unroll
+        for (int r = G - 1; r > 0; --r) s[r] = s[r - 1];
+        s[0] = v;
+        ++held;
+        if ((pos & (G - 1)) == 0) {
+            if (held == G) {
+                if constexpr (G == 4) {
+                    *reinterpret_cast<uint4*>(g + pos) = make_uint4(s[0], s[1], s[2], s[3]);
+                } else {
+                    *reinterpret_cast<ulonglong2*>(g + pos) = make_ulonglong2(s[0], s[1]);
+                }
+            } else {
+#pragma unroll
+                for (int r = 0; r < G; ++r)
+                    if (r < held) g[pos + r] = s[r];
+            }
+            held = 0;
+        }
+    };
+
     unsigned long long i = m_ext;
-    g[rs + len] = (IdxT)i;
+    push(rs + len, (IdxT)i);
     uint64_t wcur = ~0ull;
     uint32_t word = 0;
     for (uint64_t k = len; k > 0; --k) {
@@ -57,13 +95,19 @@ __global__ void __launch_bounds__(kThreads) compute_ranks_kernel(const uint32_t*
         }
         const uint32_t c = (word >> (30u - 2u * (uint32_t)(t & 15))) & 3u;
         const unsigned long long Cc = c == 0 ? C0 : c == 1 ? C1 : c == 2 ? C2 : C3;
-        i = Cc + occ_rank(blocks, super, c, i);
+        const unsigned long long sup =
+            kStage ? s_super[((i >> kSuperShift) << 2) + c] : __ldg(super + ((i >> kSuperShift) << 2) + c);
+        i = Cc + sup + occ_rank_in_super(blocks, c, i);
         if (i > n_ext) {
             atomicOr(d_err, 8u);
             i = n_ext;
         }
-        g[rs + k - 1] = (IdxT)i;
+        push(rs + k - 1, (IdxT)i);
     }
+    // the lowest positions of the read, below its first complete group
+#pragma unroll
+    for (int r = 0; r < G; ++r)
+        if (r < held) g[rs + r] = s[r];
 }
 
 template <class IdxT>
@@ -193,10 +237,20 @@ void launch_compute_ranks(Launcher& L, const uint32_t* text, const uint64_t* d_o
     // per suffix: one 32-byte occurrence block, a g write, a quarter byte of text
     const double bytes = (double)(n_int - nreads) * (32.0 + 8.0) + (double)n_int * sizeof(IdxT) + n_int / 4.0 +
                          16.0 * nreads;
-    SBWT_LAUNCH(L, "compute_ranks", bytes, 0, nullptr, compute_ranks_kernel<IdxT>, ceil_div_u(nreads, kThreads),
-                kThreads, 0, text, reinterpret_cast<const unsigned long long*>(d_offsets),
-                (unsigned long long)j_begin, (unsigned long long)nreads, blocks, super, d_C,
-                (unsigned long long)n_ext, (unsigned long long)m_ext, g, d_err);
+    const size_t stage = ((n_ext >> kSuperShift) + 1) * 32;
+    if (stage <= kSuperStageBytes) {
+        auto* const kern = compute_ranks_kernel<IdxT, true>;
+        SBWT_LAUNCH(L, "compute_ranks", bytes, 0, nullptr, kern, ceil_div_u(nreads, kThreads), kThreads, stage, text,
+                    reinterpret_cast<const unsigned long long*>(d_offsets), (unsigned long long)j_begin,
+                    (unsigned long long)nreads, blocks, super, d_C, (unsigned long long)n_ext,
+                    (unsigned long long)m_ext, g, d_err);
+    } else {
+        auto* const kern = compute_ranks_kernel<IdxT, false>;
+        SBWT_LAUNCH(L, "compute_ranks", bytes, 0, nullptr, kern, ceil_div_u(nreads, kThreads), kThreads, 0, text,
+                    reinterpret_cast<const unsigned long long*>(d_offsets), (unsigned long long)j_begin,
+                    (unsigned long long)nreads, blocks, super, d_C, (unsigned long long)n_ext,
+                    (unsigned long long)m_ext, g, d_err);
+    }
 }
 
 template <class IdxT>

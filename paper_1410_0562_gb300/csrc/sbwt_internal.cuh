@@ -71,15 +71,15 @@ __device__ __forceinline__ unsigned long long match_code(unsigned long long x, u
     return ~(y | (y >> 1)) & 0x5555555555555555ull;
 }
 
-// rank(c, i, B) for a symbol code c (Eq. 2), from one 32-byte block load.
-__device__ __forceinline__ unsigned long long occ_rank(const OccBlock* __restrict__ blocks,
-                                                       const unsigned long long* __restrict__ super,
-                                                       uint32_t c, unsigned long long i) {
+// rank(c, i) within i's superblock: the block counter plus the matches of
+// c among the first (i & 63) rows of the block (one 32-byte sector).
+__device__ __forceinline__ unsigned long long occ_rank_in_super(const OccBlock* __restrict__ blocks, uint32_t c,
+                                                                unsigned long long i) {
     const ulonglong2* p = reinterpret_cast<const ulonglong2*>(blocks + (i >> kOccShift));
-    ulonglong2 s = __ldg(p);
-    ulonglong2 d = __ldg(p + 1);
-    uint32_t r = (uint32_t)(i & (kOccSpan - 1));
-    unsigned long long m0 = match_code(s.x, c), m1 = match_code(s.y, c);
+    const ulonglong2 s = __ldg(p);
+    const ulonglong2 d = __ldg(p + 1);
+    const uint32_t r = (uint32_t)(i & (kOccSpan - 1));
+    const unsigned long long m0 = match_code(s.x, c), m1 = match_code(s.y, c);
     uint32_t in_block;
     if (r <= 32) {
         in_block = __popcll(m0 & low_bits(2 * r));
@@ -87,8 +87,14 @@ __device__ __forceinline__ unsigned long long occ_rank(const OccBlock* __restric
         in_block = __popcll(m0) + __popcll(m1 & low_bits(2 * (r - 32)));
     }
     if (c == 0) in_block -= __popcll(d.x & low_bits(r));
-    uint32_t cnt = (uint32_t)(d.y >> (16 * c)) & 0xFFFFu;
-    return __ldg(super + ((i >> kSuperShift) << 2) + c) + cnt + in_block;
+    return ((uint32_t)(d.y >> (16 * c)) & 0xFFFFu) + in_block;
+}
+
+// rank(c, i, B) for a symbol code c (Eq. 2): superblock counter + the above.
+__device__ __forceinline__ unsigned long long occ_rank(const OccBlock* __restrict__ blocks,
+                                                       const unsigned long long* __restrict__ super,
+                                                       uint32_t c, unsigned long long i) {
+    return __ldg(super + ((i >> kSuperShift) << 2) + c) + occ_rank_in_super(blocks, c, i);
 }
 
 // ---------------------------------------------------------------------------

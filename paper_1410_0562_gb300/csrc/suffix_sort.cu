@@ -62,10 +62,11 @@ constexpr int kGItems = 16;
 constexpr int kGTile = kThreads * kGItems;  // elements per group-kernel tile
 constexpr unsigned kMaxGroupChunks = 2048;
 
-// Local sorts: kLThreads x kLItems pairs per CTA.
-constexpr int kLThreads = 512;
+// Local sorts: kLThreads x kLItems pairs per CTA, four CTAs per SM (small
+// CTAs keep more independent batches in flight between their barriers).
+constexpr int kLThreads = 256;
 constexpr int kLItems = 8;
-constexpr uint32_t kLCap = kLThreads * kLItems;  // 4096 long suffixes per unit at most
+constexpr uint32_t kLCap = kLThreads * kLItems;  // 2048 long suffixes per unit at most
 constexpr uint32_t kWindow = kLCap / 2;          // rows per window
 constexpr uint32_t kLSlots = kLCap + kLCap / kLItems;
 constexpr uint32_t kNone = 0xFFFFFFFFu;
@@ -656,7 +657,7 @@ __device__ __forceinline__ void batch_write_unsorted(Batch& b, uint32_t k, uint3
 // its first unit start ws (k0 = lcb in window ws, 0 after), in row order;
 // the sorted j-th long suffix takes the j-th of those rows, srow[j].  A
 // global-path unit ends a batch and is skipped.
-__global__ void __launch_bounds__(kLThreads, 2) sa_local_sort_kernel(
+__global__ void __launch_bounds__(kLThreads, 4) sa_local_sort_kernel(
     uint32_t n, const uint32_t* __restrict__ ll_t, const uint32_t* __restrict__ ll_row,
     const unsigned long long* __restrict__ ll_key, Units u, uint32_t nwin, uint32_t* __restrict__ sa,
     uint32_t* __restrict__ rank, uint32_t* __restrict__ loc_act, uint32_t* __restrict__ d_cnt,
@@ -833,7 +834,7 @@ __global__ void __launch_bounds__(kThreads) sa_round_gather_local_kernel(
 // One round for the local units, a batch of units per CTA step: sort the
 // unsorted members by (rank[t], rank[t + h]); a member of the group whose
 // head row is H that lands at offset x of its group takes row H + x.
-__global__ void __launch_bounds__(kLThreads, 2) sa_round_local_kernel(
+__global__ void __launch_bounds__(kLThreads, 4) sa_round_local_kernel(
     uint32_t* __restrict__ loc_act, const uint32_t* __restrict__ loc_next, Units u, uint32_t nwin, uint32_t n,
     uint32_t* __restrict__ rank, uint32_t* __restrict__ sa, uint32_t* __restrict__ d_cnt,
     uint32_t* __restrict__ d_err) {
