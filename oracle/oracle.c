@@ -52,8 +52,9 @@
  *     terminators included, so C[c_1] = m_ext.
  *   - Insert ties: new symbols with equal g_sa keep their SA_int order and
  *     go before old row g_sa; the final row of new symbol i is g_sa[i]+i.
- *   - Symbols are ordered by byte value (the alphabet is given in strictly
- *     increasing byte order); a byte outside the alphabet is an error.
+ *   - Symbols are ordered by byte value (the alphabet, 1 to 16 bytes, is
+ *     given in strictly increasing byte order); a byte outside the alphabet
+ *     is an error.
  *   - Reverse order: a block added before every read already in B_ext has
  *     terminators smaller than every old one, so Algorithm 2 starts each of
  *     its reads at i := 0.
@@ -131,7 +132,7 @@ static int suffix_cmp_void(const void *a, const void *b) {
 /* Check offsets and that every byte belongs to the alphabet. */
 static int validate(const uint8_t *reads, const uint64_t *offsets, uint64_t m,
                     const uint8_t *alphabet, int sigma) {
-    if (sigma < 1 || sigma > 4) return ORACLE_EINVAL;
+    if (sigma < 1 || sigma > 16) return ORACLE_EINVAL;
     for (int a = 1; a < sigma; ++a)
         if (alphabet[a] <= alphabet[a - 1]) return ORACLE_EINVAL;
     if (offsets[0] != 0) return ORACLE_EINVAL;
@@ -294,6 +295,7 @@ static int block_g_lemma1(const uint8_t *B_ext, uint64_t n_ext,
                           const uint8_t *reads, const uint64_t *offsets,
                           uint64_t j0, uint64_t j1, const uint8_t *alphabet,
                           int sigma, int before, uint64_t *g) {
+    if (sigma < 1 || sigma > 16) return ORACLE_EINVAL; /* count arrays hold sigma + 1 <= 17 */
     g_reads = reads;
     g_offsets = offsets;
     uint64_t *occ = (uint64_t *)calloc((n_ext + 1) * (size_t)(sigma + 1), sizeof(uint64_t));
@@ -308,7 +310,7 @@ static int block_g_lemma1(const uint8_t *B_ext, uint64_t n_ext,
         for (int y = 0; y <= sigma; ++y)
             occ[(k + 1) * (sigma + 1) + y] = occ[k * (sigma + 1) + y] + (x == y);
     }
-    uint64_t C[5] = {0, 0, 0, 0, 0};
+    uint64_t C[17] = {0}; /* sigma + 1 <= 17 entries */
     for (int x = 1; x <= sigma; ++x) C[x] = C[x - 1] + occ[n_ext * (sigma + 1) + x - 1];
     uint64_t m_ext = occ[n_ext * (sigma + 1) + 0];
 #if ORACLE_PLANT == 5
@@ -450,6 +452,7 @@ int oracle_setbwte_reverse(const uint8_t *reads, const uint64_t *offsets, uint64
 int oracle_lf_invert(const uint8_t *B, uint64_t n, uint64_t m,
                      const uint8_t *alphabet, int sigma, uint8_t *reads_out,
                      uint64_t cap, uint64_t *offsets_out) {
+    if (sigma < 1 || sigma > 16) return ORACLE_EINVAL; /* count arrays hold sigma + 1 <= 17 */
     uint64_t *occ = (uint64_t *)calloc((n + 1) * (size_t)(sigma + 1), sizeof(uint64_t));
     uint8_t *tmp = (uint8_t *)malloc(n + 1);
     if (!occ || !tmp) {
@@ -465,7 +468,7 @@ int oracle_lf_invert(const uint8_t *B, uint64_t n, uint64_t m,
             occ[(k + 1) * (sigma + 1) + y] = occ[k * (sigma + 1) + y] + (x == y);
     }
     if (!rc && occ[n * (sigma + 1)] != m) rc = ORACLE_EINVAL;
-    uint64_t C[5] = {0, 0, 0, 0, 0};
+    uint64_t C[17] = {0}; /* sigma + 1 <= 17 entries */
     for (int x = 1; x <= sigma && !rc; ++x) C[x] = C[x - 1] + occ[n * (sigma + 1) + x - 1];
     uint64_t w = 0;
     if (!rc) offsets_out[0] = 0;
@@ -504,6 +507,7 @@ int oracle_lf_invert(const uint8_t *B, uint64_t n, uint64_t m,
  * the full prefix-count table above).  Same contract as oracle_lf_invert. */
 int oracle_lf_invert_sampled(const uint8_t *B, uint64_t n, uint64_t m, const uint8_t *alphabet, int sigma,
                              uint8_t *reads_out, uint64_t cap, uint64_t *offsets_out) {
+    if (sigma < 1 || sigma > 16) return ORACLE_EINVAL; /* count arrays hold sigma + 1 <= 17 */
     const uint64_t nck = n / 64 + 1;
     uint64_t *ck = (uint64_t *)calloc(nck * (size_t)(sigma + 1), sizeof(uint64_t));
     int8_t *code = (int8_t *)malloc(n + 1);
@@ -515,7 +519,7 @@ int oracle_lf_invert_sampled(const uint8_t *B, uint64_t n, uint64_t m, const uin
         return ORACLE_ENOMEM;
     }
     int rc = ORACLE_OK;
-    uint64_t tot[5] = {0, 0, 0, 0, 0};
+    uint64_t tot[17] = {0};
     for (uint64_t k = 0; k < n && !rc; ++k) {
         if (k % 64 == 0)
             for (int y = 0; y <= sigma; ++y) ck[(k / 64) * (sigma + 1) + y] = tot[y];
@@ -529,7 +533,7 @@ int oracle_lf_invert_sampled(const uint8_t *B, uint64_t n, uint64_t m, const uin
     if (!rc && n % 64 == 0)
         for (int y = 0; y <= sigma; ++y) ck[(n / 64) * (sigma + 1) + y] = tot[y];
     if (!rc && tot[0] != m) rc = ORACLE_EINVAL;
-    uint64_t C[5] = {0, 0, 0, 0, 0};
+    uint64_t C[17] = {0}; /* sigma + 1 <= 17 entries */
     for (int x = 1; x <= sigma && !rc; ++x) C[x] = C[x - 1] + tot[x - 1];
     uint64_t w = 0;
     if (!rc) offsets_out[0] = 0;

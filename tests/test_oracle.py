@@ -155,6 +155,46 @@ def test_lemma1_ranks_equal_direct_ranks(seed):
     assert np.array_equal(g1, g2)
 
 
+WIDE_ALPHABETS = [b"ACGNT", b"ABCDEFGH", b"ABCDEFGHIJKLMNOP", bytes(range(0x61, 0x61 + 13))]
+
+
+@pytest.mark.parametrize("seed", range(24))
+def test_wide_alphabet_vs_brute_force(seed):
+    """Alphabets of 5 to 16 symbols: the same definition (Eq. 1), symbols
+    ordered by byte value."""
+    rng = np.random.default_rng(900 + seed)
+    alpha = WIDE_ALPHABETS[seed % len(WIDE_ALPHABETS)]
+    reads = random_set(rng, int(rng.integers(0, 10)), 9, alphabet=alpha)
+    data, off = pack(reads)
+    assert bytes(oracle.bwt(data, off, alpha)) == brute.bwt(reads)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_wide_alphabet_partition_lemma1_and_inversion(seed):
+    rng = np.random.default_rng(950 + seed)
+    alpha = WIDE_ALPHABETS[seed % len(WIDE_ALPHABETS)]
+    reads = random_set(rng, int(rng.integers(2, 50)), 30, alphabet=alpha)
+    data, off = pack(reads)
+    m = len(reads)
+    one_shot = oracle.bwt(data, off, alpha)
+    cuts = sorted(set(int(x) for x in rng.integers(1, m, size=3)))
+    bounds = [0] + cuts + [m]
+    assert np.array_equal(oracle.setbwte(data, off, bounds, alphabet=alpha), one_shot)
+    assert np.array_equal(oracle.setbwte(data, off, bounds, alphabet=alpha, reverse=True), one_shot)
+    j0 = int(rng.integers(1, m))
+    d_old, o_old = pack(reads[:j0])
+    B_ext = oracle.bwt(d_old, o_old, alpha)
+    assert np.array_equal(oracle.block_g_lemma1(B_ext, data, off, j0, m, alphabet=alpha),
+                          oracle.block_g_direct(data, off, j0, m))
+    rec, roff = oracle.lf_invert(one_shot, m, alphabet=alpha)
+    assert np.array_equal(rec, data) and np.array_equal(roff, off)
+
+
+def test_alphabet_size_limit():
+    with pytest.raises(oracle.OracleError):
+        oracle.bwt(*pack([b"AB"]), alphabet=bytes(range(0x41, 0x41 + 17)))
+
+
 def test_worked_example_intermediates():
     """AC then A: Algorithm 1 step by step (derivation in tests/golden)."""
     data, off = pack([b"AC", b"A"])
