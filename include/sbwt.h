@@ -24,8 +24,11 @@
  *   - A handle is not thread-safe: one call at a time per handle.
  *   - Host pointers are owned by the caller and only read (or written) during
  *     the call.  Device pointers must be device memory of the index's GPU.
- *   - Alphabet: 1 to 4 distinct bytes in strictly increasing byte order
- *     (c_1 < ... < c_sigma, Section 2), none of them '$' or 0.
+ *   - Alphabet: 1 to 16 distinct bytes in strictly increasing byte order
+ *     (c_1 < ... < c_sigma, Section 2), none of them '$' or 0.  Up to 4
+ *     symbols are held as 2-bit codes (text and rank dictionary, half a byte
+ *     per row of B); 5 to 16 symbols as 4-bit codes (one byte per row).
+ *     sbwt_bwt_noalloc takes 1 to 4 symbols only.
  *   - Read set: `reads` holds the concatenated bytes of m reads and `offsets`
  *     m+1 non-decreasing uint64 values with offsets[0] = 0; read j is
  *     reads[offsets[j] .. offsets[j+1]).  Empty reads are allowed.
@@ -288,8 +291,9 @@ int sbwt_load(const char *path, size_t hbm_budget_bytes, const sbwt_options *opt
  * first call before any stream capture.  All calls share the array and it
  * keeps the last call's contents; two calls whose GPU work overlapped would
  * race, so this function holds a process-wide lock until its stream has
- * finished.  Errors: SBWT_EINVAL (bad alphabet or offsets, a byte outside the
- * alphabet, more than SBWT_NOALLOC_MAX_SUFFIXES suffixes), SBWT_ERANGE
+ * finished.  Errors: SBWT_EINVAL (bad alphabet or offsets, an alphabet of
+ * more than 4 symbols, a byte outside the alphabet, more than
+ * SBWT_NOALLOC_MAX_SUFFIXES suffixes), SBWT_ERANGE
  * (cap < n), SBWT_EDEVICE. */
 #define SBWT_NOALLOC_MAX_SUFFIXES (1u << 18)
 int sbwt_bwt_noalloc(const char *alphabet, const uint8_t *reads, const uint64_t *offsets, uint64_t m,

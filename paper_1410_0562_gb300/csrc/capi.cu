@@ -47,9 +47,11 @@ constexpr unsigned kPlanCap = 4096;  // blocks a device-planned append may have
 }  // namespace
 
 struct sbwt_index {
-    uint8_t alphabet[4] = {0, 0, 0, 0};
+    uint8_t alphabet[16] = {0};
     int sigma = 0;
-    uint32_t alpha4 = 0;
+    uint32_t alpha4 = 0;     // the first four symbols, packed (2-bit kernels)
+    Alphabet16 alpha16 = {};  // all symbols (4-bit kernels, read-back)
+    int code_bits = 2;       // 2 for up to 4 symbols, 4 for 5 to 16
     size_t budget = 0;
     uint32_t index_bits = 0;
     uint64_t M = kDefaultBlock;
@@ -207,10 +209,11 @@ int device_init(sbwt_index* idx) {
     if (cudaMallocHost(&idx->h_summary, sizeof(PlanSummary)) != cudaSuccess) return SBWT_EDEVICE;
     // the committed dictionary starts empty: one zero block, one zero superblock, C = 0
     Dict& d = idx->dict[idx->cur];
-    if (grow(d.blocks, sizeof(OccBlock)) || grow(d.super, 32) || grow(d.C, 32)) return SBWT_ENOMEM;
-    zero_async(d.blocks, sizeof(OccBlock), idx->stream);
-    zero_async(d.super, 32, idx->stream);
-    zero_async(d.C, 32, idx->stream);
+    const size_t bb = dict_block_bytes(idx->code_bits), cb = 8 * dict_codes(idx->code_bits);
+    if (grow(d.blocks, bb) || grow(d.super, cb) || grow(d.C, cb)) return SBWT_ENOMEM;
+    zero_async(d.blocks, bb, idx->stream);
+    zero_async(d.super, cb, idx->stream);
+    zero_async(d.C, cb, idx->stream);
     if (grow(idx->err, 4)) return SBWT_ENOMEM;
     if (cudaStreamSynchronize(idx->stream) != cudaSuccess) return SBWT_EDEVICE;
     idx->dev_ready = true;
@@ -269,7 +272,7 @@ std::vector<Need> buffer_needs(sbwt_index* idx, const Plan& p, bool host_input, 
         v.push_back({&idx->reads, (size_t)p.nbytes});
         v.push_back({&idx->offsets, (size_t)(m_new + 1) * 8});
     }
-    v.push_back({&idx->text, (size_t)((p.npos + 31) / 32 * 2 + kTextPadWords) * 4});
+    v.push_back({&idx->text, (size_t)(text_words(p.npos, idx->code_bits) + kTextPadWords) * 4});
     v.push_back({&idx->term, (size_t)((p.npos + 31) / 32 + kTermPadWords) * 4});
     for (DevBuf* b : {&idx->keys, &idx->keys_alt}) v.push_back({b, (size_t)cap * 8});
     for (DevBuf* b : {&idx->vals, &idx->vals_alt, &idx->sa, &idx->sa2, &idx->rank, &idx->act_pos0, &idx->act_pos1,
@@ -282,12 +285,14 @@ std::vector<Need> buffer_needs(sbwt_index* idx, const Plan& p, bool host_input, 
     v.push_back({&idx->g, (size_t)cap * w});
     v.push_back({&idx->gsa, (size_t)cap * w});
     v.push_back({&idx->bint, (size_t)cap});
-    v.push_back({&idx->sb_tot, (size_t)dict_supers(n_final) * 16});
+    const int cb = idx->code_bits;
+    const uint64_t nsb = dict_supers_of(n_final, cb);
+    v.push_back({&idx->sb_tot, (size_t)nsb * 4 * dict_codes(cb)});
     for (int k = 0; k < 3; ++k) {
         if (k == idx->cur) continue;
-        v.push_back({&idx->dict[k].blocks, (size_t)dict_blocks(n_final) * sizeof(OccBlock), true});
-        v.push_back({&idx->dict[k].super, (size_t)dict_supers(n_final) * 32, true});
-        v.push_back({&idx->dict[k].C, 32, true});
+        v.push_back({&idx->dict[k].blocks, (size_t)dict_blocks(n_final) * dict_block_bytes(cb), true});
+        v.push_back({&idx->dict[k].super, (size_t)nsb * 8 * dict_codes(cb), true});
+        v.push_back({&idx->dict[k].C, 8 * dict_codes(cb), true});
     }
     return v;
 }
@@ -401,21 +406,21 @@ void run_block(sbwt_index* idx, const BlockPlan& bp, const uint64_t* d_offsets, 
     const cudaStream_t s = L.stream;
     if (q >= 2) cudaStreamWaitEvent(idx->side, idx->ev_consumed[q & 1], 0);
     L.stream = idx->side;
-    suffix_sort_block(L, text, term, bp.base, n, (uint32_t)bp.max_len, b);
+    suffix_sort_block(L, text, term, bp.base, n, (uint32_t)bp.max_len, idx->code_bits, b);
     cudaEventRecord(idx->ev_sorted[q & 1], idx->side);
     L.stream = s;
     // ComputeRanks needs only the dictionary; the gather waits for the sort
-    launch_compute_ranks<IdxT>(L, text, d_offsets, bp.j0, bp.j1 - bp.j0, bp.n_int, (const OccBlock*)src.blocks.p,
+    launch_compute_ranks<IdxT>(L, text, d_offsets, bp.j0, bp.j1 - bp.j0, bp.n_int, (const void*)src.blocks.p,
                                (const unsigned long long*)src.super.p, (const unsigned long long*)src.C.p, n_ext,
-                               prepend ? 0 : m_ext, (IdxT*)idx->g.p, (uint32_t*)idx->err.p);
+                               prepend ? 0 : m_ext, (IdxT*)idx->g.p, (uint32_t*)idx->err.p, idx->code_bits);
     cudaStreamWaitEvent(s, idx->ev_sorted[q & 1], 0);
     launch_bint_gather<IdxT>(L, text, term, bp.base, b.sa, (const IdxT*)idx->g.p, n, (uint8_t*)idx->bint.p,
-                             (IdxT*)idx->gsa.p);
+                             (IdxT*)idx->gsa.p, idx->code_bits);
     cudaEventRecord(idx->ev_consumed[q & 1], s);
-    launch_insert<IdxT>(L, (const OccBlock*)src.blocks.p, n_ext, (const uint8_t*)idx->bint.p,
-                        (const IdxT*)idx->gsa.p, bp.n_int, (OccBlock*)dst.blocks.p,
+    launch_insert<IdxT>(L, (const void*)src.blocks.p, n_ext, (const uint8_t*)idx->bint.p,
+                        (const IdxT*)idx->gsa.p, bp.n_int, (void*)dst.blocks.p,
                         (unsigned long long*)dst.super.p, (unsigned long long*)dst.C.p, m_ext + (bp.j1 - bp.j0),
-                        (uint32_t*)idx->sb_tot.p);
+                        (uint32_t*)idx->sb_tot.p, idx->code_bits);
 }
 
 Plan host_plan(const uint64_t* h_off, uint64_t m_new, uint64_t M) {
@@ -433,7 +438,7 @@ int append_impl(sbwt_index* idx, const uint8_t* d_reads, const uint64_t* d_offse
         p.cap = std::max(p.cap, b.n_int);
         p.max_len = std::max(p.max_len, b.max_len);
     }
-    p.slots = suffix_sort_log_slots((uint32_t)p.max_len);
+    p.slots = suffix_sort_log_slots((uint32_t)p.max_len, idx->code_bits);
     const uint64_t n_final = idx->n + p.npos;
     if (idx->index_bits == 32 && n_final >= 0xFFFFFFFFull) return SBWT_EINVAL;
     p.idx64 = idx->index_bits == 64 || n_final >= 0xFFFFFFFFull;
@@ -469,15 +474,19 @@ int append_impl(sbwt_index* idx, const uint8_t* d_reads, const uint64_t* d_offse
 
     // Everything the device does for this append, after the input copies.
     auto enqueue = [&]() {
-        const uint64_t text_words = (p.npos + 31) / 32 * 2, term_words = (p.npos + 31) / 32;
-        cudaMemsetAsync((uint32_t*)idx->text.p + text_words, 0, kTextPadWords * 4, s);
+        const uint64_t tw = text_words(p.npos, idx->code_bits), term_words = (p.npos + 31) / 32;
+        cudaMemsetAsync((uint32_t*)idx->text.p + tw, 0, kTextPadWords * 4, s);
         cudaMemsetAsync((uint32_t*)idx->term.p + term_words, 0, kTermPadWords * 4, s);
         cudaMemsetAsync(idx->err.p, 0, 4, s);
         // A byte outside the alphabet sets bit 0 of the error word; the blocks
         // still run (into scratch dictionaries) and the check at the end
         // refuses the result, which saves a round trip on every valid append.
-        launch_pack(L, d_reads, d_offsets, m_new, p.npos, idx->alpha4, idx->sigma, (uint32_t*)idx->text.p,
-                    (uint32_t*)idx->term.p, (uint32_t*)idx->err.p);
+        if (idx->code_bits == 4)
+            launch_pack_w(L, d_reads, d_offsets, m_new, p.npos, idx->alpha16, idx->sigma, (uint32_t*)idx->text.p,
+                          (uint32_t*)idx->term.p, (uint32_t*)idx->err.p);
+        else
+            launch_pack(L, d_reads, d_offsets, m_new, p.npos, idx->alpha4, idx->sigma, (uint32_t*)idx->text.p,
+                        (uint32_t*)idx->term.p, (uint32_t*)idx->err.p);
         int src = idx->cur;
         uint64_t n_ext = idx->n, m_ext = idx->m;
         cudaEventRecord(idx->ev_fork, s);  // the sorts read the packed text
@@ -574,7 +583,7 @@ int append_impl(sbwt_index* idx, const uint8_t* d_reads, const uint64_t* d_offse
 int parse_alphabet(const char* alphabet, sbwt_index* idx) {
     if (!alphabet) return SBWT_EINVAL;
     size_t len = strlen(alphabet);
-    if (len < 1 || len > 4) return SBWT_EINVAL;
+    if (len < 1 || len > 16) return SBWT_EINVAL;
     for (size_t a = 0; a < len; ++a) {
         uint8_t c = (uint8_t)alphabet[a];
         if (c == '$') return SBWT_EINVAL;
@@ -582,8 +591,10 @@ int parse_alphabet(const char* alphabet, sbwt_index* idx) {
         idx->alphabet[a] = c;
     }
     idx->sigma = (int)len;
+    idx->code_bits = len > 4 ? 4 : 2;
     idx->alpha4 = 0;
     for (int a = 0; a < 4; ++a) idx->alpha4 |= (uint32_t)idx->alphabet[a < (int)len ? a : 0] << (8 * a);
+    for (int a = 0; a < 16; ++a) idx->alpha16.a[a] = idx->alphabet[a < (int)len ? a : 0];
     return SBWT_OK;
 }
 
@@ -593,7 +604,10 @@ int parse_alphabet(const char* alphabet, sbwt_index* idx) {
 // checksum of everything before it.
 // ---------------------------------------------------------------------------
 constexpr char kFileMagic[8] = {'S', 'B', 'W', 'T', 'I', 'D', 'X', '1'};
+// Version 1: up to 4 symbols, the 2-bit dictionary.  Version 2: 5 to 16
+// symbols, the 4-bit dictionary; symbols 5.. in alphabet_hi.
 constexpr uint32_t kFileVersion = 1;
+constexpr uint32_t kFileVersionWide = 2;
 
 struct FileHeader {
     char magic[8];
@@ -602,8 +616,9 @@ struct FileHeader {
     uint8_t alphabet[4];
     uint32_t index_bits;
     uint64_t n, m;
-    uint64_t n_blocks, n_supers;  // array lengths: dict_blocks(n), dict_supers(n)
-    uint64_t reserved[4];
+    uint64_t n_blocks, n_supers;  // array lengths: dict_blocks(n), the superblocks of the layout
+    uint8_t alphabet_hi[12];
+    uint8_t reserved[20];
 };
 static_assert(sizeof(FileHeader) == 88, "fixed header layout");
 
@@ -922,12 +937,12 @@ int sbwt_get_bwt(sbwt_index* idx, uint8_t* out, uint64_t cap, uint64_t* n_out) {
     // chunks already unpacked
     constexpr uint64_t kChunkRows = 1ull << 24;
     const cudaStream_t s = idx->stream;
-    const OccBlock* blocks = (const OccBlock*)idx->dict[idx->cur].blocks.p;
+    const void* blocks = idx->dict[idx->cur].blocks.p;
     uint8_t* staged = (uint8_t*)idx->out_bytes.p;
     int e = 0;
     for (uint64_t r0 = 0; r0 < idx->n; r0 += kChunkRows, e ^= 1) {
         const uint64_t r1 = std::min(idx->n, r0 + kChunkRows);
-        launch_unpack(idx->L, blocks, r0, r1, idx->alpha4, staged);
+        launch_unpack(idx->L, blocks, r0, r1, idx->alpha16, staged, idx->code_bits);
         cudaEventRecord(idx->ev_sorted[e], s);
         cudaStreamWaitEvent(idx->side, idx->ev_sorted[e], 0);
         cudaMemcpyAsync(out + r0, staged + r0, r1 - r0, cudaMemcpyDeviceToHost, idx->side);
@@ -945,7 +960,7 @@ int sbwt_rank_batch(sbwt_index* idx, const uint8_t* cs, const uint64_t* ks, uint
     for (uint64_t i = 0; i < q; ++i) {
         if (ks[i] > idx->n) return SBWT_EINVAL;
         int code = -1;
-        if (cs[i] == '$') code = 4;
+        if (cs[i] == '$') code = (int)dict_codes(idx->code_bits);  // the terminator's query code
         for (int a = 0; a < idx->sigma; ++a)
             if (cs[i] == idx->alphabet[a]) code = a;
         if (code < 0) return SBWT_EINVAL;
@@ -964,9 +979,9 @@ int sbwt_rank_batch(sbwt_index* idx, const uint8_t* cs, const uint64_t* ks, uint
     cudaMemcpyAsync(idx->q_codes.p, codes.data(), q, cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(idx->q_ks.p, ks, q * 8, cudaMemcpyHostToDevice, s);
     const Dict& d = idx->dict[idx->cur];
-    launch_rank_batch(idx->L, (const OccBlock*)d.blocks.p, (const unsigned long long*)d.super.p,
+    launch_rank_batch(idx->L, (const void*)d.blocks.p, (const unsigned long long*)d.super.p,
                       (const uint8_t*)idx->q_codes.p, (const unsigned long long*)idx->q_ks.p, q,
-                      (unsigned long long*)idx->q_out.p);
+                      (unsigned long long*)idx->q_out.p, idx->code_bits);
     cudaMemcpyAsync(out, idx->q_out.p, q * 8, cudaMemcpyDeviceToHost, s);
     if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) return SBWT_EDEVICE;
     return SBWT_OK;
@@ -992,9 +1007,9 @@ int sbwt_count(sbwt_index* idx, const uint8_t* patterns, const uint64_t* offsets
     if (total) cudaMemcpyAsync(idx->c_pats.p, patterns, total, cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(idx->c_offs.p, offsets, (q + 1) * 8, cudaMemcpyHostToDevice, s);
     const Dict& d = idx->dict[idx->cur];
-    launch_count(idx->L, (const OccBlock*)d.blocks.p, (const unsigned long long*)d.super.p,
-                 (const unsigned long long*)d.C.p, idx->n, idx->alpha4, idx->sigma, (const uint8_t*)idx->c_pats.p,
-                 (const uint64_t*)idx->c_offs.p, q, total, (unsigned long long*)idx->q_out.p);
+    launch_count(idx->L, (const void*)d.blocks.p, (const unsigned long long*)d.super.p,
+                 (const unsigned long long*)d.C.p, idx->n, idx->alpha16, idx->sigma, (const uint8_t*)idx->c_pats.p,
+                 (const uint64_t*)idx->c_offs.p, q, total, (unsigned long long*)idx->q_out.p, idx->code_bits);
     cudaMemcpyAsync(counts, idx->q_out.p, q * 8, cudaMemcpyDeviceToHost, s);
     if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) return SBWT_EDEVICE;
     return SBWT_OK;
@@ -1028,9 +1043,9 @@ int sbwt_reset(sbwt_index* idx) {
     if (!idx->dev_ready) return SBWT_OK;
     if (set_device(idx)) return SBWT_EDEVICE;
     Dict& d = idx->dict[idx->cur];
-    zero_async(d.blocks, sizeof(OccBlock), idx->stream);
-    zero_async(d.super, 32, idx->stream);
-    zero_async(d.C, 32, idx->stream);
+    zero_async(d.blocks, dict_block_bytes(idx->code_bits), idx->stream);
+    zero_async(d.super, 8 * dict_codes(idx->code_bits), idx->stream);
+    zero_async(d.C, 8 * dict_codes(idx->code_bits), idx->stream);
     if (cudaStreamSynchronize(idx->stream) != cudaSuccess) return SBWT_EDEVICE;
     return SBWT_OK;
 }
@@ -1038,30 +1053,30 @@ int sbwt_reset(sbwt_index* idx) {
 int sbwt_save(sbwt_index* idx, const char* path) {
     if (!idx || !path) return SBWT_EINVAL;
     if (busy(idx)) return SBWT_EBUSY;
+    const int cb = idx->code_bits;
+    const size_t bb = dict_block_bytes(cb), codes = dict_codes(cb);
     FileHeader h = {};
     memcpy(h.magic, kFileMagic, sizeof(h.magic));
-    h.version = kFileVersion;
+    h.version = cb == 4 ? kFileVersionWide : kFileVersion;
     h.sigma = (uint32_t)idx->sigma;
     memcpy(h.alphabet, idx->alphabet, 4);
+    memcpy(h.alphabet_hi, idx->alphabet + 4, 12);
     h.index_bits = idx->index_bits;
     h.n = idx->n;
     h.m = idx->m;
     h.n_blocks = dict_blocks(idx->n);
-    h.n_supers = dict_supers(idx->n);
-    std::vector<OccBlock> blocks(h.n_blocks);
-    std::vector<unsigned long long> super(4 * h.n_supers), C(4, 0ull);
+    h.n_supers = dict_supers_of(idx->n, cb);
+    std::vector<uint8_t> blocks(h.n_blocks * bb, 0);
+    std::vector<unsigned long long> super(codes * h.n_supers, 0ull), C(codes, 0ull);
     if (idx->dev_ready) {  // else the index is empty: all zero
         if (set_device(idx) || cudaStreamSynchronize(idx->stream) != cudaSuccess) return SBWT_EDEVICE;
         const Dict& d = idx->dict[idx->cur];
-        if (cudaMemcpy(blocks.data(), d.blocks.p, blocks.size() * sizeof(OccBlock), cudaMemcpyDeviceToHost) !=
-                cudaSuccess ||
+        if (cudaMemcpy(blocks.data(), d.blocks.p, blocks.size(), cudaMemcpyDeviceToHost) != cudaSuccess ||
             cudaMemcpy(super.data(), d.super.p, super.size() * 8, cudaMemcpyDeviceToHost) != cudaSuccess ||
-            cudaMemcpy(C.data(), d.C.p, 32, cudaMemcpyDeviceToHost) != cudaSuccess) {
+            cudaMemcpy(C.data(), d.C.p, C.size() * 8, cudaMemcpyDeviceToHost) != cudaSuccess) {
             cudaGetLastError();
             return SBWT_EDEVICE;
         }
-    } else {
-        memset(blocks.data(), 0, blocks.size() * sizeof(OccBlock));
     }
     Fnv1a sum;
     File out;
@@ -1071,8 +1086,8 @@ int sbwt_save(sbwt_index* idx, const char* path) {
         sum.add(p, n);
         return fwrite(p, 1, n, out.f) == n;
     };
-    bool ok = put(&h, sizeof(h)) && put(blocks.data(), blocks.size() * sizeof(OccBlock)) &&
-              put(super.data(), super.size() * 8) && put(C.data(), 32);
+    bool ok = put(&h, sizeof(h)) && put(blocks.data(), blocks.size()) && put(super.data(), super.size() * 8) &&
+              put(C.data(), C.size() * 8);
     const uint64_t digest = sum.h;
     ok = ok && fwrite(&digest, 1, 8, out.f) == 8;
     ok = fclose(out.f) == 0 && ok;
@@ -1089,32 +1104,38 @@ int sbwt_load(const char* path, size_t hbm_budget_bytes, const sbwt_options* opt
     if (!in.f) return SBWT_EIO;
     FileHeader h;
     if (fread(&h, 1, sizeof(h), in.f) != sizeof(h)) return SBWT_EIO;
-    if (memcmp(h.magic, kFileMagic, sizeof(h.magic)) != 0 || h.version != kFileVersion) return SBWT_EINVAL;
-    if (h.sigma < 1 || h.sigma > 4 || (h.index_bits != 0 && h.index_bits != 32 && h.index_bits != 64) ||
-        h.n_blocks != dict_blocks(h.n) || h.n_supers != dict_supers(h.n) || h.m > h.n)
+    if (memcmp(h.magic, kFileMagic, sizeof(h.magic)) != 0) return SBWT_EINVAL;
+    const bool wide = h.version == kFileVersionWide;
+    if (h.version != kFileVersion && !wide) return SBWT_EINVAL;
+    const int cb = wide ? 4 : 2;
+    if (h.sigma < 1 || h.sigma > (wide ? 16u : 4u) || (wide && h.sigma <= 4) ||
+        (h.index_bits != 0 && h.index_bits != 32 && h.index_bits != 64) || h.n_blocks != dict_blocks(h.n) ||
+        h.n_supers != dict_supers_of(h.n, cb) || h.m > h.n)
         return SBWT_EINVAL;
+    const size_t bb = dict_block_bytes(cb), codes = dict_codes(cb);
     // the arrays must be exactly what the rest of the file holds
     if (fseek(in.f, 0, SEEK_END) != 0) return SBWT_EIO;
     const long size = ftell(in.f);
-    const uint64_t want = sizeof(h) + h.n_blocks * sizeof(OccBlock) + h.n_supers * 32 + 32 + 8;
+    const uint64_t want = sizeof(h) + h.n_blocks * bb + h.n_supers * codes * 8 + codes * 8 + 8;
     if (size < 0 || (uint64_t)size != want) return SBWT_EINVAL;
     if (fseek(in.f, (long)sizeof(h), SEEK_SET) != 0) return SBWT_EIO;
-    std::vector<OccBlock> blocks(h.n_blocks);
-    std::vector<unsigned long long> super(4 * h.n_supers), C(4);
+    std::vector<uint8_t> blocks(h.n_blocks * bb);
+    std::vector<unsigned long long> super(codes * h.n_supers), C(codes);
     uint64_t digest = 0;
-    if (fread(blocks.data(), 1, blocks.size() * sizeof(OccBlock), in.f) != blocks.size() * sizeof(OccBlock) ||
-        fread(super.data(), 1, super.size() * 8, in.f) != super.size() * 8 || fread(C.data(), 1, 32, in.f) != 32 ||
-        fread(&digest, 1, 8, in.f) != 8)
+    if (fread(blocks.data(), 1, blocks.size(), in.f) != blocks.size() ||
+        fread(super.data(), 1, super.size() * 8, in.f) != super.size() * 8 ||
+        fread(C.data(), 1, C.size() * 8, in.f) != C.size() * 8 || fread(&digest, 1, 8, in.f) != 8)
         return SBWT_EIO;
     Fnv1a sum;
     sum.add(&h, sizeof(h));
-    sum.add(blocks.data(), blocks.size() * sizeof(OccBlock));
+    sum.add(blocks.data(), blocks.size());
     sum.add(super.data(), super.size() * 8);
-    sum.add(C.data(), 32);
+    sum.add(C.data(), C.size() * 8);
     if (sum.h != digest) return SBWT_EINVAL;
 
-    char alpha[5] = {0, 0, 0, 0, 0};
-    memcpy(alpha, h.alphabet, h.sigma);
+    char alpha[17] = {0};
+    memcpy(alpha, h.alphabet, std::min<uint32_t>(h.sigma, 4));
+    if (h.sigma > 4) memcpy(alpha + 4, h.alphabet_hi, h.sigma - 4);
     sbwt_options o = {};
     if (opt) o = *opt;
     if (o.index_bits == 0) o.index_bits = h.index_bits;
@@ -1127,14 +1148,12 @@ int sbwt_load(const char* path, size_t hbm_budget_bytes, const sbwt_options* opt
     };
     if (int rc = device_init(idx)) return fail(rc);
     Dict& d = idx->dict[idx->cur];
-    if (int rc = reserve(idx, {{&d.blocks, blocks.size() * sizeof(OccBlock), true},
-                               {&d.super, super.size() * 8, true},
-                               {&d.C, 32, true}}))
+    if (int rc = reserve(idx, {{&d.blocks, blocks.size(), true}, {&d.super, super.size() * 8, true},
+                               {&d.C, C.size() * 8, true}}))
         return fail(rc);
-    if (cudaMemcpy(d.blocks.p, blocks.data(), blocks.size() * sizeof(OccBlock), cudaMemcpyHostToDevice) !=
-            cudaSuccess ||
+    if (cudaMemcpy(d.blocks.p, blocks.data(), blocks.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(d.super.p, super.data(), super.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(d.C.p, C.data(), 32, cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaMemcpy(d.C.p, C.data(), C.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess) {
         cudaGetLastError();
         return fail(SBWT_EDEVICE);
     }

@@ -167,54 +167,227 @@ __global__ void __launch_bounds__(kThreads) insert_kernel(const OccBlock* __rest
     }
 }
 
+// ---------------------------------------------------------------------------
+// The same merge for the 4-bit dictionary (5 to 16 symbols): one output
+// block per thread, a CTA of 256 threads builds four 64-block superblocks;
+// the 12-bit block counters are scanned per code across the 64 threads of a
+// superblock (two warps).
+
+__device__ __forceinline__ unsigned long long funnel_r(unsigned long long lo, unsigned long long hi, uint32_t bs) {
+    return bs == 0 ? lo : (lo >> bs) | (hi << (64 - bs));
+}
+
+struct WindowW {
+    unsigned long long w[4], dm;
+};
+
+// 64 old rows starting at row s (rows past the old end read as zero).
+__device__ __forceinline__ WindowW old_window_w(const OccBlockW* __restrict__ old_blocks, uint64_t nb_old, uint64_t s) {
+    const uint64_t bs = s >> kOccShift;
+    const uint32_t off = (uint32_t)(s & (kOccSpan - 1));
+    const OccBlockW& A = old_blocks[bs];
+    unsigned long long x[9];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) x[k] = A.sym[k];
+    unsigned long long da = A.dmask, db = 0;
+#pragma unroll
+    for (int k = 4; k < 9; ++k) x[k] = 0;
+    if (bs + 1 < nb_old) {
+        const OccBlockW& B = old_blocks[bs + 1];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) x[4 + k] = B.sym[k];
+        db = B.dmask;
+    }
+    // shift the 512-bit pair right by 4 * off bits: whole words first
+    const uint32_t sh = 4 * off, ws = sh >> 6, bsh = sh & 63;
+    if (ws & 2) {
+#pragma unroll
+        for (int k = 0; k < 7; ++k) x[k] = k + 2 < 9 ? x[k + 2] : 0ull;
+    }
+    if (ws & 1) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) x[k] = x[k + 1];
+    }
+    WindowW w;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) w.w[k] = funnel_r(x[k], x[k + 1], bsh);
+    w.dm = off == 0 ? da : ((da >> off) | (db << (64 - off)));
+    return w;
+}
+
+// Splice one row holding `code` (terminator when dollar) in at position p.
+__device__ __forceinline__ void splice_w(WindowW& w, uint32_t p, uint32_t code, uint32_t dollar) {
+    const uint32_t k = p >> 4, b = 4 * (p & 15);
+#pragma unroll
+    for (int j = 3; j > 0; --j)
+        if ((uint32_t)j > k) w.w[j] = (w.w[j] << 4) | (w.w[j - 1] >> 60);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        if ((uint32_t)j == k) {
+            const unsigned long long keep = low_bits(b);
+            w.w[j] = (w.w[j] & keep) | ((unsigned long long)code << b) | ((w.w[j] & ~keep) << 4);
+        }
+    }
+    const unsigned long long keepd = low_bits(p);
+    w.dm = (w.dm & keepd) | ((unsigned long long)dollar << p) | ((w.dm & ~keepd) << 1);
+}
+
+template <class IdxT>
+__global__ void __launch_bounds__(kThreads) insert_w_kernel(const OccBlockW* __restrict__ old_blocks,
+                                                            unsigned long long n_ext, const uint8_t* __restrict__ bint,
+                                                            const IdxT* __restrict__ gsa, unsigned long long n_int,
+                                                            OccBlockW* __restrict__ new_blocks,
+                                                            unsigned long long n_new, unsigned long long nsb,
+                                                            uint32_t* __restrict__ sb_tot) {
+    __shared__ uint32_t warp_tot[kThreads / 32][kSigmaW];
+    const uint64_t nb_new = (n_new >> kOccShift) + 1;
+    const uint64_t nb_old = (n_ext >> kOccShift) + 1;
+    const uint64_t b = (uint64_t)blockIdx.x * kThreads + threadIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    WindowW w;
+    w.w[0] = w.w[1] = w.w[2] = w.w[3] = w.dm = 0;
+    uint32_t cnt[kSigmaW];
+#pragma unroll
+    for (int c = 0; c < kSigmaW; ++c) cnt[c] = 0;
+    if (b < nb_new) {
+        const uint64_t o = b << kOccShift;
+        uint64_t lo = 0, hi = n_int;  // first i with g_sa[i] + i >= o
+        while (lo < hi) {
+            const uint64_t mid = lo + ((hi - lo) >> 1);
+            if ((uint64_t)gsa[mid] + mid < o) lo = mid + 1; else hi = mid;
+        }
+        uint64_t i = lo;
+        const uint64_t s_old = o >= i ? min((unsigned long long)(o - i), n_ext) : 0ull;
+        w = old_window_w(old_blocks, nb_old, s_old);
+        while (i < n_int) {
+            const uint64_t row = (uint64_t)gsa[i] + i;
+            if (row >= o + kOccSpan) break;
+            const uint8_t x = bint[i];
+            splice_w(w, (uint32_t)(row - o), x == kBintDollar ? 0u : x, x == kBintDollar ? 1u : 0u);
+            ++i;
+        }
+        const uint32_t valid = n_new > o ? (uint32_t)min((unsigned long long)kOccSpan, n_new - o) : 0u;
+        unsigned long long vm[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const uint32_t rows = valid > 16u * k ? min(valid - 16u * k, 16u) : 0u;
+            vm[k] = low_bits(4 * rows);
+            w.w[k] &= vm[k];
+        }
+        w.dm &= low_bits(valid);
+#pragma unroll
+        for (int c = 0; c < kSigmaW; ++c) {
+            uint32_t s = 0;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) s += __popcll(match_code4(w.w[k], c) & vm[k]);
+            cnt[c] = s;
+        }
+        cnt[0] -= __popcll(w.dm);
+    }
+    // per code: inclusive scan over the superblock's 64 threads (two warps)
+    uint32_t incl[kSigmaW];
+#pragma unroll
+    for (int c = 0; c < kSigmaW; ++c) {
+        uint32_t x = cnt[c];
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
+            if (lane >= d) x += y;
+        }
+        incl[c] = x;
+        if (lane == 31) warp_tot[warp][c] = x;
+    }
+    __syncthreads();
+    if (warp & 1) {
+#pragma unroll
+        for (int c = 0; c < kSigmaW; ++c) incl[c] += warp_tot[warp - 1][c];
+    }
+    if (b < nb_new) {
+        unsigned long long cw[3] = {0ull, 0ull, 0ull};
+#pragma unroll
+        for (int c = 0; c < kSigmaW; ++c) {
+            const unsigned long long v = (incl[c] - cnt[c]) & 0xFFFu;  // exclusive: below 4096
+            const int o = 12 * c, wd = o >> 6, sh = o & 63;
+            cw[wd] |= v << sh;
+            if (sh > 52) cw[wd + 1] |= v >> (64 - sh);
+        }
+        ulonglong2* dst = reinterpret_cast<ulonglong2*>(new_blocks + b);
+        dst[0] = make_ulonglong2(w.w[0], w.w[1]);
+        dst[1] = make_ulonglong2(w.w[2], w.w[3]);
+        dst[2] = make_ulonglong2(w.dm, cw[0]);
+        dst[3] = make_ulonglong2(cw[1], cw[2]);
+    }
+    const uint64_t s = b >> (kSuperShiftW - kOccShift);
+    if ((b & (kBlocksPerSuperW - 1)) == kBlocksPerSuperW - 1 && s < nsb) {
+#pragma unroll
+        for (int c = 0; c < kSigmaW; ++c) sb_tot[(uint64_t)kSigmaW * s + c] = incl[c];
+    }
+}
+
 constexpr int kScanThreads = 1024;
 
+template <int kCodes>
 __global__ void __launch_bounds__(kScanThreads) super_scan_kernel(const uint32_t* __restrict__ sb_tot,
                                                                   unsigned long long nsb,
                                                                   unsigned long long* __restrict__ super,
                                                                   unsigned long long* __restrict__ C,
                                                                   unsigned long long m) {
-    unsigned long long carry[4] = {0, 0, 0, 0};
+    unsigned long long carry[kCodes];
+#pragma unroll
+    for (int c = 0; c < kCodes; ++c) carry[c] = 0;
     for (unsigned long long base = 0; base < nsb; base += kScanThreads) {
         const unsigned long long s = base + threadIdx.x;
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const unsigned long long v = s < nsb ? sb_tot[4 * s + c] : 0ull;
+        for (int c = 0; c < kCodes; ++c) {
+            const unsigned long long v = s < nsb ? sb_tot[kCodes * s + c] : 0ull;
             unsigned long long tot;
             const unsigned long long ex = cta_exclusive_scan<SumOp, kScanThreads>(v, tot);
-            if (s < nsb) super[4 * s + c] = carry[c] + ex;
+            if (s < nsb) super[kCodes * s + c] = carry[c] + ex;
             carry[c] += tot;
         }
     }
     if (threadIdx.x == 0) {
-        C[0] = m;
-        C[1] = m + carry[0];
-        C[2] = C[1] + carry[1];
-        C[3] = C[2] + carry[2];
+        unsigned long long run = m;  // Lemma 1's C counts the terminators too
+#pragma unroll
+        for (int c = 0; c < kCodes; ++c) {
+            C[c] = run;
+            run += carry[c];
+        }
     }
 }
 
 }  // namespace
 
 template <class IdxT>
-void launch_insert(Launcher& L, const OccBlock* old_blocks, uint64_t n_ext, const uint8_t* bint, const IdxT* gsa,
-                   uint64_t n_int, OccBlock* new_blocks, unsigned long long* new_super, unsigned long long* new_C,
-                   uint64_t m_new, uint32_t* sb_tot) {
+void launch_insert(Launcher& L, const void* old_blocks, uint64_t n_ext, const uint8_t* bint, const IdxT* gsa,
+                   uint64_t n_int, void* new_blocks, unsigned long long* new_super, unsigned long long* new_C,
+                   uint64_t m_new, uint32_t* sb_tot, int code_bits) {
     const uint64_t n_new = n_ext + n_int;
+    if (code_bits == 4) {
+        const uint64_t nsb = dict_supers_w(n_new);
+        const double bytes = 64.0 * dict_blocks(n_ext) + (1.0 + sizeof(IdxT)) * n_int + 64.0 * dict_blocks(n_new);
+        SBWT_LAUNCH(L, "insert_merge", bytes, 0, nullptr, insert_w_kernel<IdxT>,
+                    ceil_div_u(nsb * kBlocksPerSuperW, kThreads), kThreads, 0,
+                    static_cast<const OccBlockW*>(old_blocks), (unsigned long long)n_ext, bint, gsa,
+                    (unsigned long long)n_int, static_cast<OccBlockW*>(new_blocks), (unsigned long long)n_new,
+                    (unsigned long long)nsb, sb_tot);
+        SBWT_LAUNCH(L, "super_scan", 192.0 * nsb, 0, nullptr, super_scan_kernel<kSigmaW>, 1, kScanThreads, 0, sb_tot,
+                    (unsigned long long)nsb, new_super, new_C, (unsigned long long)m_new);
+        return;
+    }
     const uint64_t nsb = dict_supers(n_new);
     const double bytes = 32.0 * dict_blocks(n_ext) + (1.0 + sizeof(IdxT)) * n_int + 32.0 * dict_blocks(n_new);
-    SBWT_LAUNCH(L, "insert_merge", bytes, 0, nullptr, insert_kernel<IdxT>, (unsigned)nsb, kThreads, 0, old_blocks,
-                (unsigned long long)n_ext, bint, gsa, (unsigned long long)n_int, new_blocks,
-                (unsigned long long)n_new, sb_tot);
-    SBWT_LAUNCH(L, "super_scan", 48.0 * nsb, 0, nullptr, super_scan_kernel, 1, kScanThreads, 0, sb_tot,
+    SBWT_LAUNCH(L, "insert_merge", bytes, 0, nullptr, insert_kernel<IdxT>, (unsigned)nsb, kThreads, 0,
+                static_cast<const OccBlock*>(old_blocks), (unsigned long long)n_ext, bint, gsa,
+                (unsigned long long)n_int, static_cast<OccBlock*>(new_blocks), (unsigned long long)n_new, sb_tot);
+    SBWT_LAUNCH(L, "super_scan", 48.0 * nsb, 0, nullptr, super_scan_kernel<4>, 1, kScanThreads, 0, sb_tot,
                 (unsigned long long)nsb, new_super, new_C, (unsigned long long)m_new);
 }
 
-template void launch_insert<uint32_t>(Launcher&, const OccBlock*, uint64_t, const uint8_t*, const uint32_t*,
-                                      uint64_t, OccBlock*, unsigned long long*, unsigned long long*, uint64_t,
-                                      uint32_t*);
-template void launch_insert<unsigned long long>(Launcher&, const OccBlock*, uint64_t, const uint8_t*,
-                                                const unsigned long long*, uint64_t, OccBlock*,
-                                                unsigned long long*, unsigned long long*, uint64_t, uint32_t*);
+template void launch_insert<uint32_t>(Launcher&, const void*, uint64_t, const uint8_t*, const uint32_t*, uint64_t,
+                                      void*, unsigned long long*, unsigned long long*, uint64_t, uint32_t*, int);
+template void launch_insert<unsigned long long>(Launcher&, const void*, uint64_t, const uint8_t*,
+                                                const unsigned long long*, uint64_t, void*, unsigned long long*,
+                                                unsigned long long*, uint64_t, uint32_t*, int);
 
 }  // namespace sbwt

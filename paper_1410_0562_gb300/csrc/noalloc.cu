@@ -74,7 +74,7 @@ int setup(int dev, DeviceState** out) {
             return SBWT_EDEVICE;
         }
         if (radix_temp_words(kMax) * 4 > kRadixTempBytes || suffix_sort_chunk_words(kMax) * 8 > kChunksBytes ||
-            suffix_sort_log_slots((uint32_t)kMax) * 4 > kCountLogBytes || suffix_sort_unit_bytes(kMax) > kUnitsBytes)
+            suffix_sort_log_slots((uint32_t)kMax, 2) * 4 > kCountLogBytes || suffix_sort_unit_bytes(kMax) > kUnitsBytes)
             return SBWT_EDEVICE;
         suffix_sort_init();
         st.base = static_cast<unsigned char*>(p);
@@ -191,7 +191,7 @@ extern "C" int sbwt_bwt_noalloc(const char* alphabet, const uint8_t* reads, cons
         return SBWT_EDEVICE;
     }
     launch_pack(L, d_reads, d_off, m, n, alpha4, sigma, text, term, err);
-    suffix_sort_block(L, text, term, 0, (uint32_t)n, (uint32_t)max_len, sb);
+    suffix_sort_block(L, text, term, 0, (uint32_t)n, (uint32_t)max_len, 2, sb);
     launch_bint(L, text, term, 0, sb.sa, (uint32_t)n, bint);
     SBWT_LAUNCH(L, "bint_to_bytes", 2.0 * n, 0, nullptr, bint_to_bytes_kernel, ceil_div_u(n, kThreads), kThreads, 0,
                 bint, (uint32_t)n, alpha4, d_out);

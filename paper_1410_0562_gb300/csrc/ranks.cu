@@ -32,20 +32,22 @@ __global__ void __launch_bounds__(kThreads) bint_kernel(const uint32_t* __restri
 // 16 / sizeof(IdxT) positions is complete (g starts on a 16-byte boundary).
 constexpr uint32_t kSuperStageBytes = 48 * 1024;
 
-template <class IdxT, bool kStage>
+template <class IdxT, bool kStage, int kB>
 __global__ void __launch_bounds__(kThreads) compute_ranks_kernel(const uint32_t* __restrict__ text,
                                                                  const unsigned long long* __restrict__ offsets,
                                                                  unsigned long long j_begin,
                                                                  unsigned long long nreads,
-                                                                 const OccBlock* __restrict__ blocks,
+                                                                 const typename DictLayout<kB>::Block* __restrict__ blocks,
                                                                  const unsigned long long* __restrict__ super,
                                                                  const unsigned long long* __restrict__ d_C,
                                                                  unsigned long long n_ext,
                                                                  unsigned long long m_ext, IdxT* __restrict__ g,
                                                                  uint32_t* __restrict__ d_err) {
+    constexpr int kSS = DictLayout<kB>::kSuperShift, kCodes = DictLayout<kB>::kCodes;
+    constexpr uint32_t kPer = 32 / kB;  // codes per text word
     extern __shared__ unsigned long long s_super[];
     if (kStage) {
-        const uint32_t words = ((uint32_t)(n_ext >> kSuperShift) + 1) * 4;
+        const uint32_t words = ((uint32_t)(n_ext >> kSS) + 1) * kCodes;
         for (uint32_t x = threadIdx.x; x < words; x += kThreads) s_super[x] = super[x];
         __syncthreads();
     }
@@ -89,15 +91,19 @@ __global__ void __launch_bounds__(kThreads) compute_ranks_kernel(const uint32_t*
     uint32_t word = 0;
     for (uint64_t k = len; k > 0; --k) {
         const uint64_t t = P + k - 1;
-        if ((t >> 4) != wcur) {
-            wcur = t >> 4;
+        if (t / kPer != wcur) {
+            wcur = t / kPer;
             word = __ldg(text + wcur);
         }
-        const uint32_t c = (word >> (30u - 2u * (uint32_t)(t & 15))) & 3u;
-        const unsigned long long Cc = c == 0 ? C0 : c == 1 ? C1 : c == 2 ? C2 : C3;
-        const unsigned long long sup =
-            kStage ? s_super[((i >> kSuperShift) << 2) + c] : __ldg(super + ((i >> kSuperShift) << 2) + c);
-        i = Cc + sup + occ_rank_in_super(blocks, c, i);
+        const uint32_t c = (word >> (32u - kB - kB * (uint32_t)(t % kPer))) & ((1u << kB) - 1u);
+        unsigned long long Cc;
+        if constexpr (kB == 2) {
+            Cc = c == 0 ? C0 : c == 1 ? C1 : c == 2 ? C2 : C3;
+        } else {
+            Cc = __ldg(d_C + c);
+        }
+        const unsigned long long sup = kStage ? s_super[(i >> kSS) * kCodes + c] : __ldg(super + (i >> kSS) * kCodes + c);
+        i = Cc + sup + DictLayout<kB>::in_super(blocks, c, i);
         if (i > n_ext) {
             atomicOr(d_err, 8u);
             i = n_ext;
@@ -110,18 +116,8 @@ __global__ void __launch_bounds__(kThreads) compute_ranks_kernel(const uint32_t*
         if (r < held) g[rs + r] = s[r];
 }
 
-template <class IdxT>
-__global__ void __launch_bounds__(kThreads) gather_kernel(const uint32_t* __restrict__ sa,
-                                                          const IdxT* __restrict__ g, uint32_t n,
-                                                          IdxT* __restrict__ gsa) {
-    const uint32_t i = blockIdx.x * kThreads + threadIdx.x;
-    if (i >= n) return;
-    const uint32_t t = sa[i];
-    gsa[i] = t < n ? g[t] : (IdxT)0;
-}
-
 // B_int and g_sa in one pass over SA_int (both index by SA_int[i]).
-template <class IdxT>
+template <class IdxT, int kB>
 __global__ void __launch_bounds__(kThreads) bint_gather_kernel(const uint32_t* __restrict__ text,
                                                                const uint32_t* __restrict__ term,
                                                                unsigned long long base,
@@ -133,7 +129,7 @@ __global__ void __launch_bounds__(kThreads) bint_gather_kernel(const uint32_t* _
     if (i >= n) return;
     const uint32_t t = sa[i] < n ? sa[i] : 0u;
     const uint64_t P = base + t;
-    bint[i] = (t == 0 || is_term(term, P - 1)) ? kBintDollar : (uint8_t)text_code(text, P - 1);
+    bint[i] = (t == 0 || is_term(term, P - 1)) ? kBintDollar : (uint8_t)text_code_b<kB>(text, P - 1);
     gsa[i] = g[t];
 }
 
@@ -219,6 +215,103 @@ __global__ void __launch_bounds__(kThreads) unpack_kernel(const OccBlock* __rest
     }
 }
 
+// The queries and the read-back for the 4-bit dictionary (5 to 16 symbols).
+__global__ void __launch_bounds__(kThreads) rank_batch_w_kernel(const OccBlockW* __restrict__ blocks,
+                                                                const unsigned long long* __restrict__ super,
+                                                                const uint8_t* __restrict__ codes,
+                                                                const unsigned long long* __restrict__ ks,
+                                                                unsigned long long q,
+                                                                unsigned long long* __restrict__ out) {
+    const uint64_t i = (uint64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (i >= q) return;
+    const uint32_t c = codes[i];
+    const unsigned long long k = ks[i];
+    if (c < kSigmaW) {
+        out[i] = dict_rank<4>(blocks, super, c, k);
+    } else {  // terminators: every row before k that holds no symbol
+        unsigned long long s = 0;
+        for (uint32_t x = 0; x < kSigmaW; ++x) s += dict_rank<4>(blocks, super, x, k);
+        out[i] = k - s;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) count_w_kernel(const OccBlockW* __restrict__ blocks,
+                                                           const unsigned long long* __restrict__ super,
+                                                           const unsigned long long* __restrict__ d_C,
+                                                           unsigned long long n, Alphabet16 alpha, int sigma,
+                                                           const uint8_t* __restrict__ pats,
+                                                           const unsigned long long* __restrict__ offs,
+                                                           unsigned long long q, unsigned long long* __restrict__ out) {
+    const uint64_t i = (uint64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (i >= q) return;
+    unsigned long long lo = 0, hi = n;
+    for (uint64_t k = offs[i + 1]; k > offs[i] && lo < hi; --k) {
+        const uint32_t b = pats[k - 1];
+        uint32_t c = kSigmaW;
+        for (int a = 0; a < sigma; ++a)
+            if (b == alpha.a[a]) c = (uint32_t)a;
+        if (c == kSigmaW) {  // not in the alphabet: no occurrence
+            lo = hi = 0;
+            break;
+        }
+        const unsigned long long Cc = __ldg(d_C + c);
+        lo = Cc + dict_rank<4>(blocks, super, c, lo);
+        hi = Cc + dict_rank<4>(blocks, super, c, hi);
+    }
+    out[i] = hi > lo ? hi - lo : 0ull;
+}
+
+__global__ void __launch_bounds__(kThreads) unpack_w_kernel(const OccBlockW* __restrict__ blocks,
+                                                            unsigned long long r0, unsigned long long r1,
+                                                            Alphabet16 alpha, uint8_t* __restrict__ out) {
+    // one occurrence block (64 rows) per thread, as for unpack_kernel
+    const uint64_t b = (r0 >> kOccShift) + (uint64_t)blockIdx.x * kThreads + threadIdx.x;
+    const uint64_t row0 = b << kOccShift;
+    if (row0 >= r1) return;
+    const OccBlockW blk = blocks[b];
+    uint32_t words[16];
+#pragma unroll
+    for (int w = 0; w < 16; ++w) {
+        uint32_t x = 0;
+#pragma unroll
+        for (int q4 = 0; q4 < 4; ++q4) {
+            const uint32_t q = 4 * w + q4;
+            const uint32_t c = (uint32_t)(blk.sym[q >> 4] >> (4 * (q & 15))) & 15u;
+            const uint32_t byte = ((blk.dmask >> q) & 1ull) ? (uint32_t)'$' : (uint32_t)alpha.a[c];
+            x |= byte << (8 * q4);
+        }
+        words[w] = x;
+    }
+    if (row0 + kOccSpan <= r1) {
+        uint4* dst = reinterpret_cast<uint4*>(out + row0);
+#pragma unroll
+        for (int v = 0; v < 4; ++v)
+            dst[v] = make_uint4(words[4 * v], words[4 * v + 1], words[4 * v + 2], words[4 * v + 3]);
+    } else {
+        for (uint32_t q = 0; q < (uint32_t)(r1 - row0); ++q) out[row0 + q] = (uint8_t)(words[q >> 2] >> (8 * (q & 3)));
+    }
+}
+
+uint32_t alpha4_of(const Alphabet16& alpha) {
+    uint32_t a4 = 0;
+    for (int a = 0; a < 4; ++a) a4 |= (uint32_t)alpha.a[a] << (8 * a);
+    return a4;
+}
+
+template <class IdxT, int kB>
+void compute_ranks_w(Launcher& L, const uint32_t* text, const uint64_t* d_offsets, uint64_t j_begin, uint64_t nreads,
+                     double bytes, const void* blocks, const unsigned long long* super, const unsigned long long* d_C,
+                     uint64_t n_ext, uint64_t m_ext, IdxT* g, uint32_t* d_err) {
+    using Block = typename DictLayout<kB>::Block;
+    const size_t stage = ((n_ext >> DictLayout<kB>::kSuperShift) + 1) * DictLayout<kB>::kCodes * 8;
+    auto* const kern = stage <= kSuperStageBytes ? compute_ranks_kernel<IdxT, true, kB>
+                                                 : compute_ranks_kernel<IdxT, false, kB>;
+    SBWT_LAUNCH(L, "compute_ranks", bytes, 0, nullptr, kern, ceil_div_u(nreads, kThreads), kThreads,
+                stage <= kSuperStageBytes ? stage : 0, text, reinterpret_cast<const unsigned long long*>(d_offsets),
+                (unsigned long long)j_begin, (unsigned long long)nreads, static_cast<const Block*>(blocks), super, d_C,
+                (unsigned long long)n_ext, (unsigned long long)m_ext, g, d_err);
+}
+
 }  // namespace
 
 void launch_bint(Launcher& L, const uint32_t* text, const uint32_t* term, uint64_t base, const uint32_t* sa,
@@ -230,85 +323,88 @@ void launch_bint(Launcher& L, const uint32_t* text, const uint32_t* term, uint64
 
 template <class IdxT>
 void launch_compute_ranks(Launcher& L, const uint32_t* text, const uint64_t* d_offsets, uint64_t j_begin,
-                          uint64_t nreads, uint64_t n_int, const OccBlock* blocks, const unsigned long long* super,
-                          const unsigned long long* d_C, uint64_t n_ext, uint64_t m_ext, IdxT* g,
-                          uint32_t* d_err) {
+                          uint64_t nreads, uint64_t n_int, const void* blocks, const unsigned long long* super,
+                          const unsigned long long* d_C, uint64_t n_ext, uint64_t m_ext, IdxT* g, uint32_t* d_err,
+                          int code_bits) {
     if (nreads == 0) return;
-    // per suffix: one 32-byte occurrence block, a g write, a quarter byte of text
-    const double bytes = (double)(n_int - nreads) * (32.0 + 8.0) + (double)n_int * sizeof(IdxT) + n_int / 4.0 +
-                         16.0 * nreads;
-    const size_t stage = ((n_ext >> kSuperShift) + 1) * 32;
-    if (stage <= kSuperStageBytes) {
-        auto* const kern = compute_ranks_kernel<IdxT, true>;
-        SBWT_LAUNCH(L, "compute_ranks", bytes, 0, nullptr, kern, ceil_div_u(nreads, kThreads), kThreads, stage, text,
-                    reinterpret_cast<const unsigned long long*>(d_offsets), (unsigned long long)j_begin,
-                    (unsigned long long)nreads, blocks, super, d_C, (unsigned long long)n_ext,
-                    (unsigned long long)m_ext, g, d_err);
+    // per suffix: one occurrence block, a g write, the text codes
+    const double bytes = (double)(n_int - nreads) * (code_bits == 4 ? 64.0 : 32.0) + (double)n_int * sizeof(IdxT) +
+                         n_int * code_bits / 8.0 + 16.0 * nreads;
+    if (code_bits == 4) {
+        compute_ranks_w<IdxT, 4>(L, text, d_offsets, j_begin, nreads, bytes, blocks, super, d_C, n_ext, m_ext, g, d_err);
     } else {
-        auto* const kern = compute_ranks_kernel<IdxT, false>;
-        SBWT_LAUNCH(L, "compute_ranks", bytes, 0, nullptr, kern, ceil_div_u(nreads, kThreads), kThreads, 0, text,
-                    reinterpret_cast<const unsigned long long*>(d_offsets), (unsigned long long)j_begin,
-                    (unsigned long long)nreads, blocks, super, d_C, (unsigned long long)n_ext,
-                    (unsigned long long)m_ext, g, d_err);
+        compute_ranks_w<IdxT, 2>(L, text, d_offsets, j_begin, nreads, bytes, blocks, super, d_C, n_ext, m_ext, g, d_err);
     }
 }
 
 template <class IdxT>
-void launch_gather(Launcher& L, const uint32_t* sa, const IdxT* g, uint32_t n, IdxT* gsa) {
-    if (n == 0) return;
-    SBWT_LAUNCH(L, "gather_gsa", (double)n * (4 + 2 * sizeof(IdxT)), 0, nullptr, gather_kernel<IdxT>,
-                ceil_div_u(n, kThreads), kThreads, 0, sa, g, n, gsa);
-}
-
-template <class IdxT>
 void launch_bint_gather(Launcher& L, const uint32_t* text, const uint32_t* term, uint64_t base, const uint32_t* sa,
-                        const IdxT* g, uint32_t n, uint8_t* bint, IdxT* gsa) {
+                        const IdxT* g, uint32_t n, uint8_t* bint, IdxT* gsa, int code_bits) {
     if (n == 0) return;
     // per suffix: SA_int read, one text word and one bitmap word (random), a
     // random g sector, B_int and g_sa writes
-    SBWT_LAUNCH(L, "bint_gather", (double)n * (4 + 4 + 4 + 32 + 1 + sizeof(IdxT)), 0, nullptr,
-                bint_gather_kernel<IdxT>, ceil_div_u(n, kThreads), kThreads, 0, text, term,
-                (unsigned long long)base, sa, g, n, bint, gsa);
+    auto* const kern = code_bits == 4 ? bint_gather_kernel<IdxT, 4> : bint_gather_kernel<IdxT, 2>;
+    SBWT_LAUNCH(L, "bint_gather", (double)n * (4 + 4 + 4 + 32 + 1 + sizeof(IdxT)), 0, nullptr, kern,
+                ceil_div_u(n, kThreads), kThreads, 0, text, term, (unsigned long long)base, sa, g, n, bint, gsa);
 }
 
-void launch_rank_batch(Launcher& L, const OccBlock* blocks, const unsigned long long* super, const uint8_t* codes,
-                       const unsigned long long* ks, uint64_t q, unsigned long long* out) {
+void launch_rank_batch(Launcher& L, const void* blocks, const unsigned long long* super, const uint8_t* codes,
+                       const unsigned long long* ks, uint64_t q, unsigned long long* out, int code_bits) {
     if (q == 0) return;
-    SBWT_LAUNCH(L, "rank_query", (double)q * (1 + 8 + 32 + 8 + 8), 0, nullptr, rank_batch_kernel,
-                ceil_div_u(q, kThreads), kThreads, 0, blocks, super, codes, ks, (unsigned long long)q, out);
+    if (code_bits == 4) {
+        SBWT_LAUNCH(L, "rank_query", (double)q * (1 + 8 + 64 + 8 + 8), 0, nullptr, rank_batch_w_kernel,
+                    ceil_div_u(q, kThreads), kThreads, 0, static_cast<const OccBlockW*>(blocks), super, codes, ks,
+                    (unsigned long long)q, out);
+    } else {
+        SBWT_LAUNCH(L, "rank_query", (double)q * (1 + 8 + 32 + 8 + 8), 0, nullptr, rank_batch_kernel,
+                    ceil_div_u(q, kThreads), kThreads, 0, static_cast<const OccBlock*>(blocks), super, codes, ks,
+                    (unsigned long long)q, out);
+    }
 }
 
-void launch_count(Launcher& L, const OccBlock* blocks, const unsigned long long* super,
-                  const unsigned long long* d_C, uint64_t n, uint32_t alpha4, int sigma, const uint8_t* pats,
-                  const uint64_t* offs, uint64_t q, uint64_t total_len, unsigned long long* out) {
+void launch_count(Launcher& L, const void* blocks, const unsigned long long* super, const unsigned long long* d_C,
+                  uint64_t n, const Alphabet16& alpha, int sigma, const uint8_t* pats, const uint64_t* offs,
+                  uint64_t q, uint64_t total_len, unsigned long long* out, int code_bits) {
     if (q == 0) return;
-    SBWT_LAUNCH(L, "count_query", (double)total_len * (1 + 2 * 40) + 16.0 * q, 0, nullptr, count_kernel,
-                ceil_div_u(q, kThreads), kThreads, 0, blocks, super, d_C, (unsigned long long)n, alpha4, sigma, pats,
-                reinterpret_cast<const unsigned long long*>(offs), (unsigned long long)q, out);
+    if (code_bits == 4) {
+        SBWT_LAUNCH(L, "count_query", (double)total_len * (1 + 2 * 72) + 16.0 * q, 0, nullptr, count_w_kernel,
+                    ceil_div_u(q, kThreads), kThreads, 0, static_cast<const OccBlockW*>(blocks), super, d_C,
+                    (unsigned long long)n, alpha, sigma, pats, reinterpret_cast<const unsigned long long*>(offs),
+                    (unsigned long long)q, out);
+    } else {
+        SBWT_LAUNCH(L, "count_query", (double)total_len * (1 + 2 * 40) + 16.0 * q, 0, nullptr, count_kernel,
+                    ceil_div_u(q, kThreads), kThreads, 0, static_cast<const OccBlock*>(blocks), super, d_C,
+                    (unsigned long long)n, alpha4_of(alpha), sigma, pats,
+                    reinterpret_cast<const unsigned long long*>(offs), (unsigned long long)q, out);
+    }
 }
 
-void launch_unpack(Launcher& L, const OccBlock* blocks, uint64_t r0, uint64_t r1, uint32_t alpha4, uint8_t* out) {
+void launch_unpack(Launcher& L, const void* blocks, uint64_t r0, uint64_t r1, const Alphabet16& alpha, uint8_t* out,
+                   int code_bits) {
     if (r1 <= r0) return;
     const uint64_t nblocks = ((r1 - 1) >> kOccShift) - (r0 >> kOccShift) + 1;
-    SBWT_LAUNCH(L, "unpack_bwt", (double)(r1 - r0) * (1 + 0.5), 0, nullptr, unpack_kernel,
-                ceil_div_u(nblocks, kThreads), kThreads, 0, blocks, (unsigned long long)r0, (unsigned long long)r1,
-                alpha4, out);
+    if (code_bits == 4) {
+        SBWT_LAUNCH(L, "unpack_bwt", (double)(r1 - r0) * (1 + 1.0), 0, nullptr, unpack_w_kernel,
+                    ceil_div_u(nblocks, kThreads), kThreads, 0, static_cast<const OccBlockW*>(blocks),
+                    (unsigned long long)r0, (unsigned long long)r1, alpha, out);
+    } else {
+        SBWT_LAUNCH(L, "unpack_bwt", (double)(r1 - r0) * (1 + 0.5), 0, nullptr, unpack_kernel,
+                    ceil_div_u(nblocks, kThreads), kThreads, 0, static_cast<const OccBlock*>(blocks),
+                    (unsigned long long)r0, (unsigned long long)r1, alpha4_of(alpha), out);
+    }
 }
 
 template void launch_compute_ranks<uint32_t>(Launcher&, const uint32_t*, const uint64_t*, uint64_t, uint64_t,
-                                             uint64_t, const OccBlock*, const unsigned long long*,
-                                             const unsigned long long*, uint64_t, uint64_t, uint32_t*, uint32_t*);
+                                             uint64_t, const void*, const unsigned long long*,
+                                             const unsigned long long*, uint64_t, uint64_t, uint32_t*, uint32_t*, int);
 template void launch_compute_ranks<unsigned long long>(Launcher&, const uint32_t*, const uint64_t*, uint64_t,
-                                                       uint64_t, uint64_t, const OccBlock*,
-                                                       const unsigned long long*, const unsigned long long*,
-                                                       uint64_t, uint64_t, unsigned long long*, uint32_t*);
+                                                       uint64_t, uint64_t, const void*, const unsigned long long*,
+                                                       const unsigned long long*, uint64_t, uint64_t,
+                                                       unsigned long long*, uint32_t*, int);
 template void launch_bint_gather<uint32_t>(Launcher&, const uint32_t*, const uint32_t*, uint64_t, const uint32_t*,
-                                           const uint32_t*, uint32_t, uint8_t*, uint32_t*);
+                                           const uint32_t*, uint32_t, uint8_t*, uint32_t*, int);
 template void launch_bint_gather<unsigned long long>(Launcher&, const uint32_t*, const uint32_t*, uint64_t,
                                                      const uint32_t*, const unsigned long long*, uint32_t, uint8_t*,
-                                                     unsigned long long*);
-template void launch_gather<uint32_t>(Launcher&, const uint32_t*, const uint32_t*, uint32_t, uint32_t*);
-template void launch_gather<unsigned long long>(Launcher&, const uint32_t*, const unsigned long long*, uint32_t,
-                                                unsigned long long*);
+                                                     unsigned long long*, int);
 
 }  // namespace sbwt

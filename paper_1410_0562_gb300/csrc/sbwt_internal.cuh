@@ -29,6 +29,16 @@ constexpr int kTermPadWords = 2;
 __device__ __forceinline__ uint32_t text_code(const uint32_t* __restrict__ text, uint64_t t) {
     return (text[t >> 4] >> (30u - 2u * (uint32_t)(t & 15))) & 3u;
 }
+// The same text with 4-bit codes (alphabets of 5 to 16 symbols):
+// text[t >> 3] holds positions 8w .. 8w+7, MSB first, the code of t at bits
+// 28 - 4*(t & 7).
+template <int kB>
+__device__ __forceinline__ uint32_t text_code_b(const uint32_t* __restrict__ text, uint64_t t) {
+    constexpr uint32_t kPer = 32 / kB;
+    return (text[t / kPer] >> (32u - kB - kB * (uint32_t)(t % kPer))) & ((1u << kB) - 1u);
+}
+// text words of an append of npos positions (without the padding)
+inline uint64_t text_words(uint64_t npos, int code_bits) { return (npos + 31) / 32 * (uint64_t)code_bits; }
 __device__ __forceinline__ uint32_t is_term(const uint32_t* __restrict__ term, uint64_t t) {
     return (term[t >> 5] >> (t & 31)) & 1u;
 }
@@ -95,6 +105,100 @@ __device__ __forceinline__ unsigned long long occ_rank(const OccBlock* __restric
                                                        const unsigned long long* __restrict__ super,
                                                        uint32_t c, unsigned long long i) {
     return __ldg(super + ((i >> kSuperShift) << 2) + c) + occ_rank_in_super(blocks, c, i);
+}
+
+// ---------------------------------------------------------------------------
+// The dictionary for 4-bit codes (alphabets of 5 to 16 symbols), one 64-byte
+// block per 64 rows:
+//   sym[4]  : row q at bits 4*(q & 15) of sym[q >> 4] (LSB first); a
+//             terminator is stored as code 0
+//   dmask   : bit q set iff row q holds a terminator
+//   cnt[3]  : sixteen 12-bit counts, code c at bits 12c of the 192-bit field
+//             cnt[0] | cnt[1] << 64 | cnt[2] << 128: code c (terminators
+//             excluded) in [superblock start, block start)
+// Superblocks span 2^12 rows (64 blocks, so the counts fit 12 bits);
+// super[16*s + c] counts code c in [0, 2^12 s).  A dictionary of n rows has
+// (n >> 6) + 1 blocks and ceil(blocks / 64) superblocks.
+// ---------------------------------------------------------------------------
+constexpr int kSuperShiftW = 12;
+constexpr int kBlocksPerSuperW = 1 << (kSuperShiftW - kOccShift);  // 64
+constexpr int kSigmaW = 16;
+
+struct __align__(64) OccBlockW {
+    unsigned long long sym[4];
+    unsigned long long dmask;
+    unsigned long long cnt[3];
+};
+static_assert(sizeof(OccBlockW) == 64, "two sectors per wide occurrence block");
+
+// Mask with bit 4q set for every 4-bit field q of x equal to code c.
+__device__ __forceinline__ unsigned long long match_code4(unsigned long long x, uint32_t c) {
+    unsigned long long y = x ^ (0x1111111111111111ull * c);
+    y |= y >> 1;
+    y |= y >> 2;
+    return ~y & 0x1111111111111111ull;
+}
+
+__device__ __forceinline__ uint32_t cnt12(const unsigned long long (&cw)[3], uint32_t c) {
+    const uint32_t o = 12u * c;
+    const uint32_t w = o >> 6, sh = o & 63u;
+    unsigned long long v = cw[w] >> sh;
+    if (sh > 52) v |= cw[w + 1] << (64 - sh);
+    return (uint32_t)v & 0xFFFu;
+}
+
+// rank(c, i) within i's superblock for the wide dictionary.
+__device__ __forceinline__ unsigned long long occ_rank_in_super_w(const OccBlockW* __restrict__ blocks, uint32_t c,
+                                                                  unsigned long long i) {
+    const ulonglong2* p = reinterpret_cast<const ulonglong2*>(blocks + (i >> kOccShift));
+    const ulonglong2 s01 = __ldg(p), s23 = __ldg(p + 1), dc = __ldg(p + 2), c12 = __ldg(p + 3);
+    const unsigned long long sym[4] = {s01.x, s01.y, s23.x, s23.y};
+    const unsigned long long cw[3] = {dc.y, c12.x, c12.y};
+    const uint32_t r = (uint32_t)(i & (kOccSpan - 1));
+    uint32_t in_block = 0;
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+        const uint32_t rows = r > 16u * w ? min(r - 16u * w, 16u) : 0u;
+        in_block += __popcll(match_code4(sym[w], c) & low_bits(4 * rows));
+    }
+    if (c == 0) in_block -= __popcll(dc.x & low_bits(r));
+    return cnt12(cw, c) + in_block;
+}
+
+__device__ __forceinline__ unsigned long long occ_rank_w(const OccBlockW* __restrict__ blocks,
+                                                         const unsigned long long* __restrict__ super, uint32_t c,
+                                                         unsigned long long i) {
+    return __ldg(super + ((i >> kSuperShiftW) << 4) + c) + occ_rank_in_super_w(blocks, c, i);
+}
+
+// The two dictionary layouts behind one interface, by code width kB.
+template <int kB>
+struct DictLayout;
+template <>
+struct DictLayout<2> {
+    using Block = OccBlock;
+    static constexpr int kSuperShift = sbwt::kSuperShift;
+    static constexpr int kCodes = 4;
+    __device__ __forceinline__ static unsigned long long in_super(const Block* __restrict__ b, uint32_t c,
+                                                                  unsigned long long i) {
+        return occ_rank_in_super(b, c, i);
+    }
+};
+template <>
+struct DictLayout<4> {
+    using Block = OccBlockW;
+    static constexpr int kSuperShift = kSuperShiftW;
+    static constexpr int kCodes = kSigmaW;
+    __device__ __forceinline__ static unsigned long long in_super(const Block* __restrict__ b, uint32_t c,
+                                                                  unsigned long long i) {
+        return occ_rank_in_super_w(b, c, i);
+    }
+};
+template <int kB>
+__device__ __forceinline__ unsigned long long dict_rank(const typename DictLayout<kB>::Block* __restrict__ blocks,
+                                                        const unsigned long long* __restrict__ super, uint32_t c,
+                                                        unsigned long long i) {
+    return __ldg(super + (i >> DictLayout<kB>::kSuperShift) * DictLayout<kB>::kCodes + c) + DictLayout<kB>::in_super(blocks, c, i);
 }
 
 // ---------------------------------------------------------------------------

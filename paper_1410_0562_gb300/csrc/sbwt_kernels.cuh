@@ -6,10 +6,18 @@
 
 namespace sbwt {
 
+// The alphabet of an index, by value (a kernel parameter).
+struct Alphabet16 {
+    uint8_t a[16];
+};
+
 // pack.cu: reads + offsets (device) -> 2-bit text and terminator bitmap of
 // the whole append; sets *d_err != 0 when a byte is outside the alphabet.
 void launch_pack(Launcher& L, const uint8_t* d_reads, const uint64_t* d_offsets, uint64_t m, uint64_t npos,
                  uint32_t alpha4, int sigma, uint32_t* text, uint32_t* term, uint32_t* d_err);
+// The same with 4-bit codes (5 to 16 symbols); text starts on a 16-byte boundary.
+void launch_pack_w(Launcher& L, const uint8_t* d_reads, const uint64_t* d_offsets, uint64_t m, uint64_t npos,
+                   const Alphabet16& alpha, int sigma, uint32_t* text, uint32_t* term, uint32_t* d_err);
 
 // suffix_sort.cu: ConstructSA of one block of n suffixes starting at text
 // position `base`.  Results: sa (SA_int), rank (its inverse).
@@ -26,12 +34,13 @@ struct SuffixSortBuffers {
     uint32_t* err;                        // error flags (bits 2..7)
 };
 void suffix_sort_init();  // once per device (includes radix_init)
-uint32_t suffix_sort_rounds(uint32_t max_len);
-size_t suffix_sort_log_slots(uint32_t max_len);
+// code_bits: 2 (alphabets of up to 4 symbols) or 4 (5 to 16 symbols)
+uint32_t suffix_sort_rounds(uint32_t max_len, int code_bits);
+size_t suffix_sort_log_slots(uint32_t max_len, int code_bits);
 size_t suffix_sort_chunk_words(uint64_t cap);
 size_t suffix_sort_unit_bytes(uint64_t cap);
 void suffix_sort_block(Launcher& L, const uint32_t* text, const uint32_t* term, uint64_t base, uint32_t n,
-                       uint32_t max_len, const SuffixSortBuffers& b);
+                       uint32_t max_len, int code_bits, const SuffixSortBuffers& b);
 
 // ranks.cu
 // B_int[i] = code of the symbol before block suffix SA[i], kBintDollar at a
@@ -40,37 +49,40 @@ void launch_bint(Launcher& L, const uint32_t* text, const uint32_t* term, uint64
                  uint32_t n, uint8_t* bint);
 // ComputeRanks (Algorithm 2 with Lemma 1): g[t] for every block position.
 // A row index past n_ext (impossible for a consistent dictionary) is clamped
-// and flagged in *d_err (bit 3) instead of being dereferenced.
+// and flagged in *d_err (bit 3) instead of being dereferenced.  blocks is an
+// OccBlock array for code_bits == 2, an OccBlockW array for code_bits == 4;
+// g starts on a 16-byte boundary.
 template <class IdxT>
 void launch_compute_ranks(Launcher& L, const uint32_t* text, const uint64_t* d_offsets, uint64_t j_begin,
-                          uint64_t nreads, uint64_t n_int, const OccBlock* blocks, const unsigned long long* super,
-                          const unsigned long long* d_C, uint64_t n_ext, uint64_t m_ext, IdxT* g, uint32_t* d_err);
-// g_sa[i] = g[SA_int[i]].
-template <class IdxT>
-void launch_gather(Launcher& L, const uint32_t* sa, const IdxT* g, uint32_t n, IdxT* gsa);
+                          uint64_t nreads, uint64_t n_int, const void* blocks, const unsigned long long* super,
+                          const unsigned long long* d_C, uint64_t n_ext, uint64_t m_ext, IdxT* g, uint32_t* d_err,
+                          int code_bits);
 // B_int and g_sa fused: one pass over SA_int after ComputeRanks.
 template <class IdxT>
 void launch_bint_gather(Launcher& L, const uint32_t* text, const uint32_t* term, uint64_t base, const uint32_t* sa,
-                        const IdxT* g, uint32_t n, uint8_t* bint, IdxT* gsa);
-// rank queries: codes 0..3, or 4 for the terminator.
-void launch_rank_batch(Launcher& L, const OccBlock* blocks, const unsigned long long* super, const uint8_t* codes,
-                       const unsigned long long* ks, uint64_t q, unsigned long long* out);
+                        const IdxT* g, uint32_t n, uint8_t* bint, IdxT* gsa, int code_bits);
+// rank queries: codes 0..sigma-1, or 4 (16 for code_bits == 4) for the terminator.
+void launch_rank_batch(Launcher& L, const void* blocks, const unsigned long long* super, const uint8_t* codes,
+                       const unsigned long long* ks, uint64_t q, unsigned long long* out, int code_bits);
 // Backward-search counts of q patterns (pattern i = pats[offs[i] .. offs[i+1])).
-void launch_count(Launcher& L, const OccBlock* blocks, const unsigned long long* super,
-                  const unsigned long long* d_C, uint64_t n, uint32_t alpha4, int sigma, const uint8_t* pats,
-                  const uint64_t* offs, uint64_t q, uint64_t total_len, unsigned long long* out);
+void launch_count(Launcher& L, const void* blocks, const unsigned long long* super, const unsigned long long* d_C,
+                  uint64_t n, const Alphabet16& alpha, int sigma, const uint8_t* pats, const uint64_t* offs,
+                  uint64_t q, uint64_t total_len, unsigned long long* out, int code_bits);
 // B as bytes, rows [r0, r1) (r0 a multiple of 64): alphabet byte per code,
 // '$' for a terminator row; out[r] for row r.
-void launch_unpack(Launcher& L, const OccBlock* blocks, uint64_t r0, uint64_t r1, uint32_t alpha4, uint8_t* out);
+void launch_unpack(Launcher& L, const void* blocks, uint64_t r0, uint64_t r1, const Alphabet16& alpha, uint8_t* out,
+                   int code_bits);
 
 // insert.cu: Insert (Section 5) as a stable merge of the old dictionary
 // (n_ext rows) with n_int new symbols at rows g_sa[i] + i; writes the new
 // dictionary's symbols, terminator masks and block counters, then the
 // superblock counters and C[] (m = terminators in the new dictionary).
+// Blocks are OccBlock (code_bits 2) or OccBlockW (code_bits 4); sb_tot holds
+// 4 (16) words per superblock.
 template <class IdxT>
-void launch_insert(Launcher& L, const OccBlock* old_blocks, uint64_t n_ext, const uint8_t* bint, const IdxT* gsa,
-                   uint64_t n_int, OccBlock* new_blocks, unsigned long long* new_super, unsigned long long* new_C,
-                   uint64_t m_new, uint32_t* sb_tot);
+void launch_insert(Launcher& L, const void* old_blocks, uint64_t n_ext, const uint8_t* bint, const IdxT* gsa,
+                   uint64_t n_int, void* new_blocks, unsigned long long* new_super, unsigned long long* new_C,
+                   uint64_t m_new, uint32_t* sb_tot, int code_bits);
 
 // plan.cu: checks device-resident offsets (offsets[0] = 0, non-decreasing,
 // every read shorter than max_block suffixes; summary->bad != 0 otherwise),
@@ -94,5 +106,10 @@ void launch_plan(Launcher& L, const uint64_t* d_offsets, uint64_t m, uint64_t M,
 // Sizes of a dictionary of n rows.
 inline uint64_t dict_blocks(uint64_t n) { return (n >> kOccShift) + 1; }
 inline uint64_t dict_supers(uint64_t n) { return (dict_blocks(n) + kBlocksPerSuper - 1) / kBlocksPerSuper; }
+inline uint64_t dict_supers_w(uint64_t n) { return (dict_blocks(n) + kBlocksPerSuperW - 1) / kBlocksPerSuperW; }
+// Bytes per occurrence block, superblock counters and C of each layout.
+inline size_t dict_block_bytes(int code_bits) { return code_bits == 4 ? sizeof(OccBlockW) : sizeof(OccBlock); }
+inline uint64_t dict_supers_of(uint64_t n, int code_bits) { return code_bits == 4 ? dict_supers_w(n) : dict_supers(n); }
+inline size_t dict_codes(int code_bits) { return code_bits == 4 ? (size_t)kSigmaW : 4; }
 
 }  // namespace sbwt

@@ -72,13 +72,13 @@ constexpr uint32_t kLSlots = kLCap + kLCap / kLItems;
 constexpr uint32_t kNone = 0xFFFFFFFFu;
 constexpr uint32_t kShortFlag = 0x80000000u;  // digit flag: the bucket holds suffixes with len < P
 constexpr int kScanThreads = 1024;
-// Buckets: the first kPc codes and min(len, kPc); their dense numbers need
-// kDigitBits bits (5,592,405 valid pairs for 11 codes).  Two long suffixes
-// share a bucket iff their keys agree above kBucketShift.
-constexpr uint32_t kPc = 11;
+// Buckets: the first P codes and min(len, P); their dense numbers need
+// kDigitBits bits (5,592,405 valid pairs for 11 two-bit codes, 1,118,481 for
+// 5 four-bit codes).  Two long suffixes share a bucket iff their keys agree
+// above kBucketShift.
 constexpr int kDigitBits = 24;
 constexpr uint32_t kDigitMask = (1u << kDigitBits) - 1;
-constexpr int kBucketShift = 5 + 58 - 2 * (int)kPc;
+constexpr int kBucketShift = 41;
 
 // Unit table: one entry per window of kWindow rows of the digit-sorted
 // array, stored as one array per field so a scan over windows reads it with
@@ -102,31 +102,62 @@ inline Units units_at(void* base, uint64_t cap) {
     return Units{p, p + s, p + 2 * s, p + 3 * s, p + 4 * s, p + 5 * s, p + 6 * s, p + 7 * s};
 }
 
-__device__ __forceinline__ unsigned long long initial_key(const uint32_t* __restrict__ text,
-                                                          const uint32_t* __restrict__ term, uint64_t P) {
-    // distance to the terminator, capped at kH0 (terminator bitmap window)
-    const uint64_t tw = P >> 5;
-    const unsigned long long tb = (((unsigned long long)term[tw + 1] << 32) | term[tw]) >> (P & 31);
-    const unsigned long long near = tb & ((1ull << kH0) - 1);
-    const uint32_t len = near ? (uint32_t)(__ffsll((long long)near) - 1) : kH0;
-    // 32 codes from P, MSB first
-    const uint64_t wi = P >> 4;
-    const uint32_t s = 2u * (uint32_t)(P & 15);
-    const unsigned long long hi = ((unsigned long long)text[wi] << 32) | text[wi + 1];
-    const unsigned long long lo = text[wi + 2];
-    const unsigned long long v = (hi << s) | ((lo << s) >> 32);
-    unsigned long long k58 = v >> 6;  // codes P .. P+28
-    if (len < kH0) k58 &= ~((1ull << (2 * (kH0 - len))) - 1ull);
-    return (k58 << 5) | len;
+// Key geometry per code width kB (2 bits for up to 4 symbols, 4 bits for 5
+// to 16): H codes in the key (H kB <= 58 bits), buckets of P codes, digits
+// of 24 bits either way, and the codes of the bucket prefix always above
+// bit kBucketShift.
+template <int kB>
+struct KeyGeom {
+    static constexpr uint32_t H = kB == 2 ? 29 : 14;
+    static constexpr uint32_t P = kB == 2 ? 11 : 5;
+    static constexpr uint32_t CB = H * kB;           // code bits of a key
+    static constexpr int kLog = kB == 2 ? 4 : 3;     // log2 of codes per text word
+    static_assert(5 + (int)CB - kB * (int)P == kBucketShift, "bucket prefix above kBucketShift");
+    static_assert(H <= kH0, "length field");
+};
+
+// The length field of a key: min(len, H), except that a suffix reaching at
+// least H codes stores kH0 — so "terminated inside the key" is field < kH0
+// for either width, and the order of keys is unchanged.
+template <int kB>
+__device__ __forceinline__ uint32_t len_field(uint32_t len) {
+    return len < KeyGeom<kB>::H ? len : kH0;
 }
 
-// The same key when len = min(distance to the terminator, kH0) is known:
-// only the text window is read, as one 16-byte load (plus 8 bytes when the
-// three words cross it; the text array starts on a 16-byte boundary and
-// carries 4 padding words).
+// The key's H codes from the three text words w0 w1 w2 that hold position
+// P, with the codes at and past the terminator zeroed.
+template <int kB>
+__device__ __forceinline__ unsigned long long key_codes(uint32_t w0, uint32_t w1, uint32_t w2, uint64_t P,
+                                                        uint32_t field) {
+    using G = KeyGeom<kB>;
+    const uint32_t s = kB * (uint32_t)(P & ((1u << G::kLog) - 1));
+    const unsigned long long hi = ((unsigned long long)w0 << 32) | w1;
+    const unsigned long long v = (hi << s) | (((unsigned long long)w2 << s) >> 32);  // codes from P, MSB first
+    unsigned long long k = v >> (64 - G::CB);
+    if (field < G::H) k &= ~((1ull << (kB * (G::H - field))) - 1ull);
+    return (k << 5) | field;
+}
+
+template <int kB>
+__device__ __forceinline__ unsigned long long initial_key(const uint32_t* __restrict__ text,
+                                                          const uint32_t* __restrict__ term, uint64_t P) {
+    using G = KeyGeom<kB>;
+    // distance to the terminator, capped at H (terminator bitmap window)
+    const uint64_t tw = P >> 5;
+    const unsigned long long tb = (((unsigned long long)term[tw + 1] << 32) | term[tw]) >> (P & 31);
+    const unsigned long long near = tb & ((1ull << G::H) - 1);
+    const uint32_t len = near ? (uint32_t)(__ffsll((long long)near) - 1) : G::H;
+    const uint64_t wi = P >> G::kLog;
+    return key_codes<kB>(text[wi], text[wi + 1], text[wi + 2], P, len_field<kB>(len));
+}
+
+// The same key when its length field is known: only the text window is
+// read, as one 16-byte load (plus 8 bytes when the three words cross it; the
+// text array starts on a 16-byte boundary and carries 4 padding words).
+template <int kB>
 __device__ __forceinline__ unsigned long long key_with_len(const uint32_t* __restrict__ text, uint64_t P,
-                                                           uint32_t len) {
-    const uint64_t wi = P >> 4;
+                                                           uint32_t field) {
+    const uint64_t wi = P >> KeyGeom<kB>::kLog;
     const uint32_t q = (uint32_t)(wi & 3);
     const uint4 a = __ldg(reinterpret_cast<const uint4*>(text + (wi - q)));
     uint2 b = make_uint2(0u, 0u);
@@ -141,31 +172,35 @@ __device__ __forceinline__ unsigned long long key_with_len(const uint32_t* __res
     } else {
         w0 = a.w, w1 = b.x, w2 = b.y;
     }
-    const uint32_t s = 2u * (uint32_t)(P & 15);
-    const unsigned long long hi = ((unsigned long long)w0 << 32) | w1;
-    const unsigned long long v = (hi << s) | (((unsigned long long)w2 << s) >> 32);
-    unsigned long long k58 = v >> 6;
-    if (len < kH0) k58 &= ~((1ull << (2 * (kH0 - len))) - 1ull);
-    return (k58 << 5) | len;
+    return key_codes<kB>(w0, w1, w2, P, field);
 }
 
 // Dense number of the bucket (p, l) of key K among all valid pairs in (p, l)
-// order, pc = P codes.  A pair is valid when the codes of p at and past l are
-// zero.  Pairs before (p, l): the p pairs (p' < p, l' = P); for each l' < P
-// the multiples of 4^(P - l') below p (short pairs with p' < p), in all
-// sum_{k=1..P} ceil(p / 4^k), which for p >= 1 is P + sum_k floor((p-1) /
-// 4^k) = P + ((p-1) - s4(p-1)) / 3 with s4 the base-4 digit sum (Legendre's
-// formula); and the short pairs (p, l') with l' < l, i.e. those whose zero
-// tail p has.  Bit 31 flags a short bucket.
-__device__ __forceinline__ uint32_t bucket_digit(unsigned long long K, uint32_t pc) {
+// order, P codes of b = 2^kB values each.  A pair is valid when the codes of
+// p at and past l are zero.  Pairs before (p, l): the p pairs (p' < p,
+// l' = P); for each l' < P the multiples of b^(P - l') below p (short pairs
+// with p' < p), in all sum_{k=1..P} ceil(p / b^k), which for p >= 1 is
+// P + sum_k floor((p-1) / b^k) = P + ((p-1) - s_b(p-1)) / (b-1) with s_b the
+// base-b digit sum (Legendre's formula); and the short pairs (p, l') with
+// l' < l, i.e. those whose zero tail p has.  Bit 31 flags a short bucket.
+template <int kB>
+__device__ __forceinline__ uint32_t bucket_digit(unsigned long long K) {
+    using G = KeyGeom<kB>;
+    constexpr uint32_t pc = G::P;
     const uint32_t l = min((uint32_t)(K & 31), pc);
-    const uint32_t p = (uint32_t)((K >> 5) >> (58 - 2 * pc));
-    const uint32_t zero_codes = p ? (uint32_t)(__ffs(p) - 1) >> 1 : pc;
+    const uint32_t p = (uint32_t)((K >> 5) >> (G::CB - kB * pc));
+    const uint32_t zero_codes = p ? (uint32_t)(__ffs(p) - 1) / kB : pc;
     uint32_t o = p;
     if (p) {
         const uint32_t x = p - 1;
-        const uint32_t s4 = (uint32_t)__popc(x & 0x55555555u) + 2u * (uint32_t)__popc(x & 0xAAAAAAAAu);
-        o += pc + (x - s4) / 3;
+        uint32_t sb;
+        if constexpr (kB == 2) {
+            sb = (uint32_t)__popc(x & 0x55555555u) + 2u * (uint32_t)__popc(x & 0xAAAAAAAAu);
+        } else {
+            sb = (uint32_t)__popc(x & 0x11111111u) + 2u * (uint32_t)__popc(x & 0x22222222u) +
+                 4u * (uint32_t)__popc(x & 0x44444444u) + 8u * (uint32_t)__popc(x & 0x88888888u);
+        }
+        o += pc + (x - sb) / ((1u << kB) - 1u);
     }
     const uint32_t first_valid = pc > zero_codes ? pc - zero_codes : 0;
     o += l > first_valid ? l - first_valid : 0;
@@ -176,16 +211,16 @@ __device__ __forceinline__ uint32_t bucket_digit(unsigned long long K, uint32_t 
 // 0..23, bit 31 the short flag) and min(len, kH0) (bits 24..28) in the low
 // word, t in the high word.  The sort orders by the low kDigitBits bits and
 // carries the rest.
+template <int kB>
 __global__ void __launch_bounds__(kThreads) sa_digit_keys_kernel(const uint32_t* __restrict__ text,
                                                                  const uint32_t* __restrict__ term,
-                                                                 unsigned long long base, uint32_t n, uint32_t pc,
+                                                                 unsigned long long base, uint32_t n,
                                                                  unsigned long long* __restrict__ elems,
                                                                  uint32_t* __restrict__ d_n) {
     if (blockIdx.x == 0 && threadIdx.x == 0) *d_n = n;
-    for (uint32_t t = blockIdx.x * kThreads + threadIdx.x; t < n; t += gridDim.x * kThreads)
-    {
-        const unsigned long long K = initial_key(text, term, base + t);
-        elems[t] = bucket_digit(K, pc) | ((uint32_t)(K & 31) << 24) | ((unsigned long long)t << 32);
+    for (uint32_t t = blockIdx.x * kThreads + threadIdx.x; t < n; t += gridDim.x * kThreads) {
+        const unsigned long long K = initial_key<kB>(text, term, base + t);
+        elems[t] = bucket_digit<kB>(K) | ((uint32_t)(K & 31) << 24) | ((unsigned long long)t << 32);
     }
 }
 
@@ -195,6 +230,7 @@ __global__ void __launch_bounds__(kThreads) sa_digit_keys_kernel(const uint32_t*
 // here.  The k-th long row i of window w, suffix t, is listed as (ll_t,
 // ll_row, ll_key)[w kWindow + k] = (t, i, its key), so a unit's long rows
 // are a few contiguous runs.
+template <int kB>
 __global__ void __launch_bounds__(kThreads) sa_unit_begin_kernel(const uint32_t* __restrict__ text,
                                                                  unsigned long long base,
                                                                  const unsigned long long* __restrict__ elems,
@@ -230,7 +266,7 @@ __global__ void __launch_bounds__(kThreads) sa_unit_begin_kernel(const uint32_t*
                 const uint32_t k = lo + lct + __popc(bl & ((1u << lane) - 1u));
                 ll_t[k] = t;
                 ll_row[k] = i;
-                ll_key[k] = key_with_len(text, base + (t < n ? t : 0u), len);
+                ll_key[k] = key_with_len<kB>(text, base + (t < n ? t : 0u), len);
             }
             if (first == kNone) {
                 if (bb) {
@@ -784,6 +820,7 @@ __global__ void __launch_bounds__(kLThreads, 4) sa_local_sort_kernel(
 // The global-path list: every row of a unit with more than kLCap long
 // suffixes, in row order, as (key, t, row).  One CTA per window; a window's
 // rows belong to its owner unit up to the window's own unit start.
+template <int kB>
 __global__ void __launch_bounds__(kThreads) sa_large_gather_kernel(
     const uint32_t* __restrict__ text, unsigned long long base, uint32_t n,
     const unsigned long long* __restrict__ elems, Units u, uint32_t nwin, unsigned long long* __restrict__ lkeys,
@@ -802,7 +839,7 @@ __global__ void __launch_bounds__(kThreads) sa_large_gather_kernel(
                 const unsigned long long e = elems[i];
                 const uint32_t t = (uint32_t)(e >> 32);
                 const uint32_t o = lofs + (i - qbeg);
-                lkeys[o] = key_with_len(text, base + (t < n ? t : 0u), ((uint32_t)e >> 24) & 31u);
+                lkeys[o] = key_with_len<kB>(text, base + (t < n ? t : 0u), ((uint32_t)e >> 24) & 31u);
                 lvals[o] = t;
                 lpos[o] = i;
             }
@@ -1124,7 +1161,7 @@ void suffix_sort_init() {
     const int dev = current_device();
     cudaFuncSetAttribute(sa_local_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLocalSortSmem);
     cudaFuncSetAttribute(sa_round_local_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRoundLocalSmem);
-    g_keys_ctas[dev] = persistent_ctas((const void*)sa_digit_keys_kernel, kThreads, 0);
+    g_keys_ctas[dev] = persistent_ctas((const void*)sa_digit_keys_kernel<2>, kThreads, 0);
     g_round_keys_ctas[dev] = persistent_ctas((const void*)sa_round_keys_kernel, kThreads, 0);
     g_groups_ctas[dev] = std::min<unsigned>(kMaxGroupChunks,
                                             persistent_ctas((const void*)sa_groups_apply_kernel<false>, kThreads, 0));
@@ -1132,9 +1169,9 @@ void suffix_sort_init() {
     g_round_local_ctas[dev] = persistent_ctas((const void*)sa_round_local_kernel, kLThreads, kRoundLocalSmem);
 }
 
-uint32_t suffix_sort_rounds(uint32_t max_len) {
+uint32_t suffix_sort_rounds(uint32_t max_len, int code_bits) {
     uint32_t r = 0;
-    uint64_t resolved = kH0;
+    uint64_t resolved = code_bits == 4 ? KeyGeom<4>::H : KeyGeom<2>::H;
     while (resolved <= max_len) {
         resolved *= 2;
         ++r;
@@ -1144,7 +1181,9 @@ uint32_t suffix_sort_rounds(uint32_t max_len) {
 
 // slot 0: n; 1: size of the global-path list; 2 + 2r: global-path unsorted
 // members after round r (r = 0: the initial sort); 3 + 2r: local ones
-size_t suffix_sort_log_slots(uint32_t max_len) { return 4 + 2 * (size_t)suffix_sort_rounds(max_len); }
+size_t suffix_sort_log_slots(uint32_t max_len, int code_bits) {
+    return 4 + 2 * (size_t)suffix_sort_rounds(max_len, code_bits);
+}
 
 size_t suffix_sort_chunk_words(uint64_t cap) {
     (void)cap;
@@ -1175,25 +1214,28 @@ void run_groups(Launcher& L, const SuffixSortBuffers& b, const unsigned long lon
 }  // namespace
 
 void suffix_sort_block(Launcher& L, const uint32_t* text, const uint32_t* term, uint64_t base, uint32_t n,
-                       uint32_t max_len, const SuffixSortBuffers& b) {
+                       uint32_t max_len, int code_bits, const SuffixSortBuffers& b) {
     if (n == 0) return;
     const int dev = current_device();
     const uint64_t gtiles = (uint64_t)n / kGTile + 1;
     auto grid_of = [](unsigned ctas, uint64_t need) {
         return (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(std::max(1u, ctas), need));
     };
-    const uint32_t rounds = suffix_sort_rounds(max_len);
+    const bool wide = code_bits == 4;
+    const uint32_t rounds = suffix_sort_rounds(max_len, code_bits);
     const uint32_t nwin = (uint32_t)(((uint64_t)n + kWindow - 1) / kWindow);
     const unsigned warp_grid = grid_of(g_keys_ctas[dev], (uint64_t)nwin / (kThreads / 32) + 1);
     const Units units = units_at(b.units, n);
-    const uint32_t pc = kPc;
     const int digit_bits = kDigitBits;
+    auto* const digit_keys = wide ? sa_digit_keys_kernel<4> : sa_digit_keys_kernel<2>;
+    auto* const unit_begin = wide ? sa_unit_begin_kernel<4> : sa_unit_begin_kernel<2>;
+    auto* const large_gather = wide ? sa_large_gather_kernel<4> : sa_large_gather_kernel<2>;
 
     uint32_t* d_n = b.count_log;
     uint32_t* d_large = b.count_log + 1;
-    SBWT_LAUNCH(L, "sa_digit_keys", (double)n * 8 + n / 4.0 + n / 8.0, 0, nullptr, sa_digit_keys_kernel,
+    SBWT_LAUNCH(L, "sa_digit_keys", (double)n * 8 + n * code_bits / 8.0 + n / 8.0, 0, nullptr, digit_keys,
                 grid_of(g_keys_ctas[dev], (uint64_t)n / kThreads + 1), kThreads, 0, text, term,
-                (unsigned long long)base, n, pc, b.keys, d_n);
+                (unsigned long long)base, n, b.keys, d_n);
     const bool da = radix_sort_keys(L, b.keys, b.keys_alt, d_n, n, 0, digit_bits, b.radix_temp, b.err);
     const unsigned long long* elems = da ? b.keys_alt : b.keys;  // (digit, t) in row order
     // the other 64-bit array holds the keys of the listed long rows, then the
@@ -1205,7 +1247,7 @@ void suffix_sort_block(Launcher& L, const uint32_t* text, const uint32_t* term, 
     uint32_t* ll_t = b.loc_next;
     uint32_t* ll_row = b.act_suf[0];
     unsigned long long* ll_key = other;
-    SBWT_LAUNCH(L, "sa_unit_begin", (double)n * 24 + 32.0 * nwin, 0, nullptr, sa_unit_begin_kernel,
+    SBWT_LAUNCH(L, "sa_unit_begin", (double)n * 24 + 32.0 * nwin, 0, nullptr, unit_begin,
                 warp_grid, kThreads, 0, text, (unsigned long long)base, elems, n, nwin, units, b.sa, b.rank,
                 ll_t, ll_row, ll_key, b.err);
     SBWT_LAUNCH(L, "sa_unit_scan", 96.0 * nwin, 0, nullptr, sa_unit_scan_kernel, 1, kScanThreads, 0, units, nwin, n,
@@ -1216,7 +1258,7 @@ void suffix_sort_block(Launcher& L, const uint32_t* text, const uint32_t* term, 
                 grid_of(g_local_ctas[dev], nwin), kLThreads, kLocalSortSmem, n, ll_t, ll_row, ll_key, units, nwin, b.sa, b.rank, b.loc_act, b.count_log + 3, b.err);
     // the list of the device-wide path goes to the other array (the long
     // rows' keys are dead once the local sort has run)
-    SBWT_LAUNCH(L, "sa_large_gather", 32.0 * nwin, 24, d_large, sa_large_gather_kernel, grid_of(g_local_ctas[dev], nwin),
+    SBWT_LAUNCH(L, "sa_large_gather", 32.0 * nwin, 24, d_large, large_gather, grid_of(g_local_ctas[dev], nwin),
                 kThreads, 0, text, (unsigned long long)base, n, elems, units, nwin, other, b.vals,
                 b.act_pos[0]);
     unsigned long long* spare = da ? b.keys_alt : b.keys;  // the elements are dead now
@@ -1226,7 +1268,7 @@ void suffix_sort_block(Launcher& L, const uint32_t* text, const uint32_t* term, 
                      b.act_suf[1], b.count_log + 2, grid_of(g_groups_ctas[dev], gtiles));
 
     const int bits = n > 1 ? 32 - __builtin_clz(n - 1) : 1;
-    uint32_t h = kH0;
+    uint32_t h = wide ? KeyGeom<4>::H : KeyGeom<2>::H;
     int cur = 1;
     for (uint32_t r = 1; r <= rounds; ++r, h *= 2) {
         const uint32_t* cnt = b.count_log + 2 + 2 * (r - 1);

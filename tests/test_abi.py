@@ -44,7 +44,8 @@ def test_strerror(lib):
         assert isinstance(sb.strerror(code), str) and sb.strerror(code)
 
 
-@pytest.mark.parametrize("alpha", [b"", b"ACGTN", b"CA", b"AAC", b"A$", b"ACC"])
+@pytest.mark.parametrize("alpha", [b"", b"ACGTN", b"CA", b"AAC", b"A$", b"ACC", b"ABCDEFGHIJKLMNOPQ",
+                                   b"ABCDEFGH$"])
 def test_create_rejects_bad_alphabet(lib, alpha):
     h = ctypes.c_void_p()
     assert lib.sbwt_create(alpha, 0, ctypes.byref(h)) == sb.SBWT_EINVAL
@@ -53,7 +54,7 @@ def test_create_rejects_bad_alphabet(lib, alpha):
 
 def test_create_does_not_touch_the_gpu(lib):
     # works on a machine without a GPU: device state is created lazily
-    for alpha in (b"A", b"AC", b"ACG", b"ACGT", b"abn", b"imps"):
+    for alpha in (b"A", b"AC", b"ACG", b"ACGT", b"abn", b"imps", b"ACGNT", b"ABCDEFGHIJKLMNOP"):
         h = sb.sbwt_create(alpha)
         assert sb.sbwt_size(h) == (0, 0)
         sb.sbwt_reset(h)
