@@ -45,7 +45,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="short", choices=["short", "tiny", "serve"])
+    ap.add_argument("--workload", default="short", choices=["short", "tiny", "serve", "wide"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-form measurement")
@@ -65,6 +65,9 @@ def dist_env():
 def make_workload(name: str, rank: int, n_reads: int = 1_000_000):
     if name == "tiny":
         w = readgen.tiny()
+    elif name == "wide":
+        w = readgen.wide(n_reads=n_reads, seed_genome=0x14100562 + 7 + 1000 * rank,
+                         seed_reads=0x05621410 + 7 + 1000 * rank)
     else:
         # every rank indexes its own read set (same shape, its own seeds)
         w = readgen.short(n_reads=n_reads, seed_genome=0x14100562 + 2 + 1000 * rank,
@@ -246,7 +249,7 @@ def cpu_baseline(w, n_reads: int):
     off = w.offsets[: n_reads + 1]
     reads = w.reads[: int(off[-1])]
     t = time.perf_counter()
-    oracle.bwt(reads, off)
+    oracle.bwt(reads, off, w.alphabet)
     dt = time.perf_counter() - t
     return {"value": float(off[-1]) / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"first {n_reads} reads ({int(off[-1])} bp) of the workload, full BWT by the oracle, "
@@ -264,11 +267,11 @@ def run_reference(args):
     import oracle
     oracle.build()
     for _ in range(args.warmup):
-        oracle.bwt(reads, off)
+        oracle.bwt(reads, off, w.alphabet)
     times = []
     for _ in range(args.steps):
         t = time.perf_counter()
-        oracle.bwt(reads, off)
+        oracle.bwt(reads, off, w.alphabet)
         times.append(time.perf_counter() - t)
     total = sum(times)
     value = float(off[-1]) * args.steps / total / 1e6
@@ -308,7 +311,7 @@ def run_gb300(args):
     w = make_workload(args.workload, rank)
     bases = w.bases
     stream = torch.cuda.Stream()
-    idx = sb.SetBWT(b"ACGT", index_bits=w.index_bits, block_suffixes=w.block_suffixes,
+    idx = sb.SetBWT(w.alphabet, index_bits=w.index_bits, block_suffixes=w.block_suffixes,
                     stream=stream.cuda_stream, device=local)
     d_reads = torch.from_numpy(w.reads).to("cuda")
     d_off = torch.from_numpy(w.offsets.astype(np.int64)).to("cuda")
@@ -398,7 +401,7 @@ def run_gb300(args):
     # the whole append replayed from a captured CUDA graph
     batched = None
     if not args.no_batched:
-        idx_b = sb.SetBWT(b"ACGT", index_bits=w.index_bits, stream=stream.cuda_stream, device=local)
+        idx_b = sb.SetBWT(w.alphabet, index_bits=w.index_bits, stream=stream.cuda_stream, device=local)
         best_M, tune = sb.sbwt_autotune_block_suffixes(idx_b.handle, d_reads.data_ptr(), d_off.data_ptr(), w.m,
                                                        [1 << 22, 1 << 23, 1 << 24, 1 << 25, 1 << 26, 1 << 27])
         sb.sbwt_set_graph_replay(idx_b.handle, True)
@@ -493,7 +496,7 @@ def run_gb300(args):
     if clocks:
         line["clocks"] = clocks
     if not args.no_cpu_baseline and world == 1:
-        line["cpu_baseline"] = cpu_baseline(w, 200_000 if args.workload == "short" else w.m)
+        line["cpu_baseline"] = cpu_baseline(w, 200_000 if args.workload in ("short", "wide") else w.m)
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -406,7 +406,7 @@ void run_block(sbwt_index* idx, const BlockPlan& bp, const uint64_t* d_offsets, 
     const cudaStream_t s = L.stream;
     if (q >= 2) cudaStreamWaitEvent(idx->side, idx->ev_consumed[q & 1], 0);
     L.stream = idx->side;
-    suffix_sort_block(L, text, term, bp.base, n, (uint32_t)bp.max_len, idx->code_bits, b);
+    suffix_sort_block(L, text, term, bp.base, n, (uint32_t)bp.max_len, idx->code_bits, idx->sigma, b);
     cudaEventRecord(idx->ev_sorted[q & 1], idx->side);
     L.stream = s;
     // ComputeRanks needs only the dictionary; the gather waits for the sort

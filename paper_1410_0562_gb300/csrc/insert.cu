@@ -326,32 +326,51 @@ __global__ void __launch_bounds__(kThreads) insert_w_kernel(const OccBlockW* __r
 
 constexpr int kScanThreads = 1024;
 
+// Superblock counters from the per-superblock totals: one warp per code
+// scans the superblocks in runs of 256 (8 per lane); then C[] (Lemma 1's C
+// counts the terminators too).
 template <int kCodes>
 __global__ void __launch_bounds__(kScanThreads) super_scan_kernel(const uint32_t* __restrict__ sb_tot,
                                                                   unsigned long long nsb,
                                                                   unsigned long long* __restrict__ super,
                                                                   unsigned long long* __restrict__ C,
                                                                   unsigned long long m) {
-    unsigned long long carry[kCodes];
+    static_assert(kCodes <= kScanThreads / 32, "one warp per code");
+    __shared__ unsigned long long totals[kCodes];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (warp < kCodes) {
+        constexpr int kPer = 8;  // consecutive superblocks per lane: eight loads in flight
+        unsigned long long carry = 0;
+        for (unsigned long long base = 0; base < nsb; base += 32 * kPer) {
+            const unsigned long long s0 = base + (unsigned long long)lane * kPer;
+            unsigned long long v[kPer], lt = 0;
 #pragma unroll
-    for (int c = 0; c < kCodes; ++c) carry[c] = 0;
-    for (unsigned long long base = 0; base < nsb; base += kScanThreads) {
-        const unsigned long long s = base + threadIdx.x;
+            for (int j = 0; j < kPer; ++j) {
+                v[j] = s0 + j < nsb ? sb_tot[kCodes * (s0 + j) + warp] : 0ull;
+                lt += v[j];
+            }
+            unsigned long long x = lt;
 #pragma unroll
-        for (int c = 0; c < kCodes; ++c) {
-            const unsigned long long v = s < nsb ? sb_tot[kCodes * s + c] : 0ull;
-            unsigned long long tot;
-            const unsigned long long ex = cta_exclusive_scan<SumOp, kScanThreads>(v, tot);
-            if (s < nsb) super[kCodes * s + c] = carry[c] + ex;
-            carry[c] += tot;
+            for (int d = 1; d < 32; d <<= 1) {
+                const unsigned long long y = __shfl_up_sync(0xffffffffu, x, d);
+                if (lane >= d) x += y;
+            }
+            unsigned long long run = carry + x - lt;
+#pragma unroll
+            for (int j = 0; j < kPer; ++j) {
+                if (s0 + j < nsb) super[kCodes * (s0 + j) + warp] = run;
+                run += v[j];
+            }
+            carry += __shfl_sync(0xffffffffu, x, 31);
         }
+        if (lane == 0) totals[warp] = carry;
     }
+    __syncthreads();
     if (threadIdx.x == 0) {
-        unsigned long long run = m;  // Lemma 1's C counts the terminators too
-#pragma unroll
+        unsigned long long run = m;
         for (int c = 0; c < kCodes; ++c) {
             C[c] = run;
-            run += carry[c];
+            run += totals[c];
         }
     }
 }

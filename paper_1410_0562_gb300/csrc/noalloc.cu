@@ -191,7 +191,7 @@ extern "C" int sbwt_bwt_noalloc(const char* alphabet, const uint8_t* reads, cons
         return SBWT_EDEVICE;
     }
     launch_pack(L, d_reads, d_off, m, n, alpha4, sigma, text, term, err);
-    suffix_sort_block(L, text, term, 0, (uint32_t)n, (uint32_t)max_len, 2, sb);
+    suffix_sort_block(L, text, term, 0, (uint32_t)n, (uint32_t)max_len, 2, sigma, sb);
     launch_bint(L, text, term, 0, sb.sa, (uint32_t)n, bint);
     SBWT_LAUNCH(L, "bint_to_bytes", 2.0 * n, 0, nullptr, bint_to_bytes_kernel, ceil_div_u(n, kThreads), kThreads, 0,
                 bint, (uint32_t)n, alpha4, d_out);

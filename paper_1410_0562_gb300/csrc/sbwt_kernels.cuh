@@ -40,7 +40,7 @@ size_t suffix_sort_log_slots(uint32_t max_len, int code_bits);
 size_t suffix_sort_chunk_words(uint64_t cap);
 size_t suffix_sort_unit_bytes(uint64_t cap);
 void suffix_sort_block(Launcher& L, const uint32_t* text, const uint32_t* term, uint64_t base, uint32_t n,
-                       uint32_t max_len, int code_bits, const SuffixSortBuffers& b);
+                       uint32_t max_len, int code_bits, int sigma, const SuffixSortBuffers& b);
 
 // ranks.cu
 // B_int[i] = code of the symbol before block suffix SA[i], kBintDollar at a

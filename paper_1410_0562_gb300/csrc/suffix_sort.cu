@@ -103,16 +103,15 @@ inline Units units_at(void* base, uint64_t cap) {
 }
 
 // Key geometry per code width kB (2 bits for up to 4 symbols, 4 bits for 5
-// to 16): H codes in the key (H kB <= 58 bits), buckets of P codes, digits
-// of 24 bits either way, and the codes of the bucket prefix always above
-// bit kBucketShift.
+// to 16): H codes in the key (H kB <= 58 bits) and buckets of P codes (for
+// 4-bit codes P is the smallest bucket length, for 16 symbols; fewer
+// symbols take longer buckets, chosen per index), digits of 24 bits.
 template <int kB>
 struct KeyGeom {
     static constexpr uint32_t H = kB == 2 ? 29 : 14;
     static constexpr uint32_t P = kB == 2 ? 11 : 5;
     static constexpr uint32_t CB = H * kB;           // code bits of a key
     static constexpr int kLog = kB == 2 ? 4 : 3;     // log2 of codes per text word
-    static_assert(5 + (int)CB - kB * (int)P == kBucketShift, "bucket prefix above kBucketShift");
     static_assert(H <= kH0, "length field");
 };
 
@@ -176,35 +175,54 @@ __device__ __forceinline__ unsigned long long key_with_len(const uint32_t* __res
 }
 
 // Dense number of the bucket (p, l) of key K among all valid pairs in (p, l)
-// order, P codes of b = 2^kB values each.  A pair is valid when the codes of
-// p at and past l are zero.  Pairs before (p, l): the p pairs (p' < p,
-// l' = P); for each l' < P the multiples of b^(P - l') below p (short pairs
-// with p' < p), in all sum_{k=1..P} ceil(p / b^k), which for p >= 1 is
-// P + sum_k floor((p-1) / b^k) = P + ((p-1) - s_b(p-1)) / (b-1) with s_b the
-// base-b digit sum (Legendre's formula); and the short pairs (p, l') with
-// l' < l, i.e. those whose zero tail p has.  Bit 31 flags a short bucket.
-template <int kB>
+// order, P = 11 two-bit codes.  A pair is valid when the codes of p at and
+// past l are zero.  Pairs before (p, l): the p pairs (p' < p, l' = P); for
+// each l' < P the multiples of 4^(P - l') below p (short pairs with p' < p),
+// in all sum_{k=1..P} ceil(p / 4^k), which for p >= 1 is P + sum_k
+// floor((p-1) / 4^k) = P + ((p-1) - s4(p-1)) / 3 with s4 the base-4 digit
+// sum (Legendre's formula); and the short pairs (p, l') with l' < l, i.e.
+// those whose zero tail p has.  Bit 31 flags a short bucket.
 __device__ __forceinline__ uint32_t bucket_digit(unsigned long long K) {
-    using G = KeyGeom<kB>;
+    using G = KeyGeom<2>;
     constexpr uint32_t pc = G::P;
     const uint32_t l = min((uint32_t)(K & 31), pc);
-    const uint32_t p = (uint32_t)((K >> 5) >> (G::CB - kB * pc));
-    const uint32_t zero_codes = p ? (uint32_t)(__ffs(p) - 1) / kB : pc;
+    const uint32_t p = (uint32_t)((K >> 5) >> (G::CB - 2 * pc));
+    const uint32_t zero_codes = p ? (uint32_t)(__ffs(p) - 1) >> 1 : pc;
     uint32_t o = p;
     if (p) {
         const uint32_t x = p - 1;
-        uint32_t sb;
-        if constexpr (kB == 2) {
-            sb = (uint32_t)__popc(x & 0x55555555u) + 2u * (uint32_t)__popc(x & 0xAAAAAAAAu);
-        } else {
-            sb = (uint32_t)__popc(x & 0x11111111u) + 2u * (uint32_t)__popc(x & 0x22222222u) +
-                 4u * (uint32_t)__popc(x & 0x44444444u) + 8u * (uint32_t)__popc(x & 0x88888888u);
-        }
-        o += pc + (x - sb) / ((1u << kB) - 1u);
+        const uint32_t s4 = (uint32_t)__popc(x & 0x55555555u) + 2u * (uint32_t)__popc(x & 0xAAAAAAAAu);
+        o += pc + (x - s4) / 3;
     }
     const uint32_t first_valid = pc > zero_codes ? pc - zero_codes : 0;
     o += l > first_valid ? l - first_valid : 0;
     return o | (l < pc ? kShortFlag : 0u);
+}
+
+// The bucket number for 4-bit codes of an alphabet of sigma symbols, in
+// base sigma so that the pairs are as dense as for 2-bit codes: buckets of
+// the first pw codes (pw chosen on the host so that every valid pair fits
+// kDigitBits bits).  With p the pw codes read as a base-sigma number, s(p)
+// their digit sum and z the zero codes at the end of p, the count of pairs
+// before (p, l) above becomes, for p >= 1, p + pw + (p - s(p)) / (sigma - 1)
+// - z, since s(p - 1) = s(p) - 1 + z (sigma - 1); plus the short pairs
+// (p, l') with pw - z <= l' < l.
+__device__ __forceinline__ uint32_t bucket_digit_sigma(unsigned long long K, uint32_t sigma, uint32_t pw) {
+    using G = KeyGeom<4>;
+    const uint32_t l = min((uint32_t)(K & 31), pw);
+    const unsigned long long codes = (K >> 5) >> (G::CB - 4 * pw);  // the first pw codes
+    uint32_t p = 0, s = 0;
+    for (uint32_t q = 0; q < pw; ++q) {
+        const uint32_t c = (uint32_t)(codes >> (4 * (pw - 1 - q))) & 15u;
+        p = p * sigma + c;
+        s += c;
+    }
+    const uint32_t z = codes ? (uint32_t)(__ffsll((long long)codes) - 1) / 4 : pw;
+    uint32_t o = p;
+    if (p) o += pw + (p - s) / (sigma - 1) - z;
+    const uint32_t first_valid = pw > z ? pw - z : 0;
+    o += l > first_valid ? l - first_valid : 0;
+    return o | (l < pw ? kShortFlag : 0u);
 }
 
 // Element of block position t for the bucket split: its bucket digit (bits
@@ -215,12 +233,19 @@ template <int kB>
 __global__ void __launch_bounds__(kThreads) sa_digit_keys_kernel(const uint32_t* __restrict__ text,
                                                                  const uint32_t* __restrict__ term,
                                                                  unsigned long long base, uint32_t n,
+                                                                 uint32_t sigma, uint32_t pw,
                                                                  unsigned long long* __restrict__ elems,
                                                                  uint32_t* __restrict__ d_n) {
     if (blockIdx.x == 0 && threadIdx.x == 0) *d_n = n;
     for (uint32_t t = blockIdx.x * kThreads + threadIdx.x; t < n; t += gridDim.x * kThreads) {
         const unsigned long long K = initial_key<kB>(text, term, base + t);
-        elems[t] = bucket_digit<kB>(K) | ((uint32_t)(K & 31) << 24) | ((unsigned long long)t << 32);
+        uint32_t d;
+        if constexpr (kB == 2) {
+            d = bucket_digit(K);
+        } else {
+            d = bucket_digit_sigma(K, sigma, pw);
+        }
+        elems[t] = d | ((uint32_t)(K & 31) << 24) | ((unsigned long long)t << 32);
     }
 }
 
@@ -512,18 +537,16 @@ __device__ __forceinline__ uint32_t carry_in_head(uint32_t heads, uint32_t g0) {
 
 // Sort of `count` <= kLCap (key, value) pairs held blocked in registers
 // (as for block_merge_sort) when the list is cut into segments of equal
-// key >> kShift, contiguous and in segment order, none longer than kSeg: an
+// key >> shift, contiguous and in segment order, none longer than kSeg: an
 // item's place is its segment's first index plus the number of items of its
 // segment before it in (key, value) order (values are distinct, so the order
 // is total).  Returns false, with the registers untouched, when a segment is
 // longer than kSeg.  On success skey/sval hold the sorted list too.
 constexpr uint32_t kSeg = 64;
 
-template <int kShift>
 __device__ __forceinline__ bool block_segment_sort(unsigned long long (&k)[kLItems], uint32_t (&v)[kLItems],
                                                    uint32_t count, unsigned long long* skey, uint32_t* sval,
-                                                   uint32_t* sseg) {
-    constexpr int shift = kShift;
+                                                   uint32_t* sseg, int shift) {
     const uint32_t g0 = threadIdx.x * kLItems;
     __syncthreads();
 #pragma unroll
@@ -591,11 +614,10 @@ __device__ __forceinline__ bool block_segment_sort(unsigned long long (&k)[kLIte
 
 // Sorts the blocked items by (key, value): segment by segment as above,
 // else by a merge sort of the list; leaves the sorted keys in skey.
-template <int kShift>
 __device__ __forceinline__ void block_sort(unsigned long long (&k)[kLItems], uint32_t (&v)[kLItems],
                                            uint32_t count, unsigned long long* skey, uint32_t* sval,
-                                           uint32_t* sseg) {
-    if (block_segment_sort<kShift>(k, v, count, skey, sval, sseg)) {
+                                           uint32_t* sseg, int shift) {
+    if (block_segment_sort(k, v, count, skey, sval, sseg, shift)) {
         __syncthreads();
         return;
     }
@@ -697,7 +719,7 @@ __global__ void __launch_bounds__(kLThreads, 4) sa_local_sort_kernel(
     uint32_t n, const uint32_t* __restrict__ ll_t, const uint32_t* __restrict__ ll_row,
     const unsigned long long* __restrict__ ll_key, Units u, uint32_t nwin, uint32_t* __restrict__ sa,
     uint32_t* __restrict__ rank, uint32_t* __restrict__ loc_act, uint32_t* __restrict__ d_cnt,
-    uint32_t* __restrict__ d_err) {
+    uint32_t* __restrict__ d_err, int seg_shift) {
     extern __shared__ __align__(16) unsigned char smem[];
     unsigned long long* skey = reinterpret_cast<unsigned long long*>(smem);
     uint32_t* sval = reinterpret_cast<uint32_t*>(skey + kLSlots);
@@ -779,7 +801,7 @@ __global__ void __launch_bounds__(kLThreads, 4) sa_local_sort_kernel(
         }
 #pragma unroll
         for (int j = 0; j < kLItems; ++j) srow[skew(g0 + j)] = rw[j];  // an out-of-range t is skipped when written
-        block_sort<kBucketShift>(kk, v, cnt, skey, sval, sseg);  // segments: buckets
+        block_sort(kk, v, cnt, skey, sval, sseg, seg_shift);  // segments: buckets
 
         // group heads: a new key, or a key that contains its terminator
         const unsigned long long kprev = (g0 > 0 && g0 <= cnt) ? skey[skew(g0 - 1)] : 0ull;
@@ -920,7 +942,7 @@ __global__ void __launch_bounds__(kLThreads, 4) sa_round_local_kernel(
                 kk[j] = ((unsigned long long)here << 32) | loc_next[src];
             }
         }
-        block_sort<32>(kk, v, total, skey, sval, sseg);  // segments: the old groups (equal rank[t])
+        block_sort(kk, v, total, skey, sval, sseg, 32);  // segments: the old groups (equal rank[t])
 
         const unsigned long long kprev = (g0 > 0 && g0 <= total) ? skey[skew(g0 - 1)] : 0ull;
         uint32_t heads = 0, starts = 0;  // new groups; old groups (a new head row)
@@ -1214,7 +1236,7 @@ void run_groups(Launcher& L, const SuffixSortBuffers& b, const unsigned long lon
 }  // namespace
 
 void suffix_sort_block(Launcher& L, const uint32_t* text, const uint32_t* term, uint64_t base, uint32_t n,
-                       uint32_t max_len, int code_bits, const SuffixSortBuffers& b) {
+                       uint32_t max_len, int code_bits, int sigma, const SuffixSortBuffers& b) {
     if (n == 0) return;
     const int dev = current_device();
     const uint64_t gtiles = (uint64_t)n / kGTile + 1;
@@ -1223,6 +1245,19 @@ void suffix_sort_block(Launcher& L, const uint32_t* text, const uint32_t* term, 
     };
     const bool wide = code_bits == 4;
     const uint32_t rounds = suffix_sort_rounds(max_len, code_bits);
+    // 4-bit codes: buckets of pw codes numbered in base sigma, pw as large as
+    // the 24-bit digits allow (pairs: sum_{l <= pw} sigma^l)
+    uint32_t pw = KeyGeom<4>::P;
+    if (wide && sigma >= 2) {
+        pw = 1;
+        for (uint32_t P = 1; P <= KeyGeom<4>::H; ++P) {
+            uint64_t pairs = 0, pow = 1;
+            for (uint32_t l = 0; l <= P; ++l, pow *= (uint64_t)sigma) pairs += pow;
+            if (pairs > (1ull << kDigitBits)) break;
+            pw = P;
+        }
+    }
+    const int seg_shift = wide ? 5 + (int)KeyGeom<4>::CB - 4 * (int)pw : kBucketShift;
     const uint32_t nwin = (uint32_t)(((uint64_t)n + kWindow - 1) / kWindow);
     const unsigned warp_grid = grid_of(g_keys_ctas[dev], (uint64_t)nwin / (kThreads / 32) + 1);
     const Units units = units_at(b.units, n);
@@ -1235,7 +1270,7 @@ void suffix_sort_block(Launcher& L, const uint32_t* text, const uint32_t* term, 
     uint32_t* d_large = b.count_log + 1;
     SBWT_LAUNCH(L, "sa_digit_keys", (double)n * 8 + n * code_bits / 8.0 + n / 8.0, 0, nullptr, digit_keys,
                 grid_of(g_keys_ctas[dev], (uint64_t)n / kThreads + 1), kThreads, 0, text, term,
-                (unsigned long long)base, n, b.keys, d_n);
+                (unsigned long long)base, n, (uint32_t)std::max(sigma, 2), pw, b.keys, d_n);
     const bool da = radix_sort_keys(L, b.keys, b.keys_alt, d_n, n, 0, digit_bits, b.radix_temp, b.err);
     const unsigned long long* elems = da ? b.keys_alt : b.keys;  // (digit, t) in row order
     // the other 64-bit array holds the keys of the listed long rows, then the
@@ -1255,7 +1290,8 @@ void suffix_sort_block(Launcher& L, const uint32_t* text, const uint32_t* term, 
     // per long row: its list entry (t, row, key), SA and rank writes; per
     // unsorted member the compacted entry
     SBWT_LAUNCH(L, "sa_local_sort", (double)n * 24, 4, b.count_log + 3, sa_local_sort_kernel,
-                grid_of(g_local_ctas[dev], nwin), kLThreads, kLocalSortSmem, n, ll_t, ll_row, ll_key, units, nwin, b.sa, b.rank, b.loc_act, b.count_log + 3, b.err);
+                grid_of(g_local_ctas[dev], nwin), kLThreads, kLocalSortSmem, n, ll_t, ll_row, ll_key, units, nwin,
+                b.sa, b.rank, b.loc_act, b.count_log + 3, b.err, seg_shift);
     // the list of the device-wide path goes to the other array (the long
     // rows' keys are dead once the local sort has run)
     SBWT_LAUNCH(L, "sa_large_gather", 32.0 * nwin, 24, d_large, large_gather, grid_of(g_local_ctas[dev], nwin),

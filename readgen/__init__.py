@@ -159,6 +159,7 @@ class Workload:
     block_suffixes: int
     index_bits: int
     appends: tuple  # read-count boundaries of the sbwt_append calls
+    alphabet: bytes = DNA
 
     @property
     def m(self) -> int:
@@ -211,6 +212,42 @@ def repetitive(n_reads: int = 300_000, genome_size: int = 2_000, seed_genome: in
     g = genome(genome_size, seed_genome)
     reads, off = sampled_reads(g, n_reads, 100, 0.01, seed_reads)
     return Workload(f"repetitive-{n_reads}x100-g{genome_size}", reads, off, 1 << 25, 64, (0, n_reads))
+
+
+def genome_alpha(size: int, seed: int, probs) -> np.ndarray:
+    """An i.i.d. genome of codes 0..len(probs)-1 drawn with the given probabilities."""
+    return _rng(seed).choice(len(probs), size=size, p=np.asarray(probs, dtype=np.float64)).astype(np.uint8)
+
+
+def sampled_reads_alpha(g: np.ndarray, n_reads: int, length: int, sub_rate: float, seed: int, alphabet: bytes):
+    """Reads of one length sampled from genome g (codes into ``alphabet``) at
+    uniform offsets, forward strand, with uniform substitutions (the new
+    symbol is one of the other len(alphabet) - 1)."""
+    rng = _rng(seed)
+    sigma = len(alphabet)
+    starts = rng.integers(0, len(g) - length + 1, size=n_reads)
+    out = np.empty((n_reads, length), dtype=np.uint8)
+    chunk = 1 << 18
+    for c0 in range(0, n_reads, chunk):
+        s = starts[c0:c0 + chunk]
+        win = np.lib.stride_tricks.sliding_window_view(g, length)[s]
+        sub = rng.random(win.shape) < sub_rate
+        shift = rng.integers(1, sigma, size=win.shape, dtype=np.uint8)
+        out[c0:c0 + chunk] = np.where(sub, (win + shift) % sigma, win)
+    lut = np.frombuffer(alphabet, dtype=np.uint8)
+    return lut[out.ravel()], offsets_from_lengths(np.full(n_reads, length))
+
+
+def wide(n_reads: int = 1_000_000, genome_size: int = 10_000_000, seed_genome: int = 0x14100562 + 7,
+         seed_reads: int = 0x05621410 + 7) -> Workload:
+    """The short-read shape over a five-symbol alphabet (A, C, G, N, T; N at
+    4%): 1M x 100 bp reads from a 10 Mbp i.i.d. genome, forward strand, 1%
+    substitutions; blocks of 16,777,216 suffixes; 32-bit indices.  Exercises
+    the 4-bit-code path."""
+    alphabet = b"ACGNT"
+    g = genome_alpha(genome_size, seed_genome, [0.24, 0.24, 0.24, 0.04, 0.24])
+    reads, off = sampled_reads_alpha(g, n_reads, 100, 0.01, seed_reads, alphabet)
+    return Workload(f"wide-ACGNT-{n_reads}x100-g{genome_size}", reads, off, 1 << 24, 32, (0, n_reads), alphabet)
 
 
 def serving(n_resident: int = 20_000_000, genome_size: int = 200_000_000, n_requests: int = 48,
