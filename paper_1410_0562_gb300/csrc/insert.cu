@@ -326,51 +326,45 @@ __global__ void __launch_bounds__(kThreads) insert_w_kernel(const OccBlockW* __r
 
 constexpr int kScanThreads = 1024;
 
-// Superblock counters from the per-superblock totals: one warp per code
-// scans the superblocks in runs of 256 (8 per lane); then C[] (Lemma 1's C
-// counts the terminators too).
+// Superblock counters from the per-superblock totals, one CTA: each thread
+// takes a contiguous range of superblocks, sums it per code, the CTA scans
+// those sums (one scan per code), and each thread writes its range's
+// prefixes; then C[] (Lemma 1's C counts the terminators too).
 template <int kCodes>
 __global__ void __launch_bounds__(kScanThreads) super_scan_kernel(const uint32_t* __restrict__ sb_tot,
                                                                   unsigned long long nsb,
                                                                   unsigned long long* __restrict__ super,
                                                                   unsigned long long* __restrict__ C,
                                                                   unsigned long long m) {
-    static_assert(kCodes <= kScanThreads / 32, "one warp per code");
-    __shared__ unsigned long long totals[kCodes];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (warp < kCodes) {
-        constexpr int kPer = 8;  // consecutive superblocks per lane: eight loads in flight
-        unsigned long long carry = 0;
-        for (unsigned long long base = 0; base < nsb; base += 32 * kPer) {
-            const unsigned long long s0 = base + (unsigned long long)lane * kPer;
-            unsigned long long v[kPer], lt = 0;
+    const unsigned long long per = (nsb + kScanThreads - 1) / kScanThreads;
+    const unsigned long long s0 = min(nsb, (unsigned long long)threadIdx.x * per), s1 = min(nsb, s0 + per);
+    unsigned long long run[kCodes];
 #pragma unroll
-            for (int j = 0; j < kPer; ++j) {
-                v[j] = s0 + j < nsb ? sb_tot[kCodes * (s0 + j) + warp] : 0ull;
-                lt += v[j];
-            }
-            unsigned long long x = lt;
+    for (int c = 0; c < kCodes; ++c) run[c] = 0;
+    for (unsigned long long s = s0; s < s1; ++s) {
 #pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const unsigned long long y = __shfl_up_sync(0xffffffffu, x, d);
-                if (lane >= d) x += y;
-            }
-            unsigned long long run = carry + x - lt;
-#pragma unroll
-            for (int j = 0; j < kPer; ++j) {
-                if (s0 + j < nsb) super[kCodes * (s0 + j) + warp] = run;
-                run += v[j];
-            }
-            carry += __shfl_sync(0xffffffffu, x, 31);
-        }
-        if (lane == 0) totals[warp] = carry;
+        for (int c = 0; c < kCodes; ++c) run[c] += sb_tot[kCodes * s + c];
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned long long run = m;
+#pragma unroll
+    for (int c = 0; c < kCodes; ++c) {
+        unsigned long long tot;
+        const unsigned long long ex = cta_exclusive_scan<SumOp, kScanThreads>(run[c], tot);
+        run[c] = ex;
+        if (threadIdx.x == 0) C[c] = tot;  // the code's total for now; turned into C[] below
+    }
+    for (unsigned long long s = s0; s < s1; ++s) {
+#pragma unroll
         for (int c = 0; c < kCodes; ++c) {
-            C[c] = run;
-            run += totals[c];
+            super[kCodes * s + c] = run[c];
+            run[c] += sb_tot[kCodes * s + c];
+        }
+    }
+    if (threadIdx.x == 0) {
+        unsigned long long acc = m;
+        for (int c = 0; c < kCodes; ++c) {
+            const unsigned long long t = C[c];
+            C[c] = acc;
+            acc += t;
         }
     }
 }

@@ -32,6 +32,29 @@ __global__ void __launch_bounds__(kThreads) bint_kernel(const uint32_t* __restri
 // 16 / sizeof(IdxT) positions is complete (g starts on a 16-byte boundary).
 constexpr uint32_t kSuperStageBytes = 48 * 1024;
 
+// rank(c, i) within i's superblock of the 2-bit dictionary, with row
+// arithmetic in the index type I (32 bits for a 32-bit index) and no
+// branches over r or c.
+template <class I>
+__device__ __forceinline__ I occ_in_super_i(const OccBlock* __restrict__ blocks, uint32_t c, I i) {
+    const ulonglong2* p = reinterpret_cast<const ulonglong2*>(blocks + (i >> kOccShift));
+    const ulonglong2 s = __ldg(p);
+    const ulonglong2 d = __ldg(p + 1);
+    const uint32_t r = (uint32_t)i & (kOccSpan - 1);
+    const uint32_t r2 = 2 * r;
+    const unsigned long long rep = (c & 2) ? ((c & 1) ? 0xFFFFFFFFFFFFFFFFull : 0xAAAAAAAAAAAAAAAAull)
+                                           : ((c & 1) ? 0x5555555555555555ull : 0ull);
+    const unsigned long long y0 = s.x ^ rep, y1 = s.y ^ rep;
+    const unsigned long long m0 = ~(y0 | (y0 >> 1)) & 0x5555555555555555ull;
+    const unsigned long long m1 = ~(y1 | (y1 >> 1)) & 0x5555555555555555ull;
+    const unsigned long long lo0 = r2 >= 64 ? ~0ull : (1ull << r2) - 1ull;
+    const unsigned long long lo1 = r2 > 64 ? (1ull << (r2 - 64)) - 1ull : 0ull;
+    const unsigned long long dm = c == 0 ? d.x : 0ull;
+    const uint32_t in_block = (uint32_t)__popcll(m0 & lo0) + (uint32_t)__popcll(m1 & lo1) -
+                              (uint32_t)__popcll(dm & ((1ull << r) - 1ull));
+    return (I)(((uint32_t)(d.y >> (16 * c)) & 0xFFFFu) + in_block);
+}
+
 template <class IdxT, bool kStage, int kB>
 __global__ void __launch_bounds__(kThreads) compute_ranks_kernel(const uint32_t* __restrict__ text,
                                                                  const unsigned long long* __restrict__ offsets,
@@ -43,12 +66,16 @@ __global__ void __launch_bounds__(kThreads) compute_ranks_kernel(const uint32_t*
                                                                  unsigned long long n_ext,
                                                                  unsigned long long m_ext, IdxT* __restrict__ g,
                                                                  uint32_t* __restrict__ d_err) {
+    // row and position arithmetic in the index type: a 32-bit index has
+    // fewer than 2^32 rows and text positions
+    using I = IdxT;
     constexpr int kSS = DictLayout<kB>::kSuperShift, kCodes = DictLayout<kB>::kCodes;
     constexpr uint32_t kPer = 32 / kB;  // codes per text word
-    extern __shared__ unsigned long long s_super[];
+    extern __shared__ unsigned long long s_raw[];
+    I* s_super = reinterpret_cast<I*>(s_raw);
     if (kStage) {
         const uint32_t words = ((uint32_t)(n_ext >> kSS) + 1) * kCodes;
-        for (uint32_t x = threadIdx.x; x < words; x += kThreads) s_super[x] = super[x];
+        for (uint32_t x = threadIdx.x; x < words; x += kThreads) s_super[x] = (I)super[x];
         __syncthreads();
     }
     const uint64_t j = (uint64_t)blockIdx.x * kThreads + threadIdx.x;
@@ -56,15 +83,16 @@ __global__ void __launch_bounds__(kThreads) compute_ranks_kernel(const uint32_t*
     const uint64_t jj = j_begin + j;
     const uint64_t o0 = offsets[j_begin];
     const uint64_t oj = offsets[jj];
-    const uint64_t len = offsets[jj + 1] - oj;
-    const uint64_t rs = oj - o0 + j;  // block-local position of the read's first symbol
-    const uint64_t P = oj + jj;       // the same position in the append's text
-    const unsigned long long C0 = d_C[0], C1 = d_C[1], C2 = d_C[2], C3 = d_C[3];
+    const I len = (I)(offsets[jj + 1] - oj);
+    const I rs = (I)(oj - o0 + j);  // block-local position of the read's first symbol
+    const I P = (I)(oj + jj);       // the same position in the append's text
+    const I C0 = (I)d_C[0], C1 = (I)d_C[1], C2 = (I)d_C[2], C3 = (I)d_C[3];
+    const I nx = (I)n_ext;
 
     constexpr int G = 16 / (int)sizeof(IdxT);
     IdxT s[G];  // s[0]: the newest value (lowest position)
     int held = 0;
-    auto push = [&](uint64_t pos, IdxT v) {
+    auto push = [&](I pos, IdxT v) {
 #pragma unroll
         for (int r = G - 1; r > 0; --r) s[r] = s[r - 1];
         s[0] = v;
@@ -85,30 +113,32 @@ __global__ void __launch_bounds__(kThreads) compute_ranks_kernel(const uint32_t*
         }
     };
 
-    unsigned long long i = m_ext;
-    push(rs + len, (IdxT)i);
-    uint64_t wcur = ~0ull;
+    I i = (I)m_ext;
+    push(rs + len, i);
+    I wcur = ~(I)0;
     uint32_t word = 0;
-    for (uint64_t k = len; k > 0; --k) {
-        const uint64_t t = P + k - 1;
+    for (I k = len; k > 0; --k) {
+        const I t = P + k - 1;
         if (t / kPer != wcur) {
             wcur = t / kPer;
             word = __ldg(text + wcur);
         }
         const uint32_t c = (word >> (32u - kB - kB * (uint32_t)(t % kPer))) & ((1u << kB) - 1u);
-        unsigned long long Cc;
+        I Cc, in;
         if constexpr (kB == 2) {
-            Cc = c == 0 ? C0 : c == 1 ? C1 : c == 2 ? C2 : C3;
+            Cc = (c & 2) ? ((c & 1) ? C3 : C2) : ((c & 1) ? C1 : C0);
+            in = occ_in_super_i<I>(blocks, c, i);
         } else {
-            Cc = __ldg(d_C + c);
+            Cc = (I)__ldg(d_C + c);
+            in = (I)DictLayout<kB>::in_super(blocks, c, i);
         }
-        const unsigned long long sup = kStage ? s_super[(i >> kSS) * kCodes + c] : __ldg(super + (i >> kSS) * kCodes + c);
-        i = Cc + sup + DictLayout<kB>::in_super(blocks, c, i);
-        if (i > n_ext) {
+        const I sup = kStage ? s_super[(i >> kSS) * kCodes + c] : (I)__ldg(super + (i >> kSS) * kCodes + c);
+        i = Cc + sup + in;
+        if (i > nx) {
             atomicOr(d_err, 8u);
-            i = n_ext;
+            i = nx;
         }
-        push(rs + k - 1, (IdxT)i);
+        push(rs + k - 1, i);
     }
     // the lowest positions of the read, below its first complete group
 #pragma unroll
@@ -242,14 +272,16 @@ __global__ void __launch_bounds__(kThreads) count_w_kernel(const OccBlockW* __re
                                                            const uint8_t* __restrict__ pats,
                                                            const unsigned long long* __restrict__ offs,
                                                            unsigned long long q, unsigned long long* __restrict__ out) {
+    __shared__ uint8_t code_of[256];  // byte -> code, kSigmaW when not in the alphabet
+    code_of[threadIdx.x] = kSigmaW;
+    __syncthreads();
+    if ((int)threadIdx.x < sigma) code_of[alpha.a[threadIdx.x]] = (uint8_t)threadIdx.x;
+    __syncthreads();
     const uint64_t i = (uint64_t)blockIdx.x * kThreads + threadIdx.x;
     if (i >= q) return;
     unsigned long long lo = 0, hi = n;
     for (uint64_t k = offs[i + 1]; k > offs[i] && lo < hi; --k) {
-        const uint32_t b = pats[k - 1];
-        uint32_t c = kSigmaW;
-        for (int a = 0; a < sigma; ++a)
-            if (b == alpha.a[a]) c = (uint32_t)a;
+        const uint32_t c = code_of[pats[k - 1]];
         if (c == kSigmaW) {  // not in the alphabet: no occurrence
             lo = hi = 0;
             break;
@@ -264,7 +296,11 @@ __global__ void __launch_bounds__(kThreads) count_w_kernel(const OccBlockW* __re
 __global__ void __launch_bounds__(kThreads) unpack_w_kernel(const OccBlockW* __restrict__ blocks,
                                                             unsigned long long r0, unsigned long long r1,
                                                             Alphabet16 alpha, uint8_t* __restrict__ out) {
-    // one occurrence block (64 rows) per thread, as for unpack_kernel
+    // one occurrence block (64 rows) per thread, as for unpack_kernel; the
+    // alphabet is looked up from shared memory
+    __shared__ uint8_t sym_byte[kSigmaW];
+    if (threadIdx.x < kSigmaW) sym_byte[threadIdx.x] = alpha.a[threadIdx.x];
+    __syncthreads();
     const uint64_t b = (r0 >> kOccShift) + (uint64_t)blockIdx.x * kThreads + threadIdx.x;
     const uint64_t row0 = b << kOccShift;
     if (row0 >= r1) return;
@@ -277,7 +313,7 @@ __global__ void __launch_bounds__(kThreads) unpack_w_kernel(const OccBlockW* __r
         for (int q4 = 0; q4 < 4; ++q4) {
             const uint32_t q = 4 * w + q4;
             const uint32_t c = (uint32_t)(blk.sym[q >> 4] >> (4 * (q & 15))) & 15u;
-            const uint32_t byte = ((blk.dmask >> q) & 1ull) ? (uint32_t)'$' : (uint32_t)alpha.a[c];
+            const uint32_t byte = ((blk.dmask >> q) & 1ull) ? (uint32_t)'$' : (uint32_t)sym_byte[c];
             x |= byte << (8 * q4);
         }
         words[w] = x;
@@ -303,7 +339,7 @@ void compute_ranks_w(Launcher& L, const uint32_t* text, const uint64_t* d_offset
                      double bytes, const void* blocks, const unsigned long long* super, const unsigned long long* d_C,
                      uint64_t n_ext, uint64_t m_ext, IdxT* g, uint32_t* d_err) {
     using Block = typename DictLayout<kB>::Block;
-    const size_t stage = ((n_ext >> DictLayout<kB>::kSuperShift) + 1) * DictLayout<kB>::kCodes * 8;
+    const size_t stage = ((n_ext >> DictLayout<kB>::kSuperShift) + 1) * DictLayout<kB>::kCodes * sizeof(IdxT);
     auto* const kern = stage <= kSuperStageBytes ? compute_ranks_kernel<IdxT, true, kB>
                                                  : compute_ranks_kernel<IdxT, false, kB>;
     SBWT_LAUNCH(L, "compute_ranks", bytes, 0, nullptr, kern, ceil_div_u(nreads, kThreads), kThreads,

@@ -139,11 +139,16 @@ __device__ __forceinline__ unsigned long long match_code4(unsigned long long x, 
     return ~y & 0x1111111111111111ull;
 }
 
-__device__ __forceinline__ uint32_t cnt12(const unsigned long long (&cw)[3], uint32_t c) {
+// 12-bit count of code c from the three counter words (selects, no
+// indexing by c, so the words stay in registers).
+__device__ __forceinline__ uint32_t cnt12(unsigned long long c0, unsigned long long c1, unsigned long long c2,
+                                          uint32_t c) {
     const uint32_t o = 12u * c;
     const uint32_t w = o >> 6, sh = o & 63u;
-    unsigned long long v = cw[w] >> sh;
-    if (sh > 52) v |= cw[w + 1] << (64 - sh);
+    const unsigned long long lo = w == 0 ? c0 : (w == 1 ? c1 : c2);
+    const unsigned long long hi = w == 0 ? c1 : c2;
+    unsigned long long v = lo >> sh;
+    if (sh > 52) v |= hi << (64 - sh);
     return (uint32_t)v & 0xFFFu;
 }
 
@@ -153,7 +158,6 @@ __device__ __forceinline__ unsigned long long occ_rank_in_super_w(const OccBlock
     const ulonglong2* p = reinterpret_cast<const ulonglong2*>(blocks + (i >> kOccShift));
     const ulonglong2 s01 = __ldg(p), s23 = __ldg(p + 1), dc = __ldg(p + 2), c12 = __ldg(p + 3);
     const unsigned long long sym[4] = {s01.x, s01.y, s23.x, s23.y};
-    const unsigned long long cw[3] = {dc.y, c12.x, c12.y};
     const uint32_t r = (uint32_t)(i & (kOccSpan - 1));
     uint32_t in_block = 0;
 #pragma unroll
@@ -162,7 +166,7 @@ __device__ __forceinline__ unsigned long long occ_rank_in_super_w(const OccBlock
         in_block += __popcll(match_code4(sym[w], c) & low_bits(4 * rows));
     }
     if (c == 0) in_block -= __popcll(dc.x & low_bits(r));
-    return cnt12(cw, c) + in_block;
+    return cnt12(dc.y, c12.x, c12.y, c) + in_block;
 }
 
 __device__ __forceinline__ unsigned long long occ_rank_w(const OccBlockW* __restrict__ blocks,

@@ -282,7 +282,7 @@ def check_full_size(w, B, samples=3, seed=17):
         p = int(rng.integers(0, int(lens[r]) + 1))
         row = oracle.row_of_suffix(w.reads, w.offsets, r, p)
         assert B[row] == oracle.bwt_symbol_of_suffix(w.reads, w.offsets, r, p)
-    rec, roff = oracle.lf_invert_sampled(B, w.m)
+    rec, roff = oracle.lf_invert_sampled(B, w.m, alphabet=w.alphabet)
     assert np.array_equal(roff, w.offsets) and np.array_equal(rec, w.reads)
 
 

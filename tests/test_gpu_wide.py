@@ -15,6 +15,7 @@ import pytest
 import oracle
 import paper_1410_0562_gb300 as sb
 import readgen
+from test_gpu_parity import check_full_size
 from test_oracle import pack
 
 pytestmark = pytest.mark.gpu
@@ -165,8 +166,10 @@ def test_wide_save_load_prepend_and_host_tier(tmp_path):
 
 def test_wide_larger_genome_reads():
     """20k reads x 100 bp over A,C,G,N,T from a 400 kbp genome (5x
-    coverage): buckets of five 4-bit codes are large, so both the CTA-local
-    and the device-wide sort paths and several doubling rounds run."""
+    coverage; the CTA-local sorts and three doubling rounds of 14-code
+    keys), then 3,000 x 80 bp reads from a 300-symbol genome (~800x
+    coverage: buckets and groups far over the CTA-local capacity, so the
+    device-wide path runs)."""
     rng = np.random.default_rng(2024)
     genome = rng.choice(np.frombuffer(b"ACGNT", np.uint8), size=400_000, p=[0.24, 0.24, 0.24, 0.04, 0.24])
     starts = rng.integers(0, len(genome) - 100, size=20_000)
@@ -175,3 +178,19 @@ def test_wide_larger_genome_reads():
     expect = oracle.bwt(data, off, b"ACGNT")
     assert np.array_equal(build(b"ACGNT", data, off).bwt(), expect)
     assert np.array_equal(build(b"ACGNT", data, off, M=1 << 16, cuts=[0, 9_000, 20_000]).bwt(), expect)
+    small = rng.choice(np.frombuffer(b"ACGNT", np.uint8), size=300)
+    starts = rng.integers(0, len(small) - 80, size=3_000)
+    reads = [bytes(small[s:s + 80]) for s in starts]
+    data, off = pack(reads)
+    expect = oracle.bwt(data, off, b"ACGNT")
+    assert np.array_equal(build(b"ACGNT", data, off).bwt(), expect)
+
+
+def test_wide_workload_full_size():
+    """The wide workload (1M x 100 bp over A,C,G,N,T, blocks of 2^24) in the
+    launch configuration the benchmark times: multiset, terminator rows,
+    sampled rows counted by the oracle and LF inversion of the whole B."""
+    w = readgen.wide()
+    idx = build(w.alphabet, w.reads, w.offsets, M=w.block_suffixes, index_bits=w.index_bits)
+    assert idx.size() == (oracle.num_suffixes(w.offsets), w.m)
+    check_full_size(w, idx.bwt(), samples=2)
