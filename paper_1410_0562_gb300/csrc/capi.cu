@@ -68,6 +68,9 @@ struct sbwt_index {
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_sorted[2] = {nullptr, nullptr},
                 ev_consumed[2] = {nullptr, nullptr};
+    // host appends: block k's text is packed as soon as its reads arrive;
+    // its sort waits on ev_packed[k] (grown on demand)
+    std::vector<cudaEvent_t> ev_packed;
     bool dev_ready = false;
 
     uint64_t n = 0, m = 0;
@@ -287,7 +290,8 @@ std::vector<Need> buffer_needs(sbwt_index* idx, const Plan& p, bool host_input, 
     v.push_back({&idx->bint, (size_t)cap});
     const int cb = idx->code_bits;
     const uint64_t nsb = dict_supers_of(n_final, cb);
-    v.push_back({&idx->sb_tot, (size_t)nsb * 4 * dict_codes(cb)});
+    // superblock totals, then the superblock scan's per-256 totals (insert.cu)
+    v.push_back({&idx->sb_tot, (size_t)(((nsb * dict_codes(cb) + 3) & ~3ull) * 4 + (nsb / 256 + 1) * 8 * dict_codes(cb))});
     for (int k = 0; k < 3; ++k) {
         if (k == idx->cur) continue;
         v.push_back({&idx->dict[k].blocks, (size_t)dict_blocks(n_final) * dict_block_bytes(cb), true});
@@ -377,7 +381,8 @@ int reserve(sbwt_index* idx, const std::vector<Need>& needs) {
 // Block k of the append, the q-th to run (q = k unless the append prepends).
 template <class IdxT>
 void run_block(sbwt_index* idx, const BlockPlan& bp, const uint64_t* d_offsets, const Dict& src, Dict& dst,
-               uint64_t n_ext, uint64_t m_ext, size_t slots, size_t k, size_t q, bool prepend) {
+               uint64_t n_ext, uint64_t m_ext, size_t slots, size_t k, size_t q, bool prepend,
+               cudaEvent_t packed) {
     Launcher& L = idx->L;
     const uint32_t n = (uint32_t)bp.n_int;
     SuffixSortBuffers b;
@@ -405,6 +410,7 @@ void run_block(sbwt_index* idx, const BlockPlan& bp, const uint64_t* d_offsets, 
     // block k - 2 has read it
     const cudaStream_t s = L.stream;
     if (q >= 2) cudaStreamWaitEvent(idx->side, idx->ev_consumed[q & 1], 0);
+    if (packed) cudaStreamWaitEvent(idx->side, packed, 0);  // this block's text is in place
     L.stream = idx->side;
     suffix_sort_block(L, text, term, bp.base, n, (uint32_t)bp.max_len, idx->code_bits, idx->sigma, b);
     cudaEventRecord(idx->ev_sorted[q & 1], idx->side);
@@ -454,9 +460,37 @@ int append_impl(sbwt_index* idx, const uint8_t* d_reads, const uint64_t* d_offse
     const auto t_plan = std::chrono::steady_clock::now();
     L.add_host("host:plan", std::chrono::duration<double, std::milli>(t_plan - t_start).count());
 
+    // Host reads of an append with several blocks arrive block by block: the
+    // copy of block k's bytes, then the packing of its words, and its sort
+    // starts while the later blocks' bytes are still on the way.  Chunk k
+    // packs the words up to the one holding block k's last position, so it
+    // copies the bytes of every position below that word's end (a few
+    // positions into block k + 1 at most).  Graph capture keeps one copy.
+    const bool pipelined = host_input && !idx->graph_replay && p.blocks.size() > 1 && p.nbytes > 0;
+    std::vector<uint64_t> chunk_bytes, chunk_words;
+    if (pipelined) {
+        for (const BlockPlan& b : p.blocks) {
+            const uint64_t pos_end = std::min<uint64_t>(p.npos, ((b.base + b.n_int - 1) / 32 + 1) * 32);
+            // first read whose first position is at or past pos_end
+            uint64_t lo = 0, hi = m_new;
+            while (lo < hi) {
+                const uint64_t mid = lo + (hi - lo) / 2;
+                if (h_off[mid] + mid < pos_end) lo = mid + 1; else hi = mid;
+            }
+            chunk_bytes.push_back(h_off[lo]);
+            chunk_words.push_back((pos_end + 31) / 32);
+        }
+        chunk_bytes.back() = p.nbytes;
+        chunk_words.back() = (p.npos + 31) / 32;
+        while (idx->ev_packed.size() < p.blocks.size()) {
+            cudaEvent_t e = nullptr;
+            if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return SBWT_EDEVICE;
+            idx->ev_packed.push_back(e);
+        }
+    }
     if (host_input) {
-        if (p.nbytes) cudaMemcpyAsync(idx->reads.p, h_reads, p.nbytes, cudaMemcpyHostToDevice, s);
         cudaMemcpyAsync(idx->offsets.p, h_off, (m_new + 1) * 8, cudaMemcpyHostToDevice, s);
+        if (p.nbytes && !pipelined) cudaMemcpyAsync(idx->reads.p, h_reads, p.nbytes, cudaMemcpyHostToDevice, s);
         d_reads = (const uint8_t*)idx->reads.p;
         d_offsets = (const uint64_t*)idx->offsets.p;
     }
@@ -481,16 +515,32 @@ int append_impl(sbwt_index* idx, const uint8_t* d_reads, const uint64_t* d_offse
         // A byte outside the alphabet sets bit 0 of the error word; the blocks
         // still run (into scratch dictionaries) and the check at the end
         // refuses the result, which saves a round trip on every valid append.
-        if (idx->code_bits == 4)
-            launch_pack_w(L, d_reads, d_offsets, m_new, p.npos, idx->alpha16, idx->sigma, (uint32_t*)idx->text.p,
-                          (uint32_t*)idx->term.p, (uint32_t*)idx->err.p);
-        else
-            launch_pack(L, d_reads, d_offsets, m_new, p.npos, idx->alpha4, idx->sigma, (uint32_t*)idx->text.p,
-                        (uint32_t*)idx->term.p, (uint32_t*)idx->err.p);
+        auto pack = [&](uint64_t w0, uint64_t w1) {
+            if (idx->code_bits == 4)
+                launch_pack_w(L, d_reads, d_offsets, m_new, p.npos, idx->alpha16, idx->sigma,
+                              (uint32_t*)idx->text.p, (uint32_t*)idx->term.p, (uint32_t*)idx->err.p, w0, w1);
+            else
+                launch_pack(L, d_reads, d_offsets, m_new, p.npos, idx->alpha4, idx->sigma, (uint32_t*)idx->text.p,
+                            (uint32_t*)idx->term.p, (uint32_t*)idx->err.p, w0, w1);
+        };
+        if (pipelined) {
+            uint64_t b0 = 0, w0 = 0;
+            for (size_t k = 0; k < p.blocks.size(); ++k) {
+                if (chunk_bytes[k] > b0)
+                    cudaMemcpyAsync((uint8_t*)idx->reads.p + b0, h_reads + b0, chunk_bytes[k] - b0,
+                                    cudaMemcpyHostToDevice, s);
+                pack(w0, chunk_words[k]);
+                cudaEventRecord(idx->ev_packed[k], s);
+                b0 = std::max(b0, chunk_bytes[k]);
+                w0 = std::max(w0, chunk_words[k]);
+            }
+        } else {
+            pack(0, ~0ull);
+        }
         int src = idx->cur;
         uint64_t n_ext = idx->n, m_ext = idx->m;
         cudaEventRecord(idx->ev_fork, s);  // the sorts read the packed text
-        cudaStreamWaitEvent(idx->side, idx->ev_fork, 0);
+        if (!pipelined) cudaStreamWaitEvent(idx->side, idx->ev_fork, 0);
         const size_t nb = p.blocks.size();
         for (size_t q = 0; q < nb; ++q) {
             // prepending runs the blocks last to first, so each one's reads go
@@ -498,12 +548,13 @@ int append_impl(sbwt_index* idx, const uint8_t* d_reads, const uint64_t* d_offse
             const size_t k = p.prepend ? nb - 1 - q : q;
             const BlockPlan& bp = p.blocks[k];
             const int dst = other[q & 1];
+            cudaEvent_t packed = pipelined ? idx->ev_packed[k] : nullptr;
             if (p.idx64)
                 run_block<unsigned long long>(idx, bp, d_offsets, idx->dict[src], idx->dict[dst], n_ext, m_ext,
-                                              p.slots, k, q, p.prepend);
+                                              p.slots, k, q, p.prepend, packed);
             else
                 run_block<uint32_t>(idx, bp, d_offsets, idx->dict[src], idx->dict[dst], n_ext, m_ext, p.slots, k, q,
-                                    p.prepend);
+                                    p.prepend, packed);
             n_ext += bp.n_int;
             m_ext += bp.j1 - bp.j0;
             src = dst;
@@ -1182,6 +1233,8 @@ void sbwt_destroy(sbwt_index* idx) {
         }
         for (cudaEvent_t e : {idx->ev_fork, idx->ev_join, idx->ev_sorted[0], idx->ev_sorted[1],
                               idx->ev_consumed[0], idx->ev_consumed[1]})
+            if (e) cudaEventDestroy(e);
+        for (cudaEvent_t e : idx->ev_packed)
             if (e) cudaEventDestroy(e);
         if (idx->own_stream) cudaStreamDestroy(idx->stream);
     }

@@ -324,18 +324,80 @@ __global__ void __launch_bounds__(kThreads) insert_w_kernel(const OccBlockW* __r
     }
 }
 
-constexpr int kScanThreads = 1024;
+constexpr int kScanThreads = 256;
 
-// Superblock counters from the per-superblock totals, one CTA: each thread
-// takes a contiguous range of superblocks, sums it per code, the CTA scans
-// those sums (one scan per code), and each thread writes its range's
-// prefixes; then C[] (Lemma 1's C counts the terminators too).
+// Superblock counters from the per-superblock totals in three steps: each
+// CTA scans 256 superblocks (one scan per code) and keeps its totals; one
+// CTA scans those totals and writes C[] (Lemma 1's C counts the terminators
+// too); each CTA adds its offsets.  Up to kSmallScan superblocks take one
+// CTA instead (below).
 template <int kCodes>
-__global__ void __launch_bounds__(kScanThreads) super_scan_kernel(const uint32_t* __restrict__ sb_tot,
-                                                                  unsigned long long nsb,
-                                                                  unsigned long long* __restrict__ super,
-                                                                  unsigned long long* __restrict__ C,
-                                                                  unsigned long long m) {
+__global__ void __launch_bounds__(kScanThreads) super_local_kernel(const uint32_t* __restrict__ sb_tot,
+                                                                   unsigned long long nsb,
+                                                                   unsigned long long* __restrict__ super,
+                                                                   unsigned long long* __restrict__ chunk_tot) {
+    const unsigned long long s = (unsigned long long)blockIdx.x * kScanThreads + threadIdx.x;
+#pragma unroll 1
+    for (int c = 0; c < kCodes; ++c) {
+        const unsigned long long v = s < nsb ? sb_tot[kCodes * s + c] : 0ull;
+        unsigned long long tot;
+        const unsigned long long ex = cta_exclusive_scan<SumOp, kScanThreads>(v, tot);
+        if (s < nsb) super[kCodes * s + c] = ex;
+        if (threadIdx.x == 0) chunk_tot[(unsigned long long)kCodes * blockIdx.x + c] = tot;
+    }
+}
+
+template <int kCodes>
+__global__ void __launch_bounds__(kScanThreads) super_chunks_kernel(unsigned long long* __restrict__ chunk_tot,
+                                                                    unsigned long long nchunks,
+                                                                    unsigned long long* __restrict__ C,
+                                                                    unsigned long long m) {
+    __shared__ unsigned long long code_tot[kCodes];
+#pragma unroll 1
+    for (int c = 0; c < kCodes; ++c) {
+        unsigned long long carry = 0;
+        for (unsigned long long b = 0; b < nchunks; b += kScanThreads) {
+            const unsigned long long k = b + threadIdx.x;
+            const unsigned long long v = k < nchunks ? chunk_tot[kCodes * k + c] : 0ull;
+            unsigned long long tot;
+            const unsigned long long ex = cta_exclusive_scan<SumOp, kScanThreads>(v, tot);
+            if (k < nchunks) chunk_tot[kCodes * k + c] = carry + ex;
+            carry += tot;
+        }
+        if (threadIdx.x == 0) code_tot[c] = carry;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long acc = m;
+        for (int c = 0; c < kCodes; ++c) {
+            C[c] = acc;
+            acc += code_tot[c];
+        }
+    }
+}
+
+template <int kCodes>
+__global__ void __launch_bounds__(kScanThreads) super_add_kernel(unsigned long long* __restrict__ super,
+                                                                 unsigned long long nsb,
+                                                                 const unsigned long long* __restrict__ chunk_tot) {
+    const unsigned long long s = (unsigned long long)blockIdx.x * kScanThreads + threadIdx.x;
+    if (s >= nsb) return;
+#pragma unroll
+    for (int c = 0; c < kCodes; ++c) super[kCodes * s + c] += chunk_tot[(unsigned long long)kCodes * blockIdx.x + c];
+}
+
+// The same in one CTA for a few superblocks: each thread takes a contiguous
+// range, sums it per code, the CTA scans the sums and each thread writes
+// its range's prefixes.
+constexpr uint64_t kSmallScan = 8 * kScanThreads;
+
+template <int kCodes>
+__global__ void __launch_bounds__(kScanThreads) super_scan_small_kernel(const uint32_t* __restrict__ sb_tot,
+                                                                        unsigned long long nsb,
+                                                                        unsigned long long* __restrict__ super,
+                                                                        unsigned long long* __restrict__ C,
+                                                                        unsigned long long m) {
+    __shared__ unsigned long long code_tot[kCodes];
     const unsigned long long per = (nsb + kScanThreads - 1) / kScanThreads;
     const unsigned long long s0 = min(nsb, (unsigned long long)threadIdx.x * per), s1 = min(nsb, s0 + per);
     unsigned long long run[kCodes];
@@ -348,9 +410,8 @@ __global__ void __launch_bounds__(kScanThreads) super_scan_kernel(const uint32_t
 #pragma unroll
     for (int c = 0; c < kCodes; ++c) {
         unsigned long long tot;
-        const unsigned long long ex = cta_exclusive_scan<SumOp, kScanThreads>(run[c], tot);
-        run[c] = ex;
-        if (threadIdx.x == 0) C[c] = tot;  // the code's total for now; turned into C[] below
+        run[c] = cta_exclusive_scan<SumOp, kScanThreads>(run[c], tot);
+        if (threadIdx.x == 0) code_tot[c] = tot;
     }
     for (unsigned long long s = s0; s < s1; ++s) {
 #pragma unroll
@@ -359,14 +420,31 @@ __global__ void __launch_bounds__(kScanThreads) super_scan_kernel(const uint32_t
             run[c] += sb_tot[kCodes * s + c];
         }
     }
+    __syncthreads();
     if (threadIdx.x == 0) {
         unsigned long long acc = m;
         for (int c = 0; c < kCodes; ++c) {
-            const unsigned long long t = C[c];
             C[c] = acc;
-            acc += t;
+            acc += code_tot[c];
         }
     }
+}
+
+template <int kCodes>
+void super_scan(Launcher& L, const uint32_t* sb_tot, uint64_t nsb, unsigned long long* super, unsigned long long* C,
+                uint64_t m, unsigned long long* chunk_tot) {
+    if (nsb <= kSmallScan) {
+        SBWT_LAUNCH(L, "super_scan", (4.0 + 8.0) * kCodes * nsb, 0, nullptr, super_scan_small_kernel<kCodes>, 1,
+                    kScanThreads, 0, sb_tot, (unsigned long long)nsb, super, C, (unsigned long long)m);
+        return;
+    }
+    const unsigned nchunks = ceil_div_u(nsb, kScanThreads);
+    SBWT_LAUNCH(L, "super_scan", (4.0 + 16.0) * kCodes * nsb, 0, nullptr, super_local_kernel<kCodes>, nchunks,
+                kScanThreads, 0, sb_tot, (unsigned long long)nsb, super, chunk_tot);
+    SBWT_LAUNCH(L, "super_scan", 16.0 * kCodes * nchunks, 0, nullptr, super_chunks_kernel<kCodes>, 1, kScanThreads, 0,
+                chunk_tot, (unsigned long long)nchunks, C, (unsigned long long)m);
+    SBWT_LAUNCH(L, "super_scan", (16.0 + 8.0) * kCodes * nsb, 0, nullptr, super_add_kernel<kCodes>, nchunks,
+                kScanThreads, 0, super, (unsigned long long)nsb, chunk_tot);
 }
 
 }  // namespace
@@ -376,6 +454,10 @@ void launch_insert(Launcher& L, const void* old_blocks, uint64_t n_ext, const ui
                    uint64_t n_int, void* new_blocks, unsigned long long* new_super, unsigned long long* new_C,
                    uint64_t m_new, uint32_t* sb_tot, int code_bits) {
     const uint64_t n_new = n_ext + n_int;
+    // the superblock scan's per-chunk totals live after the superblock totals
+    const uint64_t nsb_all = dict_supers_of(n_new, code_bits);
+    unsigned long long* chunk_tot =
+        reinterpret_cast<unsigned long long*>(sb_tot + ((nsb_all * dict_codes(code_bits) + 3) & ~3ull));
     if (code_bits == 4) {
         const uint64_t nsb = dict_supers_w(n_new);
         const double bytes = 64.0 * dict_blocks(n_ext) + (1.0 + sizeof(IdxT)) * n_int + 64.0 * dict_blocks(n_new);
@@ -384,8 +466,7 @@ void launch_insert(Launcher& L, const void* old_blocks, uint64_t n_ext, const ui
                     static_cast<const OccBlockW*>(old_blocks), (unsigned long long)n_ext, bint, gsa,
                     (unsigned long long)n_int, static_cast<OccBlockW*>(new_blocks), (unsigned long long)n_new,
                     (unsigned long long)nsb, sb_tot);
-        SBWT_LAUNCH(L, "super_scan", 192.0 * nsb, 0, nullptr, super_scan_kernel<kSigmaW>, 1, kScanThreads, 0, sb_tot,
-                    (unsigned long long)nsb, new_super, new_C, (unsigned long long)m_new);
+        super_scan<kSigmaW>(L, sb_tot, nsb, new_super, new_C, m_new, chunk_tot);
         return;
     }
     const uint64_t nsb = dict_supers(n_new);
@@ -393,8 +474,7 @@ void launch_insert(Launcher& L, const void* old_blocks, uint64_t n_ext, const ui
     SBWT_LAUNCH(L, "insert_merge", bytes, 0, nullptr, insert_kernel<IdxT>, (unsigned)nsb, kThreads, 0,
                 static_cast<const OccBlock*>(old_blocks), (unsigned long long)n_ext, bint, gsa,
                 (unsigned long long)n_int, static_cast<OccBlock*>(new_blocks), (unsigned long long)n_new, sb_tot);
-    SBWT_LAUNCH(L, "super_scan", 48.0 * nsb, 0, nullptr, super_scan_kernel<4>, 1, kScanThreads, 0, sb_tot,
-                (unsigned long long)nsb, new_super, new_C, (unsigned long long)m_new);
+    super_scan<4>(L, sb_tot, nsb, new_super, new_C, m_new, chunk_tot);
 }
 
 template void launch_insert<uint32_t>(Launcher&, const void*, uint64_t, const uint8_t*, const uint32_t*, uint64_t,

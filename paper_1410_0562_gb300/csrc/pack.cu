@@ -6,6 +6,8 @@
 // terminator at offsets[j+1] + j, i.e. every read is followed by one
 // terminator slot (T = S_0 $_0 S_1 $_1 ..., Section 2 of arXiv 1410.0562).
 // The byte behind position t of read j is therefore reads[t - j].
+#include <algorithm>
+
 #include "sbwt_kernels.cuh"
 
 namespace sbwt {
@@ -19,10 +21,11 @@ __global__ void __launch_bounds__(kThreads) pack_kernel(const uint8_t* __restric
                                                         unsigned long long m, unsigned long long npos,
                                                         uint32_t alpha4, int sigma, uint32_t* __restrict__ text,
                                                         uint32_t* __restrict__ term,
-                                                        uint32_t* __restrict__ d_err) {
-    const uint64_t w = (uint64_t)blockIdx.x * kThreads + threadIdx.x;
+                                                        uint32_t* __restrict__ d_err, unsigned long long w_begin,
+                                                        unsigned long long w_end) {
+    const uint64_t w = w_begin + (uint64_t)blockIdx.x * kThreads + threadIdx.x;
     const uint64_t t0 = w * 32;
-    if (t0 >= npos) return;
+    if (w >= w_end || t0 >= npos) return;
     // read holding t0: the last j with offsets[j] + j <= t0
     uint64_t lo = 0, hi = m;  // invariant: offsets[lo] + lo <= t0 < offsets[hi] + hi
     while (hi - lo > 1) {
@@ -66,15 +69,16 @@ __global__ void __launch_bounds__(kThreads) pack_w_kernel(const uint8_t* __restr
                                                           unsigned long long m, unsigned long long npos,
                                                           Alphabet16 alpha, int sigma, uint32_t* __restrict__ text,
                                                           uint32_t* __restrict__ term,
-                                                          uint32_t* __restrict__ d_err) {
+                                                          uint32_t* __restrict__ d_err, unsigned long long w_begin,
+                                                          unsigned long long w_end) {
     __shared__ uint8_t code_of[256];
     code_of[threadIdx.x] = 0xFF;
     __syncthreads();
     if ((int)threadIdx.x < sigma) code_of[alpha.a[threadIdx.x]] = (uint8_t)threadIdx.x;
     __syncthreads();
-    const uint64_t w = (uint64_t)blockIdx.x * kThreads + threadIdx.x;
+    const uint64_t w = w_begin + (uint64_t)blockIdx.x * kThreads + threadIdx.x;
     const uint64_t t0 = w * 32;
-    if (t0 >= npos) return;
+    if (w >= w_end || t0 >= npos) return;
     uint64_t lo = 0, hi = m;  // invariant: offsets[lo] + lo <= t0 < offsets[hi] + hi
     while (hi - lo > 1) {
         uint64_t mid = lo + (hi - lo) / 2;
@@ -109,23 +113,31 @@ __global__ void __launch_bounds__(kThreads) pack_w_kernel(const uint8_t* __restr
 }  // namespace
 
 void launch_pack_w(Launcher& L, const uint8_t* d_reads, const uint64_t* d_offsets, uint64_t m, uint64_t npos,
-                   const Alphabet16& alpha, int sigma, uint32_t* text, uint32_t* term, uint32_t* d_err) {
-    const uint64_t words = (npos + 31) / 32;
-    if (words == 0) return;
-    const unsigned grid = ceil_div_u(words, kThreads);
-    SBWT_LAUNCH(L, "pack_reads", (double)(npos - m) + 8.0 * (m + 1) + npos / 2.0 + npos / 8.0, 0, nullptr,
+                   const Alphabet16& alpha, int sigma, uint32_t* text, uint32_t* term, uint32_t* d_err,
+                   uint64_t w_begin, uint64_t w_end) {
+    w_end = std::min<uint64_t>(w_end, (npos + 31) / 32);
+    if (w_end <= w_begin) return;
+    const double pos = (double)std::min<uint64_t>(npos, w_end * 32) - (double)(w_begin * 32);
+    const unsigned grid = ceil_div_u(w_end - w_begin, kThreads);
+    SBWT_LAUNCH(L, "pack_reads", pos + 8.0 * (m + 1) * pos / npos + pos / 2.0 + pos / 8.0, 0, nullptr,
                 pack_w_kernel, grid, kThreads, 0, d_reads, reinterpret_cast<const unsigned long long*>(d_offsets),
-                (unsigned long long)m, (unsigned long long)npos, alpha, sigma, text, term, d_err);
+                (unsigned long long)m, (unsigned long long)npos, alpha, sigma, text, term, d_err,
+                (unsigned long long)w_begin, (unsigned long long)w_end);
 }
 
 void launch_pack(Launcher& L, const uint8_t* d_reads, const uint64_t* d_offsets, uint64_t m, uint64_t npos,
-                 uint32_t alpha4, int sigma, uint32_t* text, uint32_t* term, uint32_t* d_err) {
-    const uint64_t words = (npos + 31) / 32;
-    if (words == 0) return;
-    const unsigned grid = ceil_div_u(words, kThreads);
-    SBWT_LAUNCH(L, "pack_reads", (double)(npos - m) + 8.0 * (m + 1) + npos / 4.0 + npos / 8.0, 0, nullptr,
+                 uint32_t alpha4, int sigma, uint32_t* text, uint32_t* term, uint32_t* d_err, uint64_t w_begin,
+                 uint64_t w_end) {
+    w_end = std::min<uint64_t>(w_end, (npos + 31) / 32);
+    if (w_end <= w_begin) return;
+    // per position: its byte (about one per position), the text and bitmap
+    // writes; the offsets read by the binary searches
+    const double pos = (double)std::min<uint64_t>(npos, w_end * 32) - (double)(w_begin * 32);
+    const unsigned grid = ceil_div_u(w_end - w_begin, kThreads);
+    SBWT_LAUNCH(L, "pack_reads", pos + 8.0 * (m + 1) * pos / npos + pos / 4.0 + pos / 8.0, 0, nullptr,
                 pack_kernel, grid, kThreads, 0, d_reads, reinterpret_cast<const unsigned long long*>(d_offsets),
-                (unsigned long long)m, (unsigned long long)npos, alpha4, sigma, text, term, d_err);
+                (unsigned long long)m, (unsigned long long)npos, alpha4, sigma, text, term, d_err,
+                (unsigned long long)w_begin, (unsigned long long)w_end);
 }
 
 }  // namespace sbwt

@@ -99,9 +99,10 @@ __global__ void __launch_bounds__(kThreads) radix_upsweep_kernel(const KeyT* __r
 
 // Output offset of every (chunk, digit): the digit's start in the sorted
 // output (exclusive scan of the totals) plus the same digit's count in all
-// earlier chunks.  CTA x handles digits [32x, 32x + 32); its 1024 threads
-// are 32 digits x 32 groups of consecutive chunks.
-constexpr int kScanThreads = 1024;
+// earlier chunks.  CTA x handles digits [32x, 32x + 32); its 256 threads are
+// 32 digits x 8 groups of consecutive chunks (small CTAs find room on SMs
+// that the other stream's kernels keep busy).
+constexpr int kScanThreads = 256;
 constexpr int kScanGroups = kScanThreads / 32;
 
 __global__ void __launch_bounds__(kScanThreads) radix_chunk_scan_kernel(uint32_t* __restrict__ chunk_counts,

@@ -13,11 +13,15 @@ struct Alphabet16 {
 
 // pack.cu: reads + offsets (device) -> 2-bit text and terminator bitmap of
 // the whole append; sets *d_err != 0 when a byte is outside the alphabet.
+// [w_begin, w_end) limits the launch to those 32-position words (the bytes
+// of their positions must be in d_reads already).
 void launch_pack(Launcher& L, const uint8_t* d_reads, const uint64_t* d_offsets, uint64_t m, uint64_t npos,
-                 uint32_t alpha4, int sigma, uint32_t* text, uint32_t* term, uint32_t* d_err);
+                 uint32_t alpha4, int sigma, uint32_t* text, uint32_t* term, uint32_t* d_err, uint64_t w_begin = 0,
+                 uint64_t w_end = ~0ull);
 // The same with 4-bit codes (5 to 16 symbols); text starts on a 16-byte boundary.
 void launch_pack_w(Launcher& L, const uint8_t* d_reads, const uint64_t* d_offsets, uint64_t m, uint64_t npos,
-                   const Alphabet16& alpha, int sigma, uint32_t* text, uint32_t* term, uint32_t* d_err);
+                   const Alphabet16& alpha, int sigma, uint32_t* text, uint32_t* term, uint32_t* d_err,
+                   uint64_t w_begin = 0, uint64_t w_end = ~0ull);
 
 // suffix_sort.cu: ConstructSA of one block of n suffixes starting at text
 // position `base`.  Results: sa (SA_int), rank (its inverse).
@@ -78,7 +82,8 @@ void launch_unpack(Launcher& L, const void* blocks, uint64_t r0, uint64_t r1, co
 // dictionary's symbols, terminator masks and block counters, then the
 // superblock counters and C[] (m = terminators in the new dictionary).
 // Blocks are OccBlock (code_bits 2) or OccBlockW (code_bits 4); sb_tot holds
-// 4 (16) words per superblock.
+// 4 (16) words per superblock, rounded up to 4 words, then 4 (16) 64-bit
+// words per 256 superblocks.
 template <class IdxT>
 void launch_insert(Launcher& L, const void* old_blocks, uint64_t n_ext, const uint8_t* bint, const IdxT* gsa,
                    uint64_t n_int, void* new_blocks, unsigned long long* new_super, unsigned long long* new_C,

@@ -71,7 +71,7 @@ constexpr uint32_t kWindow = kLCap / 2;          // rows per window
 constexpr uint32_t kLSlots = kLCap + kLCap / kLItems;
 constexpr uint32_t kNone = 0xFFFFFFFFu;
 constexpr uint32_t kShortFlag = 0x80000000u;  // digit flag: the bucket holds suffixes with len < P
-constexpr int kScanThreads = 1024;
+constexpr int kScanThreads = 256;  // the unit scan: one small CTA, kScanPer windows per thread
 // Buckets: the first P codes and min(len, P); their dense numbers need
 // kDigitBits bits (5,592,405 valid pairs for 11 two-bit codes, 1,118,481 for
 // 5 four-bit codes).  Two long suffixes share a bucket iff their keys agree
@@ -313,12 +313,16 @@ __global__ void __launch_bounds__(kThreads) sa_unit_begin_kernel(const uint32_t*
 }
 
 // kScanPer consecutive windows of one field (vector accesses when whole)
-constexpr int kScanPer = 8;
+constexpr int kScanPer = 16;
+static_assert(kScanPer % 4 == 0, "whole 16-byte vectors");
 __device__ __forceinline__ void load_run(const uint32_t* p, uint32_t w0, uint32_t nwin, uint32_t fill,
                                          uint32_t (&v)[kScanPer]) {
     if (w0 + kScanPer <= nwin) {
-        const uint4 a = *reinterpret_cast<const uint4*>(p + w0), b = *reinterpret_cast<const uint4*>(p + w0 + 4);
-        v[0] = a.x, v[1] = a.y, v[2] = a.z, v[3] = a.w, v[4] = b.x, v[5] = b.y, v[6] = b.z, v[7] = b.w;
+#pragma unroll
+        for (int q = 0; q < kScanPer; q += 4) {
+            const uint4 a = *reinterpret_cast<const uint4*>(p + w0 + q);
+            v[q] = a.x, v[q + 1] = a.y, v[q + 2] = a.z, v[q + 3] = a.w;
+        }
     } else {
 #pragma unroll
         for (int q = 0; q < kScanPer; ++q) v[q] = w0 + q < nwin ? p[w0 + q] : fill;
@@ -326,8 +330,9 @@ __device__ __forceinline__ void load_run(const uint32_t* p, uint32_t w0, uint32_
 }
 __device__ __forceinline__ void store_run(uint32_t* p, uint32_t w0, uint32_t nwin, const uint32_t (&v)[kScanPer]) {
     if (w0 + kScanPer <= nwin) {
-        *reinterpret_cast<uint4*>(p + w0) = make_uint4(v[0], v[1], v[2], v[3]);
-        *reinterpret_cast<uint4*>(p + w0 + 4) = make_uint4(v[4], v[5], v[6], v[7]);
+#pragma unroll
+        for (int q = 0; q < kScanPer; q += 4)
+            *reinterpret_cast<uint4*>(p + w0 + q) = make_uint4(v[q], v[q + 1], v[q + 2], v[q + 3]);
     } else {
 #pragma unroll
         for (int q = 0; q < kScanPer; ++q)
