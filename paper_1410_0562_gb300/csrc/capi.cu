@@ -291,7 +291,8 @@ std::vector<Need> buffer_needs(sbwt_index* idx, const Plan& p, bool host_input, 
     const int cb = idx->code_bits;
     const uint64_t nsb = dict_supers_of(n_final, cb);
     // superblock totals, then the superblock scan's per-256 totals (insert.cu)
-    v.push_back({&idx->sb_tot, (size_t)(((nsb * dict_codes(cb) + 3) & ~3ull) * 4 + (nsb / 256 + 1) * 8 * dict_codes(cb))});
+    const size_t sb_words = (size_t)((nsb * dict_codes(cb) + 3) & ~3ull);
+    v.push_back({&idx->sb_tot, sb_words * 4 + (size_t)(nsb / 256 + 1) * 8 * dict_codes(cb)});
     for (int k = 0; k < 3; ++k) {
         if (k == idx->cur) continue;
         v.push_back({&idx->dict[k].blocks, (size_t)dict_blocks(n_final) * dict_block_bytes(cb), true});

@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(kThreads) compute_ranks_kernel(const uint32_t*
                                                                  const unsigned long long* __restrict__ offsets,
                                                                  unsigned long long j_begin,
                                                                  unsigned long long nreads,
-                                                                 const typename DictLayout<kB>::Block* __restrict__ blocks,
+                                                                 const typename DictLayout<kB>::Block* blocks,
                                                                  const unsigned long long* __restrict__ super,
                                                                  const unsigned long long* __restrict__ d_C,
                                                                  unsigned long long n_ext,
@@ -335,9 +335,9 @@ uint32_t alpha4_of(const Alphabet16& alpha) {
 }
 
 template <class IdxT, int kB>
-void compute_ranks_w(Launcher& L, const uint32_t* text, const uint64_t* d_offsets, uint64_t j_begin, uint64_t nreads,
-                     double bytes, const void* blocks, const unsigned long long* super, const unsigned long long* d_C,
-                     uint64_t n_ext, uint64_t m_ext, IdxT* g, uint32_t* d_err) {
+void compute_ranks_launch(Launcher& L, const uint32_t* text, const uint64_t* d_offsets, uint64_t j_begin,
+                          uint64_t nreads, double bytes, const void* blocks, const unsigned long long* super,
+                          const unsigned long long* d_C, uint64_t n_ext, uint64_t m_ext, IdxT* g, uint32_t* d_err) {
     using Block = typename DictLayout<kB>::Block;
     const size_t stage = ((n_ext >> DictLayout<kB>::kSuperShift) + 1) * DictLayout<kB>::kCodes * sizeof(IdxT);
     auto* const kern = stage <= kSuperStageBytes ? compute_ranks_kernel<IdxT, true, kB>
@@ -367,9 +367,11 @@ void launch_compute_ranks(Launcher& L, const uint32_t* text, const uint64_t* d_o
     const double bytes = (double)(n_int - nreads) * (code_bits == 4 ? 64.0 : 32.0) + (double)n_int * sizeof(IdxT) +
                          n_int * code_bits / 8.0 + 16.0 * nreads;
     if (code_bits == 4) {
-        compute_ranks_w<IdxT, 4>(L, text, d_offsets, j_begin, nreads, bytes, blocks, super, d_C, n_ext, m_ext, g, d_err);
+        compute_ranks_launch<IdxT, 4>(L, text, d_offsets, j_begin, nreads, bytes, blocks, super, d_C, n_ext, m_ext, g,
+                                      d_err);
     } else {
-        compute_ranks_w<IdxT, 2>(L, text, d_offsets, j_begin, nreads, bytes, blocks, super, d_C, n_ext, m_ext, g, d_err);
+        compute_ranks_launch<IdxT, 2>(L, text, d_offsets, j_begin, nreads, bytes, blocks, super, d_C, n_ext, m_ext, g,
+                                      d_err);
     }
 }
 

@@ -202,7 +202,8 @@ template <int kB>
 __device__ __forceinline__ unsigned long long dict_rank(const typename DictLayout<kB>::Block* __restrict__ blocks,
                                                         const unsigned long long* __restrict__ super, uint32_t c,
                                                         unsigned long long i) {
-    return __ldg(super + (i >> DictLayout<kB>::kSuperShift) * DictLayout<kB>::kCodes + c) + DictLayout<kB>::in_super(blocks, c, i);
+    using D = DictLayout<kB>;
+    return __ldg(super + (i >> D::kSuperShift) * D::kCodes + c) + D::in_super(blocks, c, i);
 }
 
 // ---------------------------------------------------------------------------

@@ -226,8 +226,8 @@ __device__ __forceinline__ uint32_t bucket_digit_sigma(unsigned long long K, uin
 }
 
 // Element of block position t for the bucket split: its bucket digit (bits
-// 0..23, bit 31 the short flag) and min(len, kH0) (bits 24..28) in the low
-// word, t in the high word.  The sort orders by the low kDigitBits bits and
+// 0..23, bit 31 the short flag) and the key's length field (bits 24..28) in
+// the low word, t in the high word.  The sort orders by the low kDigitBits bits and
 // carries the rest.
 template <int kB>
 __global__ void __launch_bounds__(kThreads) sa_digit_keys_kernel(const uint32_t* __restrict__ text,
