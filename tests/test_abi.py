@@ -142,6 +142,30 @@ def test_load_checks_the_file_before_any_device_work(lib, tmp_path):
         assert e.value.code == sb.SBWT_EDEVICE
 
 
+def test_wide_alphabet_file_layout(lib, tmp_path):
+    """An index of 5 to 16 symbols is written as file version 2: the 88-byte
+    header (symbols 5.. after the first four), one 64-byte block, one
+    superblock and C[] of 16 counters each, the checksum."""
+    import struct
+    path = tmp_path / "wide.sbwt"
+    sb.SetBWT(b"ACGNT").save(path)  # never appended: no device work
+    data = path.read_bytes()
+    assert data[:8] == b"SBWTIDX1"
+    version, sigma = struct.unpack_from("<II", data, 8)
+    assert (version, sigma) == (2, 5)
+    assert data[16:20] == b"ACGN" and data[56:57] == b"T"
+    assert len(data) == 88 + 64 + 16 * 8 + 16 * 8 + 8
+    narrow = tmp_path / "narrow.sbwt"
+    sb.SetBWT(b"ACGT").save(narrow)
+    assert struct.unpack_from("<II", narrow.read_bytes(), 8) == (1, 4)
+    assert len(narrow.read_bytes()) == 88 + 32 + 4 * 8 + 4 * 8 + 8
+    import torch
+    if not torch.cuda.is_available():
+        with pytest.raises(sb.SbwtError) as e:  # the file checks pass; the device step fails
+            sb.SetBWT.load(path)
+        assert e.value.code == sb.SBWT_EDEVICE
+
+
 def test_save_rejects_null_path(lib):
     idx = sb.SetBWT(b"ACGT")
     assert lib.sbwt_save(idx.handle, None) == sb.SBWT_EINVAL
