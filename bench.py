@@ -37,6 +37,14 @@ import readgen  # noqa: E402
 
 METRIC = "BWT build Mbp/s"
 UNIT = "Mbp/s"
+# What bounds the kernels that can take the largest share, from their ncu
+# captures (profiles/): the HBM fraction alone understates how close they are.
+LIMITERS = {
+    "sa_local_sort": "instruction issue and shared-memory latency: 43% issue, 15% DRAM under ncu "
+                     "(profiles/sa_local_sort_short-1Mx100.md)",
+    "radix_downsweep": "shared-memory ranking and staging: 40% issue, 36% DRAM, 0.46 of the copy bandwidth "
+                       "alone under ncu (profiles/radix_downsweep_short-1Mx100.md)",
+}
 
 
 def parse():
@@ -472,6 +480,8 @@ def run_gb300(args):
                 "traffic": traffic,
                 "algorithmic_bytes_per_launch": dom["bytes"] / max(dom["launches"], 1),
                 "avg_launch_us": 1e3 * dom["ms"] / max(dom["launches"], 1)}
+    if dom["name"] in LIMITERS:
+        roofline["limiter"] = LIMITERS[dom["name"]]
     kernels = {s["name"]: {"launches": s["launches"], "ms_per_step": s["ms"],
                            "GBps": (s["bytes"] / (s["ms"] / 1e3) / 1e9) if s["ms"] > 0 else None}
                for s in sorted(breakdown, key=lambda s: -s["ms"])}
