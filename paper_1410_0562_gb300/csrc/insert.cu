@@ -9,7 +9,9 @@
 // keep their relative order.
 //
 // One CTA builds one superblock (1024 occurrence blocks of 64 rows), four
-// consecutive blocks per thread.  For output block b (rows [o, o+64)) a binary
+// consecutive blocks per thread (or one per thread, 1024 threads, when the
+// new rows are at least a quarter of the result: the splicing then needs the
+// parallelism more than the binary searches need sharing).  For output block b (rows [o, o+64)) a binary
 // search finds i0 = |{i : g_sa[i] + i < o}|; the block then holds the old rows
 // starting at o - i0, into which the new symbols with final rows in [o, o+64)
 // are spliced in ascending order.  Per-block counts are scanned across the
@@ -22,8 +24,6 @@ namespace sbwt {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kPerThread = kBlocksPerSuper / kThreads;  // 4
-static_assert(kPerThread == 4, "four output blocks per thread");
 
 struct Window {
     unsigned long long w0, w1, dm;
@@ -78,14 +78,18 @@ __device__ __forceinline__ void splice(Window& w, uint32_t p, uint32_t code, uin
     w.dm = (w.dm & keepd) | ((unsigned long long)dollar << p) | ((w.dm & ~keepd) << 1);
 }
 
-template <class IdxT>
-__global__ void __launch_bounds__(kThreads) insert_kernel(const OccBlock* __restrict__ old_blocks,
+// kPer output blocks per thread (kBlocksPerSuper / kPer threads): 4 for a
+// block of sparse new rows (one binary search serves four blocks), 1 when
+// new rows are dense (four times the threads for the splicing).
+template <class IdxT, int kPer>
+__global__ void __launch_bounds__(kBlocksPerSuper / kPer) insert_kernel(const OccBlock* __restrict__ old_blocks,
                                                           unsigned long long n_ext, const uint8_t* __restrict__ bint,
                                                           const IdxT* __restrict__ gsa, unsigned long long n_int,
                                                           OccBlock* __restrict__ new_blocks,
                                                           unsigned long long n_new, uint32_t* __restrict__ sb_tot) {
     const uint64_t nb_new = (n_new >> kOccShift) + 1;
     const uint64_t nb_old = (n_ext >> kOccShift) + 1;
+    constexpr int kPerThread = kPer, kT = kBlocksPerSuper / kPer;
     const uint64_t b0 = (uint64_t)blockIdx.x * kBlocksPerSuper + (uint64_t)threadIdx.x * kPerThread;
     Window win[kPerThread];
     uint32_t cnt[kPerThread][4];
@@ -139,8 +143,8 @@ __global__ void __launch_bounds__(kThreads) insert_kernel(const OccBlock* __rest
         t23 += (unsigned long long)cnt[bb][2] | ((unsigned long long)cnt[bb][3] << 32);
     }
     unsigned long long tot01, tot23;
-    const unsigned long long e01 = cta_exclusive_scan<SumOp, kThreads>(t01, tot01);
-    const unsigned long long e23 = cta_exclusive_scan<SumOp, kThreads>(t23, tot23);
+    const unsigned long long e01 = cta_exclusive_scan<SumOp, kT>(t01, tot01);
+    const unsigned long long e23 = cta_exclusive_scan<SumOp, kT>(t23, tot23);
     uint32_t pref[4] = {(uint32_t)e01, (uint32_t)(e01 >> 32), (uint32_t)e23, (uint32_t)(e23 >> 32)};
 #pragma unroll
     for (int bb = 0; bb < kPerThread; ++bb) {
@@ -471,7 +475,10 @@ void launch_insert(Launcher& L, const void* old_blocks, uint64_t n_ext, const ui
     }
     const uint64_t nsb = dict_supers(n_new);
     const double bytes = 32.0 * dict_blocks(n_ext) + (1.0 + sizeof(IdxT)) * n_int + 32.0 * dict_blocks(n_new);
-    SBWT_LAUNCH(L, "insert_merge", bytes, 0, nullptr, insert_kernel<IdxT>, (unsigned)nsb, kThreads, 0,
+    // dense new rows (at least a quarter of the result): one block per thread
+    const bool dense = 4 * n_int >= n_new;
+    auto* const kern = dense ? insert_kernel<IdxT, 1> : insert_kernel<IdxT, 4>;
+    SBWT_LAUNCH(L, "insert_merge", bytes, 0, nullptr, kern, (unsigned)nsb, dense ? kBlocksPerSuper : kThreads, 0,
                 static_cast<const OccBlock*>(old_blocks), (unsigned long long)n_ext, bint, gsa,
                 (unsigned long long)n_int, static_cast<OccBlock*>(new_blocks), (unsigned long long)n_new, sb_tot);
     super_scan<4>(L, sb_tot, nsb, new_super, new_C, m_new, chunk_tot);
