@@ -11,8 +11,9 @@
 // One CTA builds one superblock (1024 occurrence blocks of 64 rows), four
 // consecutive blocks per thread (or one per thread, 1024 threads, when the
 // new rows are at least a quarter of the result: the splicing then needs the
-// parallelism more than the binary searches need sharing).  For output block b (rows [o, o+64)) a binary
-// search finds i0 = |{i : g_sa[i] + i < o}|; the block then holds the old rows
+// parallelism more than the binary searches need sharing).  For output
+// block b (rows [o, o+64)) a binary search finds i0 = |{i : g_sa[i] + i <
+// o}|; the block then holds the old rows
 // starting at o - i0, into which the new symbols with final rows in [o, o+64)
 // are spliced in ascending order.  Per-block counts are scanned across the
 // CTA for the 16-bit block counters; a one-CTA pass scans the superblock
