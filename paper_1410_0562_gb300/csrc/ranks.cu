@@ -163,51 +163,58 @@ __global__ void __launch_bounds__(kThreads) bint_gather_kernel(const uint32_t* _
     gsa[i] = g[t];
 }
 
-__global__ void __launch_bounds__(kThreads) rank_batch_kernel(const OccBlock* __restrict__ blocks,
+// rank(c, k) queries, codes 0..kCodes-1, or kCodes for the terminator.
+template <int kB>
+__global__ void __launch_bounds__(kThreads) rank_batch_kernel(const typename DictLayout<kB>::Block* blocks,
                                                               const unsigned long long* __restrict__ super,
                                                               const uint8_t* __restrict__ codes,
                                                               const unsigned long long* __restrict__ ks,
                                                               unsigned long long q,
                                                               unsigned long long* __restrict__ out) {
+    constexpr uint32_t kCodes = DictLayout<kB>::kCodes;
     const uint64_t i = (uint64_t)blockIdx.x * kThreads + threadIdx.x;
     if (i >= q) return;
     const uint32_t c = codes[i];
     const unsigned long long k = ks[i];
-    if (c < 4) {
-        out[i] = occ_rank(blocks, super, c, k);
+    if (c < kCodes) {
+        out[i] = dict_rank<kB>(blocks, super, c, k);
     } else {  // terminators: every row before k that holds no symbol
         unsigned long long s = 0;
-        for (uint32_t x = 0; x < 4; ++x) s += occ_rank(blocks, super, x, k);
+        for (uint32_t x = 0; x < kCodes; ++x) s += dict_rank<kB>(blocks, super, x, k);
         out[i] = k - s;
     }
 }
 
 // FM-index backward search (Lemma 1 applied to a pattern instead of a new
 // read): the rows of the suffixes that start with P[k..] are [lo, hi); one
-// step per symbol, right to left, from [0, n).  hi - lo counts P.
-__global__ void __launch_bounds__(kThreads) count_kernel(const OccBlock* __restrict__ blocks,
+// step per symbol, right to left, from [0, n).  hi - lo counts P.  A byte
+// outside the alphabet (code table in shared memory) counts zero.
+template <int kB>
+__global__ void __launch_bounds__(kThreads) count_kernel(const typename DictLayout<kB>::Block* blocks,
                                                          const unsigned long long* __restrict__ super,
                                                          const unsigned long long* __restrict__ d_C,
-                                                         unsigned long long n, uint32_t alpha4, int sigma,
+                                                         unsigned long long n, Alphabet16 alpha, int sigma,
                                                          const uint8_t* __restrict__ pats,
                                                          const unsigned long long* __restrict__ offs,
                                                          unsigned long long q, unsigned long long* __restrict__ out) {
+    constexpr uint32_t kNot = 0xFFu;
+    __shared__ uint8_t code_of[256];
+    code_of[threadIdx.x] = kNot;
+    __syncthreads();
+    if ((int)threadIdx.x < sigma) code_of[alpha.a[threadIdx.x]] = (uint8_t)threadIdx.x;
+    __syncthreads();
     const uint64_t i = (uint64_t)blockIdx.x * kThreads + threadIdx.x;
     if (i >= q) return;
-    const unsigned long long C0 = d_C[0], C1 = d_C[1], C2 = d_C[2], C3 = d_C[3];
     unsigned long long lo = 0, hi = n;
     for (uint64_t k = offs[i + 1]; k > offs[i] && lo < hi; --k) {
-        const uint32_t b = pats[k - 1];
-        uint32_t c = 4;
-        for (int a = 0; a < sigma; ++a)
-            if (b == ((alpha4 >> (8 * a)) & 0xFFu)) c = (uint32_t)a;
-        if (c == 4) {  // not in the alphabet: no occurrence
+        const uint32_t c = code_of[pats[k - 1]];
+        if (c == kNot) {  // not in the alphabet: no occurrence
             lo = hi = 0;
             break;
         }
-        const unsigned long long Cc = c == 0 ? C0 : c == 1 ? C1 : c == 2 ? C2 : C3;
-        lo = Cc + occ_rank(blocks, super, c, lo);
-        hi = Cc + occ_rank(blocks, super, c, hi);
+        const unsigned long long Cc = __ldg(d_C + c);
+        lo = Cc + dict_rank<kB>(blocks, super, c, lo);
+        hi = Cc + dict_rank<kB>(blocks, super, c, hi);
     }
     out[i] = hi > lo ? hi - lo : 0ull;
 }
@@ -245,54 +252,7 @@ __global__ void __launch_bounds__(kThreads) unpack_kernel(const OccBlock* __rest
     }
 }
 
-// The queries and the read-back for the 4-bit dictionary (5 to 16 symbols).
-__global__ void __launch_bounds__(kThreads) rank_batch_w_kernel(const OccBlockW* __restrict__ blocks,
-                                                                const unsigned long long* __restrict__ super,
-                                                                const uint8_t* __restrict__ codes,
-                                                                const unsigned long long* __restrict__ ks,
-                                                                unsigned long long q,
-                                                                unsigned long long* __restrict__ out) {
-    const uint64_t i = (uint64_t)blockIdx.x * kThreads + threadIdx.x;
-    if (i >= q) return;
-    const uint32_t c = codes[i];
-    const unsigned long long k = ks[i];
-    if (c < kSigmaW) {
-        out[i] = dict_rank<4>(blocks, super, c, k);
-    } else {  // terminators: every row before k that holds no symbol
-        unsigned long long s = 0;
-        for (uint32_t x = 0; x < kSigmaW; ++x) s += dict_rank<4>(blocks, super, x, k);
-        out[i] = k - s;
-    }
-}
-
-__global__ void __launch_bounds__(kThreads) count_w_kernel(const OccBlockW* __restrict__ blocks,
-                                                           const unsigned long long* __restrict__ super,
-                                                           const unsigned long long* __restrict__ d_C,
-                                                           unsigned long long n, Alphabet16 alpha, int sigma,
-                                                           const uint8_t* __restrict__ pats,
-                                                           const unsigned long long* __restrict__ offs,
-                                                           unsigned long long q, unsigned long long* __restrict__ out) {
-    __shared__ uint8_t code_of[256];  // byte -> code, kSigmaW when not in the alphabet
-    code_of[threadIdx.x] = kSigmaW;
-    __syncthreads();
-    if ((int)threadIdx.x < sigma) code_of[alpha.a[threadIdx.x]] = (uint8_t)threadIdx.x;
-    __syncthreads();
-    const uint64_t i = (uint64_t)blockIdx.x * kThreads + threadIdx.x;
-    if (i >= q) return;
-    unsigned long long lo = 0, hi = n;
-    for (uint64_t k = offs[i + 1]; k > offs[i] && lo < hi; --k) {
-        const uint32_t c = code_of[pats[k - 1]];
-        if (c == kSigmaW) {  // not in the alphabet: no occurrence
-            lo = hi = 0;
-            break;
-        }
-        const unsigned long long Cc = __ldg(d_C + c);
-        lo = Cc + dict_rank<4>(blocks, super, c, lo);
-        hi = Cc + dict_rank<4>(blocks, super, c, hi);
-    }
-    out[i] = hi > lo ? hi - lo : 0ull;
-}
-
+// The read-back for the 4-bit dictionary (5 to 16 symbols).
 __global__ void __launch_bounds__(kThreads) unpack_w_kernel(const OccBlockW* __restrict__ blocks,
                                                             unsigned long long r0, unsigned long long r1,
                                                             Alphabet16 alpha, uint8_t* __restrict__ out) {
@@ -390,11 +350,11 @@ void launch_rank_batch(Launcher& L, const void* blocks, const unsigned long long
                        const unsigned long long* ks, uint64_t q, unsigned long long* out, int code_bits) {
     if (q == 0) return;
     if (code_bits == 4) {
-        SBWT_LAUNCH(L, "rank_query", (double)q * (1 + 8 + 64 + 8 + 8), 0, nullptr, rank_batch_w_kernel,
+        SBWT_LAUNCH(L, "rank_query", (double)q * (1 + 8 + 64 + 8 + 8), 0, nullptr, rank_batch_kernel<4>,
                     ceil_div_u(q, kThreads), kThreads, 0, static_cast<const OccBlockW*>(blocks), super, codes, ks,
                     (unsigned long long)q, out);
     } else {
-        SBWT_LAUNCH(L, "rank_query", (double)q * (1 + 8 + 32 + 8 + 8), 0, nullptr, rank_batch_kernel,
+        SBWT_LAUNCH(L, "rank_query", (double)q * (1 + 8 + 32 + 8 + 8), 0, nullptr, rank_batch_kernel<2>,
                     ceil_div_u(q, kThreads), kThreads, 0, static_cast<const OccBlock*>(blocks), super, codes, ks,
                     (unsigned long long)q, out);
     }
@@ -405,15 +365,15 @@ void launch_count(Launcher& L, const void* blocks, const unsigned long long* sup
                   uint64_t q, uint64_t total_len, unsigned long long* out, int code_bits) {
     if (q == 0) return;
     if (code_bits == 4) {
-        SBWT_LAUNCH(L, "count_query", (double)total_len * (1 + 2 * 72) + 16.0 * q, 0, nullptr, count_w_kernel,
+        SBWT_LAUNCH(L, "count_query", (double)total_len * (1 + 2 * 72) + 16.0 * q, 0, nullptr, count_kernel<4>,
                     ceil_div_u(q, kThreads), kThreads, 0, static_cast<const OccBlockW*>(blocks), super, d_C,
                     (unsigned long long)n, alpha, sigma, pats, reinterpret_cast<const unsigned long long*>(offs),
                     (unsigned long long)q, out);
     } else {
-        SBWT_LAUNCH(L, "count_query", (double)total_len * (1 + 2 * 40) + 16.0 * q, 0, nullptr, count_kernel,
+        SBWT_LAUNCH(L, "count_query", (double)total_len * (1 + 2 * 40) + 16.0 * q, 0, nullptr, count_kernel<2>,
                     ceil_div_u(q, kThreads), kThreads, 0, static_cast<const OccBlock*>(blocks), super, d_C,
-                    (unsigned long long)n, alpha4_of(alpha), sigma, pats,
-                    reinterpret_cast<const unsigned long long*>(offs), (unsigned long long)q, out);
+                    (unsigned long long)n, alpha, sigma, pats, reinterpret_cast<const unsigned long long*>(offs),
+                    (unsigned long long)q, out);
     }
 }
 

@@ -100,13 +100,6 @@ __device__ __forceinline__ unsigned long long occ_rank_in_super(const OccBlock* 
     return ((uint32_t)(d.y >> (16 * c)) & 0xFFFFu) + in_block;
 }
 
-// rank(c, i, B) for a symbol code c (Eq. 2): superblock counter + the above.
-__device__ __forceinline__ unsigned long long occ_rank(const OccBlock* __restrict__ blocks,
-                                                       const unsigned long long* __restrict__ super,
-                                                       uint32_t c, unsigned long long i) {
-    return __ldg(super + ((i >> kSuperShift) << 2) + c) + occ_rank_in_super(blocks, c, i);
-}
-
 // ---------------------------------------------------------------------------
 // The dictionary for 4-bit codes (alphabets of 5 to 16 symbols), one 64-byte
 // block per 64 rows:
