@@ -1,0 +1,92 @@
+"""The host side of the benchmark, without a GPU: the whole-job throughput
+formula, the traffic record's scaling and staleness check, the clock-sample
+summary, and the reference arm (the oracle timed on the host) printing one
+JSON line with the contract's keys."""
+import argparse
+import io
+import json
+import os
+import shutil
+from contextlib import redirect_stdout
+
+import pytest
+
+import bench
+
+
+def test_whole_job_throughput_is_all_ranks_bases_over_the_slowest_time():
+    # 100 Mbp per rank, 2 ranks, 5 steps in 1 s: 1000 Mbp/s
+    assert bench.whole_job_mbps(100_000_000, 2, 5, 1000.0) == pytest.approx(1000.0)
+    assert bench.max_over_ranks(3.5) == 3.5
+
+
+def test_traffic_scales_by_units_and_names_its_kernel():
+    with open(os.path.join(bench.ROOT, "profiles", "ncu_traffic.json")) as f:
+        rec = json.load(f)
+    alg = 16.0 * 1_000_000  # a launch over 1M units
+    t = bench.load_traffic(rec["kernel"], alg)
+    if t is not None:
+        assert t == pytest.approx(alg / rec["algorithmic_bytes_per_unit"] * rec["dram_bytes_per_unit"])
+    assert bench.load_traffic("some_other_kernel", alg) is None
+
+
+def test_traffic_is_null_once_the_kernel_source_changes(tmp_path, monkeypatch):
+    with open(os.path.join(bench.ROOT, "profiles", "ncu_traffic.json")) as f:
+        rec = json.load(f)
+    (tmp_path / "profiles").mkdir()
+    csrc = tmp_path / "paper_1410_0562_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    shutil.copy(os.path.join(bench.ROOT, "profiles", "ncu_traffic.json"), tmp_path / "profiles")
+    for name in rec["source_files"]:
+        shutil.copy(os.path.join(bench.ROOT, "paper_1410_0562_gb300", "csrc", name), csrc / name)
+    in_tree = bench.load_traffic(rec["kernel"], 16.0)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.load_traffic(rec["kernel"], 16.0) == in_tree  # an unedited copy reads as the tree does
+    with open(csrc / rec["source_files"][0], "a") as f:
+        f.write("\n// edited\n")
+    assert bench.load_traffic(rec["kernel"], 16.0) is None
+
+
+def test_clock_summary_reads_median_max_and_active_reasons(tmp_path):
+    c = bench.Clocks(0)
+    c.path = str(tmp_path / "clocks.csv")
+    with open(c.path, "w") as f:
+        f.write("1965, 2070, Not Active, Not Active, Not Active, Not Active\n")
+        f.write("1980, 2070, Not Active, Not Active, Not Active, Active\n")
+        f.write("[N/A], 2070, Not Active, Not Active, Not Active, Not Active\n")
+        f.write("2010, 2070, Not Active, Not Active, Not Active, Not Active\n")
+        f.write("short line\n")
+    c.proc = object()  # as if nvidia-smi had been started
+    s = c.summary()
+    assert s == {"sm_mhz": 1980.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    c.proc = None
+    assert c.summary() is None
+
+
+def test_reference_arm_prints_one_contract_line():
+    args = argparse.Namespace(impl="reference", gpus=1, steps=1, warmup=0, workload="tiny")
+    buf = io.StringIO()
+    with redirect_stdout(buf):
+        assert bench.run_reference(args) == 0
+    lines = [ln for ln in buf.getvalue().splitlines() if ln.strip()]
+    assert len(lines) == 1
+    line = json.loads(lines[0])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in line
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC and line["unit"] == bench.UNIT
+    assert line["value"] > 0 and line["higher_is_better"] is True and line["vs_baseline"] is None
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+    assert line["e2e"] == {"value": line["value"], "unit": bench.UNIT, "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
+    assert line["config"]["workload"].startswith("tiny-1000x100")
+
+
+def test_reference_arm_is_silent_on_other_ranks(monkeypatch):
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    args = argparse.Namespace(impl="reference", gpus=2, steps=1, warmup=0, workload="tiny")
+    buf = io.StringIO()
+    with redirect_stdout(buf):
+        assert bench.run_reference(args) == 0
+    assert buf.getvalue() == ""
