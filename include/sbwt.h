@@ -80,8 +80,8 @@ typedef struct {
     uint32_t reserved[7];    /* must be zero */
 } sbwt_options;
 
-/* Creates an empty index over `alphabet` (a NUL-terminated string of 1..4
- * bytes in strictly increasing order).  hbm_budget_bytes caps the device
+/* Creates an empty index over `alphabet` (a NUL-terminated string of 1..16
+ * bytes in strictly increasing order, see the conventions).  hbm_budget_bytes caps the device
  * memory the index may hold, its working buffers included (0 = no cap beyond
  * the device's free memory).  Device state is created lazily by the first
  * call that needs the GPU, so this call does not touch the GPU.
@@ -102,17 +102,19 @@ int sbwt_create_ex(const char *alphabet, size_t hbm_budget_bytes, const sbwt_opt
 int sbwt_append(sbwt_index *idx, const uint8_t *reads, const uint64_t *offsets, uint64_t m);
 /* Like sbwt_append, but the m reads go BEFORE every read already in the
  * index: they take ids 0 .. m-1 (in the given order) and the old reads'
- * ids move up by m.  This is the reverse order Section 2 allows ("reversal
- * is also possible"): Algorithm 1 runs over the new blocks from the last to
- * the first, and Algorithm 2 starts every new read at i := 0, since a new
+ * ids move up by m.  Section 2 notes that the order of insertion can be
+ * reversed; this is that order: Algorithm 1 runs over the new blocks from
+ * the last to the first, and Algorithm 2 starts every new read at i := 0, since a new
  * terminator is smaller than every old one.  The result equals one append
  * of (new reads ++ old reads).  Same arguments, conventions and errors as
  * sbwt_append. */
 int sbwt_prepend(sbwt_index *idx, const uint8_t *reads, const uint64_t *offsets, uint64_t m);
 
 /* As sbwt_append, but `d_reads` (offsets[m] bytes) and `d_offsets` (m+1
- * values) are DEVICE pointers on the index's GPU.  The offsets are copied to
- * the host once to plan the blocks.  Blocks until done. */
+ * values) are DEVICE pointers on the index's GPU.  The offsets are checked
+ * and the blocks planned on the device; only the block table comes back to
+ * the host (the offsets themselves only for an append of more blocks than
+ * that table holds).  Blocks until done. */
 int sbwt_append_device(sbwt_index *idx, const uint8_t *d_reads, const uint64_t *d_offsets, uint64_t m);
 
 /* Writes B (n bytes, see conventions) into host buffer `out` of `cap` bytes

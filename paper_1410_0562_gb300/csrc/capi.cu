@@ -360,7 +360,7 @@ int move_dicts_to_host(sbwt_index* idx) {
 
 // Budget check first (nothing changes on failure), then growth.  When the
 // HBM budget cannot hold the dictionaries, they move to pinned host memory
-// (B_ext "in system memory", Section 5) and only the working set stays in HBM.
+// (Section 5 keeps B_ext in system memory) and only the working set stays in HBM.
 int reserve(sbwt_index* idx, const std::vector<Need>& needs) {
     bool dict_host = idx->dict_host || idx->host_tier_forced;
     if (idx->budget && hbm_after(idx, needs, dict_host) > idx->budget) {
