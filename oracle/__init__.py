@@ -104,19 +104,13 @@ def _declare(lib):
     return lib
 
 
-def use_library(path: str):
-    """Point this module at another build of oracle.c (a planted-mistake
-    build in the tests); ``use_library(None)`` goes back to the normal one."""
-    global _lib
-    with _lock:
-        _lib = _declare(ctypes.CDLL(path)) if path else None
-
-
 def _load():
     global _lib
     with _lock:
         if _lib is None:
-            lib = ctypes.CDLL(build())
+            # ORACLE_LIBRARY names another build of oracle.c (the planted-
+            # mistake builds, in the tests that run the pins against them)
+            lib = ctypes.CDLL(os.environ.get("ORACLE_LIBRARY") or build())
             _declare(lib)
             _lib = lib
     return _lib

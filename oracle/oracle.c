@@ -78,7 +78,15 @@
  *   3: a shorter suffix sorts after a longer one with the same prefix
  *   4: Insert puts new symbols after the old row g_sa (tie order flipped)
  *   5: C[c] leaves out the terminators
- *   6: the reverse order starts Algorithm 2 at i := m_ext, not 0            */
+ *   6: the reverse order starts Algorithm 2 at i := m_ext, not 0
+ *   7: counting skips overlapping occurrences
+ *   8: the sampled inversion takes each checkpoint after its own row
+ *   9: the row of a suffix counts the suffix itself
+ *  10: rank(c, k) counts rows 0..k instead of 0..k-1
+ *  11: Lemma 1's C[] only covers the first four symbols
+ *  12: the direct g leaves out the last old read
+ *  13: B_int holds '$' for a read's terminator suffix
+ *  14: the full LF inversion's C[] leaves out the terminators             */
 #ifndef ORACLE_PLANT
 #define ORACLE_PLANT 0
 #endif
@@ -196,7 +204,11 @@ int oracle_bwt(const uint8_t *reads, const uint64_t *offsets, uint64_t m,
 uint64_t oracle_rank(const uint8_t *B, uint64_t n, uint8_t c, uint64_t k) {
     uint64_t cnt = 0;
     if (k > n) k = n;
+#if ORACLE_PLANT == 10
+    for (uint64_t i = 0; i <= k && i < n; ++i) cnt += B[i] == c;
+#else
     for (uint64_t i = 0; i < k; ++i) cnt += B[i] == c;
+#endif
     return cnt;
 }
 
@@ -242,7 +254,11 @@ int oracle_block_bint(const uint8_t *reads, const uint64_t *offsets, uint64_t j0
     g_offsets = offsets;
     for (uint64_t i = 0; i < n_int; ++i) {
         suffix_t s = locate(j0, j1, sa[i]);
+#if ORACLE_PLANT == 13
+        bint[i] = s.p == read_len(s.r) ? (uint8_t)'$' : preceding_symbol(&s);
+#else
         bint[i] = preceding_symbol(&s);
+#endif
     }
     return ORACLE_OK;
 }
@@ -255,7 +271,11 @@ int oracle_block_g_direct(const uint8_t *reads, const uint64_t *offsets,
     g_reads = reads;
     g_offsets = offsets;
     uint64_t n_old, n_new;
+#if ORACLE_PLANT == 12
+    suffix_t *old = enumerate_suffixes(0, j0 ? j0 - 1 : 0, &n_old);
+#else
     suffix_t *old = enumerate_suffixes(0, j0, &n_old);
+#endif
     suffix_t *neu = enumerate_suffixes(j0, j1, &n_new);
     if (!old || !neu) {
         free(old);
@@ -311,7 +331,11 @@ static int block_g_lemma1(const uint8_t *B_ext, uint64_t n_ext,
             occ[(k + 1) * (sigma + 1) + y] = occ[k * (sigma + 1) + y] + (x == y);
     }
     uint64_t C[17] = {0}; /* sigma + 1 <= 17 entries */
+#if ORACLE_PLANT == 11
+    for (int x = 1; x <= sigma && x <= 4; ++x) C[x] = C[x - 1] + occ[n_ext * (sigma + 1) + x - 1];
+#else
     for (int x = 1; x <= sigma; ++x) C[x] = C[x - 1] + occ[n_ext * (sigma + 1) + x - 1];
+#endif
     uint64_t m_ext = occ[n_ext * (sigma + 1) + 0];
 #if ORACLE_PLANT == 5
     for (int x = 1; x <= sigma; ++x) C[x] -= m_ext;
@@ -470,6 +494,9 @@ int oracle_lf_invert(const uint8_t *B, uint64_t n, uint64_t m,
     if (!rc && occ[n * (sigma + 1)] != m) rc = ORACLE_EINVAL;
     uint64_t C[17] = {0}; /* sigma + 1 <= 17 entries */
     for (int x = 1; x <= sigma && !rc; ++x) C[x] = C[x - 1] + occ[n * (sigma + 1) + x - 1];
+#if ORACLE_PLANT == 14
+    for (int x = 1; x <= sigma && !rc; ++x) C[x] -= m;
+#endif
     uint64_t w = 0;
     if (!rc) offsets_out[0] = 0;
     for (uint64_t r = 0; r < m && !rc; ++r) {
@@ -521,14 +548,20 @@ int oracle_lf_invert_sampled(const uint8_t *B, uint64_t n, uint64_t m, const uin
     int rc = ORACLE_OK;
     uint64_t tot[17] = {0};
     for (uint64_t k = 0; k < n && !rc; ++k) {
+#if ORACLE_PLANT != 8
         if (k % 64 == 0)
             for (int y = 0; y <= sigma; ++y) ck[(k / 64) * (sigma + 1) + y] = tot[y];
+#endif
         int x = bcode(B[k], alphabet, sigma);
         if (x < 0) rc = ORACLE_EINVAL;
         else {
             code[k] = (int8_t)x;
             ++tot[x];
         }
+#if ORACLE_PLANT == 8
+        if (k % 64 == 0)
+            for (int y = 0; y <= sigma; ++y) ck[(k / 64) * (sigma + 1) + y] = tot[y];
+#endif
     }
     if (!rc && n % 64 == 0)
         for (int y = 0; y <= sigma; ++y) ck[(n / 64) * (sigma + 1) + y] = tot[y];
@@ -580,8 +613,16 @@ uint64_t oracle_count(const uint8_t *reads, const uint64_t *offsets, uint64_t m,
     for (uint64_t r = 0; r < m; ++r) {
         const uint64_t L = offsets[r + 1] - offsets[r];
         if (len > L) continue;
+#if ORACLE_PLANT == 7
+        for (uint64_t p = 0; p + len <= L; ++p)
+            if (memcmp(reads + offsets[r] + p, P, len) == 0) {
+                ++cnt;
+                if (len) p += len - 1;
+            }
+#else
         for (uint64_t p = 0; p + len <= L; ++p)
             cnt += memcmp(reads + offsets[r] + p, P, len) == 0;
+#endif
     }
     return cnt;
 }
@@ -600,7 +641,11 @@ uint64_t oracle_row_of_suffix(const uint8_t *reads, const uint64_t *offsets,
     suffix_t y;
     for (y.r = 0; y.r < m; ++y.r)
         for (y.p = 0; y.p <= read_len(y.r); ++y.p)
+#if ORACLE_PLANT == 9
+            row += suffix_cmp(&y, &x) <= 0;
+#else
             row += suffix_cmp(&y, &x) < 0;
+#endif
     return row;
 }
 

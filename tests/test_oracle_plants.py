@@ -1,48 +1,43 @@
 """Each deliberate mistake planted in a copy of the oracle (ORACLE_PLANT in
-oracle/oracle.c) must make at least one pin fail: the pins are strong enough
-to catch a wrong start rank in Algorithm 2, reversed terminator order, a
-wrong length tie-break, a flipped Insert tie, a C[] without terminators and
-a reverse-order Algorithm 1 that starts Algorithm 2 at m_ext."""
-import numpy as np
+oracle/oracle.c) must make the oracle's pins fail.  The pins
+(tests/test_oracle.py and tests/test_oracle_properties.py) run in a child
+pytest against the planted build (ORACLE_LIBRARY); the build with no plant
+must pass the same run, so a failure means the mistake was caught.
+
+The plants cover every oracle function: Algorithm 2's start rank, the
+terminator order and the length tie-break of the suffix order, Insert's tie
+order, C[] without terminators, the reverse-order start rank, overlapping
+pattern counts, the checkpoints of the sampled LF inversion, the row of one
+suffix, rank's range, C[] for alphabets past four symbols, the direct g's
+set of old reads, B_int at a terminator suffix and the full inversion's
+C[]."""
+import os
+import subprocess
+import sys
+
 import pytest
 
-import brute
 import oracle
-from test_oracle import load_golden, pack, random_set
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+PINS = [os.path.join(HERE, "test_oracle.py"), os.path.join(HERE, "test_oracle_properties.py")]
+PLANTS = range(1, 15)
 
 
-def _pins_hold() -> bool:
-    try:
-        for alpha, reads, expect in load_golden():
-            if bytes(oracle.bwt(*pack(reads), alpha)) != expect:
-                return False
-        for seed in range(30):
-            rng = np.random.default_rng(seed)
-            reads = random_set(rng, int(rng.integers(1, 10)), 9)
-            data, off = pack(reads)
-            if bytes(oracle.bwt(data, off)) != brute.bwt(reads):
-                return False
-            m = len(reads)
-            if m > 1:
-                one = oracle.bwt(data, off)
-                if not np.array_equal(oracle.setbwte(data, off, list(range(m + 1))), one):
-                    return False
-                if not np.array_equal(oracle.setbwte(data, off, list(range(m + 1)), reverse=True), one):
-                    return False
-        return True
-    except oracle.OracleError:
-        return False
+def _run_pins(lib_path: str) -> subprocess.CompletedProcess:
+    env = dict(os.environ, ORACLE_LIBRARY=lib_path)
+    return subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", *PINS],
+                          cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
 
 
-@pytest.mark.parametrize("plant", [1, 2, 3, 4, 5, 6])
+def test_pins_pass_on_an_unplanted_build(tmp_path):
+    r = _run_pins(oracle.build_planted(0, str(tmp_path / "liboracle_plant0.so")))
+    assert r.returncode == 0, r.stdout[-2000:]
+
+
+@pytest.mark.parametrize("plant", PLANTS)
 def test_planted_mistake_is_caught(plant, tmp_path):
-    path = oracle.build_planted(plant, str(tmp_path / f"liboracle_plant{plant}.so"))
-    try:
-        oracle.use_library(path)
-        assert not _pins_hold(), f"planted mistake {plant} slipped through the pins"
-    finally:
-        oracle.use_library(None)
-
-
-def test_unplanted_oracle_passes_the_same_pins():
-    assert _pins_hold()
+    r = _run_pins(oracle.build_planted(plant, str(tmp_path / f"liboracle_plant{plant}.so")))
+    # exit code 1: tests ran and at least one failed (not a crash or a usage error)
+    assert r.returncode == 1, f"planted mistake {plant} slipped through the pins:\n{r.stdout[-2000:]}"
