@@ -109,6 +109,30 @@ def test_no_cpu_fallback_without_a_device(lib):
     sb.sbwt_destroy(h)
 
 
+def test_index_width_is_checked_on_the_host(lib):
+    """With 32-bit row indices an append that would reach 2^32 - 1 rows is
+    refused before any device work; with automatic width it passes that
+    check (and then needs the device).  The reads are three of 2^31 - 2
+    bases in lazily mapped zero pages that the refused call never reads."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present: the automatic-width append would run")
+    L = (1 << 31) - 2
+    reads = np.zeros(3 * L, np.uint8)
+    off = np.array([0, L, 2 * L, 3 * L], np.uint64)
+    h = sb.sbwt_create_ex(b"ACGT", index_bits=32)
+    with pytest.raises(sb.SbwtError) as e:
+        sb.sbwt_append(h, reads, off)
+    assert e.value.code == sb.SBWT_EINVAL
+    assert sb.sbwt_size(h) == (0, 0)
+    sb.sbwt_destroy(h)
+    h = sb.sbwt_create_ex(b"ACGT", index_bits=0)
+    with pytest.raises(sb.SbwtError) as e:
+        sb.sbwt_append(h, reads, off)
+    assert e.value.code == sb.SBWT_EDEVICE
+    sb.sbwt_destroy(h)
+
+
 def test_load_checks_the_file_before_any_device_work(lib, tmp_path):
     """Missing file -> SBWT_EIO; not an index file, a flipped byte or a
     truncated file -> SBWT_EINVAL; a valid file of an empty index reaches the
