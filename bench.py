@@ -40,8 +40,6 @@ UNIT = "Mbp/s"
 # What bounds the kernels that can take the largest share, from their ncu
 # captures (profiles/): the HBM fraction alone understates how close they are.
 LIMITERS = {
-    "sa_local_sort": "instruction issue and shared-memory latency: 43% issue, 15% DRAM under ncu "
-                     "(profiles/sa_local_sort_short-1Mx100.md)",
     "radix_downsweep": "shared-memory ranking and staging: 40% issue, 36% DRAM, 0.46 of the copy bandwidth "
                        "alone under ncu (profiles/radix_downsweep_short-1Mx100.md)",
 }

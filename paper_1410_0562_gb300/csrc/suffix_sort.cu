@@ -29,20 +29,22 @@
 //    w is every bucket that starts inside window w.  A unit holds whole
 //    buckets, so its rows are final as a set, and as long as its buckets are
 //    at most kWindow long it holds at most 2 kWindow = kLCap rows.
-// 3. Local sort.  One CTA per unit with at most kLCap long suffixes: it
-//    regenerates their keys from the packed text, sorts each bucket in
-//    shared memory by (key, t) (counting, for buckets of at most kSeg; a
-//    merge sort of the unit otherwise), and writes SA, rank and
-//    the unit's still-unsorted members (in row order, in place in the unit's
-//    own range of loc_act).  A unit with more long suffixes goes to the
-//    global path: its suffixes (with their rows) are gathered into one list
-//    that the device-wide radix sort orders by the full key.
+// 3. Local sort of every unit with at most kLCap long suffixes: each bucket
+//    is sorted by (key, t), and SA, rank and the unit's still-unsorted
+//    members (in row order, in place in the unit's own range of loc_act)
+//    are written.  One warp per unit does it in chunks of whole buckets of
+//    at most kWChunk rows, with no CTA barrier; a unit with a longer bucket
+//    is left to a CTA-batch kernel (counting for buckets of at most kSeg, a
+//    merge sort of the batch otherwise).  A unit with more long suffixes
+//    goes to the global path: its suffixes (with their rows) are gathered
+//    into one list that the device-wide radix sort orders by the full key.
 // 4. Round with offset h (29, 58, ...): each unsorted member t is re-sorted
 //    inside its group by rank[t + h]; t + h never leaves the read because an
 //    unsorted member has len >= h.  All next-ranks are read before any rank
 //    of the round is written (a separate gather launch).  Unit-local groups:
-//    one CTA sorts the unit's members by (rank[t], rank[t + h]); a
-//    group whose head row is H keeps rows H .. H + size - 1.  Groups from the
+//    the unit's members are sorted by (rank[t], rank[t + h]), by one warp
+//    when they fit one chunk, else in a CTA batch; a group whose head row is
+//    H keeps rows H .. H + size - 1.  Groups from the
 //    global path: one device-wide radix sort of all of them by the same pair,
 //    as one list, so the k-th sorted element goes to the k-th active row.
 //    Rounds continue until the resolved prefix exceeds the longest read of
@@ -62,14 +64,15 @@ constexpr int kGItems = 16;
 constexpr int kGTile = kThreads * kGItems;  // elements per group-kernel tile
 constexpr unsigned kMaxGroupChunks = 2048;
 
-// Local sorts: kLThreads x kLItems pairs per CTA, four CTAs per SM (small
-// CTAs keep more independent batches in flight between their barriers).
+// CTA-batch local sorts (the units the warp kernels leave): kLThreads x
+// kLItems pairs per CTA, four CTAs per SM.
 constexpr int kLThreads = 256;
 constexpr int kLItems = 8;
 constexpr uint32_t kLCap = kLThreads * kLItems;  // 2048 long suffixes per unit at most
 constexpr uint32_t kWindow = kLCap / 2;          // rows per window
 constexpr uint32_t kLSlots = kLCap + kLCap / kLItems;
 constexpr uint32_t kNone = 0xFFFFFFFFu;
+constexpr uint32_t kFallback = 0xFFFFFFFEu;  // u.cnt of a unit the warp local sort left to the CTA one
 constexpr uint32_t kShortFlag = 0x80000000u;  // digit flag: the bucket holds suffixes with len < P
 constexpr int kScanThreads = 256;  // the unit scan: one small CTA, kScanPer windows per thread
 // Buckets: the first P codes and min(len, P); their dense numbers need
@@ -732,15 +735,34 @@ __global__ void __launch_bounds__(kLThreads, 4) sa_local_sort_kernel(
     uint32_t* sseg = srow + kLSlots;
     __shared__ Batch b;
     __shared__ uint32_t run_start[kLThreads], run_src[kLThreads];
+    __shared__ uint32_t first_left;
 
     const uint32_t per = (nwin + gridDim.x - 1) / gridDim.x;
     const uint32_t wbeg = min(nwin, blockIdx.x * per), wend = min(nwin, wbeg + per);
     for (uint32_t w = wbeg; w < wend;) {
         const uint32_t x = w + threadIdx.x;
+        // only the units the warp kernel left here (u.cnt = kFallback) are
+        // sorted; every other unit ends a batch like a global-path unit
         uint32_t c = kLCap + 1, ub = kNone;
+        bool left = false;
         if (x < wend) {
             ub = u.beg[x];
-            c = ub == kNone ? 0u : (u.lofs[x] != kNone ? kLCap + 1 : u.nlong[x]);
+            left = ub != kNone && u.lofs[x] == kNone && u.cnt[x] == kFallback;
+            c = ub == kNone ? 0u : (left ? u.nlong[x] : kLCap + 1);
+        }
+        if (threadIdx.x == 0) first_left = kNone;
+        __syncthreads();
+        if (left) atomicMin(&first_left, x);
+        __syncthreads();
+        const uint32_t fl = first_left;
+        __syncthreads();  // read by every thread before thread 0 resets it
+        if (fl == kNone) {
+            w += kLThreads;
+            continue;
+        }
+        if (fl > w) {
+            w = fl;
+            continue;
         }
         uint32_t total;
         const uint32_t k = form_batch(b, c, ub, total);
@@ -844,6 +866,197 @@ __global__ void __launch_bounds__(kLThreads, 4) sa_local_sort_kernel(
     }
 }
 
+// Warp-per-unit local sort.  Each warp takes whole local units and sorts
+// their buckets in chunks of at most kWChunk long rows held in warp-private
+// shared memory, with no CTA barrier.  A chunk ends at a bucket start, so
+// its slots are exactly its sorted positions.  Inside a bucket an item's
+// place is the count of bucket members below it in (key, t) order; its
+// group head (equal unresolved keys) the count below it in key order; it
+// is an unsorted member when its key is unresolved (length field kH0) and
+// shared.  A unit with a bucket longer than one chunk, or with more list
+// runs than the run table holds, is marked kFallback in u.cnt and left to
+// sa_local_sort_kernel; what the warp wrote for it before giving up is
+// written again, identically, there.  The results are those of the CTA
+// kernel: SA, rank (the head's row), the unsorted members in sorted order
+// at loc_act[beg ..], the unit's count and the block total.
+constexpr int kWChunk = 256;
+constexpr int kWStripes = kWChunk / 32;
+constexpr int kWRuns = 32;
+constexpr int kWWarps = 8;
+
+struct WarpTile {
+    unsigned long long key[kWChunk];
+    uint32_t t[kWChunk];
+    uint32_t row[kWChunk];
+    uint32_t tpos[kWChunk];      // t of the suffix at each sorted position
+    uint32_t run_start[kWRuns];  // first unit slot of each list run
+    uint32_t run_src[kWRuns];    // list index of that slot
+    uint8_t act[kWChunk];        // the suffix at this sorted position is an unsorted member
+};
+
+// List index of unit slot g (runs in slot order, r the run of an earlier
+// slot of this lane or 0).
+__device__ __forceinline__ uint32_t warp_list_index(const WarpTile& T, uint32_t nruns, uint32_t g, uint32_t& r) {
+    while (r + 1 < nruns && T.run_start[r + 1] <= g) ++r;
+    return T.run_src[r] + (g - T.run_start[r]);
+}
+
+__global__ void __launch_bounds__(kWWarps * 32) sa_local_sort_warp_kernel(
+    uint32_t n, const uint32_t* __restrict__ ll_t, const uint32_t* __restrict__ ll_row,
+    const unsigned long long* __restrict__ ll_key, Units u, uint32_t nwin, uint32_t* __restrict__ sa,
+    uint32_t* __restrict__ rank, uint32_t* __restrict__ loc_act, uint32_t* __restrict__ d_cnt, int seg_shift) {
+    __shared__ WarpTile tiles[kWWarps];
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t below = (1u << lane) - 1u;
+    WarpTile& T = tiles[threadIdx.x >> 5];
+    const uint32_t warps = gridDim.x * kWWarps;
+    for (uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nwin; w += warps) {
+        const uint32_t beg = u.beg[w];
+        if (beg == kNone || u.lofs[w] != kNone) continue;
+        const uint32_t N = u.nlong[w];
+        if (N == 0) continue;
+        // the unit's list runs: window w from its unit start, then the
+        // windows up to the next unit start (their rows before it)
+        uint32_t nruns = 0, got = 0;
+        for (uint32_t x0 = w; x0 < nwin; x0 += 32) {
+            const uint32_t x = x0 + lane;
+            uint32_t avail = 0, k0 = 0;
+            bool stop = true;
+            if (x < nwin) {
+                if (x == w) {
+                    k0 = u.lcb[w];
+                    avail = u.lct[w] - k0;
+                    stop = false;
+                } else {
+                    stop = u.beg[x] != kNone;
+                    avail = stop ? u.lcb[x] : u.lct[x];
+                }
+            }
+            const uint32_t stops = __ballot_sync(0xffffffffu, stop);
+            const uint32_t first_stop = stops ? (uint32_t)__ffs(stops) - 1 : 32u;
+            if (lane > first_stop) avail = 0;
+            uint32_t inc = avail;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= (uint32_t)o) inc += y;
+            }
+            const uint32_t nonempty = __ballot_sync(0xffffffffu, avail > 0);
+            if (avail > 0) {
+                const uint32_t r = nruns + __popc(nonempty & below);
+                if (r < kWRuns) {
+                    T.run_start[r] = got + inc - avail;
+                    T.run_src[r] = x * kWindow + k0;
+                }
+            }
+            nruns += __popc(nonempty);
+            got += __shfl_sync(0xffffffffu, inc, 31);
+            if (first_stop < 32) break;
+        }
+        __syncwarp();
+        bool ok = nruns <= kWRuns && got == N;
+        uint32_t acnt = 0;  // unsorted members of the unit so far
+        for (uint32_t s = 0; ok && s < N;) {
+            const uint32_t c = min((uint32_t)kWChunk, N - s);
+            uint32_t r = 0;
+#pragma unroll
+            for (int j = 0; j < kWStripes; ++j) {
+                const uint32_t q = j * 32 + lane;
+                if (q < c) {
+                    const uint32_t src = warp_list_index(T, nruns, s + q, r);
+                    T.key[q] = ll_key[src];
+                    T.t[q] = ll_t[src];
+                    T.row[q] = ll_row[src];
+                }
+            }
+            unsigned long long next_key = 0;
+            const bool more = s + c < N;
+            if (more) {
+                uint32_t r2 = 0;
+                next_key = ll_key[warp_list_index(T, nruns, s + c, r2)];
+            }
+            __syncwarp();
+            // end the chunk at its last bucket start when its last bucket
+            // goes on past it
+            uint32_t cut = c;
+            if (more && (next_key >> seg_shift) == (T.key[c - 1] >> seg_shift)) {
+                uint32_t last = 0;
+#pragma unroll
+                for (int j = 0; j < kWStripes; ++j) {
+                    const uint32_t q = j * 32 + lane;
+                    if (q >= 1 && q < c && (T.key[q] >> seg_shift) != (T.key[q - 1] >> seg_shift)) last = q;
+                }
+                last = __reduce_max_sync(0xffffffffu, last);
+                if (last == 0) {  // one bucket fills the chunk
+                    ok = false;
+                    break;
+                }
+                cut = last;
+            }
+            uint32_t bs_carry = 0;
+#pragma unroll
+            for (int j = 0; j < kWStripes; ++j) {
+                const uint32_t q = j * 32 + lane;
+                const bool in = q < cut;
+                const unsigned long long K = in ? T.key[q] : 0ull;
+                const unsigned long long B = K >> seg_shift;
+                const bool head = in && (q == 0 || (T.key[q - 1] >> seg_shift) != B);
+                uint32_t bs = head ? q : 0u;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t y = __shfl_up_sync(0xffffffffu, bs, o);
+                    if (lane >= (uint32_t)o) bs = max(bs, y);
+                }
+                bs = max(bs, bs_carry);
+                bs_carry = __shfl_sync(0xffffffffu, bs, 31);
+                if (in) {
+                    const uint32_t t = T.t[q];
+                    uint32_t lt_pair = 0, lt_key = 0, eq = 0;
+                    for (uint32_t x = bs; x < cut; ++x) {
+                        const unsigned long long kx = T.key[x];
+                        if ((kx >> seg_shift) != B) break;
+                        const uint32_t tx = T.t[x];
+                        lt_key += kx < K;
+                        eq += kx == K;
+                        lt_pair += (kx < K || (kx == K && tx < t)) ? 1u : 0u;
+                    }
+                    const uint32_t p = bs + lt_pair;
+                    const bool unresolved = (uint32_t)(K & 31) >= kH0;
+                    const uint32_t hp = unresolved ? bs + lt_key : p;
+                    const uint32_t row = T.row[p];
+                    if (row < n && t < n) {
+                        sa[row] = t;
+                        rank[t] = T.row[hp];
+                    }
+                    T.tpos[p] = t;
+                    T.act[p] = (unresolved && eq >= 2) ? 1 : 0;
+                }
+            }
+            __syncwarp();
+            // the chunk's unsorted members, in sorted order
+#pragma unroll
+            for (int j = 0; j < kWStripes; ++j) {
+                const uint32_t q = j * 32 + lane;
+                const bool a = q < cut && T.act[q];
+                const uint32_t bal = __ballot_sync(0xffffffffu, a);
+                if (a) loc_act[beg + acnt + __popc(bal & below)] = T.tpos[q];
+                acnt += __popc(bal);
+            }
+            __syncwarp();
+            s += cut;
+        }
+        if (lane == 0) {
+            if (!ok) {
+                u.cnt[w] = kFallback;
+            } else {
+                u.cnt[w] = acnt;
+                if (acnt) atomicAdd(d_cnt, acnt);
+            }
+        }
+        __syncwarp();
+    }
+}
+
 // The global-path list: every row of a unit with more than kLCap long
 // suffixes, in row order, as (key, t, row).  One CTA per window; a window's
 // rows belong to its owner unit up to the window's own unit start.
@@ -907,15 +1120,35 @@ __global__ void __launch_bounds__(kLThreads, 4) sa_round_local_kernel(
     uint32_t* sval = reinterpret_cast<uint32_t*>(skey + kLSlots);
     uint32_t* sseg = sval + kLSlots;
     __shared__ Batch b;
+    __shared__ uint32_t first_left;
 
     const uint32_t per = (nwin + gridDim.x - 1) / gridDim.x;
     const uint32_t wbeg = min(nwin, blockIdx.x * per), wend = min(nwin, wbeg + per);
     for (uint32_t w = wbeg; w < wend;) {
         const uint32_t x = w + threadIdx.x;
+        // units of at most kWChunk members are the warp kernel's (it ran
+        // first; their counts only shrank); they end a batch
         uint32_t c = kLCap + 1, ub = kNone;
+        bool left = false;
         if (x < wend) {
             ub = u.beg[x];
-            c = (ub != kNone && u.lofs[x] == kNone) ? min(u.cnt[x], kLCap) : 0u;
+            const uint32_t cx = (ub != kNone && u.lofs[x] == kNone) ? u.cnt[x] : 0u;
+            left = cx > (uint32_t)kWChunk;
+            c = left ? min(cx, kLCap) : (cx ? kLCap + 1 : 0u);
+        }
+        if (threadIdx.x == 0) first_left = kNone;
+        __syncthreads();
+        if (left) atomicMin(&first_left, x);
+        __syncthreads();
+        const uint32_t fl = first_left;
+        __syncthreads();  // read by every thread before thread 0 resets it
+        if (fl == kNone) {
+            w += kLThreads;
+            continue;
+        }
+        if (fl > w) {
+            w = fl;
+            continue;
         }
         uint32_t total;
         const uint32_t k = form_batch(b, c, ub, total);
@@ -983,6 +1216,94 @@ __global__ void __launch_bounds__(kLThreads, 4) sa_round_local_kernel(
         }
         batch_write_unsorted(b, k, w, v, act, total, loc_act, u.cnt, d_cnt);
         w += k;
+    }
+}
+
+// One round for the local units of at most kWChunk unsorted members, one
+// warp per unit: the members and their keys (rank[t], rank[t + h]) are
+// loaded into the warp's tile before any rank of the unit changes; inside
+// an old group (equal rank[t], consecutive in the member list) a member's
+// place is the count below it in (key, t) order, its new group head the
+// count below it in key order.  Same results as sa_round_local_kernel,
+// which takes the larger units.
+__global__ void __launch_bounds__(kWWarps * 32) sa_round_local_warp_kernel(
+    uint32_t* __restrict__ loc_act, const uint32_t* __restrict__ loc_next, Units u, uint32_t nwin, uint32_t n,
+    uint32_t* __restrict__ rank, uint32_t* __restrict__ sa, uint32_t* __restrict__ d_cnt,
+    uint32_t* __restrict__ d_err) {
+    __shared__ WarpTile tiles[kWWarps];
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t below = (1u << lane) - 1u;
+    WarpTile& T = tiles[threadIdx.x >> 5];
+    const uint32_t warps = gridDim.x * kWWarps;
+    for (uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nwin; w += warps) {
+        const uint32_t beg = u.beg[w];
+        if (beg == kNone || u.lofs[w] != kNone) continue;
+        const uint32_t cnt = u.cnt[w];
+        if (cnt == 0 || cnt > (uint32_t)kWChunk) continue;
+#pragma unroll
+        for (int j = 0; j < kWStripes; ++j) {
+            const uint32_t q = j * 32 + lane;
+            if (q < cnt) {
+                const uint32_t t = loc_act[beg + q];
+                const uint32_t here = t < n ? rank[t] : 0u;
+                T.key[q] = ((unsigned long long)here << 32) | loc_next[beg + q];
+                T.t[q] = t;
+            }
+        }
+        __syncwarp();
+        uint32_t bs_carry = 0;
+#pragma unroll
+        for (int j = 0; j < kWStripes; ++j) {
+            const uint32_t q = j * 32 + lane;
+            const bool in = q < cnt;
+            const unsigned long long K = in ? T.key[q] : 0ull;
+            const uint32_t here = (uint32_t)(K >> 32);
+            const bool head = in && (q == 0 || (uint32_t)(T.key[q - 1] >> 32) != here);
+            uint32_t bs = head ? q : 0u;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, bs, o);
+                if (lane >= (uint32_t)o) bs = max(bs, y);
+            }
+            bs = max(bs, bs_carry);
+            bs_carry = __shfl_sync(0xffffffffu, bs, 31);
+            if (in) {
+                const uint32_t t = T.t[q];
+                uint32_t lt_pair = 0, lt_key = 0, eq = 0;
+                for (uint32_t x = bs; x < cnt; ++x) {
+                    const unsigned long long kx = T.key[x];
+                    if ((uint32_t)(kx >> 32) != here) break;
+                    const uint32_t tx = T.t[x];
+                    lt_key += kx < K;
+                    eq += kx == K;
+                    lt_pair += (kx < K || (kx == K && tx < t)) ? 1u : 0u;
+                }
+                const uint32_t row = here + lt_pair;
+                if (row < n && t < n) {
+                    sa[row] = t;
+                    rank[t] = here + lt_key;
+                } else {
+                    atomicOr(d_err, 64u);
+                }
+                T.tpos[bs + lt_pair] = t;
+                T.act[bs + lt_pair] = eq >= 2 ? 1 : 0;
+            }
+        }
+        __syncwarp();
+        uint32_t acnt = 0;
+#pragma unroll
+        for (int j = 0; j < kWStripes; ++j) {
+            const uint32_t q = j * 32 + lane;
+            const bool a = q < cnt && T.act[q];
+            const uint32_t bal = __ballot_sync(0xffffffffu, a);
+            if (a) loc_act[beg + acnt + __popc(bal & below)] = T.tpos[q];
+            acnt += __popc(bal);
+        }
+        if (lane == 0) {
+            u.cnt[w] = acnt;
+            if (acnt) atomicAdd(d_cnt, acnt);
+        }
+        __syncwarp();
     }
 }
 
@@ -1173,6 +1494,8 @@ unsigned g_keys_ctas[64] = {0};
 unsigned g_round_keys_ctas[64] = {0};
 unsigned g_groups_ctas[64] = {0};
 unsigned g_local_ctas[64] = {0};
+unsigned g_local_warp_ctas[64] = {0};
+unsigned g_round_warp_ctas[64] = {0};
 unsigned g_round_local_ctas[64] = {0};
 
 int current_device() {
@@ -1193,6 +1516,8 @@ void suffix_sort_init() {
     g_groups_ctas[dev] = std::min<unsigned>(kMaxGroupChunks,
                                             persistent_ctas((const void*)sa_groups_apply_kernel<false>, kThreads, 0));
     g_local_ctas[dev] = persistent_ctas((const void*)sa_local_sort_kernel, kLThreads, kLocalSortSmem);
+    g_local_warp_ctas[dev] = persistent_ctas((const void*)sa_local_sort_warp_kernel, kWWarps * 32, 0);
+    g_round_warp_ctas[dev] = persistent_ctas((const void*)sa_round_local_warp_kernel, kWWarps * 32, 0);
     g_round_local_ctas[dev] = persistent_ctas((const void*)sa_round_local_kernel, kLThreads, kRoundLocalSmem);
 }
 
@@ -1294,9 +1619,13 @@ void suffix_sort_block(Launcher& L, const uint32_t* text, const uint32_t* term, 
                 d_large, b.count_log + 3, (int)rounds + 1, 2);
     // per long row: its list entry (t, row, key), SA and rank writes; per
     // unsorted member the compacted entry
-    SBWT_LAUNCH(L, "sa_local_sort", (double)n * 24, 4, b.count_log + 3, sa_local_sort_kernel,
-                grid_of(g_local_ctas[dev], nwin), kLThreads, kLocalSortSmem, n, ll_t, ll_row, ll_key, units, nwin,
-                b.sa, b.rank, b.loc_act, b.count_log + 3, b.err, seg_shift);
+    SBWT_LAUNCH(L, "sa_local_sort", (double)n * 24, 4, b.count_log + 3, sa_local_sort_warp_kernel,
+                grid_of(g_local_warp_ctas[dev], (uint64_t)nwin / kWWarps + 1), kWWarps * 32, 0, n, ll_t, ll_row,
+                ll_key, units, nwin, b.sa, b.rank, b.loc_act, b.count_log + 3, seg_shift);
+    // the units with a bucket longer than a warp chunk
+    SBWT_LAUNCH(L, "sa_local_sort_cta", 0, 0, nullptr, sa_local_sort_kernel, grid_of(g_local_ctas[dev], nwin),
+                kLThreads, kLocalSortSmem, n, ll_t, ll_row, ll_key, units, nwin, b.sa, b.rank, b.loc_act,
+                b.count_log + 3, b.err, seg_shift);
     // the list of the device-wide path goes to the other array (the long
     // rows' keys are dead once the local sort has run)
     SBWT_LAUNCH(L, "sa_large_gather", 32.0 * nwin, 24, d_large, large_gather, grid_of(g_local_ctas[dev], nwin),
@@ -1320,9 +1649,12 @@ void suffix_sort_block(Launcher& L, const uint32_t* text, const uint32_t* term, 
         SBWT_LAUNCH(L, "sa_round_keys", 0, 24, cnt, sa_round_keys_kernel,
                     grid_of(g_round_keys_ctas[dev], (uint64_t)n / kThreads + 1), kThreads, 0, b.act_suf[cur], cnt,
                     b.rank, h, n, bits, b.keys, b.vals, b.err);
-        SBWT_LAUNCH(L, "sa_round_local", 0, 24, loc_cnt, sa_round_local_kernel, grid_of(g_round_local_ctas[dev], nwin),
-                    kLThreads, kRoundLocalSmem, b.loc_act, b.loc_next, units, nwin, n, b.rank, b.sa,
-                    b.count_log + 3 + 2 * r, b.err);
+        SBWT_LAUNCH(L, "sa_round_local", 0, 24, loc_cnt, sa_round_local_warp_kernel,
+                    grid_of(g_round_warp_ctas[dev], (uint64_t)nwin / kWWarps + 1), kWWarps * 32, 0, b.loc_act,
+                    b.loc_next, units, nwin, n, b.rank, b.sa, b.count_log + 3 + 2 * r, b.err);
+        SBWT_LAUNCH(L, "sa_round_local_cta", 0, 0, nullptr, sa_round_local_kernel,
+                    grid_of(g_round_local_ctas[dev], nwin), kLThreads, kRoundLocalSmem, b.loc_act, b.loc_next,
+                    units, nwin, n, b.rank, b.sa, b.count_log + 3 + 2 * r, b.err);
         const bool a = radix_sort_pairs_fused(L, b.keys, b.vals, b.keys_alt, b.vals_alt, cnt, n, 0, 2 * bits,
                                               b.radix_temp, b.err);
         run_groups<false>(L, b, a ? b.keys_alt : b.keys, a ? b.vals_alt : b.vals, b.act_pos[cur], cnt, n,
