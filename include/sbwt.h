@@ -51,7 +51,7 @@ extern "C" {
 #define SBWT_ENOMEM (-2)   /* the HBM budget (or the device) cannot hold the result */
 #define SBWT_ERANGE (-3)   /* output buffer too small; the needed size is reported */
 #define SBWT_EDEVICE (-4)  /* a CUDA error, or a device-side wait that gave up */
-#define SBWT_ENOTSUP (-5)  /* option not supported by this build */
+#define SBWT_ENOTSUP (-5)  /* option the library does not support */
 #define SBWT_EBUSY (-6)    /* the index is serving: only submit/wait are allowed */
 #define SBWT_ETIMEDOUT (-7) /* sbwt_wait: the request is not done yet */
 #define SBWT_EIO (-8)       /* sbwt_save / sbwt_load: the file cannot be written or read */
