@@ -99,9 +99,15 @@ static inline unsigned atomicMin(uint32_t* p, uint32_t v) {
 #define __shared__ static
 #define __align__(n) alignas(n)
 
+struct uint4 {
+    unsigned x, y, z, w;
+};
+static inline uint4 make_uint4(unsigned a, unsigned b, unsigned c, unsigned d) { return uint4{a, b, c, d}; }
+
 #include "constants.inc"
 alignas(16) static unsigned char g_dyn_smem[(size_t)kLSlots * 20];  // the larger of the two CTA kernels' needs
 #include "scan.inc"
+#include "unit_scan.inc"
 #include "cta_local.inc"
 #include "warp_local.inc"
 #include "cta_round.inc"
@@ -200,6 +206,23 @@ extern "C" int emu_round(uint32_t* loc_act, const uint32_t* loc_next, uint32_t* 
     memcpy(rank, g_rank, n * 4ull);
     memcpy(sa, g_sa, n * 4ull);
     memcpy(cnt, g_cnt, nwin * 4ull);
+    for (auto& m : maps) munmap(m.first, m.second);
+    return 0;
+}
+
+// The unit scan of one block (one CTA): unit ends, long counts, owners,
+// global-path offsets, zeroed counts and round counters.  Unit fields are
+// laid out as on the device (one stride of words per field).
+extern "C" int emu_unit_scan(uint32_t* fields, uint64_t stride, uint32_t nwin, uint32_t n, uint32_t* d_large_n,
+                             uint32_t* zero_slots, int nzero, int zero_stride) {
+    std::vector<std::pair<void*, size_t>> maps;
+    uint32_t* g = guarded(fields, stride * 8, maps);
+    uint32_t* gz = guarded(zero_slots, (size_t)nzero * zero_stride, maps);
+    Units u{g, g + stride, g + 2 * stride, g + 3 * stride, g + 4 * stride, g + 5 * stride, g + 6 * stride,
+            g + 7 * stride};
+    run_grid(1, kScanThreads, [&] { sa_unit_scan_kernel(u, nwin, n, d_large_n, gz, nzero, zero_stride); });
+    memcpy(fields, g, stride * 8 * 4);
+    memcpy(zero_slots, gz, (size_t)nzero * zero_stride * 4);
     for (auto& m : maps) munmap(m.first, m.second);
     return 0;
 }

@@ -1,4 +1,4 @@
-"""The local-sort kernels of the suffix sort, run on the CPU.
+"""The unit scan and the local-sort kernels of the suffix sort, run on the CPU.
 
 The text of the warp-per-unit kernels and of the CTA-batch kernels that take
 the units they leave is cut out of csrc/suffix_sort.cu and compiled for the
@@ -18,7 +18,11 @@ compared with the contract both kernels share:
   (rank[t], rank[t + h], t); a member at offset x of the old group headed by
   row H takes row H + x, its rank is H plus the offset of its new group's
   first member, and the members of new groups of two or more are listed
-  again in order.
+  again in order;
+* the unit scan (one CTA over the window table): each unit's end (the next
+  unit's start) and long count, the unit owning each window's first row,
+  the offsets of the device-wide units (over 2048 long rows) in window
+  order, zeroed counts and round counters.
 
 The inputs keep the order the pipeline guarantees: inside a bucket (and
 inside an old group) the entries are in t order.  No GPU is used."""
@@ -58,6 +62,7 @@ def emu(tmp_path_factory):
     parts = {
         "constants.inc": _cut(src, "constexpr int kThreads = 256;", "// Key geometry per code width"),
         "scan.inc": _cut(hdr, "struct SumOp {", "// Launch bookkeeping"),
+        "unit_scan.inc": _cut(src, "// kScanPer consecutive windows of one field", "// one spare slot per kLItems"),
         "cta_local.inc": _cut(src, "// one spare slot per kLItems", "// Warp-per-unit local sort."),
         "warp_local.inc": _cut(src, "// Warp-per-unit local sort.", "// The global-path list:"),
         "cta_round.inc": _cut(src, "// One round for the local units, a batch of units per CTA step",
@@ -300,3 +305,71 @@ def test_round(emu, case):
         assert cnt[w] == len(act)
         assert list(loc_act[beg[w]:beg[w] + len(act)]) == act
     assert int(d_cnt[0]) == sum(len(a) for a in e_loc.values())
+
+
+# ---- the unit scan ------------------------------------------------------------
+
+@pytest.mark.timeout(600)
+@pytest.mark.parametrize("case", [dict(seed=21, n_target=30000), dict(seed=22, n_target=60000, p_big=0.01,
+                                  big=(2500, 4000)), dict(seed=23, n_target=5000000, max_bucket=64, p_short=0.3),
+                                  dict(seed=24, n_target=20000, p_hugeshort=0.02)])
+def test_unit_scan(emu, case):
+    """Unit ends, long counts, window owners and the offsets of the units
+    of the device-wide path, from the window table of a block."""
+    case = dict(case)
+    rng = np.random.default_rng(case.pop("seed"))
+    n, is_long, keys, starts, t_of_row = make_block(rng, case.pop("n_target"), 41, **case)
+    nwin = (n + kWindow - 1) // kWindow
+    is_start = np.zeros(n + 1, bool)
+    is_start[starts] = True
+    beg = np.full(nwin, kNone, np.uint32)
+    lcb = np.zeros(nwin, np.uint32)
+    lct = np.zeros(nwin, np.uint32)
+    long_before = np.concatenate([[0], np.cumsum(is_long)])
+    for w in range(nwin):
+        lo, hi = w * kWindow, min(n, (w + 1) * kWindow)
+        st = np.nonzero(is_start[lo:hi])[0]
+        lct[w] = long_before[hi] - long_before[lo]
+        if len(st):
+            beg[w] = lo + st[0]
+            lcb[w] = long_before[lo + st[0]] - long_before[lo]
+        else:
+            lcb[w] = lct[w]
+    stride = (n // kWindow + 2 + 7) & ~7  # the device layout's words per field
+    fields = np.zeros(8 * stride, np.uint32)
+    fields[0:nwin] = beg
+    fields[stride:stride + nwin] = lcb
+    fields[2 * stride:2 * stride + nwin] = lct
+    fields[6 * stride:6 * stride + nwin] = 7  # counts to be zeroed
+    zero_slots = np.full(3 * 2, 9, np.uint32)
+    d_large = np.zeros(1, np.uint32)
+    emu.emu_unit_scan(_p(fields), ctypes.c_uint64(stride), ctypes.c_uint32(nwin), ctypes.c_uint32(n), _p(d_large),
+                      _p(zero_slots), ctypes.c_int(3), ctypes.c_int(2))
+    end = fields[3 * stride:3 * stride + nwin]
+    nlong = fields[4 * stride:4 * stride + nwin]
+    lofs = fields[5 * stride:5 * stride + nwin]
+    cnt = fields[6 * stride:6 * stride + nwin]
+    owner = fields[7 * stride:7 * stride + nwin]
+    unit_ws = [w for w in range(nwin) if beg[w] != kNone]
+    off = 0
+    last = None
+    for w in range(nwin):
+        if beg[w] != kNone:
+            a = unit_ws.index(w)
+            e = int(beg[unit_ws[a + 1]]) if a + 1 < len(unit_ws) else n
+            nl = long_before[e] - long_before[beg[w]]
+            assert end[w] == e and nlong[w] == nl
+            if nl > kLCap:
+                assert lofs[w] == off
+                off += e - int(beg[w])
+            else:
+                assert lofs[w] == kNone
+        else:
+            assert end[w] == 0 and nlong[w] == 0 and lofs[w] == kNone
+        # the unit whose rows include the window's first row
+        assert owner[w] == (w if beg[w] == w * kWindow else last)
+        if beg[w] != kNone:
+            last = w
+    assert int(d_large[0]) == off
+    assert np.all(cnt == 0)
+    assert list(zero_slots) == [0, 9, 0, 9, 0, 9]
