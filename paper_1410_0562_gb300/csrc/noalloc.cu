@@ -119,11 +119,15 @@ extern "C" int sbwt_bwt_noalloc(const char* alphabet, const uint8_t* reads, cons
     int sigma = 0;
     if (parse_alphabet(alphabet, &alpha4, &sigma)) return SBWT_EINVAL;
     if (offsets[0] != 0) return SBWT_EINVAL;
+    // Every read adds at least its terminator, so more than kMax reads can
+    // never fit; the byte count and the read count are tested against the
+    // limit one at a time, so no sum of caller values can wrap.
+    if (m > kMax) return SBWT_EINVAL;
     uint64_t max_len = 0;
     for (uint64_t j = 0; j < m; ++j) {
         if (offsets[j + 1] < offsets[j]) return SBWT_EINVAL;
+        if (offsets[j + 1] > kMax || j + 1 > kMax - offsets[j + 1]) return SBWT_EINVAL;  // over the maximum
         if (offsets[j + 1] - offsets[j] > max_len) max_len = offsets[j + 1] - offsets[j];
-        if (offsets[j + 1] + j + 1 > kMax) return SBWT_EINVAL;  // over the fixed maximum
     }
     const uint64_t nbytes = offsets[m];
     const uint64_t n = nbytes + m;
@@ -187,6 +191,9 @@ extern "C" int sbwt_bwt_noalloc(const char* alphabet, const uint8_t* reads, cons
     ok &= cudaMemsetAsync(term + term_words, 0, kTermPadWords * 4, s) == cudaSuccess;
     ok &= cudaMemsetAsync(err, 0, 4, s) == cudaSuccess;
     if (!ok) {
+        // copies queued before the failure may still be writing the shared
+        // array: let them finish before the lock is released
+        cudaStreamSynchronize(s);
         cudaGetLastError();
         return SBWT_EDEVICE;
     }
@@ -198,8 +205,13 @@ extern "C" int sbwt_bwt_noalloc(const char* alphabet, const uint8_t* reads, cons
     ok &= cudaMemcpyAsync(&h_err, err, 4, cudaMemcpyDeviceToHost, s) == cudaSuccess;
     ok &= cudaMemcpyAsync(out, d_out, n, cudaMemcpyDeviceToHost, s) == cudaSuccess;
     ok &= cudaGetLastError() == cudaSuccess;
+    // always drain the stream before the lock is released, even after a
+    // failed launch or copy, so no later call can overlap this one's work
     ok &= cudaStreamSynchronize(s) == cudaSuccess;
-    if (!ok) return SBWT_EDEVICE;
+    if (!ok) {
+        cudaGetLastError();
+        return SBWT_EDEVICE;
+    }
     if (h_err & 1u) return SBWT_EINVAL;  // a byte outside the alphabet
     if (h_err) return SBWT_EDEVICE;
     return SBWT_OK;

@@ -193,3 +193,22 @@ def test_wide_alphabet_file_layout(lib, tmp_path):
 def test_save_rejects_null_path(lib):
     idx = sb.SetBWT(b"ACGT")
     assert lib.sbwt_save(idx.handle, None) == sb.SBWT_EINVAL
+
+
+def test_noalloc_rejects_sizes_that_would_wrap(lib):
+    """sbwt_bwt_noalloc checks its size limit on the host before any device
+    work, with offsets whose sums would wrap past 2^64."""
+    out = np.zeros(16, np.uint8)
+    got = ctypes.c_uint64()
+    top = np.iinfo(np.uint64).max
+    for offs in ([0, top], [0, top, top], [0, top - 1, top], [0, sb.SBWT_NOALLOC_MAX_SUFFIXES]):
+        o = np.array(offs, np.uint64)
+        rc = lib.sbwt_bwt_noalloc(b"ACGT", ctypes.c_void_p(out.ctypes.data), ctypes.c_void_p(o.ctypes.data),
+                                  len(o) - 1, ctypes.c_void_p(out.ctypes.data), 16, ctypes.byref(got), None)
+        assert rc == sb.SBWT_EINVAL, offs
+    # more reads than the maximum can hold terminators for
+    m = sb.SBWT_NOALLOC_MAX_SUFFIXES + 1
+    o = np.zeros(m + 1, np.uint64)
+    rc = lib.sbwt_bwt_noalloc(b"ACGT", ctypes.c_void_p(out.ctypes.data), ctypes.c_void_p(o.ctypes.data), m,
+                              ctypes.c_void_p(out.ctypes.data), 16, ctypes.byref(got), None)
+    assert rc == sb.SBWT_EINVAL
