@@ -251,20 +251,30 @@ def wide(n_reads: int = 1_000_000, genome_size: int = 10_000_000, seed_genome: i
 
 
 def serving(n_resident: int = 20_000_000, genome_size: int = 200_000_000, n_requests: int = 48,
-            seed_genome: int = 0x14100562 + 5, seed_reads: int = 0x05621410 + 5, max_request: int = 1_000_000):
+            seed_genome: int = 0x14100562 + 5, seed_reads: int = 0x05621410 + 5, max_request: int = 1_000_000,
+            min_request: int = 10_000):
     """The serving workload: a resident set of n_resident x 100 bp reads (1%
     substitutions) from a seeded i.i.d. genome, and request read sets whose
-    sizes are log-uniform in [10k, max_request] reads of length U[100, 150]
-    from the same genome.  Returns (resident Workload, list of (reads,
-    offsets))."""
+    sizes are log-uniform in [min_request, max_request] reads (10k to 1M by
+    default) of length U[100, 150] from the same genome.  Returns (resident
+    Workload, list of (reads, offsets))."""
     g = genome(genome_size, seed_genome)
     reads, off = sampled_reads(g, n_resident, 100, 0.01, seed_reads)
     resident = Workload(f"serving-resident-{n_resident}x100-g{genome_size}", reads, off, 1 << 25, 64,
                         (0, n_resident))
     rng = _rng(seed_reads ^ 0xA5A5)
-    sizes = np.exp(rng.uniform(np.log(10_000), np.log(max_request), size=n_requests)).astype(np.int64)
+    sizes = np.exp(rng.uniform(np.log(min_request), np.log(max_request), size=n_requests)).astype(np.int64)
     requests = []
     for i, m in enumerate(sizes):
         lengths = rng.integers(100, 151, size=int(m))
         requests.append(sampled_reads(g, int(m), lengths, 0.01, seed_reads + 1 + i))
     return resident, requests
+
+
+def serving_scaled(scale: int = 20):
+    """The serving workload at 1/scale of its size in every dimension: the
+    resident reads, the genome and the request sizes (so 1M resident reads
+    from a 10 Mbp genome and requests of 500 to 50k reads at scale 20), with
+    the same seeds, read lengths and request count."""
+    return serving(n_resident=20_000_000 // scale, genome_size=200_000_000 // scale, n_requests=48,
+                   max_request=1_000_000 // scale, min_request=10_000 // scale)
