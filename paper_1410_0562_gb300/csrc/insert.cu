@@ -8,167 +8,326 @@
 // and new suffixes never tie because their terminators differ).  Old rows
 // keep their relative order.
 //
-// One CTA builds one superblock (1024 occurrence blocks of 64 rows), four
-// consecutive blocks per thread (or one per thread, 1024 threads, when the
-// new rows are at least a quarter of the result: the splicing then needs the
-// parallelism more than the binary searches need sharing).  For output
-// block b (rows [o, o+64)) a binary search finds i0 = |{i : g_sa[i] + i <
-// o}|; the block then holds the old rows
-// starting at o - i0, into which the new symbols with final rows in [o, o+64)
-// are spliced in ascending order.  Per-block counts are scanned across the
-// CTA for the 16-bit block counters; a one-CTA pass scans the superblock
-// totals into the 64-bit superblock counters and C[] (Lemma 1's C[c] counts
-// every smaller symbol, the terminators included).
+// The 2-bit dictionary: one CTA builds one superblock (1024 occurrence blocks
+// of 64 rows) from the new symbols that land in it, which bint_gather's plan
+// names; it marks each output block's new rows in shared memory, derives
+// where each block's old rows start from a scan of those marks, spreads the
+// old rows around the new ones and scans the per-block counts for the 16-bit
+// block counters (insert_kernel below).  The 4-bit dictionary (5 to 16
+// symbols) splices the new symbols of each block one by one after a binary
+// search for the first of them.  A one-CTA pass (three steps for many
+// superblocks) then scans the superblock totals into the 64-bit superblock
+// counters and C[] (Lemma 1's C[c] counts every smaller symbol, the
+// terminators included).
 #include "sbwt_kernels.cuh"
 
 namespace sbwt {
 namespace {
 
 constexpr int kThreads = 256;
+constexpr int kInsertThreads = 512;  // threads of a 2-bit Insert CTA (one superblock)
+constexpr int kRun = 8;              // consecutive new symbols a thread places at once
 
 struct Window {
     unsigned long long w0, w1, dm;
 };
 
-// 64 old rows starting at row s (rows past the old end read as zero).
-__device__ __forceinline__ Window old_window(const OccBlock* __restrict__ old_blocks, uint64_t nb_old, uint64_t s) {
+// The two old blocks a 64-row window starting at row s reads (the second one
+// zero past the old end), loaded before any of them is used.
+struct OldPair {
+    unsigned long long a0, a1, da, b0, b1, db;
+};
+__device__ __forceinline__ OldPair old_pair(const OccBlock* __restrict__ old_blocks, uint64_t nb_old, uint64_t s) {
     const uint64_t bs = s >> kOccShift;
-    const uint32_t off = (uint32_t)(s & (kOccSpan - 1));
-    const OccBlock& A = old_blocks[bs];
-    const unsigned long long a0 = A.sym[0], a1 = A.sym[1], da = A.dmask;
-    unsigned long long a2 = 0, a3 = 0, db = 0;
+    const ulonglong2* A = reinterpret_cast<const ulonglong2*>(old_blocks + bs);
+    const ulonglong2 a01 = A[0], ad = A[1];
+    ulonglong2 b01 = make_ulonglong2(0ull, 0ull), bd = make_ulonglong2(0ull, 0ull);
     if (bs + 1 < nb_old) {
-        const OccBlock& B = old_blocks[bs + 1];
-        a2 = B.sym[0];
-        a3 = B.sym[1];
-        db = B.dmask;
+        b01 = A[2];
+        bd = A[3];
     }
+    return OldPair{a01.x, a01.y, ad.x, b01.x, b01.y, bd.x};
+}
+
+// 64 old rows starting at row s, from the pair of blocks holding them.
+__device__ __forceinline__ Window old_window_of(const OldPair& o, uint64_t s) {
+    const uint32_t off = (uint32_t)(s & (kOccSpan - 1));
     Window w;
     const uint32_t sh = 2 * off;  // 0 .. 126 bits
     if (sh == 0) {
-        w.w0 = a0;
-        w.w1 = a1;
+        w.w0 = o.a0;
+        w.w1 = o.a1;
     } else if (sh < 64) {
-        w.w0 = (a0 >> sh) | (a1 << (64 - sh));
-        w.w1 = (a1 >> sh) | (a2 << (64 - sh));
+        w.w0 = (o.a0 >> sh) | (o.a1 << (64 - sh));
+        w.w1 = (o.a1 >> sh) | (o.b0 << (64 - sh));
     } else if (sh == 64) {
-        w.w0 = a1;
-        w.w1 = a2;
+        w.w0 = o.a1;
+        w.w1 = o.b0;
     } else {
         const uint32_t s2 = sh - 64;
-        w.w0 = (a1 >> s2) | (a2 << (64 - s2));
-        w.w1 = (a2 >> s2) | (a3 << (64 - s2));
+        w.w0 = (o.a1 >> s2) | (o.b0 << (64 - s2));
+        w.w1 = (o.b0 >> s2) | (o.b1 << (64 - s2));
     }
-    w.dm = off == 0 ? da : ((da >> off) | (db << (64 - off)));
+    w.dm = off == 0 ? o.da : ((o.da >> off) | (o.db << (64 - off)));
     return w;
 }
 
-// Splice one row holding `code` (terminator when dollar) in at position p of
-// the 64-row window; rows p.. move up by one and row 63 falls off.
-__device__ __forceinline__ void splice(Window& w, uint32_t p, uint32_t code, uint32_t dollar) {
-    if (p < 32) {
-        w.w1 = (w.w1 << 2) | (w.w0 >> 62);
-        const unsigned long long keep = low_bits(2 * p);
-        w.w0 = (w.w0 & keep) | ((unsigned long long)code << (2 * p)) | ((w.w0 & ~keep) << 2);
-    } else {
-        const uint32_t q = p - 32;
-        const unsigned long long keep = low_bits(2 * q);
-        w.w1 = (w.w1 & keep) | ((unsigned long long)code << (2 * q)) | ((w.w1 & ~keep) << 2);
-    }
-    const unsigned long long keepd = low_bits(p);
-    w.dm = (w.dm & keepd) | ((unsigned long long)dollar << p) | ((w.dm & ~keepd) << 1);
+// Opens an empty row at position p of the 64-row window: rows p.. move up by
+// one and row 63 falls off.
+__device__ __forceinline__ void open_row(Window& w, uint32_t p) {
+    const unsigned long long kl = p < 32 ? low_bits(2 * p) : ~0ull;        // rows below p in w0
+    const unsigned long long kh = p < 32 ? 0ull : low_bits(2 * p - 64);   // rows below p in w1
+    const unsigned long long carry = p < 32 ? w.w0 >> 62 : 0ull;          // row 31 moves to row 32
+    w.w1 = (w.w1 & kh) | ((w.w1 & ~kh) << 2) | carry;
+    w.w0 = (w.w0 & kl) | ((w.w0 & ~kl) << 2);
+    const unsigned long long kd = low_bits(p);
+    w.dm = (w.dm & kd) | ((w.dm & ~kd) << 1);
 }
 
-// kPer output blocks per thread (kBlocksPerSuper / kPer threads): 4 for a
-// block of sparse new rows (one binary search serves four blocks), 1 when
-// new rows are dense (four times the threads for the splicing).
-template <class IdxT, int kPer>
-__global__ void __launch_bounds__(kBlocksPerSuper / kPer) insert_kernel(const OccBlock* __restrict__ old_blocks,
-                                                          unsigned long long n_ext, const uint8_t* __restrict__ bint,
-                                                          const IdxT* __restrict__ gsa, unsigned long long n_int,
-                                                          OccBlock* __restrict__ new_blocks,
-                                                          unsigned long long n_new, uint32_t* __restrict__ sb_tot) {
+// Spreads the old rows of window w over the rows of an output block whose
+// new rows are the set bits of F: the old rows keep their order and fill
+// the clear bits of F, the rows of F are left empty.  Few new rows: open one
+// row per set bit; many: move each of the few old rows to its place.
+__device__ __forceinline__ Window spread_old(Window w, unsigned long long F) {
+    const uint32_t k = __popcll(F);
+    if (k <= 32) {
+        while (F) {
+            open_row(w, __ffsll((long long)F) - 1);
+            F &= F - 1;
+        }
+        return w;
+    }
+    Window o{0ull, 0ull, 0ull};
+    unsigned long long z = ~F;
+    uint32_t src = 0;
+    while (z) {
+        const uint32_t p = __ffsll((long long)z) - 1;
+        z &= z - 1;
+        const unsigned long long code = ((src < 32 ? w.w0 >> (2 * src) : w.w1 >> (2 * src - 64))) & 3ull;
+        if (p < 32) o.w0 |= code << (2 * p); else o.w1 |= code << (2 * p - 64);
+        o.dm |= ((w.dm >> src) & 1ull) << p;
+        ++src;
+    }
+    return o;
+}
+
+// One CTA builds one superblock of the next dictionary (kBlocksPerSuper
+// output blocks of 64 rows, rows [O, O + 2^16)) from the new symbols
+// [ins_i0[S], ins_i0[S+1]) that land in it (bint_gather wrote that plan):
+//  1. the CTA reads those new symbols' rows g_sa[i] + i and codes (a run of
+//     consecutive ones per thread) and sets, per output block, the mask F of
+//     its new rows, their terminator bits and their codes at their rows
+//     (shared memory; a thread merges the bits of its run per block first);
+//  2. a scan of popcount(F) over the blocks gives the new symbols before each
+//     block, so block b's old rows are the contiguous run starting at old row
+//     64 b - (new symbols before row 64 b);
+//  3. each thread builds output blocks (strided, so loads and stores of a
+//     warp are contiguous): the 64-row old window, spread over the clear bits
+//     of F, OR the new codes;
+//  4. a scan of the per-block counts gives the 16-bit block counters.
+// Every index that comes from g_sa is checked; an inconsistent plan flags
+// *d_err (bit 10) and never leads outside the arrays.
+template <class IdxT, int kT>
+__global__ void __launch_bounds__(kT) insert_kernel(const OccBlock* __restrict__ old_blocks, unsigned long long n_ext,
+                                                    const uint8_t* __restrict__ bint, const IdxT* __restrict__ gsa,
+                                                    unsigned long long n_int, const uint32_t* __restrict__ ins_i0,
+                                                    OccBlock* __restrict__ new_blocks, unsigned long long n_new,
+                                                    uint32_t* __restrict__ sb_tot, uint32_t* __restrict__ d_err) {
+    constexpr int kNB = kBlocksPerSuper, kPer = kNB / kT;
+    __shared__ uint32_t sF[2][kNB];  // new rows of each block (rows 0-31, 32-63); later its counts
+    __shared__ uint32_t sD[2][kNB];  // terminator mask: of the new rows, later of the whole block
+    __shared__ uint32_t sC[4][kNB];  // 2-bit codes, 16 rows per word: of the new rows, later of the block
+    __shared__ uint32_t sP[2][kNB];  // new symbols before each block; later the block counters
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint64_t S = blockIdx.x;
+    const uint64_t O = S << kSuperShift;
+    const uint64_t b_first = S * kNB;
     const uint64_t nb_new = (n_new >> kOccShift) + 1;
     const uint64_t nb_old = (n_ext >> kOccShift) + 1;
-    constexpr int kPerThread = kPer, kT = kBlocksPerSuper / kPer;
-    const uint64_t b0 = (uint64_t)blockIdx.x * kBlocksPerSuper + (uint64_t)threadIdx.x * kPerThread;
-    Window win[kPerThread];
-    uint32_t cnt[kPerThread][4];
-#pragma unroll
-    for (int bb = 0; bb < kPerThread; ++bb) {
-        win[bb].w0 = win[bb].w1 = win[bb].dm = 0;
-        cnt[bb][0] = cnt[bb][1] = cnt[bb][2] = cnt[bb][3] = 0;
+    for (int x = tid; x < kNB; x += kT) {
+        sF[0][x] = sF[1][x] = sD[0][x] = sD[1][x] = 0u;
+        sC[0][x] = sC[1][x] = sC[2][x] = sC[3][x] = 0u;
     }
-    if (b0 < nb_new) {
-        uint64_t lo = 0, hi = n_int;  // first i with g_sa[i] + i >= o
-        const uint64_t o0 = b0 << kOccShift;
-        while (lo < hi) {
-            const uint64_t mid = lo + ((hi - lo) >> 1);
-            if ((uint64_t)gsa[mid] + mid < o0) lo = mid + 1; else hi = mid;
-        }
-        uint64_t i = lo;
+    uint64_t i_begin = ins_i0[S], i_end = ins_i0[S + 1];
+    if (i_end > n_int || i_begin > i_end) {
+        if (tid == 0) atomicOr(d_err, 1024u);
+        i_end = min(i_end, (uint64_t)n_int);
+        i_begin = min(i_begin, i_end);
+    }
+    __syncthreads();
+
+    // 1. the new rows of every block of this superblock: each thread takes a
+    //    run of kRun consecutive new symbols (consecutive rows, so a run
+    //    touches one or two blocks when the new rows are dense), gathers
+    //    their bits per block in registers and ORs each block's bits into
+    //    shared memory once
+    for (uint64_t base = i_begin + (uint64_t)tid * kRun; base < i_end; base += (uint64_t)kT * kRun) {
+        uint64_t loc[kRun];
+        uint32_t xs[kRun];
 #pragma unroll
-        for (int bb = 0; bb < kPerThread; ++bb) {
-            const uint64_t b = b0 + bb;
-            if (b >= nb_new) break;
-            const uint64_t o = b << kOccShift;
-            // o - i old rows precede this block; clamped so a bad g_sa can
-            // never send the window past the old dictionary
-            const uint64_t s_old = o >= i ? min((unsigned long long)(o - i), n_ext) : 0ull;
-            Window w = old_window(old_blocks, nb_old, s_old);
-            while (i < n_int) {
-                const uint64_t row = (uint64_t)gsa[i] + i;
-                if (row >= o + kOccSpan) break;
-                const uint8_t x = bint[i];
-                splice(w, (uint32_t)(row - o), x == kBintDollar ? 0u : x, x == kBintDollar ? 1u : 0u);
-                ++i;
+        for (int u = 0; u < kRun; ++u) {
+            const uint64_t i = base + u;
+            loc[u] = i < i_end ? (uint64_t)gsa[i] + i - O : ~0ull;
+            xs[u] = i < i_end ? bint[i] : 0u;
+        }
+        uint32_t cj = 0xFFFFFFFFu;
+        unsigned long long f = 0, dm = 0, c0 = 0, c1 = 0;
+        auto flush = [&]() {
+            if (cj == 0xFFFFFFFFu) return;
+            if ((uint32_t)f) atomicOr(&sF[0][cj], (uint32_t)f);
+            if ((uint32_t)(f >> 32)) atomicOr(&sF[1][cj], (uint32_t)(f >> 32));
+            if ((uint32_t)dm) atomicOr(&sD[0][cj], (uint32_t)dm);
+            if ((uint32_t)(dm >> 32)) atomicOr(&sD[1][cj], (uint32_t)(dm >> 32));
+            if ((uint32_t)c0) atomicOr(&sC[0][cj], (uint32_t)c0);
+            if ((uint32_t)(c0 >> 32)) atomicOr(&sC[1][cj], (uint32_t)(c0 >> 32));
+            if ((uint32_t)c1) atomicOr(&sC[2][cj], (uint32_t)c1);
+            if ((uint32_t)(c1 >> 32)) atomicOr(&sC[3][cj], (uint32_t)(c1 >> 32));
+        };
+#pragma unroll
+        for (int u = 0; u < kRun; ++u) {
+            if (base + u >= i_end) break;
+            const uint64_t local = loc[u];
+            if (local >= (1ull << kSuperShift)) {  // not in this superblock: the plan is inconsistent
+                atomicOr(d_err, 1024u);
+                continue;
             }
-            const uint32_t valid = n_new > o ? (uint32_t)min((unsigned long long)kOccSpan, n_new - o) : 0u;
-            const unsigned long long v0 = low_bits(2 * min(valid, 32u));
-            const unsigned long long v1 = valid > 32 ? low_bits(2 * (valid - 32)) : 0ull;
-            w.w0 &= v0;
-            w.w1 &= v1;
-            w.dm &= low_bits(valid);
+            const uint32_t j = (uint32_t)(local >> kOccShift), q = (uint32_t)local & 63u;
+            if (j != cj) {
+                flush();
+                cj = j;
+                f = dm = c0 = c1 = 0;
+            }
+            f |= 1ull << q;
+            if (xs[u] == kBintDollar) {
+                dm |= 1ull << q;
+            } else {
+                const unsigned long long cv = (unsigned long long)(xs[u] & 3u) << (2u * (q & 31u));
+                if (q < 32) c0 |= cv; else c1 |= cv;
+            }
+        }
+        flush();
+    }
+    __syncthreads();
+
+    // 2. new symbols before each block (blocks kPer * tid .. in order)
+    {
+        uint32_t c[kPer], tot = 0;
 #pragma unroll
-            for (uint32_t c = 0; c < 4; ++c)
-                cnt[bb][c] = __popcll(match_code(w.w0, c) & v0) + __popcll(match_code(w.w1, c) & v1);
-            cnt[bb][0] -= __popcll(w.dm);
-            win[bb] = w;
+        for (int bb = 0; bb < kPer; ++bb) {
+            const int j = kPer * tid + bb;
+            c[bb] = __popc(sF[0][j]) + __popc(sF[1][j]);
+            tot += c[bb];
+        }
+        uint32_t all;
+        uint32_t ex = cta_exclusive_scan<SumOp, kT>(tot, all);
+#pragma unroll
+        for (int bb = 0; bb < kPer; ++bb) {
+            sP[0][kPer * tid + bb] = ex;
+            ex += c[bb];
+        }
+        // two new symbols on one row, or one outside this superblock
+        if (tid == 0 && all != (uint32_t)(i_end - i_begin)) atomicOr(d_err, 1024u);
+    }
+    __syncthreads();
+
+    // 3. build blocks tid, tid + kT, ...; keep them in shared memory.  The
+    //    old blocks of every window are loaded before any is used.
+    OldPair op[kPer];
+    uint64_t s_old[kPer];
+#pragma unroll
+    for (int bb = 0; bb < kPer; ++bb) {
+        const int j = tid + bb * kT;
+        const uint64_t b = b_first + j;
+        const uint64_t o = b << kOccShift;
+        const uint64_t inew = i_begin + sP[0][j];  // new symbols before row o
+        s_old[bb] = o - inew;
+        if (b < nb_new && (inew > o || s_old[bb] > n_ext)) {
+            atomicOr(d_err, 1024u);
+            s_old[bb] = inew > o ? 0ull : (uint64_t)n_ext;
+        }
+        if (b >= nb_new) s_old[bb] = 0;
+        op[bb] = old_pair(old_blocks, nb_old, s_old[bb]);
+    }
+#pragma unroll
+    for (int bb = 0; bb < kPer; ++bb) {
+        const int j = tid + bb * kT;
+        const uint64_t b = b_first + j;
+        if (b >= nb_new) {
+            sF[0][j] = sF[1][j] = 0u;
+            continue;
+        }
+        const uint64_t o = b << kOccShift;
+        const unsigned long long F = (unsigned long long)sF[0][j] | ((unsigned long long)sF[1][j] << 32);
+        Window w = spread_old(old_window_of(op[bb], s_old[bb]), F);
+        w.w0 |= (unsigned long long)sC[0][j] | ((unsigned long long)sC[1][j] << 32);
+        w.w1 |= (unsigned long long)sC[2][j] | ((unsigned long long)sC[3][j] << 32);
+        w.dm |= (unsigned long long)sD[0][j] | ((unsigned long long)sD[1][j] << 32);
+        const uint32_t valid = n_new > o ? (uint32_t)min((unsigned long long)kOccSpan, n_new - o) : 0u;
+        const unsigned long long v0 = low_bits(2 * min(valid, 32u));
+        const unsigned long long v1 = valid > 32 ? low_bits(2 * (valid - 32)) : 0ull;
+        w.w0 &= v0;
+        w.w1 &= v1;
+        w.dm &= low_bits(valid);
+        uint32_t cnt[4];
+#pragma unroll
+        for (uint32_t c = 0; c < 4; ++c) cnt[c] = __popcll(match_code(w.w0, c) & v0) + __popcll(match_code(w.w1, c) & v1);
+        cnt[0] -= __popcll(w.dm);
+        sC[0][j] = (uint32_t)w.w0;
+        sC[1][j] = (uint32_t)(w.w0 >> 32);
+        sC[2][j] = (uint32_t)w.w1;
+        sC[3][j] = (uint32_t)(w.w1 >> 32);
+        sD[0][j] = (uint32_t)w.dm;
+        sD[1][j] = (uint32_t)(w.dm >> 32);
+        sF[0][j] = cnt[0] | (cnt[1] << 16);
+        sF[1][j] = cnt[2] | (cnt[3] << 16);
+    }
+    __syncthreads();
+
+    // 4. 16-bit block counters: exclusive scan of the counts in block order
+    {
+        unsigned long long t01 = 0, t23 = 0;
+        uint32_t a[kPer], d[kPer];
+#pragma unroll
+        for (int bb = 0; bb < kPer; ++bb) {
+            a[bb] = sF[0][kPer * tid + bb];
+            d[bb] = sF[1][kPer * tid + bb];
+            t01 += (unsigned long long)(a[bb] & 0xFFFFu) | ((unsigned long long)(a[bb] >> 16) << 32);
+            t23 += (unsigned long long)(d[bb] & 0xFFFFu) | ((unsigned long long)(d[bb] >> 16) << 32);
+        }
+        unsigned long long tot01, tot23;
+        const unsigned long long e01 = cta_exclusive_scan<SumOp, kT>(t01, tot01);
+        const unsigned long long e23 = cta_exclusive_scan<SumOp, kT>(t23, tot23);
+        uint32_t p0 = (uint32_t)e01, p1 = (uint32_t)(e01 >> 32), p2 = (uint32_t)e23, p3 = (uint32_t)(e23 >> 32);
+#pragma unroll
+        for (int bb = 0; bb < kPer; ++bb) {
+            sP[0][kPer * tid + bb] = p0 | (p1 << 16);
+            sP[1][kPer * tid + bb] = p2 | (p3 << 16);
+            p0 += a[bb] & 0xFFFFu;
+            p1 += a[bb] >> 16;
+            p2 += d[bb] & 0xFFFFu;
+            p3 += d[bb] >> 16;
+        }
+        if (tid == 0) {
+            uint32_t* t = sb_tot + 4ull * S;
+            t[0] = (uint32_t)tot01;
+            t[1] = (uint32_t)(tot01 >> 32);
+            t[2] = (uint32_t)tot23;
+            t[3] = (uint32_t)(tot23 >> 32);
         }
     }
-    // 16-bit block counters: exclusive scan of the per-thread totals.
-    unsigned long long t01 = 0, t23 = 0;
+    __syncthreads();
+
+    // 5. write the blocks out (a warp stores 32 consecutive blocks)
 #pragma unroll
-    for (int bb = 0; bb < kPerThread; ++bb) {
-        t01 += (unsigned long long)cnt[bb][0] | ((unsigned long long)cnt[bb][1] << 32);
-        t23 += (unsigned long long)cnt[bb][2] | ((unsigned long long)cnt[bb][3] << 32);
-    }
-    unsigned long long tot01, tot23;
-    const unsigned long long e01 = cta_exclusive_scan<SumOp, kT>(t01, tot01);
-    const unsigned long long e23 = cta_exclusive_scan<SumOp, kT>(t23, tot23);
-    uint32_t pref[4] = {(uint32_t)e01, (uint32_t)(e01 >> 32), (uint32_t)e23, (uint32_t)(e23 >> 32)};
-#pragma unroll
-    for (int bb = 0; bb < kPerThread; ++bb) {
-        const uint64_t b = b0 + bb;
+    for (int bb = 0; bb < kPer; ++bb) {
+        const int j = tid + bb * kT;
+        const uint64_t b = b_first + j;
         if (b >= nb_new) break;
-        OccBlock out;
-        out.sym[0] = win[bb].w0;
-        out.sym[1] = win[bb].w1;
-        out.dmask = win[bb].dm;
-        out.cnt = (unsigned long long)pref[0] | ((unsigned long long)pref[1] << 16) |
-                  ((unsigned long long)pref[2] << 32) | ((unsigned long long)pref[3] << 48);
         ulonglong2* dst = reinterpret_cast<ulonglong2*>(new_blocks + b);
-        dst[0] = make_ulonglong2(out.sym[0], out.sym[1]);
-        dst[1] = make_ulonglong2(out.dmask, out.cnt);
-#pragma unroll
-        for (int c = 0; c < 4; ++c) pref[c] += cnt[bb][c];
-    }
-    if (threadIdx.x == 0) {
-        uint32_t* t = sb_tot + 4ull * blockIdx.x;
-        t[0] = (uint32_t)tot01;
-        t[1] = (uint32_t)(tot01 >> 32);
-        t[2] = (uint32_t)tot23;
-        t[3] = (uint32_t)(tot23 >> 32);
+        dst[0] = make_ulonglong2((unsigned long long)sC[0][j] | ((unsigned long long)sC[1][j] << 32),
+                                 (unsigned long long)sC[2][j] | ((unsigned long long)sC[3][j] << 32));
+        dst[1] = make_ulonglong2((unsigned long long)sD[0][j] | ((unsigned long long)sD[1][j] << 32),
+                                 (unsigned long long)sP[0][j] | ((unsigned long long)sP[1][j] << 32));
     }
 }
 
@@ -456,8 +615,8 @@ void super_scan(Launcher& L, const uint32_t* sb_tot, uint64_t nsb, unsigned long
 
 template <class IdxT>
 void launch_insert(Launcher& L, const void* old_blocks, uint64_t n_ext, const uint8_t* bint, const IdxT* gsa,
-                   uint64_t n_int, void* new_blocks, unsigned long long* new_super, unsigned long long* new_C,
-                   uint64_t m_new, uint32_t* sb_tot, int code_bits) {
+                   uint64_t n_int, const uint32_t* ins_i0, void* new_blocks, unsigned long long* new_super,
+                   unsigned long long* new_C, uint64_t m_new, uint32_t* sb_tot, uint32_t* d_err, int code_bits) {
     const uint64_t n_new = n_ext + n_int;
     // the superblock scan's per-chunk totals live after the superblock totals
     const uint64_t nsb_all = dict_supers_of(n_new, code_bits);
@@ -475,20 +634,21 @@ void launch_insert(Launcher& L, const void* old_blocks, uint64_t n_ext, const ui
         return;
     }
     const uint64_t nsb = dict_supers(n_new);
-    const double bytes = 32.0 * dict_blocks(n_ext) + (1.0 + sizeof(IdxT)) * n_int + 32.0 * dict_blocks(n_new);
-    // dense new rows (at least a quarter of the result): one block per thread
-    const bool dense = 4 * n_int >= n_new;
-    auto* const kern = dense ? insert_kernel<IdxT, 1> : insert_kernel<IdxT, 4>;
-    SBWT_LAUNCH(L, "insert_merge", bytes, 0, nullptr, kern, (unsigned)nsb, dense ? kBlocksPerSuper : kThreads, 0,
-                static_cast<const OccBlock*>(old_blocks), (unsigned long long)n_ext, bint, gsa,
-                (unsigned long long)n_int, static_cast<OccBlock*>(new_blocks), (unsigned long long)n_new, sb_tot);
+    const double bytes = 32.0 * dict_blocks(n_ext) + (1.0 + sizeof(IdxT)) * n_int + 32.0 * dict_blocks(n_new) +
+                         4.0 * (nsb + 1);
+    SBWT_LAUNCH(L, "insert_merge", bytes, 0, nullptr, (insert_kernel<IdxT, kInsertThreads>), (unsigned)nsb,
+                kInsertThreads, 0, static_cast<const OccBlock*>(old_blocks), (unsigned long long)n_ext, bint, gsa,
+                (unsigned long long)n_int, ins_i0, static_cast<OccBlock*>(new_blocks), (unsigned long long)n_new,
+                sb_tot, d_err);
     super_scan<4>(L, sb_tot, nsb, new_super, new_C, m_new, chunk_tot);
 }
 
 template void launch_insert<uint32_t>(Launcher&, const void*, uint64_t, const uint8_t*, const uint32_t*, uint64_t,
-                                      void*, unsigned long long*, unsigned long long*, uint64_t, uint32_t*, int);
+                                      const uint32_t*, void*, unsigned long long*, unsigned long long*, uint64_t,
+                                      uint32_t*, uint32_t*, int);
 template void launch_insert<unsigned long long>(Launcher&, const void*, uint64_t, const uint8_t*,
-                                                const unsigned long long*, uint64_t, void*, unsigned long long*,
-                                                unsigned long long*, uint64_t, uint32_t*, int);
+                                                const unsigned long long*, uint64_t, const uint32_t*, void*,
+                                                unsigned long long*, unsigned long long*, uint64_t, uint32_t*,
+                                                uint32_t*, int);
 
 }  // namespace sbwt

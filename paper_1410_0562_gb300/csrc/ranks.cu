@@ -146,7 +146,13 @@ __global__ void __launch_bounds__(kThreads) compute_ranks_kernel(const uint32_t*
         if (r < held) g[rs + r] = s[r];
 }
 
-// B_int and g_sa in one pass over SA_int (both index by SA_int[i]).
+// B_int and g_sa in one pass over SA_int (both index by SA_int[i]).  With
+// ins_i0 set, it also writes Insert's plan: new symbol i lands on row
+// r_i = g_sa[i] + i of the next dictionary (strictly increasing in i), and
+// ins_i0[S] = |{i : r_i < S * 2^super_shift}| for S = 0 .. nsb, so the CTA
+// that builds superblock S takes the new symbols [ins_i0[S], ins_i0[S+1]).
+// Thread i writes the entries S with r_{i-1} < S * 2^super_shift <= r_i
+// (all S up to r_0 for i = 0; the last thread also those past r_{n-1}).
 template <class IdxT, int kB>
 __global__ void __launch_bounds__(kThreads) bint_gather_kernel(const uint32_t* __restrict__ text,
                                                                const uint32_t* __restrict__ term,
@@ -154,13 +160,32 @@ __global__ void __launch_bounds__(kThreads) bint_gather_kernel(const uint32_t* _
                                                                const uint32_t* __restrict__ sa,
                                                                const IdxT* __restrict__ g, uint32_t n,
                                                                uint8_t* __restrict__ bint,
-                                                               IdxT* __restrict__ gsa) {
+                                                               IdxT* __restrict__ gsa, uint32_t* __restrict__ ins_i0,
+                                                               unsigned long long nsb, int super_shift) {
     const uint32_t i = blockIdx.x * kThreads + threadIdx.x;
-    if (i >= n) return;
-    const uint32_t t = sa[i] < n ? sa[i] : 0u;
-    const uint64_t P = base + t;
-    bint[i] = (t == 0 || is_term(term, P - 1)) ? kBintDollar : (uint8_t)text_code_b<kB>(text, P - 1);
-    gsa[i] = g[t];
+    const bool valid = i < n;
+    unsigned long long r = 0;
+    if (valid) {
+        const uint32_t t = sa[i] < n ? sa[i] : 0u;
+        const uint64_t P = base + t;
+        bint[i] = (t == 0 || is_term(term, P - 1)) ? kBintDollar : (uint8_t)text_code_b<kB>(text, P - 1);
+        const IdxT v = g[t];
+        gsa[i] = v;
+        r = (unsigned long long)v + i;
+    }
+    if (ins_i0 == nullptr) return;
+    // every lane of the warp is still here (the grid is whole warps)
+    unsigned long long prev = __shfl_up_sync(0xffffffffu, r, 1);
+    if (!valid) return;
+    if ((threadIdx.x & 31) == 0 && i > 0) {
+        const uint32_t tp = sa[i - 1] < n ? sa[i - 1] : 0u;
+        prev = (unsigned long long)g[tp] + (i - 1);
+    }
+    const unsigned long long s_lo = i == 0 ? 0ull : (prev >> super_shift) + 1;
+    const unsigned long long s_hi = min(r >> super_shift, nsb);
+    for (unsigned long long S = s_lo; S <= s_hi; ++S) ins_i0[S] = i;
+    if (i == n - 1)
+        for (unsigned long long S = (r >> super_shift) + 1; S <= nsb; ++S) ins_i0[S] = n;
 }
 
 // rank(c, k) queries, codes 0..kCodes-1, or kCodes for the terminator.
@@ -337,13 +362,15 @@ void launch_compute_ranks(Launcher& L, const uint32_t* text, const uint64_t* d_o
 
 template <class IdxT>
 void launch_bint_gather(Launcher& L, const uint32_t* text, const uint32_t* term, uint64_t base, const uint32_t* sa,
-                        const IdxT* g, uint32_t n, uint8_t* bint, IdxT* gsa, int code_bits) {
+                        const IdxT* g, uint32_t n, uint8_t* bint, IdxT* gsa, int code_bits, uint32_t* ins_i0,
+                        uint64_t nsb, int super_shift) {
     if (n == 0) return;
     // per suffix: SA_int read, one text word and one bitmap word (random), a
-    // random g sector, B_int and g_sa writes
+    // random g sector, B_int and g_sa writes; 4 bytes per plan entry
     auto* const kern = code_bits == 4 ? bint_gather_kernel<IdxT, 4> : bint_gather_kernel<IdxT, 2>;
-    SBWT_LAUNCH(L, "bint_gather", (double)n * (4 + 4 + 4 + 32 + 1 + sizeof(IdxT)), 0, nullptr, kern,
-                ceil_div_u(n, kThreads), kThreads, 0, text, term, (unsigned long long)base, sa, g, n, bint, gsa);
+    SBWT_LAUNCH(L, "bint_gather", (double)n * (4 + 4 + 4 + 32 + 1 + sizeof(IdxT)) + (ins_i0 ? 4.0 * (nsb + 1) : 0.0),
+                0, nullptr, kern, ceil_div_u(n, kThreads), kThreads, 0, text, term, (unsigned long long)base, sa, g,
+                n, bint, gsa, ins_i0, (unsigned long long)nsb, super_shift);
 }
 
 void launch_rank_batch(Launcher& L, const void* blocks, const unsigned long long* super, const uint8_t* codes,
@@ -400,9 +427,10 @@ template void launch_compute_ranks<unsigned long long>(Launcher&, const uint32_t
                                                        const unsigned long long*, uint64_t, uint64_t,
                                                        unsigned long long*, uint32_t*, int);
 template void launch_bint_gather<uint32_t>(Launcher&, const uint32_t*, const uint32_t*, uint64_t, const uint32_t*,
-                                           const uint32_t*, uint32_t, uint8_t*, uint32_t*, int);
+                                           const uint32_t*, uint32_t, uint8_t*, uint32_t*, int, uint32_t*, uint64_t,
+                                           int);
 template void launch_bint_gather<unsigned long long>(Launcher&, const uint32_t*, const uint32_t*, uint64_t,
                                                      const uint32_t*, const unsigned long long*, uint32_t, uint8_t*,
-                                                     unsigned long long*, int);
+                                                     unsigned long long*, int, uint32_t*, uint64_t, int);
 
 }  // namespace sbwt

@@ -61,10 +61,13 @@ void launch_compute_ranks(Launcher& L, const uint32_t* text, const uint64_t* d_o
                           uint64_t nreads, uint64_t n_int, const void* blocks, const unsigned long long* super,
                           const unsigned long long* d_C, uint64_t n_ext, uint64_t m_ext, IdxT* g, uint32_t* d_err,
                           int code_bits);
-// B_int and g_sa fused: one pass over SA_int after ComputeRanks.
+// B_int and g_sa fused: one pass over SA_int after ComputeRanks.  With
+// ins_i0 non-null it also writes Insert's plan (nsb + 1 entries: the first
+// new symbol of each superblock of 2^super_shift rows of the next dictionary).
 template <class IdxT>
 void launch_bint_gather(Launcher& L, const uint32_t* text, const uint32_t* term, uint64_t base, const uint32_t* sa,
-                        const IdxT* g, uint32_t n, uint8_t* bint, IdxT* gsa, int code_bits);
+                        const IdxT* g, uint32_t n, uint8_t* bint, IdxT* gsa, int code_bits, uint32_t* ins_i0 = nullptr,
+                        uint64_t nsb = 0, int super_shift = 0);
 // rank queries: codes 0..sigma-1, or 4 (16 for code_bits == 4) for the terminator.
 void launch_rank_batch(Launcher& L, const void* blocks, const unsigned long long* super, const uint8_t* codes,
                        const unsigned long long* ks, uint64_t q, unsigned long long* out, int code_bits);
@@ -83,11 +86,12 @@ void launch_unpack(Launcher& L, const void* blocks, uint64_t r0, uint64_t r1, co
 // superblock counters and C[] (m = terminators in the new dictionary).
 // Blocks are OccBlock (code_bits 2) or OccBlockW (code_bits 4); sb_tot holds
 // 4 (16) words per superblock, rounded up to 4 words, then 4 (16) 64-bit
-// words per 256 superblocks.
+// words per 256 superblocks.  ins_i0 is the plan bint_gather wrote (2-bit
+// dictionary; unused for 4-bit codes); an inconsistent plan sets *d_err bit 10.
 template <class IdxT>
 void launch_insert(Launcher& L, const void* old_blocks, uint64_t n_ext, const uint8_t* bint, const IdxT* gsa,
-                   uint64_t n_int, void* new_blocks, unsigned long long* new_super, unsigned long long* new_C,
-                   uint64_t m_new, uint32_t* sb_tot, int code_bits);
+                   uint64_t n_int, const uint32_t* ins_i0, void* new_blocks, unsigned long long* new_super,
+                   unsigned long long* new_C, uint64_t m_new, uint32_t* sb_tot, uint32_t* d_err, int code_bits);
 
 // plan.cu: checks device-resident offsets (offsets[0] = 0, non-decreasing,
 // every read shorter than max_block suffixes; summary->bad != 0 otherwise),

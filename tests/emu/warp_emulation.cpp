@@ -8,101 +8,7 @@
 // memory with an inaccessible page right after its last element and right
 // before its first, so an access outside it faults.  A lane that skips an
 // intrinsic its warp executes hangs the emulation (the test's timeout).
-#include <algorithm>
-#include <atomic>
-#include <barrier>
-#include <cstdint>
-#include <cstring>
-#include <memory>
-#include <thread>
-#include <vector>
-#include <sys/mman.h>
-#include <unistd.h>
-
-using std::max;
-using std::min;
-
-struct Dim { unsigned x = 0, y = 0, z = 0; };
-thread_local Dim threadIdx, blockIdx;
-static Dim blockDim, gridDim;
-thread_local unsigned emu_lane;
-
-struct EmuWarp {
-    std::barrier<> bar{32};
-    unsigned long long xch[32];
-};
-thread_local EmuWarp* g_warp;
-struct EmuCta {
-    std::unique_ptr<std::barrier<>> bar;
-    std::vector<int> xch;
-};
-static EmuCta g_cta;
-
-static inline void __syncwarp(unsigned = 0xffffffffu) { g_warp->bar.arrive_and_wait(); }
-template <class T>
-static T emu_get(T v, unsigned src) {
-    g_warp->xch[emu_lane] = (unsigned long long)v;
-    g_warp->bar.arrive_and_wait();
-    T r = (T)g_warp->xch[src];
-    g_warp->bar.arrive_and_wait();
-    return r;
-}
-static inline unsigned __ballot_sync(unsigned, int pred) {
-    g_warp->xch[emu_lane] = pred ? 1 : 0;
-    g_warp->bar.arrive_and_wait();
-    unsigned m = 0;
-    for (int l = 0; l < 32; ++l) m |= (unsigned)(g_warp->xch[l] & 1) << l;
-    g_warp->bar.arrive_and_wait();
-    return m;
-}
-template <class T>
-static T __shfl_up_sync(unsigned, T v, int d) { return emu_get(v, emu_lane >= (unsigned)d ? emu_lane - d : emu_lane); }
-template <class T>
-static T __shfl_sync(unsigned, T v, int src) { return emu_get(v, (unsigned)src); }
-static inline unsigned __reduce_max_sync(unsigned, unsigned v) {
-    g_warp->xch[emu_lane] = v;
-    g_warp->bar.arrive_and_wait();
-    unsigned m = 0;
-    for (int l = 0; l < 32; ++l) m = std::max(m, (unsigned)g_warp->xch[l]);
-    g_warp->bar.arrive_and_wait();
-    return m;
-}
-static inline void __syncthreads() { g_cta.bar->arrive_and_wait(); }
-static inline int __syncthreads_count(int pred) {
-    g_cta.xch[threadIdx.x] = pred ? 1 : 0;
-    g_cta.bar->arrive_and_wait();
-    int c = 0;
-    for (int v : g_cta.xch) c += v;
-    g_cta.bar->arrive_and_wait();
-    return c;
-}
-static inline int __syncthreads_or(int pred) { return __syncthreads_count(pred) > 0; }
-static inline int __popc(unsigned x) { return __builtin_popcount(x); }
-static inline int __ffs(unsigned x) { return __builtin_ffs((int)x); }
-static inline int __clz(unsigned x) { return x ? __builtin_clz(x) : 32; }
-static inline unsigned atomicAdd(uint32_t* p, uint32_t v) { return std::atomic_ref<uint32_t>(*p).fetch_add(v); }
-static inline unsigned atomicOr(uint32_t* p, uint32_t v) { return std::atomic_ref<uint32_t>(*p).fetch_or(v); }
-static inline unsigned atomicMin(uint32_t* p, uint32_t v) {
-    std::atomic_ref<uint32_t> a(*p);
-    uint32_t cur = a.load();
-    while (v < cur && !a.compare_exchange_weak(cur, v)) {
-    }
-    return cur;
-}
-
-#define __global__
-#define __device__
-#define __host__
-#define __forceinline__ inline
-#define __restrict__ __restrict
-#define __launch_bounds__(...)
-#define __shared__ static
-#define __align__(n) alignas(n)
-
-struct uint4 {
-    unsigned x, y, z, w;
-};
-static inline uint4 make_uint4(unsigned a, unsigned b, unsigned c, unsigned d) { return uint4{a, b, c, d}; }
+#include "cuda_emu.h"
 
 #include "constants.inc"
 alignas(16) static unsigned char g_dyn_smem[(size_t)kLSlots * 20];  // the larger of the two CTA kernels' needs
@@ -112,42 +18,6 @@ alignas(16) static unsigned char g_dyn_smem[(size_t)kLSlots * 20];  // the large
 #include "warp_local.inc"
 #include "cta_round.inc"
 #include "warp_round.inc"
-
-template <class T>
-static T* guarded(const T* src, size_t count, std::vector<std::pair<void*, size_t>>& maps) {
-    const size_t pg = (size_t)sysconf(_SC_PAGESIZE);
-    const size_t bytes = count * sizeof(T);
-    const size_t body = (bytes + pg - 1) / pg * pg;
-    const size_t total = body + 2 * pg;
-    char* m = (char*)mmap(nullptr, total, PROT_READ | PROT_WRITE, MAP_PRIVATE | MAP_ANONYMOUS, -1, 0);
-    mprotect(m, pg, PROT_NONE);
-    mprotect(m + pg + body, pg, PROT_NONE);
-    maps.push_back({m, total});
-    T* p = (T*)(m + pg + body - bytes);
-    if (bytes) memcpy(p, src, bytes);
-    return p;
-}
-
-template <class F>
-static void run_grid(unsigned grid, unsigned threads, F body) {
-    gridDim.x = grid;
-    blockDim.x = threads;
-    for (unsigned b = 0; b < grid; ++b) {
-        g_cta.bar = std::make_unique<std::barrier<>>(threads);
-        g_cta.xch.assign(threads, 0);
-        std::vector<EmuWarp> warps(threads / 32);
-        std::vector<std::thread> th;
-        for (unsigned i = 0; i < threads; ++i)
-            th.emplace_back([&, b, i] {
-                blockIdx.x = b;
-                threadIdx.x = i;
-                emu_lane = i & 31;
-                g_warp = &warps[i >> 5];
-                body();
-            });
-        for (auto& t : th) t.join();
-    }
-}
 
 // The initial local sort of one block: the warp kernel (unless use_warp is
 // 0: then every local unit is marked for the CTA kernel), then the CTA kernel.

@@ -1,0 +1,184 @@
+"""The 2-bit Insert kernel (Section 5's stable merge) run on the CPU.
+
+The text of ``insert_kernel`` and of the dictionary layout it writes is cut
+out of csrc/insert.cu and csrc/sbwt_internal.cuh and compiled for the host
+with tests/emu/cuda_emu.h (one thread per GPU thread, warp intrinsics and CTA
+barriers emulated, every array between inaccessible pages).  Its output
+dictionary is compared, block by block, with the oracle's Insert (new symbol
+i on row g_sa[i] + i, the old rows in order around them) packed into the
+same layout here: 2-bit codes, terminator mask, 16-bit counters relative to
+the superblock, and the per-superblock totals.  The merge does not need a
+BWT, so old rows, new symbols and the non-decreasing g_sa are drawn at
+random, sparse, dense and clustered.  No GPU is used."""
+import ctypes
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CSRC = os.path.join(ROOT, "paper_1410_0562_gb300", "csrc")
+EMU = os.path.join(os.path.dirname(os.path.abspath(__file__)), "emu", "insert_emulation.cpp")
+
+CODE = {ord("A"): 0, ord("C"): 1, ord("G"): 2, ord("T"): 3}
+SUPER_ROWS = 1 << 16
+BLOCK = np.dtype([("s0", "<u8"), ("s1", "<u8"), ("dm", "<u8"), ("cnt", "<u8")])
+
+
+def _cut(text, start, end):
+    i = text.index(start)
+    return text[i:text.index(end, i)]
+
+
+@pytest.fixture(scope="module")
+def emu(tmp_path_factory):
+    if not shutil.which("g++"):
+        pytest.skip("g++ is not available")
+    d = tmp_path_factory.mktemp("insemu")
+    ins = open(os.path.join(CSRC, "insert.cu")).read()
+    hdr = open(os.path.join(CSRC, "sbwt_internal.cuh")).read()
+    (d / "dict.inc").write_text(_cut(hdr, "constexpr int kOccShift = 6;",
+                                     "// rank(c, i) within i's superblock: the block counter"))
+    (d / "scan.inc").write_text(_cut(hdr, "struct SumOp {", "// Launch bookkeeping"))
+    (d / "insert.inc").write_text(_cut(ins, "constexpr int kInsertThreads", "// ------------------------------------------------"
+                                                                 "---------------------------\n// The same merge"))
+    lib = d / "libinsemu.so"
+    subprocess.check_call(["g++", "-O1", "-std=c++20", "-shared", "-fPIC", "-pthread", "-I", str(d), "-o", str(lib),
+                           EMU])
+    L = ctypes.CDLL(str(lib))
+    P, U64 = ctypes.c_void_p, ctypes.c_uint64
+    L.emu_insert.argtypes = [P, U64, P, P, ctypes.c_int, U64, P, P, U64, P, P]
+    L.emu_insert.restype = ctypes.c_int
+    return L
+
+
+def pack_dict(B: np.ndarray) -> np.ndarray:
+    """B (bytes over ACGT and '$') in the 2-bit dictionary layout: 64 rows per
+    block, codes LSB first, terminators as code 0 plus a mask bit, counts of
+    each code before the block within its superblock of 2^16 rows."""
+    n = len(B)
+    nb = (n >> 6) + 1
+    codes = np.zeros(nb * 64, np.uint64)
+    dollar = np.zeros(nb * 64, np.uint64)
+    lut = np.zeros(256, np.uint64)
+    for c, v in CODE.items():
+        lut[c] = v
+    codes[:n] = lut[B]
+    dollar[:n] = B == ord("$")
+    codes = codes.reshape(nb, 64)
+    dollar = dollar.reshape(nb, 64)
+    sh2 = (2 * np.arange(32)).astype(np.uint64)
+    out = np.zeros(nb, BLOCK)
+    out["s0"] = np.bitwise_or.reduce(codes[:, :32] << sh2, axis=1)
+    out["s1"] = np.bitwise_or.reduce(codes[:, 32:] << sh2, axis=1)
+    out["dm"] = np.bitwise_or.reduce(dollar << np.arange(64).astype(np.uint64), axis=1)
+    counts = np.stack([((codes == c) & (dollar == 0)).sum(axis=1) for c in range(4)], axis=1).astype(np.int64)
+    excl = np.cumsum(counts, axis=0) - counts
+    first = (np.arange(nb) // 1024) * 1024
+    rel = (excl - excl[first]).astype(np.uint64)
+    out["cnt"] = rel[:, 0] | (rel[:, 1] << 16) | (rel[:, 2] << 32) | (rel[:, 3] << 48)
+    return out
+
+
+def super_totals(B: np.ndarray) -> np.ndarray:
+    nb = (len(B) >> 6) + 1
+    nsb = (nb + 1023) // 1024
+    tot = np.zeros((nsb, 4), np.uint32)
+    for s in range(nsb):
+        chunk = B[s * SUPER_ROWS:(s + 1) * SUPER_ROWS]
+        for c, v in CODE.items():
+            tot[s, v] = np.count_nonzero(chunk == c)
+    return tot.ravel()
+
+
+def plan(gsa: np.ndarray, n_new: int) -> np.ndarray:
+    """First new symbol of every superblock: |{i : g_sa[i] + i < S * 2^16}|."""
+    nb = (n_new >> 6) + 1
+    nsb = (nb + 1023) // 1024
+    r = gsa.astype(np.int64) + np.arange(len(gsa))
+    return np.searchsorted(r, np.arange(nsb + 1) * SUPER_ROWS, side="left").astype(np.uint32)
+
+
+def run(emu, B_ext, bint, gsa, width=4, ins_plan=None):
+    n_ext, n_int = len(B_ext), len(bint)
+    n_new = n_ext + n_int
+    old = pack_dict(B_ext)
+    codes = np.array([255 if b == ord("$") else CODE[int(b)] for b in bint], np.uint8)
+    g = np.ascontiguousarray(gsa, np.uint32 if width == 4 else np.uint64)
+    p = plan(gsa, n_new) if ins_plan is None else ins_plan
+    nb = (n_new >> 6) + 1
+    nsb = (nb + 1023) // 1024
+    new = np.zeros(nb, BLOCK)
+    tot = np.zeros(4 * nsb, np.uint32)
+    err = ctypes.c_uint32(0)
+    ptr = lambda a: ctypes.c_void_p(a.ctypes.data)  # noqa: E731
+    assert emu.emu_insert(ptr(old), n_ext, ptr(codes), ptr(g), width, n_int, ptr(p), ptr(new), n_new, ptr(tot),
+                          ctypes.byref(err)) == 0
+    return new, tot, err.value
+
+
+def random_case(rng, n_ext, n_int, kind, p_dollar=0.05):
+    sym = np.frombuffer(b"ACGT", np.uint8)
+    B_ext = rng.choice(sym, size=n_ext)
+    B_ext[rng.random(n_ext) < p_dollar] = ord("$")
+    bint = rng.choice(sym, size=n_int)
+    bint[rng.random(n_int) < p_dollar] = ord("$")
+    if kind == "uniform":
+        gsa = np.sort(rng.integers(0, n_ext + 1, size=n_int))
+    elif kind == "clustered":  # runs of equal g_sa: long runs of consecutive new rows
+        anchors = np.sort(rng.integers(0, n_ext + 1, size=max(1, n_int // 200)))
+        gsa = np.sort(rng.choice(anchors, size=n_int))
+    else:  # every new symbol at one place
+        gsa = np.full(n_int, int(rng.integers(0, n_ext + 1)))
+    return B_ext.astype(np.uint8), bint.astype(np.uint8), gsa.astype(np.uint64)
+
+
+def check(emu, B_ext, bint, gsa, width=4):
+    new, tot, err = run(emu, B_ext, bint, gsa, width)
+    expect = oracle.insert(B_ext, bint, gsa)
+    assert err == 0
+    want = pack_dict(expect)
+    for f in ("s0", "s1", "dm", "cnt"):
+        bad = np.nonzero(new[f] != want[f])[0]
+        assert len(bad) == 0, f"{f} differs in blocks {bad[:8].tolist()}"
+    assert np.array_equal(tot, super_totals(expect))
+
+
+def test_worked_example(emu):
+    """The two-read example of the readings: B_ext = C$A after read AC; read
+    A adds B_int = A$ at g_sa = [1, 1]; the result is CA$$A."""
+    check(emu, np.frombuffer(b"", np.uint8), np.frombuffer(b"C$A", np.uint8), np.zeros(3, np.uint64))
+    check(emu, np.frombuffer(b"C$A", np.uint8), np.frombuffer(b"A$", np.uint8), np.array([1, 1], np.uint64))
+    assert bytes(oracle.insert(b"C$A", b"A$", [1, 1])) == b"CA$$A"
+
+
+@pytest.mark.parametrize("n_ext,n_int,kind", [
+    (0, 1, "uniform"), (0, 5000, "uniform"), (1, 1, "uniform"), (63, 2, "uniform"), (64, 64, "one"),
+    (65, 200, "uniform"), (4095, 60, "uniform"), (4096, 9000, "clustered"), (3000, 3000, "one"),
+    (70_000, 700, "uniform"), (70_000, 25_000, "clustered"), (65_536 - 100, 300, "uniform"),
+    (20_000, 110_000, "uniform"),
+])
+def test_merge_matches_the_oracle(emu, n_ext, n_int, kind):
+    rng = np.random.default_rng(n_ext * 7 + n_int)
+    B_ext, bint, gsa = random_case(rng, n_ext, n_int, kind)
+    check(emu, B_ext, bint, gsa, width=4 if (n_ext + n_int) % 2 else 8)
+
+
+def test_inconsistent_plan_is_flagged_without_leaving_the_arrays(emu):
+    """A g_sa that is not non-decreasing (impossible from ComputeRanks) puts
+    two new symbols on one row or outside their superblock: the kernel flags
+    bit 10 and every access stays inside the arrays (guard pages)."""
+    rng = np.random.default_rng(9)
+    B_ext, bint, gsa = random_case(rng, 5000, 800, "uniform")
+    bad = gsa.copy()[::-1].copy()  # decreasing
+    _, _, err = run(emu, B_ext, bint, bad)
+    assert err & 1024
+    # a plan that names more new symbols than there are
+    p = plan(gsa, len(B_ext) + len(bint))
+    p[-1] = len(bint) + 5
+    _, _, err = run(emu, B_ext, bint, gsa, ins_plan=p)
+    assert err & 1024
