@@ -180,13 +180,18 @@ int sbwt_set_capture(sbwt_index *idx, int on);
 int sbwt_get_stage(sbwt_index *idx, int stage, void *out, uint64_t cap, uint64_t *count_out);
 
 /* ---- batched form: CUDA-graph replay --------------------------------------
- * With replay on, an append whose plan, sizes, index state (rows, reads, the
- * buffer holding the current dictionary) and buffers repeat an earlier
- * append's is captured into a CUDA graph the second time it is seen and
- * replayed from then on, so the whole block pipeline of Algorithm 1 costs
- * one launch.  Results are identical with replay on or off.  Up to 8 graphs
- * are kept; they are dropped when a buffer grows and by sbwt_destroy.  Off
- * by default. */
+ * With replay on, every append is captured into a CUDA graph and launched as
+ * one unit: the whole block pipeline of Algorithm 1 (every block's
+ * ConstructSA, ComputeRanks, B_int/g_sa and Insert, on both streams) is one
+ * graph launch.  The library keeps one instantiated graph per pipeline shape
+ * (the sequence of kernels an append launches, which follows from its block
+ * count and longest read) and updates it in place with each append's sizes,
+ * buffers and index state, so appends of different reads into a growing
+ * index reuse it.  sbwt_get_kernel_stats counts the graph launches, updates
+ * and instantiations as "host:graph_launch", "host:graph_update" and
+ * "host:graph_instantiate".  Results are identical with replay on or off.
+ * Up to 8 graphs are kept; sbwt_destroy and turning replay off drop them.
+ * Off by default. */
 int sbwt_set_graph_replay(sbwt_index *idx, int on);
 
 /* Autotunes M (suffixes per block, Algorithm 1) for reads like the given

@@ -80,7 +80,7 @@ struct sbwt_index {
     DevBuf reads, offsets, text, term, err;
     DevBuf keys, keys_alt, vals, vals_alt, sa, sa2, rank, act_pos0, act_pos1, act_suf0, act_suf1, loc_act, loc_next;
     DevBuf units;
-    DevBuf radix_temp, chunks, count_log, g, gsa, bint, sb_tot;
+    DevBuf radix_temp, chunks, count_log, g, gsa, bint, sb_tot, ins_plan;
     DevBuf out_bytes, q_codes, q_ks, q_out, c_pats, c_offs;
 
     uint32_t* h_err = nullptr;      // pinned
@@ -91,15 +91,15 @@ struct sbwt_index {
     PlanSummary* h_summary = nullptr;
 
     Launcher L;
-    // CUDA graphs of whole appends, keyed by everything a launch depends on
+    // Instantiated CUDA graphs of whole appends, one per pipeline shape (the
+    // sequence of kernels an append launches); each append is captured and
+    // updates the graph of its shape in place before it is launched.
     struct GraphEntry {
-        std::vector<unsigned long long> sig;
         cudaGraphExec_t exec = nullptr;
         Launcher::GraphLog log;
     };
     bool graph_replay = false;
-    std::vector<GraphEntry> graphs;                    // most recent last
-    std::vector<std::vector<unsigned long long>> seen;  // signatures run once, eagerly
+    std::vector<GraphEntry> graphs;  // most recent last
     void* server = nullptr;           // continuous-batching server, when serving
     std::thread::id server_worker;    // the only thread that may change the index then
     bool capture = false;
@@ -113,7 +113,7 @@ struct sbwt_index {
                                   &keys_alt,   &vals,     &vals_alt,  &sa,       &rank,     &act_pos0,
                                   &act_pos1,   &act_suf0, &act_suf1,  &loc_act,  &loc_next, &units,     &sa2,
                                   &radix_temp, &chunks,
-                                  &count_log,  &g,        &gsa,       &bint,     &sb_tot,   &out_bytes,
+                                  &count_log,  &g,        &gsa,       &bint,     &sb_tot,   &ins_plan, &out_bytes,
                                   &q_codes,    &q_ks,     &q_out,     &plan,     &c_pats,   &c_offs};
         for (auto& d : dict) {
             v.push_back(&d.blocks);
@@ -293,6 +293,7 @@ std::vector<Need> buffer_needs(sbwt_index* idx, const Plan& p, bool host_input, 
     // superblock totals, then the superblock scan's per-256 totals (insert.cu)
     const size_t sb_words = (size_t)((nsb * dict_codes(cb) + 3) & ~3ull);
     v.push_back({&idx->sb_tot, sb_words * 4 + (size_t)(nsb / 256 + 1) * 8 * dict_codes(cb)});
+    v.push_back({&idx->ins_plan, (size_t)(nsb + 1) * 4});  // Insert's first new symbol per superblock
     for (int k = 0; k < 3; ++k) {
         if (k == idx->cur) continue;
         v.push_back({&idx->dict[k].blocks, (size_t)dict_blocks(n_final) * dict_block_bytes(cb), true});
@@ -303,10 +304,11 @@ std::vector<Need> buffer_needs(sbwt_index* idx, const Plan& p, bool host_input, 
 }
 
 void drop_graphs(sbwt_index* idx) {
-    for (auto& g : idx->graphs)
+    for (auto& g : idx->graphs) {
         if (g.exec) cudaGraphExecDestroy(g.exec);
+        idx->L.recycle(g.log);
+    }
     idx->graphs.clear();
-    idx->seen.clear();
 }
 
 size_t rounded(size_t b) { return (b + 255) & ~(size_t)255; }
@@ -369,11 +371,12 @@ int reserve(sbwt_index* idx, const std::vector<Need>& needs) {
     }
     if (dict_host && !idx->dict_host) {
         if (int rc = move_dicts_to_host(idx)) return rc;
-        if (!idx->graphs.empty()) drop_graphs(idx);
     }
+    // (a buffer that grows or moves needs no graph dropped: every append's
+    // capture names the current buffers, and a graph is updated from it
+    // before each launch)
     for (const Need& n : needs) {
         const bool host = n.dict && dict_host;
-        if ((n.buf->bytes < rounded(n.bytes) || n.buf->host != host) && !idx->graphs.empty()) drop_graphs(idx);
         if (int rc = grow(*n.buf, n.bytes, host)) return rc;
     }
     return SBWT_OK;
@@ -421,13 +424,15 @@ void run_block(sbwt_index* idx, const BlockPlan& bp, const uint64_t* d_offsets, 
                                (const unsigned long long*)src.super.p, (const unsigned long long*)src.C.p, n_ext,
                                prepend ? 0 : m_ext, (IdxT*)idx->g.p, (uint32_t*)idx->err.p, idx->code_bits);
     cudaStreamWaitEvent(s, idx->ev_sorted[q & 1], 0);
+    // the 2-bit Insert takes its plan (first new symbol per superblock) from the gather
+    uint32_t* plan = idx->code_bits == 2 ? (uint32_t*)idx->ins_plan.p : nullptr;
     launch_bint_gather<IdxT>(L, text, term, bp.base, b.sa, (const IdxT*)idx->g.p, n, (uint8_t*)idx->bint.p,
-                             (IdxT*)idx->gsa.p, idx->code_bits);
+                             (IdxT*)idx->gsa.p, idx->code_bits, plan, dict_supers(n_ext + bp.n_int), kSuperShift);
     cudaEventRecord(idx->ev_consumed[q & 1], s);
     launch_insert<IdxT>(L, (const void*)src.blocks.p, n_ext, (const uint8_t*)idx->bint.p,
-                        (const IdxT*)idx->gsa.p, bp.n_int, (void*)dst.blocks.p,
+                        (const IdxT*)idx->gsa.p, bp.n_int, plan, (void*)dst.blocks.p,
                         (unsigned long long*)dst.super.p, (unsigned long long*)dst.C.p, m_ext + (bp.j1 - bp.j0),
-                        (uint32_t*)idx->sb_tot.p, idx->code_bits);
+                        (uint32_t*)idx->sb_tot.p, (uint32_t*)idx->err.p, idx->code_bits);
 }
 
 Plan host_plan(const uint64_t* h_off, uint64_t m_new, uint64_t M) {
@@ -567,49 +572,64 @@ int append_impl(sbwt_index* idx, const uint8_t* d_reads, const uint64_t* d_offse
 
     const Launcher::GraphLog* replayed = nullptr;
     if (idx->graph_replay) {
-        // replay a captured graph of an identical append (same plan, sizes,
-        // index state and buffers); capture one on the second sighting
-        std::vector<unsigned long long> sig = {m_new, p.npos, p.nbytes, idx->n, idx->m, (unsigned long long)idx->cur,
-                                               p.idx64, L.profiling, std::hash<std::string>{}(L.only),
-                                               (unsigned long long)(uintptr_t)d_reads,
-                                               (unsigned long long)(uintptr_t)d_offsets, p.blocks.size(),
-                                               (unsigned long long)p.prepend};
-        for (const BlockPlan& b : p.blocks) sig.insert(sig.end(), {b.j0, b.j1, b.n_int, b.base, b.max_len});
-        for (DevBuf* b : idx->all_bufs()) sig.push_back((unsigned long long)(uintptr_t)b->p);
-        auto it = std::find_if(idx->graphs.begin(), idx->graphs.end(),
-                               [&](const sbwt_index::GraphEntry& g) { return g.sig == sig; });
-        if (it == idx->graphs.end() && std::find(idx->seen.begin(), idx->seen.end(), sig) != idx->seen.end()) {
-            sbwt_index::GraphEntry g;
-            g.sig = sig;
-            cudaGraph_t graph = nullptr;
-            L.capture = &g.log;
-            cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
-            if (e == cudaSuccess) {
-                enqueue();
-                e = cudaStreamEndCapture(s, &graph);
-            }
-            L.capture = nullptr;
-            if (e == cudaSuccess) e = cudaGraphInstantiate(&g.exec, graph, 0);
+        // The batched form: the append is captured into a graph; the graph
+        // instantiated for the same pipeline shape (the same kernels in the
+        // same order) is updated in place with this append's sizes, buffers
+        // and index state, and the whole append is launched as one unit.  A
+        // shape seen for the first time is instantiated (at most 8 kept).
+        sbwt_index::GraphEntry g;
+        cudaGraph_t graph = nullptr;
+        L.capture = &g.log;
+        cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            enqueue();
+            e = cudaStreamEndCapture(s, &graph);
+        }
+        L.capture = nullptr;
+        if (e != cudaSuccess) {
             if (graph) cudaGraphDestroy(graph);
+            L.recycle(g.log);
+            cudaGetLastError();
+            return SBWT_EDEVICE;
+        }
+        auto it = std::find_if(idx->graphs.begin(), idx->graphs.end(), [&](const sbwt_index::GraphEntry& x) {
+            return x.log.launches == g.log.launches && x.log.timed.size() == g.log.timed.size();
+        });
+        if (it != idx->graphs.end()) {
+            cudaGraphExecUpdateResultInfo info;
+            if (cudaGraphExecUpdate(it->exec, graph, &info) == cudaSuccess) {
+                L.recycle(it->log);
+                it->log = std::move(g.log);
+                L.add_host("host:graph_update", 0.0);
+            } else {  // not updatable after all: instantiate this shape anew
+                cudaGetLastError();
+                cudaGraphExecDestroy(it->exec);
+                L.recycle(it->log);
+                idx->graphs.erase(it);
+                it = idx->graphs.end();
+            }
+        }
+        if (it == idx->graphs.end()) {
+            e = cudaGraphInstantiate(&g.exec, graph, 0);
             if (e != cudaSuccess) {
+                cudaGraphDestroy(graph);
+                L.recycle(g.log);
                 cudaGetLastError();
                 return SBWT_EDEVICE;
             }
             if (idx->graphs.size() >= 8) {
                 cudaGraphExecDestroy(idx->graphs.front().exec);
+                L.recycle(idx->graphs.front().log);
                 idx->graphs.erase(idx->graphs.begin());
             }
             idx->graphs.push_back(std::move(g));
             it = idx->graphs.end() - 1;
+            L.add_host("host:graph_instantiate", 0.0);
         }
-        if (it != idx->graphs.end()) {
-            if (cudaGraphLaunch(it->exec, s) != cudaSuccess) return SBWT_EDEVICE;
-            replayed = &it->log;
-        } else {
-            if (idx->seen.size() >= 8) idx->seen.erase(idx->seen.begin());
-            idx->seen.push_back(sig);
-            enqueue();
-        }
+        cudaGraphDestroy(graph);
+        if (cudaGraphLaunch(it->exec, s) != cudaSuccess) return SBWT_EDEVICE;
+        L.add_host("host:graph_launch", 0.0);
+        replayed = &it->log;
     } else {
         enqueue();
     }
@@ -793,6 +813,15 @@ cudaError_t Launcher::resolve() {
     pending_.clear();
     cudaGetLastError();
     return err;
+}
+
+void Launcher::recycle(GraphLog& g) {
+    for (const Pending& p : g.timed) {
+        free_events_.push_back(p.a);
+        free_events_.push_back(p.b);
+    }
+    g.timed.clear();
+    g.launches.clear();
 }
 
 void Launcher::add_host(const char* name, double ms) {

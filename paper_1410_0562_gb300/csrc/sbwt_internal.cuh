@@ -297,6 +297,8 @@ class Launcher {
     // After a replay of a captured graph (stream idle): counts its launches
     // and, if it was captured with profiling, folds in its event times.
     cudaError_t account_replay(const GraphLog& g);
+    // Returns the events of a graph log that no graph uses any more.
+    void recycle(GraphLog& g);
 
     int before(const char* name, double fixed, double per_unit = 0, const uint32_t* d_units = nullptr);
     void after(int token);

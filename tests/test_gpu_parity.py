@@ -307,9 +307,28 @@ def test_full_size_repetitive_reads():
     check_full_size(w, idx.bwt(), samples=2)
 
 
+def test_graph_replay_serves_different_appends_into_a_growing_index():
+    """The batched form: every append is one graph launch; the graph
+    instantiated for a pipeline shape is updated in place for the later
+    appends of that shape, which carry other reads (other host buffers) into
+    a larger index."""
+    w = readgen.tiny()
+    cuts = [0, 150, 300, 450, 600, 750, 900, 1000]
+    idx = sb.SetBWT(b"ACGT", block_suffixes=20_000)  # one block per append
+    sb.sbwt_set_graph_replay(idx.handle, True)
+    for a, b in zip(cuts[:-1], cuts[1:]):
+        reads = w.reads[int(w.offsets[a]):int(w.offsets[b])].copy()  # a fresh host buffer each time
+        idx.append(reads, w.offsets[a:b + 1] - w.offsets[a])
+        assert np.array_equal(idx.bwt(), oracle.bwt(w.reads[: int(w.offsets[b])], w.offsets[: b + 1]))
+    counts = {s["name"]: s["launches"] for s in sb.sbwt_get_kernel_stats(idx.handle)}
+    assert counts["host:graph_launch"] == len(cuts) - 1
+    assert counts["host:graph_instantiate"] == 1
+    assert counts["host:graph_update"] == len(cuts) - 2
+
+
 def test_graph_replay_matches_eager():
-    """The batched form: repeated identical appends are captured into a CUDA
-    graph and replayed; every replay gives the oracle's B."""
+    """The batched form: repeated identical appends run as graph launches;
+    every one gives the oracle's B."""
     w = readgen.tiny()
     expect = oracle.bwt(w.reads, w.offsets)
     idx = sb.SetBWT(b"ACGT", block_suffixes=20_000)  # several blocks per append
