@@ -3,17 +3,33 @@
 A step builds the BWT of the whole workload from an empty index: one
 ``sbwt_append`` of every read, which runs Algorithm 1 of arXiv 1410.0562 over
 all its blocks (ConstructSA, B_int, ComputeRanks, the g[SA_int] gather,
-Insert) in the library's CUDA kernels.  Default workload: 1M x 100 bp reads
-from a seeded 10 Mbp i.i.d. genome with 1% substitutions (uniform offsets and
-strands), blocks of 2^24 suffixes, 32-bit indices -- a synthetic stand-in
-shaped like the paper's short-read set.
+Insert) in the library's CUDA kernels.  Headline workload (``value``): 1M x
+100 bp reads from a seeded 10 Mbp i.i.d. genome with 1% substitutions
+(uniform offsets and strands), blocks of 2^24 suffixes, 32-bit indices -- a
+synthetic stand-in shaped like the paper's short-read set.
 
 ``value`` is timed with CUDA events on the library's stream, inputs already in
 HBM; between timed steps a 256 MB buffer is written to flush L2 (outside the
 timed region).  ``e2e`` times the host-buffer C-ABI call: H2D of the reads
-from pinned memory, the build, and the D2H of B.  ``--impl reference`` times
-the CPU oracle (a plain single-threaded suffix sort by direct comparison) on a
-bounded sample of the same workload.
+from pinned memory, the build, and the D2H of B.  The same line carries the
+other workloads as keys, each timed the same way:
+
+* ``batched``: 2M reads of U[50, 250] bp from a 50 Mbp genome, 64-bit
+  indices: the plain per-block pipeline (every step of every block in turn
+  on one stream, blocks of 2^24, occurrence sampling 64, eager launches)
+  against the batched form (block size and sampling from the autotuner,
+  block sorts overlapping the ranking and Insert of earlier blocks, every
+  append one CUDA-graph launch), with per-kernel fractions of the HBM peak;
+* ``long``: 20k log-normal long reads (mean 10 kbp, 10% errors) from a 100 Mbp
+  genome, plain and batched;
+* ``served``: a resident index of 20M x 100 bp reads (2 Gbp) under an 8 GB HBM
+  budget, then 48 append requests of 10k-1M reads served closed-loop and as
+  Poisson streams at 0.5x and 0.9x of the sustained rate (p50/p99 latency),
+  a profiled append against the DRAM-resident dictionary, and a 2M-read index
+  served from the pinned host tier under a 512 MB budget.
+
+``--impl reference`` times the CPU oracle (a plain single-threaded suffix sort
+by direct comparison) on a bounded sample of the same workload.
 
 Under torchrun (N > 1) each rank builds an independent index of its own read
 set (replicas: the path has no exchange step), so per-GPU work is fixed.
@@ -51,13 +67,12 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="short", choices=["short", "tiny", "serve", "wide"])
+    ap.add_argument("--workload", default="short", choices=["short", "tiny", "wide"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--no-batched", action="store_true", help="skip the batched-form measurement")
-    ap.add_argument("--no-serving", action="store_true", help="skip the served-form measurement")
-    ap.add_argument("--profile-steps", type=int, default=None,
-                    help="steps run under per-kernel event timing (default: the timed steps)")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched workload and form")
+    ap.add_argument("--no-long", action="store_true", help="skip the long-read workload")
+    ap.add_argument("--no-serving", action="store_true", help="skip the served workload")
     return ap.parse_args()
 
 
@@ -296,6 +311,187 @@ def run_reference(args):
     return 0
 
 
+class Timer:
+    """Builds from device-resident reads, timed with CUDA events on the
+    library stream; L2 is flushed (a 256 MB write) before every timed step,
+    outside the events."""
+
+    def __init__(self, torch, stream, flush):
+        self.torch, self.stream, self.flush = torch, stream, flush
+
+    def steps(self, step, k: int, warmup: int):
+        torch = self.torch
+        for _ in range(warmup):
+            step()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+        for i in range(k):
+            with torch.cuda.stream(self.stream):
+                self.flush.fill_(i & 0xFF)
+                ev[i][0].record(self.stream)
+            step()
+            ev[i][1].record(self.stream)
+        torch.cuda.synchronize()
+        return [a.elapsed_time(b) for a, b in ev]
+
+
+def kernel_table(stats, peak):
+    """Per-kernel time, launches, algorithmic GB/s and fraction of the HBM peak."""
+    out = {}
+    for s in sorted((s for s in stats if not s["name"].startswith("host:")), key=lambda s: -s["ms"]):
+        gbps = s["bytes"] / (s["ms"] / 1e3) / 1e9 if s["ms"] > 0 else None
+        out[s["name"]] = {"launches": s["launches"], "ms_per_step": round(s["ms"], 4),
+                          "GBps": round(gbps, 1) if gbps else None, "frac": round(gbps / peak, 3) if gbps else None}
+    return out
+
+
+def profiled_step(sb, idx, step):
+    """One untimed step with every kernel bracketed by events."""
+    sb.sbwt_reset_kernel_stats(idx.handle)
+    sb.sbwt_set_profiling(idx.handle, True)
+    step()
+    stats = sb.sbwt_get_kernel_stats(idx.handle)
+    sb.sbwt_set_profiling(idx.handle, False)
+    sb.sbwt_reset_kernel_stats(idx.handle)
+    return stats
+
+
+def host_counts(stats):
+    return {s["name"][5:]: s["launches"] for s in stats if s["name"].startswith("host:graph")}
+
+
+def check_b(B, w):
+    """Cheap checks of a benchmarked B that tie the number to a correct
+    result: its length, the terminator count, the symbol multiset and the
+    terminator rows (row r holds the last symbol of read r)."""
+    assert len(B) == w.bases + w.m
+    counts = np.bincount(B, minlength=256)
+    expect = np.bincount(w.reads, minlength=256)
+    expect[ord("$")] += w.m
+    assert np.array_equal(counts, expect), "symbol multiset differs from the reads"
+    lens = np.diff(w.offsets.astype(np.int64))
+    last = np.where(lens > 0, w.reads[np.maximum(w.offsets[1:].astype(np.int64) - 1, 0)], ord("$"))
+    assert np.array_equal(B[: w.m], last.astype(np.uint8)), "terminator rows differ"
+
+
+def measure_forms(sb, torch, timer, w, local, args, peak, plain_M, candidates, stream, dist=None):
+    """The plain per-block pipeline (Algorithm 1's loop: every step of every
+    block in turn on one stream, eager launches, blocks of plain_M suffixes,
+    occurrence sampling 64) and the batched form (block size and occurrence
+    sampling from the autotuner, each block's suffix sort overlapping the
+    previous blocks' ranking and Insert, every append one CUDA-graph launch)
+    on the same device-resident reads; both must give the same B."""
+    d_reads = torch.from_numpy(w.reads).to("cuda")
+    d_off = torch.from_numpy(w.offsets.astype(np.int64)).to("cuda")
+    out = {"workload": w.name, "reads": w.m, "bases": w.bases, "index_bits": w.index_bits}
+    idx = sb.SetBWT(w.alphabet, index_bits=w.index_bits, block_suffixes=plain_M, stream=stream.cuda_stream,
+                    device=local)
+    sb.sbwt_set_block_overlap(idx.handle, False)
+
+    def step():
+        idx.reset()
+        idx.append_device(d_reads.data_ptr(), d_off.data_ptr(), w.m)
+
+    ms = timer.steps(step, args.steps, args.warmup)
+    tot = max_over_ranks(sum(ms), dist)
+    kern = kernel_table(profiled_step(sb, idx, step), peak)
+    B = idx.bwt()
+    check_b(B, w)
+    idx.close()
+    out["plain"] = {"value": whole_job_mbps(w.bases, 1, args.steps, tot), "unit": UNIT,
+                    "ms_per_step": tot / args.steps, "block_suffixes": plain_M, "occ_sampling": 64,
+                    "block_overlap": False, "graph_replay": False, "kernels": kern}
+    if args.no_batched:
+        return out
+    idx_b = sb.SetBWT(w.alphabet, index_bits=w.index_bits, stream=stream.cuda_stream, device=local)
+    best_M, best_s, tune = sb.sbwt_autotune(idx_b.handle, d_reads.data_ptr(), d_off.data_ptr(), w.m, candidates,
+                                            [64, 128, 256])
+    sb.sbwt_set_graph_replay(idx_b.handle, True)
+
+    def step_b():
+        idx_b.reset()
+        idx_b.append_device(d_reads.data_ptr(), d_off.data_ptr(), w.m)
+
+    sb.sbwt_reset_kernel_stats(idx_b.handle)
+    ms_b = timer.steps(step_b, args.steps, args.warmup)
+    graphs = host_counts(sb.sbwt_get_kernel_stats(idx_b.handle))
+    tot_b = max_over_ranks(sum(ms_b), dist)
+    kern_b = kernel_table(profiled_step(sb, idx_b, step_b), peak)
+    Bb = idx_b.bwt()
+    assert np.array_equal(Bb, B), "batched form differs from the plain pipeline"
+    idx_b.close()
+    out["batched"] = {"value": whole_job_mbps(w.bases, 1, args.steps, tot_b), "unit": UNIT,
+                      "ms_per_step": tot_b / args.steps, "block_suffixes": int(best_M), "occ_sampling": int(best_s),
+                      "block_overlap": True, "graph_replay": True, "graph_counts": graphs,
+                      "autotune_ms": {f"{k[0]}/{k[1]}": round(v, 3) for k, v in tune.items()}, "kernels": kern_b}
+    out["batched_over_plain"] = out["batched"]["value"] / out["plain"]["value"]
+    del d_reads, d_off
+    return out
+
+
+def measure_served(sb, torch, w_res, requests, local, stream, peak):
+    """The serving workload: a resident index of the 20M x 100 bp reads
+    under an 8 GB HBM budget, then the append requests served closed-loop
+    (sustained rate) and as Poisson streams at 0.5x and 0.9x of it; a
+    profiled append of the largest request shows ComputeRanks and Insert
+    against the DRAM-resident dictionary; a 2M-read index under a 512 MB
+    budget serves from the pinned host tier."""
+    d_reads = torch.from_numpy(w_res.reads).to("cuda")
+    d_off = torch.from_numpy(w_res.offsets.astype(np.int64)).to("cuda")
+
+    def fresh(budget=8 << 30):
+        ix = sb.SetBWT(b"ACGT", hbm_budget=budget, index_bits=64, block_suffixes=1 << 25,
+                       stream=stream.cuda_stream, device=local)
+        ix.append_device(d_reads.data_ptr(), d_off.data_ptr(), w_res.m)
+        return ix
+
+    fresh().close()  # sizes the buffers once
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ix = sb.SetBWT(b"ACGT", hbm_budget=8 << 30, index_bits=64, block_suffixes=1 << 25,
+                   stream=stream.cuda_stream, device=local)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+    ix.append_device(d_reads.data_ptr(), d_off.data_ptr(), w_res.m)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    build_ms = e0.elapsed_time(e1)
+    hbm, host = sb.sbwt_memory(ix.handle)
+    n_rows, _ = ix.size()
+    # one profiled append of the largest request into the resident index
+    big = max(requests, key=lambda r: len(r[1]))
+    sb.sbwt_reset_kernel_stats(ix.handle)
+    sb.sbwt_set_profiling(ix.handle, True)
+    ix.append(*big)
+    kern = kernel_table(sb.sbwt_get_kernel_stats(ix.handle), peak)
+    ix.close()
+    report = serving_report(sb, fresh, requests)
+    out = {"workload": w_res.name, "resident_rows": n_rows, "resident_build_ms": build_ms,
+           "resident_build_Mbps": w_res.bases / build_ms / 1e3, "memory_after_build": {"hbm": hbm, "host": host},
+           "requests": len(requests), "request_bases": sum(int(o[-1]) for _, o in requests),
+           "hbm_budget": 8 << 30, "serving": report,
+           "largest_request_append": {"reads": len(big[1]) - 1, "bases": int(big[1][-1]), "kernels": kern}}
+    del d_reads, d_off
+    torch.cuda.empty_cache()
+    # host tier: a 2M-read resident index whose dictionaries live in pinned host memory
+    m2 = 2_000_000
+    small_reads = w_res.reads[: int(w_res.offsets[m2])]
+    small_off = w_res.offsets[: m2 + 1]
+    ix2 = sb.SetBWT(b"ACGT", hbm_budget=512 << 20, index_bits=64, block_suffixes=1 << 21,
+                    stream=stream.cuda_stream, device=local)
+    t = time.perf_counter()
+    ix2.append(small_reads, small_off)
+    build2 = time.perf_counter() - t
+    hbm2, host2 = sb.sbwt_memory(ix2.handle)
+    small_reqs = [r for r in requests if len(r[1]) - 1 <= 100_000][:12]
+    rep2 = measure_serving(sb, ix2, small_reqs)
+    ix2.close()
+    out["host_tier"] = {"resident_reads": m2, "hbm_budget": 512 << 20, "build_s": build2,
+                        "build_Mbps": int(small_off[-1]) / build2 / 1e6, "memory": {"hbm": hbm2, "host": host2},
+                        "serving": rep2}
+    return out
+
+
 def run_gb300(args):
     import torch
 
@@ -313,15 +509,17 @@ def run_gb300(args):
     if dist:
         dist.barrier()
     sb.load()
+    peak, peak_kind = load_peaks()
 
     w = make_workload(args.workload, rank)
     bases = w.bases
     stream = torch.cuda.Stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    timer = Timer(torch, stream, flush)
     idx = sb.SetBWT(w.alphabet, index_bits=w.index_bits, block_suffixes=w.block_suffixes,
                     stream=stream.cuda_stream, device=local)
     d_reads = torch.from_numpy(w.reads).to("cuda")
     d_off = torch.from_numpy(w.offsets.astype(np.int64)).to("cuda")
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     torch.cuda.synchronize()
 
     def step():
@@ -334,29 +532,18 @@ def run_gb300(args):
 
     # one untimed step with every kernel timed: the per-kernel breakdown and
     # the dominant kernel
-    sb.sbwt_reset_kernel_stats(idx.handle)
-    sb.sbwt_set_profiling(idx.handle, True)
-    step()
-    breakdown = [s for s in sb.sbwt_get_kernel_stats(idx.handle) if not s["name"].startswith("host:")]
+    breakdown = [s for s in profiled_step(sb, idx, step) if not s["name"].startswith("host:")]
     dominant = max(breakdown, key=lambda s: s["ms"])["name"]
 
     # timed region: K steps, each bracketed by events on the library stream;
     # inside, only the dominant kernel carries events (for the roofline)
     sb.sbwt_set_profiling_only(idx.handle, dominant)
     sb.sbwt_reset_kernel_stats(idx.handle)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     with Clocks(local) as clk:
-        for k in range(args.steps):
-            with torch.cuda.stream(stream):
-                flush.fill_(k & 0xFF)  # L2 flush, outside the events
-                ev[k][0].record(stream)
-            step()
-            ev[k][1].record(stream)
-        torch.cuda.synchronize()
-    ms_steps = [a.elapsed_time(b) for a, b in ev]
+        ms_steps = timer.steps(step, args.steps, 0)
     all_stats = sb.sbwt_get_kernel_stats(idx.handle)
     stats = [s for s in all_stats if not s["name"].startswith("host:")]
     host_phases = {s["name"][5:]: s["ms"] / args.steps for s in all_stats if s["name"].startswith("host:")}
@@ -365,10 +552,9 @@ def run_gb300(args):
     if dist:
         dist.barrier()
 
-    # the result is the one the oracle pins: spot-check it on this rank
+    # the result the oracle pins: cheap whole-B checks on this rank
     B = idx.bwt()
-    assert len(B) == bases + w.m
-    assert int(np.count_nonzero(B == ord("$"))) == w.m
+    check_b(B, w)
 
     # end to end through the host-buffer C ABI: pinned H2D, build, D2H of B
     e2e = None
@@ -386,81 +572,41 @@ def run_gb300(args):
             rc = sb.load().sbwt_get_bwt(idx.handle, ctypes.c_void_p(out_ptr), bases + w.m, ctypes.byref(got))
             assert rc == 0
 
-        for _ in range(max(1, args.warmup)):
-            e2e_step()
-        torch.cuda.synchronize()
-        e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-                for _ in range(args.steps)]
-        for k in range(args.steps):
-            with torch.cuda.stream(stream):
-                flush.fill_(k & 0xFF)
-                e_ev[k][0].record(stream)
-            e2e_step()
-            e_ev[k][1].record(stream)
-        torch.cuda.synchronize()
-        e_ms = max_over_ranks(float(sum(a.elapsed_time(b) for a, b in e_ev)), dist)
+        e_ms = max_over_ranks(float(sum(timer.steps(e2e_step, args.steps, max(1, args.warmup)))), dist)
+        assert np.array_equal(h_out.numpy(), B)
         e2e = {"value": whole_job_mbps(bases, world, args.steps, e_ms), "unit": UNIT,
                "h2d_bytes_per_step": int(w.reads.nbytes + w.offsets.nbytes),
                "d2h_bytes_per_step": int(bases + w.m)}
+    idx.close()
+    del d_reads, d_off
 
-    # the batched form on the same reads: block size from the autotuner and
-    # the whole append replayed from a captured CUDA graph
-    batched = None
-    if not args.no_batched:
-        idx_b = sb.SetBWT(w.alphabet, index_bits=w.index_bits, stream=stream.cuda_stream, device=local)
-        best_M, tune = sb.sbwt_autotune_block_suffixes(idx_b.handle, d_reads.data_ptr(), d_off.data_ptr(), w.m,
-                                                       [1 << 22, 1 << 23, 1 << 24, 1 << 25, 1 << 26, 1 << 27])
-        sb.sbwt_set_graph_replay(idx_b.handle, True)
-        sb.sbwt_set_profiling_only(idx_b.handle, dominant)
-
-        def step_b():
-            idx_b.reset()
-            idx_b.append_device(d_reads.data_ptr(), d_off.data_ptr(), w.m)
-
-        # the index alternates between two dictionary buffers, so two graphs:
-        # each is seen once eagerly, then captured; replays from then on
-        for _ in range(max(4, args.warmup)):
-            step_b()
-        sb.sbwt_reset_kernel_stats(idx_b.handle)
-        b_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-                for _ in range(args.steps)]
-        torch.cuda.synchronize()
-        for k in range(args.steps):
-            with torch.cuda.stream(stream):
-                flush.fill_(k & 0xFF)
-                b_ev[k][0].record(stream)
-            step_b()
-            b_ev[k][1].record(stream)
-        torch.cuda.synchronize()
-        b_ms = max_over_ranks(float(sum(a.elapsed_time(b) for a, b in b_ev)), dist)
-        b_stats = [s for s in sb.sbwt_get_kernel_stats(idx_b.handle) if not s["name"].startswith("host:")]
-        b_dom = next((s for s in b_stats if s["name"] == dominant), None)
-        Bb = idx_b.bwt()
-        assert np.array_equal(Bb, B), "batched form differs from the plain pipeline"
-        batched = {"value": whole_job_mbps(bases, world, args.steps, b_ms), "unit": UNIT,
-                   "ms_per_step": b_ms / args.steps, "block_suffixes": int(best_M), "graph_replay": True,
-                   "autotune_ms": {str(k): round(v, 3) for k, v in tune.items()},
-                   "gpu_launches": int(sum(s["launches"] for s in b_stats)),
-                   "dominant_kernel_GBps": (b_dom["bytes"] / (b_dom["ms"] / 1e3) / 1e9
-                                            if b_dom and b_dom["ms"] > 0 else None)}
-        idx_b.close()
-
-    # the served form: requests of 10k..200k reads (U[100,150] bp) from the
-    # same genome arriving at an index that holds the whole workload
-    served = None
-    if not args.no_serving and args.workload == "short":
-        g = readgen.genome(10_000_000, 0x14100562 + 2 + 1000 * rank)
-        rs = np.random.default_rng(99 + rank)
-        sizes = np.exp(rs.uniform(np.log(10_000), np.log(200_000), size=24)).astype(np.int64)
-        requests = [readgen.sampled_reads(g, int(mm), rs.integers(100, 151, size=int(mm)), 0.01, 500 + i)
-                    for i, mm in enumerate(sizes)]
-        def fresh():
-            ix = sb.SetBWT(b"ACGT", block_suffixes=w.block_suffixes, index_bits=w.index_bits,
-                           stream=stream.cuda_stream, device=local)
-            ix.append_device(d_reads.data_ptr(), d_off.data_ptr(), w.m)
-            return ix
-
-        served = serving_report(sb, fresh, requests)
+    # the other workloads: batched (2M reads of U[50,250] bp, plain pipeline
+    # against the batched form), long reads, and the served form on a 2 Gbp
+    # resident index
+    cands = [1 << 22, 1 << 23, 1 << 24, 1 << 25, 1 << 26]
+    batched = long_reads = served = None
+    if args.workload == "short" and not args.no_batched:
+        wb = readgen.batched(seed_genome=0x14100562 + 3 + 1000 * rank, seed_reads=0x05621410 + 3 + 1000 * rank)
+        batched = measure_forms(sb, torch, timer, wb, local, args, peak, 1 << 24, cands, stream)
+        if not args.no_cpu_baseline and world == 1:
+            batched["cpu_baseline"] = cpu_baseline(wb, 100_000)
+        del wb
+    if args.workload == "short" and not args.no_long:
+        wl = readgen.long(seed_genome=0x14100562 + 4 + 1000 * rank, seed_reads=0x05621410 + 4 + 1000 * rank)
+        long_reads = measure_forms(sb, torch, timer, wl, local, args, peak, 1 << 25, cands + [1 << 27], stream)
+        if not args.no_cpu_baseline and world == 1:
+            long_reads["cpu_baseline"] = cpu_baseline(wl, 1_000)
+        del wl
+    if args.workload == "short" and not args.no_serving:
+        t = time.perf_counter()
+        res, reqs = readgen.serving(seed_genome=0x14100562 + 5 + 1000 * rank,
+                                    seed_reads=0x05621410 + 5 + 1000 * rank)
+        gen_s = time.perf_counter() - t
+        served = measure_served(sb, torch, res, reqs, local, stream, peak)
+        served["generation_s"] = gen_s
+        if not args.no_cpu_baseline and world == 1:
+            served["cpu_baseline"] = cpu_baseline(res, 100_000)
+        del res, reqs
 
     if rank != 0:
         if dist:
@@ -469,20 +615,16 @@ def run_gb300(args):
 
     value = whole_job_mbps(bases, world, args.steps, total_ms)
     dom = next(s for s in stats if s["name"] == dominant)
-    peak, peak_kind = load_peaks()
     achieved = dom["bytes"] / (dom["ms"] / 1e3) / 1e9 if dom["ms"] > 0 else 0.0
     per_launch = dom["bytes"] / max(dom["launches"], 1)
     traffic = load_traffic(dom["name"], per_launch)
     roofline = {"bound": "hbm", "kernel": dom["name"], "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": peak_kind,
                 "traffic": traffic,
-                "algorithmic_bytes_per_launch": dom["bytes"] / max(dom["launches"], 1),
+                "algorithmic_bytes_per_launch": per_launch,
                 "avg_launch_us": 1e3 * dom["ms"] / max(dom["launches"], 1)}
     if dom["name"] in LIMITERS:
         roofline["limiter"] = LIMITERS[dom["name"]]
-    kernels = {s["name"]: {"launches": s["launches"], "ms_per_step": s["ms"],
-                           "GBps": (s["bytes"] / (s["ms"] / 1e3) / 1e9) if s["ms"] > 0 else None}
-               for s in sorted(breakdown, key=lambda s: -s["ms"])}
     launches = int(sum(s["launches"] for s in stats))
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -495,10 +637,11 @@ def run_gb300(args):
         "roofline": roofline,
         "e2e": e2e,
         "gpu_launches": launches,
-        "batched": batched,
-        "served": served,
-        "kernels": kernels,  # one untimed step with every kernel timed
+        "kernels": kernel_table(breakdown, peak),  # one untimed step with every kernel timed
         "host_ms_per_step": host_phases,
+        "batched": batched,
+        "long": long_reads,
+        "served": served,
     }
     clocks = clk.summary()
     if clocks:
@@ -511,82 +654,10 @@ def run_gb300(args):
     return 0
 
 
-def run_serve_workload(args):
-    """The serving workload: a resident index of 20M x 100 bp reads (2 Gbp)
-    under an 8 GB HBM budget, then append requests of 10k..1M reads arriving
-    all at once (sustained rate) and as Poisson streams at 0.5x and 0.9x of
-    it.  A second, smaller index under a 512 MB budget keeps its dictionaries
-    in the pinned host tier and serves the same way."""
-    import torch
-
-    import paper_1410_0562_gb300 as sb
-    rank, world, local = dist_env()
-    if rank != 0:
-        return 0
-    torch.cuda.set_device(local)
-    sb.build()
-    sb.load()
-    t = time.perf_counter()
-    resident, requests = readgen.serving()
-    gen_s = time.perf_counter() - t
-    stream = torch.cuda.Stream()
-    idx = sb.SetBWT(b"ACGT", hbm_budget=8 << 30, index_bits=64, block_suffixes=1 << 25,
-                    stream=stream.cuda_stream, device=local)
-    d_reads = torch.from_numpy(resident.reads).to("cuda")
-    d_off = torch.from_numpy(resident.offsets.astype(np.int64)).to("cuda")
-    torch.cuda.synchronize()
-    t = time.perf_counter()
-    idx.append_device(d_reads.data_ptr(), d_off.data_ptr(), resident.m)
-    build_s = time.perf_counter() - t
-    hbm, host = sb.sbwt_memory(idx.handle)
-    n, m = idx.size()
-    idx.close()
-
-    def fresh():
-        ix = sb.SetBWT(b"ACGT", hbm_budget=8 << 30, index_bits=64, block_suffixes=1 << 25,
-                       stream=stream.cuda_stream, device=local)
-        ix.append_device(d_reads.data_ptr(), d_off.data_ptr(), resident.m)
-        return ix
-
-    report = serving_report(sb, fresh, requests)
-    del d_reads, d_off
-    torch.cuda.empty_cache()
-
-    # host tier: dictionaries in pinned host memory under a tight budget
-    small = readgen.Workload("resident-2Mx100", resident.reads[: int(resident.offsets[2_000_000])],
-                             resident.offsets[: 2_000_001], 1 << 21, 64, (0, 2_000_000))
-    idx2 = sb.SetBWT(b"ACGT", hbm_budget=512 << 20, index_bits=64, block_suffixes=1 << 21,
-                     stream=stream.cuda_stream, device=local)
-    t = time.perf_counter()
-    idx2.append(small.reads, small.offsets)
-    build2_s = time.perf_counter() - t
-    hbm2, host2 = sb.sbwt_memory(idx2.handle)
-    small_reqs = [r for r in requests if len(r[1]) - 1 <= 100_000][:12]
-    report2 = {"sustained": measure_serving(sb, idx2, small_reqs)}
-    idx2.close()
-    line = {
-        "metric": "append throughput, served (Mbp/s); p50/p99 append latency", "unit": UNIT,
-        "value": report["sustained"]["Mbps"], "higher_is_better": True, "n_gpus": 1, "data": "synthetic",
-        "dtype": "u64",
-        "config": {"workload": resident.name, "requests": len(requests), "hbm_budget": 8 << 30,
-                   "block_suffixes": 1 << 25},
-        "resident_build_s": build_s, "resident_build_Mbps": resident.bases / build_s / 1e6,
-        "generation_s": gen_s, "resident_rows": n, "resident_reads": m,
-        "memory_after_build": {"hbm": hbm, "host": host},
-        "serving": report,
-        "host_tier": {"resident": small.name, "hbm_budget": 512 << 20, "build_s": build2_s,
-                      "memory": {"hbm": hbm2, "host": host2}, "serving": report2},
-    }
-    print(json.dumps(line), flush=True)
-    return 0
-
-
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
-    if args.workload == "serve":
-        return run_serve_workload(args)
     return run_gb300(args)
 
 

@@ -77,7 +77,15 @@ typedef struct {
                                 and the same kernels reach them over the host link
                                 (Section 5 keeps B_ext in system memory); the
                                 per-block working set stays in HBM */
-    uint32_t reserved[7];    /* must be zero */
+    uint32_t occ_sampling;   /* rows per occurrence block of the rank dictionary
+                                (Section 5 keeps counters every 128 symbols): 64,
+                                128 or 256; 0 = 64.  64 is one 32-byte sector per
+                                block (4 bits per row of B, one sector per rank
+                                query); 128 and 256 hold 3.5 and 3.25 bits per row
+                                and read two to four sectors per query.
+                                Alphabets of 5 to 16 symbols take 64 only
+                                (SBWT_ENOTSUP otherwise). */
+    uint32_t reserved[6];    /* must be zero */
 } sbwt_options;
 
 /* Creates an empty index over `alphabet` (a NUL-terminated string of 1..16
@@ -194,6 +202,15 @@ int sbwt_get_stage(sbwt_index *idx, int stage, void *out, uint64_t cap, uint64_t
  * Off by default. */
 int sbwt_set_graph_replay(sbwt_index *idx, int on);
 
+/* Block overlap (on by default): the suffix sort of each block runs on a
+ * second stream, ahead of the ranking, gather and Insert of the blocks before
+ * it, which keep their order on the index's stream (the overlap of the
+ * paper's pipeline, Section 7, Figure 1, with the GPU doing every stage).
+ * Off: the plain per-block loop of Algorithm 1, every step of every block in
+ * turn on the index's stream.  Results are identical.  Waits for the index's
+ * stream; SBWT_EBUSY while serving. */
+int sbwt_set_block_overlap(sbwt_index *idx, int on);
+
 /* Autotunes M (suffixes per block, Algorithm 1) for reads like the given
  * ones: builds their BWT with each candidate M (three times; the fastest of
  * the last two counts), keeps the fastest M in the index and reports it in
@@ -205,6 +222,23 @@ int sbwt_set_graph_replay(sbwt_index *idx, int on);
  * or the error of a failing append. */
 int sbwt_autotune_block_suffixes(sbwt_index *idx, const uint8_t *d_reads, const uint64_t *d_offsets, uint64_t m,
                                  const uint64_t *candidates, int ncand, uint64_t *best_out, double *ms_out);
+
+/* Autotunes M and the occurrence sampling together (Algorithm 1's block
+ * size; Section 5's counter spacing): every pair of a block size from
+ * block_suffixes[0 .. n_block) and a sampling from samplings[0 .. n_sampling)
+ * (64, 128 or 256 rows) builds the BWT of the given device reads three times
+ * (the fastest of the last two counts).  The fastest pair is kept in the
+ * index and reported in *best_block_out and *best_sampling_out (either may
+ * be NULL); ms_out, if not NULL, gets n_sampling x n_block times in ms, row
+ * by sampling (-1: did not fit the HBM budget).  block_suffixes NULL =
+ * {2^22 .. 2^27}; samplings NULL = {64, 128, 256} (64 alone for 5 to 16
+ * symbols).  The index is emptied before and after.  Errors: SBWT_EINVAL
+ * (bad arguments or candidates), SBWT_ENOTSUP (a sampling other than 64 for
+ * 5 to 16 symbols), SBWT_EBUSY, SBWT_ENOMEM (no pair fits), or the error of
+ * a failing append. */
+int sbwt_autotune(sbwt_index *idx, const uint8_t *d_reads, const uint64_t *d_offsets, uint64_t m,
+                  const uint64_t *block_suffixes, int n_block, const uint32_t *samplings, int n_sampling,
+                  uint64_t *best_block_out, uint32_t *best_sampling_out, double *ms_out);
 
 /* ---- per-kernel timing ---------------------------------------------------
  * With profiling on, every kernel launch is bracketed by CUDA events on the

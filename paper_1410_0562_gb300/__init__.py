@@ -42,7 +42,8 @@ EXPORTS = (
     "sbwt_create", "sbwt_create_ex", "sbwt_append", "sbwt_prepend", "sbwt_append_device", "sbwt_get_bwt", "sbwt_rank",
     "sbwt_rank_batch", "sbwt_count", "sbwt_memory", "sbwt_size", "sbwt_reset", "sbwt_destroy", "sbwt_strerror", "sbwt_get_stream",
     "sbwt_set_capture", "sbwt_get_stage", "sbwt_set_profiling", "sbwt_set_profiling_only", "sbwt_get_kernel_stats",
-    "sbwt_reset_kernel_stats", "sbwt_set_graph_replay", "sbwt_autotune_block_suffixes", "sbwt_serve_start",
+    "sbwt_reset_kernel_stats", "sbwt_set_graph_replay", "sbwt_set_block_overlap", "sbwt_autotune_block_suffixes",
+    "sbwt_autotune", "sbwt_serve_start",
     "sbwt_submit", "sbwt_wait", "sbwt_serve_stop", "sbwt_save", "sbwt_load", "sbwt_bwt_noalloc",
 )
 
@@ -59,7 +60,7 @@ class SbwtError(RuntimeError):
 class sbwt_options(ctypes.Structure):
     _fields_ = [("index_bits", ctypes.c_uint32), ("block_suffixes", ctypes.c_uint64),
                 ("stream", ctypes.c_void_p), ("device", ctypes.c_int32), ("host_tier", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32 * 7)]
+                ("occ_sampling", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 6)]
 
 
 class sbwt_kernel_stat(ctypes.Structure):
@@ -111,7 +112,10 @@ def load() -> ctypes.CDLL:
             "sbwt_get_kernel_stats": ([P, ctypes.POINTER(sbwt_kernel_stat), I, ctypes.POINTER(I)], I),
             "sbwt_reset_kernel_stats": ([P], I),
             "sbwt_set_graph_replay": ([P, I], I),
+            "sbwt_set_block_overlap": ([P, I], I),
             "sbwt_autotune_block_suffixes": ([P, P, P, U64, P, I, ctypes.POINTER(U64), P], I),
+            "sbwt_autotune": ([P, P, P, U64, P, I, P, I, ctypes.POINTER(U64), ctypes.POINTER(ctypes.c_uint32), P],
+                              I),
             "sbwt_serve_start": ([P, U64], I),
             "sbwt_submit": ([P, P, P, U64, ctypes.POINTER(U64)], I),
             "sbwt_wait": ([P, U64, U64, ctypes.POINTER(U64), ctypes.POINTER(ctypes.c_double)], I),
@@ -159,17 +163,17 @@ def sbwt_save(h, path) -> None:
 
 
 def sbwt_load(path, hbm_budget: int = 0, index_bits: int = 0, block_suffixes: int = 0, stream: int = 0,
-              device: int = -1, host_tier: int = 0):
+              device: int = -1, host_tier: int = 0, occ_sampling: int = 0):
     """A new index handle built from a file written by sbwt_save."""
-    opt = sbwt_options(index_bits, block_suffixes, stream or None, device, host_tier)
+    opt = sbwt_options(index_bits, block_suffixes, stream or None, device, host_tier, occ_sampling)
     out = ctypes.c_void_p()
     _check(load().sbwt_load(os.fsencode(path), hbm_budget, ctypes.byref(opt), ctypes.byref(out)), "sbwt_load")
     return out
 
 
 def sbwt_create_ex(alphabet: bytes = b"ACGT", hbm_budget: int = 0, index_bits: int = 0, block_suffixes: int = 0,
-                   stream: int = 0, device: int = -1, host_tier: int = 0):
-    opt = sbwt_options(index_bits, block_suffixes, stream or None, device, host_tier)
+                   stream: int = 0, device: int = -1, host_tier: int = 0, occ_sampling: int = 0):
+    opt = sbwt_options(index_bits, block_suffixes, stream or None, device, host_tier, occ_sampling)
     h = ctypes.c_void_p()
     _check(load().sbwt_create_ex(alphabet, hbm_budget, ctypes.byref(opt), ctypes.byref(h)), "sbwt_create_ex")
     return h
@@ -299,6 +303,10 @@ def sbwt_reset_kernel_stats(h):
     _check(load().sbwt_reset_kernel_stats(h), "sbwt_reset_kernel_stats")
 
 
+def sbwt_set_block_overlap(h, on: bool):
+    _check(load().sbwt_set_block_overlap(h, int(on)), "sbwt_set_block_overlap")
+
+
 def sbwt_set_graph_replay(h, on: bool):
     _check(load().sbwt_set_graph_replay(h, int(on)), "sbwt_set_graph_replay")
 
@@ -313,6 +321,22 @@ def sbwt_autotune_block_suffixes(h, d_reads: int, d_offsets: int, m: int, candid
                                                ctypes.c_void_p(cands.ctypes.data), len(cands), ctypes.byref(best),
                                                ctypes.c_void_p(ms.ctypes.data)), "sbwt_autotune_block_suffixes")
     return best.value, {int(c): float(t) for c, t in zip(cands, ms)}
+
+
+def sbwt_autotune(h, d_reads: int, d_offsets: int, m: int, block_suffixes=None, samplings=None):
+    """Returns (best M, best occurrence sampling, {(sampling, M): ms}) after
+    timing every pair of candidates; the index keeps the best pair."""
+    Ms = np.ascontiguousarray(block_suffixes if block_suffixes is not None else
+                              [1 << 22, 1 << 23, 1 << 24, 1 << 25, 1 << 26, 1 << 27], dtype=np.uint64)
+    Ss = np.ascontiguousarray(samplings if samplings is not None else [64, 128, 256], dtype=np.uint32)
+    ms = np.zeros(len(Ms) * len(Ss), dtype=np.float64)
+    best_m, best_s = ctypes.c_uint64(), ctypes.c_uint32()
+    _check(load().sbwt_autotune(h, ctypes.c_void_p(d_reads), ctypes.c_void_p(d_offsets), m,
+                                ctypes.c_void_p(Ms.ctypes.data), len(Ms), ctypes.c_void_p(Ss.ctypes.data), len(Ss),
+                                ctypes.byref(best_m), ctypes.byref(best_s), ctypes.c_void_p(ms.ctypes.data)),
+           "sbwt_autotune")
+    times = {(int(s_), int(m_)): float(ms[i * len(Ms) + j]) for i, s_ in enumerate(Ss) for j, m_ in enumerate(Ms)}
+    return best_m.value, best_s.value, times
 
 
 def sbwt_bwt_noalloc(alphabet: bytes, reads, offsets, stream: int = 0) -> np.ndarray:
@@ -357,16 +381,18 @@ class SetBWT:
     """An index handle: ``SetBWT(b"ACGT").append(reads, offsets).bwt()``."""
 
     def __init__(self, alphabet: bytes = b"ACGT", hbm_budget: int = 0, index_bits: int = 0,
-                 block_suffixes: int = 0, stream: int = 0, device: int = -1, host_tier: int = 0):
+                 block_suffixes: int = 0, stream: int = 0, device: int = -1, host_tier: int = 0,
+                 occ_sampling: int = 0):
         self.alphabet = alphabet
-        self._h = sbwt_create_ex(alphabet, hbm_budget, index_bits, block_suffixes, stream, device, host_tier)
+        self._h = sbwt_create_ex(alphabet, hbm_budget, index_bits, block_suffixes, stream, device, host_tier,
+                                 occ_sampling)
 
     @classmethod
     def load(cls, path, hbm_budget: int = 0, index_bits: int = 0, block_suffixes: int = 0, stream: int = 0,
-             device: int = -1, host_tier: int = 0) -> "SetBWT":
+             device: int = -1, host_tier: int = 0, occ_sampling: int = 0) -> "SetBWT":
         """An index read from a file that save() wrote."""
         self = cls.__new__(cls)
-        self._h = sbwt_load(path, hbm_budget, index_bits, block_suffixes, stream, device, host_tier)
+        self._h = sbwt_load(path, hbm_budget, index_bits, block_suffixes, stream, device, host_tier, occ_sampling)
         self.alphabet = None
         return self
 

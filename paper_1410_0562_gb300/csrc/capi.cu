@@ -52,6 +52,7 @@ struct sbwt_index {
     uint32_t alpha4 = 0;     // the first four symbols, packed (2-bit kernels)
     Alphabet16 alpha16 = {};  // all symbols (4-bit kernels, read-back)
     int code_bits = 2;       // 2 for up to 4 symbols, 4 for 5 to 16
+    int occ_k = 1;           // occurrence sampling of 64 occ_k rows (1, 2 or 4; 1 for 4-bit codes)
     size_t budget = 0;
     uint32_t index_bits = 0;
     uint64_t M = kDefaultBlock;
@@ -66,6 +67,7 @@ struct sbwt_index {
     // sort reads only the packed text.  Its SA_int goes to one of two buffers
     // (sa, sa2 by block parity).
     cudaStream_t side = nullptr;
+    bool overlap = true;  // sorts on `side` ahead of the chain; off: every step in turn on `stream`
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_sorted[2] = {nullptr, nullptr},
                 ev_consumed[2] = {nullptr, nullptr};
     // host appends: block k's text is packed as soon as its reads arrive;
@@ -212,7 +214,7 @@ int device_init(sbwt_index* idx) {
     if (cudaMallocHost(&idx->h_summary, sizeof(PlanSummary)) != cudaSuccess) return SBWT_EDEVICE;
     // the committed dictionary starts empty: one zero block, one zero superblock, C = 0
     Dict& d = idx->dict[idx->cur];
-    const size_t bb = dict_block_bytes(idx->code_bits), cb = 8 * dict_codes(idx->code_bits);
+    const size_t bb = dict_block_bytes(idx->code_bits, idx->occ_k), cb = 8 * dict_codes(idx->code_bits);
     if (grow(d.blocks, bb) || grow(d.super, cb) || grow(d.C, cb)) return SBWT_ENOMEM;
     zero_async(d.blocks, bb, idx->stream);
     zero_async(d.super, cb, idx->stream);
@@ -296,7 +298,8 @@ std::vector<Need> buffer_needs(sbwt_index* idx, const Plan& p, bool host_input, 
     v.push_back({&idx->ins_plan, (size_t)(nsb + 1) * 4});  // Insert's first new symbol per superblock
     for (int k = 0; k < 3; ++k) {
         if (k == idx->cur) continue;
-        v.push_back({&idx->dict[k].blocks, (size_t)dict_blocks(n_final) * dict_block_bytes(cb), true});
+        v.push_back({&idx->dict[k].blocks, (size_t)dict_blocks(n_final, idx->occ_k) * dict_block_bytes(cb, idx->occ_k),
+                     true});
         v.push_back({&idx->dict[k].super, (size_t)nsb * 8 * dict_codes(cb), true});
         v.push_back({&idx->dict[k].C, 8 * dict_codes(cb), true});
     }
@@ -410,19 +413,22 @@ void run_block(sbwt_index* idx, const BlockPlan& bp, const uint64_t* d_offsets, 
     const uint32_t* text = (const uint32_t*)idx->text.p;
     const uint32_t* term = (const uint32_t*)idx->term.p;
 
-    // the sort, on the side stream; its SA buffer is free once the gather of
-    // block k - 2 has read it
+    // the sort, on the side stream (or, without overlap, on the index's
+    // stream, before this block's other steps); its SA buffer is free once
+    // the gather of block k - 2 has read it
     const cudaStream_t s = L.stream;
-    if (q >= 2) cudaStreamWaitEvent(idx->side, idx->ev_consumed[q & 1], 0);
-    if (packed) cudaStreamWaitEvent(idx->side, packed, 0);  // this block's text is in place
-    L.stream = idx->side;
+    const cudaStream_t ss = idx->overlap ? idx->side : s;
+    if (q >= 2) cudaStreamWaitEvent(ss, idx->ev_consumed[q & 1], 0);
+    if (packed) cudaStreamWaitEvent(ss, packed, 0);  // this block's text is in place
+    L.stream = ss;
     suffix_sort_block(L, text, term, bp.base, n, (uint32_t)bp.max_len, idx->code_bits, idx->sigma, b);
-    cudaEventRecord(idx->ev_sorted[q & 1], idx->side);
+    cudaEventRecord(idx->ev_sorted[q & 1], ss);
     L.stream = s;
     // ComputeRanks needs only the dictionary; the gather waits for the sort
-    launch_compute_ranks<IdxT>(L, text, d_offsets, bp.j0, bp.j1 - bp.j0, bp.n_int, (const void*)src.blocks.p,
+    launch_compute_ranks<IdxT>(L, text, d_offsets, bp.j0, bp.j1 - bp.j0, bp.n_int, bp.max_len, (const void*)src.blocks.p,
                                (const unsigned long long*)src.super.p, (const unsigned long long*)src.C.p, n_ext,
-                               prepend ? 0 : m_ext, (IdxT*)idx->g.p, (uint32_t*)idx->err.p, idx->code_bits);
+                               prepend ? 0 : m_ext, (IdxT*)idx->g.p, (uint32_t*)idx->err.p, idx->code_bits,
+                               idx->occ_k);
     cudaStreamWaitEvent(s, idx->ev_sorted[q & 1], 0);
     // the 2-bit Insert takes its plan (first new symbol per superblock) from the gather
     uint32_t* plan = idx->code_bits == 2 ? (uint32_t*)idx->ins_plan.p : nullptr;
@@ -432,7 +438,7 @@ void run_block(sbwt_index* idx, const BlockPlan& bp, const uint64_t* d_offsets, 
     launch_insert<IdxT>(L, (const void*)src.blocks.p, n_ext, (const uint8_t*)idx->bint.p,
                         (const IdxT*)idx->gsa.p, bp.n_int, plan, (void*)dst.blocks.p,
                         (unsigned long long*)dst.super.p, (unsigned long long*)dst.C.p, m_ext + (bp.j1 - bp.j0),
-                        (uint32_t*)idx->sb_tot.p, (uint32_t*)idx->err.p, idx->code_bits);
+                        (uint32_t*)idx->sb_tot.p, (uint32_t*)idx->err.p, idx->code_bits, idx->occ_k);
 }
 
 Plan host_plan(const uint64_t* h_off, uint64_t m_new, uint64_t M) {
@@ -676,10 +682,13 @@ int parse_alphabet(const char* alphabet, sbwt_index* idx) {
 // checksum of everything before it.
 // ---------------------------------------------------------------------------
 constexpr char kFileMagic[8] = {'S', 'B', 'W', 'T', 'I', 'D', 'X', '1'};
-// Version 1: up to 4 symbols, the 2-bit dictionary.  Version 2: 5 to 16
-// symbols, the 4-bit dictionary; symbols 5.. in alphabet_hi.
-constexpr uint32_t kFileVersion = 1;
+// Version 3: up to 4 symbols, the bit-plane dictionary with the occurrence
+// sampling in the header.  Version 2: 5 to 16 symbols, the 4-bit dictionary;
+// symbols 5.. in alphabet_hi.  Version 1 (read only): up to 4 symbols, 2-bit
+// codes interleaved in 64-row blocks (converted to bit planes on load).
+constexpr uint32_t kFileVersionPacked = 1;
 constexpr uint32_t kFileVersionWide = 2;
+constexpr uint32_t kFileVersion = 3;
 
 struct FileHeader {
     char magic[8];
@@ -688,9 +697,10 @@ struct FileHeader {
     uint8_t alphabet[4];
     uint32_t index_bits;
     uint64_t n, m;
-    uint64_t n_blocks, n_supers;  // array lengths: dict_blocks(n), the superblocks of the layout
+    uint64_t n_blocks, n_supers;  // array lengths: dict_blocks(n, k), the superblocks of the layout
     uint8_t alphabet_hi[12];
-    uint8_t reserved[20];
+    uint32_t occ_sampling;  // rows per occurrence block (version 3; 0 reads as 64)
+    uint8_t reserved[16];
 };
 static_assert(sizeof(FileHeader) == 88, "fixed header layout");
 
@@ -934,11 +944,18 @@ int sbwt_create_ex(const char* alphabet, size_t hbm_budget_bytes, const sbwt_opt
         bool bad = opt->index_bits != 0 && opt->index_bits != 32 && opt->index_bits != 64;
         bad |= opt->block_suffixes > kMaxBlock;
         bad |= opt->host_tier > 3;
+        bad |= opt->occ_sampling != 0 && opt->occ_sampling != 64 && opt->occ_sampling != 128 &&
+               opt->occ_sampling != 256;
         for (uint32_t r : opt->reserved) bad |= r != 0;
         if (bad) {
             delete idx;
             return SBWT_EINVAL;
         }
+        if (idx->code_bits == 4 && opt->occ_sampling > 64) {  // the 4-bit dictionary samples every 64 rows only
+            delete idx;
+            return SBWT_ENOTSUP;
+        }
+        if (opt->occ_sampling) idx->occ_k = (int)(opt->occ_sampling / 64);
         idx->index_bits = opt->index_bits;
         if (opt->block_suffixes) idx->M = opt->block_suffixes;
         idx->stream = (cudaStream_t)opt->stream;
@@ -1023,7 +1040,7 @@ int sbwt_get_bwt(sbwt_index* idx, uint8_t* out, uint64_t cap, uint64_t* n_out) {
     int e = 0;
     for (uint64_t r0 = 0; r0 < idx->n; r0 += kChunkRows, e ^= 1) {
         const uint64_t r1 = std::min(idx->n, r0 + kChunkRows);
-        launch_unpack(idx->L, blocks, r0, r1, idx->alpha16, staged, idx->code_bits);
+        launch_unpack(idx->L, blocks, r0, r1, idx->alpha16, staged, idx->code_bits, idx->occ_k);
         cudaEventRecord(idx->ev_sorted[e], s);
         cudaStreamWaitEvent(idx->side, idx->ev_sorted[e], 0);
         cudaMemcpyAsync(out + r0, staged + r0, r1 - r0, cudaMemcpyDeviceToHost, idx->side);
@@ -1062,7 +1079,7 @@ int sbwt_rank_batch(sbwt_index* idx, const uint8_t* cs, const uint64_t* ks, uint
     const Dict& d = idx->dict[idx->cur];
     launch_rank_batch(idx->L, (const void*)d.blocks.p, (const unsigned long long*)d.super.p,
                       (const uint8_t*)idx->q_codes.p, (const unsigned long long*)idx->q_ks.p, q,
-                      (unsigned long long*)idx->q_out.p, idx->code_bits);
+                      (unsigned long long*)idx->q_out.p, idx->code_bits, idx->occ_k);
     cudaMemcpyAsync(out, idx->q_out.p, q * 8, cudaMemcpyDeviceToHost, s);
     if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) return SBWT_EDEVICE;
     return SBWT_OK;
@@ -1090,7 +1107,7 @@ int sbwt_count(sbwt_index* idx, const uint8_t* patterns, const uint64_t* offsets
     const Dict& d = idx->dict[idx->cur];
     launch_count(idx->L, (const void*)d.blocks.p, (const unsigned long long*)d.super.p,
                  (const unsigned long long*)d.C.p, idx->n, idx->alpha16, idx->sigma, (const uint8_t*)idx->c_pats.p,
-                 (const uint64_t*)idx->c_offs.p, q, total, (unsigned long long*)idx->q_out.p, idx->code_bits);
+                 (const uint64_t*)idx->c_offs.p, q, total, (unsigned long long*)idx->q_out.p, idx->code_bits, idx->occ_k);
     cudaMemcpyAsync(counts, idx->q_out.p, q * 8, cudaMemcpyDeviceToHost, s);
     if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) return SBWT_EDEVICE;
     return SBWT_OK;
@@ -1124,7 +1141,7 @@ int sbwt_reset(sbwt_index* idx) {
     if (!idx->dev_ready) return SBWT_OK;
     if (set_device(idx)) return SBWT_EDEVICE;
     Dict& d = idx->dict[idx->cur];
-    zero_async(d.blocks, dict_block_bytes(idx->code_bits), idx->stream);
+    zero_async(d.blocks, dict_block_bytes(idx->code_bits, idx->occ_k), idx->stream);
     zero_async(d.super, 8 * dict_codes(idx->code_bits), idx->stream);
     zero_async(d.C, 8 * dict_codes(idx->code_bits), idx->stream);
     if (cudaStreamSynchronize(idx->stream) != cudaSuccess) return SBWT_EDEVICE;
@@ -1134,8 +1151,8 @@ int sbwt_reset(sbwt_index* idx) {
 int sbwt_save(sbwt_index* idx, const char* path) {
     if (!idx || !path) return SBWT_EINVAL;
     if (busy(idx)) return SBWT_EBUSY;
-    const int cb = idx->code_bits;
-    const size_t bb = dict_block_bytes(cb), codes = dict_codes(cb);
+    const int cb = idx->code_bits, k = idx->occ_k;
+    const size_t bb = dict_block_bytes(cb, k), codes = dict_codes(cb);
     FileHeader h = {};
     memcpy(h.magic, kFileMagic, sizeof(h.magic));
     h.version = cb == 4 ? kFileVersionWide : kFileVersion;
@@ -1143,9 +1160,10 @@ int sbwt_save(sbwt_index* idx, const char* path) {
     memcpy(h.alphabet, idx->alphabet, 4);
     memcpy(h.alphabet_hi, idx->alphabet + 4, 12);
     h.index_bits = idx->index_bits;
+    h.occ_sampling = 64u * (uint32_t)k;
     h.n = idx->n;
     h.m = idx->m;
-    h.n_blocks = dict_blocks(idx->n);
+    h.n_blocks = dict_blocks(idx->n, k);
     h.n_supers = dict_supers_of(idx->n, cb);
     std::vector<uint8_t> blocks(h.n_blocks * bb, 0);
     std::vector<unsigned long long> super(codes * h.n_supers, 0ull), C(codes, 0ull);
@@ -1186,14 +1204,17 @@ int sbwt_load(const char* path, size_t hbm_budget_bytes, const sbwt_options* opt
     FileHeader h;
     if (fread(&h, 1, sizeof(h), in.f) != sizeof(h)) return SBWT_EIO;
     if (memcmp(h.magic, kFileMagic, sizeof(h.magic)) != 0) return SBWT_EINVAL;
-    const bool wide = h.version == kFileVersionWide;
-    if (h.version != kFileVersion && !wide) return SBWT_EINVAL;
+    const bool wide = h.version == kFileVersionWide, packed = h.version == kFileVersionPacked;
+    if (h.version != kFileVersion && !wide && !packed) return SBWT_EINVAL;
     const int cb = wide ? 4 : 2;
+    const uint32_t sampling = h.version == kFileVersion ? (h.occ_sampling ? h.occ_sampling : 64u) : 64u;
+    if (sampling != 64 && sampling != 128 && sampling != 256) return SBWT_EINVAL;
+    const int k = (int)(sampling / 64);
     if (h.sigma < 1 || h.sigma > (wide ? 16u : 4u) || (wide && h.sigma <= 4) ||
-        (h.index_bits != 0 && h.index_bits != 32 && h.index_bits != 64) || h.n_blocks != dict_blocks(h.n) ||
+        (h.index_bits != 0 && h.index_bits != 32 && h.index_bits != 64) || h.n_blocks != dict_blocks(h.n, k) ||
         h.n_supers != dict_supers_of(h.n, cb) || h.m > h.n)
         return SBWT_EINVAL;
-    const size_t bb = dict_block_bytes(cb), codes = dict_codes(cb);
+    const size_t bb = dict_block_bytes(cb, k), codes = dict_codes(cb);
     // the arrays must be exactly what the rest of the file holds
     if (fseek(in.f, 0, SEEK_END) != 0) return SBWT_EIO;
     const long size = ftell(in.f);
@@ -1213,6 +1234,22 @@ int sbwt_load(const char* path, size_t hbm_budget_bytes, const sbwt_options* opt
     sum.add(super.data(), super.size() * 8);
     sum.add(C.data(), C.size() * 8);
     if (sum.h != digest) return SBWT_EINVAL;
+    if (packed) {
+        // version 1 blocks: two words of 2-bit codes (row q at bits 2 (q & 31)
+        // of word q >> 5), the terminator mask and the counts; make them
+        // bit planes
+        unsigned long long* w = reinterpret_cast<unsigned long long*>(blocks.data());
+        for (uint64_t b = 0; b < h.n_blocks; ++b, w += 4) {
+            unsigned long long lo = 0, hi = 0;
+            for (int q = 0; q < 64; ++q) {
+                const unsigned long long c = (w[q >> 5] >> (2 * (q & 31))) & 3ull;
+                lo |= (c & 1ull) << q;
+                hi |= (c >> 1) << q;
+            }
+            w[0] = lo;
+            w[1] = hi;
+        }
+    }
 
     char alpha[17] = {0};
     memcpy(alpha, h.alphabet, std::min<uint32_t>(h.sigma, 4));
@@ -1220,6 +1257,8 @@ int sbwt_load(const char* path, size_t hbm_budget_bytes, const sbwt_options* opt
     sbwt_options o = {};
     if (opt) o = *opt;
     if (o.index_bits == 0) o.index_bits = h.index_bits;
+    if (o.occ_sampling != 0 && o.occ_sampling != sampling) return SBWT_EINVAL;  // the file's layout decides
+    o.occ_sampling = sampling;
     if (h.n >= 0xFFFFFFFFull && o.index_bits == 32) return SBWT_EINVAL;
     sbwt_index* idx = nullptr;
     if (int rc = sbwt_create_ex(alpha, hbm_budget_bytes, &o, &idx)) return rc;
@@ -1314,60 +1353,124 @@ int sbwt_get_stage(sbwt_index* idx, int stage, void* out, uint64_t cap, uint64_t
     return SBWT_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Occurrence sampling of an empty index: 64 k rows per block.  The committed
+// dictionary (empty: one zero block) is laid out again for k.
+int set_occ_k(sbwt_index* idx, int k) {
+    if (k != 1 && k != 2 && k != 4) return SBWT_EINVAL;
+    if (idx->code_bits == 4 && k != 1) return SBWT_ENOTSUP;
+    if (idx->n != 0) return SBWT_EINVAL;
+    if (k == idx->occ_k) return SBWT_OK;
+    idx->occ_k = k;
+    if (!idx->dev_ready) return SBWT_OK;
+    if (set_device(idx) || cudaStreamSynchronize(idx->stream) != cudaSuccess) return SBWT_EDEVICE;
+    Dict& d = idx->dict[idx->cur];
+    const size_t bb = dict_block_bytes(idx->code_bits, k);
+    if (int rc = grow(d.blocks, bb, d.blocks.host)) return rc;
+    zero_async(d.blocks, bb, idx->stream);
+    if (cudaStreamSynchronize(idx->stream) != cudaSuccess) return SBWT_EDEVICE;
+    return SBWT_OK;
+}
+
+// Builds the reads' BWT three times with the index's current settings and
+// returns the faster of the last two in ms (the first sizes the buffers),
+// -1 when it does not fit the HBM budget.  The index is left empty.
+int time_build(sbwt_index* idx, const uint8_t* d_reads, const uint64_t* d_offsets, uint64_t m, double* ms_out) {
+    double t_min = -1;
+    for (int rep = 0; rep < 3; ++rep) {
+        if (int rc = sbwt_reset(idx)) return rc;
+        const auto t0 = std::chrono::steady_clock::now();
+        const int a = sbwt_append_device(idx, d_reads, d_offsets, m);
+        const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        if (a == SBWT_ENOMEM) {
+            t_min = -1;
+            break;
+        }
+        if (a != SBWT_OK) return a;
+        if (rep > 0 && (t_min < 0 || ms < t_min)) t_min = ms;
+    }
+    *ms_out = t_min;
+    return sbwt_reset(idx);
+}
+
+}  // namespace
+
+extern "C" {
+
 int sbwt_autotune_block_suffixes(sbwt_index* idx, const uint8_t* d_reads, const uint64_t* d_offsets, uint64_t m,
                                  const uint64_t* candidates, int ncand, uint64_t* best_out, double* ms_out) {
-    static const uint64_t kDefaults[] = {1ull << 22, 1ull << 23, 1ull << 24, 1ull << 25, 1ull << 26, 1ull << 27};
+    uint32_t sampling = 64u * (uint32_t)(idx ? idx->occ_k : 1);
+    return sbwt_autotune(idx, d_reads, d_offsets, m, candidates, ncand, &sampling, 1, best_out, nullptr, ms_out);
+}
+
+int sbwt_autotune(sbwt_index* idx, const uint8_t* d_reads, const uint64_t* d_offsets, uint64_t m,
+                  const uint64_t* block_suffixes, int n_block, const uint32_t* samplings, int n_sampling,
+                  uint64_t* best_block_out, uint32_t* best_sampling_out, double* ms_out) {
+    static const uint64_t kDefaultM[] = {1ull << 22, 1ull << 23, 1ull << 24, 1ull << 25, 1ull << 26, 1ull << 27};
+    static const uint32_t kDefaultS[] = {64, 128, 256};
     if (!idx || !d_offsets || m == 0) return SBWT_EINVAL;
-    if (!candidates) {
-        candidates = kDefaults;
-        ncand = (int)(sizeof(kDefaults) / sizeof(kDefaults[0]));
+    if (busy(idx)) return SBWT_EBUSY;
+    if (!block_suffixes) {
+        block_suffixes = kDefaultM;
+        n_block = (int)(sizeof(kDefaultM) / sizeof(kDefaultM[0]));
     }
-    if (ncand <= 0) return SBWT_EINVAL;
-    for (int c = 0; c < ncand; ++c)
-        if (candidates[c] == 0 || candidates[c] > kMaxBlock) return SBWT_EINVAL;
+    if (!samplings) {
+        samplings = kDefaultS;
+        n_sampling = idx->code_bits == 4 ? 1 : 3;
+    }
+    if (n_block <= 0 || n_sampling <= 0) return SBWT_EINVAL;
+    for (int c = 0; c < n_block; ++c)
+        if (block_suffixes[c] == 0 || block_suffixes[c] > kMaxBlock) return SBWT_EINVAL;
+    for (int c = 0; c < n_sampling; ++c) {
+        if (samplings[c] != 64 && samplings[c] != 128 && samplings[c] != 256) return SBWT_EINVAL;
+        if (idx->code_bits == 4 && samplings[c] != 64) return SBWT_ENOTSUP;
+    }
     const uint64_t saved_M = idx->M;
+    const int saved_k = idx->occ_k;
     const bool saved_replay = idx->graph_replay;
     idx->graph_replay = false;
-    uint64_t best = 0;
+    uint64_t best_M = 0;
+    int best_k = 0;
     double best_ms = 0;
-    int rc = SBWT_OK;
-    for (int c = 0; c < ncand && rc == SBWT_OK; ++c) {
-        idx->M = candidates[c];
-        double t_min = -1;
-        for (int rep = 0; rep < 3; ++rep) {  // the first run sizes the buffers
-            if ((rc = sbwt_reset(idx)) != SBWT_OK) break;
-            const auto t0 = std::chrono::steady_clock::now();
-            const int a = sbwt_append_device(idx, d_reads, d_offsets, m);
-            const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-            if (a == SBWT_ENOMEM) {  // does not fit the budget: skip this candidate
-                t_min = -1;
-                break;
+    int rc = sbwt_reset(idx);
+    for (int si = 0; si < n_sampling && rc == SBWT_OK; ++si) {
+        if ((rc = set_occ_k(idx, (int)(samplings[si] / 64))) != SBWT_OK) break;
+        for (int c = 0; c < n_block && rc == SBWT_OK; ++c) {
+            idx->M = block_suffixes[c];
+            double t = -1;
+            rc = time_build(idx, d_reads, d_offsets, m, &t);
+            if (ms_out) ms_out[(size_t)si * n_block + c] = t;
+            if (rc == SBWT_OK && t >= 0 && (best_M == 0 || t < best_ms)) {
+                best_M = block_suffixes[c];
+                best_k = idx->occ_k;
+                best_ms = t;
             }
-            if (a != SBWT_OK) {
-                rc = a;
-                break;
-            }
-            if (rep > 0 && (t_min < 0 || ms < t_min)) t_min = ms;
-        }
-        if (ms_out) ms_out[c] = t_min;
-        if (t_min >= 0 && (best == 0 || t_min < best_ms)) {
-            best = candidates[c];
-            best_ms = t_min;
         }
     }
     idx->graph_replay = saved_replay;
     const int rr = sbwt_reset(idx);
+    if (rc == SBWT_OK && best_M == 0) rc = SBWT_ENOMEM;
     if (rc != SBWT_OK) {
         idx->M = saved_M;
+        set_occ_k(idx, saved_k);
         return rc;
     }
-    if (best == 0) {
-        idx->M = saved_M;
-        return SBWT_ENOMEM;
-    }
-    idx->M = best;
-    if (best_out) *best_out = best;
+    idx->M = best_M;
+    if (int r2 = set_occ_k(idx, best_k)) return r2;
+    if (best_block_out) *best_block_out = best_M;
+    if (best_sampling_out) *best_sampling_out = 64u * (uint32_t)best_k;
     return rr;
+}
+
+int sbwt_set_block_overlap(sbwt_index* idx, int on) {
+    if (!idx) return SBWT_EINVAL;
+    if (busy(idx)) return SBWT_EBUSY;
+    if (idx->dev_ready && (set_device(idx) || cudaStreamSynchronize(idx->stream) != cudaSuccess)) return SBWT_EDEVICE;
+    idx->overlap = on != 0;
+    return SBWT_OK;
 }
 
 int sbwt_set_graph_replay(sbwt_index* idx, int on) {

@@ -25,66 +25,72 @@ namespace sbwt {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kInsertThreads = 512;  // threads of a 2-bit Insert CTA (one superblock)
+constexpr int kInsertThreads = 512;        // threads of a 2-bit Insert CTA (one superblock), dense new rows
+constexpr int kInsertThreadsSparse = 256;  // the same for sparse new rows
 constexpr int kRun = 8;              // consecutive new symbols a thread places at once
 
+// 64 rows of the 2-bit dictionary as its three bit planes (bit p: row p).
 struct Window {
-    unsigned long long w0, w1, dm;
+    unsigned long long lo, hi, dm;
 };
 
-// The two old blocks a 64-row window starting at row s reads (the second one
-// zero past the old end), loaded before any of them is used.
+// The two 64-row parts a window starting at old row s reads (the second one
+// zero past the old end), loaded before any of them is used.  Part P of a
+// dictionary of sampling 64 K rows is words 3 (P % K) .. of block P / K.
 struct OldPair {
-    unsigned long long a0, a1, da, b0, b1, db;
+    Window a, b;
 };
-__device__ __forceinline__ OldPair old_pair(const OccBlock* __restrict__ old_blocks, uint64_t nb_old, uint64_t s) {
-    const uint64_t bs = s >> kOccShift;
-    const ulonglong2* A = reinterpret_cast<const ulonglong2*>(old_blocks + bs);
-    const ulonglong2 a01 = A[0], ad = A[1];
-    ulonglong2 b01 = make_ulonglong2(0ull, 0ull), bd = make_ulonglong2(0ull, 0ull);
-    if (bs + 1 < nb_old) {
-        b01 = A[2];
-        bd = A[3];
+template <int K>
+__device__ __forceinline__ const unsigned long long* part_words(const unsigned long long* __restrict__ words,
+                                                                uint64_t part) {
+    return words + (part / K) * Occ<K>::kWords + 3 * (part % K);
+}
+template <int K>
+__device__ __forceinline__ OldPair old_pair(const unsigned long long* __restrict__ old_words, uint64_t nparts_old,
+                                            uint64_t s) {
+    const uint64_t P = s >> kOccShift;
+    OldPair o;
+    o.b = Window{0ull, 0ull, 0ull};
+    if constexpr (K == 1) {
+        const ulonglong2* A = reinterpret_cast<const ulonglong2*>(old_words) + 2 * P;
+        const ulonglong2 a0 = A[0], a1 = A[1];
+        o.a = Window{a0.x, a0.y, a1.x};
+        if (P + 1 < nparts_old) {
+            const ulonglong2 b0 = A[2], b1 = A[3];
+            o.b = Window{b0.x, b0.y, b1.x};
+        }
+    } else {
+        const unsigned long long* pa = part_words<K>(old_words, P);
+        o.a = Window{pa[0], pa[1], pa[2]};
+        if (P + 1 < nparts_old) {
+            const unsigned long long* pb = part_words<K>(old_words, P + 1);
+            o.b = Window{pb[0], pb[1], pb[2]};
+        }
     }
-    return OldPair{a01.x, a01.y, ad.x, b01.x, b01.y, bd.x};
+    return o;
 }
 
-// 64 old rows starting at row s, from the pair of blocks holding them.
+// 64 old rows starting at row s, from the pair of parts holding them.
 __device__ __forceinline__ Window old_window_of(const OldPair& o, uint64_t s) {
     const uint32_t off = (uint32_t)(s & (kOccSpan - 1));
-    Window w;
-    const uint32_t sh = 2 * off;  // 0 .. 126 bits
-    if (sh == 0) {
-        w.w0 = o.a0;
-        w.w1 = o.a1;
-    } else if (sh < 64) {
-        w.w0 = (o.a0 >> sh) | (o.a1 << (64 - sh));
-        w.w1 = (o.a1 >> sh) | (o.b0 << (64 - sh));
-    } else if (sh == 64) {
-        w.w0 = o.a1;
-        w.w1 = o.b0;
-    } else {
-        const uint32_t s2 = sh - 64;
-        w.w0 = (o.a1 >> s2) | (o.b0 << (64 - s2));
-        w.w1 = (o.b0 >> s2) | (o.b1 << (64 - s2));
-    }
-    w.dm = off == 0 ? o.da : ((o.da >> off) | (o.db << (64 - off)));
-    return w;
+    if (off == 0) return o.a;
+    return Window{(o.a.lo >> off) | (o.b.lo << (64 - off)), (o.a.hi >> off) | (o.b.hi << (64 - off)),
+                  (o.a.dm >> off) | (o.b.dm << (64 - off))};
 }
 
-// Opens an empty row at position p of the 64-row window: rows p.. move up by
-// one and row 63 falls off.
+// Opens an empty row at position p of the window: rows p.. move up by one
+// and row 63 falls off (the same shift on each plane).
+__device__ __forceinline__ unsigned long long open_bit(unsigned long long x, unsigned long long below) {
+    return (x & below) | ((x & ~below) << 1);
+}
 __device__ __forceinline__ void open_row(Window& w, uint32_t p) {
-    const unsigned long long kl = p < 32 ? low_bits(2 * p) : ~0ull;        // rows below p in w0
-    const unsigned long long kh = p < 32 ? 0ull : low_bits(2 * p - 64);   // rows below p in w1
-    const unsigned long long carry = p < 32 ? w.w0 >> 62 : 0ull;          // row 31 moves to row 32
-    w.w1 = (w.w1 & kh) | ((w.w1 & ~kh) << 2) | carry;
-    w.w0 = (w.w0 & kl) | ((w.w0 & ~kl) << 2);
-    const unsigned long long kd = low_bits(p);
-    w.dm = (w.dm & kd) | ((w.dm & ~kd) << 1);
+    const unsigned long long below = (1ull << p) - 1ull;
+    w.lo = open_bit(w.lo, below);
+    w.hi = open_bit(w.hi, below);
+    w.dm = open_bit(w.dm, below);
 }
 
-// Spreads the old rows of window w over the rows of an output block whose
+// Spreads the old rows of window w over the rows of an output part whose
 // new rows are the set bits of F: the old rows keep their order and fill
 // the clear bits of F, the rows of F are left empty.  Few new rows: open one
 // row per set bit; many: move each of the few old rows to its place.
@@ -103,8 +109,8 @@ __device__ __forceinline__ Window spread_old(Window w, unsigned long long F) {
     while (z) {
         const uint32_t p = __ffsll((long long)z) - 1;
         z &= z - 1;
-        const unsigned long long code = ((src < 32 ? w.w0 >> (2 * src) : w.w1 >> (2 * src - 64))) & 3ull;
-        if (p < 32) o.w0 |= code << (2 * p); else o.w1 |= code << (2 * p - 64);
+        o.lo |= ((w.lo >> src) & 1ull) << p;
+        o.hi |= ((w.hi >> src) & 1ull) << p;
         o.dm |= ((w.dm >> src) & 1ull) << p;
         ++src;
     }
@@ -112,38 +118,42 @@ __device__ __forceinline__ Window spread_old(Window w, unsigned long long F) {
 }
 
 // One CTA builds one superblock of the next dictionary (kBlocksPerSuper
-// output blocks of 64 rows, rows [O, O + 2^16)) from the new symbols
+// output parts of 64 rows, rows [O, O + 2^16)) from the new symbols
 // [ins_i0[S], ins_i0[S+1]) that land in it (bint_gather wrote that plan):
 //  1. the CTA reads those new symbols' rows g_sa[i] + i and codes (a run of
-//     consecutive ones per thread) and sets, per output block, the mask F of
-//     its new rows, their terminator bits and their codes at their rows
-//     (shared memory; a thread merges the bits of its run per block first);
-//  2. a scan of popcount(F) over the blocks gives the new symbols before each
-//     block, so block b's old rows are the contiguous run starting at old row
-//     64 b - (new symbols before row 64 b);
-//  3. each thread builds output blocks (strided, so loads and stores of a
+//     consecutive ones per thread) and sets, per output part, the mask F of
+//     its new rows and their three planes at their rows (shared memory; a
+//     thread merges the bits of its run per part first);
+//  2. a scan of popcount(F) over the parts gives the new symbols before each
+//     part, so part j's old rows are the contiguous run starting at old row
+//     64 j - (new symbols before row 64 j);
+//  3. each thread builds output parts (strided, so loads and stores of a
 //     warp are contiguous): the 64-row old window, spread over the clear bits
-//     of F, OR the new codes;
-//  4. a scan of the per-block counts gives the 16-bit block counters.
+//     of F, OR the new rows' planes;
+//  4. a scan of the per-part counts gives the 16-bit block counters (the
+//     count before the first part of each occurrence block);
+//  5. the parts are written into their blocks of 64 K rows.
 // Every index that comes from g_sa is checked; an inconsistent plan flags
 // *d_err (bit 10) and never leads outside the arrays.
-template <class IdxT, int kT>
-__global__ void __launch_bounds__(kT) insert_kernel(const OccBlock* __restrict__ old_blocks, unsigned long long n_ext,
-                                                    const uint8_t* __restrict__ bint, const IdxT* __restrict__ gsa,
-                                                    unsigned long long n_int, const uint32_t* __restrict__ ins_i0,
-                                                    OccBlock* __restrict__ new_blocks, unsigned long long n_new,
-                                                    uint32_t* __restrict__ sb_tot, uint32_t* __restrict__ d_err) {
+template <class IdxT, int kT, int K>
+__global__ void __launch_bounds__(kT, kT == 256 ? 4 : 2) insert_kernel(const unsigned long long* __restrict__ old_words,
+                                                    unsigned long long n_ext, const uint8_t* __restrict__ bint,
+                                                    const IdxT* __restrict__ gsa, unsigned long long n_int,
+                                                    const uint32_t* __restrict__ ins_i0,
+                                                    unsigned long long* __restrict__ new_words,
+                                                    unsigned long long n_new, uint32_t* __restrict__ sb_tot,
+                                                    uint32_t* __restrict__ d_err) {
     constexpr int kNB = kBlocksPerSuper, kPer = kNB / kT;
-    __shared__ uint32_t sF[2][kNB];  // new rows of each block (rows 0-31, 32-63); later its counts
-    __shared__ uint32_t sD[2][kNB];  // terminator mask: of the new rows, later of the whole block
-    __shared__ uint32_t sC[4][kNB];  // 2-bit codes, 16 rows per word: of the new rows, later of the block
-    __shared__ uint32_t sP[2][kNB];  // new symbols before each block; later the block counters
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    __shared__ uint32_t sF[2][kNB];  // new rows of each part (rows 0-31, 32-63); later its counts
+    __shared__ uint32_t sD[2][kNB];  // terminator plane: of the new rows, later of the whole part
+    __shared__ uint32_t sC[4][kNB];  // lo plane (words 0, 1) and hi plane (2, 3): of the new rows, then the part
+    __shared__ uint32_t sP[2][kNB];  // new symbols before each part; later the block counters
+    const int tid = threadIdx.x;
     const uint64_t S = blockIdx.x;
     const uint64_t O = S << kSuperShift;
-    const uint64_t b_first = S * kNB;
-    const uint64_t nb_new = (n_new >> kOccShift) + 1;
-    const uint64_t nb_old = (n_ext >> kOccShift) + 1;
+    const uint64_t p_first = S * kNB;
+    const uint64_t np_new = dict_parts(n_new, K);
+    const uint64_t np_old = dict_parts(n_ext, K);
     for (int x = tid; x < kNB; x += kT) {
         sF[0][x] = sF[1][x] = sD[0][x] = sD[1][x] = 0u;
         sC[0][x] = sC[1][x] = sC[2][x] = sC[3][x] = 0u;
@@ -156,10 +166,10 @@ __global__ void __launch_bounds__(kT) insert_kernel(const OccBlock* __restrict__
     }
     __syncthreads();
 
-    // 1. the new rows of every block of this superblock: each thread takes a
+    // 1. the new rows of every part of this superblock: each thread takes a
     //    run of kRun consecutive new symbols (consecutive rows, so a run
-    //    touches one or two blocks when the new rows are dense), gathers
-    //    their bits per block in registers and ORs each block's bits into
+    //    touches one or two parts when the new rows are dense), gathers
+    //    their bits per part in registers and ORs each part's bits into
     //    shared memory once
     for (uint64_t base = i_begin + (uint64_t)tid * kRun; base < i_end; base += (uint64_t)kT * kRun) {
         uint64_t loc[kRun];
@@ -171,17 +181,17 @@ __global__ void __launch_bounds__(kT) insert_kernel(const OccBlock* __restrict__
             xs[u] = i < i_end ? bint[i] : 0u;
         }
         uint32_t cj = 0xFFFFFFFFu;
-        unsigned long long f = 0, dm = 0, c0 = 0, c1 = 0;
+        unsigned long long f = 0, dm = 0, lo = 0, hi = 0;
         auto flush = [&]() {
             if (cj == 0xFFFFFFFFu) return;
             if ((uint32_t)f) atomicOr(&sF[0][cj], (uint32_t)f);
             if ((uint32_t)(f >> 32)) atomicOr(&sF[1][cj], (uint32_t)(f >> 32));
             if ((uint32_t)dm) atomicOr(&sD[0][cj], (uint32_t)dm);
             if ((uint32_t)(dm >> 32)) atomicOr(&sD[1][cj], (uint32_t)(dm >> 32));
-            if ((uint32_t)c0) atomicOr(&sC[0][cj], (uint32_t)c0);
-            if ((uint32_t)(c0 >> 32)) atomicOr(&sC[1][cj], (uint32_t)(c0 >> 32));
-            if ((uint32_t)c1) atomicOr(&sC[2][cj], (uint32_t)c1);
-            if ((uint32_t)(c1 >> 32)) atomicOr(&sC[3][cj], (uint32_t)(c1 >> 32));
+            if ((uint32_t)lo) atomicOr(&sC[0][cj], (uint32_t)lo);
+            if ((uint32_t)(lo >> 32)) atomicOr(&sC[1][cj], (uint32_t)(lo >> 32));
+            if ((uint32_t)hi) atomicOr(&sC[2][cj], (uint32_t)hi);
+            if ((uint32_t)(hi >> 32)) atomicOr(&sC[3][cj], (uint32_t)(hi >> 32));
         };
 #pragma unroll
         for (int u = 0; u < kRun; ++u) {
@@ -195,21 +205,22 @@ __global__ void __launch_bounds__(kT) insert_kernel(const OccBlock* __restrict__
             if (j != cj) {
                 flush();
                 cj = j;
-                f = dm = c0 = c1 = 0;
+                f = dm = lo = hi = 0;
             }
-            f |= 1ull << q;
+            const unsigned long long bit = 1ull << q;
+            f |= bit;
             if (xs[u] == kBintDollar) {
-                dm |= 1ull << q;
+                dm |= bit;
             } else {
-                const unsigned long long cv = (unsigned long long)(xs[u] & 3u) << (2u * (q & 31u));
-                if (q < 32) c0 |= cv; else c1 |= cv;
+                if (xs[u] & 1u) lo |= bit;
+                if (xs[u] & 2u) hi |= bit;
             }
         }
         flush();
     }
     __syncthreads();
 
-    // 2. new symbols before each block (blocks kPer * tid .. in order)
+    // 2. new symbols before each part (parts kPer * tid .. in order)
     {
         uint32_t c[kPer], tot = 0;
 #pragma unroll
@@ -230,52 +241,50 @@ __global__ void __launch_bounds__(kT) insert_kernel(const OccBlock* __restrict__
     }
     __syncthreads();
 
-    // 3. build blocks tid, tid + kT, ...; keep them in shared memory.  The
-    //    old blocks of every window are loaded before any is used.
+    // 3. build parts tid, tid + kT, ...; keep them in shared memory.  The
+    //    old parts of every window are loaded before any is used.
     OldPair op[kPer];
     uint64_t s_old[kPer];
 #pragma unroll
     for (int bb = 0; bb < kPer; ++bb) {
         const int j = tid + bb * kT;
-        const uint64_t b = b_first + j;
+        const uint64_t b = p_first + j;
         const uint64_t o = b << kOccShift;
         const uint64_t inew = i_begin + sP[0][j];  // new symbols before row o
         s_old[bb] = o - inew;
-        if (b < nb_new && (inew > o || s_old[bb] > n_ext)) {
-            atomicOr(d_err, 1024u);
-            s_old[bb] = inew > o ? 0ull : (uint64_t)n_ext;
-        }
-        if (b >= nb_new) s_old[bb] = 0;
-        op[bb] = old_pair(old_blocks, nb_old, s_old[bb]);
+        // (parts past the last row, in the last block of 64 K rows, hold
+        // nothing: their window is never used)
+        if (b < np_new && o <= n_new && (inew > o || s_old[bb] > n_ext)) atomicOr(d_err, 1024u);
+        if (inew > o || s_old[bb] > n_ext) s_old[bb] = inew > o ? 0ull : (uint64_t)n_ext;
+        if (b >= np_new) s_old[bb] = 0;
+        op[bb] = old_pair<K>(old_words, np_old, s_old[bb]);
     }
 #pragma unroll
     for (int bb = 0; bb < kPer; ++bb) {
         const int j = tid + bb * kT;
-        const uint64_t b = b_first + j;
-        if (b >= nb_new) {
+        const uint64_t b = p_first + j;
+        if (b >= np_new) {
             sF[0][j] = sF[1][j] = 0u;
             continue;
         }
         const uint64_t o = b << kOccShift;
         const unsigned long long F = (unsigned long long)sF[0][j] | ((unsigned long long)sF[1][j] << 32);
         Window w = spread_old(old_window_of(op[bb], s_old[bb]), F);
-        w.w0 |= (unsigned long long)sC[0][j] | ((unsigned long long)sC[1][j] << 32);
-        w.w1 |= (unsigned long long)sC[2][j] | ((unsigned long long)sC[3][j] << 32);
+        w.lo |= (unsigned long long)sC[0][j] | ((unsigned long long)sC[1][j] << 32);
+        w.hi |= (unsigned long long)sC[2][j] | ((unsigned long long)sC[3][j] << 32);
         w.dm |= (unsigned long long)sD[0][j] | ((unsigned long long)sD[1][j] << 32);
         const uint32_t valid = n_new > o ? (uint32_t)min((unsigned long long)kOccSpan, n_new - o) : 0u;
-        const unsigned long long v0 = low_bits(2 * min(valid, 32u));
-        const unsigned long long v1 = valid > 32 ? low_bits(2 * (valid - 32)) : 0ull;
-        w.w0 &= v0;
-        w.w1 &= v1;
-        w.dm &= low_bits(valid);
+        const unsigned long long vm = low_bits(valid);
+        w.lo &= vm;
+        w.hi &= vm;
+        w.dm &= vm;
         uint32_t cnt[4];
 #pragma unroll
-        for (uint32_t c = 0; c < 4; ++c) cnt[c] = __popcll(match_code(w.w0, c) & v0) + __popcll(match_code(w.w1, c) & v1);
-        cnt[0] -= __popcll(w.dm);
-        sC[0][j] = (uint32_t)w.w0;
-        sC[1][j] = (uint32_t)(w.w0 >> 32);
-        sC[2][j] = (uint32_t)w.w1;
-        sC[3][j] = (uint32_t)(w.w1 >> 32);
+        for (uint32_t c = 0; c < 4; ++c) cnt[c] = __popcll(plane_match(w.lo, w.hi, w.dm, c) & vm);
+        sC[0][j] = (uint32_t)w.lo;
+        sC[1][j] = (uint32_t)(w.lo >> 32);
+        sC[2][j] = (uint32_t)w.hi;
+        sC[3][j] = (uint32_t)(w.hi >> 32);
         sD[0][j] = (uint32_t)w.dm;
         sD[1][j] = (uint32_t)(w.dm >> 32);
         sF[0][j] = cnt[0] | (cnt[1] << 16);
@@ -283,7 +292,7 @@ __global__ void __launch_bounds__(kT) insert_kernel(const OccBlock* __restrict__
     }
     __syncthreads();
 
-    // 4. 16-bit block counters: exclusive scan of the counts in block order
+    // 4. 16-bit block counters: exclusive scan of the counts in part order
     {
         unsigned long long t01 = 0, t23 = 0;
         uint32_t a[kPer], d[kPer];
@@ -317,17 +326,29 @@ __global__ void __launch_bounds__(kT) insert_kernel(const OccBlock* __restrict__
     }
     __syncthreads();
 
-    // 5. write the blocks out (a warp stores 32 consecutive blocks)
+    // 5. write the parts out (a warp stores 32 consecutive parts); the first
+    //    part of each occurrence block also writes the block's counters
 #pragma unroll
     for (int bb = 0; bb < kPer; ++bb) {
         const int j = tid + bb * kT;
-        const uint64_t b = b_first + j;
-        if (b >= nb_new) break;
-        ulonglong2* dst = reinterpret_cast<ulonglong2*>(new_blocks + b);
-        dst[0] = make_ulonglong2((unsigned long long)sC[0][j] | ((unsigned long long)sC[1][j] << 32),
-                                 (unsigned long long)sC[2][j] | ((unsigned long long)sC[3][j] << 32));
-        dst[1] = make_ulonglong2((unsigned long long)sD[0][j] | ((unsigned long long)sD[1][j] << 32),
-                                 (unsigned long long)sP[0][j] | ((unsigned long long)sP[1][j] << 32));
+        const uint64_t b = p_first + j;
+        if (b >= np_new) break;
+        const unsigned long long lo = (unsigned long long)sC[0][j] | ((unsigned long long)sC[1][j] << 32);
+        const unsigned long long hi = (unsigned long long)sC[2][j] | ((unsigned long long)sC[3][j] << 32);
+        const unsigned long long dm = (unsigned long long)sD[0][j] | ((unsigned long long)sD[1][j] << 32);
+        const unsigned long long cnt = (unsigned long long)sP[0][j] | ((unsigned long long)sP[1][j] << 32);
+        if constexpr (K == 1) {
+            ulonglong2* dst = reinterpret_cast<ulonglong2*>(new_words) + 2 * b;
+            dst[0] = make_ulonglong2(lo, hi);
+            dst[1] = make_ulonglong2(dm, cnt);
+        } else {
+            unsigned long long* dst = new_words + (b / K) * Occ<K>::kWords;
+            const uint32_t q = (uint32_t)(b % K);
+            dst[3 * q] = lo;
+            dst[3 * q + 1] = hi;
+            dst[3 * q + 2] = dm;
+            if (q == 0) dst[3 * K] = cnt;
+        }
     }
 }
 
@@ -616,7 +637,8 @@ void super_scan(Launcher& L, const uint32_t* sb_tot, uint64_t nsb, unsigned long
 template <class IdxT>
 void launch_insert(Launcher& L, const void* old_blocks, uint64_t n_ext, const uint8_t* bint, const IdxT* gsa,
                    uint64_t n_int, const uint32_t* ins_i0, void* new_blocks, unsigned long long* new_super,
-                   unsigned long long* new_C, uint64_t m_new, uint32_t* sb_tot, uint32_t* d_err, int code_bits) {
+                   unsigned long long* new_C, uint64_t m_new, uint32_t* sb_tot, uint32_t* d_err, int code_bits,
+                   int occ_k) {
     const uint64_t n_new = n_ext + n_int;
     // the superblock scan's per-chunk totals live after the superblock totals
     const uint64_t nsb_all = dict_supers_of(n_new, code_bits);
@@ -634,21 +656,34 @@ void launch_insert(Launcher& L, const void* old_blocks, uint64_t n_ext, const ui
         return;
     }
     const uint64_t nsb = dict_supers(n_new);
-    const double bytes = 32.0 * dict_blocks(n_ext) + (1.0 + sizeof(IdxT)) * n_int + 32.0 * dict_blocks(n_new) +
+    const double bb = (double)dict_block_bytes(2, occ_k);
+    const double bytes = bb * dict_blocks(n_ext, occ_k) + (1.0 + sizeof(IdxT)) * n_int + bb * dict_blocks(n_new, occ_k) +
                          4.0 * (nsb + 1);
-    SBWT_LAUNCH(L, "insert_merge", bytes, 0, nullptr, (insert_kernel<IdxT, kInsertThreads>), (unsigned)nsb,
-                kInsertThreads, 0, static_cast<const OccBlock*>(old_blocks), (unsigned long long)n_ext, bint, gsa,
-                (unsigned long long)n_int, ins_i0, static_cast<OccBlock*>(new_blocks), (unsigned long long)n_new,
-                sb_tot, d_err);
+    // Dense new rows (a quarter of the result or more): 512 threads, so the
+    // runs of new symbols spread over more threads.  Sparse: 256 threads of
+    // four parts each, so more CTAs (superblocks) are resident per SM and
+    // their load latencies overlap.
+    const bool dense = 4 * n_int >= n_new;
+    const int threads = dense ? kInsertThreads : kInsertThreadsSparse;
+    auto* const kern = dense ? (occ_k == 4 ? insert_kernel<IdxT, kInsertThreads, 4>
+                                           : (occ_k == 2 ? insert_kernel<IdxT, kInsertThreads, 2>
+                                                         : insert_kernel<IdxT, kInsertThreads, 1>))
+                             : (occ_k == 4 ? insert_kernel<IdxT, kInsertThreadsSparse, 4>
+                                           : (occ_k == 2 ? insert_kernel<IdxT, kInsertThreadsSparse, 2>
+                                                         : insert_kernel<IdxT, kInsertThreadsSparse, 1>));
+    SBWT_LAUNCH(L, "insert_merge", bytes, 0, nullptr, kern, (unsigned)nsb, threads, 0,
+                static_cast<const unsigned long long*>(old_blocks), (unsigned long long)n_ext, bint, gsa,
+                (unsigned long long)n_int, ins_i0, static_cast<unsigned long long*>(new_blocks),
+                (unsigned long long)n_new, sb_tot, d_err);
     super_scan<4>(L, sb_tot, nsb, new_super, new_C, m_new, chunk_tot);
 }
 
 template void launch_insert<uint32_t>(Launcher&, const void*, uint64_t, const uint8_t*, const uint32_t*, uint64_t,
                                       const uint32_t*, void*, unsigned long long*, unsigned long long*, uint64_t,
-                                      uint32_t*, uint32_t*, int);
+                                      uint32_t*, uint32_t*, int, int);
 template void launch_insert<unsigned long long>(Launcher&, const void*, uint64_t, const uint8_t*,
                                                 const unsigned long long*, uint64_t, const uint32_t*, void*,
                                                 unsigned long long*, unsigned long long*, uint64_t, uint32_t*,
-                                                uint32_t*, int);
+                                                uint32_t*, int, int);
 
 }  // namespace sbwt

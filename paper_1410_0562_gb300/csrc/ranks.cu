@@ -33,34 +33,27 @@ __global__ void __launch_bounds__(kThreads) bint_kernel(const uint32_t* __restri
 constexpr uint32_t kSuperStageBytes = 48 * 1024;
 
 // rank(c, i) within i's superblock of the 2-bit dictionary, with row
-// arithmetic in the index type I (32 bits for a 32-bit index) and no
-// branches over r or c.
-template <class I>
-__device__ __forceinline__ I occ_in_super_i(const OccBlock* __restrict__ blocks, uint32_t c, I i) {
-    const ulonglong2* p = reinterpret_cast<const ulonglong2*>(blocks + (i >> kOccShift));
-    const ulonglong2 s = __ldg(p);
-    const ulonglong2 d = __ldg(p + 1);
-    const uint32_t r = (uint32_t)i & (kOccSpan - 1);
-    const uint32_t r2 = 2 * r;
-    const unsigned long long rep = (c & 2) ? ((c & 1) ? 0xFFFFFFFFFFFFFFFFull : 0xAAAAAAAAAAAAAAAAull)
-                                           : ((c & 1) ? 0x5555555555555555ull : 0ull);
-    const unsigned long long y0 = s.x ^ rep, y1 = s.y ^ rep;
-    const unsigned long long m0 = ~(y0 | (y0 >> 1)) & 0x5555555555555555ull;
-    const unsigned long long m1 = ~(y1 | (y1 >> 1)) & 0x5555555555555555ull;
-    const unsigned long long lo0 = r2 >= 64 ? ~0ull : (1ull << r2) - 1ull;
-    const unsigned long long lo1 = r2 > 64 ? (1ull << (r2 - 64)) - 1ull : 0ull;
-    const unsigned long long dm = c == 0 ? d.x : 0ull;
-    const uint32_t in_block = (uint32_t)__popcll(m0 & lo0) + (uint32_t)__popcll(m1 & lo1) -
-                              (uint32_t)__popcll(dm & ((1ull << r) - 1ull));
-    return (I)(((uint32_t)(d.y >> (16 * c)) & 0xFFFFu) + in_block);
+// arithmetic in the index type I (32 bits for a 32-bit index).
+template <class I, int K>
+__device__ __forceinline__ I occ_in_super_i(const unsigned long long* __restrict__ words, uint32_t c, I i) {
+    if constexpr (K == 1) {
+        const ulonglong2* p = reinterpret_cast<const ulonglong2*>(words) + 2 * (i >> kOccShift);
+        const ulonglong2 s = __ldg(p);      // lo, hi
+        const ulonglong2 d = __ldg(p + 1);  // dm, counts
+        const uint32_t r = (uint32_t)i & (kOccSpan - 1);
+        const unsigned long long m = plane_match(s.x, s.y, d.x, c) & ((1ull << r) - 1ull);
+        return (I)(((uint32_t)(d.y >> (16 * c)) & 0xFFFFu) + (uint32_t)__popcll(m));
+    } else {
+        return (I)occ_rank_in_super<K>(words, c, (unsigned long long)i);
+    }
 }
 
-template <class IdxT, bool kStage, int kB>
+template <class IdxT, bool kStage, int kB, int K>
 __global__ void __launch_bounds__(kThreads) compute_ranks_kernel(const uint32_t* __restrict__ text,
                                                                  const unsigned long long* __restrict__ offsets,
                                                                  unsigned long long j_begin,
                                                                  unsigned long long nreads,
-                                                                 const typename DictLayout<kB>::Block* blocks,
+                                                                 const typename DictLayout<kB, K>::Block* blocks,
                                                                  const unsigned long long* __restrict__ super,
                                                                  const unsigned long long* __restrict__ d_C,
                                                                  unsigned long long n_ext,
@@ -69,7 +62,7 @@ __global__ void __launch_bounds__(kThreads) compute_ranks_kernel(const uint32_t*
     // row and position arithmetic in the index type: a 32-bit index has
     // fewer than 2^32 rows and text positions
     using I = IdxT;
-    constexpr int kSS = DictLayout<kB>::kSuperShift, kCodes = DictLayout<kB>::kCodes;
+    constexpr int kSS = DictLayout<kB, K>::kSuperShift, kCodes = DictLayout<kB, K>::kCodes;
     constexpr uint32_t kPer = 32 / kB;  // codes per text word
     extern __shared__ unsigned long long s_raw[];
     I* s_super = reinterpret_cast<I*>(s_raw);
@@ -127,10 +120,10 @@ __global__ void __launch_bounds__(kThreads) compute_ranks_kernel(const uint32_t*
         I Cc, in;
         if constexpr (kB == 2) {
             Cc = (c & 2) ? ((c & 1) ? C3 : C2) : ((c & 1) ? C1 : C0);
-            in = occ_in_super_i<I>(blocks, c, i);
+            in = occ_in_super_i<I, K>(blocks, c, i);
         } else {
             Cc = (I)__ldg(d_C + c);
-            in = (I)DictLayout<kB>::in_super(blocks, c, i);
+            in = (I)DictLayout<kB, K>::in_super(blocks, c, i);
         }
         const I sup = kStage ? s_super[(i >> kSS) * kCodes + c] : (I)__ldg(super + (i >> kSS) * kCodes + c);
         i = Cc + sup + in;
@@ -144,6 +137,112 @@ __global__ void __launch_bounds__(kThreads) compute_ranks_kernel(const uint32_t*
 #pragma unroll
     for (int r = 0; r < G; ++r)
         if (r < held) g[rs + r] = s[r];
+}
+
+// ComputeRanks for long reads, one thread per segment of kSegRows positions
+// of a read, so a block of few long reads still runs many LF chains at once.
+// Segment q of read j covers positions [a, b) = [q kSegRows, min((q+1)
+// kSegRows, len + 1)), the terminator at len.  The last segment starts, as
+// Algorithm 2 does, from the terminator's rank start.  Any other segment first
+// needs g at b exactly: backward search (Lemma 1 applied to the interval of
+// old suffixes that start with P[b .. e)) over the L symbols from b on; once
+// that interval is empty, its lower end is the number of old suffixes
+// smaller than P[b ..] whatever follows e, which is g[b] (with L doubled while
+// the L-mer still occurs in B_ext, and the exact chain from the terminator
+// once e would pass the read's end).  From g[b] it steps down to a with
+// Lemma 1, like the per-read kernel.  Reads of up to 2 kSegRows symbols take
+// the per-read kernel.
+constexpr uint32_t kSegRows = 256;
+constexpr uint32_t kProbe0 = 32;  // first backward-search window
+
+template <class IdxT, bool kStage, int kB, int K>
+__global__ void __launch_bounds__(kThreads) compute_ranks_seg_kernel(const uint32_t* __restrict__ text,
+                                                                     const unsigned long long* __restrict__ offsets,
+                                                                     unsigned long long j_begin,
+                                                                     unsigned long long nreads, uint32_t segs,
+                                                                     const typename DictLayout<kB, K>::Block* blocks,
+                                                                     const unsigned long long* __restrict__ super,
+                                                                     const unsigned long long* __restrict__ d_C,
+                                                                     unsigned long long n_ext,
+                                                                     unsigned long long m_start,
+                                                                     IdxT* __restrict__ g, uint32_t* __restrict__ d_err) {
+    using I = IdxT;
+    using D = DictLayout<kB, K>;
+    constexpr int kSS = D::kSuperShift, kCodes = D::kCodes;
+    constexpr uint32_t kPer = 32 / kB;
+    extern __shared__ unsigned long long s_raw[];
+    I* s_super = reinterpret_cast<I*>(s_raw);
+    if (kStage) {
+        const uint32_t words = ((uint32_t)(n_ext >> kSS) + 1) * kCodes;
+        for (uint32_t x = threadIdx.x; x < words; x += kThreads) s_super[x] = (I)super[x];
+        __syncthreads();
+    }
+    const uint64_t t = (uint64_t)blockIdx.x * kThreads + threadIdx.x;
+    const uint64_t j = t / segs;
+    const uint32_t q = (uint32_t)(t % segs);
+    if (j >= nreads) return;
+    const uint64_t jj = j_begin + j;
+    const uint64_t o0 = offsets[j_begin];
+    const uint64_t oj = offsets[jj];
+    const I len = (I)(offsets[jj + 1] - oj);
+    const I a = (I)q * kSegRows;
+    if (a > len) return;  // this read has fewer segments
+    const I b = min((I)(a + kSegRows), (I)(len + 1));
+    const I rs = (I)(oj - o0 + j);  // block-local position of the read's first symbol
+    const I P = (I)(oj + jj);       // the same position in the append's text
+    const I nx = (I)n_ext;
+    auto code_at = [&](I k) -> uint32_t {  // symbol at read position k < len
+        const I tt = P + k;
+        return (__ldg(text + tt / kPer) >> (32u - kB - kB * (uint32_t)(tt % kPer))) & ((1u << kB) - 1u);
+    };
+    // Lemma 1: rank of c P[k..] among the old suffixes from the rank i of P[k..]
+    auto step = [&](uint32_t c, I i) -> I {
+        const I Cc = (I)__ldg(d_C + c);
+        const I sup = kStage ? s_super[(i >> kSS) * kCodes + c] : (I)__ldg(super + (i >> kSS) * kCodes + c);
+        I r = Cc + sup + (I)D::in_super(blocks, c, i);
+        if (r > nx) {
+            atomicOr(d_err, 8u);
+            r = nx;
+        }
+        return r;
+    };
+    // the chain from the terminator (exact start) down to position `to`
+    auto chain_from_end = [&](I to) -> I {
+        I i = (I)m_start;
+        for (I k = len; k > to; --k) i = step(code_at(k - 1), i);
+        return i;
+    };
+    I i, top;  // i = g at position top
+    if (b == len + 1) {
+        i = (I)m_start;  // the segment holds the terminator
+        top = len;
+        g[rs + len] = i;
+    } else {
+        top = b;
+        i = 0;
+        for (uint64_t L = kProbe0;; L *= 4) {
+            if ((uint64_t)b + L > (uint64_t)len) {
+                i = chain_from_end(b);
+                break;
+            }
+            I lo = 0, hi = nx;
+            I k = (I)(b + L);
+            for (; k > b && lo < hi; --k) {
+                const uint32_t c = code_at(k - 1);
+                lo = step(c, lo);
+                hi = step(c, hi);
+            }
+            if (lo == hi) {  // no old suffix starts with P[k .. b + L): lo is exact from here
+                for (; k > b; --k) lo = step(code_at(k - 1), lo);
+                i = lo;
+                break;
+            }
+        }
+    }
+    for (I k = top; k > a; --k) {
+        i = step(code_at(k - 1), i);
+        g[rs + k - 1] = i;
+    }
 }
 
 // B_int and g_sa in one pass over SA_int (both index by SA_int[i]).  With
@@ -189,23 +288,23 @@ __global__ void __launch_bounds__(kThreads) bint_gather_kernel(const uint32_t* _
 }
 
 // rank(c, k) queries, codes 0..kCodes-1, or kCodes for the terminator.
-template <int kB>
-__global__ void __launch_bounds__(kThreads) rank_batch_kernel(const typename DictLayout<kB>::Block* blocks,
+template <int kB, int K>
+__global__ void __launch_bounds__(kThreads) rank_batch_kernel(const typename DictLayout<kB, K>::Block* blocks,
                                                               const unsigned long long* __restrict__ super,
                                                               const uint8_t* __restrict__ codes,
                                                               const unsigned long long* __restrict__ ks,
                                                               unsigned long long q,
                                                               unsigned long long* __restrict__ out) {
-    constexpr uint32_t kCodes = DictLayout<kB>::kCodes;
+    constexpr uint32_t kCodes = DictLayout<kB, K>::kCodes;
     const uint64_t i = (uint64_t)blockIdx.x * kThreads + threadIdx.x;
     if (i >= q) return;
     const uint32_t c = codes[i];
     const unsigned long long k = ks[i];
     if (c < kCodes) {
-        out[i] = dict_rank<kB>(blocks, super, c, k);
+        out[i] = dict_rank<kB, K>(blocks, super, c, k);
     } else {  // terminators: every row before k that holds no symbol
         unsigned long long s = 0;
-        for (uint32_t x = 0; x < kCodes; ++x) s += dict_rank<kB>(blocks, super, x, k);
+        for (uint32_t x = 0; x < kCodes; ++x) s += dict_rank<kB, K>(blocks, super, x, k);
         out[i] = k - s;
     }
 }
@@ -214,8 +313,8 @@ __global__ void __launch_bounds__(kThreads) rank_batch_kernel(const typename Dic
 // read): the rows of the suffixes that start with P[k..] are [lo, hi); one
 // step per symbol, right to left, from [0, n).  hi - lo counts P.  A byte
 // outside the alphabet (code table in shared memory) counts zero.
-template <int kB>
-__global__ void __launch_bounds__(kThreads) count_kernel(const typename DictLayout<kB>::Block* blocks,
+template <int kB, int K>
+__global__ void __launch_bounds__(kThreads) count_kernel(const typename DictLayout<kB, K>::Block* blocks,
                                                          const unsigned long long* __restrict__ super,
                                                          const unsigned long long* __restrict__ d_C,
                                                          unsigned long long n, Alphabet16 alpha, int sigma,
@@ -238,42 +337,43 @@ __global__ void __launch_bounds__(kThreads) count_kernel(const typename DictLayo
             break;
         }
         const unsigned long long Cc = __ldg(d_C + c);
-        lo = Cc + dict_rank<kB>(blocks, super, c, lo);
-        hi = Cc + dict_rank<kB>(blocks, super, c, hi);
+        lo = Cc + dict_rank<kB, K>(blocks, super, c, lo);
+        hi = Cc + dict_rank<kB, K>(blocks, super, c, hi);
     }
     out[i] = hi > lo ? hi - lo : 0ull;
 }
 
-__global__ void __launch_bounds__(kThreads) unpack_kernel(const OccBlock* __restrict__ blocks,
+// The read-back of the 2-bit dictionary: one 64-row part per thread, 64
+// output bytes written as four 16-byte stores when the part is whole; rows
+// [r0, r1), r0 a multiple of 64.
+template <int K>
+__global__ void __launch_bounds__(kThreads) unpack_kernel(const unsigned long long* __restrict__ words,
                                                           unsigned long long r0, unsigned long long r1,
                                                           uint32_t alpha4, uint8_t* __restrict__ out) {
-    // one occurrence block (64 rows) per thread, 64 output bytes written as
-    // four 16-byte stores when the block is whole; rows [r0, r1), r0 a
-    // multiple of 64
-    const uint64_t b = (r0 >> kOccShift) + (uint64_t)blockIdx.x * kThreads + threadIdx.x;
-    const uint64_t row0 = b << kOccShift;
+    const uint64_t part = (r0 >> kOccShift) + (uint64_t)blockIdx.x * kThreads + threadIdx.x;
+    const uint64_t row0 = part << kOccShift;
     if (row0 >= r1) return;
-    const OccBlock blk = blocks[b];
-    uint32_t words[16];
+    const unsigned long long* p = words + (part / K) * Occ<K>::kWords + 3 * (part % K);
+    const unsigned long long lo = p[0], hi = p[1], dm = p[2];
+    uint32_t wd[16];
 #pragma unroll
     for (int w = 0; w < 16; ++w) {
         uint32_t x = 0;
 #pragma unroll
         for (int q4 = 0; q4 < 4; ++q4) {
             const uint32_t q = 4 * w + q4;
-            const uint32_t c = (uint32_t)(blk.sym[q >> 5] >> (2 * (q & 31))) & 3u;
-            const uint32_t byte = ((blk.dmask >> q) & 1ull) ? (uint32_t)'$' : ((alpha4 >> (8 * c)) & 0xFFu);
+            const uint32_t c = (uint32_t)((lo >> q) & 1ull) | ((uint32_t)((hi >> q) & 1ull) << 1);
+            const uint32_t byte = ((dm >> q) & 1ull) ? (uint32_t)'$' : ((alpha4 >> (8 * c)) & 0xFFu);
             x |= byte << (8 * q4);
         }
-        words[w] = x;
+        wd[w] = x;
     }
     if (row0 + kOccSpan <= r1) {
         uint4* dst = reinterpret_cast<uint4*>(out + row0);
 #pragma unroll
-        for (int v = 0; v < 4; ++v)
-            dst[v] = make_uint4(words[4 * v], words[4 * v + 1], words[4 * v + 2], words[4 * v + 3]);
+        for (int v = 0; v < 4; ++v) dst[v] = make_uint4(wd[4 * v], wd[4 * v + 1], wd[4 * v + 2], wd[4 * v + 3]);
     } else {
-        for (uint32_t q = 0; q < (uint32_t)(r1 - row0); ++q) out[row0 + q] = (uint8_t)(words[q >> 2] >> (8 * (q & 3)));
+        for (uint32_t q = 0; q < (uint32_t)(r1 - row0); ++q) out[row0 + q] = (uint8_t)(wd[q >> 2] >> (8 * (q & 3)));
     }
 }
 
@@ -319,18 +419,39 @@ uint32_t alpha4_of(const Alphabet16& alpha) {
     return a4;
 }
 
-template <class IdxT, int kB>
+template <class IdxT, int kB, int K>
 void compute_ranks_launch(Launcher& L, const uint32_t* text, const uint64_t* d_offsets, uint64_t j_begin,
-                          uint64_t nreads, double bytes, const void* blocks, const unsigned long long* super,
-                          const unsigned long long* d_C, uint64_t n_ext, uint64_t m_ext, IdxT* g, uint32_t* d_err) {
-    using Block = typename DictLayout<kB>::Block;
-    const size_t stage = ((n_ext >> DictLayout<kB>::kSuperShift) + 1) * DictLayout<kB>::kCodes * sizeof(IdxT);
-    auto* const kern = stage <= kSuperStageBytes ? compute_ranks_kernel<IdxT, true, kB>
-                                                 : compute_ranks_kernel<IdxT, false, kB>;
+                          uint64_t nreads, uint64_t max_len, double bytes, const void* blocks,
+                          const unsigned long long* super, const unsigned long long* d_C, uint64_t n_ext,
+                          uint64_t m_ext, IdxT* g, uint32_t* d_err) {
+    using D = DictLayout<kB, K>;
+    using Block = typename D::Block;
+    const size_t stage = ((n_ext >> D::kSuperShift) + 1) * D::kCodes * sizeof(IdxT);
+    const bool staged = stage <= kSuperStageBytes;
+    const auto* offs = reinterpret_cast<const unsigned long long*>(d_offsets);
+    if (max_len > 2 * kSegRows) {  // long reads: one thread per segment
+        const uint32_t segs = (uint32_t)(max_len / kSegRows + 1);
+        auto* const kern = staged ? compute_ranks_seg_kernel<IdxT, true, kB, K>
+                                  : compute_ranks_seg_kernel<IdxT, false, kB, K>;
+        SBWT_LAUNCH(L, "compute_ranks", bytes, 0, nullptr, kern, ceil_div_u(nreads * segs, kThreads), kThreads,
+                    staged ? stage : 0, text, offs, (unsigned long long)j_begin, (unsigned long long)nreads, segs,
+                    static_cast<const Block*>(blocks), super, d_C, (unsigned long long)n_ext,
+                    (unsigned long long)m_ext, g, d_err);
+        return;
+    }
+    auto* const kern = staged ? compute_ranks_kernel<IdxT, true, kB, K> : compute_ranks_kernel<IdxT, false, kB, K>;
     SBWT_LAUNCH(L, "compute_ranks", bytes, 0, nullptr, kern, ceil_div_u(nreads, kThreads), kThreads,
-                stage <= kSuperStageBytes ? stage : 0, text, reinterpret_cast<const unsigned long long*>(d_offsets),
-                (unsigned long long)j_begin, (unsigned long long)nreads, static_cast<const Block*>(blocks), super, d_C,
-                (unsigned long long)n_ext, (unsigned long long)m_ext, g, d_err);
+                staged ? stage : 0, text, offs, (unsigned long long)j_begin, (unsigned long long)nreads,
+                static_cast<const Block*>(blocks), super, d_C, (unsigned long long)n_ext, (unsigned long long)m_ext,
+                g, d_err);
+}
+
+// Sectors a rank query of the 2-bit dictionary reads: one for sampling 64,
+// the counts plus the parts before the row for 128 and 256 (on average half
+// of them, rounded up to whole sectors).
+double rank_query_bytes(int code_bits, int occ_k) {
+    if (code_bits == 4) return 64.0;
+    return occ_k == 1 ? 32.0 : (occ_k == 2 ? 64.0 : 96.0);
 }
 
 }  // namespace
@@ -344,19 +465,25 @@ void launch_bint(Launcher& L, const uint32_t* text, const uint32_t* term, uint64
 
 template <class IdxT>
 void launch_compute_ranks(Launcher& L, const uint32_t* text, const uint64_t* d_offsets, uint64_t j_begin,
-                          uint64_t nreads, uint64_t n_int, const void* blocks, const unsigned long long* super,
-                          const unsigned long long* d_C, uint64_t n_ext, uint64_t m_ext, IdxT* g, uint32_t* d_err,
-                          int code_bits) {
+                          uint64_t nreads, uint64_t n_int, uint64_t max_len, const void* blocks,
+                          const unsigned long long* super, const unsigned long long* d_C, uint64_t n_ext,
+                          uint64_t m_ext, IdxT* g, uint32_t* d_err, int code_bits, int occ_k) {
     if (nreads == 0) return;
-    // per suffix: one occurrence block, a g write, the text codes
-    const double bytes = (double)(n_int - nreads) * (code_bits == 4 ? 64.0 : 32.0) + (double)n_int * sizeof(IdxT) +
-                         n_int * code_bits / 8.0 + 16.0 * nreads;
+    // per suffix: one rank query's sectors, a g write, the text codes
+    const double bytes = (double)(n_int - nreads) * rank_query_bytes(code_bits, occ_k) +
+                         (double)n_int * sizeof(IdxT) + n_int * code_bits / 8.0 + 16.0 * nreads;
     if (code_bits == 4) {
-        compute_ranks_launch<IdxT, 4>(L, text, d_offsets, j_begin, nreads, bytes, blocks, super, d_C, n_ext, m_ext, g,
-                                      d_err);
+        compute_ranks_launch<IdxT, 4, 1>(L, text, d_offsets, j_begin, nreads, max_len, bytes, blocks, super, d_C,
+                                         n_ext, m_ext, g, d_err);
+    } else if (occ_k == 4) {
+        compute_ranks_launch<IdxT, 2, 4>(L, text, d_offsets, j_begin, nreads, max_len, bytes, blocks, super, d_C,
+                                         n_ext, m_ext, g, d_err);
+    } else if (occ_k == 2) {
+        compute_ranks_launch<IdxT, 2, 2>(L, text, d_offsets, j_begin, nreads, max_len, bytes, blocks, super, d_C,
+                                         n_ext, m_ext, g, d_err);
     } else {
-        compute_ranks_launch<IdxT, 2>(L, text, d_offsets, j_begin, nreads, bytes, blocks, super, d_C, n_ext, m_ext, g,
-                                      d_err);
+        compute_ranks_launch<IdxT, 2, 1>(L, text, d_offsets, j_begin, nreads, max_len, bytes, blocks, super, d_C,
+                                         n_ext, m_ext, g, d_err);
     }
 }
 
@@ -373,59 +500,91 @@ void launch_bint_gather(Launcher& L, const uint32_t* text, const uint32_t* term,
                 n, bint, gsa, ins_i0, (unsigned long long)nsb, super_shift);
 }
 
+namespace {
+template <int K>
+void rank_batch_k(Launcher& L, const void* blocks, const unsigned long long* super, const uint8_t* codes,
+                  const unsigned long long* ks, uint64_t q, unsigned long long* out) {
+    SBWT_LAUNCH(L, "rank_query", (double)q * (1 + 8 + rank_query_bytes(2, K) + 8 + 8), 0, nullptr,
+                (rank_batch_kernel<2, K>), ceil_div_u(q, kThreads), kThreads, 0,
+                static_cast<const unsigned long long*>(blocks), super, codes, ks, (unsigned long long)q, out);
+}
+template <int K>
+void count_k(Launcher& L, const void* blocks, const unsigned long long* super, const unsigned long long* d_C,
+             uint64_t n, const Alphabet16& alpha, int sigma, const uint8_t* pats, const uint64_t* offs, uint64_t q,
+             uint64_t total_len, unsigned long long* out) {
+    SBWT_LAUNCH(L, "count_query", (double)total_len * (1 + 2 * (rank_query_bytes(2, K) + 8)) + 16.0 * q, 0,
+                nullptr, (count_kernel<2, K>), ceil_div_u(q, kThreads), kThreads, 0,
+                static_cast<const unsigned long long*>(blocks), super, d_C, (unsigned long long)n, alpha, sigma, pats,
+                reinterpret_cast<const unsigned long long*>(offs), (unsigned long long)q, out);
+}
+template <int K>
+void unpack_k(Launcher& L, const void* blocks, uint64_t r0, uint64_t r1, const Alphabet16& alpha, uint8_t* out,
+              uint64_t nparts) {
+    SBWT_LAUNCH(L, "unpack_bwt", (double)(r1 - r0) * (1 + 0.375 + 0.125 / K), 0, nullptr, unpack_kernel<K>,
+                ceil_div_u(nparts, kThreads), kThreads, 0, static_cast<const unsigned long long*>(blocks),
+                (unsigned long long)r0, (unsigned long long)r1, alpha4_of(alpha), out);
+}
+}  // namespace
+
 void launch_rank_batch(Launcher& L, const void* blocks, const unsigned long long* super, const uint8_t* codes,
-                       const unsigned long long* ks, uint64_t q, unsigned long long* out, int code_bits) {
+                       const unsigned long long* ks, uint64_t q, unsigned long long* out, int code_bits, int occ_k) {
     if (q == 0) return;
     if (code_bits == 4) {
-        SBWT_LAUNCH(L, "rank_query", (double)q * (1 + 8 + 64 + 8 + 8), 0, nullptr, rank_batch_kernel<4>,
+        SBWT_LAUNCH(L, "rank_query", (double)q * (1 + 8 + 64 + 8 + 8), 0, nullptr, (rank_batch_kernel<4, 1>),
                     ceil_div_u(q, kThreads), kThreads, 0, static_cast<const OccBlockW*>(blocks), super, codes, ks,
                     (unsigned long long)q, out);
+    } else if (occ_k == 4) {
+        rank_batch_k<4>(L, blocks, super, codes, ks, q, out);
+    } else if (occ_k == 2) {
+        rank_batch_k<2>(L, blocks, super, codes, ks, q, out);
     } else {
-        SBWT_LAUNCH(L, "rank_query", (double)q * (1 + 8 + 32 + 8 + 8), 0, nullptr, rank_batch_kernel<2>,
-                    ceil_div_u(q, kThreads), kThreads, 0, static_cast<const OccBlock*>(blocks), super, codes, ks,
-                    (unsigned long long)q, out);
+        rank_batch_k<1>(L, blocks, super, codes, ks, q, out);
     }
 }
 
 void launch_count(Launcher& L, const void* blocks, const unsigned long long* super, const unsigned long long* d_C,
                   uint64_t n, const Alphabet16& alpha, int sigma, const uint8_t* pats, const uint64_t* offs,
-                  uint64_t q, uint64_t total_len, unsigned long long* out, int code_bits) {
+                  uint64_t q, uint64_t total_len, unsigned long long* out, int code_bits, int occ_k) {
     if (q == 0) return;
     if (code_bits == 4) {
-        SBWT_LAUNCH(L, "count_query", (double)total_len * (1 + 2 * 72) + 16.0 * q, 0, nullptr, count_kernel<4>,
+        SBWT_LAUNCH(L, "count_query", (double)total_len * (1 + 2 * 72) + 16.0 * q, 0, nullptr, (count_kernel<4, 1>),
                     ceil_div_u(q, kThreads), kThreads, 0, static_cast<const OccBlockW*>(blocks), super, d_C,
                     (unsigned long long)n, alpha, sigma, pats, reinterpret_cast<const unsigned long long*>(offs),
                     (unsigned long long)q, out);
+    } else if (occ_k == 4) {
+        count_k<4>(L, blocks, super, d_C, n, alpha, sigma, pats, offs, q, total_len, out);
+    } else if (occ_k == 2) {
+        count_k<2>(L, blocks, super, d_C, n, alpha, sigma, pats, offs, q, total_len, out);
     } else {
-        SBWT_LAUNCH(L, "count_query", (double)total_len * (1 + 2 * 40) + 16.0 * q, 0, nullptr, count_kernel<2>,
-                    ceil_div_u(q, kThreads), kThreads, 0, static_cast<const OccBlock*>(blocks), super, d_C,
-                    (unsigned long long)n, alpha, sigma, pats, reinterpret_cast<const unsigned long long*>(offs),
-                    (unsigned long long)q, out);
+        count_k<1>(L, blocks, super, d_C, n, alpha, sigma, pats, offs, q, total_len, out);
     }
 }
 
 void launch_unpack(Launcher& L, const void* blocks, uint64_t r0, uint64_t r1, const Alphabet16& alpha, uint8_t* out,
-                   int code_bits) {
+                   int code_bits, int occ_k) {
     if (r1 <= r0) return;
-    const uint64_t nblocks = ((r1 - 1) >> kOccShift) - (r0 >> kOccShift) + 1;
+    const uint64_t nparts = ((r1 - 1) >> kOccShift) - (r0 >> kOccShift) + 1;
     if (code_bits == 4) {
         SBWT_LAUNCH(L, "unpack_bwt", (double)(r1 - r0) * (1 + 1.0), 0, nullptr, unpack_w_kernel,
-                    ceil_div_u(nblocks, kThreads), kThreads, 0, static_cast<const OccBlockW*>(blocks),
+                    ceil_div_u(nparts, kThreads), kThreads, 0, static_cast<const OccBlockW*>(blocks),
                     (unsigned long long)r0, (unsigned long long)r1, alpha, out);
+    } else if (occ_k == 4) {
+        unpack_k<4>(L, blocks, r0, r1, alpha, out, nparts);
+    } else if (occ_k == 2) {
+        unpack_k<2>(L, blocks, r0, r1, alpha, out, nparts);
     } else {
-        SBWT_LAUNCH(L, "unpack_bwt", (double)(r1 - r0) * (1 + 0.5), 0, nullptr, unpack_kernel,
-                    ceil_div_u(nblocks, kThreads), kThreads, 0, static_cast<const OccBlock*>(blocks),
-                    (unsigned long long)r0, (unsigned long long)r1, alpha4_of(alpha), out);
+        unpack_k<1>(L, blocks, r0, r1, alpha, out, nparts);
     }
 }
 
 template void launch_compute_ranks<uint32_t>(Launcher&, const uint32_t*, const uint64_t*, uint64_t, uint64_t,
-                                             uint64_t, const void*, const unsigned long long*,
-                                             const unsigned long long*, uint64_t, uint64_t, uint32_t*, uint32_t*, int);
+                                             uint64_t, uint64_t, const void*, const unsigned long long*,
+                                             const unsigned long long*, uint64_t, uint64_t, uint32_t*, uint32_t*, int,
+                                             int);
 template void launch_compute_ranks<unsigned long long>(Launcher&, const uint32_t*, const uint64_t*, uint64_t,
-                                                       uint64_t, uint64_t, const void*, const unsigned long long*,
-                                                       const unsigned long long*, uint64_t, uint64_t,
-                                                       unsigned long long*, uint32_t*, int);
+                                                       uint64_t, uint64_t, uint64_t, const void*,
+                                                       const unsigned long long*, const unsigned long long*, uint64_t,
+                                                       uint64_t, unsigned long long*, uint32_t*, int, int);
 template void launch_bint_gather<uint32_t>(Launcher&, const uint32_t*, const uint32_t*, uint64_t, const uint32_t*,
                                            const uint32_t*, uint32_t, uint8_t*, uint32_t*, int, uint32_t*, uint64_t,
                                            int);

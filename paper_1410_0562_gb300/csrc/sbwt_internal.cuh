@@ -44,60 +44,78 @@ __device__ __forceinline__ uint32_t is_term(const uint32_t* __restrict__ term, u
 }
 
 // ---------------------------------------------------------------------------
-// Rank dictionary over B (Section 5's occurrence counters, re-laid out for
-// one 32-byte sector per rank query).  Row r of B lives in occurrence block
-// r >> 6 (64 rows per block):
-//   sym[2]  : 2-bit codes, row q of the block at bits 2*(q & 31) of
-//             sym[q >> 5] (LSB first); a terminator is stored as code 0
-//   dmask   : bit q set iff row q holds a terminator
-//   cnt     : four 16-bit counts, count of code c (terminators excluded) in
-//             [superblock start, block start), at bits 16c
-// Superblocks span 2^16 rows; super[4*s + c] counts code c in [0, 2^16 s).
-// A dictionary of n rows has (n >> 6) + 1 blocks and (n >> 16) + 1
-// superblocks, so rank(c, n) needs no special case; rows >= n are zero.
-// rank(c, i) = super[4*(i>>16)+c] + cnt_c(block i>>6) + matches of c among
-// the first (i & 63) rows of the block, minus terminators when c == 0.
+// Rank dictionary over B (Section 5's occurrence counters), the 2-bit codes
+// held as bit planes.  Occurrence sampling S = 64 K rows (K = 1, 2 or 4:
+// counters every 64, 128 or 256 rows).  Occurrence block b covers rows
+// [S b, S (b+1)) in 3K + 1 64-bit words:
+//   part q (rows S b + 64 q ... + 63, q < K): lo, hi, dm at words 3q, 3q+1,
+//     3q+2 -- bit p of lo / hi is bit 0 / bit 1 of the code of the part's
+//     row p (a terminator is stored as code 0), bit p of dm is set iff that
+//     row holds a terminator;
+//   word 3K: four 16-bit counts, count of code c (terminators excluded) in
+//     [superblock start, block start), at bits 16c.
+// With K = 1 a block is one 32-byte sector, so a rank query reads one
+// sector; K = 2 and 4 hold 3.5 and 3.25 bits per row instead of 4 and a
+// query reads two to four sectors.  Superblocks span 2^16 rows;
+// super[4*s + c] counts code c in [0, 2^16 s).  A dictionary of n rows has
+// n / S + 1 blocks and (n >> 16) + 1 superblocks, so rank(c, n) needs no
+// special case; rows >= n are zero.
+//   rank(c, i) = super[4*(i>>16)+c] + count_c(block of i) + the rows of
+//   that block before i whose planes spell c and that hold no terminator.
 // ---------------------------------------------------------------------------
-constexpr int kOccShift = 6;
+constexpr int kOccShift = 6;  // rows of a part
 constexpr int kOccSpan = 1 << kOccShift;
 constexpr int kSuperShift = 16;
-constexpr int kBlocksPerSuper = 1 << (kSuperShift - kOccShift);  // 1024
+constexpr int kBlocksPerSuper = 1 << (kSuperShift - kOccShift);  // 1024 parts of 64 rows
 constexpr uint8_t kBintDollar = 255;                              // B_int code of a terminator
 
-struct __align__(32) OccBlock {
-    unsigned long long sym[2];
-    unsigned long long dmask;
-    unsigned long long cnt;
+template <int K>
+struct Occ {
+    static_assert(K == 1 || K == 2 || K == 4, "occurrence sampling of 64, 128 or 256 rows");
+    static constexpr int kWords = 3 * K + 1;                                       // words per block
+    static constexpr int kShift = kOccShift + (K == 1 ? 0 : (K == 2 ? 1 : 2));     // log2 rows per block
 };
-static_assert(sizeof(OccBlock) == 32, "one sector per occurrence block");
+
+// 64-row parts of a dictionary of n rows with blocks of 64 k rows: every
+// part of every block, the last block included.
+__host__ __device__ __forceinline__ unsigned long long dict_parts(unsigned long long n, int k) {
+    return (n / (64ull * (unsigned long long)k) + 1) * (unsigned long long)k;
+}
 
 __device__ __forceinline__ unsigned long long low_bits(uint32_t nbits) {
     return nbits >= 64 ? ~0ull : ((1ull << nbits) - 1ull);
 }
 
-// Mask with bit 2q set for every 2-bit field q of x equal to code c.
-__device__ __forceinline__ unsigned long long match_code(unsigned long long x, uint32_t c) {
-    unsigned long long y = x ^ (0x5555555555555555ull * c);
-    return ~(y | (y >> 1)) & 0x5555555555555555ull;
+// The rows of a part that hold code c (bit p for its row p); terminator rows
+// never match.
+__device__ __forceinline__ unsigned long long plane_match(unsigned long long lo, unsigned long long hi,
+                                                          unsigned long long dm, uint32_t c) {
+    return ((c & 1u) ? lo : ~lo) & ((c & 2u) ? hi : ~hi) & ~dm;
 }
 
-// rank(c, i) within i's superblock: the block counter plus the matches of
-// c among the first (i & 63) rows of the block (one 32-byte sector).
-__device__ __forceinline__ unsigned long long occ_rank_in_super(const OccBlock* __restrict__ blocks, uint32_t c,
-                                                                unsigned long long i) {
-    const ulonglong2* p = reinterpret_cast<const ulonglong2*>(blocks + (i >> kOccShift));
-    const ulonglong2 s = __ldg(p);
-    const ulonglong2 d = __ldg(p + 1);
-    const uint32_t r = (uint32_t)(i & (kOccSpan - 1));
-    const unsigned long long m0 = match_code(s.x, c), m1 = match_code(s.y, c);
-    uint32_t in_block;
-    if (r <= 32) {
-        in_block = __popcll(m0 & low_bits(2 * r));
+// rank(c, i) within i's superblock: the block counter plus the rows of the
+// block before i that hold c.
+template <int K>
+__device__ __forceinline__ unsigned long long occ_rank_in_super(const unsigned long long* __restrict__ words,
+                                                                uint32_t c, unsigned long long i) {
+    const unsigned long long* p = words + (i >> Occ<K>::kShift) * Occ<K>::kWords;
+    if constexpr (K == 1) {
+        const ulonglong2 a = __ldg(reinterpret_cast<const ulonglong2*>(p));
+        const ulonglong2 d = __ldg(reinterpret_cast<const ulonglong2*>(p) + 1);
+        const uint32_t r = (uint32_t)i & 63u;
+        return ((uint32_t)(d.y >> (16 * c)) & 0xFFFFu) + __popcll(plane_match(a.x, a.y, d.x, c) & ((1ull << r) - 1ull));
     } else {
-        in_block = __popcll(m0) + __popcll(m1 & low_bits(2 * (r - 32)));
+        const uint32_t r = (uint32_t)i & (64u * K - 1u), q = r >> 6;
+        uint32_t in_block = 0;
+#pragma unroll
+        for (int s = 0; s < K; ++s) {
+            if ((uint32_t)s <= q) {
+                const unsigned long long m = plane_match(__ldg(p + 3 * s), __ldg(p + 3 * s + 1), __ldg(p + 3 * s + 2), c);
+                in_block += __popcll((uint32_t)s < q ? m : (m & ((1ull << (r & 63u)) - 1ull)));
+            }
+        }
+        return ((uint32_t)(__ldg(p + 3 * K) >> (16 * c)) & 0xFFFFu) + in_block;
     }
-    if (c == 0) in_block -= __popcll(d.x & low_bits(r));
-    return ((uint32_t)(d.y >> (16 * c)) & 0xFFFFu) + in_block;
 }
 
 // ---------------------------------------------------------------------------
@@ -168,21 +186,22 @@ __device__ __forceinline__ unsigned long long occ_rank_w(const OccBlockW* __rest
     return __ldg(super + ((i >> kSuperShiftW) << 4) + c) + occ_rank_in_super_w(blocks, c, i);
 }
 
-// The two dictionary layouts behind one interface, by code width kB.
-template <int kB>
+// The dictionary layouts behind one interface, by code width kB and (2-bit
+// codes) occurrence sampling 64 K rows.
+template <int kB, int K>
 struct DictLayout;
-template <>
-struct DictLayout<2> {
-    using Block = OccBlock;
+template <int K>
+struct DictLayout<2, K> {
+    using Block = unsigned long long;  // the dictionary as an array of 64-bit words
     static constexpr int kSuperShift = sbwt::kSuperShift;
     static constexpr int kCodes = 4;
     __device__ __forceinline__ static unsigned long long in_super(const Block* __restrict__ b, uint32_t c,
                                                                   unsigned long long i) {
-        return occ_rank_in_super(b, c, i);
+        return occ_rank_in_super<K>(b, c, i);
     }
 };
 template <>
-struct DictLayout<4> {
+struct DictLayout<4, 1> {
     using Block = OccBlockW;
     static constexpr int kSuperShift = kSuperShiftW;
     static constexpr int kCodes = kSigmaW;
@@ -191,11 +210,11 @@ struct DictLayout<4> {
         return occ_rank_in_super_w(b, c, i);
     }
 };
-template <int kB>
-__device__ __forceinline__ unsigned long long dict_rank(const typename DictLayout<kB>::Block* __restrict__ blocks,
+template <int kB, int K>
+__device__ __forceinline__ unsigned long long dict_rank(const typename DictLayout<kB, K>::Block* __restrict__ blocks,
                                                         const unsigned long long* __restrict__ super, uint32_t c,
                                                         unsigned long long i) {
-    using D = DictLayout<kB>;
+    using D = DictLayout<kB, K>;
     return __ldg(super + (i >> D::kSuperShift) * D::kCodes + c) + D::in_super(blocks, c, i);
 }
 

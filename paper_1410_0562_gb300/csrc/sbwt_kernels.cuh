@@ -53,14 +53,18 @@ void launch_bint(Launcher& L, const uint32_t* text, const uint32_t* term, uint64
                  uint32_t n, uint8_t* bint);
 // ComputeRanks (Algorithm 2 with Lemma 1): g[t] for every block position.
 // A row index past n_ext (impossible for a consistent dictionary) is clamped
-// and flagged in *d_err (bit 3) instead of being dereferenced.  blocks is an
-// OccBlock array for code_bits == 2, an OccBlockW array for code_bits == 4;
-// g starts on a 16-byte boundary.
+// and flagged in *d_err (bit 3) instead of being dereferenced.  blocks is the
+// bit-plane dictionary of sampling 64 occ_k rows for code_bits == 2 (occ_k
+// 1, 2 or 4), an OccBlockW array for code_bits == 4 (occ_k 1); g starts on a
+// 16-byte boundary.
+// max_len bounds the block's read lengths: reads longer than 512 symbols are
+// ranked in segments of 256 positions, each started exactly by a backward
+// search (see ranks.cu).
 template <class IdxT>
 void launch_compute_ranks(Launcher& L, const uint32_t* text, const uint64_t* d_offsets, uint64_t j_begin,
-                          uint64_t nreads, uint64_t n_int, const void* blocks, const unsigned long long* super,
-                          const unsigned long long* d_C, uint64_t n_ext, uint64_t m_ext, IdxT* g, uint32_t* d_err,
-                          int code_bits);
+                          uint64_t nreads, uint64_t n_int, uint64_t max_len, const void* blocks,
+                          const unsigned long long* super, const unsigned long long* d_C, uint64_t n_ext,
+                          uint64_t m_ext, IdxT* g, uint32_t* d_err, int code_bits, int occ_k);
 // B_int and g_sa fused: one pass over SA_int after ComputeRanks.  With
 // ins_i0 non-null it also writes Insert's plan (nsb + 1 entries: the first
 // new symbol of each superblock of 2^super_shift rows of the next dictionary).
@@ -70,28 +74,30 @@ void launch_bint_gather(Launcher& L, const uint32_t* text, const uint32_t* term,
                         uint64_t nsb = 0, int super_shift = 0);
 // rank queries: codes 0..sigma-1, or 4 (16 for code_bits == 4) for the terminator.
 void launch_rank_batch(Launcher& L, const void* blocks, const unsigned long long* super, const uint8_t* codes,
-                       const unsigned long long* ks, uint64_t q, unsigned long long* out, int code_bits);
+                       const unsigned long long* ks, uint64_t q, unsigned long long* out, int code_bits, int occ_k);
 // Backward-search counts of q patterns (pattern i = pats[offs[i] .. offs[i+1])).
 void launch_count(Launcher& L, const void* blocks, const unsigned long long* super, const unsigned long long* d_C,
                   uint64_t n, const Alphabet16& alpha, int sigma, const uint8_t* pats, const uint64_t* offs,
-                  uint64_t q, uint64_t total_len, unsigned long long* out, int code_bits);
+                  uint64_t q, uint64_t total_len, unsigned long long* out, int code_bits, int occ_k);
 // B as bytes, rows [r0, r1) (r0 a multiple of 64): alphabet byte per code,
 // '$' for a terminator row; out[r] for row r.
 void launch_unpack(Launcher& L, const void* blocks, uint64_t r0, uint64_t r1, const Alphabet16& alpha, uint8_t* out,
-                   int code_bits);
+                   int code_bits, int occ_k);
 
 // insert.cu: Insert (Section 5) as a stable merge of the old dictionary
 // (n_ext rows) with n_int new symbols at rows g_sa[i] + i; writes the new
 // dictionary's symbols, terminator masks and block counters, then the
 // superblock counters and C[] (m = terminators in the new dictionary).
-// Blocks are OccBlock (code_bits 2) or OccBlockW (code_bits 4); sb_tot holds
-// 4 (16) words per superblock, rounded up to 4 words, then 4 (16) 64-bit
-// words per 256 superblocks.  ins_i0 is the plan bint_gather wrote (2-bit
-// dictionary; unused for 4-bit codes); an inconsistent plan sets *d_err bit 10.
+// Blocks are the bit-plane dictionary of sampling 64 occ_k rows (code_bits
+// 2) or OccBlockW (code_bits 4, occ_k 1); sb_tot holds 4 (16) words per
+// superblock, rounded up to 4 words, then 4 (16) 64-bit words per 256
+// superblocks.  ins_i0 is the plan bint_gather wrote (2-bit dictionary;
+// unused for 4-bit codes); an inconsistent plan sets *d_err bit 10.
 template <class IdxT>
 void launch_insert(Launcher& L, const void* old_blocks, uint64_t n_ext, const uint8_t* bint, const IdxT* gsa,
                    uint64_t n_int, const uint32_t* ins_i0, void* new_blocks, unsigned long long* new_super,
-                   unsigned long long* new_C, uint64_t m_new, uint32_t* sb_tot, uint32_t* d_err, int code_bits);
+                   unsigned long long* new_C, uint64_t m_new, uint32_t* sb_tot, uint32_t* d_err, int code_bits,
+                   int occ_k);
 
 // plan.cu: checks device-resident offsets (offsets[0] = 0, non-decreasing,
 // every read shorter than max_block suffixes; summary->bad != 0 otherwise),
@@ -112,12 +118,15 @@ struct PlanSummary {
 void launch_plan(Launcher& L, const uint64_t* d_offsets, uint64_t m, uint64_t M, uint64_t max_block,
                  PlanBlock* table, unsigned cap, PlanSummary* summary);
 
-// Sizes of a dictionary of n rows.
-inline uint64_t dict_blocks(uint64_t n) { return (n >> kOccShift) + 1; }
-inline uint64_t dict_supers(uint64_t n) { return (dict_blocks(n) + kBlocksPerSuper - 1) / kBlocksPerSuper; }
+// Sizes of a dictionary of n rows: occurrence blocks of 64 k rows (k = 1, 2
+// or 4 for the 2-bit layout, 1 for the 4-bit one).
+inline uint64_t dict_blocks(uint64_t n, int k = 1) { return n / (64ull * (uint64_t)k) + 1; }
+inline uint64_t dict_supers(uint64_t n) { return (n >> kSuperShift) + 1; }
 inline uint64_t dict_supers_w(uint64_t n) { return (dict_blocks(n) + kBlocksPerSuperW - 1) / kBlocksPerSuperW; }
 // Bytes per occurrence block, superblock counters and C of each layout.
-inline size_t dict_block_bytes(int code_bits) { return code_bits == 4 ? sizeof(OccBlockW) : sizeof(OccBlock); }
+inline size_t dict_block_bytes(int code_bits, int k = 1) {
+    return code_bits == 4 ? sizeof(OccBlockW) : (size_t)8 * (3 * k + 1);
+}
 inline uint64_t dict_supers_of(uint64_t n, int code_bits) { return code_bits == 4 ? dict_supers_w(n) : dict_supers(n); }
 inline size_t dict_codes(int code_bits) { return code_bits == 4 ? (size_t)kSigmaW : 4; }
 

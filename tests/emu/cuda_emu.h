@@ -112,6 +112,8 @@ static inline unsigned __reduce_or_sync(unsigned mask, unsigned v) {
     return r;
 }
 static inline int __popcll(unsigned long long x) { return __builtin_popcountll(x); }
+template <class T>
+static inline T __ldg(const T* p) { return *p; }
 static inline int __ffsll(long long x) { return __builtin_ffsll(x); }
 struct ulonglong2 {
     unsigned long long x, y;

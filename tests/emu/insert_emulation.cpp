@@ -10,35 +10,66 @@
 #include "scan.inc"
 #include "insert.inc"
 
-// One Insert launch: nsb CTAs of kInsertThreads threads over the old dictionary (n_ext
-// rows), the new symbols (bint, gsa; n_int of them) and the plan ins_i0
-// (nsb + 1 entries); writes the new dictionary's blocks and the superblock
-// totals.  gsa_bytes is 4 or 8 (the index width).
-extern "C" int emu_insert(const void* old_blocks, unsigned long long n_ext, const uint8_t* bint, const void* gsa,
-                          int gsa_bytes, unsigned long long n_int, const uint32_t* ins_i0, void* new_blocks,
-                          unsigned long long n_new, uint32_t* sb_tot, uint32_t* d_err) {
+// One Insert launch: nsb CTAs of kInsertThreads threads over the old
+// dictionary (n_ext rows, blocks of 64 k rows as 64-bit words), the new
+// symbols (bint, gsa; n_int of them) and the plan ins_i0 (nsb + 1 entries);
+// writes the new dictionary's words and the superblock totals.  gsa_bytes is
+// 4 or 8 (the index width).
+template <int K, int kT, class IdxT>
+static void run_insert(const unsigned long long* old_words, unsigned long long n_ext, const uint8_t* bint,
+                       const IdxT* gsa, unsigned long long n_int, const uint32_t* ins_i0, unsigned long long* new_words,
+                       unsigned long long n_new, uint32_t* sb_tot, uint32_t* d_err) {
     std::vector<std::pair<void*, size_t>> maps;
-    const uint64_t nb_old = (n_ext >> kOccShift) + 1, nb_new = (n_new >> kOccShift) + 1;
-    const uint64_t nsb = (nb_new + kBlocksPerSuper - 1) / kBlocksPerSuper;
-    const OccBlock* g_old = guarded(static_cast<const OccBlock*>(old_blocks), nb_old, maps);
+    const uint64_t w_old = (n_ext / (64ull * K) + 1) * Occ<K>::kWords, w_new = (n_new / (64ull * K) + 1) * Occ<K>::kWords;
+    const uint64_t nsb = (n_new >> kSuperShift) + 1;
+    const unsigned long long* g_old = guarded(old_words, w_old, maps);
     const uint8_t* g_bint = guarded(bint, n_int, maps);
     const uint32_t* g_plan = guarded(ins_i0, nsb + 1, maps);
-    OccBlock* g_new = guarded(static_cast<OccBlock*>(new_blocks), nb_new, maps);
+    unsigned long long* g_new = guarded(new_words, w_new, maps);
     uint32_t* g_tot = guarded(sb_tot, 4 * nsb, maps);
-    if (gsa_bytes == 4) {
-        const uint32_t* g_gsa = guarded(static_cast<const uint32_t*>(gsa), n_int, maps);
-        run_grid((unsigned)nsb, kInsertThreads, [&] {
-            insert_kernel<uint32_t, kInsertThreads>(g_old, n_ext, g_bint, g_gsa, n_int, g_plan, g_new, n_new, g_tot, d_err);
-        });
-    } else {
-        const unsigned long long* g_gsa = guarded(static_cast<const unsigned long long*>(gsa), n_int, maps);
-        run_grid((unsigned)nsb, kInsertThreads, [&] {
-            insert_kernel<unsigned long long, kInsertThreads>(g_old, n_ext, g_bint, g_gsa, n_int, g_plan, g_new, n_new, g_tot,
-                                                   d_err);
-        });
-    }
-    memcpy(new_blocks, g_new, nb_new * sizeof(OccBlock));
+    const IdxT* g_gsa = guarded(gsa, n_int, maps);
+    run_grid((unsigned)nsb, kT, [&] {
+        insert_kernel<IdxT, kT, K>(g_old, n_ext, g_bint, g_gsa, n_int, g_plan, g_new, n_new, g_tot, d_err);
+    });
+    memcpy(new_words, g_new, w_new * 8);
     memcpy(sb_tot, g_tot, 4 * nsb * 4);
     for (auto& m : maps) munmap(m.first, m.second);
+}
+
+template <int K, int kT>
+static void run_width(const void* old_words, unsigned long long n_ext, const uint8_t* bint, const void* gsa,
+                      int gsa_bytes, unsigned long long n_int, const uint32_t* ins_i0, void* new_words,
+                      unsigned long long n_new, uint32_t* sb_tot, uint32_t* d_err) {
+    const auto* o = static_cast<const unsigned long long*>(old_words);
+    auto* w = static_cast<unsigned long long*>(new_words);
+    if (gsa_bytes == 4)
+        run_insert<K, kT>(o, n_ext, bint, static_cast<const uint32_t*>(gsa), n_int, ins_i0, w, n_new, sb_tot, d_err);
+    else
+        run_insert<K, kT>(o, n_ext, bint, static_cast<const unsigned long long*>(gsa), n_int, ins_i0, w, n_new,
+                          sb_tot, d_err);
+}
+
+// the CTA size the launcher picks: 512 threads for dense new rows, 256 else
+template <int K>
+static void run_density(const void* old_words, unsigned long long n_ext, const uint8_t* bint, const void* gsa,
+                        int gsa_bytes, unsigned long long n_int, const uint32_t* ins_i0, void* new_words,
+                        unsigned long long n_new, uint32_t* sb_tot, uint32_t* d_err) {
+    if (4 * n_int >= n_new)
+        run_width<K, kInsertThreads>(old_words, n_ext, bint, gsa, gsa_bytes, n_int, ins_i0, new_words, n_new, sb_tot,
+                                     d_err);
+    else
+        run_width<K, kInsertThreadsSparse>(old_words, n_ext, bint, gsa, gsa_bytes, n_int, ins_i0, new_words, n_new,
+                                           sb_tot, d_err);
+}
+
+extern "C" int emu_insert(const void* old_words, unsigned long long n_ext, const uint8_t* bint, const void* gsa,
+                          int gsa_bytes, unsigned long long n_int, const uint32_t* ins_i0, void* new_words,
+                          unsigned long long n_new, uint32_t* sb_tot, uint32_t* d_err, int occ_k) {
+    if (occ_k == 4)
+        run_density<4>(old_words, n_ext, bint, gsa, gsa_bytes, n_int, ins_i0, new_words, n_new, sb_tot, d_err);
+    else if (occ_k == 2)
+        run_density<2>(old_words, n_ext, bint, gsa, gsa_bytes, n_int, ins_i0, new_words, n_new, sb_tot, d_err);
+    else
+        run_density<1>(old_words, n_ext, bint, gsa, gsa_bytes, n_int, ins_i0, new_words, n_new, sb_tot, d_err);
     return 0;
 }

@@ -181,8 +181,15 @@ def test_wide_alphabet_file_layout(lib, tmp_path):
     assert len(data) == 88 + 64 + 16 * 8 + 16 * 8 + 8
     narrow = tmp_path / "narrow.sbwt"
     sb.SetBWT(b"ACGT").save(narrow)
-    assert struct.unpack_from("<II", narrow.read_bytes(), 8) == (1, 4)
+    assert struct.unpack_from("<II", narrow.read_bytes(), 8) == (3, 4)
+    assert struct.unpack_from("<I", narrow.read_bytes(), 68) == (64,)
     assert len(narrow.read_bytes()) == 88 + 32 + 4 * 8 + 4 * 8 + 8
+    # sampling 128 and 256: blocks of 7 and 13 words
+    for rows, words in ((128, 7), (256, 13)):
+        f = tmp_path / f"narrow{rows}.sbwt"
+        sb.SetBWT(b"ACGT", occ_sampling=rows).save(f)
+        assert struct.unpack_from("<I", f.read_bytes(), 68) == (rows,)
+        assert len(f.read_bytes()) == 88 + 8 * words + 4 * 8 + 4 * 8 + 8
     import torch
     if not torch.cuda.is_available():
         with pytest.raises(sb.SbwtError) as e:  # the file checks pass; the device step fails
@@ -212,3 +219,48 @@ def test_noalloc_rejects_sizes_that_would_wrap(lib):
     rc = lib.sbwt_bwt_noalloc(b"ACGT", ctypes.c_void_p(out.ctypes.data), ctypes.c_void_p(o.ctypes.data), m,
                               ctypes.c_void_p(out.ctypes.data), 16, ctypes.byref(got), None)
     assert rc == sb.SBWT_EINVAL
+
+
+def test_occurrence_sampling_option(lib):
+    """64, 128 and 256 rows per occurrence block for up to 4 symbols; 5 to 16
+    symbols take 64 only; any other value is refused."""
+    for rows in (0, 64, 128, 256):
+        sb.SetBWT(b"ACGT", occ_sampling=rows).close()
+    for rows in (1, 32, 96, 192, 512):
+        with pytest.raises(sb.SbwtError) as e:
+            sb.SetBWT(b"ACGT", occ_sampling=rows)
+        assert e.value.code == sb.SBWT_EINVAL
+    sb.SetBWT(b"ACGNT", occ_sampling=64).close()
+    with pytest.raises(sb.SbwtError) as e:
+        sb.SetBWT(b"ACGNT", occ_sampling=128)
+    assert e.value.code == sb.SBWT_ENOTSUP
+
+
+def fnv1a(data: bytes) -> int:
+    h = 1469598103934665603
+    for b in data:
+        h = ((h ^ b) * 1099511628211) & 0xFFFFFFFFFFFFFFFF
+    return h
+
+
+def test_version_1_file_passes_the_checks(lib, tmp_path):
+    """A file of the first layout (2-bit codes interleaved in 64-row blocks,
+    version 1) is still read: its checks pass before the device step."""
+    import struct
+    header = bytearray(88)
+    header[:8] = b"SBWTIDX1"
+    struct.pack_into("<II4sI", header, 8, 1, 4, b"ACGT", 32)
+    struct.pack_into("<QQQQ", header, 24, 0, 0, 1, 1)  # n, m, one block, one superblock
+    body = bytes(header) + bytes(32) + bytes(32) + bytes(32)
+    path = tmp_path / "v1.sbwt"
+    path.write_bytes(body + struct.pack("<Q", fnv1a(body)))
+    import torch
+    if not torch.cuda.is_available():
+        with pytest.raises(sb.SbwtError) as e:
+            sb.SetBWT.load(path)
+        assert e.value.code == sb.SBWT_EDEVICE
+    # a wrong checksum is refused before any device work
+    path.write_bytes(body + struct.pack("<Q", fnv1a(body) ^ 1))
+    with pytest.raises(sb.SbwtError) as e:
+        sb.SetBWT.load(path)
+    assert e.value.code == sb.SBWT_EINVAL

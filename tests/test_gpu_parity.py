@@ -23,11 +23,11 @@ def _lib():
     sb.load()
 
 
-def gpu_bwt(reads, offsets, alphabet=b"ACGT", M=0, cuts=None, index_bits=0, capture=False):
+def gpu_bwt(reads, offsets, alphabet=b"ACGT", M=0, cuts=None, index_bits=0, capture=False, occ_sampling=0):
     """Build through the C ABI, appending reads [cuts[k], cuts[k+1]) per call."""
     m = len(offsets) - 1
     cuts = list(cuts) if cuts else [0, m]
-    idx = sb.SetBWT(alphabet, index_bits=index_bits, block_suffixes=M)
+    idx = sb.SetBWT(alphabet, index_bits=index_bits, block_suffixes=M, occ_sampling=occ_sampling)
     if capture:
         sb.sbwt_set_capture(idx.handle, True)
     offsets = np.asarray(offsets, np.uint64)
@@ -231,38 +231,6 @@ def test_repeated_appends_reuse_buffers():
     assert np.array_equal(gpu_bwt(w.reads, w.offsets, cuts=cuts).bwt(), oracle.bwt(w.reads, w.offsets))
 
 
-def test_short_read_workload_full_size():
-    """The 1M x 100 bp short-read workload (10 Mbp genome, 1% substitutions,
-    blocks of 2^24 suffixes, 32-bit indices) in the launch configuration the
-    benchmark times.  The oracle cannot sort 101M suffixes in test time, so:
-    sampled rows computed one by one by the oracle, the terminator rows, the
-    symbol multiset, and LF inversion of the whole B back to every read."""
-    w = readgen.short()
-    idx = gpu_bwt(w.reads, w.offsets, M=w.block_suffixes, index_bits=w.index_bits)
-    B = idx.bwt()
-    n = oracle.num_suffixes(w.offsets)
-    assert len(B) == n and idx.size() == (n, w.m)
-    # multiset: same symbols as the reads, exactly m terminators
-    counts = np.bincount(B, minlength=256)
-    expect_counts = np.bincount(w.reads, minlength=256)
-    expect_counts[ord("$")] += w.m
-    assert np.array_equal(counts, expect_counts)
-    # rows 0..m-1 are $_0..$_{m-1}: the last symbol of each read
-    last = w.reads[(w.offsets[1:] - 1).astype(np.int64)]
-    assert np.array_equal(B[: w.m], last)
-    # sampled suffixes: their rows by direct counting, and B there
-    rng = np.random.default_rng(17)
-    for _ in range(6):
-        r = int(rng.integers(0, w.m))
-        L = int(w.offsets[r + 1] - w.offsets[r])
-        p = int(rng.integers(0, L + 1))
-        row = oracle.row_of_suffix(w.reads, w.offsets, r, p)
-        assert B[row] == oracle.bwt_symbol_of_suffix(w.reads, w.offsets, r, p)
-    # LF inversion recovers every read
-    rec, roff = oracle.lf_invert(B, w.m)
-    assert np.array_equal(roff, w.offsets) and np.array_equal(rec, w.reads)
-
-
 def check_full_size(w, B, samples=3, seed=17):
     """Properties that pin B at any size: the symbol multiset, the terminator
     rows, rows of sampled suffixes counted one by one by the oracle, and LF
@@ -284,17 +252,6 @@ def check_full_size(w, B, samples=3, seed=17):
         assert B[row] == oracle.bwt_symbol_of_suffix(w.reads, w.offsets, r, p)
     rec, roff = oracle.lf_invert_sampled(B, w.m, alphabet=w.alphabet)
     assert np.array_equal(roff, w.offsets) and np.array_equal(rec, w.reads)
-
-
-@pytest.mark.parametrize("name", ["batched", "long"])
-def test_full_size_batched_and_long_reads(name):
-    """2M reads of U[50,250] bp from a 50 Mbp genome, and 20k log-normal long
-    reads (mean 10 kbp) with 10% errors from a 100 Mbp genome; 64-bit
-    indices, blocks of 2^25 suffixes."""
-    w = readgen.batched() if name == "batched" else readgen.long()
-    idx = gpu_bwt(w.reads, w.offsets, M=1 << 25, index_bits=64)
-    assert idx.size() == (oracle.num_suffixes(w.offsets), w.m)
-    check_full_size(w, idx.bwt(), samples=2)
 
 
 def test_full_size_repetitive_reads():
@@ -464,3 +421,60 @@ def test_prepend_places_reads_first(M):
     # into an empty index, a prepend is an append
     e = sb.SetBWT(b"ACGT", block_suffixes=M).prepend(*a)
     assert np.array_equal(e.bwt(), oracle.bwt(*a))
+
+
+@pytest.mark.parametrize("sampling", [64, 128, 256])
+def test_occurrence_sampling(sampling):
+    """Every occurrence sampling gives the oracle's B, ranks and counts: the
+    tiny workload in two appends and in many small blocks, a ragged set over
+    superblock-straddling sizes with empty reads and repeats, and rank
+    queries at the block and superblock edges."""
+    w = readgen.tiny()
+    expect = oracle.bwt(w.reads, w.offsets)
+    for M, cuts in ((w.block_suffixes, w.appends), (777, [0, 100, 640, 1000])):
+        idx = gpu_bwt(w.reads, w.offsets, M=M, cuts=cuts, occ_sampling=sampling)
+        assert np.array_equal(idx.bwt(), expect)
+    reads, off = readgen.ragged_reads(1300, 0, 200, seed=sampling, p_empty=0.03, p_repeat=0.05)
+    B = oracle.bwt(reads, off)
+    idx = gpu_bwt(reads, off, M=40_000, cuts=[0, 300, 1300], occ_sampling=sampling, index_bits=64)
+    assert np.array_equal(idx.bwt(), B)
+    n = len(B)
+    ks = np.unique(np.concatenate([[0, 1, 63, 64, 65, 127, 128, 129, 255, 256, 257, 65535, 65536, 65537, n - 1, n],
+                                   np.random.default_rng(1).integers(0, n + 1, size=300)]))
+    ks = ks[ks <= n]
+    for c in b"$ACGT":
+        cum = np.concatenate([[0], np.cumsum(B == c)])
+        assert np.array_equal(idx.rank_batch(np.full(len(ks), c, np.uint8), ks.astype(np.uint64)), cum[ks])
+    pats = [b"A", b"CG", b"TTA", b"ACGTA", b"GGGG"]
+    assert list(idx.count(pats)) == [oracle.count(reads, off, p) for p in pats]
+
+
+def test_autotune_picks_block_size_and_sampling():
+    """The joint autotuner times every (sampling, M) pair on the given reads,
+    keeps the fastest in the index, and the index it leaves builds the
+    oracle's B."""
+    import torch
+    w = readgen.tiny()
+    d_reads = torch.from_numpy(w.reads).cuda()
+    d_off = torch.from_numpy(w.offsets.astype(np.int64)).cuda()
+    idx = sb.SetBWT(b"ACGT")
+    best_m, best_s, times = sb.sbwt_autotune(idx.handle, d_reads.data_ptr(), d_off.data_ptr(), w.m,
+                                             [20_000, 1 << 20], [64, 128, 256])
+    assert best_m in (20_000, 1 << 20) and best_s in (64, 128, 256)
+    assert len(times) == 6 and all(t > 0 for t in times.values())
+    assert times[(best_s, best_m)] == min(times.values())
+    assert idx.size() == (0, 0)
+    idx.append_device(d_reads.data_ptr(), d_off.data_ptr(), w.m)
+    assert np.array_equal(idx.bwt(), oracle.bwt(w.reads, w.offsets))
+
+
+def test_block_overlap_off_gives_the_same_b():
+    """The plain per-block loop (every step of every block in turn on one
+    stream) and the overlapped pipeline give the oracle's B."""
+    w = readgen.tiny()
+    expect = oracle.bwt(w.reads, w.offsets)
+    for overlap in (False, True, False):
+        idx = sb.SetBWT(b"ACGT", block_suffixes=9_000)
+        sb.sbwt_set_block_overlap(idx.handle, overlap)
+        idx.append(w.reads, w.offsets)
+        assert np.array_equal(idx.bwt(), expect)

@@ -4,10 +4,11 @@ The text of ``insert_kernel`` and of the dictionary layout it writes is cut
 out of csrc/insert.cu and csrc/sbwt_internal.cuh and compiled for the host
 with tests/emu/cuda_emu.h (one thread per GPU thread, warp intrinsics and CTA
 barriers emulated, every array between inaccessible pages).  Its output
-dictionary is compared, block by block, with the oracle's Insert (new symbol
+dictionary is compared, word by word, with the oracle's Insert (new symbol
 i on row g_sa[i] + i, the old rows in order around them) packed into the
-same layout here: 2-bit codes, terminator mask, 16-bit counters relative to
-the superblock, and the per-superblock totals.  The merge does not need a
+same layout here: per 64-row part the low-bit, high-bit and terminator
+planes, per occurrence block of 64, 128 or 256 rows the 16-bit counters
+relative to the superblock, and the per-superblock totals.  The merge does not need a
 BWT, so old rows, new symbols and the non-decreasing g_sa are drawn at
 random, sparse, dense and clustered.  No GPU is used."""
 import ctypes
@@ -26,7 +27,6 @@ EMU = os.path.join(os.path.dirname(os.path.abspath(__file__)), "emu", "insert_em
 
 CODE = {ord("A"): 0, ord("C"): 1, ord("G"): 2, ord("T"): 3}
 SUPER_ROWS = 1 << 16
-BLOCK = np.dtype([("s0", "<u8"), ("s1", "<u8"), ("dm", "<u8"), ("cnt", "<u8")])
 
 
 def _cut(text, start, end):
@@ -51,42 +51,43 @@ def emu(tmp_path_factory):
                            EMU])
     L = ctypes.CDLL(str(lib))
     P, U64 = ctypes.c_void_p, ctypes.c_uint64
-    L.emu_insert.argtypes = [P, U64, P, P, ctypes.c_int, U64, P, P, U64, P, P]
+    L.emu_insert.argtypes = [P, U64, P, P, ctypes.c_int, U64, P, P, U64, P, P, ctypes.c_int]
     L.emu_insert.restype = ctypes.c_int
     return L
 
 
-def pack_dict(B: np.ndarray) -> np.ndarray:
-    """B (bytes over ACGT and '$') in the 2-bit dictionary layout: 64 rows per
-    block, codes LSB first, terminators as code 0 plus a mask bit, counts of
-    each code before the block within its superblock of 2^16 rows."""
+def pack_dict(B: np.ndarray, k: int = 1) -> np.ndarray:
+    """B (bytes over ACGT and '$') in the 2-bit dictionary layout, as 64-bit
+    words: blocks of 64 k rows, each the (lo, hi, terminator) planes of its
+    64-row parts, then the counts of each code before the block within its
+    superblock of 2^16 rows (16 bits per code)."""
     n = len(B)
-    nb = (n >> 6) + 1
-    codes = np.zeros(nb * 64, np.uint64)
-    dollar = np.zeros(nb * 64, np.uint64)
+    nb = n // (64 * k) + 1
+    rows = nb * 64 * k
     lut = np.zeros(256, np.uint64)
     for c, v in CODE.items():
         lut[c] = v
+    codes = np.zeros(rows, np.uint64)
+    dollar = np.zeros(rows, np.uint64)
     codes[:n] = lut[B]
     dollar[:n] = B == ord("$")
-    codes = codes.reshape(nb, 64)
-    dollar = dollar.reshape(nb, 64)
-    sh2 = (2 * np.arange(32)).astype(np.uint64)
-    out = np.zeros(nb, BLOCK)
-    out["s0"] = np.bitwise_or.reduce(codes[:, :32] << sh2, axis=1)
-    out["s1"] = np.bitwise_or.reduce(codes[:, 32:] << sh2, axis=1)
-    out["dm"] = np.bitwise_or.reduce(dollar << np.arange(64).astype(np.uint64), axis=1)
-    counts = np.stack([((codes == c) & (dollar == 0)).sum(axis=1) for c in range(4)], axis=1).astype(np.int64)
+    sh = np.arange(64).astype(np.uint64)
+    parts = lambda x: np.bitwise_or.reduce(x.reshape(-1, 64) << sh, axis=1).reshape(nb, k)  # noqa: E731
+    lo, hi, dm = parts(codes & np.uint64(1)), parts(codes >> np.uint64(1)), parts(dollar)
+    counts = np.stack([((codes == c) & (dollar == 0)).reshape(nb, -1).sum(axis=1) for c in range(4)],
+                      axis=1).astype(np.int64)
     excl = np.cumsum(counts, axis=0) - counts
-    first = (np.arange(nb) // 1024) * 1024
+    per_super = SUPER_ROWS // (64 * k)
+    first = (np.arange(nb) // per_super) * per_super
     rel = (excl - excl[first]).astype(np.uint64)
-    out["cnt"] = rel[:, 0] | (rel[:, 1] << 16) | (rel[:, 2] << 32) | (rel[:, 3] << 48)
-    return out
+    out = np.zeros((nb, 3 * k + 1), np.uint64)
+    out[:, 0:3 * k:3], out[:, 1:3 * k:3], out[:, 2:3 * k:3] = lo, hi, dm
+    out[:, 3 * k] = rel[:, 0] | (rel[:, 1] << np.uint64(16)) | (rel[:, 2] << np.uint64(32)) | (rel[:, 3] << np.uint64(48))
+    return out.ravel()
 
 
 def super_totals(B: np.ndarray) -> np.ndarray:
-    nb = (len(B) >> 6) + 1
-    nsb = (nb + 1023) // 1024
+    nsb = (len(B) >> 16) + 1
     tot = np.zeros((nsb, 4), np.uint32)
     for s in range(nsb):
         chunk = B[s * SUPER_ROWS:(s + 1) * SUPER_ROWS]
@@ -97,27 +98,25 @@ def super_totals(B: np.ndarray) -> np.ndarray:
 
 def plan(gsa: np.ndarray, n_new: int) -> np.ndarray:
     """First new symbol of every superblock: |{i : g_sa[i] + i < S * 2^16}|."""
-    nb = (n_new >> 6) + 1
-    nsb = (nb + 1023) // 1024
+    nsb = (n_new >> 16) + 1
     r = gsa.astype(np.int64) + np.arange(len(gsa))
     return np.searchsorted(r, np.arange(nsb + 1) * SUPER_ROWS, side="left").astype(np.uint32)
 
 
-def run(emu, B_ext, bint, gsa, width=4, ins_plan=None):
+def run(emu, B_ext, bint, gsa, width=4, ins_plan=None, k=1):
     n_ext, n_int = len(B_ext), len(bint)
     n_new = n_ext + n_int
-    old = pack_dict(B_ext)
+    old = pack_dict(B_ext, k)
     codes = np.array([255 if b == ord("$") else CODE[int(b)] for b in bint], np.uint8)
     g = np.ascontiguousarray(gsa, np.uint32 if width == 4 else np.uint64)
     p = plan(gsa, n_new) if ins_plan is None else ins_plan
-    nb = (n_new >> 6) + 1
-    nsb = (nb + 1023) // 1024
-    new = np.zeros(nb, BLOCK)
+    nsb = (n_new >> 16) + 1
+    new = np.zeros((n_new // (64 * k) + 1) * (3 * k + 1), np.uint64)
     tot = np.zeros(4 * nsb, np.uint32)
     err = ctypes.c_uint32(0)
     ptr = lambda a: ctypes.c_void_p(a.ctypes.data)  # noqa: E731
     assert emu.emu_insert(ptr(old), n_ext, ptr(codes), ptr(g), width, n_int, ptr(p), ptr(new), n_new, ptr(tot),
-                          ctypes.byref(err)) == 0
+                          ctypes.byref(err), k) == 0
     return new, tot, err.value
 
 
@@ -137,14 +136,13 @@ def random_case(rng, n_ext, n_int, kind, p_dollar=0.05):
     return B_ext.astype(np.uint8), bint.astype(np.uint8), gsa.astype(np.uint64)
 
 
-def check(emu, B_ext, bint, gsa, width=4):
-    new, tot, err = run(emu, B_ext, bint, gsa, width)
+def check(emu, B_ext, bint, gsa, width=4, k=1):
+    new, tot, err = run(emu, B_ext, bint, gsa, width, k=k)
     expect = oracle.insert(B_ext, bint, gsa)
     assert err == 0
-    want = pack_dict(expect)
-    for f in ("s0", "s1", "dm", "cnt"):
-        bad = np.nonzero(new[f] != want[f])[0]
-        assert len(bad) == 0, f"{f} differs in blocks {bad[:8].tolist()}"
+    want = pack_dict(expect, k)
+    bad = np.nonzero(new != want)[0]
+    assert len(bad) == 0, f"words differ at {bad[:8].tolist()} (block of {3 * k + 1} words)"
     assert np.array_equal(tot, super_totals(expect))
 
 
@@ -156,16 +154,17 @@ def test_worked_example(emu):
     assert bytes(oracle.insert(b"C$A", b"A$", [1, 1])) == b"CA$$A"
 
 
+@pytest.mark.parametrize("k", [1, 2, 4])
 @pytest.mark.parametrize("n_ext,n_int,kind", [
     (0, 1, "uniform"), (0, 5000, "uniform"), (1, 1, "uniform"), (63, 2, "uniform"), (64, 64, "one"),
     (65, 200, "uniform"), (4095, 60, "uniform"), (4096, 9000, "clustered"), (3000, 3000, "one"),
     (70_000, 700, "uniform"), (70_000, 25_000, "clustered"), (65_536 - 100, 300, "uniform"),
     (20_000, 110_000, "uniform"),
 ])
-def test_merge_matches_the_oracle(emu, n_ext, n_int, kind):
+def test_merge_matches_the_oracle(emu, n_ext, n_int, kind, k):
     rng = np.random.default_rng(n_ext * 7 + n_int)
     B_ext, bint, gsa = random_case(rng, n_ext, n_int, kind)
-    check(emu, B_ext, bint, gsa, width=4 if (n_ext + n_int) % 2 else 8)
+    check(emu, B_ext, bint, gsa, width=4 if (n_ext + n_int) % 2 else 8, k=k)
 
 
 def test_inconsistent_plan_is_flagged_without_leaving_the_arrays(emu):

@@ -1,0 +1,154 @@
+"""ComputeRanks (Algorithm 2 with Lemma 1) run on the CPU: the per-read
+kernel and the segmented kernel for long reads.
+
+The text of both kernels and of the dictionary layout is cut out of
+csrc/ranks.cu and csrc/sbwt_internal.cuh and compiled for the host with
+tests/emu/cuda_emu.h (one thread per GPU thread, every array between
+inaccessible pages).  The dictionary of the reads already indexed is packed
+here from the oracle's B (bit planes, counters every 64, 128 or 256 rows,
+superblock counters and C[] with the terminators counted), the new reads'
+text in the append layout, and g is compared with the oracle's direct count
+of smaller old suffixes for every position of the block.  The segmented
+kernel starts each segment of 256 positions from a backward search whose
+window doubles while it still occurs in B_ext; reads drawn from a short
+genome make those windows repeat.  No GPU is used."""
+import ctypes
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle
+import readgen
+from test_insert_emulation import CODE, pack_dict
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CSRC = os.path.join(ROOT, "paper_1410_0562_gb300", "csrc")
+EMU = os.path.join(os.path.dirname(os.path.abspath(__file__)), "emu", "ranks_emulation.cpp")
+SEG_ROWS = 256
+
+
+def _cut(text, start, end):
+    i = text.index(start)
+    return text[i:text.index(end, i)]
+
+
+@pytest.fixture(scope="module")
+def emu(tmp_path_factory):
+    if not shutil.which("g++"):
+        pytest.skip("g++ is not available")
+    d = tmp_path_factory.mktemp("rankemu")
+    src = open(os.path.join(CSRC, "ranks.cu")).read()
+    hdr = open(os.path.join(CSRC, "sbwt_internal.cuh")).read()
+    (d / "dict.inc").write_text("constexpr int kThreads = 256;\n" + _cut(
+        hdr, "constexpr int kOccShift = 6;", "// ---------------------------------------------------------------------------\n// CTA-wide scans"))
+    kern = _cut(src, "// Algorithm 2, one thread per read:", "// B_int and g_sa in one pass over SA_int")
+    kern = kern.replace("extern __shared__ unsigned long long s_raw[];", "unsigned long long* s_raw = g_dyn_smem;")
+    (d / "ranks.inc").write_text(kern)
+    lib = d / "librankemu.so"
+    subprocess.check_call(["g++", "-O1", "-std=c++20", "-shared", "-fPIC", "-pthread", "-I", str(d), "-o", str(lib),
+                           EMU])
+    L = ctypes.CDLL(str(lib))
+    P, U64, U32, I = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int
+    L.emu_compute_ranks.argtypes = [I, I, U32, P, U64, P, U64, P, P, P, U64, U64, P, U64, P]
+    L.emu_compute_ranks.restype = I
+    return L
+
+
+def dictionary(B: np.ndarray, m: int, k: int):
+    """Blocks, superblock counters and C[] of B (m terminators)."""
+    words = pack_dict(B, k)
+    nsb = (len(B) >> 16) + 1
+    sup = np.zeros((nsb, 4), np.uint64)
+    for s in range(1, nsb):
+        chunk = B[: s << 16]
+        sup[s] = [np.count_nonzero(chunk == c) for c in b"ACGT"]
+    tot = [np.count_nonzero(B == c) for c in b"ACGT"]
+    C = np.array([m, m + tot[0], m + tot[0] + tot[1], m + tot[0] + tot[1] + tot[2]], np.uint64)
+    return words, sup.ravel(), C
+
+
+def append_text(reads: np.ndarray, off: np.ndarray) -> np.ndarray:
+    """2-bit codes of an append's positions (read j's symbol k at off[j] + j +
+    k, a terminator after each read stored as code 0), 16 per word, MSB first,
+    with four zero words of padding."""
+    m = len(off) - 1
+    npos = int(off[-1]) + m
+    codes = np.zeros(npos, np.uint32)
+    lut = np.zeros(256, np.uint32)
+    for c, v in CODE.items():
+        lut[c] = v
+    pos = np.arange(int(off[-1])) + np.repeat(np.arange(m), np.diff(off.astype(np.int64)))
+    codes[pos] = lut[reads]
+    nw = (npos + 15) // 16
+    padded = np.zeros(nw * 16, np.uint32)
+    padded[:npos] = codes
+    sh = (30 - 2 * np.arange(16)).astype(np.uint32)
+    words = np.bitwise_or.reduce(padded.reshape(nw, 16) << sh, axis=1).astype(np.uint32)
+    return np.concatenate([words, np.zeros(4, np.uint32)])
+
+
+def run(emu, old_reads, old_off, new_reads, new_off, k=1, seg=False):
+    B = oracle.bwt(old_reads, old_off)
+    m_ext = len(old_off) - 1
+    words, sup, C = dictionary(B, m_ext, k)
+    text = append_text(new_reads, new_off)
+    nreads = len(new_off) - 1
+    n_int = int(new_off[-1]) + nreads
+    max_len = int(np.diff(new_off.astype(np.int64)).max())
+    segs = max_len // SEG_ROWS + 1
+    g = np.zeros(max(n_int, 1), np.uint32)
+    err = ctypes.c_uint32(0)
+    ptr = lambda a: ctypes.c_void_p(a.ctypes.data)  # noqa: E731
+    off = np.ascontiguousarray(new_off, np.uint64)
+    assert emu.emu_compute_ranks(k, int(seg), segs, ptr(text), len(text), ptr(off), nreads, ptr(words), ptr(sup),
+                                 ptr(C), len(B), m_ext, ptr(g), n_int, ctypes.byref(err)) == 0
+    return g[:n_int], err.value
+
+
+def expected_g(old, new):
+    reads = np.concatenate([old[0], new[0]])
+    lens = np.concatenate([np.diff(old[1].astype(np.int64)), np.diff(new[1].astype(np.int64))])
+    off = readgen.offsets_from_lengths(lens)
+    m0 = len(old[1]) - 1
+    return oracle.block_g_direct(reads, off, m0, len(off) - 1).astype(np.uint32)
+
+
+@pytest.mark.parametrize("k", [1, 2, 4])
+def test_per_read_kernel_matches_direct_counts(emu, k):
+    old = readgen.ragged_reads(400, 0, 120, seed=31, p_empty=0.03, p_repeat=0.05)
+    new = readgen.ragged_reads(150, 0, 120, seed=32, p_empty=0.03, p_repeat=0.05)
+    g, err = run(emu, *old, *new, k=k)
+    assert err == 0
+    assert np.array_equal(g, expected_g(old, new))
+
+
+@pytest.mark.parametrize("k", [1, 4])
+@pytest.mark.parametrize("repeat", [True, False])
+def test_segmented_kernel_matches_direct_counts(emu, k, repeat):
+    """Long reads (513 to 3000 symbols) sampled from a genome: a 300-symbol
+    unit repeated twelve times makes the backward-search windows occur in
+    B_ext, so segments widen their window, up to the terminator's exact
+    chain; a 100 kbp i.i.d. genome lets the first window settle most
+    segments."""
+    g_ = np.tile(readgen.genome(300, seed=300), 12) if repeat else readgen.genome(100_000, seed=1)
+    old = readgen.sampled_reads(g_, 30, np.random.default_rng(1).integers(200, 3000, size=30), 0.01, seed=33)
+    lens = np.random.default_rng(2).integers(600, 3000, size=12)
+    lens[0] = 513  # just over the per-read limit: two segments and a partial third
+    new = readgen.sampled_reads(g_, 12, lens, 0.01, seed=34)
+    g, err = run(emu, *old, *new, k=k, seg=True)
+    assert err == 0
+    assert np.array_equal(g, expected_g(old, new))
+    # the per-read kernel agrees on the same block
+    g2, _ = run(emu, *old, *new, k=k, seg=False)
+    assert np.array_equal(g2, g)
+
+
+def test_segmented_kernel_against_an_empty_index(emu):
+    """No old reads: every window's interval is empty at once (g = 0)."""
+    empty = (np.zeros(0, np.uint8), np.zeros(1, np.uint64))
+    new = readgen.ragged_reads(6, 700, 1500, seed=35)
+    g, err = run(emu, *empty, *new, seg=True)
+    assert err == 0 and not np.any(g)
