@@ -70,13 +70,20 @@ typedef struct {
                                 a stream the library creates and owns */
     int32_t device;          /* CUDA device ordinal; -1 = the current device */
     uint32_t host_tier;      /* 0 or 1 = allowed, 2 = forbidden, 3 = always (the
-                                dictionaries live in host memory from the first
+                                dictionary lives in host memory from the first
                                 append on, whatever the budget): when the HBM budget
                                 cannot hold the rank dictionaries (B_ext and its
-                                counters), they move to mapped pinned host memory
-                                and the same kernels reach them over the host link
-                                (Section 5 keeps B_ext in system memory); the
-                                per-block working set stays in HBM */
+                                counters), the index keeps ONE dictionary, in mapped
+                                pinned host memory, which the same kernels reach over
+                                the host link (Section 5 keeps B_ext in system
+                                memory) and Insert rewrites in place, from its top
+                                down in chunks staged in HBM: about 4 bits per row of
+                                B in host memory (3.25 with occ_sampling 256), and
+                                only the per-block working set in HBM.  A byte
+                                outside the alphabet is still refused with the index
+                                unchanged; a device error during such an append
+                                leaves the index unusable (SBWT_EDEVICE) until
+                                sbwt_reset. */
     uint32_t occ_sampling;   /* rows per occurrence block of the rank dictionary
                                 (Section 5 keeps counters every 128 symbols): 64,
                                 128 or 256; 0 = 64.  64 is one 32-byte sector per
@@ -201,6 +208,15 @@ int sbwt_get_stage(sbwt_index *idx, int stage, void *out, uint64_t cap, uint64_t
  * Up to 8 graphs are kept; sbwt_destroy and turning replay off drop them.
  * Off by default. */
 int sbwt_set_graph_replay(sbwt_index *idx, int on);
+
+/* The host link the host tier works over, measured on the index's device
+ * and stream: H2D and D2H copies of 256 MB between pinned host memory and
+ * HBM, and random 32-byte sector reads by a kernel from mapped pinned host
+ * memory (the access of ComputeRanks and rank queries to a host-tier
+ * dictionary), in GB/s; any out pointer may be NULL.  Allocates 256 MB of
+ * pinned host memory and 256 MB of HBM for the measurement and frees them
+ * (outside the HBM budget).  Errors: SBWT_ENOMEM, SBWT_EDEVICE, SBWT_EBUSY. */
+int sbwt_host_link(sbwt_index *idx, double *h2d_gbs, double *d2h_gbs, double *random_read_gbs);
 
 /* Block overlap (on by default): the suffix sort of each block runs on a
  * second stream, ahead of the ranking, gather and Insert of the blocks before

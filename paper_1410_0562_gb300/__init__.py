@@ -40,11 +40,11 @@ SBWT_STAGE_GSA = 3
 #: every symbol include/sbwt.h declares, in header order
 EXPORTS = (
     "sbwt_create", "sbwt_create_ex", "sbwt_append", "sbwt_prepend", "sbwt_append_device", "sbwt_get_bwt", "sbwt_rank",
-    "sbwt_rank_batch", "sbwt_count", "sbwt_memory", "sbwt_size", "sbwt_reset", "sbwt_destroy", "sbwt_strerror", "sbwt_get_stream",
-    "sbwt_set_capture", "sbwt_get_stage", "sbwt_set_profiling", "sbwt_set_profiling_only", "sbwt_get_kernel_stats",
-    "sbwt_reset_kernel_stats", "sbwt_set_graph_replay", "sbwt_set_block_overlap", "sbwt_autotune_block_suffixes",
-    "sbwt_autotune", "sbwt_serve_start",
-    "sbwt_submit", "sbwt_wait", "sbwt_serve_stop", "sbwt_save", "sbwt_load", "sbwt_bwt_noalloc",
+    "sbwt_rank_batch", "sbwt_count", "sbwt_memory", "sbwt_size", "sbwt_reset", "sbwt_destroy", "sbwt_strerror",
+    "sbwt_get_stream", "sbwt_set_capture", "sbwt_get_stage", "sbwt_set_profiling", "sbwt_set_profiling_only",
+    "sbwt_get_kernel_stats", "sbwt_reset_kernel_stats", "sbwt_set_graph_replay", "sbwt_host_link",
+    "sbwt_set_block_overlap", "sbwt_autotune_block_suffixes", "sbwt_autotune", "sbwt_serve_start", "sbwt_submit",
+    "sbwt_wait", "sbwt_serve_stop", "sbwt_save", "sbwt_load", "sbwt_bwt_noalloc",
 )
 
 #: most suffixes (reads + one terminator each) sbwt_bwt_noalloc accepts
@@ -113,6 +113,8 @@ def load() -> ctypes.CDLL:
             "sbwt_reset_kernel_stats": ([P], I),
             "sbwt_set_graph_replay": ([P, I], I),
             "sbwt_set_block_overlap": ([P, I], I),
+            "sbwt_host_link": ([P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                ctypes.POINTER(ctypes.c_double)], I),
             "sbwt_autotune_block_suffixes": ([P, P, P, U64, P, I, ctypes.POINTER(U64), P], I),
             "sbwt_autotune": ([P, P, P, U64, P, I, P, I, ctypes.POINTER(U64), ctypes.POINTER(ctypes.c_uint32), P],
                               I),
@@ -301,6 +303,13 @@ def sbwt_get_kernel_stats(h) -> list:
 
 def sbwt_reset_kernel_stats(h):
     _check(load().sbwt_reset_kernel_stats(h), "sbwt_reset_kernel_stats")
+
+
+def sbwt_host_link(h):
+    """(H2D GB/s, D2H GB/s, random 32-byte host reads GB/s) of the index's device."""
+    a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(load().sbwt_host_link(h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), "sbwt_host_link")
+    return a.value, b.value, c.value
 
 
 def sbwt_set_block_overlap(h, on: bool):

@@ -82,7 +82,10 @@ struct sbwt_index {
     DevBuf reads, offsets, text, term, err;
     DevBuf keys, keys_alt, vals, vals_alt, sa, sa2, rank, act_pos0, act_pos1, act_suf0, act_suf1, loc_act, loc_next;
     DevBuf units;
-    DevBuf radix_temp, chunks, count_log, g, gsa, bint, sb_tot, ins_plan;
+    DevBuf radix_temp, chunks, count_log, g, gsa, bint, sb_tot, ins_plan, stage;
+    // The host tier rewrites its one dictionary in place: an append that
+    // fails after the rewrite began leaves it broken until sbwt_reset.
+    bool broken = false;
     DevBuf out_bytes, q_codes, q_ks, q_out, c_pats, c_offs;
 
     uint32_t* h_err = nullptr;      // pinned
@@ -115,7 +118,7 @@ struct sbwt_index {
                                   &keys_alt,   &vals,     &vals_alt,  &sa,       &rank,     &act_pos0,
                                   &act_pos1,   &act_suf0, &act_suf1,  &loc_act,  &loc_next, &units,     &sa2,
                                   &radix_temp, &chunks,
-                                  &count_log,  &g,        &gsa,       &bint,     &sb_tot,   &ins_plan, &out_bytes,
+                                  &count_log,  &g,        &gsa,       &bint,     &sb_tot,   &ins_plan, &stage, &out_bytes,
                                   &q_codes,    &q_ks,     &q_out,     &plan,     &c_pats,   &c_offs};
         for (auto& d : dict) {
             v.push_back(&d.blocks);
@@ -268,7 +271,12 @@ struct Need {
     bool dict = false;  // a dictionary buffer: may live in the host tier
 };
 
-std::vector<Need> buffer_needs(sbwt_index* idx, const Plan& p, bool host_input, uint64_t m_new) {
+// The buffers an append needs: the block working set, and either the two
+// scratch dictionaries blocks alternate between (in HBM, or in the host tier
+// if the committed one is there), or, in place (the host tier), the staging
+// buffer of the chunked in-place Insert.
+std::vector<Need> buffer_needs(sbwt_index* idx, const Plan& p, bool host_input, uint64_t m_new,
+                               bool in_place = false) {
     const uint64_t cap = std::max<uint64_t>(p.cap, 1);
     const size_t w = p.idx64 ? 8 : 4;
     const uint64_t n_final = idx->n + p.npos;
@@ -296,6 +304,10 @@ std::vector<Need> buffer_needs(sbwt_index* idx, const Plan& p, bool host_input, 
     const size_t sb_words = (size_t)((nsb * dict_codes(cb) + 3) & ~3ull);
     v.push_back({&idx->sb_tot, sb_words * 4 + (size_t)(nsb / 256 + 1) * 8 * dict_codes(cb)});
     v.push_back({&idx->ins_plan, (size_t)(nsb + 1) * 4});  // Insert's first new symbol per superblock
+    if (in_place) {
+        v.push_back({&idx->stage, insert_stage_bytes(cb, idx->occ_k)});
+        return v;
+    }
     for (int k = 0; k < 3; ++k) {
         if (k == idx->cur) continue;
         v.push_back({&idx->dict[k].blocks, (size_t)dict_blocks(n_final, idx->occ_k) * dict_block_bytes(cb, idx->occ_k),
@@ -385,11 +397,67 @@ int reserve(sbwt_index* idx, const std::vector<Need>& needs) {
     return SBWT_OK;
 }
 
+// Grows b to at least `bytes` in its tier, keeping its contents (the host
+// tier's one dictionary grows in place; a quarter of slack per growth).
+int grow_keep(DevBuf& b, size_t bytes, cudaStream_t s) {
+    bytes = rounded(bytes);
+    if (b.bytes >= bytes) return SBWT_OK;
+    const size_t nb = std::max(bytes, rounded(b.bytes + b.bytes / 4));
+    void* p = alloc_tier(nb, b.host);
+    if (!p) return SBWT_ENOMEM;
+    if (b.p && b.bytes &&
+        (cudaMemcpyAsync(p, b.p, b.bytes, cudaMemcpyDefault, s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)) {
+        cudaGetLastError();
+        if (b.host) cudaFreeHost(p); else cudaFree(p);
+        return SBWT_EDEVICE;
+    }
+    if (b.p) {
+        if (b.host) cudaFreeHost(b.p); else cudaFree(b.p);
+    }
+    b.p = p;
+    b.bytes = nb;
+    return SBWT_OK;
+}
+
+// The buffers of an append under the HBM budget.  While the dictionaries fit
+// it, blocks alternate between two scratch dictionaries in HBM and the
+// committed one is switched at the end.  Beyond it (or with the host tier
+// forced) the index keeps ONE dictionary, in mapped pinned host memory
+// (Section 5 keeps B_ext in system memory under a constant working set,
+// Section 6): Insert rewrites it in place, so the host holds about 4 bits per
+// row (3.25 with sampling 256) instead of three copies, and HBM holds only the
+// block working set and the staging buffer.
+int reserve_append(sbwt_index* idx, const Plan& p, bool host_input, uint64_t m_new, bool* in_place) {
+    *in_place = false;
+    if (!(idx->dict_host || idx->host_tier_forced)) {
+        auto needs = buffer_needs(idx, p, host_input, m_new, false);
+        if (!idx->budget || hbm_after(idx, needs, false) <= idx->budget) return reserve(idx, needs);
+        if (!idx->host_tier_allowed) return SBWT_ENOMEM;
+    }
+    auto needs = buffer_needs(idx, p, host_input, m_new, true);
+    if (idx->budget && hbm_after(idx, needs, true) > idx->budget) return SBWT_ENOMEM;
+    if (!idx->dict_host) {
+        if (int rc = move_dicts_to_host(idx)) return rc;
+    }
+    for (const Need& n : needs)
+        if (int rc = grow(*n.buf, n.bytes, false)) return rc;
+    const int cb = idx->code_bits;
+    const uint64_t n_final = idx->n + p.npos;
+    Dict& d = idx->dict[idx->cur];
+    if (int rc = grow_keep(d.blocks, (size_t)dict_blocks(n_final, idx->occ_k) * dict_block_bytes(cb, idx->occ_k),
+                           idx->stream))
+        return rc;
+    if (int rc = grow_keep(d.super, (size_t)dict_supers_of(n_final, cb) * 8 * dict_codes(cb), idx->stream)) return rc;
+    if (int rc = grow_keep(d.C, 8 * dict_codes(cb), idx->stream)) return rc;
+    *in_place = true;
+    return SBWT_OK;
+}
+
 // Block k of the append, the q-th to run (q = k unless the append prepends).
 template <class IdxT>
 void run_block(sbwt_index* idx, const BlockPlan& bp, const uint64_t* d_offsets, const Dict& src, Dict& dst,
                uint64_t n_ext, uint64_t m_ext, size_t slots, size_t k, size_t q, bool prepend,
-               cudaEvent_t packed) {
+               cudaEvent_t packed, bool in_place) {
     Launcher& L = idx->L;
     const uint32_t n = (uint32_t)bp.n_int;
     SuffixSortBuffers b;
@@ -438,7 +506,8 @@ void run_block(sbwt_index* idx, const BlockPlan& bp, const uint64_t* d_offsets, 
     launch_insert<IdxT>(L, (const void*)src.blocks.p, n_ext, (const uint8_t*)idx->bint.p,
                         (const IdxT*)idx->gsa.p, bp.n_int, plan, (void*)dst.blocks.p,
                         (unsigned long long*)dst.super.p, (unsigned long long*)dst.C.p, m_ext + (bp.j1 - bp.j0),
-                        (uint32_t*)idx->sb_tot.p, (uint32_t*)idx->err.p, idx->code_bits, idx->occ_k);
+                        (uint32_t*)idx->sb_tot.p, (uint32_t*)idx->err.p, idx->code_bits, idx->occ_k,
+                        in_place ? (unsigned long long*)idx->stage.p : nullptr);
 }
 
 Plan host_plan(const uint64_t* h_off, uint64_t m_new, uint64_t M) {
@@ -462,7 +531,8 @@ int append_impl(sbwt_index* idx, const uint8_t* d_reads, const uint64_t* d_offse
     p.idx64 = idx->index_bits == 64 || n_final >= 0xFFFFFFFFull;
 
     if (int rc = device_init(idx)) return rc;
-    if (int rc = reserve(idx, buffer_needs(idx, p, host_input, m_new))) return rc;
+    bool in_place = false;
+    if (int rc = reserve_append(idx, p, host_input, m_new, &in_place)) return rc;
     cudaStream_t s = idx->stream;
     Launcher& L = idx->L;
     if (L.settle_units() != cudaSuccess) return SBWT_EDEVICE;  // the count log is about to be reused
@@ -478,7 +548,10 @@ int append_impl(sbwt_index* idx, const uint8_t* d_reads, const uint64_t* d_offse
     // packs the words up to the one holding block k's last position, so it
     // copies the bytes of every position below that word's end (a few
     // positions into block k + 1 at most).  Graph capture keeps one copy.
-    const bool pipelined = host_input && !idx->graph_replay && p.blocks.size() > 1 && p.nbytes > 0;
+    // (in place, the foreign-byte check runs before the first block, so the
+    // append is eager and packs all of its reads first)
+    const bool graph = idx->graph_replay && !in_place;
+    const bool pipelined = host_input && !graph && !in_place && p.blocks.size() > 1 && p.nbytes > 0;
     std::vector<uint64_t> chunk_bytes, chunk_words;
     if (pipelined) {
         for (const BlockPlan& b : p.blocks) {
@@ -513,13 +586,14 @@ int append_impl(sbwt_index* idx, const uint8_t* d_reads, const uint64_t* d_offse
     int final_cur = idx->cur;
     uint64_t final_n = idx->n, final_m = idx->m;
     for (size_t k = 0; k < p.blocks.size(); ++k) {
-        final_cur = other[k & 1];
+        final_cur = in_place ? idx->cur : other[k & 1];
         final_n += p.blocks[k].n_int;
         final_m += p.blocks[k].j1 - p.blocks[k].j0;
     }
 
-    // Everything the device does for this append, after the input copies.
-    auto enqueue = [&]() {
+    // Everything the device does for this append, after the input copies:
+    // the packing of the reads, then the blocks.
+    auto enqueue_pack = [&]() {
         const uint64_t tw = text_words(p.npos, idx->code_bits), term_words = (p.npos + 31) / 32;
         cudaMemsetAsync((uint32_t*)idx->text.p + tw, 0, kTextPadWords * 4, s);
         cudaMemsetAsync((uint32_t*)idx->term.p + term_words, 0, kTermPadWords * 4, s);
@@ -549,6 +623,8 @@ int append_impl(sbwt_index* idx, const uint8_t* d_reads, const uint64_t* d_offse
         } else {
             pack(0, ~0ull);
         }
+    };
+    auto enqueue_blocks = [&]() {
         int src = idx->cur;
         uint64_t n_ext = idx->n, m_ext = idx->m;
         cudaEventRecord(idx->ev_fork, s);  // the sorts read the packed text
@@ -559,14 +635,14 @@ int append_impl(sbwt_index* idx, const uint8_t* d_reads, const uint64_t* d_offse
             // before those of the blocks already inserted
             const size_t k = p.prepend ? nb - 1 - q : q;
             const BlockPlan& bp = p.blocks[k];
-            const int dst = other[q & 1];
+            const int dst = in_place ? src : other[q & 1];
             cudaEvent_t packed = pipelined ? idx->ev_packed[k] : nullptr;
             if (p.idx64)
                 run_block<unsigned long long>(idx, bp, d_offsets, idx->dict[src], idx->dict[dst], n_ext, m_ext,
-                                              p.slots, k, q, p.prepend, packed);
+                                              p.slots, k, q, p.prepend, packed, in_place);
             else
                 run_block<uint32_t>(idx, bp, d_offsets, idx->dict[src], idx->dict[dst], n_ext, m_ext, p.slots, k, q,
-                                    p.prepend, packed);
+                                    p.prepend, packed, in_place);
             n_ext += bp.n_int;
             m_ext += bp.j1 - bp.j0;
             src = dst;
@@ -575,9 +651,22 @@ int append_impl(sbwt_index* idx, const uint8_t* d_reads, const uint64_t* d_offse
         cudaStreamWaitEvent(s, idx->ev_join, 0);
         cudaMemcpyAsync(idx->h_err, idx->err.p, 4, cudaMemcpyDeviceToHost, s);
     };
+    auto enqueue = [&]() {
+        enqueue_pack();
+        enqueue_blocks();
+    };
 
     const Launcher::GraphLog* replayed = nullptr;
-    if (idx->graph_replay) {
+    if (in_place) {
+        // the one dictionary is about to be rewritten: refuse a byte outside
+        // the alphabet first, so such an append leaves the index unchanged
+        enqueue_pack();
+        cudaMemcpyAsync(idx->h_err, idx->err.p, 4, cudaMemcpyDeviceToHost, s);
+        if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) return SBWT_EDEVICE;
+        if (*idx->h_err & 1u) return SBWT_EINVAL;
+        if (*idx->h_err) return SBWT_EDEVICE;
+        enqueue_blocks();
+    } else if (graph) {
         // The batched form: the append is captured into a graph; the graph
         // instantiated for the same pipeline shape (the same kernels in the
         // same order) is updated in place with this append's sizes, buffers
@@ -641,13 +730,19 @@ int append_impl(sbwt_index* idx, const uint8_t* d_reads, const uint64_t* d_offse
     }
     const auto t_launch = std::chrono::steady_clock::now();
     L.add_host("host:launch", std::chrono::duration<double, std::milli>(t_launch - t_plan).count());
-    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) return SBWT_EDEVICE;
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) {
+        if (in_place) idx->broken = true;
+        return SBWT_EDEVICE;
+    }
     L.add_host("host:wait",
                std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_launch).count());
     if (L.settle_units() != cudaSuccess) return SBWT_EDEVICE;
     if (replayed && L.account_replay(*replayed) != cudaSuccess) return SBWT_EDEVICE;
     if (*idx->h_err & 1u) return SBWT_EINVAL;  // a byte outside the alphabet; the index is unchanged
-    if (*idx->h_err) return SBWT_EDEVICE;      // a kernel caught an inconsistent index; keep the old one
+    if (*idx->h_err) {  // a kernel caught an inconsistent index: keep the old one (rewritten in place: broken)
+        if (in_place) idx->broken = true;
+        return SBWT_EDEVICE;
+    }
     idx->cur = final_cur;
     idx->n = final_n;
     idx->m = final_m;
@@ -718,6 +813,23 @@ struct File {
         if (f) fclose(f);
     }
 };
+
+// Host-link bandwidth probe: random 32-byte sector reads from mapped pinned
+// host memory, the access of ComputeRanks and rank queries to a host-tier
+// dictionary.  Each thread reads kLinkReads sectors at hashed offsets.
+constexpr int kLinkReads = 64;
+__global__ void __launch_bounds__(256) link_random_read_kernel(const ulonglong2* __restrict__ host, uint64_t sectors,
+                                                               unsigned long long* __restrict__ sink) {
+    uint64_t x = (uint64_t)blockIdx.x * 256 + threadIdx.x + 1;
+    unsigned long long acc = 0;
+    for (int r = 0; r < kLinkReads; ++r) {
+        x = x * 6364136223846793005ull + 1442695040888963407ull;  // LCG step (Knuth's MMIX constants)
+        const uint64_t sct = (x >> 17) % sectors;
+        const ulonglong2 a = host[2 * sct], b = host[2 * sct + 1];
+        acc += a.x ^ a.y ^ b.x ^ b.y;
+    }
+    if (acc == 0x5bd1e995ull) sink[0] = acc;  // keeps the loads
+}
 
 }  // namespace
 
@@ -974,6 +1086,7 @@ int sbwt_create(const char* alphabet, size_t hbm_budget_bytes, sbwt_index** out)
 int sbwt_append(sbwt_index* idx, const uint8_t* reads, const uint64_t* offsets, uint64_t m) {
     if (!idx || !offsets) return SBWT_EINVAL;
     if (busy(idx)) return SBWT_EBUSY;
+    if (idx->broken) return SBWT_EDEVICE;  // an in-place append failed: reset first
     const auto t0 = std::chrono::steady_clock::now();
     if (m < kDevicePlanMin) {
         if (validate_offsets(offsets, m)) return SBWT_EINVAL;
@@ -997,6 +1110,7 @@ int sbwt_append(sbwt_index* idx, const uint8_t* reads, const uint64_t* offsets, 
 int sbwt_prepend(sbwt_index* idx, const uint8_t* reads, const uint64_t* offsets, uint64_t m) {
     if (!idx || !offsets) return SBWT_EINVAL;
     if (busy(idx)) return SBWT_EBUSY;
+    if (idx->broken) return SBWT_EDEVICE;  // an in-place append failed: reset first
     const auto t0 = std::chrono::steady_clock::now();
     if (validate_offsets(offsets, m)) return SBWT_EINVAL;
     if (m == 0) return SBWT_OK;
@@ -1009,6 +1123,7 @@ int sbwt_prepend(sbwt_index* idx, const uint8_t* reads, const uint64_t* offsets,
 int sbwt_append_device(sbwt_index* idx, const uint8_t* d_reads, const uint64_t* d_offsets, uint64_t m) {
     if (!idx || !d_offsets) return SBWT_EINVAL;
     if (busy(idx)) return SBWT_EBUSY;
+    if (idx->broken) return SBWT_EDEVICE;  // an in-place append failed: reset first
     const auto t0 = std::chrono::steady_clock::now();
     if (int rc = device_init(idx)) return rc;
     if (m == 0) return SBWT_OK;
@@ -1022,6 +1137,7 @@ int sbwt_append_device(sbwt_index* idx, const uint8_t* d_reads, const uint64_t* 
 int sbwt_get_bwt(sbwt_index* idx, uint8_t* out, uint64_t cap, uint64_t* n_out) {
     if (!idx || !n_out) return SBWT_EINVAL;
     if (busy(idx)) return SBWT_EBUSY;
+    if (idx->broken) return SBWT_EDEVICE;  // an in-place append failed: reset first
     *n_out = idx->n;
     if (cap < idx->n) return SBWT_ERANGE;
     if (idx->n == 0) return SBWT_OK;
@@ -1048,12 +1164,14 @@ int sbwt_get_bwt(sbwt_index* idx, uint8_t* out, uint64_t cap, uint64_t* n_out) {
     cudaEventRecord(idx->ev_join, idx->side);
     cudaStreamWaitEvent(s, idx->ev_join, 0);
     if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) return SBWT_EDEVICE;
+    if (idx->out_bytes.host) free_buf(idx->out_bytes);  // the host tier keeps only its dictionary in host memory
     return SBWT_OK;
 }
 
 int sbwt_rank_batch(sbwt_index* idx, const uint8_t* cs, const uint64_t* ks, uint64_t q, uint64_t* out) {
     if (!idx || (q && (!cs || !ks || !out))) return SBWT_EINVAL;
     if (busy(idx)) return SBWT_EBUSY;
+    if (idx->broken) return SBWT_EDEVICE;  // an in-place append failed: reset first
     std::vector<uint8_t> codes(q);
     for (uint64_t i = 0; i < q; ++i) {
         if (ks[i] > idx->n) return SBWT_EINVAL;
@@ -1088,6 +1206,7 @@ int sbwt_rank_batch(sbwt_index* idx, const uint8_t* cs, const uint64_t* ks, uint
 int sbwt_count(sbwt_index* idx, const uint8_t* patterns, const uint64_t* offsets, uint64_t q, uint64_t* counts) {
     if (!idx || (q && (!offsets || !counts))) return SBWT_EINVAL;
     if (busy(idx)) return SBWT_EBUSY;
+    if (idx->broken) return SBWT_EDEVICE;  // an in-place append failed: reset first
     if (q == 0) return SBWT_OK;
     if (offsets[0] != 0) return SBWT_EINVAL;
     for (uint64_t i = 0; i < q; ++i)
@@ -1137,6 +1256,7 @@ int sbwt_reset(sbwt_index* idx) {
     if (!idx) return SBWT_EINVAL;
     if (busy(idx)) return SBWT_EBUSY;
     idx->n = idx->m = 0;
+    idx->broken = false;
     idx->last_valid = false;
     if (!idx->dev_ready) return SBWT_OK;
     if (set_device(idx)) return SBWT_EDEVICE;
@@ -1151,6 +1271,7 @@ int sbwt_reset(sbwt_index* idx) {
 int sbwt_save(sbwt_index* idx, const char* path) {
     if (!idx || !path) return SBWT_EINVAL;
     if (busy(idx)) return SBWT_EBUSY;
+    if (idx->broken) return SBWT_EDEVICE;  // an in-place append failed: reset first
     const int cb = idx->code_bits, k = idx->occ_k;
     const size_t bb = dict_block_bytes(cb, k), codes = dict_codes(cb);
     FileHeader h = {};
@@ -1463,6 +1584,55 @@ int sbwt_autotune(sbwt_index* idx, const uint8_t* d_reads, const uint64_t* d_off
     if (best_block_out) *best_block_out = best_M;
     if (best_sampling_out) *best_sampling_out = 64u * (uint32_t)best_k;
     return rr;
+}
+
+int sbwt_host_link(sbwt_index* idx, double* h2d_gbs, double* d2h_gbs, double* random_read_gbs) {
+    if (!idx) return SBWT_EINVAL;
+    if (busy(idx)) return SBWT_EBUSY;
+    if (int rc = device_init(idx)) return rc;
+    constexpr size_t kBytes = 256ull << 20;
+    void *h = nullptr, *d = nullptr;
+    if (cudaHostAlloc(&h, kBytes, cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess ||
+        cudaMalloc(&d, kBytes) != cudaSuccess) {
+        cudaGetLastError();
+        if (h) cudaFreeHost(h);
+        return SBWT_ENOMEM;
+    }
+    const cudaStream_t s = idx->stream;
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    memset(h, 1, kBytes);
+    auto best_of = [&](auto&& body) {
+        float best = 1e30f;
+        for (int rep = 0; rep < 4; ++rep) {
+            cudaEventRecord(a, s);
+            body();
+            cudaEventRecord(b, s);
+            cudaEventSynchronize(b);
+            float ms = 0;
+            cudaEventElapsedTime(&ms, a, b);
+            if (rep > 0 && ms < best) best = ms;  // the first run warms up
+        }
+        return (double)best;
+    };
+    const double t_h2d = best_of([&] { cudaMemcpyAsync(d, h, kBytes, cudaMemcpyHostToDevice, s); });
+    const double t_d2h = best_of([&] { cudaMemcpyAsync(h, d, kBytes, cudaMemcpyDeviceToHost, s); });
+    const unsigned grid = persistent_ctas((const void*)link_random_read_kernel, 256, 0);
+    const double t_rnd = best_of([&] {
+        link_random_read_kernel<<<grid, 256, 0, s>>>(static_cast<const ulonglong2*>(h), kBytes / 32,
+                                                     static_cast<unsigned long long*>(d));
+    });
+    const bool ok = cudaGetLastError() == cudaSuccess && cudaStreamSynchronize(s) == cudaSuccess;
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaFree(d);
+    cudaFreeHost(h);
+    if (!ok) return SBWT_EDEVICE;
+    if (h2d_gbs) *h2d_gbs = kBytes / (t_h2d * 1e6);
+    if (d2h_gbs) *d2h_gbs = kBytes / (t_d2h * 1e6);
+    if (random_read_gbs) *random_read_gbs = (double)grid * 256 * kLinkReads * 32 / (t_rnd * 1e6);
+    return SBWT_OK;
 }
 
 int sbwt_set_block_overlap(sbwt_index* idx, int on) {

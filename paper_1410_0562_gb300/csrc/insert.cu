@@ -27,6 +27,9 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kInsertThreads = 512;        // threads of a 2-bit Insert CTA (one superblock), dense new rows
 constexpr int kInsertThreadsSparse = 256;  // the same for sparse new rows
+constexpr uint64_t kStageSupers = 512;      // superblocks per chunk of an in-place Insert
+constexpr unsigned kStageGrid = 1216;       // CTAs of the staging copy (8 per SM)
+constexpr uint64_t kStageBlocksW = 1ull << 19;  // output blocks per chunk of an in-place 4-bit Insert
 constexpr int kRun = 8;              // consecutive new symbols a thread places at once
 
 // 64 rows of the 2-bit dictionary as its three bit planes (bit p: row p).
@@ -45,29 +48,54 @@ __device__ __forceinline__ const unsigned long long* part_words(const unsigned l
                                                                 uint64_t part) {
     return words + (part / K) * Occ<K>::kWords + 3 * (part % K);
 }
+// The old parts a window starting at row s reads, from blocks [base, base +
+// avail) of the old dictionary held in old_words (the whole dictionary, or a
+// staged copy of some of its blocks); a part outside them reads as zero and
+// flags *d_err (an inconsistent plan).
 template <int K>
 __device__ __forceinline__ OldPair old_pair(const unsigned long long* __restrict__ old_words, uint64_t nparts_old,
-                                            uint64_t s) {
+                                            uint64_t s, uint64_t base, uint64_t avail, uint32_t* __restrict__ d_err) {
     const uint64_t P = s >> kOccShift;
     OldPair o;
-    o.b = Window{0ull, 0ull, 0ull};
+    o.a = o.b = Window{0ull, 0ull, 0ull};
+    const uint64_t ba = P / K;
+    if (ba < base || ba - base >= avail) {
+        atomicOr(d_err, 1024u);
+        return o;
+    }
+    const bool has_b = P + 1 < nparts_old && (P + 1) / K - base < avail;
     if constexpr (K == 1) {
-        const ulonglong2* A = reinterpret_cast<const ulonglong2*>(old_words) + 2 * P;
+        const ulonglong2* A = reinterpret_cast<const ulonglong2*>(old_words) + 2 * (P - base);
         const ulonglong2 a0 = A[0], a1 = A[1];
         o.a = Window{a0.x, a0.y, a1.x};
-        if (P + 1 < nparts_old) {
+        if (has_b) {
             const ulonglong2 b0 = A[2], b1 = A[3];
             o.b = Window{b0.x, b0.y, b1.x};
         }
     } else {
-        const unsigned long long* pa = part_words<K>(old_words, P);
+        const unsigned long long* pa = old_words + (ba - base) * Occ<K>::kWords + 3 * (P % K);
         o.a = Window{pa[0], pa[1], pa[2]};
-        if (P + 1 < nparts_old) {
-            const unsigned long long* pb = part_words<K>(old_words, P + 1);
+        if (has_b) {
+            const unsigned long long* pb = old_words + ((P + 1) / K - base) * Occ<K>::kWords + 3 * ((P + 1) % K);
             o.b = Window{pb[0], pb[1], pb[2]};
         }
     }
     return o;
+}
+
+// The old blocks that superblocks [S0, S1) of the next dictionary read,
+// [b_lo, b_hi]: their windows start at old row S0 2^16 - ins_i0[S0] at the
+// lowest and end within two parts of S1 2^16 - ins_i0[S1] (at most n_ext).
+template <int K>
+__device__ __forceinline__ void staged_range(const uint32_t* __restrict__ ins_i0, uint64_t n_ext, uint64_t S0,
+                                             uint64_t S1, uint64_t& b_lo, uint64_t& b_hi) {
+    const uint64_t o0 = S0 << kSuperShift, o1 = S1 << kSuperShift;
+    const uint64_t lo_row = o0 - min((uint64_t)ins_i0[S0], o0);
+    const uint64_t hi_row = min((uint64_t)n_ext, o1 - min((uint64_t)ins_i0[S1], o1)) + 2 * kOccSpan;
+    const uint64_t rows_per_block = 64ull * K;
+    const uint64_t last = n_ext / rows_per_block;  // the old dictionary's last block
+    b_lo = min(lo_row / rows_per_block, last);
+    b_hi = min(hi_row / rows_per_block, last);
 }
 
 // 64 old rows starting at row s, from the pair of parts holding them.
@@ -135,6 +163,10 @@ __device__ __forceinline__ Window spread_old(Window w, unsigned long long F) {
 //  5. the parts are written into their blocks of 64 K rows.
 // Every index that comes from g_sa is checked; an inconsistent plan flags
 // *d_err (bit 10) and never leads outside the arrays.
+// With `staged`, the grid covers superblocks [sb_first, sb_first + grid)
+// and old_words holds a staged copy of the old blocks they read
+// (staged_range, at most stage_blocks of them); without it, old_words is the
+// whole old dictionary and sb_first is 0.
 template <class IdxT, int kT, int K>
 __global__ void __launch_bounds__(kT, kT == 256 ? 4 : 2) insert_kernel(const unsigned long long* __restrict__ old_words,
                                                     unsigned long long n_ext, const uint8_t* __restrict__ bint,
@@ -142,18 +174,25 @@ __global__ void __launch_bounds__(kT, kT == 256 ? 4 : 2) insert_kernel(const uns
                                                     const uint32_t* __restrict__ ins_i0,
                                                     unsigned long long* __restrict__ new_words,
                                                     unsigned long long n_new, uint32_t* __restrict__ sb_tot,
-                                                    uint32_t* __restrict__ d_err) {
+                                                    uint32_t* __restrict__ d_err, unsigned long long sb_first,
+                                                    int staged, unsigned long long stage_blocks) {
     constexpr int kNB = kBlocksPerSuper, kPer = kNB / kT;
     __shared__ uint32_t sF[2][kNB];  // new rows of each part (rows 0-31, 32-63); later its counts
     __shared__ uint32_t sD[2][kNB];  // terminator plane: of the new rows, later of the whole part
     __shared__ uint32_t sC[4][kNB];  // lo plane (words 0, 1) and hi plane (2, 3): of the new rows, then the part
     __shared__ uint32_t sP[2][kNB];  // new symbols before each part; later the block counters
     const int tid = threadIdx.x;
-    const uint64_t S = blockIdx.x;
+    const uint64_t S = sb_first + blockIdx.x;
     const uint64_t O = S << kSuperShift;
     const uint64_t p_first = S * kNB;
     const uint64_t np_new = dict_parts(n_new, K);
     const uint64_t np_old = dict_parts(n_ext, K);
+    uint64_t base = 0, avail = n_ext / (64ull * K) + 1;  // old blocks old_words holds
+    if (staged) {
+        uint64_t b_hi;
+        staged_range<K>(ins_i0, n_ext, sb_first, sb_first + gridDim.x, base, b_hi);
+        avail = min(b_hi - base + 1, (uint64_t)stage_blocks);
+    }
     for (int x = tid; x < kNB; x += kT) {
         sF[0][x] = sF[1][x] = sD[0][x] = sD[1][x] = 0u;
         sC[0][x] = sC[1][x] = sC[2][x] = sC[3][x] = 0u;
@@ -256,8 +295,12 @@ __global__ void __launch_bounds__(kT, kT == 256 ? 4 : 2) insert_kernel(const uns
         // nothing: their window is never used)
         if (b < np_new && o <= n_new && (inew > o || s_old[bb] > n_ext)) atomicOr(d_err, 1024u);
         if (inew > o || s_old[bb] > n_ext) s_old[bb] = inew > o ? 0ull : (uint64_t)n_ext;
-        if (b >= np_new) s_old[bb] = 0;
-        op[bb] = old_pair<K>(old_words, np_old, s_old[bb]);
+        if (b >= np_new) {
+            s_old[bb] = 0;
+            op[bb].a = op[bb].b = Window{0ull, 0ull, 0ull};
+        } else {
+            op[bb] = old_pair<K>(old_words, np_old, s_old[bb], base, avail, d_err);
+        }
     }
 #pragma unroll
     for (int bb = 0; bb < kPer; ++bb) {
@@ -352,6 +395,30 @@ __global__ void __launch_bounds__(kT, kT == 256 ? 4 : 2) insert_kernel(const uns
     }
 }
 
+// Copies the old blocks that superblocks [S0, S1) of the next dictionary
+// read (staged_range) from the dictionary being rewritten in place into the
+// staging buffer, before those superblocks overwrite any of them.
+template <int K>
+__global__ void __launch_bounds__(kThreads) stage_old_kernel(const unsigned long long* __restrict__ old_words,
+                                                             unsigned long long n_ext,
+                                                             const uint32_t* __restrict__ ins_i0,
+                                                             unsigned long long S0, unsigned long long S1,
+                                                             unsigned long long* __restrict__ stage,
+                                                             unsigned long long stage_blocks,
+                                                             uint32_t* __restrict__ d_err) {
+    uint64_t b_lo, b_hi;
+    staged_range<K>(ins_i0, n_ext, S0, S1, b_lo, b_hi);
+    uint64_t blocks = b_hi - b_lo + 1;
+    if (blocks > stage_blocks) {  // cannot happen for a consistent plan: the chunk's parts need fewer
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(d_err, 1024u);
+        blocks = stage_blocks;
+    }
+    const uint64_t words = blocks * Occ<K>::kWords;
+    const unsigned long long* src = old_words + b_lo * Occ<K>::kWords;
+    for (uint64_t w = (uint64_t)blockIdx.x * kThreads + threadIdx.x; w < words; w += (uint64_t)gridDim.x * kThreads)
+        stage[w] = src[w];
+}
+
 // ---------------------------------------------------------------------------
 // The same merge for the 4-bit dictionary (5 to 16 symbols): one output
 // block per thread, a CTA of 256 threads builds four 64-block superblocks;
@@ -367,18 +434,27 @@ struct WindowW {
 };
 
 // 64 old rows starting at row s (rows past the old end read as zero).
-__device__ __forceinline__ WindowW old_window_w(const OccBlockW* __restrict__ old_blocks, uint64_t nb_old, uint64_t s) {
+// old_blocks holds old blocks [base, base + avail) (all of them, or a
+// staged copy); a block outside reads as zero and flags *d_err.
+__device__ __forceinline__ WindowW old_window_w(const OccBlockW* __restrict__ old_blocks, uint64_t nb_old, uint64_t s,
+                                                uint64_t base, uint64_t avail, uint32_t* __restrict__ d_err) {
     const uint64_t bs = s >> kOccShift;
     const uint32_t off = (uint32_t)(s & (kOccSpan - 1));
-    const OccBlockW& A = old_blocks[bs];
+    if (bs < base || bs - base >= avail) {
+        atomicOr(d_err, 1024u);
+        WindowW z;
+        z.w[0] = z.w[1] = z.w[2] = z.w[3] = z.dm = 0ull;
+        return z;
+    }
+    const OccBlockW& A = old_blocks[bs - base];
     unsigned long long x[9];
 #pragma unroll
     for (int k = 0; k < 4; ++k) x[k] = A.sym[k];
     unsigned long long da = A.dmask, db = 0;
 #pragma unroll
     for (int k = 4; k < 9; ++k) x[k] = 0;
-    if (bs + 1 < nb_old) {
-        const OccBlockW& B = old_blocks[bs + 1];
+    if (bs + 1 < nb_old && bs + 1 - base < avail) {
+        const OccBlockW& B = old_blocks[bs + 1 - base];
 #pragma unroll
         for (int k = 0; k < 4; ++k) x[4 + k] = B.sym[k];
         db = B.dmask;
@@ -417,17 +493,77 @@ __device__ __forceinline__ void splice_w(WindowW& w, uint32_t p, uint32_t code, 
     w.dm = (w.dm & keepd) | ((unsigned long long)dollar << p) | ((w.dm & ~keepd) << 1);
 }
 
+// The first new symbol at or after row o: |{i : g_sa[i] + i < o}|.
+template <class IdxT>
+__device__ __forceinline__ uint64_t first_new_at(const IdxT* __restrict__ gsa, uint64_t n_int, uint64_t o) {
+    uint64_t lo = 0, hi = n_int;
+    while (lo < hi) {
+        const uint64_t mid = lo + ((hi - lo) >> 1);
+        if ((uint64_t)gsa[mid] + mid < o) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// The old blocks [b_lo, b_hi] that output blocks [b0, b1) of the 4-bit
+// dictionary read (as staged_range for the 2-bit one).
+template <class IdxT>
+__device__ __forceinline__ void staged_range_w(const IdxT* __restrict__ gsa, uint64_t n_int, uint64_t n_ext,
+                                               uint64_t b0, uint64_t b1, uint64_t& b_lo, uint64_t& b_hi) {
+    const uint64_t o0 = b0 << kOccShift, o1 = b1 << kOccShift;
+    const uint64_t i0 = first_new_at(gsa, n_int, o0), i1 = first_new_at(gsa, n_int, o1);
+    const uint64_t nb = (n_ext >> kOccShift) + 1;
+    b_lo = min((o0 - min(i0, o0)) >> kOccShift, nb - 1);
+    b_hi = min((min((uint64_t)n_ext, o1 - min(i1, o1)) + 2 * kOccSpan) >> kOccShift, nb - 1);
+}
+
+template <class IdxT>
+__global__ void __launch_bounds__(kThreads) stage_old_w_kernel(const OccBlockW* __restrict__ old_blocks,
+                                                               unsigned long long n_ext, const IdxT* __restrict__ gsa,
+                                                               unsigned long long n_int, unsigned long long b0,
+                                                               unsigned long long b1, OccBlockW* __restrict__ stage,
+                                                               unsigned long long stage_blocks,
+                                                               uint32_t* __restrict__ d_err) {
+    __shared__ unsigned long long s_lo, s_n;
+    if (threadIdx.x == 0) {
+        uint64_t lo, hi;
+        staged_range_w(gsa, n_int, n_ext, b0, b1, lo, hi);
+        uint64_t nblk = hi - lo + 1;
+        if (nblk > stage_blocks) {
+            if (blockIdx.x == 0) atomicOr(d_err, 1024u);
+            nblk = stage_blocks;
+        }
+        s_lo = lo;
+        s_n = nblk;
+    }
+    __syncthreads();
+    const ulonglong2* src = reinterpret_cast<const ulonglong2*>(old_blocks + s_lo);
+    ulonglong2* dst = reinterpret_cast<ulonglong2*>(stage);
+    for (uint64_t v = (uint64_t)blockIdx.x * kThreads + threadIdx.x; v < 4 * s_n; v += (uint64_t)gridDim.x * kThreads)
+        dst[v] = src[v];
+}
+
 template <class IdxT>
 __global__ void __launch_bounds__(kThreads) insert_w_kernel(const OccBlockW* __restrict__ old_blocks,
                                                             unsigned long long n_ext, const uint8_t* __restrict__ bint,
                                                             const IdxT* __restrict__ gsa, unsigned long long n_int,
                                                             OccBlockW* __restrict__ new_blocks,
                                                             unsigned long long n_new, unsigned long long nsb,
-                                                            uint32_t* __restrict__ sb_tot) {
+                                                            uint32_t* __restrict__ sb_tot, uint32_t* __restrict__ d_err,
+                                                            unsigned long long b_first, int staged,
+                                                            unsigned long long stage_blocks) {
     __shared__ uint32_t warp_tot[kThreads / 32][kSigmaW];
+    __shared__ unsigned long long s_base, s_avail;
     const uint64_t nb_new = (n_new >> kOccShift) + 1;
     const uint64_t nb_old = (n_ext >> kOccShift) + 1;
-    const uint64_t b = (uint64_t)blockIdx.x * kThreads + threadIdx.x;
+    const uint64_t b = b_first + (uint64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (threadIdx.x == 0) {
+        uint64_t lo = 0, hi = nb_old - 1;
+        if (staged) staged_range_w(gsa, n_int, n_ext, b_first, b_first + (uint64_t)gridDim.x * kThreads, lo, hi);
+        s_base = lo;
+        s_avail = staged ? min(hi - lo + 1, (uint64_t)stage_blocks) : nb_old;
+    }
+    __syncthreads();
+    const uint64_t base = s_base, avail = s_avail;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     WindowW w;
     w.w[0] = w.w[1] = w.w[2] = w.w[3] = w.dm = 0;
@@ -443,7 +579,7 @@ __global__ void __launch_bounds__(kThreads) insert_w_kernel(const OccBlockW* __r
         }
         uint64_t i = lo;
         const uint64_t s_old = o >= i ? min((unsigned long long)(o - i), n_ext) : 0ull;
-        w = old_window_w(old_blocks, nb_old, s_old);
+        w = old_window_w(old_blocks, nb_old, s_old, base, avail, d_err);
         while (i < n_int) {
             const uint64_t row = (uint64_t)gsa[i] + i;
             if (row >= o + kOccSpan) break;
@@ -634,11 +770,20 @@ void super_scan(Launcher& L, const uint32_t* sb_tot, uint64_t nsb, unsigned long
 
 }  // namespace
 
+uint64_t insert_stage_blocks(int occ_k) {
+    return (uint64_t)kStageSupers * kBlocksPerSuper / occ_k + 8;
+}
+
+size_t insert_stage_bytes(int code_bits, int occ_k) {
+    return code_bits == 4 ? (size_t)(kStageBlocksW + 8) * sizeof(OccBlockW)
+                          : (size_t)insert_stage_blocks(occ_k) * 8 * (3 * occ_k + 1);
+}
+
 template <class IdxT>
 void launch_insert(Launcher& L, const void* old_blocks, uint64_t n_ext, const uint8_t* bint, const IdxT* gsa,
                    uint64_t n_int, const uint32_t* ins_i0, void* new_blocks, unsigned long long* new_super,
                    unsigned long long* new_C, uint64_t m_new, uint32_t* sb_tot, uint32_t* d_err, int code_bits,
-                   int occ_k) {
+                   int occ_k, unsigned long long* stage) {
     const uint64_t n_new = n_ext + n_int;
     // the superblock scan's per-chunk totals live after the superblock totals
     const uint64_t nsb_all = dict_supers_of(n_new, code_bits);
@@ -646,19 +791,38 @@ void launch_insert(Launcher& L, const void* old_blocks, uint64_t n_ext, const ui
         reinterpret_cast<unsigned long long*>(sb_tot + ((nsb_all * dict_codes(code_bits) + 3) & ~3ull));
     if (code_bits == 4) {
         const uint64_t nsb = dict_supers_w(n_new);
-        const double bytes = 64.0 * dict_blocks(n_ext) + (1.0 + sizeof(IdxT)) * n_int + 64.0 * dict_blocks(n_new);
-        SBWT_LAUNCH(L, "insert_merge", bytes, 0, nullptr, insert_w_kernel<IdxT>,
-                    ceil_div_u(nsb * kBlocksPerSuperW, kThreads), kThreads, 0,
-                    static_cast<const OccBlockW*>(old_blocks), (unsigned long long)n_ext, bint, gsa,
-                    (unsigned long long)n_int, static_cast<OccBlockW*>(new_blocks), (unsigned long long)n_new,
-                    (unsigned long long)nsb, sb_tot);
+        const uint64_t nb_all = nsb * kBlocksPerSuperW;  // output blocks the grid covers
+        const auto* old_b = static_cast<const OccBlockW*>(old_blocks);
+        auto* new_b = static_cast<OccBlockW*>(new_blocks);
+        if (!stage) {
+            const double bytes = 64.0 * dict_blocks(n_ext) + (1.0 + sizeof(IdxT)) * n_int + 64.0 * dict_blocks(n_new);
+            SBWT_LAUNCH(L, "insert_merge", bytes, 0, nullptr, insert_w_kernel<IdxT>, ceil_div_u(nb_all, kThreads),
+                        kThreads, 0, old_b, (unsigned long long)n_ext, bint, gsa, (unsigned long long)n_int, new_b,
+                        (unsigned long long)n_new, (unsigned long long)nsb, sb_tot, d_err, 0ull, 0, 0ull);
+        } else {
+            // in place, from the top down in chunks of kStageBlocksW output
+            // blocks (a multiple of the CTA's blocks), as for 2-bit codes
+            const uint64_t stage_blocks = kStageBlocksW + 8;
+            const uint64_t top = (nb_all + kThreads - 1) / kThreads * kThreads;
+            for (uint64_t b1 = top; b1 > 0;) {
+                const uint64_t b0 = b1 > kStageBlocksW ? b1 - kStageBlocksW : 0;
+                SBWT_LAUNCH(L, "insert_stage", 128.0 * (b1 - b0), 0, nullptr, stage_old_w_kernel<IdxT>, kStageGrid,
+                            kThreads, 0, old_b, (unsigned long long)n_ext, gsa, (unsigned long long)n_int,
+                            (unsigned long long)b0, (unsigned long long)b1, reinterpret_cast<OccBlockW*>(stage),
+                            (unsigned long long)stage_blocks, d_err);
+                SBWT_LAUNCH(L, "insert_merge", 128.0 * (b1 - b0), 0, nullptr, insert_w_kernel<IdxT>,
+                            (unsigned)((b1 - b0) / kThreads), kThreads, 0, reinterpret_cast<const OccBlockW*>(stage),
+                            (unsigned long long)n_ext, bint, gsa, (unsigned long long)n_int, new_b,
+                            (unsigned long long)n_new, (unsigned long long)nsb, sb_tot, d_err, (unsigned long long)b0,
+                            1, (unsigned long long)stage_blocks);
+                b1 = b0;
+            }
+        }
         super_scan<kSigmaW>(L, sb_tot, nsb, new_super, new_C, m_new, chunk_tot);
         return;
     }
     const uint64_t nsb = dict_supers(n_new);
     const double bb = (double)dict_block_bytes(2, occ_k);
-    const double bytes = bb * dict_blocks(n_ext, occ_k) + (1.0 + sizeof(IdxT)) * n_int + bb * dict_blocks(n_new, occ_k) +
-                         4.0 * (nsb + 1);
     // Dense new rows (a quarter of the result or more): 512 threads, so the
     // runs of new symbols spread over more threads.  Sparse: 256 threads of
     // four parts each, so more CTAs (superblocks) are resident per SM and
@@ -671,19 +835,46 @@ void launch_insert(Launcher& L, const void* old_blocks, uint64_t n_ext, const ui
                              : (occ_k == 4 ? insert_kernel<IdxT, kInsertThreadsSparse, 4>
                                            : (occ_k == 2 ? insert_kernel<IdxT, kInsertThreadsSparse, 2>
                                                          : insert_kernel<IdxT, kInsertThreadsSparse, 1>));
-    SBWT_LAUNCH(L, "insert_merge", bytes, 0, nullptr, kern, (unsigned)nsb, threads, 0,
-                static_cast<const unsigned long long*>(old_blocks), (unsigned long long)n_ext, bint, gsa,
-                (unsigned long long)n_int, ins_i0, static_cast<unsigned long long*>(new_blocks),
-                (unsigned long long)n_new, sb_tot, d_err);
+    const auto* old_w = static_cast<const unsigned long long*>(old_blocks);
+    auto* new_w = static_cast<unsigned long long*>(new_blocks);
+    if (!stage) {
+        const double bytes = bb * dict_blocks(n_ext, occ_k) + (1.0 + sizeof(IdxT)) * n_int +
+                             bb * dict_blocks(n_new, occ_k) + 4.0 * (nsb + 1);
+        SBWT_LAUNCH(L, "insert_merge", bytes, 0, nullptr, kern, (unsigned)nsb, threads, 0, old_w,
+                    (unsigned long long)n_ext, bint, gsa, (unsigned long long)n_int, ins_i0, new_w,
+                    (unsigned long long)n_new, sb_tot, d_err, 0ull, 0, 0ull);
+    } else {
+        // In place (the host tier keeps one dictionary): superblocks from the
+        // top down in chunks of kStageSupers; each chunk first copies the old
+        // blocks it reads to the staging buffer.  A chunk's old rows all lie
+        // below its first output row (new rows only push old rows up), so
+        // the chunks above it never overwrite them before they are staged.
+        const uint64_t stage_blocks = insert_stage_blocks(occ_k);
+        auto* const stage_kern = occ_k == 4 ? stage_old_kernel<4> : (occ_k == 2 ? stage_old_kernel<2>
+                                                                                 : stage_old_kernel<1>);
+        for (uint64_t s1 = nsb; s1 > 0;) {
+            const uint64_t s0 = s1 > kStageSupers ? s1 - kStageSupers : 0;
+            const double rows = (double)(s1 - s0) * (1 << kSuperShift);
+            SBWT_LAUNCH(L, "insert_stage", 2.0 * rows / (64.0 * occ_k) * bb, 0, nullptr, stage_kern, kStageGrid,
+                        kThreads, 0, old_w, (unsigned long long)n_ext, ins_i0, (unsigned long long)s0,
+                        (unsigned long long)s1, stage, (unsigned long long)stage_blocks, d_err);
+            SBWT_LAUNCH(L, "insert_merge", 2.0 * rows / (64.0 * occ_k) * bb + (1.0 + sizeof(IdxT)) * rows *
+                                              ((double)n_int / (double)n_new), 0, nullptr, kern, (unsigned)(s1 - s0),
+                        threads, 0, stage, (unsigned long long)n_ext, bint, gsa, (unsigned long long)n_int, ins_i0,
+                        new_w, (unsigned long long)n_new, sb_tot, d_err, (unsigned long long)s0, 1,
+                        (unsigned long long)stage_blocks);
+            s1 = s0;
+        }
+    }
     super_scan<4>(L, sb_tot, nsb, new_super, new_C, m_new, chunk_tot);
 }
 
 template void launch_insert<uint32_t>(Launcher&, const void*, uint64_t, const uint8_t*, const uint32_t*, uint64_t,
                                       const uint32_t*, void*, unsigned long long*, unsigned long long*, uint64_t,
-                                      uint32_t*, uint32_t*, int, int);
+                                      uint32_t*, uint32_t*, int, int, unsigned long long*);
 template void launch_insert<unsigned long long>(Launcher&, const void*, uint64_t, const uint8_t*,
                                                 const unsigned long long*, uint64_t, const uint32_t*, void*,
                                                 unsigned long long*, unsigned long long*, uint64_t, uint32_t*,
-                                                uint32_t*, int, int);
+                                                uint32_t*, int, int, unsigned long long*);
 
 }  // namespace sbwt

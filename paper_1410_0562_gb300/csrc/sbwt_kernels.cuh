@@ -93,11 +93,17 @@ void launch_unpack(Launcher& L, const void* blocks, uint64_t r0, uint64_t r1, co
 // superblock, rounded up to 4 words, then 4 (16) 64-bit words per 256
 // superblocks.  ins_i0 is the plan bint_gather wrote (2-bit dictionary;
 // unused for 4-bit codes); an inconsistent plan sets *d_err bit 10.
+// With `stage` (2-bit dictionary only), new_blocks is old_blocks: the
+// dictionary is rewritten in place, from the top superblock down in chunks,
+// each chunk's old blocks first copied to `stage` (insert_stage_blocks(occ_k)
+// blocks, in HBM).
 template <class IdxT>
 void launch_insert(Launcher& L, const void* old_blocks, uint64_t n_ext, const uint8_t* bint, const IdxT* gsa,
                    uint64_t n_int, const uint32_t* ins_i0, void* new_blocks, unsigned long long* new_super,
                    unsigned long long* new_C, uint64_t m_new, uint32_t* sb_tot, uint32_t* d_err, int code_bits,
-                   int occ_k);
+                   int occ_k, unsigned long long* stage = nullptr);
+uint64_t insert_stage_blocks(int occ_k);
+size_t insert_stage_bytes(int code_bits, int occ_k);  // the staging buffer an in-place Insert needs
 
 // plan.cu: checks device-resident offsets (offsets[0] = 0, non-decreasing,
 // every read shorter than max_block suffixes; summary->bad != 0 otherwise),

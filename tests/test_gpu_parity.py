@@ -343,13 +343,21 @@ def test_autotune_block_suffixes():
         sb.sbwt_autotune_block_suffixes(idx.handle, d_reads.data_ptr(), d_off.data_ptr(), w.m, [0])
 
 
-def test_host_tier_forced():
-    """Rank dictionaries in mapped pinned host memory: same B, same ranks."""
+@pytest.mark.parametrize("sampling", [64, 128, 256])
+def test_host_tier_forced(sampling):
+    """The dictionary in mapped pinned host memory, rewritten in place by
+    every block's Insert: same B, same ranks; a byte outside the alphabet is
+    refused before the rewrite, leaving the index as it was."""
     w = readgen.tiny()
     expect = oracle.bwt(w.reads, w.offsets)
     idx = gpu_bwt(w.reads, w.offsets, M=20_000, cuts=w.appends)
     ref_ranks = idx.rank_batch(np.full(50, ord("C"), np.uint8), np.arange(0, 101_000, 2020, dtype=np.uint64))
-    h = sb.SetBWT(b"ACGT", block_suffixes=20_000, host_tier=3)
+    h = sb.SetBWT(b"ACGT", block_suffixes=20_000, host_tier=3, occ_sampling=sampling)
+    bad = w.reads[: int(w.offsets[300])].copy()
+    bad[777] = ord("N")
+    with pytest.raises(sb.SbwtError) as e:
+        h.append(bad, w.offsets[:301])
+    assert e.value.code == sb.SBWT_EINVAL and h.size() == (0, 0)
     h.append(w.reads[: int(w.offsets[500])], w.offsets[:501])
     h.append(w.reads[int(w.offsets[500]):], w.offsets[500:] - w.offsets[500])
     assert np.array_equal(h.bwt(), expect)
@@ -357,6 +365,18 @@ def test_host_tier_forced():
     assert host > 0
     assert np.array_equal(h.rank_batch(np.full(50, ord("C"), np.uint8), np.arange(0, 101_000, 2020, dtype=np.uint64)),
                           ref_ranks)
+    before = h.bwt().copy()
+    with pytest.raises(sb.SbwtError) as e:
+        h.append(bad, w.offsets[:301])
+    assert e.value.code == sb.SBWT_EINVAL
+    assert np.array_equal(h.bwt(), before)
+    n, _ = h.size()
+    assert 8.0 * sb.sbwt_memory(h.handle)[1] / n <= 6.0
+
+
+def test_host_link_probe():
+    h2d, d2h, rnd = sb.sbwt_host_link(sb.SetBWT(b"ACGT").handle)
+    assert h2d > 1 and d2h > 1 and rnd > 0.1
 
 
 def test_host_tier_under_budget():

@@ -107,3 +107,25 @@ def test_served_workload_one_twentieth_equals_oracle():
     B = idx.bwt()
     idx.close()
     assert_same(B, oracle_jobs.result("serving_20"))
+
+
+@pytest.mark.oracle_full("short")
+def test_short_reads_host_tier_equals_oracle():
+    """The short-read workload with its one dictionary in pinned host memory
+    (occurrence sampling 256), rewritten in place by every block's Insert,
+    from the top down in chunks staged in HBM (a 101M-row dictionary spans
+    four chunks): B equals the oracle's, and the host holds at most 6 bits per
+    row (the paper's bound of 3 n log sigma bits for DNA)."""
+    import torch
+    w = readgen.short()
+    d_reads = torch.from_numpy(w.reads).cuda()
+    d_off = torch.from_numpy(w.offsets.astype(np.int64)).cuda()
+    idx = sb.SetBWT(w.alphabet, index_bits=w.index_bits, block_suffixes=w.block_suffixes, host_tier=3,
+                    occ_sampling=256)
+    idx.append_device(d_reads.data_ptr(), d_off.data_ptr(), w.m)
+    n, _ = idx.size()
+    hbm, host = sb.sbwt_memory(idx.handle)
+    assert 8.0 * host / n <= 6.0
+    B = idx.bwt()
+    idx.close()
+    assert_same(B, oracle_jobs.result("short"))

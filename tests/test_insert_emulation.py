@@ -44,7 +44,7 @@ def emu(tmp_path_factory):
     (d / "dict.inc").write_text(_cut(hdr, "constexpr int kOccShift = 6;",
                                      "// rank(c, i) within i's superblock: the block counter"))
     (d / "scan.inc").write_text(_cut(hdr, "struct SumOp {", "// Launch bookkeeping"))
-    (d / "insert.inc").write_text(_cut(ins, "constexpr int kInsertThreads", "// ------------------------------------------------"
+    (d / "insert.inc").write_text(_cut(ins, "constexpr int kThreads = 256;", "// ------------------------------------------------"
                                                                  "---------------------------\n// The same merge"))
     lib = d / "libinsemu.so"
     subprocess.check_call(["g++", "-O1", "-std=c++20", "-shared", "-fPIC", "-pthread", "-I", str(d), "-o", str(lib),
@@ -53,6 +53,8 @@ def emu(tmp_path_factory):
     P, U64 = ctypes.c_void_p, ctypes.c_uint64
     L.emu_insert.argtypes = [P, U64, P, P, ctypes.c_int, U64, P, P, U64, P, P, ctypes.c_int]
     L.emu_insert.restype = ctypes.c_int
+    L.emu_insert_in_place.argtypes = [P, U64, P, P, ctypes.c_int, U64, P, U64, P, P, ctypes.c_int, U64]
+    L.emu_insert_in_place.restype = ctypes.c_int
     return L
 
 
@@ -181,3 +183,33 @@ def test_inconsistent_plan_is_flagged_without_leaving_the_arrays(emu):
     p[-1] = len(bint) + 5
     _, _, err = run(emu, B_ext, bint, gsa, ins_plan=p)
     assert err & 1024
+
+
+@pytest.mark.parametrize("k", [1, 2, 4])
+@pytest.mark.parametrize("n_ext,n_int,kind,chunk", [
+    (200_000, 3_000, "uniform", 1), (180_000, 90_000, "clustered", 2), (140_000, 5, "one", 1),
+    (70_000, 200_000, "uniform", 1),
+])
+def test_in_place_merge_matches_the_oracle(emu, n_ext, n_int, kind, chunk, k):
+    """The host tier's Insert rewrites the one dictionary in place, from the
+    top superblock down in chunks, staging each chunk's old blocks first;
+    chunks of one or two superblocks over dictionaries of three to five."""
+    rng = np.random.default_rng(n_ext + n_int + chunk)
+    B_ext, bint, gsa = random_case(rng, n_ext, n_int, kind)
+    n_new = n_ext + n_int
+    words = np.zeros((n_new // (64 * k) + 1) * (3 * k + 1), np.uint64)
+    old = pack_dict(B_ext, k)
+    words[: len(old)] = old
+    codes = np.array([255 if b == ord("$") else CODE[int(b)] for b in bint], np.uint8)
+    g = np.ascontiguousarray(gsa, np.uint32)
+    p = plan(gsa, n_new)
+    tot = np.zeros(4 * ((n_new >> 16) + 1), np.uint32)
+    err = ctypes.c_uint32(0)
+    ptr = lambda a: ctypes.c_void_p(a.ctypes.data)  # noqa: E731
+    assert emu.emu_insert_in_place(ptr(words), n_ext, ptr(codes), ptr(g), 4, n_int, ptr(p), n_new, ptr(tot),
+                                   ctypes.byref(err), k, chunk) == 0
+    expect = oracle.insert(B_ext, bint, gsa)
+    assert err.value == 0
+    bad = np.nonzero(words != pack_dict(expect, k))[0]
+    assert len(bad) == 0, f"words differ at {bad[:8].tolist()}"
+    assert np.array_equal(tot, super_totals(expect))
