@@ -17,7 +17,7 @@ other workloads as keys, each timed the same way:
 * ``batched``: 2M reads of U[50, 250] bp from a 50 Mbp genome, 64-bit
   indices: the plain per-block pipeline (every step of every block in turn
   on one stream, blocks of 2^24, occurrence sampling 64, eager launches)
-  against the batched form (block size and sampling from the autotuner,
+  against the batched form (block size, sampling and tile shapes from the autotuner,
   block sorts overlapping the ranking and Insert of earlier blocks, every
   append one CUDA-graph launch), with per-kernel fractions of the HBM peak;
 * ``long``: 20k log-normal long reads (mean 10 kbp, 10% errors) from a 100 Mbp
@@ -406,6 +406,7 @@ def measure_forms(sb, torch, timer, w, local, args, peak, plain_M, candidates, s
     idx_b = sb.SetBWT(w.alphabet, index_bits=w.index_bits, stream=stream.cuda_stream, device=local)
     best_M, best_s, tune = sb.sbwt_autotune(idx_b.handle, d_reads.data_ptr(), d_off.data_ptr(), w.m, candidates,
                                             [64, 128, 256])
+    best_tiles, tune_tiles = sb.sbwt_autotune_tile_shapes(idx_b.handle, d_reads.data_ptr(), d_off.data_ptr(), w.m)
     sb.sbwt_set_graph_replay(idx_b.handle, True)
 
     def step_b():
@@ -423,7 +424,10 @@ def measure_forms(sb, torch, timer, w, local, args, peak, plain_M, candidates, s
     out["batched"] = {"value": whole_job_mbps(w.bases, 1, args.steps, tot_b), "unit": UNIT,
                       "ms_per_step": tot_b / args.steps, "block_suffixes": int(best_M), "occ_sampling": int(best_s),
                       "block_overlap": True, "graph_replay": True, "graph_counts": graphs,
-                      "autotune_ms": {f"{k[0]}/{k[1]}": round(v, 3) for k, v in tune.items()}, "kernels": kern_b}
+                      "autotune_ms": {f"{k[0]}/{k[1]}": round(v, 3) for k, v in tune.items()},
+                      "tile_shapes": {"insert_threads": best_tiles[0], "rank_segment": best_tiles[1]},
+                      "autotune_tiles_ms": {f"{k[0]}/{k[1]}": round(v, 3) for k, v in tune_tiles.items()},
+                      "kernels": kern_b}
     out["batched_over_plain"] = out["batched"]["value"] / out["plain"]["value"]
     del d_reads, d_off
     return out
@@ -471,13 +475,23 @@ def measure_served(sb, torch, w_res, requests, local, stream, peak):
            "requests": len(requests), "request_bases": sum(int(o[-1]) for _, o in requests),
            "hbm_budget": 8 << 30, "serving": report,
            "largest_request_append": {"reads": len(big[1]) - 1, "bases": int(big[1][-1]), "kernels": kern}}
+    ix_probe = sb.SetBWT(b"ACGT", stream=stream.cuda_stream, device=local)
+    bw_all = sb.sbwt_measure_bandwidth(ix_probe.handle)
+    ix_probe.close()
+    out["bandwidth"] = bw_all
+    cr = kern.get("compute_ranks")
+    if cr and cr["GBps"]:
+        # ComputeRanks reads one random 32-byte sector per LF step: its
+        # roofline on a DRAM-resident dictionary is random-read bandwidth
+        out["largest_request_append"]["compute_ranks_frac_of_hbm_random_reads"] = round(
+            cr["GBps"] / bw_all["hbm_random_32B_GBps"], 3)
     del d_reads, d_off
     torch.cuda.empty_cache()
     # host tier: a 2M-read resident index whose one dictionary lives in
     # pinned host memory under a 512 MB budget, rewritten in place by Insert;
     # its kernels against the host link measured on the same device
-    h2d, d2h, rnd = sb.sbwt_host_link(ix_probe := sb.SetBWT(b"ACGT", stream=stream.cuda_stream, device=local))
-    ix_probe.close()
+    bw = bw_all
+    h2d, rnd = bw["h2d_GBps"], bw["host_random_32B_GBps"]
     m2 = 2_000_000
     small_reads = w_res.reads[: int(w_res.offsets[m2])]
     small_off = w_res.offsets[: m2 + 1]
@@ -496,7 +510,7 @@ def measure_served(sb, torch, w_res, requests, local, stream, peak):
     sb.sbwt_set_profiling(ix2.handle, False)
     rep2 = measure_serving(sb, ix2, small_reqs[1:])
     ix2.close()
-    link = {"h2d_GBps": h2d, "d2h_GBps": d2h, "random_32B_read_GBps": rnd}
+    link = bw
     tiered = {}
     for name in ("compute_ranks", "insert_merge", "insert_stage"):
         k = tier_k.get(name)

@@ -209,14 +209,20 @@ int sbwt_get_stage(sbwt_index *idx, int stage, void *out, uint64_t cap, uint64_t
  * Off by default. */
 int sbwt_set_graph_replay(sbwt_index *idx, int on);
 
-/* The host link the host tier works over, measured on the index's device
- * and stream: H2D and D2H copies of 256 MB between pinned host memory and
- * HBM, and random 32-byte sector reads by a kernel from mapped pinned host
- * memory (the access of ComputeRanks and rank queries to a host-tier
- * dictionary), in GB/s; any out pointer may be NULL.  Allocates 256 MB of
- * pinned host memory and 256 MB of HBM for the measurement and frees them
- * (outside the HBM budget).  Errors: SBWT_ENOMEM, SBWT_EDEVICE, SBWT_EBUSY. */
-int sbwt_host_link(sbwt_index *idx, double *h2d_gbs, double *d2h_gbs, double *random_read_gbs);
+/* Bandwidths the index's kernels work against, measured on its device and
+ * stream: H2D and D2H copies of 256 MB between pinned host memory and HBM
+ * (the host link the host tier uses), and random 32-byte sector reads by a
+ * kernel from mapped pinned host memory and from 1 GB of HBM (the access of
+ * ComputeRanks and rank queries to a dictionary that is not in L2), in GB/s.
+ * Allocates 256 MB of pinned host memory and 1 GB of HBM for the
+ * measurement and frees them (outside the HBM budget).  Errors:
+ * SBWT_EINVAL, SBWT_ENOMEM, SBWT_EDEVICE, SBWT_EBUSY. */
+typedef struct {
+    double h2d_gbs, d2h_gbs;   /* copies over the host link */
+    double host_random_gbs;    /* random 32-byte reads from mapped pinned host memory */
+    double hbm_random_gbs;     /* random 32-byte reads from HBM */
+} sbwt_bandwidth;
+int sbwt_measure_bandwidth(sbwt_index *idx, sbwt_bandwidth *out);
 
 /* Block overlap (on by default): the suffix sort of each block runs on a
  * second stream, ahead of the ranking, gather and Insert of the blocks before
@@ -238,6 +244,35 @@ int sbwt_set_block_overlap(sbwt_index *idx, int on);
  * or the error of a failing append. */
 int sbwt_autotune_block_suffixes(sbwt_index *idx, const uint8_t *d_reads, const uint64_t *d_offsets, uint64_t m,
                                  const uint64_t *candidates, int ncand, uint64_t *best_out, double *ms_out);
+
+/* Launch shapes of the kernels whose best shape depends on the reads:
+ * insert_threads is the CTA size of the 2-bit Insert (256 or 512 threads
+ * per output superblock; 0 = 512 while a quarter or more of the result's
+ * rows are new, else 256); rank_segment is the number of positions one
+ * ComputeRanks thread walks for reads longer than twice it (256, 512 or
+ * 1024; 0 = 256; shorter reads take one thread each).  Results are
+ * identical for every shape.  sbwt_set_tile_shapes sets them (SBWT_EINVAL
+ * for another value or a nonzero reserved field), sbwt_get_tile_shapes
+ * reads them. */
+typedef struct {
+    uint32_t insert_threads;
+    uint32_t rank_segment;
+    uint32_t reserved[2]; /* must be zero */
+} sbwt_tile_shapes;
+int sbwt_set_tile_shapes(sbwt_index *idx, const sbwt_tile_shapes *shapes);
+int sbwt_get_tile_shapes(const sbwt_index *idx, sbwt_tile_shapes *out);
+
+/* Autotunes the tile shapes with the index's current M and sampling: builds
+ * the BWT of the given device reads three times with each candidate (the
+ * fastest of the last two counts), keeps the fastest in the index and copies
+ * it to *best_out (may be NULL); ms_out, if not NULL, gets each candidate's
+ * time (-1: did not fit the HBM budget).  candidates NULL = five shapes:
+ * insert_threads 0, 256 and 512 with rank_segment 256, and rank_segment 512
+ * and 1024.  The index is emptied before and after.  Errors: SBWT_EINVAL,
+ * SBWT_EBUSY, SBWT_ENOMEM (no candidate fits), or a failing append's. */
+int sbwt_autotune_tile_shapes(sbwt_index *idx, const uint8_t *d_reads, const uint64_t *d_offsets, uint64_t m,
+                              const sbwt_tile_shapes *candidates, int ncand, sbwt_tile_shapes *best_out,
+                              double *ms_out);
 
 /* Autotunes M and the occurrence sampling together (Algorithm 1's block
  * size; Section 5's counter spacing): every pair of a block size from

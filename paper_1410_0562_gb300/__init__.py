@@ -42,8 +42,9 @@ EXPORTS = (
     "sbwt_create", "sbwt_create_ex", "sbwt_append", "sbwt_prepend", "sbwt_append_device", "sbwt_get_bwt", "sbwt_rank",
     "sbwt_rank_batch", "sbwt_count", "sbwt_memory", "sbwt_size", "sbwt_reset", "sbwt_destroy", "sbwt_strerror",
     "sbwt_get_stream", "sbwt_set_capture", "sbwt_get_stage", "sbwt_set_profiling", "sbwt_set_profiling_only",
-    "sbwt_get_kernel_stats", "sbwt_reset_kernel_stats", "sbwt_set_graph_replay", "sbwt_host_link",
-    "sbwt_set_block_overlap", "sbwt_autotune_block_suffixes", "sbwt_autotune", "sbwt_serve_start", "sbwt_submit",
+    "sbwt_get_kernel_stats", "sbwt_reset_kernel_stats", "sbwt_set_graph_replay", "sbwt_measure_bandwidth",
+    "sbwt_set_block_overlap", "sbwt_autotune_block_suffixes", "sbwt_set_tile_shapes", "sbwt_get_tile_shapes",
+    "sbwt_autotune_tile_shapes", "sbwt_autotune", "sbwt_serve_start", "sbwt_submit",
     "sbwt_wait", "sbwt_serve_stop", "sbwt_save", "sbwt_load", "sbwt_bwt_noalloc",
 )
 
@@ -113,8 +114,10 @@ def load() -> ctypes.CDLL:
             "sbwt_reset_kernel_stats": ([P], I),
             "sbwt_set_graph_replay": ([P, I], I),
             "sbwt_set_block_overlap": ([P, I], I),
-            "sbwt_host_link": ([P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
-                                ctypes.POINTER(ctypes.c_double)], I),
+            "sbwt_set_tile_shapes": ([P, P], I),
+            "sbwt_get_tile_shapes": ([P, P], I),
+            "sbwt_autotune_tile_shapes": ([P, P, P, U64, P, I, P, P], I),
+            "sbwt_measure_bandwidth": ([P, P], I),
             "sbwt_autotune_block_suffixes": ([P, P, P, U64, P, I, ctypes.POINTER(U64), P], I),
             "sbwt_autotune": ([P, P, P, U64, P, I, P, I, ctypes.POINTER(U64), ctypes.POINTER(ctypes.c_uint32), P],
                               I),
@@ -305,11 +308,48 @@ def sbwt_reset_kernel_stats(h):
     _check(load().sbwt_reset_kernel_stats(h), "sbwt_reset_kernel_stats")
 
 
-def sbwt_host_link(h):
-    """(H2D GB/s, D2H GB/s, random 32-byte host reads GB/s) of the index's device."""
-    a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
-    _check(load().sbwt_host_link(h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), "sbwt_host_link")
-    return a.value, b.value, c.value
+class sbwt_bandwidth(ctypes.Structure):
+    _fields_ = [("h2d_gbs", ctypes.c_double), ("d2h_gbs", ctypes.c_double), ("host_random_gbs", ctypes.c_double),
+                ("hbm_random_gbs", ctypes.c_double)]
+
+
+def sbwt_measure_bandwidth(h) -> dict:
+    """H2D / D2H copy GB/s over the host link and random 32-byte read GB/s
+    from pinned host memory and from HBM, on the index's device."""
+    b = sbwt_bandwidth()
+    _check(load().sbwt_measure_bandwidth(h, ctypes.byref(b)), "sbwt_measure_bandwidth")
+    return {"h2d_GBps": b.h2d_gbs, "d2h_GBps": b.d2h_gbs, "host_random_32B_GBps": b.host_random_gbs,
+            "hbm_random_32B_GBps": b.hbm_random_gbs}
+
+
+class sbwt_tile_shapes(ctypes.Structure):
+    _fields_ = [("insert_threads", ctypes.c_uint32), ("rank_segment", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32 * 2)]
+
+
+def sbwt_set_tile_shapes(h, insert_threads: int = 0, rank_segment: int = 0):
+    _check(load().sbwt_set_tile_shapes(h, ctypes.byref(sbwt_tile_shapes(insert_threads, rank_segment))),
+           "sbwt_set_tile_shapes")
+
+
+def sbwt_get_tile_shapes(h):
+    t = sbwt_tile_shapes()
+    _check(load().sbwt_get_tile_shapes(h, ctypes.byref(t)), "sbwt_get_tile_shapes")
+    return t.insert_threads, t.rank_segment
+
+
+def sbwt_autotune_tile_shapes(h, d_reads: int, d_offsets: int, m: int, candidates=None):
+    """Returns ((insert_threads, rank_segment) kept, {shape: ms}); candidates
+    is a list of (insert_threads, rank_segment) pairs, None for the defaults."""
+    n = len(candidates) if candidates is not None else 0
+    arr = (sbwt_tile_shapes * max(n, 1))(*[sbwt_tile_shapes(a, b) for a, b in (candidates or [])])
+    ms = np.zeros(max(n, 5), dtype=np.float64)
+    best = sbwt_tile_shapes()
+    _check(load().sbwt_autotune_tile_shapes(h, ctypes.c_void_p(d_reads), ctypes.c_void_p(d_offsets), m,
+                                            arr if n else None, n, ctypes.byref(best),
+                                            ctypes.c_void_p(ms.ctypes.data)), "sbwt_autotune_tile_shapes")
+    shapes = candidates if n else [(0, 256), (256, 256), (512, 256), (0, 512), (0, 1024)]
+    return (best.insert_threads, best.rank_segment), {tuple(c): float(t) for c, t in zip(shapes, ms)}
 
 
 def sbwt_set_block_overlap(h, on: bool):

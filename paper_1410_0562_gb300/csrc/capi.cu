@@ -53,6 +53,7 @@ struct sbwt_index {
     Alphabet16 alpha16 = {};  // all symbols (4-bit kernels, read-back)
     int code_bits = 2;       // 2 for up to 4 symbols, 4 for 5 to 16
     int occ_k = 1;           // occurrence sampling of 64 occ_k rows (1, 2 or 4; 1 for 4-bit codes)
+    sbwt_tile_shapes tiles = {};  // launch shapes the autotuner may pick (0 = the built-in choice)
     size_t budget = 0;
     uint32_t index_bits = 0;
     uint64_t M = kDefaultBlock;
@@ -305,7 +306,8 @@ std::vector<Need> buffer_needs(sbwt_index* idx, const Plan& p, bool host_input, 
     v.push_back({&idx->sb_tot, sb_words * 4 + (size_t)(nsb / 256 + 1) * 8 * dict_codes(cb)});
     v.push_back({&idx->ins_plan, (size_t)(nsb + 1) * 4});  // Insert's first new symbol per superblock
     if (in_place) {
-        v.push_back({&idx->stage, insert_stage_bytes(cb, idx->occ_k)});
+        v.push_back({&idx->stage, (size_t)insert_stage_blocks(cb, idx->occ_k, n_final) *
+                                      dict_block_bytes(cb, idx->occ_k)});
         return v;
     }
     for (int k = 0; k < 3; ++k) {
@@ -496,7 +498,7 @@ void run_block(sbwt_index* idx, const BlockPlan& bp, const uint64_t* d_offsets, 
     launch_compute_ranks<IdxT>(L, text, d_offsets, bp.j0, bp.j1 - bp.j0, bp.n_int, bp.max_len, (const void*)src.blocks.p,
                                (const unsigned long long*)src.super.p, (const unsigned long long*)src.C.p, n_ext,
                                prepend ? 0 : m_ext, (IdxT*)idx->g.p, (uint32_t*)idx->err.p, idx->code_bits,
-                               idx->occ_k);
+                               idx->occ_k, idx->tiles.rank_segment ? idx->tiles.rank_segment : 256u);
     cudaStreamWaitEvent(s, idx->ev_sorted[q & 1], 0);
     // the 2-bit Insert takes its plan (first new symbol per superblock) from the gather
     uint32_t* plan = idx->code_bits == 2 ? (uint32_t*)idx->ins_plan.p : nullptr;
@@ -507,7 +509,8 @@ void run_block(sbwt_index* idx, const BlockPlan& bp, const uint64_t* d_offsets, 
                         (const IdxT*)idx->gsa.p, bp.n_int, plan, (void*)dst.blocks.p,
                         (unsigned long long*)dst.super.p, (unsigned long long*)dst.C.p, m_ext + (bp.j1 - bp.j0),
                         (uint32_t*)idx->sb_tot.p, (uint32_t*)idx->err.p, idx->code_bits, idx->occ_k,
-                        in_place ? (unsigned long long*)idx->stage.p : nullptr);
+                        in_place ? (unsigned long long*)idx->stage.p : nullptr,
+                        idx->stage.bytes / dict_block_bytes(idx->code_bits, idx->occ_k), (int)idx->tiles.insert_threads);
 }
 
 Plan host_plan(const uint64_t* h_off, uint64_t m_new, uint64_t M) {
@@ -814,9 +817,9 @@ struct File {
     }
 };
 
-// Host-link bandwidth probe: random 32-byte sector reads from mapped pinned
-// host memory, the access of ComputeRanks and rank queries to a host-tier
-// dictionary.  Each thread reads kLinkReads sectors at hashed offsets.
+// Random 32-byte sector reads (from mapped pinned host memory or from HBM),
+// the access of ComputeRanks and rank queries to a dictionary that is not in
+// L2.  Each thread reads kLinkReads sectors at pseudo-random offsets.
 constexpr int kLinkReads = 64;
 __global__ void __launch_bounds__(256) link_random_read_kernel(const ulonglong2* __restrict__ host, uint64_t sectors,
                                                                unsigned long long* __restrict__ sink) {
@@ -1521,6 +1524,64 @@ int time_build(sbwt_index* idx, const uint8_t* d_reads, const uint64_t* d_offset
 
 extern "C" {
 
+int sbwt_set_tile_shapes(sbwt_index* idx, const sbwt_tile_shapes* shapes) {
+    if (!idx || !shapes) return SBWT_EINVAL;
+    if (busy(idx)) return SBWT_EBUSY;
+    const uint32_t it = shapes->insert_threads, rs = shapes->rank_segment;
+    if ((it != 0 && it != 256 && it != 512) || (rs != 0 && rs != 256 && rs != 512 && rs != 1024)) return SBWT_EINVAL;
+    for (uint32_t r : shapes->reserved)
+        if (r) return SBWT_EINVAL;
+    if (idx->dev_ready && (set_device(idx) || cudaStreamSynchronize(idx->stream) != cudaSuccess)) return SBWT_EDEVICE;
+    idx->tiles = *shapes;
+    return SBWT_OK;
+}
+
+int sbwt_get_tile_shapes(const sbwt_index* idx, sbwt_tile_shapes* out) {
+    if (!idx || !out) return SBWT_EINVAL;
+    *out = idx->tiles;
+    return SBWT_OK;
+}
+
+int sbwt_autotune_tile_shapes(sbwt_index* idx, const uint8_t* d_reads, const uint64_t* d_offsets, uint64_t m,
+                              const sbwt_tile_shapes* candidates, int ncand, sbwt_tile_shapes* best_out,
+                              double* ms_out) {
+    static const sbwt_tile_shapes kDefaults[] = {
+        {0, 256, {0, 0}}, {256, 256, {0, 0}}, {512, 256, {0, 0}}, {0, 512, {0, 0}}, {0, 1024, {0, 0}}};
+    if (!idx || !d_offsets || m == 0) return SBWT_EINVAL;
+    if (busy(idx)) return SBWT_EBUSY;
+    if (!candidates) {
+        candidates = kDefaults;
+        ncand = (int)(sizeof(kDefaults) / sizeof(kDefaults[0]));
+    }
+    if (ncand <= 0) return SBWT_EINVAL;
+    const sbwt_tile_shapes saved = idx->tiles;
+    const bool saved_replay = idx->graph_replay;
+    idx->graph_replay = false;
+    int best = -1;
+    double best_ms = 0;
+    int rc = sbwt_reset(idx);
+    for (int c = 0; c < ncand && rc == SBWT_OK; ++c) {
+        if ((rc = sbwt_set_tile_shapes(idx, &candidates[c])) != SBWT_OK) break;
+        double t = -1;
+        rc = time_build(idx, d_reads, d_offsets, m, &t);
+        if (ms_out) ms_out[c] = t;
+        if (rc == SBWT_OK && t >= 0 && (best < 0 || t < best_ms)) {
+            best = c;
+            best_ms = t;
+        }
+    }
+    idx->graph_replay = saved_replay;
+    const int rr = sbwt_reset(idx);
+    if (rc == SBWT_OK && best < 0) rc = SBWT_ENOMEM;
+    if (rc != SBWT_OK) {
+        idx->tiles = saved;
+        return rc;
+    }
+    idx->tiles = candidates[best];
+    if (best_out) *best_out = candidates[best];
+    return rr;
+}
+
 int sbwt_autotune_block_suffixes(sbwt_index* idx, const uint8_t* d_reads, const uint64_t* d_offsets, uint64_t m,
                                  const uint64_t* candidates, int ncand, uint64_t* best_out, double* ms_out) {
     uint32_t sampling = 64u * (uint32_t)(idx ? idx->occ_k : 1);
@@ -1586,14 +1647,14 @@ int sbwt_autotune(sbwt_index* idx, const uint8_t* d_reads, const uint64_t* d_off
     return rr;
 }
 
-int sbwt_host_link(sbwt_index* idx, double* h2d_gbs, double* d2h_gbs, double* random_read_gbs) {
-    if (!idx) return SBWT_EINVAL;
+int sbwt_measure_bandwidth(sbwt_index* idx, sbwt_bandwidth* out) {
+    if (!idx || !out) return SBWT_EINVAL;
     if (busy(idx)) return SBWT_EBUSY;
     if (int rc = device_init(idx)) return rc;
-    constexpr size_t kBytes = 256ull << 20;
+    constexpr size_t kBytes = 256ull << 20, kHbmRandom = 1ull << 30;  // the HBM buffer is far beyond L2
     void *h = nullptr, *d = nullptr;
     if (cudaHostAlloc(&h, kBytes, cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess ||
-        cudaMalloc(&d, kBytes) != cudaSuccess) {
+        cudaMalloc(&d, kHbmRandom) != cudaSuccess) {
         cudaGetLastError();
         if (h) cudaFreeHost(h);
         return SBWT_ENOMEM;
@@ -1618,10 +1679,14 @@ int sbwt_host_link(sbwt_index* idx, double* h2d_gbs, double* d2h_gbs, double* ra
     };
     const double t_h2d = best_of([&] { cudaMemcpyAsync(d, h, kBytes, cudaMemcpyHostToDevice, s); });
     const double t_d2h = best_of([&] { cudaMemcpyAsync(h, d, kBytes, cudaMemcpyDeviceToHost, s); });
+    cudaMemsetAsync(d, 1, kHbmRandom, s);
     const unsigned grid = persistent_ctas((const void*)link_random_read_kernel, 256, 0);
-    const double t_rnd = best_of([&] {
-        link_random_read_kernel<<<grid, 256, 0, s>>>(static_cast<const ulonglong2*>(h), kBytes / 32,
-                                                     static_cast<unsigned long long*>(d));
+    unsigned long long* sink = static_cast<unsigned long long*>(d);
+    const double t_host = best_of([&] {
+        link_random_read_kernel<<<grid, 256, 0, s>>>(static_cast<const ulonglong2*>(h), kBytes / 32, sink);
+    });
+    const double t_hbm = best_of([&] {
+        link_random_read_kernel<<<grid, 256, 0, s>>>(static_cast<const ulonglong2*>(d), kHbmRandom / 32, sink);
     });
     const bool ok = cudaGetLastError() == cudaSuccess && cudaStreamSynchronize(s) == cudaSuccess;
     cudaEventDestroy(a);
@@ -1629,9 +1694,11 @@ int sbwt_host_link(sbwt_index* idx, double* h2d_gbs, double* d2h_gbs, double* ra
     cudaFree(d);
     cudaFreeHost(h);
     if (!ok) return SBWT_EDEVICE;
-    if (h2d_gbs) *h2d_gbs = kBytes / (t_h2d * 1e6);
-    if (d2h_gbs) *d2h_gbs = kBytes / (t_d2h * 1e6);
-    if (random_read_gbs) *random_read_gbs = (double)grid * 256 * kLinkReads * 32 / (t_rnd * 1e6);
+    const double random_bytes = (double)grid * 256 * kLinkReads * 32;
+    out->h2d_gbs = kBytes / (t_h2d * 1e6);
+    out->d2h_gbs = kBytes / (t_d2h * 1e6);
+    out->host_random_gbs = random_bytes / (t_host * 1e6);
+    out->hbm_random_gbs = random_bytes / (t_hbm * 1e6);
     return SBWT_OK;
 }
 

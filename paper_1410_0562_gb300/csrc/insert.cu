@@ -19,6 +19,8 @@
 // superblocks) then scans the superblock totals into the 64-bit superblock
 // counters and C[] (Lemma 1's C[c] counts every smaller symbol, the
 // terminators included).
+#include <algorithm>
+
 #include "sbwt_kernels.cuh"
 
 namespace sbwt {
@@ -770,20 +772,18 @@ void super_scan(Launcher& L, const uint32_t* sb_tot, uint64_t nsb, unsigned long
 
 }  // namespace
 
-uint64_t insert_stage_blocks(int occ_k) {
-    return (uint64_t)kStageSupers * kBlocksPerSuper / occ_k + 8;
-}
-
-size_t insert_stage_bytes(int code_bits, int occ_k) {
-    return code_bits == 4 ? (size_t)(kStageBlocksW + 8) * sizeof(OccBlockW)
-                          : (size_t)insert_stage_blocks(occ_k) * 8 * (3 * occ_k + 1);
+// Old blocks a chunk can read: the chunk's rows in blocks plus a few; a
+// dictionary smaller than a chunk needs only its own blocks.
+uint64_t insert_stage_blocks(int code_bits, int occ_k, uint64_t n_final) {
+    const uint64_t chunk = code_bits == 4 ? kStageBlocksW : (uint64_t)kStageSupers * kBlocksPerSuper / occ_k;
+    return std::min<uint64_t>(chunk, dict_blocks(n_final, occ_k)) + 8;
 }
 
 template <class IdxT>
 void launch_insert(Launcher& L, const void* old_blocks, uint64_t n_ext, const uint8_t* bint, const IdxT* gsa,
                    uint64_t n_int, const uint32_t* ins_i0, void* new_blocks, unsigned long long* new_super,
                    unsigned long long* new_C, uint64_t m_new, uint32_t* sb_tot, uint32_t* d_err, int code_bits,
-                   int occ_k, unsigned long long* stage) {
+                   int occ_k, unsigned long long* stage, uint64_t stage_blocks, int insert_threads) {
     const uint64_t n_new = n_ext + n_int;
     // the superblock scan's per-chunk totals live after the superblock totals
     const uint64_t nsb_all = dict_supers_of(n_new, code_bits);
@@ -802,7 +802,6 @@ void launch_insert(Launcher& L, const void* old_blocks, uint64_t n_ext, const ui
         } else {
             // in place, from the top down in chunks of kStageBlocksW output
             // blocks (a multiple of the CTA's blocks), as for 2-bit codes
-            const uint64_t stage_blocks = kStageBlocksW + 8;
             const uint64_t top = (nb_all + kThreads - 1) / kThreads * kThreads;
             for (uint64_t b1 = top; b1 > 0;) {
                 const uint64_t b0 = b1 > kStageBlocksW ? b1 - kStageBlocksW : 0;
@@ -827,7 +826,7 @@ void launch_insert(Launcher& L, const void* old_blocks, uint64_t n_ext, const ui
     // runs of new symbols spread over more threads.  Sparse: 256 threads of
     // four parts each, so more CTAs (superblocks) are resident per SM and
     // their load latencies overlap.
-    const bool dense = 4 * n_int >= n_new;
+    const bool dense = insert_threads ? insert_threads == kInsertThreads : 4 * n_int >= n_new;
     const int threads = dense ? kInsertThreads : kInsertThreadsSparse;
     auto* const kern = dense ? (occ_k == 4 ? insert_kernel<IdxT, kInsertThreads, 4>
                                            : (occ_k == 2 ? insert_kernel<IdxT, kInsertThreads, 2>
@@ -849,7 +848,6 @@ void launch_insert(Launcher& L, const void* old_blocks, uint64_t n_ext, const ui
         // blocks it reads to the staging buffer.  A chunk's old rows all lie
         // below its first output row (new rows only push old rows up), so
         // the chunks above it never overwrite them before they are staged.
-        const uint64_t stage_blocks = insert_stage_blocks(occ_k);
         auto* const stage_kern = occ_k == 4 ? stage_old_kernel<4> : (occ_k == 2 ? stage_old_kernel<2>
                                                                                  : stage_old_kernel<1>);
         for (uint64_t s1 = nsb; s1 > 0;) {
@@ -871,10 +869,10 @@ void launch_insert(Launcher& L, const void* old_blocks, uint64_t n_ext, const ui
 
 template void launch_insert<uint32_t>(Launcher&, const void*, uint64_t, const uint8_t*, const uint32_t*, uint64_t,
                                       const uint32_t*, void*, unsigned long long*, unsigned long long*, uint64_t,
-                                      uint32_t*, uint32_t*, int, int, unsigned long long*);
+                                      uint32_t*, uint32_t*, int, int, unsigned long long*, uint64_t, int);
 template void launch_insert<unsigned long long>(Launcher&, const void*, uint64_t, const uint8_t*,
                                                 const unsigned long long*, uint64_t, const uint32_t*, void*,
                                                 unsigned long long*, unsigned long long*, uint64_t, uint32_t*,
-                                                uint32_t*, int, int, unsigned long long*);
+                                                uint32_t*, int, int, unsigned long long*, uint64_t, int);
 
 }  // namespace sbwt

@@ -139,10 +139,11 @@ __global__ void __launch_bounds__(kThreads) compute_ranks_kernel(const uint32_t*
         if (r < held) g[rs + r] = s[r];
 }
 
-// ComputeRanks for long reads, one thread per segment of kSegRows positions
-// of a read, so a block of few long reads still runs many LF chains at once.
-// Segment q of read j covers positions [a, b) = [q kSegRows, min((q+1)
-// kSegRows, len + 1)), the terminator at len.  The last segment starts, as
+// ComputeRanks for long reads, one thread per segment of seg_rows positions
+// of a read (256 unless the tile shapes say otherwise), so a block of few
+// long reads still runs many LF chains at once.  Segment q of read j covers
+// positions [a, b) = [q seg_rows, min((q+1) seg_rows, len + 1)), the
+// terminator at len.  The last segment starts, as
 // Algorithm 2 does, from the terminator's rank start.  Any other segment first
 // needs g at b exactly: backward search (Lemma 1 applied to the interval of
 // old suffixes that start with P[b .. e)) over the L symbols from b on; once
@@ -150,9 +151,8 @@ __global__ void __launch_bounds__(kThreads) compute_ranks_kernel(const uint32_t*
 // smaller than P[b ..] whatever follows e, which is g[b] (with L doubled while
 // the L-mer still occurs in B_ext, and the exact chain from the terminator
 // once e would pass the read's end).  From g[b] it steps down to a with
-// Lemma 1, like the per-read kernel.  Reads of up to 2 kSegRows symbols take
+// Lemma 1, like the per-read kernel.  Reads of up to 2 seg_rows symbols take
 // the per-read kernel.
-constexpr uint32_t kSegRows = 256;
 constexpr uint32_t kProbe0 = 32;  // first backward-search window
 
 template <class IdxT, bool kStage, int kB, int K>
@@ -160,6 +160,7 @@ __global__ void __launch_bounds__(kThreads) compute_ranks_seg_kernel(const uint3
                                                                      const unsigned long long* __restrict__ offsets,
                                                                      unsigned long long j_begin,
                                                                      unsigned long long nreads, uint32_t segs,
+                                                                     uint32_t seg_rows,
                                                                      const typename DictLayout<kB, K>::Block* blocks,
                                                                      const unsigned long long* __restrict__ super,
                                                                      const unsigned long long* __restrict__ d_C,
@@ -185,9 +186,9 @@ __global__ void __launch_bounds__(kThreads) compute_ranks_seg_kernel(const uint3
     const uint64_t o0 = offsets[j_begin];
     const uint64_t oj = offsets[jj];
     const I len = (I)(offsets[jj + 1] - oj);
-    const I a = (I)q * kSegRows;
+    const I a = (I)q * seg_rows;
     if (a > len) return;  // this read has fewer segments
-    const I b = min((I)(a + kSegRows), (I)(len + 1));
+    const I b = min((I)(a + seg_rows), (I)(len + 1));
     const I rs = (I)(oj - o0 + j);  // block-local position of the read's first symbol
     const I P = (I)(oj + jj);       // the same position in the append's text
     const I nx = (I)n_ext;
@@ -421,7 +422,7 @@ uint32_t alpha4_of(const Alphabet16& alpha) {
 
 template <class IdxT, int kB, int K>
 void compute_ranks_launch(Launcher& L, const uint32_t* text, const uint64_t* d_offsets, uint64_t j_begin,
-                          uint64_t nreads, uint64_t max_len, double bytes, const void* blocks,
+                          uint64_t nreads, uint64_t max_len, uint32_t seg_rows, double bytes, const void* blocks,
                           const unsigned long long* super, const unsigned long long* d_C, uint64_t n_ext,
                           uint64_t m_ext, IdxT* g, uint32_t* d_err) {
     using D = DictLayout<kB, K>;
@@ -429,13 +430,13 @@ void compute_ranks_launch(Launcher& L, const uint32_t* text, const uint64_t* d_o
     const size_t stage = ((n_ext >> D::kSuperShift) + 1) * D::kCodes * sizeof(IdxT);
     const bool staged = stage <= kSuperStageBytes;
     const auto* offs = reinterpret_cast<const unsigned long long*>(d_offsets);
-    if (max_len > 2 * kSegRows) {  // long reads: one thread per segment
-        const uint32_t segs = (uint32_t)(max_len / kSegRows + 1);
+    if (max_len > 2ull * seg_rows) {  // long reads: one thread per segment
+        const uint32_t segs = (uint32_t)(max_len / seg_rows + 1);
         auto* const kern = staged ? compute_ranks_seg_kernel<IdxT, true, kB, K>
                                   : compute_ranks_seg_kernel<IdxT, false, kB, K>;
         SBWT_LAUNCH(L, "compute_ranks", bytes, 0, nullptr, kern, ceil_div_u(nreads * segs, kThreads), kThreads,
                     staged ? stage : 0, text, offs, (unsigned long long)j_begin, (unsigned long long)nreads, segs,
-                    static_cast<const Block*>(blocks), super, d_C, (unsigned long long)n_ext,
+                    seg_rows, static_cast<const Block*>(blocks), super, d_C, (unsigned long long)n_ext,
                     (unsigned long long)m_ext, g, d_err);
         return;
     }
@@ -467,22 +468,22 @@ template <class IdxT>
 void launch_compute_ranks(Launcher& L, const uint32_t* text, const uint64_t* d_offsets, uint64_t j_begin,
                           uint64_t nreads, uint64_t n_int, uint64_t max_len, const void* blocks,
                           const unsigned long long* super, const unsigned long long* d_C, uint64_t n_ext,
-                          uint64_t m_ext, IdxT* g, uint32_t* d_err, int code_bits, int occ_k) {
+                          uint64_t m_ext, IdxT* g, uint32_t* d_err, int code_bits, int occ_k, uint32_t seg_rows) {
     if (nreads == 0) return;
     // per suffix: one rank query's sectors, a g write, the text codes
     const double bytes = (double)(n_int - nreads) * rank_query_bytes(code_bits, occ_k) +
                          (double)n_int * sizeof(IdxT) + n_int * code_bits / 8.0 + 16.0 * nreads;
     if (code_bits == 4) {
-        compute_ranks_launch<IdxT, 4, 1>(L, text, d_offsets, j_begin, nreads, max_len, bytes, blocks, super, d_C,
+        compute_ranks_launch<IdxT, 4, 1>(L, text, d_offsets, j_begin, nreads, max_len, seg_rows, bytes, blocks, super, d_C,
                                          n_ext, m_ext, g, d_err);
     } else if (occ_k == 4) {
-        compute_ranks_launch<IdxT, 2, 4>(L, text, d_offsets, j_begin, nreads, max_len, bytes, blocks, super, d_C,
+        compute_ranks_launch<IdxT, 2, 4>(L, text, d_offsets, j_begin, nreads, max_len, seg_rows, bytes, blocks, super, d_C,
                                          n_ext, m_ext, g, d_err);
     } else if (occ_k == 2) {
-        compute_ranks_launch<IdxT, 2, 2>(L, text, d_offsets, j_begin, nreads, max_len, bytes, blocks, super, d_C,
+        compute_ranks_launch<IdxT, 2, 2>(L, text, d_offsets, j_begin, nreads, max_len, seg_rows, bytes, blocks, super, d_C,
                                          n_ext, m_ext, g, d_err);
     } else {
-        compute_ranks_launch<IdxT, 2, 1>(L, text, d_offsets, j_begin, nreads, max_len, bytes, blocks, super, d_C,
+        compute_ranks_launch<IdxT, 2, 1>(L, text, d_offsets, j_begin, nreads, max_len, seg_rows, bytes, blocks, super, d_C,
                                          n_ext, m_ext, g, d_err);
     }
 }
@@ -580,11 +581,11 @@ void launch_unpack(Launcher& L, const void* blocks, uint64_t r0, uint64_t r1, co
 template void launch_compute_ranks<uint32_t>(Launcher&, const uint32_t*, const uint64_t*, uint64_t, uint64_t,
                                              uint64_t, uint64_t, const void*, const unsigned long long*,
                                              const unsigned long long*, uint64_t, uint64_t, uint32_t*, uint32_t*, int,
-                                             int);
+                                             int, uint32_t);
 template void launch_compute_ranks<unsigned long long>(Launcher&, const uint32_t*, const uint64_t*, uint64_t,
                                                        uint64_t, uint64_t, uint64_t, const void*,
                                                        const unsigned long long*, const unsigned long long*, uint64_t,
-                                                       uint64_t, unsigned long long*, uint32_t*, int, int);
+                                                       uint64_t, unsigned long long*, uint32_t*, int, int, uint32_t);
 template void launch_bint_gather<uint32_t>(Launcher&, const uint32_t*, const uint32_t*, uint64_t, const uint32_t*,
                                            const uint32_t*, uint32_t, uint8_t*, uint32_t*, int, uint32_t*, uint64_t,
                                            int);

@@ -57,14 +57,14 @@ void launch_bint(Launcher& L, const uint32_t* text, const uint32_t* term, uint64
 // bit-plane dictionary of sampling 64 occ_k rows for code_bits == 2 (occ_k
 // 1, 2 or 4), an OccBlockW array for code_bits == 4 (occ_k 1); g starts on a
 // 16-byte boundary.
-// max_len bounds the block's read lengths: reads longer than 512 symbols are
-// ranked in segments of 256 positions, each started exactly by a backward
-// search (see ranks.cu).
+// max_len bounds the block's read lengths: reads longer than 2 seg_rows
+// symbols are ranked in segments of seg_rows positions, each started exactly
+// by a backward search (see ranks.cu).
 template <class IdxT>
 void launch_compute_ranks(Launcher& L, const uint32_t* text, const uint64_t* d_offsets, uint64_t j_begin,
                           uint64_t nreads, uint64_t n_int, uint64_t max_len, const void* blocks,
                           const unsigned long long* super, const unsigned long long* d_C, uint64_t n_ext,
-                          uint64_t m_ext, IdxT* g, uint32_t* d_err, int code_bits, int occ_k);
+                          uint64_t m_ext, IdxT* g, uint32_t* d_err, int code_bits, int occ_k, uint32_t seg_rows = 256);
 // B_int and g_sa fused: one pass over SA_int after ComputeRanks.  With
 // ins_i0 non-null it also writes Insert's plan (nsb + 1 entries: the first
 // new symbol of each superblock of 2^super_shift rows of the next dictionary).
@@ -93,17 +93,19 @@ void launch_unpack(Launcher& L, const void* blocks, uint64_t r0, uint64_t r1, co
 // superblock, rounded up to 4 words, then 4 (16) 64-bit words per 256
 // superblocks.  ins_i0 is the plan bint_gather wrote (2-bit dictionary;
 // unused for 4-bit codes); an inconsistent plan sets *d_err bit 10.
-// With `stage` (2-bit dictionary only), new_blocks is old_blocks: the
-// dictionary is rewritten in place, from the top superblock down in chunks,
-// each chunk's old blocks first copied to `stage` (insert_stage_blocks(occ_k)
-// blocks, in HBM).
+// With `stage`, new_blocks is old_blocks: the dictionary is rewritten in
+// place, from the top superblock down in chunks, each chunk's old blocks
+// first copied to `stage` (stage_blocks dictionary blocks, in HBM, at least
+// insert_stage_blocks(code_bits, occ_k, n_new)).  insert_threads: 256 or
+// 512 threads per CTA of the 2-bit Insert, 0 = 512 while a quarter or more
+// of the result's rows are new, else 256.
 template <class IdxT>
 void launch_insert(Launcher& L, const void* old_blocks, uint64_t n_ext, const uint8_t* bint, const IdxT* gsa,
                    uint64_t n_int, const uint32_t* ins_i0, void* new_blocks, unsigned long long* new_super,
                    unsigned long long* new_C, uint64_t m_new, uint32_t* sb_tot, uint32_t* d_err, int code_bits,
-                   int occ_k, unsigned long long* stage = nullptr);
-uint64_t insert_stage_blocks(int occ_k);
-size_t insert_stage_bytes(int code_bits, int occ_k);  // the staging buffer an in-place Insert needs
+                   int occ_k, unsigned long long* stage = nullptr, uint64_t stage_blocks = 0,
+                   int insert_threads = 0);
+uint64_t insert_stage_blocks(int code_bits, int occ_k, uint64_t n_final);
 
 // plan.cu: checks device-resident offsets (offsets[0] = 0, non-decreasing,
 // every read shorter than max_block suffixes; summary->bad != 0 otherwise),

@@ -15,12 +15,12 @@ namespace sbwt {
 using namespace sbwt;
 
 // One block's ComputeRanks: the per-read kernel (seg = 0) or the segmented
-// one (seg = 1, `segs` segments per read) over the 2-bit dictionary of
+// one (seg = 1, `segs` segments of seg_rows positions per read) over the 2-bit dictionary of
 // sampling 64 k rows (n_ext rows, as 64-bit words), its superblock counters
 // and C[]; text, offsets as in an append of the block's reads alone;
 // writes g (32-bit).
 template <int K>
-static void run_k(int seg, uint32_t segs, const uint32_t* text, uint64_t text_words, const unsigned long long* offsets,
+static void run_k(int seg, uint32_t segs, uint32_t seg_rows, const uint32_t* text, uint64_t text_words, const unsigned long long* offsets,
                   unsigned long long nreads, const unsigned long long* words, const unsigned long long* super,
                   const unsigned long long* C, unsigned long long n_ext, unsigned long long m_start, uint32_t* g,
                   uint64_t n_int, uint32_t* d_err) {
@@ -35,8 +35,8 @@ static void run_k(int seg, uint32_t segs, const uint32_t* text, uint64_t text_wo
     const uint64_t threads = seg ? nreads * segs : nreads;
     run_grid((unsigned)((threads + kThreads - 1) / kThreads), kThreads, [&] {
         if (seg)
-            compute_ranks_seg_kernel<uint32_t, true, 2, K>(g_text, g_off, 0, nreads, segs, g_words, g_super, g_C, n_ext,
-                                                           m_start, g_g, d_err);
+            compute_ranks_seg_kernel<uint32_t, true, 2, K>(g_text, g_off, 0, nreads, segs, seg_rows, g_words, g_super,
+                                                           g_C, n_ext, m_start, g_g, d_err);
         else
             compute_ranks_kernel<uint32_t, true, 2, K>(g_text, g_off, 0, nreads, g_words, g_super, g_C, n_ext, m_start,
                                                        g_g, d_err);
@@ -45,16 +45,16 @@ static void run_k(int seg, uint32_t segs, const uint32_t* text, uint64_t text_wo
     for (auto& m : maps) munmap(m.first, m.second);
 }
 
-extern "C" int emu_compute_ranks(int k, int seg, uint32_t segs, const uint32_t* text, uint64_t text_words,
+extern "C" int emu_compute_ranks(int k, int seg, uint32_t segs, uint32_t seg_rows, const uint32_t* text, uint64_t text_words,
                                  const unsigned long long* offsets, unsigned long long nreads,
                                  const unsigned long long* words, const unsigned long long* super,
                                  const unsigned long long* C, unsigned long long n_ext, unsigned long long m_start,
                                  uint32_t* g, uint64_t n_int, uint32_t* d_err) {
     if (k == 4)
-        run_k<4>(seg, segs, text, text_words, offsets, nreads, words, super, C, n_ext, m_start, g, n_int, d_err);
+        run_k<4>(seg, segs, seg_rows, text, text_words, offsets, nreads, words, super, C, n_ext, m_start, g, n_int, d_err);
     else if (k == 2)
-        run_k<2>(seg, segs, text, text_words, offsets, nreads, words, super, C, n_ext, m_start, g, n_int, d_err);
+        run_k<2>(seg, segs, seg_rows, text, text_words, offsets, nreads, words, super, C, n_ext, m_start, g, n_int, d_err);
     else
-        run_k<1>(seg, segs, text, text_words, offsets, nreads, words, super, C, n_ext, m_start, g, n_int, d_err);
+        run_k<1>(seg, segs, seg_rows, text, text_words, offsets, nreads, words, super, C, n_ext, m_start, g, n_int, d_err);
     return 0;
 }

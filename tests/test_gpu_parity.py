@@ -374,21 +374,29 @@ def test_host_tier_forced(sampling):
     assert 8.0 * sb.sbwt_memory(h.handle)[1] / n <= 6.0
 
 
-def test_host_link_probe():
-    h2d, d2h, rnd = sb.sbwt_host_link(sb.SetBWT(b"ACGT").handle)
-    assert h2d > 1 and d2h > 1 and rnd > 0.1
+def test_bandwidth_probe():
+    idx = sb.SetBWT(b"ACGT")  # kept alive for the call
+    bw = sb.sbwt_measure_bandwidth(idx.handle)
+    idx.close()
+    assert bw["h2d_GBps"] > 1 and bw["d2h_GBps"] > 1
+    assert 0.1 < bw["host_random_32B_GBps"] < bw["hbm_random_32B_GBps"]
 
 
 def test_host_tier_under_budget():
-    """A budget that holds the working set but not the dictionaries moves
-    them to the host tier instead of failing; B is unchanged."""
+    """A budget between what the index needs with its dictionaries in HBM
+    and what it needs in the host tier moves them to the host tier instead
+    of failing; B is unchanged.  With the host tier forbidden the same
+    budget is SBWT_ENOMEM."""
     w = readgen.tiny()
     expect = oracle.bwt(w.reads, w.offsets)
     probe = sb.SetBWT(b"ACGT", host_tier=3)
     probe.append(w.reads, w.offsets)
-    ws_hbm, dict_host = sb.sbwt_memory(probe.handle)
-    assert dict_host > 0
-    budget = ws_hbm + 64 * 1024  # less than the three dictionaries need
+    hbm_tiered, host_tiered = sb.sbwt_memory(probe.handle)
+    full = sb.SetBWT(b"ACGT")
+    full.append(w.reads, w.offsets)
+    hbm_full, host_full = sb.sbwt_memory(full.handle)
+    assert host_tiered > 0 and host_full == 0 and hbm_tiered < hbm_full
+    budget = (hbm_tiered + hbm_full) // 2
     idx = sb.SetBWT(b"ACGT", hbm_budget=budget)
     idx.append(w.reads, w.offsets)
     assert np.array_equal(idx.bwt(), expect)
@@ -498,3 +506,28 @@ def test_block_overlap_off_gives_the_same_b():
         sb.sbwt_set_block_overlap(idx.handle, overlap)
         idx.append(w.reads, w.offsets)
         assert np.array_equal(idx.bwt(), expect)
+
+
+def test_tile_shapes_give_the_same_b():
+    """Every Insert CTA size and ComputeRanks segment length gives the
+    oracle's B (long reads take the segmented kernel), and the shape
+    autotuner keeps one of its candidates."""
+    import torch
+    rng = np.random.default_rng(41)
+    g_ = readgen.genome(200_000, seed=41)
+    lens = rng.integers(300, 4000, size=120)
+    reads, off = readgen.sampled_reads(g_, 120, lens, 0.05, seed=42)
+    expect = oracle.bwt(reads, off)
+    for shape in ((0, 256), (256, 256), (512, 256), (0, 512), (512, 1024)):
+        idx = sb.SetBWT(b"ACGT", block_suffixes=60_000)
+        sb.sbwt_set_tile_shapes(idx.handle, *shape)
+        assert sb.sbwt_get_tile_shapes(idx.handle) == shape
+        idx.append(reads[: int(off[40])], off[:41])
+        idx.append(reads[int(off[40]):], off[40:] - off[40])
+        assert np.array_equal(idx.bwt(), expect), shape
+    with pytest.raises(sb.SbwtError):
+        sb.sbwt_set_tile_shapes(idx.handle, 384, 256)
+    d_reads = torch.from_numpy(reads).cuda()
+    d_off = torch.from_numpy(off.astype(np.int64)).cuda()
+    best, times = sb.sbwt_autotune_tile_shapes(idx.handle, d_reads.data_ptr(), d_off.data_ptr(), len(off) - 1)
+    assert best in times and times[best] == min(times.values())

@@ -52,7 +52,7 @@ def emu(tmp_path_factory):
                            EMU])
     L = ctypes.CDLL(str(lib))
     P, U64, U32, I = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int
-    L.emu_compute_ranks.argtypes = [I, I, U32, P, U64, P, U64, P, P, P, U64, U64, P, U64, P]
+    L.emu_compute_ranks.argtypes = [I, I, U32, U32, P, U64, P, U64, P, P, P, U64, U64, P, U64, P]
     L.emu_compute_ranks.restype = I
     return L
 
@@ -90,7 +90,7 @@ def append_text(reads: np.ndarray, off: np.ndarray) -> np.ndarray:
     return np.concatenate([words, np.zeros(4, np.uint32)])
 
 
-def run(emu, old_reads, old_off, new_reads, new_off, k=1, seg=False):
+def run(emu, old_reads, old_off, new_reads, new_off, k=1, seg=False, seg_rows=SEG_ROWS):
     B = oracle.bwt(old_reads, old_off)
     m_ext = len(old_off) - 1
     words, sup, C = dictionary(B, m_ext, k)
@@ -98,12 +98,12 @@ def run(emu, old_reads, old_off, new_reads, new_off, k=1, seg=False):
     nreads = len(new_off) - 1
     n_int = int(new_off[-1]) + nreads
     max_len = int(np.diff(new_off.astype(np.int64)).max())
-    segs = max_len // SEG_ROWS + 1
+    segs = max_len // seg_rows + 1
     g = np.zeros(max(n_int, 1), np.uint32)
     err = ctypes.c_uint32(0)
     ptr = lambda a: ctypes.c_void_p(a.ctypes.data)  # noqa: E731
     off = np.ascontiguousarray(new_off, np.uint64)
-    assert emu.emu_compute_ranks(k, int(seg), segs, ptr(text), len(text), ptr(off), nreads, ptr(words), ptr(sup),
+    assert emu.emu_compute_ranks(k, int(seg), segs, seg_rows, ptr(text), len(text), ptr(off), nreads, ptr(words), ptr(sup),
                                  ptr(C), len(B), m_ext, ptr(g), n_int, ctypes.byref(err)) == 0
     return g[:n_int], err.value
 
@@ -125,9 +125,9 @@ def test_per_read_kernel_matches_direct_counts(emu, k):
     assert np.array_equal(g, expected_g(old, new))
 
 
-@pytest.mark.parametrize("k", [1, 4])
+@pytest.mark.parametrize("k,seg_rows", [(1, 256), (4, 256), (1, 1024)])
 @pytest.mark.parametrize("repeat", [True, False])
-def test_segmented_kernel_matches_direct_counts(emu, k, repeat):
+def test_segmented_kernel_matches_direct_counts(emu, k, seg_rows, repeat):
     """Long reads (513 to 3000 symbols) sampled from a genome: a 300-symbol
     unit repeated twelve times makes the backward-search windows occur in
     B_ext, so segments widen their window, up to the terminator's exact
@@ -138,7 +138,7 @@ def test_segmented_kernel_matches_direct_counts(emu, k, repeat):
     lens = np.random.default_rng(2).integers(600, 3000, size=12)
     lens[0] = 513  # just over the per-read limit: two segments and a partial third
     new = readgen.sampled_reads(g_, 12, lens, 0.01, seed=34)
-    g, err = run(emu, *old, *new, k=k, seg=True)
+    g, err = run(emu, *old, *new, k=k, seg=True, seg_rows=seg_rows)
     assert err == 0
     assert np.array_equal(g, expected_g(old, new))
     # the per-read kernel agrees on the same block
