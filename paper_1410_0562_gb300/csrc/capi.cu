@@ -208,11 +208,18 @@ int device_init(sbwt_index* idx) {
         idx->own_stream = true;
     }
     idx->L.stream = idx->stream;
-    if (cudaStreamCreateWithFlags(&idx->side, cudaStreamNonBlocking) != cudaSuccess) return SBWT_EDEVICE;
+    // The block sorts run ahead on the side stream and bound the pipeline
+    // (each is longer than the ranking, gather and Insert of a block): its
+    // CTAs go first whenever both streams have work waiting.
+    int prio_low = 0, prio_high = 0;
+    cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high);
+    if (cudaStreamCreateWithPriority(&idx->side, cudaStreamNonBlocking, prio_high) != cudaSuccess)
+        return SBWT_EDEVICE;
     for (cudaEvent_t* e : {&idx->ev_fork, &idx->ev_join, &idx->ev_sorted[0], &idx->ev_sorted[1],
                            &idx->ev_consumed[0], &idx->ev_consumed[1]})
         if (cudaEventCreateWithFlags(e, cudaEventDisableTiming) != cudaSuccess) return SBWT_EDEVICE;
     suffix_sort_init();
+    insert_init();
     if (cudaMallocHost(&idx->h_err, sizeof(uint32_t)) != cudaSuccess) return SBWT_EDEVICE;
     if (cudaMallocHost(&idx->h_plan, kPlanCap * sizeof(PlanBlock)) != cudaSuccess) return SBWT_EDEVICE;
     if (cudaMallocHost(&idx->h_summary, sizeof(PlanSummary)) != cudaSuccess) return SBWT_EDEVICE;
@@ -708,7 +715,9 @@ int append_impl(sbwt_index* idx, const uint8_t* d_reads, const uint64_t* d_offse
             }
         }
         if (it == idx->graphs.end()) {
-            e = cudaGraphInstantiate(&g.exec, graph, 0);
+            // the kernels keep the priority of the stream they were captured
+            // on (the block sorts first)
+            e = cudaGraphInstantiate(&g.exec, graph, cudaGraphInstantiateFlagUseNodePriority);
             if (e != cudaSuccess) {
                 cudaGraphDestroy(graph);
                 L.recycle(g.log);
@@ -819,17 +828,31 @@ struct File {
 
 // Random 32-byte sector reads (from mapped pinned host memory or from HBM),
 // the access of ComputeRanks and rank queries to a dictionary that is not in
-// L2.  Each thread reads kLinkReads sectors at pseudo-random offsets.
+// L2.  Each thread reads kLinkReads sectors at pseudo-random offsets;
+// `sectors` is a power of two.
 constexpr int kLinkReads = 64;
+constexpr int kLinkBatch = 8;
 __global__ void __launch_bounds__(256) link_random_read_kernel(const ulonglong2* __restrict__ host, uint64_t sectors,
                                                                unsigned long long* __restrict__ sink) {
     uint64_t x = (uint64_t)blockIdx.x * 256 + threadIdx.x + 1;
     unsigned long long acc = 0;
-    for (int r = 0; r < kLinkReads; ++r) {
-        x = x * 6364136223846793005ull + 1442695040888963407ull;  // LCG step (Knuth's MMIX constants)
-        const uint64_t sct = (x >> 17) % sectors;
-        const ulonglong2 a = host[2 * sct], b = host[2 * sct + 1];
-        acc += a.x ^ a.y ^ b.x ^ b.y;
+    // kLinkBatch independent sectors in flight per thread: all addresses,
+    // then all loads, then the sums
+    for (int r = 0; r < kLinkReads; r += kLinkBatch) {
+        uint64_t sct[kLinkBatch];
+#pragma unroll
+        for (int u = 0; u < kLinkBatch; ++u) {
+            x = x * 6364136223846793005ull + 1442695040888963407ull;  // LCG step (Knuth's MMIX constants)
+            sct[u] = (x >> 17) & (sectors - 1);
+        }
+        ulonglong2 a[kLinkBatch], b[kLinkBatch];
+#pragma unroll
+        for (int u = 0; u < kLinkBatch; ++u) {
+            a[u] = host[2 * sct[u]];
+            b[u] = host[2 * sct[u] + 1];
+        }
+#pragma unroll
+        for (int u = 0; u < kLinkBatch; ++u) acc += a[u].x ^ a[u].y ^ b[u].x ^ b[u].y;
     }
     if (acc == 0x5bd1e995ull) sink[0] = acc;  // keeps the loads
 }
@@ -1652,6 +1675,7 @@ int sbwt_measure_bandwidth(sbwt_index* idx, sbwt_bandwidth* out) {
     if (busy(idx)) return SBWT_EBUSY;
     if (int rc = device_init(idx)) return rc;
     constexpr size_t kBytes = 256ull << 20, kHbmRandom = 1ull << 30;  // the HBM buffer is far beyond L2
+    static_assert((kBytes & (kBytes - 1)) == 0 && (kHbmRandom & (kHbmRandom - 1)) == 0, "sector counts of 2^k");
     void *h = nullptr, *d = nullptr;
     if (cudaHostAlloc(&h, kBytes, cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess ||
         cudaMalloc(&d, kHbmRandom) != cudaSuccess) {

@@ -100,6 +100,24 @@ __device__ __forceinline__ void staged_range(const uint32_t* __restrict__ ins_i0
     b_hi = min(hi_row / rows_per_block, last);
 }
 
+// The old parts one superblock's windows read.  Its old rows are [O -
+// i_begin, O + 2^16 - i_end) (the rows below O that are not new, up to the
+// next superblock's first old row), and a window also reads the part after
+// its first one: parts [Pa, Pb] with Pb - Pa <= kBlocksPerSuper + 1, so at
+// most kBlocks blocks of 64 K rows.
+template <int K>
+struct OldRange {
+    static constexpr uint32_t kBlocks = (kBlocksPerSuper + 1) / K + 2;
+    static constexpr uint32_t kWords = kBlocks * Occ<K>::kWords;
+};
+
+// Shared memory of a 2-bit Insert CTA: the old range, then ten arrays of
+// kBlocksPerSuper words (new-row masks, planes and counts).
+template <int K>
+__host__ __device__ constexpr size_t insert_smem_bytes() {
+    return (size_t)OldRange<K>::kWords * 8 + 10 * (size_t)kBlocksPerSuper * 4;
+}
+
 // 64 old rows starting at row s, from the pair of parts holding them.
 __device__ __forceinline__ Window old_window_of(const OldPair& o, uint64_t s) {
     const uint32_t off = (uint32_t)(s & (kOccSpan - 1));
@@ -120,19 +138,55 @@ __device__ __forceinline__ void open_row(Window& w, uint32_t p) {
     w.dm = open_bit(w.dm, below);
 }
 
+// Deposits the low popc(m) rows of w, in order, into the set bits of m on
+// each plane (a parallel bit deposit): six stages that shift by 32, 16, ...,
+// 1 rows, each moving the rows whose remaining distance has that bit.  The
+// stage masks depend on m alone, so the three planes share them: stage i
+// moves the bits of mv[i], where mv[i] marks (among the positions a
+// compaction to the right would still move) those with an odd number of
+// clear bits of m below them after the moves of stages 0 .. i-1 (the
+// counts taken by a parallel suffix XOR).  This is the expand network of
+// Hacker's Delight (Warren, 2nd ed., section 7-5).
+__device__ __forceinline__ Window deposit_rows(Window w, unsigned long long m0) {
+    unsigned long long m = m0, mk = ~m << 1, mv[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        unsigned long long mp = mk ^ (mk << 1);
+        mp ^= mp << 2;
+        mp ^= mp << 4;
+        mp ^= mp << 8;
+        mp ^= mp << 16;
+        mp ^= mp << 32;
+        mv[i] = mp & m;
+        m = (m ^ mv[i]) | (mv[i] >> (1 << i));
+        mk &= ~mp;
+    }
+#pragma unroll
+    for (int i = 5; i >= 0; --i) {
+        const int sh = 1 << i;
+        w.lo = (w.lo & ~mv[i]) | ((w.lo << sh) & mv[i]);
+        w.hi = (w.hi & ~mv[i]) | ((w.hi << sh) & mv[i]);
+        w.dm = (w.dm & ~mv[i]) | ((w.dm << sh) & mv[i]);
+    }
+    return Window{w.lo & m0, w.hi & m0, w.dm & m0};
+}
+
 // Spreads the old rows of window w over the rows of an output part whose
 // new rows are the set bits of F: the old rows keep their order and fill
 // the clear bits of F, the rows of F are left empty.  Few new rows: open one
-// row per set bit; many: move each of the few old rows to its place.
+// row per set bit; few old rows: move each to its place; otherwise the
+// deposit network.
+constexpr uint32_t kOpenRows = 6;  // at most this many new rows: open them one by one
 __device__ __forceinline__ Window spread_old(Window w, unsigned long long F) {
     const uint32_t k = __popcll(F);
-    if (k <= 32) {
+    if (k <= kOpenRows) {
         while (F) {
             open_row(w, __ffsll((long long)F) - 1);
             F &= F - 1;
         }
         return w;
     }
+    if (k < 64 - kOpenRows) return deposit_rows(w, ~F);
     Window o{0ull, 0ull, 0ull};
     unsigned long long z = ~F;
     uint32_t src = 0;
@@ -147,9 +201,29 @@ __device__ __forceinline__ Window spread_old(Window w, unsigned long long F) {
     return o;
 }
 
+// kRun consecutive g_sa values from a 16-byte aligned address.
+template <class IdxT>
+__device__ __forceinline__ void load_run(const IdxT* __restrict__ p, IdxT (&v)[kRun]) {
+    static_assert(kRun == 8, "two 16-byte loads of 32-bit values, four of 64-bit ones");
+    if constexpr (sizeof(IdxT) == 4) {
+        const uint4 a = reinterpret_cast<const uint4*>(p)[0], b = reinterpret_cast<const uint4*>(p)[1];
+        v[0] = a.x, v[1] = a.y, v[2] = a.z, v[3] = a.w, v[4] = b.x, v[5] = b.y, v[6] = b.z, v[7] = b.w;
+    } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const ulonglong2 a = reinterpret_cast<const ulonglong2*>(p)[q];
+            v[2 * q] = a.x;
+            v[2 * q + 1] = a.y;
+        }
+    }
+}
+
 // One CTA builds one superblock of the next dictionary (kBlocksPerSuper
 // output parts of 64 rows, rows [O, O + 2^16)) from the new symbols
 // [ins_i0[S], ins_i0[S+1]) that land in it (bint_gather wrote that plan):
+//  0. the old blocks the superblock's windows read (OldRange) start to
+//     arrive in shared memory by asynchronous copies, which run while
+//     steps 1 and 2 do;
 //  1. the CTA reads those new symbols' rows g_sa[i] + i and codes (a run of
 //     consecutive ones per thread) and sets, per output part, the mask F of
 //     its new rows and their three planes at their rows (shared memory; a
@@ -170,7 +244,7 @@ __device__ __forceinline__ Window spread_old(Window w, unsigned long long F) {
 // (staged_range, at most stage_blocks of them); without it, old_words is the
 // whole old dictionary and sb_first is 0.
 template <class IdxT, int kT, int K>
-__global__ void __launch_bounds__(kT, kT == 256 ? 4 : 2) insert_kernel(const unsigned long long* __restrict__ old_words,
+__global__ void __launch_bounds__(kT, kT == 256 ? 3 : 2) insert_kernel(const unsigned long long* __restrict__ old_words,
                                                     unsigned long long n_ext, const uint8_t* __restrict__ bint,
                                                     const IdxT* __restrict__ gsa, unsigned long long n_int,
                                                     const uint32_t* __restrict__ ins_i0,
@@ -179,10 +253,13 @@ __global__ void __launch_bounds__(kT, kT == 256 ? 4 : 2) insert_kernel(const uns
                                                     uint32_t* __restrict__ d_err, unsigned long long sb_first,
                                                     int staged, unsigned long long stage_blocks) {
     constexpr int kNB = kBlocksPerSuper, kPer = kNB / kT;
-    __shared__ uint32_t sF[2][kNB];  // new rows of each part (rows 0-31, 32-63); later its counts
-    __shared__ uint32_t sD[2][kNB];  // terminator plane: of the new rows, later of the whole part
-    __shared__ uint32_t sC[4][kNB];  // lo plane (words 0, 1) and hi plane (2, 3): of the new rows, then the part
-    __shared__ uint32_t sP[2][kNB];  // new symbols before each part; later the block counters
+    extern __shared__ __align__(16) unsigned long long ins_smem[];
+    unsigned long long* sOld = ins_smem;  // old blocks [q_lo, q_lo + q_n)
+    using Row = uint32_t[kNB];
+    Row* sF = reinterpret_cast<Row*>(ins_smem + OldRange<K>::kWords);  // [2]: new rows of each part (rows 0-31, 32-63); later its counts
+    Row* sD = sF + 2;  // [2]: terminator plane: of the new rows, later of the whole part
+    Row* sC = sF + 4;  // [4]: lo plane (words 0, 1) and hi plane (2, 3): of the new rows, then the part
+    Row* sP = sF + 8;  // [2]: new symbols before each part; later the block counters
     const int tid = threadIdx.x;
     const uint64_t S = sb_first + blockIdx.x;
     const uint64_t O = S << kSuperShift;
@@ -205,26 +282,76 @@ __global__ void __launch_bounds__(kT, kT == 256 ? 4 : 2) insert_kernel(const uns
         i_end = min(i_end, (uint64_t)n_int);
         i_begin = min(i_begin, i_end);
     }
+
+    // 0. the old blocks of this superblock's windows, within those old_words
+    //    holds (a part outside them reads as zero and is flagged later)
+    uint64_t q_lo, q_n = 0;
+    {
+        constexpr uint64_t kSpan = 1ull << kSuperShift;
+        const uint64_t lo_row = O - min(i_begin, O);
+        const uint64_t hi_row = O + kSpan - min(i_end, O + kSpan);
+        const uint64_t pa = lo_row >> kOccShift;
+        const uint64_t pb = min((hi_row >> kOccShift) + 1, np_old - 1);
+        const uint64_t qa = max(pa / K, base), qb = min(pb / K, base + avail - 1);
+        q_lo = qa;
+        if (qa <= qb) q_n = min(qb - qa + 1, (uint64_t)OldRange<K>::kBlocks);
+        const unsigned long long* src = old_words + (qa - base) * Occ<K>::kWords;
+        const uint32_t words = (uint32_t)q_n * Occ<K>::kWords;
+        if constexpr (K == 1) {  // 32-byte blocks: 16-byte copies
+            for (uint32_t x = tid; x < words / 2; x += kT) cp_async16(sOld + 2 * x, src + 2 * x);
+        } else {
+            for (uint32_t x = tid; x < words; x += kT) cp_async8(sOld + x, src + x);
+        }
+        cp_async_commit();
+    }
     __syncthreads();
 
     // 1. the new rows of every part of this superblock: each thread takes a
-    //    run of kRun consecutive new symbols (consecutive rows, so a run
-    //    touches one or two parts when the new rows are dense), gathers
-    //    their bits per part in registers and ORs each part's bits into
-    //    shared memory once
-    for (uint64_t base = i_begin + (uint64_t)tid * kRun; base < i_end; base += (uint64_t)kT * kRun) {
-        uint64_t loc[kRun];
+    //    run of kRun consecutive new symbols (runs start at multiples of
+    //    kRun, so the superblock's first and last runs may hold fewer; a
+    //    whole run's g_sa and codes arrive as vector loads; consecutive
+    //    rows, so a run touches one or two parts when the new rows are
+    //    dense), gathers their bits per part in registers and ORs each
+    //    part's bits into shared memory once
+    for (uint64_t base = (i_begin & ~(uint64_t)(kRun - 1)) + (uint64_t)tid * kRun; base < i_end;
+         base += (uint64_t)kT * kRun) {
+        IdxT gv[kRun];
         uint32_t xs[kRun];
+        if (base >= i_begin && base + kRun <= i_end) {
+            load_run<IdxT>(gsa + base, gv);
+            const uint2 b8 = *reinterpret_cast<const uint2*>(bint + base);
+#pragma unroll
+            for (int u = 0; u < kRun; ++u) xs[u] = ((u < 4 ? b8.x : b8.y) >> (8 * (u & 3))) & 0xFFu;
+        } else {
+#pragma unroll
+            for (int u = 0; u < kRun; ++u) {
+                const uint64_t i = base + u;
+                const bool in = i >= i_begin && i < i_end;
+                gv[u] = in ? gsa[i] : (IdxT)0;
+                xs[u] = in ? bint[i] : 0u;
+            }
+        }
+        // rows inside the superblock (row arithmetic in the index type: a
+        // 32-bit index has fewer than 2^32 rows); the run's valid symbols
+        uint32_t loc[kRun], valid = 0, j_lo = 0xFFFFFFFFu, j_hi = 0;
 #pragma unroll
         for (int u = 0; u < kRun; ++u) {
             const uint64_t i = base + u;
-            loc[u] = i < i_end ? (uint64_t)gsa[i] + i - O : ~0ull;
-            xs[u] = i < i_end ? bint[i] : 0u;
+            const IdxT local = gv[u] + (IdxT)i - (IdxT)O;
+            loc[u] = (uint32_t)local;
+            if (i >= i_begin && i < i_end) {
+                if (local >= (IdxT)(1u << kSuperShift)) {  // not in this superblock: the plan is inconsistent
+                    atomicOr(d_err, 1024u);
+                } else {
+                    valid |= 1u << u;
+                    j_lo = min(j_lo, loc[u] >> kOccShift);
+                    j_hi = max(j_hi, loc[u] >> kOccShift);
+                }
+            }
         }
-        uint32_t cj = 0xFFFFFFFFu;
-        unsigned long long f = 0, dm = 0, lo = 0, hi = 0;
-        auto flush = [&]() {
-            if (cj == 0xFFFFFFFFu) return;
+        if (!valid) continue;
+        auto flush = [&](uint32_t cj, unsigned long long f, unsigned long long dm, unsigned long long lo,
+                         unsigned long long hi) {
             if ((uint32_t)f) atomicOr(&sF[0][cj], (uint32_t)f);
             if ((uint32_t)(f >> 32)) atomicOr(&sF[1][cj], (uint32_t)(f >> 32));
             if ((uint32_t)dm) atomicOr(&sD[0][cj], (uint32_t)dm);
@@ -234,17 +361,27 @@ __global__ void __launch_bounds__(kT, kT == 256 ? 4 : 2) insert_kernel(const uns
             if ((uint32_t)hi) atomicOr(&sC[2][cj], (uint32_t)hi);
             if ((uint32_t)(hi >> 32)) atomicOr(&sC[3][cj], (uint32_t)(hi >> 32));
         };
+        if (j_lo == j_hi) {  // the whole run in one part
+            unsigned long long f = 0, dm = 0, lo = 0, hi = 0;
+#pragma unroll
+            for (int u = 0; u < kRun; ++u) {
+                const unsigned long long bit = (unsigned long long)((valid >> u) & 1u) << (loc[u] & 63u);
+                f |= bit;
+                dm |= xs[u] == kBintDollar ? bit : 0ull;
+                lo |= (xs[u] != kBintDollar && (xs[u] & 1u)) ? bit : 0ull;
+                hi |= (xs[u] != kBintDollar && (xs[u] & 2u)) ? bit : 0ull;
+            }
+            flush(j_lo, f, dm, lo, hi);
+            continue;
+        }
+        uint32_t cj = 0xFFFFFFFFu;
+        unsigned long long f = 0, dm = 0, lo = 0, hi = 0;
 #pragma unroll
         for (int u = 0; u < kRun; ++u) {
-            if (base + u >= i_end) break;
-            const uint64_t local = loc[u];
-            if (local >= (1ull << kSuperShift)) {  // not in this superblock: the plan is inconsistent
-                atomicOr(d_err, 1024u);
-                continue;
-            }
-            const uint32_t j = (uint32_t)(local >> kOccShift), q = (uint32_t)local & 63u;
+            if (!((valid >> u) & 1u)) continue;
+            const uint32_t j = loc[u] >> kOccShift, q = loc[u] & 63u;
             if (j != cj) {
-                flush();
+                if (cj != 0xFFFFFFFFu) flush(cj, f, dm, lo, hi);
                 cj = j;
                 f = dm = lo = hi = 0;
             }
@@ -257,7 +394,7 @@ __global__ void __launch_bounds__(kT, kT == 256 ? 4 : 2) insert_kernel(const uns
                 if (xs[u] & 2u) hi |= bit;
             }
         }
-        flush();
+        flush(cj, f, dm, lo, hi);
     }
     __syncthreads();
 
@@ -280,30 +417,11 @@ __global__ void __launch_bounds__(kT, kT == 256 ? 4 : 2) insert_kernel(const uns
         // two new symbols on one row, or one outside this superblock
         if (tid == 0 && all != (uint32_t)(i_end - i_begin)) atomicOr(d_err, 1024u);
     }
+    cp_async_wait_all();
     __syncthreads();
 
-    // 3. build parts tid, tid + kT, ...; keep them in shared memory.  The
-    //    old parts of every window are loaded before any is used.
-    OldPair op[kPer];
-    uint64_t s_old[kPer];
-#pragma unroll
-    for (int bb = 0; bb < kPer; ++bb) {
-        const int j = tid + bb * kT;
-        const uint64_t b = p_first + j;
-        const uint64_t o = b << kOccShift;
-        const uint64_t inew = i_begin + sP[0][j];  // new symbols before row o
-        s_old[bb] = o - inew;
-        // (parts past the last row, in the last block of 64 K rows, hold
-        // nothing: their window is never used)
-        if (b < np_new && o <= n_new && (inew > o || s_old[bb] > n_ext)) atomicOr(d_err, 1024u);
-        if (inew > o || s_old[bb] > n_ext) s_old[bb] = inew > o ? 0ull : (uint64_t)n_ext;
-        if (b >= np_new) {
-            s_old[bb] = 0;
-            op[bb].a = op[bb].b = Window{0ull, 0ull, 0ull};
-        } else {
-            op[bb] = old_pair<K>(old_words, np_old, s_old[bb], base, avail, d_err);
-        }
-    }
+    // 3. build parts tid, tid + kT, ...; keep them in shared memory (the
+    //    old parts of each window come from the staged range)
 #pragma unroll
     for (int bb = 0; bb < kPer; ++bb) {
         const int j = tid + bb * kT;
@@ -313,8 +431,17 @@ __global__ void __launch_bounds__(kT, kT == 256 ? 4 : 2) insert_kernel(const uns
             continue;
         }
         const uint64_t o = b << kOccShift;
+        const uint64_t inew = i_begin + sP[0][j];  // new symbols before row o
+        uint64_t s_old = o - inew;
+        if (inew > o || s_old > n_ext) {
+            // (parts past the last row, in the last block of 64 K rows,
+            // hold nothing: their window is never used)
+            if (o <= n_new) atomicOr(d_err, 1024u);
+            s_old = inew > o ? 0ull : (uint64_t)n_ext;
+        }
+        const OldPair op = old_pair<K>(sOld, np_old, s_old, q_lo, q_n, d_err);
         const unsigned long long F = (unsigned long long)sF[0][j] | ((unsigned long long)sF[1][j] << 32);
-        Window w = spread_old(old_window_of(op[bb], s_old[bb]), F);
+        Window w = spread_old(old_window_of(op, s_old), F);
         w.lo |= (unsigned long long)sC[0][j] | ((unsigned long long)sC[1][j] << 32);
         w.hi |= (unsigned long long)sC[2][j] | ((unsigned long long)sC[3][j] << 32);
         w.dm |= (unsigned long long)sD[0][j] | ((unsigned long long)sD[1][j] << 32);
@@ -323,17 +450,19 @@ __global__ void __launch_bounds__(kT, kT == 256 ? 4 : 2) insert_kernel(const uns
         w.lo &= vm;
         w.hi &= vm;
         w.dm &= vm;
-        uint32_t cnt[4];
-#pragma unroll
-        for (uint32_t c = 0; c < 4; ++c) cnt[c] = __popcll(plane_match(w.lo, w.hi, w.dm, c) & vm);
+        // per-code counts: c = 3 on both planes, 1 and 2 on one, 0 the rest
+        const unsigned long long live = vm & ~w.dm;
+        const uint32_t n3 = __popcll(w.lo & w.hi & live);
+        const uint32_t n1 = __popcll(w.lo & live) - n3, n2 = __popcll(w.hi & live) - n3;
+        const uint32_t n0 = __popcll(live) - n1 - n2 - n3;
         sC[0][j] = (uint32_t)w.lo;
         sC[1][j] = (uint32_t)(w.lo >> 32);
         sC[2][j] = (uint32_t)w.hi;
         sC[3][j] = (uint32_t)(w.hi >> 32);
         sD[0][j] = (uint32_t)w.dm;
         sD[1][j] = (uint32_t)(w.dm >> 32);
-        sF[0][j] = cnt[0] | (cnt[1] << 16);
-        sF[1][j] = cnt[2] | (cnt[3] << 16);
+        sF[0][j] = n0 | (n1 << 16);
+        sF[1][j] = n2 | (n3 << 16);
     }
     __syncthreads();
 
@@ -770,7 +899,27 @@ void super_scan(Launcher& L, const uint32_t* sb_tot, uint64_t nsb, unsigned long
                 kScanThreads, 0, super, (unsigned long long)nsb, chunk_tot);
 }
 
+template <class IdxT, int kT, int K>
+void insert_attr() {
+    cudaFuncSetAttribute(insert_kernel<IdxT, kT, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)insert_smem_bytes<K>());
+}
+template <int kT, int K>
+void insert_attrs() {
+    insert_attr<uint32_t, kT, K>();
+    insert_attr<unsigned long long, kT, K>();
+}
+
 }  // namespace
+
+void insert_init() {
+    insert_attrs<kInsertThreads, 1>();
+    insert_attrs<kInsertThreads, 2>();
+    insert_attrs<kInsertThreads, 4>();
+    insert_attrs<kInsertThreadsSparse, 1>();
+    insert_attrs<kInsertThreadsSparse, 2>();
+    insert_attrs<kInsertThreadsSparse, 4>();
+}
 
 // Old blocks a chunk can read: the chunk's rows in blocks plus a few; a
 // dictionary smaller than a chunk needs only its own blocks.
@@ -834,12 +983,14 @@ void launch_insert(Launcher& L, const void* old_blocks, uint64_t n_ext, const ui
                              : (occ_k == 4 ? insert_kernel<IdxT, kInsertThreadsSparse, 4>
                                            : (occ_k == 2 ? insert_kernel<IdxT, kInsertThreadsSparse, 2>
                                                          : insert_kernel<IdxT, kInsertThreadsSparse, 1>));
+    const size_t smem = occ_k == 4 ? insert_smem_bytes<4>() : (occ_k == 2 ? insert_smem_bytes<2>()
+                                                                           : insert_smem_bytes<1>());
     const auto* old_w = static_cast<const unsigned long long*>(old_blocks);
     auto* new_w = static_cast<unsigned long long*>(new_blocks);
     if (!stage) {
         const double bytes = bb * dict_blocks(n_ext, occ_k) + (1.0 + sizeof(IdxT)) * n_int +
                              bb * dict_blocks(n_new, occ_k) + 4.0 * (nsb + 1);
-        SBWT_LAUNCH(L, "insert_merge", bytes, 0, nullptr, kern, (unsigned)nsb, threads, 0, old_w,
+        SBWT_LAUNCH(L, "insert_merge", bytes, 0, nullptr, kern, (unsigned)nsb, threads, smem, old_w,
                     (unsigned long long)n_ext, bint, gsa, (unsigned long long)n_int, ins_i0, new_w,
                     (unsigned long long)n_new, sb_tot, d_err, 0ull, 0, 0ull);
     } else {
@@ -858,7 +1009,7 @@ void launch_insert(Launcher& L, const void* old_blocks, uint64_t n_ext, const ui
                         (unsigned long long)s1, stage, (unsigned long long)stage_blocks, d_err);
             SBWT_LAUNCH(L, "insert_merge", 2.0 * rows / (64.0 * occ_k) * bb + (1.0 + sizeof(IdxT)) * rows *
                                               ((double)n_int / (double)n_new), 0, nullptr, kern, (unsigned)(s1 - s0),
-                        threads, 0, stage, (unsigned long long)n_ext, bint, gsa, (unsigned long long)n_int, ins_i0,
+                        threads, smem, stage, (unsigned long long)n_ext, bint, gsa, (unsigned long long)n_int, ins_i0,
                         new_w, (unsigned long long)n_new, sb_tot, d_err, (unsigned long long)s0, 1,
                         (unsigned long long)stage_blocks);
             s1 = s0;

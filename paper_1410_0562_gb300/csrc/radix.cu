@@ -25,6 +25,7 @@ constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kItems = 8;                           // keys per thread per tile
 constexpr int kTile = kThreads * kItems;            // 2048 keys per tile
+static_assert(kTile == (int)kRadixTile, "one tile size for the sort and the kernels that count for it");
 constexpr int kWarpItems = kTile / kWarps;          // 256 consecutive keys per warp
 constexpr int kBins = kRadixBins;
 constexpr int kMaxChunks = 2048;
@@ -51,34 +52,51 @@ constexpr size_t kPartials = kGridBar + 8;
 constexpr size_t kChunkOffsets = kPartials + (size_t)kFusedGroups * kBins;
 constexpr uint32_t kGridSpinLimit = 1u << 22;
 
-// Chunk c of a grid of `grid` CTAs: tiles [t0, t1).  Only the first
-// ceil(ntiles / per) chunks hold tiles.
+// Chunk c of a grid of `grid` CTAs: tiles [t0, t1) (radix_chunk_tiles).
+// Only the first ceil(ntiles / per) chunks hold tiles.
 __device__ __forceinline__ uint32_t tiles_per_chunk(uint32_t n, uint32_t grid, uint32_t& ntiles) {
     ntiles = (uint32_t)(((uint64_t)n + kTile - 1) / kTile);
     return (ntiles + grid - 1) / grid;
 }
 __device__ __forceinline__ void chunk_range(uint32_t n, uint32_t& t0, uint32_t& t1) {
-    uint32_t ntiles;
-    const uint32_t per = tiles_per_chunk(n, gridDim.x, ntiles);
-    t0 = min(ntiles, blockIdx.x * per);
-    t1 = min(ntiles, t0 + per);
+    radix_chunk_tiles(n, gridDim.x, blockIdx.x, t0, t1);
+}
+
+// Two keys from L2 (not through L1: in the fused sort other CTAs wrote them
+// earlier in the same launch).
+__device__ __forceinline__ void ld_cg_pair(const unsigned long long* p, unsigned long long& a,
+                                           unsigned long long& b) {
+    asm volatile("ld.global.cg.v2.u64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "l"(p));
 }
 
 // Digit counts of this CTA's chunk (per-warp sub-histograms in shared
 // memory h, kWarps x kBins words), also added to the digit totals of the
 // whole pass.  A chunk without tiles writes nothing: the scans skip it.
+// Whole tiles are read as 16-byte pairs, a tile's loads all issued before
+// its counts (the key arrays start on a 16-byte boundary).
 template <class KeyT>
 __device__ __forceinline__ void up_phase(const KeyT* __restrict__ keys, uint32_t n, int shift,
                                          uint32_t* __restrict__ chunk_counts, uint32_t* __restrict__ totals,
                                          uint32_t* h) {
+    static_assert(sizeof(KeyT) == 8, "pairs of 64-bit keys");
     uint32_t t0, t1;
     chunk_range(n, t0, t1);
     if (t0 >= t1) return;
     for (int i = threadIdx.x; i < kWarps * kBins; i += kThreads) h[i] = 0;
     __syncthreads();
     const uint64_t i_end = min((uint64_t)n, (uint64_t)t1 * kTile);
+    const uint64_t whole_end = (uint64_t)t0 * kTile + (i_end - (uint64_t)t0 * kTile) / kTile * kTile;
     uint32_t* my = h + (threadIdx.x >> 5) * kBins;
-    for (uint64_t i = (uint64_t)t0 * kTile + threadIdx.x; i < i_end; i += kThreads)
+    for (uint64_t b = (uint64_t)t0 * kTile; b < whole_end; b += kTile) {
+        unsigned long long v[kItems];
+#pragma unroll
+        for (int j = 0; j < kItems / 2; ++j)
+            ld_cg_pair(reinterpret_cast<const unsigned long long*>(keys) + b + 2 * (j * kThreads + threadIdx.x),
+                       v[2 * j], v[2 * j + 1]);
+#pragma unroll
+        for (int j = 0; j < kItems; ++j) atomicAdd(&my[(uint32_t)(v[j] >> shift) & (kBins - 1)], 1u);
+    }
+    for (uint64_t i = whole_end + threadIdx.x; i < i_end; i += kThreads)
         atomicAdd(&my[(uint32_t)(keys[i] >> shift) & (kBins - 1)], 1u);
     __syncthreads();
     uint32_t s = 0;
@@ -99,41 +117,45 @@ __global__ void __launch_bounds__(kThreads) radix_upsweep_kernel(const KeyT* __r
 
 // Output offset of every (chunk, digit): the digit's start in the sorted
 // output (exclusive scan of the totals) plus the same digit's count in all
-// earlier chunks.  CTA x handles digits [32x, 32x + 32); its 256 threads are
-// 32 digits x 8 groups of consecutive chunks (small CTAs find room on SMs
-// that the other stream's kernels keep busy).
+// earlier chunks.  One warp per digit (kBins / kScanWarps CTAs): 32 chunks
+// at a time, four such loads in flight, each scanned across the warp.
 constexpr int kScanThreads = 256;
-constexpr int kScanGroups = kScanThreads / 32;
+constexpr int kScanWarps = kScanThreads / 32;
+constexpr int kScanBatch = 4;
 
 __global__ void __launch_bounds__(kScanThreads) radix_chunk_scan_kernel(uint32_t* __restrict__ chunk_counts,
                                                                         int grid, const uint32_t* __restrict__ totals,
                                                                         uint32_t* __restrict__ next_totals,
                                                                         const uint32_t* __restrict__ d_n) {
-    __shared__ uint32_t start[kBins];
-    __shared__ uint32_t part[kScanGroups][33];
-    const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
-    const int d = blockIdx.x * 32 + lane;
+    const int lane = threadIdx.x & 31;
+    const uint32_t d = blockIdx.x * kScanWarps + (threadIdx.x >> 5);
     uint32_t ntiles;
     const uint32_t tpc = tiles_per_chunk(*d_n, (uint32_t)grid, ntiles);
-    const int nchunks = tpc ? (int)((ntiles + tpc - 1) / tpc) : 0;  // chunks that hold tiles
-    uint32_t tot;
-    const uint32_t ex = cta_exclusive_scan<SumOp, kScanThreads>(threadIdx.x < kBins ? totals[threadIdx.x] : 0u, tot);
-    if (threadIdx.x < kBins) start[threadIdx.x] = ex;
+    const uint32_t nchunks = tpc ? (ntiles + tpc - 1) / tpc : 0;  // chunks that hold tiles
     if (blockIdx.x == 0 && threadIdx.x < kBins) next_totals[threadIdx.x] = 0;
-    const int per = (nchunks + kScanGroups - 1) / kScanGroups;
-    const int c0 = min(nchunks, g * per), c1 = min(nchunks, c0 + per);
-    uint32_t sum = 0;
-#pragma unroll 8
-    for (int c = c0; c < c1; ++c) sum += chunk_counts[(uint64_t)c * kBins + d];
-    part[g][lane] = sum;
-    __syncthreads();
-    uint32_t run = start[d];
-    for (int q = 0; q < g; ++q) run += part[q][lane];
-#pragma unroll 8
-    for (int c = c0; c < c1; ++c) {
-        const uint32_t v = chunk_counts[(uint64_t)c * kBins + d];
-        chunk_counts[(uint64_t)c * kBins + d] = run;
-        run += v;
+    uint32_t run = 0;
+    for (uint32_t e = lane; e < d; e += 32) run += totals[e];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) run += __shfl_xor_sync(0xffffffffu, run, o);
+    for (uint32_t cb = 0; cb < nchunks; cb += 32 * kScanBatch) {
+        uint32_t v[kScanBatch];
+#pragma unroll
+        for (int j = 0; j < kScanBatch; ++j) {
+            const uint32_t c = cb + j * 32 + lane;
+            v[j] = c < nchunks ? chunk_counts[(uint64_t)c * kBins + d] : 0u;
+        }
+#pragma unroll
+        for (int j = 0; j < kScanBatch; ++j) {
+            const uint32_t c = cb + j * 32 + lane;
+            uint32_t x = v[j];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            if (c < nchunks) chunk_counts[(uint64_t)c * kBins + d] = run + x - v[j];
+            run += __shfl_sync(0xffffffffu, x, 31);
+        }
     }
 }
 
@@ -481,6 +503,16 @@ unsigned persistent_ctas(const void* kernel, int threads, size_t smem) {
     return (unsigned)(std::max(1, sms) * std::max(1, per_sm));
 }
 
+unsigned radix_keys_grid(uint64_t cap) {
+    const uint64_t tiles = cap / kTile + 1;
+    return (unsigned)std::min<uint64_t>(std::max(1u, g_keys_ctas[current_device()]), tiles);
+}
+
+uint32_t* radix_first_counts(uint32_t* temp) { return temp + kChunkOffsets; }
+uint32_t* radix_first_totals(uint32_t* temp) { return temp + kTotals; }
+
+void radix_clear(Launcher& L, uint32_t* temp) { cudaMemsetAsync(temp, 0, (kGridBar + 2) * 4, L.stream); }
+
 size_t radix_temp_words(uint64_t cap) {
     const uint64_t chunks = std::min<uint64_t>(kMaxChunks, cap / kTile + 1);
     return kChunkOffsets + (size_t)chunks * kBins + 64;
@@ -499,13 +531,13 @@ void radix_init() {
 }
 
 bool radix_sort_keys(Launcher& L, unsigned long long* keys, unsigned long long* keys_alt, const uint32_t* d_n,
-                     uint64_t cap, int begin_bit, int end_bit, uint32_t* temp, uint32_t* d_err) {
+                     uint64_t cap, int begin_bit, int end_bit, uint32_t* temp, uint32_t* d_err,
+                     bool first_counted) {
     using u64 = unsigned long long;
     const int passes = radix_passes(begin_bit, end_bit);
     if (passes <= 0) return false;
     uint32_t* chunk = temp + kChunkOffsets;
-    const uint64_t tiles = cap / kTile + 1;
-    const unsigned grid = (unsigned)std::min<uint64_t>(std::max(1u, g_keys_ctas[current_device()]), tiles);
+    const unsigned grid = radix_keys_grid(cap);
     auto* const down_kernel = radix_downsweep_kernel<u64, false>;
     const size_t down_bytes = down_smem<u64, false>();
     bool alt = false;
@@ -515,11 +547,13 @@ bool radix_sort_keys(Launcher& L, unsigned long long* keys, unsigned long long* 
         const int shift = begin_bit + kRadixBits * p;
         uint32_t* totals = temp + kTotals + (size_t)kBins * (p & 1);
         uint32_t* next_totals = temp + kTotals + (size_t)kBins * ((p + 1) & 1);
-        if (p == 0) cudaMemsetAsync(temp, 0, (kGridBar + 2) * 4, L.stream);
-        SBWT_LAUNCH(L, "radix_upsweep", 0, 8, d_n, radix_upsweep_kernel<u64>, grid, kThreads, 0, kin, d_n, shift,
-                    chunk, totals);
-        SBWT_LAUNCH(L, "radix_chunk_scan", 12.0 * grid * kBins, 0, nullptr, radix_chunk_scan_kernel, kBins / 32,
-                    kScanThreads, 0, chunk, (int)grid, totals, next_totals, d_n);
+        if (p > 0 || !first_counted) {
+            if (p == 0) radix_clear(L, temp);
+            SBWT_LAUNCH(L, "radix_upsweep", 0, 8, d_n, radix_upsweep_kernel<u64>, grid, kThreads, 0, kin, d_n,
+                        shift, chunk, totals);
+        }
+        SBWT_LAUNCH(L, "radix_chunk_scan", 12.0 * grid * kBins, 0, nullptr, radix_chunk_scan_kernel,
+                    kBins / kScanWarps, kScanThreads, 0, chunk, (int)grid, totals, next_totals, d_n);
         // per key: the 8-byte key read and written once
         SBWT_LAUNCH(L, "radix_downsweep", 0, 16, d_n, down_kernel, grid, kThreads, down_bytes, kin, nullptr, ko,
                     nullptr, d_n, shift, chunk, d_err);

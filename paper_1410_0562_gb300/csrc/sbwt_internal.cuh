@@ -388,6 +388,18 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, uint32_t pari
 }
 constexpr uint32_t kMbarSpinLimit = 1u << 20;
 
+// Per-thread asynchronous copies global -> shared (cp.async, 16 bytes with
+// both addresses 16-byte aligned, or 8 bytes 8-byte aligned); a thread's
+// copies are complete once it has passed cp_async_wait_all.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // CTAs per launch for a persistent kernel: SMs x resident CTAs per SM.
 unsigned persistent_ctas(const void* kernel, int threads, size_t smem);
 
@@ -398,10 +410,35 @@ unsigned persistent_ctas(const void* kernel, int threads, size_t smem);
 constexpr int kRadixBits = 8;
 constexpr int kRadixBins = 1 << kRadixBits;
 
+constexpr uint32_t kRadixTile = 2048;  // keys per tile of a pass
+
 inline int radix_passes(int begin_bit, int end_bit) { return (end_bit - begin_bit + kRadixBits - 1) / kRadixBits; }
+
+// A pass over n keys with a grid of `grid` CTAs splits them into chunks of
+// whole tiles, one per CTA: chunk c holds tiles [t0, t1) (empty for the
+// chunks past the last tile).
+__host__ __device__ inline void radix_chunk_tiles(uint32_t n, uint32_t grid, uint32_t c, uint32_t& t0, uint32_t& t1) {
+    const uint32_t ntiles = (uint32_t)(((uint64_t)n + kRadixTile - 1) / kRadixTile);
+    const uint32_t per = (ntiles + grid - 1) / grid;
+    const uint64_t a = (uint64_t)c * per;
+    t0 = a < ntiles ? (uint32_t)a : ntiles;
+    t1 = t0 + per < ntiles ? t0 + per : ntiles;
+}
 
 size_t radix_temp_words(uint64_t cap);
 void radix_init();  // once per device, before the first sort
+
+// The first pass of a keys-only sort may be counted by the kernel that
+// writes the keys, saving one read of them.  That kernel runs with
+// radix_keys_grid(cap) CTAs; CTA c writes the digit counts of its chunk
+// (radix_chunk_tiles with that grid) to radix_first_counts(temp)[c * 256 +
+// d] and adds them to radix_first_totals(temp)[d], which radix_clear(temp)
+// zeroed before it; a chunk without tiles writes nothing.  Then
+// radix_sort_keys(..., first_counted = true).
+unsigned radix_keys_grid(uint64_t cap);
+uint32_t* radix_first_counts(uint32_t* temp);
+uint32_t* radix_first_totals(uint32_t* temp);
+void radix_clear(Launcher& L, uint32_t* temp);
 
 // Stable LSD radix sort of (*d_n) 64-bit keys on bits [begin_bit, end_bit);
 // key bits outside that range are carried along but do not take part in the
@@ -410,7 +447,8 @@ void radix_init();  // once per device, before the first sort
 // skipped and flagged in *d_err (bit 4).  Both arrays must start on a 16-byte
 // boundary (whole tiles arrive by TMA bulk copies).
 bool radix_sort_keys(Launcher& L, unsigned long long* keys, unsigned long long* keys_alt, const uint32_t* d_n,
-                     uint64_t cap, int begin_bit, int end_bit, uint32_t* temp, uint32_t* d_err);
+                     uint64_t cap, int begin_bit, int end_bit, uint32_t* temp, uint32_t* d_err,
+                     bool first_counted = false);
 // A sort of (64-bit key, 32-bit value) pairs, keyed like radix_sort_keys,
 // in one cooperative launch (all passes, the CTAs meeting at bounded grid
 // barriers; a barrier that times out flags *d_err bit 9); the values move in

@@ -232,15 +232,29 @@ __device__ __forceinline__ uint32_t bucket_digit_sigma(unsigned long long K, uin
 // 0..23, bit 31 the short flag) and the key's length field (bits 24..28) in
 // the low word, t in the high word.  The sort orders by the low kDigitBits bits and
 // carries the rest.
+constexpr int kKeyThreads = 512;  // threads of a sa_digit_keys CTA (one radix chunk)
+
 template <int kB>
-__global__ void __launch_bounds__(kThreads) sa_digit_keys_kernel(const uint32_t* __restrict__ text,
+__global__ void __launch_bounds__(kKeyThreads) sa_digit_keys_kernel(const uint32_t* __restrict__ text,
                                                                  const uint32_t* __restrict__ term,
                                                                  unsigned long long base, uint32_t n,
                                                                  uint32_t sigma, uint32_t pw,
                                                                  unsigned long long* __restrict__ elems,
-                                                                 uint32_t* __restrict__ d_n) {
+                                                                 uint32_t* __restrict__ d_n,
+                                                                 uint32_t* __restrict__ counts,
+                                                                 uint32_t* __restrict__ totals) {
+    static_assert(kKeyThreads % kRadixBins == 0, "whole digit sets per thread group");
+    __shared__ uint32_t h[kKeyThreads / 32][kRadixBins];
     if (blockIdx.x == 0 && threadIdx.x == 0) *d_n = n;
-    for (uint32_t t = blockIdx.x * kThreads + threadIdx.x; t < n; t += gridDim.x * kThreads) {
+    uint32_t tile0, tile1;
+    radix_chunk_tiles(n, gridDim.x, blockIdx.x, tile0, tile1);
+    if (tile0 >= tile1) return;
+    for (int i = threadIdx.x; i < (kKeyThreads / 32) * kRadixBins; i += kKeyThreads) (&h[0][0])[i] = 0;
+    __syncthreads();
+    uint32_t* my = h[threadIdx.x >> 5];
+    const uint32_t t_end = (uint32_t)min((uint64_t)n, (uint64_t)tile1 * kRadixTile);
+#pragma unroll 4
+    for (uint32_t t = tile0 * kRadixTile + threadIdx.x; t < t_end; t += kKeyThreads) {
         const unsigned long long K = initial_key<kB>(text, term, base + t);
         uint32_t d;
         if constexpr (kB == 2) {
@@ -249,6 +263,16 @@ __global__ void __launch_bounds__(kThreads) sa_digit_keys_kernel(const uint32_t*
             d = bucket_digit_sigma(K, sigma, pw);
         }
         elems[t] = d | ((uint32_t)(K & 31) << 24) | ((unsigned long long)t << 32);
+        atomicAdd(&my[d & (kRadixBins - 1)], 1u);
+    }
+    __syncthreads();
+    // the first radix pass's counts of this chunk (digit bits 0..7)
+    if (threadIdx.x < kRadixBins) {
+        uint32_t c = 0;
+#pragma unroll
+        for (int w = 0; w < kKeyThreads / 32; ++w) c += h[w][threadIdx.x];
+        counts[(uint64_t)blockIdx.x * kRadixBins + threadIdx.x] = c;
+        if (c) atomicAdd(&totals[threadIdx.x], c);
     }
 }
 
@@ -1490,7 +1514,7 @@ __global__ void __launch_bounds__(kThreads) sa_groups_apply_kernel(
 constexpr size_t kLocalSortSmem = (size_t)kLSlots * (8 + 4 + 4 + 4);
 constexpr size_t kRoundLocalSmem = (size_t)kLSlots * (8 + 4 + 4);
 
-unsigned g_keys_ctas[64] = {0};
+unsigned g_window_ctas[64] = {0};
 unsigned g_round_keys_ctas[64] = {0};
 unsigned g_groups_ctas[64] = {0};
 unsigned g_local_ctas[64] = {0};
@@ -1511,7 +1535,7 @@ void suffix_sort_init() {
     const int dev = current_device();
     cudaFuncSetAttribute(sa_local_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLocalSortSmem);
     cudaFuncSetAttribute(sa_round_local_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRoundLocalSmem);
-    g_keys_ctas[dev] = persistent_ctas((const void*)sa_digit_keys_kernel<2>, kThreads, 0);
+    g_window_ctas[dev] = persistent_ctas((const void*)sa_unit_begin_kernel<2>, kThreads, 0);
     g_round_keys_ctas[dev] = persistent_ctas((const void*)sa_round_keys_kernel, kThreads, 0);
     g_groups_ctas[dev] = std::min<unsigned>(kMaxGroupChunks,
                                             persistent_ctas((const void*)sa_groups_apply_kernel<false>, kThreads, 0));
@@ -1589,7 +1613,7 @@ void suffix_sort_block(Launcher& L, const uint32_t* text, const uint32_t* term, 
     }
     const int seg_shift = wide ? 5 + (int)KeyGeom<4>::CB - 4 * (int)pw : kBucketShift;
     const uint32_t nwin = (uint32_t)(((uint64_t)n + kWindow - 1) / kWindow);
-    const unsigned warp_grid = grid_of(g_keys_ctas[dev], (uint64_t)nwin / (kThreads / 32) + 1);
+    const unsigned warp_grid = grid_of(g_window_ctas[dev], (uint64_t)nwin / (kThreads / 32) + 1);
     const Units units = units_at(b.units, n);
     const int digit_bits = kDigitBits;
     auto* const digit_keys = wide ? sa_digit_keys_kernel<4> : sa_digit_keys_kernel<2>;
@@ -1598,10 +1622,13 @@ void suffix_sort_block(Launcher& L, const uint32_t* text, const uint32_t* term, 
 
     uint32_t* d_n = b.count_log;
     uint32_t* d_large = b.count_log + 1;
+    // the keys, and the digit counts of the sort's first pass over them
+    radix_clear(L, b.radix_temp);
     SBWT_LAUNCH(L, "sa_digit_keys", (double)n * 8 + n * code_bits / 8.0 + n / 8.0, 0, nullptr, digit_keys,
-                grid_of(g_keys_ctas[dev], (uint64_t)n / kThreads + 1), kThreads, 0, text, term,
-                (unsigned long long)base, n, (uint32_t)std::max(sigma, 2), pw, b.keys, d_n);
-    const bool da = radix_sort_keys(L, b.keys, b.keys_alt, d_n, n, 0, digit_bits, b.radix_temp, b.err);
+                radix_keys_grid(n), kKeyThreads, 0, text, term, (unsigned long long)base, n,
+                (uint32_t)std::max(sigma, 2), pw, b.keys, d_n, radix_first_counts(b.radix_temp),
+                radix_first_totals(b.radix_temp));
+    const bool da = radix_sort_keys(L, b.keys, b.keys_alt, d_n, n, 0, digit_bits, b.radix_temp, b.err, true);
     const unsigned long long* elems = da ? b.keys_alt : b.keys;  // (digit, t) in row order
     // the other 64-bit array holds the keys of the listed long rows, then the
     // device-wide path's list

@@ -132,6 +132,9 @@ static inline ulonglong2 make_ulonglong2(unsigned long long a, unsigned long lon
 struct uint4 {
     unsigned x, y, z, w;
 };
+struct uint2 {
+    unsigned x, y;
+};
 static inline uint4 make_uint4(unsigned a, unsigned b, unsigned c, unsigned d) { return uint4{a, b, c, d}; }
 
 template <class T>

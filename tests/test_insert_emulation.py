@@ -44,8 +44,11 @@ def emu(tmp_path_factory):
     (d / "dict.inc").write_text(_cut(hdr, "constexpr int kOccShift = 6;",
                                      "// rank(c, i) within i's superblock: the block counter"))
     (d / "scan.inc").write_text(_cut(hdr, "struct SumOp {", "// Launch bookkeeping"))
-    (d / "insert.inc").write_text(_cut(ins, "constexpr int kThreads = 256;", "// ------------------------------------------------"
-                                                                 "---------------------------\n// The same merge"))
+    kern = _cut(ins, "constexpr int kThreads = 256;", "// ------------------------------------------------"
+                                                      "---------------------------\n// The same merge")
+    kern = kern.replace("extern __shared__ __align__(16) unsigned long long ins_smem[];",
+                        "unsigned long long* ins_smem = g_ins_smem;")
+    (d / "insert.inc").write_text(kern)
     lib = d / "libinsemu.so"
     subprocess.check_call(["g++", "-O1", "-std=c++20", "-shared", "-fPIC", "-pthread", "-I", str(d), "-o", str(lib),
                            EMU])
@@ -55,6 +58,8 @@ def emu(tmp_path_factory):
     L.emu_insert.restype = ctypes.c_int
     L.emu_insert_in_place.argtypes = [P, U64, P, P, ctypes.c_int, U64, P, U64, P, P, ctypes.c_int, U64]
     L.emu_insert_in_place.restype = ctypes.c_int
+    L.emu_spread_old.argtypes = [P, U64, P]
+    L.emu_spread_old.restype = None
     return L
 
 
@@ -213,3 +218,26 @@ def test_in_place_merge_matches_the_oracle(emu, n_ext, n_int, kind, chunk, k):
     bad = np.nonzero(words != pack_dict(expect, k))[0]
     assert len(bad) == 0, f"words differ at {bad[:8].tolist()}"
     assert np.array_equal(tot, super_totals(expect))
+
+
+def test_spread_old_places_old_rows_in_order_around_the_new_ones(emu):
+    """One output part: its old rows (the window's low 64 - k rows, on each
+    of the three planes) fill the rows where F is clear, in order, and the
+    rows of F stay empty -- for every k, so each of the three ways (opening
+    rows one by one, the deposit network, placing the few old rows) is
+    checked against a bit-by-bit reference."""
+    rng = np.random.default_rng(77)
+    inp = np.zeros(3, np.uint64)
+    out = np.zeros(3, np.uint64)
+    for k in list(range(65)) * 40:
+        rows = rng.choice(64, size=k, replace=False)
+        F = int(np.bitwise_or.reduce(np.left_shift(np.uint64(1), rows.astype(np.uint64)))) if k else 0
+        inp[:] = rng.integers(0, 2**64, size=3, dtype=np.uint64)
+        emu.emu_spread_old(inp.ctypes.data, F, out.ctypes.data)
+        for plane in range(3):
+            x, want, src = int(inp[plane]), 0, 0
+            for p in range(64):
+                if not (F >> p) & 1:
+                    want |= ((x >> src) & 1) << p
+                    src += 1
+            assert int(out[plane]) == want, (k, plane, hex(F))
