@@ -56,8 +56,8 @@ UNIT = "Mbp/s"
 # What bounds the kernels that can take the largest share, from their ncu
 # captures (profiles/): the HBM fraction alone understates how close they are.
 LIMITERS = {
-    "radix_downsweep": "shared-memory ranking and staging: 40% issue, 36% DRAM, 0.46 of the copy bandwidth "
-                       "alone under ncu (profiles/radix_downsweep_short-1Mx100.md)",
+    "radix_downsweep": "shared-memory ranking and staging: 40% issue, 37% DRAM, 0.46 of the copy bandwidth "
+                       "alone under ncu, DRAM traffic 0.94 x algorithmic (profiles/radix_downsweep_short-1Mx100.md)",
 }
 
 

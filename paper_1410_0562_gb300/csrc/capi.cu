@@ -208,18 +208,11 @@ int device_init(sbwt_index* idx) {
         idx->own_stream = true;
     }
     idx->L.stream = idx->stream;
-    // The block sorts run ahead on the side stream and bound the pipeline
-    // (each is longer than the ranking, gather and Insert of a block): its
-    // CTAs go first whenever both streams have work waiting.
-    int prio_low = 0, prio_high = 0;
-    cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high);
-    if (cudaStreamCreateWithPriority(&idx->side, cudaStreamNonBlocking, prio_high) != cudaSuccess)
-        return SBWT_EDEVICE;
+    if (cudaStreamCreateWithFlags(&idx->side, cudaStreamNonBlocking) != cudaSuccess) return SBWT_EDEVICE;
     for (cudaEvent_t* e : {&idx->ev_fork, &idx->ev_join, &idx->ev_sorted[0], &idx->ev_sorted[1],
                            &idx->ev_consumed[0], &idx->ev_consumed[1]})
         if (cudaEventCreateWithFlags(e, cudaEventDisableTiming) != cudaSuccess) return SBWT_EDEVICE;
     suffix_sort_init();
-    insert_init();
     if (cudaMallocHost(&idx->h_err, sizeof(uint32_t)) != cudaSuccess) return SBWT_EDEVICE;
     if (cudaMallocHost(&idx->h_plan, kPlanCap * sizeof(PlanBlock)) != cudaSuccess) return SBWT_EDEVICE;
     if (cudaMallocHost(&idx->h_summary, sizeof(PlanSummary)) != cudaSuccess) return SBWT_EDEVICE;
@@ -715,9 +708,7 @@ int append_impl(sbwt_index* idx, const uint8_t* d_reads, const uint64_t* d_offse
             }
         }
         if (it == idx->graphs.end()) {
-            // the kernels keep the priority of the stream they were captured
-            // on (the block sorts first)
-            e = cudaGraphInstantiate(&g.exec, graph, cudaGraphInstantiateFlagUseNodePriority);
+            e = cudaGraphInstantiate(&g.exec, graph, 0);
             if (e != cudaSuccess) {
                 cudaGraphDestroy(graph);
                 L.recycle(g.log);

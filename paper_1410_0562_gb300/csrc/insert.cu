@@ -100,24 +100,6 @@ __device__ __forceinline__ void staged_range(const uint32_t* __restrict__ ins_i0
     b_hi = min(hi_row / rows_per_block, last);
 }
 
-// The old parts one superblock's windows read.  Its old rows are [O -
-// i_begin, O + 2^16 - i_end) (the rows below O that are not new, up to the
-// next superblock's first old row), and a window also reads the part after
-// its first one: parts [Pa, Pb] with Pb - Pa <= kBlocksPerSuper + 1, so at
-// most kBlocks blocks of 64 K rows.
-template <int K>
-struct OldRange {
-    static constexpr uint32_t kBlocks = (kBlocksPerSuper + 1) / K + 2;
-    static constexpr uint32_t kWords = kBlocks * Occ<K>::kWords;
-};
-
-// Shared memory of a 2-bit Insert CTA: the old range, then ten arrays of
-// kBlocksPerSuper words (new-row masks, planes and counts).
-template <int K>
-__host__ __device__ constexpr size_t insert_smem_bytes() {
-    return (size_t)OldRange<K>::kWords * 8 + 10 * (size_t)kBlocksPerSuper * 4;
-}
-
 // 64 old rows starting at row s, from the pair of parts holding them.
 __device__ __forceinline__ Window old_window_of(const OldPair& o, uint64_t s) {
     const uint32_t off = (uint32_t)(s & (kOccSpan - 1));
@@ -221,9 +203,6 @@ __device__ __forceinline__ void load_run(const IdxT* __restrict__ p, IdxT (&v)[k
 // One CTA builds one superblock of the next dictionary (kBlocksPerSuper
 // output parts of 64 rows, rows [O, O + 2^16)) from the new symbols
 // [ins_i0[S], ins_i0[S+1]) that land in it (bint_gather wrote that plan):
-//  0. the old blocks the superblock's windows read (OldRange) start to
-//     arrive in shared memory by asynchronous copies, which run while
-//     steps 1 and 2 do;
 //  1. the CTA reads those new symbols' rows g_sa[i] + i and codes (a run of
 //     consecutive ones per thread) and sets, per output part, the mask F of
 //     its new rows and their three planes at their rows (shared memory; a
@@ -244,7 +223,7 @@ __device__ __forceinline__ void load_run(const IdxT* __restrict__ p, IdxT (&v)[k
 // (staged_range, at most stage_blocks of them); without it, old_words is the
 // whole old dictionary and sb_first is 0.
 template <class IdxT, int kT, int K>
-__global__ void __launch_bounds__(kT, kT == 256 ? 3 : 2) insert_kernel(const unsigned long long* __restrict__ old_words,
+__global__ void __launch_bounds__(kT, kT == 256 ? 4 : 2) insert_kernel(const unsigned long long* __restrict__ old_words,
                                                     unsigned long long n_ext, const uint8_t* __restrict__ bint,
                                                     const IdxT* __restrict__ gsa, unsigned long long n_int,
                                                     const uint32_t* __restrict__ ins_i0,
@@ -253,13 +232,10 @@ __global__ void __launch_bounds__(kT, kT == 256 ? 3 : 2) insert_kernel(const uns
                                                     uint32_t* __restrict__ d_err, unsigned long long sb_first,
                                                     int staged, unsigned long long stage_blocks) {
     constexpr int kNB = kBlocksPerSuper, kPer = kNB / kT;
-    extern __shared__ __align__(16) unsigned long long ins_smem[];
-    unsigned long long* sOld = ins_smem;  // old blocks [q_lo, q_lo + q_n)
-    using Row = uint32_t[kNB];
-    Row* sF = reinterpret_cast<Row*>(ins_smem + OldRange<K>::kWords);  // [2]: new rows of each part (rows 0-31, 32-63); later its counts
-    Row* sD = sF + 2;  // [2]: terminator plane: of the new rows, later of the whole part
-    Row* sC = sF + 4;  // [4]: lo plane (words 0, 1) and hi plane (2, 3): of the new rows, then the part
-    Row* sP = sF + 8;  // [2]: new symbols before each part; later the block counters
+    __shared__ uint32_t sF[2][kNB];  // new rows of each part (rows 0-31, 32-63); later its counts
+    __shared__ uint32_t sD[2][kNB];  // terminator plane: of the new rows, later of the whole part
+    __shared__ uint32_t sC[4][kNB];  // lo plane (words 0, 1) and hi plane (2, 3): of the new rows, then the part
+    __shared__ uint32_t sP[2][kNB];  // new symbols before each part; later the block counters
     const int tid = threadIdx.x;
     const uint64_t S = sb_first + blockIdx.x;
     const uint64_t O = S << kSuperShift;
@@ -283,119 +259,116 @@ __global__ void __launch_bounds__(kT, kT == 256 ? 3 : 2) insert_kernel(const uns
         i_begin = min(i_begin, i_end);
     }
 
-    // 0. the old blocks of this superblock's windows, within those old_words
-    //    holds (a part outside them reads as zero and is flagged later)
-    uint64_t q_lo, q_n = 0;
-    {
-        constexpr uint64_t kSpan = 1ull << kSuperShift;
-        const uint64_t lo_row = O - min(i_begin, O);
-        const uint64_t hi_row = O + kSpan - min(i_end, O + kSpan);
-        const uint64_t pa = lo_row >> kOccShift;
-        const uint64_t pb = min((hi_row >> kOccShift) + 1, np_old - 1);
-        const uint64_t qa = max(pa / K, base), qb = min(pb / K, base + avail - 1);
-        q_lo = qa;
-        if (qa <= qb) q_n = min(qb - qa + 1, (uint64_t)OldRange<K>::kBlocks);
-        const unsigned long long* src = old_words + (qa - base) * Occ<K>::kWords;
-        const uint32_t words = (uint32_t)q_n * Occ<K>::kWords;
-        if constexpr (K == 1) {  // 32-byte blocks: 16-byte copies
-            for (uint32_t x = tid; x < words / 2; x += kT) cp_async16(sOld + 2 * x, src + 2 * x);
-        } else {
-            for (uint32_t x = tid; x < words; x += kT) cp_async8(sOld + x, src + x);
-        }
-        cp_async_commit();
-    }
     __syncthreads();
 
-    // 1. the new rows of every part of this superblock: each thread takes a
-    //    run of kRun consecutive new symbols (runs start at multiples of
+    // 1. the new rows of every part of this superblock: each thread takes
+    //    runs of kRun consecutive new symbols (runs start at multiples of
     //    kRun, so the superblock's first and last runs may hold fewer; a
-    //    whole run's g_sa and codes arrive as vector loads; consecutive
-    //    rows, so a run touches one or two parts when the new rows are
-    //    dense), gathers their bits per part in registers and ORs each
-    //    part's bits into shared memory once
+    //    whole run's g_sa and codes arrive as vector loads).  Their rows
+    //    increase, so a run touches one or two parts when new rows are
+    //    dense: the thread gathers each part's bits (new-row mask,
+    //    terminator and code planes, as 32-bit halves) in registers and ORs
+    //    them into shared memory once per part.  A run over one or two
+    //    parts takes one pass per part over all of its symbols, so the lanes
+    //    of a warp stay together (a divergent part change in the middle of
+    //    a run cost more than the passes).
+    uint32_t cj = 0xFFFFFFFFu;  // the part being gathered
+    uint32_t f0 = 0, f1 = 0, d0 = 0, d1 = 0, l0 = 0, l1 = 0, h0 = 0, h1 = 0;
+    auto flush = [&]() {
+        if (cj == 0xFFFFFFFFu) return;
+        if (f0) atomicOr(&sF[0][cj], f0);
+        if (f1) atomicOr(&sF[1][cj], f1);
+        if (d0) atomicOr(&sD[0][cj], d0);
+        if (d1) atomicOr(&sD[1][cj], d1);
+        if (l0) atomicOr(&sC[0][cj], l0);
+        if (l1) atomicOr(&sC[1][cj], l1);
+        if (h0) atomicOr(&sC[2][cj], h0);
+        if (h1) atomicOr(&sC[3][cj], h1);
+        f0 = f1 = d0 = d1 = l0 = l1 = h0 = h1 = 0;
+    };
+    // row q of the current part with code x (a terminator when x is kBintDollar)
+    auto mark = [&](uint32_t q, uint32_t x, uint32_t on) {
+        const uint32_t b = on << (q & 31u);
+        const uint32_t blo = q < 32u ? b : 0u, bhi = q < 32u ? 0u : b;
+        const uint32_t isd = x == kBintDollar ? 0xFFFFFFFFu : 0u;
+        const uint32_t m1 = (x & 1u) ? ~isd : 0u, m2 = (x & 2u) ? ~isd : 0u;
+        f0 |= blo;
+        f1 |= bhi;
+        d0 |= blo & isd;
+        d1 |= bhi & isd;
+        l0 |= blo & m1;
+        l1 |= bhi & m1;
+        h0 |= blo & m2;
+        h1 |= bhi & m2;
+    };
     for (uint64_t base = (i_begin & ~(uint64_t)(kRun - 1)) + (uint64_t)tid * kRun; base < i_end;
          base += (uint64_t)kT * kRun) {
         IdxT gv[kRun];
         uint32_t xs[kRun];
+        uint32_t valid;
         if (base >= i_begin && base + kRun <= i_end) {
             load_run<IdxT>(gsa + base, gv);
             const uint2 b8 = *reinterpret_cast<const uint2*>(bint + base);
 #pragma unroll
             for (int u = 0; u < kRun; ++u) xs[u] = ((u < 4 ? b8.x : b8.y) >> (8 * (u & 3))) & 0xFFu;
+            valid = (1u << kRun) - 1u;
         } else {
+            valid = 0;
 #pragma unroll
             for (int u = 0; u < kRun; ++u) {
                 const uint64_t i = base + u;
                 const bool in = i >= i_begin && i < i_end;
                 gv[u] = in ? gsa[i] : (IdxT)0;
                 xs[u] = in ? bint[i] : 0u;
+                valid |= (uint32_t)in << u;
             }
         }
         // rows inside the superblock (row arithmetic in the index type: a
-        // 32-bit index has fewer than 2^32 rows); the run's valid symbols
-        uint32_t loc[kRun], valid = 0, j_lo = 0xFFFFFFFFu, j_hi = 0;
+        // 32-bit index has fewer than 2^32 rows)
+        uint32_t loc[kRun], j_lo = 0xFFFFFFFFu, j_hi = 0;
+        const IdxT rel = (IdxT)base - (IdxT)O;
 #pragma unroll
         for (int u = 0; u < kRun; ++u) {
-            const uint64_t i = base + u;
-            const IdxT local = gv[u] + (IdxT)i - (IdxT)O;
+            const IdxT local = gv[u] + rel + (IdxT)u;
             loc[u] = (uint32_t)local;
-            if (i >= i_begin && i < i_end) {
+            if ((valid >> u) & 1u) {
                 if (local >= (IdxT)(1u << kSuperShift)) {  // not in this superblock: the plan is inconsistent
                     atomicOr(d_err, 1024u);
+                    valid &= ~(1u << u);
                 } else {
-                    valid |= 1u << u;
                     j_lo = min(j_lo, loc[u] >> kOccShift);
                     j_hi = max(j_hi, loc[u] >> kOccShift);
                 }
             }
         }
         if (!valid) continue;
-        auto flush = [&](uint32_t cj, unsigned long long f, unsigned long long dm, unsigned long long lo,
-                         unsigned long long hi) {
-            if ((uint32_t)f) atomicOr(&sF[0][cj], (uint32_t)f);
-            if ((uint32_t)(f >> 32)) atomicOr(&sF[1][cj], (uint32_t)(f >> 32));
-            if ((uint32_t)dm) atomicOr(&sD[0][cj], (uint32_t)dm);
-            if ((uint32_t)(dm >> 32)) atomicOr(&sD[1][cj], (uint32_t)(dm >> 32));
-            if ((uint32_t)lo) atomicOr(&sC[0][cj], (uint32_t)lo);
-            if ((uint32_t)(lo >> 32)) atomicOr(&sC[1][cj], (uint32_t)(lo >> 32));
-            if ((uint32_t)hi) atomicOr(&sC[2][cj], (uint32_t)hi);
-            if ((uint32_t)(hi >> 32)) atomicOr(&sC[3][cj], (uint32_t)(hi >> 32));
-        };
-        if (j_lo == j_hi) {  // the whole run in one part
-            unsigned long long f = 0, dm = 0, lo = 0, hi = 0;
+        if (j_hi - j_lo < 2) {
+            // one or two parts (dense new rows): a pass over the run per
+            // part, every pass the same for all lanes, so a warp does not
+            // split at each part change
+            for (uint32_t jj = j_lo; jj <= j_hi; ++jj) {
+                if (jj != cj) {
+                    flush();
+                    cj = jj;
+                }
 #pragma unroll
-            for (int u = 0; u < kRun; ++u) {
-                const unsigned long long bit = (unsigned long long)((valid >> u) & 1u) << (loc[u] & 63u);
-                f |= bit;
-                dm |= xs[u] == kBintDollar ? bit : 0ull;
-                lo |= (xs[u] != kBintDollar && (xs[u] & 1u)) ? bit : 0ull;
-                hi |= (xs[u] != kBintDollar && (xs[u] & 2u)) ? bit : 0ull;
+                for (int u = 0; u < kRun; ++u)
+                    mark(loc[u] & 63u, xs[u], ((valid >> u) & 1u) & (uint32_t)((loc[u] >> kOccShift) == jj));
             }
-            flush(j_lo, f, dm, lo, hi);
             continue;
         }
-        uint32_t cj = 0xFFFFFFFFu;
-        unsigned long long f = 0, dm = 0, lo = 0, hi = 0;
 #pragma unroll
         for (int u = 0; u < kRun; ++u) {
             if (!((valid >> u) & 1u)) continue;
-            const uint32_t j = loc[u] >> kOccShift, q = loc[u] & 63u;
+            const uint32_t j = loc[u] >> kOccShift;
             if (j != cj) {
-                if (cj != 0xFFFFFFFFu) flush(cj, f, dm, lo, hi);
+                flush();
                 cj = j;
-                f = dm = lo = hi = 0;
             }
-            const unsigned long long bit = 1ull << q;
-            f |= bit;
-            if (xs[u] == kBintDollar) {
-                dm |= bit;
-            } else {
-                if (xs[u] & 1u) lo |= bit;
-                if (xs[u] & 2u) hi |= bit;
-            }
+            mark(loc[u] & 63u, xs[u], 1u);
         }
-        flush(cj, f, dm, lo, hi);
     }
+    flush();
     __syncthreads();
 
     // 2. new symbols before each part (parts kPer * tid .. in order)
@@ -417,11 +390,9 @@ __global__ void __launch_bounds__(kT, kT == 256 ? 3 : 2) insert_kernel(const uns
         // two new symbols on one row, or one outside this superblock
         if (tid == 0 && all != (uint32_t)(i_end - i_begin)) atomicOr(d_err, 1024u);
     }
-    cp_async_wait_all();
     __syncthreads();
 
-    // 3. build parts tid, tid + kT, ...; keep them in shared memory (the
-    //    old parts of each window come from the staged range)
+    // 3. build parts tid, tid + kT, ...; keep them in shared memory
 #pragma unroll
     for (int bb = 0; bb < kPer; ++bb) {
         const int j = tid + bb * kT;
@@ -439,7 +410,7 @@ __global__ void __launch_bounds__(kT, kT == 256 ? 3 : 2) insert_kernel(const uns
             if (o <= n_new) atomicOr(d_err, 1024u);
             s_old = inew > o ? 0ull : (uint64_t)n_ext;
         }
-        const OldPair op = old_pair<K>(sOld, np_old, s_old, q_lo, q_n, d_err);
+        const OldPair op = old_pair<K>(old_words, np_old, s_old, base, avail, d_err);
         const unsigned long long F = (unsigned long long)sF[0][j] | ((unsigned long long)sF[1][j] << 32);
         Window w = spread_old(old_window_of(op, s_old), F);
         w.lo |= (unsigned long long)sC[0][j] | ((unsigned long long)sC[1][j] << 32);
@@ -899,27 +870,7 @@ void super_scan(Launcher& L, const uint32_t* sb_tot, uint64_t nsb, unsigned long
                 kScanThreads, 0, super, (unsigned long long)nsb, chunk_tot);
 }
 
-template <class IdxT, int kT, int K>
-void insert_attr() {
-    cudaFuncSetAttribute(insert_kernel<IdxT, kT, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)insert_smem_bytes<K>());
-}
-template <int kT, int K>
-void insert_attrs() {
-    insert_attr<uint32_t, kT, K>();
-    insert_attr<unsigned long long, kT, K>();
-}
-
 }  // namespace
-
-void insert_init() {
-    insert_attrs<kInsertThreads, 1>();
-    insert_attrs<kInsertThreads, 2>();
-    insert_attrs<kInsertThreads, 4>();
-    insert_attrs<kInsertThreadsSparse, 1>();
-    insert_attrs<kInsertThreadsSparse, 2>();
-    insert_attrs<kInsertThreadsSparse, 4>();
-}
 
 // Old blocks a chunk can read: the chunk's rows in blocks plus a few; a
 // dictionary smaller than a chunk needs only its own blocks.
@@ -983,14 +934,12 @@ void launch_insert(Launcher& L, const void* old_blocks, uint64_t n_ext, const ui
                              : (occ_k == 4 ? insert_kernel<IdxT, kInsertThreadsSparse, 4>
                                            : (occ_k == 2 ? insert_kernel<IdxT, kInsertThreadsSparse, 2>
                                                          : insert_kernel<IdxT, kInsertThreadsSparse, 1>));
-    const size_t smem = occ_k == 4 ? insert_smem_bytes<4>() : (occ_k == 2 ? insert_smem_bytes<2>()
-                                                                           : insert_smem_bytes<1>());
     const auto* old_w = static_cast<const unsigned long long*>(old_blocks);
     auto* new_w = static_cast<unsigned long long*>(new_blocks);
     if (!stage) {
         const double bytes = bb * dict_blocks(n_ext, occ_k) + (1.0 + sizeof(IdxT)) * n_int +
                              bb * dict_blocks(n_new, occ_k) + 4.0 * (nsb + 1);
-        SBWT_LAUNCH(L, "insert_merge", bytes, 0, nullptr, kern, (unsigned)nsb, threads, smem, old_w,
+        SBWT_LAUNCH(L, "insert_merge", bytes, 0, nullptr, kern, (unsigned)nsb, threads, 0, old_w,
                     (unsigned long long)n_ext, bint, gsa, (unsigned long long)n_int, ins_i0, new_w,
                     (unsigned long long)n_new, sb_tot, d_err, 0ull, 0, 0ull);
     } else {
@@ -1009,7 +958,7 @@ void launch_insert(Launcher& L, const void* old_blocks, uint64_t n_ext, const ui
                         (unsigned long long)s1, stage, (unsigned long long)stage_blocks, d_err);
             SBWT_LAUNCH(L, "insert_merge", 2.0 * rows / (64.0 * occ_k) * bb + (1.0 + sizeof(IdxT)) * rows *
                                               ((double)n_int / (double)n_new), 0, nullptr, kern, (unsigned)(s1 - s0),
-                        threads, smem, stage, (unsigned long long)n_ext, bint, gsa, (unsigned long long)n_int, ins_i0,
+                        threads, 0, stage, (unsigned long long)n_ext, bint, gsa, (unsigned long long)n_int, ins_i0,
                         new_w, (unsigned long long)n_new, sb_tot, d_err, (unsigned long long)s0, 1,
                         (unsigned long long)stage_blocks);
             s1 = s0;

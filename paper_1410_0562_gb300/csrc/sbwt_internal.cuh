@@ -388,18 +388,6 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, uint32_t pari
 }
 constexpr uint32_t kMbarSpinLimit = 1u << 20;
 
-// Per-thread asynchronous copies global -> shared (cp.async, 16 bytes with
-// both addresses 16-byte aligned, or 8 bytes 8-byte aligned); a thread's
-// copies are complete once it has passed cp_async_wait_all.
-__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-
 // CTAs per launch for a persistent kernel: SMs x resident CTAs per SM.
 unsigned persistent_ctas(const void* kernel, int threads, size_t smem);
 

@@ -38,7 +38,6 @@ struct SuffixSortBuffers {
     uint32_t* err;                        // error flags (bits 2..7)
 };
 void suffix_sort_init();  // once per device (includes radix_init)
-void insert_init();       // once per device: the Insert kernels' shared memory
 // code_bits: 2 (alphabets of up to 4 symbols) or 4 (5 to 16 symbols)
 uint32_t suffix_sort_rounds(uint32_t max_len, int code_bits);
 size_t suffix_sort_log_slots(uint32_t max_len, int code_bits);

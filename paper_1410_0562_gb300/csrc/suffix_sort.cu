@@ -74,7 +74,7 @@ constexpr uint32_t kLSlots = kLCap + kLCap / kLItems;
 constexpr uint32_t kNone = 0xFFFFFFFFu;
 constexpr uint32_t kFallback = 0xFFFFFFFEu;  // u.cnt of a unit the warp local sort left to the CTA one
 constexpr uint32_t kShortFlag = 0x80000000u;  // digit flag: the bucket holds suffixes with len < P
-constexpr int kScanThreads = 256;  // the unit scan: one small CTA, kScanPer windows per thread
+constexpr int kScanThreads = 1024;  // the unit scan: one CTA, kScanPer windows per thread
 // Buckets: the first P codes and min(len, P); their dense numbers need
 // kDigitBits bits (5,592,405 valid pairs for 11 two-bit codes, 1,118,481 for
 // 5 four-bit codes).  Two long suffixes share a bucket iff their keys agree
@@ -340,7 +340,7 @@ __global__ void __launch_bounds__(kThreads) sa_unit_begin_kernel(const uint32_t*
 }
 
 // kScanPer consecutive windows of one field (vector accesses when whole)
-constexpr int kScanPer = 16;
+constexpr int kScanPer = 8;
 static_assert(kScanPer % 4 == 0, "whole 16-byte vectors");
 __device__ __forceinline__ void load_run(const uint32_t* p, uint32_t w0, uint32_t nwin, uint32_t fill,
                                          uint32_t (&v)[kScanPer]) {

@@ -135,6 +135,7 @@ struct uint4 {
 struct uint2 {
     unsigned x, y;
 };
+static inline uint2 make_uint2(unsigned a, unsigned b) { return uint2{a, b}; }
 static inline uint4 make_uint4(unsigned a, unsigned b, unsigned c, unsigned d) { return uint4{a, b, c, d}; }
 
 template <class T>

@@ -9,20 +9,7 @@
 #include "dict.inc"
 #include "scan.inc"
 
-// the asynchronous global -> shared copies, done at once
-static inline void cp_async16(void* dst, const void* src) { memcpy(dst, src, 16); }
-static inline void cp_async8(void* dst, const void* src) { memcpy(dst, src, 8); }
-static inline void cp_async_commit() {}
-static inline void cp_async_wait_all() {}
-
-// a CTA's dynamic shared memory (CTAs run one after another)
-alignas(16) static unsigned long long g_ins_smem[96 * 1024 / 8];
-
 #include "insert.inc"
-
-static_assert(insert_smem_bytes<1>() <= sizeof(g_ins_smem) && insert_smem_bytes<2>() <= sizeof(g_ins_smem) &&
-                  insert_smem_bytes<4>() <= sizeof(g_ins_smem),
-              "dynamic shared memory of the Insert kernel");
 
 // One Insert launch: nsb CTAs of kInsertThreads threads over the old
 // dictionary (n_ext rows, blocks of 64 k rows as 64-bit words), the new

@@ -46,8 +46,6 @@ def emu(tmp_path_factory):
     (d / "scan.inc").write_text(_cut(hdr, "struct SumOp {", "// Launch bookkeeping"))
     kern = _cut(ins, "constexpr int kThreads = 256;", "// ------------------------------------------------"
                                                       "---------------------------\n// The same merge")
-    kern = kern.replace("extern __shared__ __align__(16) unsigned long long ins_smem[];",
-                        "unsigned long long* ins_smem = g_ins_smem;")
     (d / "insert.inc").write_text(kern)
     lib = d / "libinsemu.so"
     subprocess.check_call(["g++", "-O1", "-std=c++20", "-shared", "-fPIC", "-pthread", "-I", str(d), "-o", str(lib),
