@@ -1035,15 +1035,17 @@ __global__ void __launch_bounds__(kWWarps * 32) sa_local_sort_warp_kernel(
                 bs_carry = __shfl_sync(0xffffffffu, bs, 31);
                 if (in) {
                     const uint32_t t = T.t[q];
-                    uint32_t lt_pair = 0, lt_key = 0, eq = 0;
+                    // a bucket's members are in t order in the chunk, so the
+                    // equal keys below t are the equal keys at slots below q
+                    uint32_t lt_key = 0, eq = 0, eq_below = 0;
                     for (uint32_t x = bs; x < cut; ++x) {
                         const unsigned long long kx = T.key[x];
                         if ((kx >> seg_shift) != B) break;
-                        const uint32_t tx = T.t[x];
                         lt_key += kx < K;
                         eq += kx == K;
-                        lt_pair += (kx < K || (kx == K && tx < t)) ? 1u : 0u;
+                        eq_below += (kx == K && x < q) ? 1u : 0u;
                     }
+                    const uint32_t lt_pair = lt_key + eq_below;
                     const uint32_t p = bs + lt_pair;
                     const bool unresolved = (uint32_t)(K & 31) >= kH0;
                     const uint32_t hp = unresolved ? bs + lt_key : p;
@@ -1293,15 +1295,17 @@ __global__ void __launch_bounds__(kWWarps * 32) sa_round_local_warp_kernel(
             bs_carry = __shfl_sync(0xffffffffu, bs, 31);
             if (in) {
                 const uint32_t t = T.t[q];
-                uint32_t lt_pair = 0, lt_key = 0, eq = 0;
+                // an old group's members are listed in t order, so the equal
+                // keys below t are the equal keys at slots below q
+                uint32_t lt_key = 0, eq = 0, eq_below = 0;
                 for (uint32_t x = bs; x < cnt; ++x) {
                     const unsigned long long kx = T.key[x];
                     if ((uint32_t)(kx >> 32) != here) break;
-                    const uint32_t tx = T.t[x];
                     lt_key += kx < K;
                     eq += kx == K;
-                    lt_pair += (kx < K || (kx == K && tx < t)) ? 1u : 0u;
+                    eq_below += (kx == K && x < q) ? 1u : 0u;
                 }
+                const uint32_t lt_pair = lt_key + eq_below;
                 const uint32_t row = here + lt_pair;
                 if (row < n && t < n) {
                     sa[row] = t;
