@@ -251,8 +251,13 @@ __global__ void __launch_bounds__(kThreads) compute_ranks_seg_kernel(const uint3
 // r_i = g_sa[i] + i of the next dictionary (strictly increasing in i), and
 // ins_i0[S] = |{i : r_i < S * 2^super_shift}| for S = 0 .. nsb, so the CTA
 // that builds superblock S takes the new symbols [ins_i0[S], ins_i0[S+1]).
-// Thread i writes the entries S with r_{i-1} < S * 2^super_shift <= r_i
-// (all S up to r_0 for i = 0; the last thread also those past r_{n-1}).
+// Element i writes the entries S with r_{i-1} < S * 2^super_shift <= r_i
+// (all S up to r_0 for i = 0; the last element also those past r_{n-1}).
+// A thread takes kGather consecutive elements: their SA entries arrive as
+// one vector, and all of their random reads (g, the text word and the
+// terminator word of each) are in flight together.
+constexpr int kGather = 4;
+
 template <class IdxT, int kB>
 __global__ void __launch_bounds__(kThreads) bint_gather_kernel(const uint32_t* __restrict__ text,
                                                                const uint32_t* __restrict__ term,
@@ -262,30 +267,64 @@ __global__ void __launch_bounds__(kThreads) bint_gather_kernel(const uint32_t* _
                                                                uint8_t* __restrict__ bint,
                                                                IdxT* __restrict__ gsa, uint32_t* __restrict__ ins_i0,
                                                                unsigned long long nsb, int super_shift) {
-    const uint32_t i = blockIdx.x * kThreads + threadIdx.x;
-    const bool valid = i < n;
-    unsigned long long r = 0;
-    if (valid) {
-        const uint32_t t = sa[i] < n ? sa[i] : 0u;
-        const uint64_t P = base + t;
-        bint[i] = (t == 0 || is_term(term, P - 1)) ? kBintDollar : (uint8_t)text_code_b<kB>(text, P - 1);
-        const IdxT v = g[t];
-        gsa[i] = v;
-        r = (unsigned long long)v + i;
+    const uint32_t i0 = (blockIdx.x * kThreads + threadIdx.x) * kGather;
+    const bool whole = i0 + kGather <= n;
+    uint32_t t[kGather];
+    if (whole) {
+        const uint4 s4 = *reinterpret_cast<const uint4*>(sa + i0);
+        t[0] = s4.x, t[1] = s4.y, t[2] = s4.z, t[3] = s4.w;
+    } else {
+#pragma unroll
+        for (int u = 0; u < kGather; ++u) t[u] = i0 + u < n ? sa[i0 + u] : 0u;
+    }
+    IdxT v[kGather];
+    uint32_t code[kGather];
+#pragma unroll
+    for (int u = 0; u < kGather; ++u) {
+        t[u] = t[u] < n ? t[u] : 0u;
+        const uint64_t P = base + t[u];
+        v[u] = (i0 + u < n) ? g[t[u]] : (IdxT)0;
+        code[u] = (t[u] == 0 || is_term(term, P - 1)) ? kBintDollar : text_code_b<kB>(text, P - 1);
+    }
+    if (whole) {
+        *reinterpret_cast<uint32_t*>(bint + i0) = code[0] | (code[1] << 8) | (code[2] << 16) | (code[3] << 24);
+        if constexpr (sizeof(IdxT) == 4) {
+            *reinterpret_cast<uint4*>(gsa + i0) = make_uint4(v[0], v[1], v[2], v[3]);
+        } else {
+            reinterpret_cast<ulonglong2*>(gsa + i0)[0] = make_ulonglong2(v[0], v[1]);
+            reinterpret_cast<ulonglong2*>(gsa + i0)[1] = make_ulonglong2(v[2], v[3]);
+        }
+    } else {
+#pragma unroll
+        for (int u = 0; u < kGather; ++u)
+            if (i0 + u < n) {
+                bint[i0 + u] = (uint8_t)code[u];
+                gsa[i0 + u] = v[u];
+            }
     }
     if (ins_i0 == nullptr) return;
-    // every lane of the warp is still here (the grid is whole warps)
-    unsigned long long prev = __shfl_up_sync(0xffffffffu, r, 1);
-    if (!valid) return;
-    if ((threadIdx.x & 31) == 0 && i > 0) {
-        const uint32_t tp = sa[i - 1] < n ? sa[i - 1] : 0u;
-        prev = (unsigned long long)g[tp] + (i - 1);
+    // r of the element before this thread's first: the previous lane's last
+    // (every lane of the warp is still here: the grid is whole warps)
+    unsigned long long r[kGather];
+#pragma unroll
+    for (int u = 0; u < kGather; ++u) r[u] = (unsigned long long)v[u] + i0 + u;
+    unsigned long long prev = __shfl_up_sync(0xffffffffu, r[kGather - 1], 1);
+    if (i0 >= n) return;
+    if ((threadIdx.x & 31) == 0 && i0 > 0) {
+        const uint32_t tp = sa[i0 - 1] < n ? sa[i0 - 1] : 0u;
+        prev = (unsigned long long)g[tp] + (i0 - 1);
     }
-    const unsigned long long s_lo = i == 0 ? 0ull : (prev >> super_shift) + 1;
-    const unsigned long long s_hi = min(r >> super_shift, nsb);
-    for (unsigned long long S = s_lo; S <= s_hi; ++S) ins_i0[S] = i;
-    if (i == n - 1)
-        for (unsigned long long S = (r >> super_shift) + 1; S <= nsb; ++S) ins_i0[S] = n;
+#pragma unroll
+    for (int u = 0; u < kGather; ++u) {
+        const uint32_t i = i0 + u;
+        if (i >= n) break;
+        const unsigned long long s_lo = i == 0 ? 0ull : (prev >> super_shift) + 1;
+        const unsigned long long s_hi = min(r[u] >> super_shift, nsb);
+        for (unsigned long long S = s_lo; S <= s_hi; ++S) ins_i0[S] = i;
+        if (i == n - 1)
+            for (unsigned long long S = (r[u] >> super_shift) + 1; S <= nsb; ++S) ins_i0[S] = n;
+        prev = r[u];
+    }
 }
 
 // rank(c, k) queries, codes 0..kCodes-1, or kCodes for the terminator.
@@ -497,7 +536,8 @@ void launch_bint_gather(Launcher& L, const uint32_t* text, const uint32_t* term,
     // random g sector, B_int and g_sa writes; 4 bytes per plan entry
     auto* const kern = code_bits == 4 ? bint_gather_kernel<IdxT, 4> : bint_gather_kernel<IdxT, 2>;
     SBWT_LAUNCH(L, "bint_gather", (double)n * (4 + 4 + 4 + 32 + 1 + sizeof(IdxT)) + (ins_i0 ? 4.0 * (nsb + 1) : 0.0),
-                0, nullptr, kern, ceil_div_u(n, kThreads), kThreads, 0, text, term, (unsigned long long)base, sa, g,
+                0, nullptr, kern, ceil_div_u(n, (uint64_t)kThreads * kGather), kThreads, 0, text, term,
+                (unsigned long long)base, sa, g,
                 n, bint, gsa, ins_i0, (unsigned long long)nsb, super_shift);
 }
 
