@@ -271,104 +271,127 @@ __global__ void __launch_bounds__(kT, kT == 256 ? 4 : 2) insert_kernel(const uns
     //    them into shared memory once per part.  A run over one or two
     //    parts takes one pass per part over all of its symbols, so the lanes
     //    of a warp stay together (a divergent part change in the middle of
-    //    a run cost more than the passes).
-    uint32_t cj = 0xFFFFFFFFu;  // the part being gathered
-    uint32_t f0 = 0, f1 = 0, d0 = 0, d1 = 0, l0 = 0, l1 = 0, h0 = 0, h1 = 0;
-    auto flush = [&]() {
-        if (cj == 0xFFFFFFFFu) return;
-        if (f0) atomicOr(&sF[0][cj], f0);
-        if (f1) atomicOr(&sF[1][cj], f1);
-        if (d0) atomicOr(&sD[0][cj], d0);
-        if (d1) atomicOr(&sD[1][cj], d1);
-        if (l0) atomicOr(&sC[0][cj], l0);
-        if (l1) atomicOr(&sC[1][cj], l1);
-        if (h0) atomicOr(&sC[2][cj], h0);
-        if (h1) atomicOr(&sC[3][cj], h1);
-        f0 = f1 = d0 = d1 = l0 = l1 = h0 = h1 = 0;
-    };
-    // row q of the current part with code x (a terminator when x is kBintDollar)
-    auto mark = [&](uint32_t q, uint32_t x, uint32_t on) {
-        const uint32_t b = on << (q & 31u);
-        const uint32_t blo = q < 32u ? b : 0u, bhi = q < 32u ? 0u : b;
-        const uint32_t isd = x == kBintDollar ? 0xFFFFFFFFu : 0u;
-        const uint32_t m1 = (x & 1u) ? ~isd : 0u, m2 = (x & 2u) ? ~isd : 0u;
-        f0 |= blo;
-        f1 |= bhi;
-        d0 |= blo & isd;
-        d1 |= bhi & isd;
-        l0 |= blo & m1;
-        l1 |= bhi & m1;
-        h0 |= blo & m2;
-        h1 |= bhi & m2;
-    };
-    for (uint64_t base = (i_begin & ~(uint64_t)(kRun - 1)) + (uint64_t)tid * kRun; base < i_end;
-         base += (uint64_t)kT * kRun) {
-        IdxT gv[kRun];
-        uint32_t xs[kRun];
-        uint32_t valid;
-        if (base >= i_begin && base + kRun <= i_end) {
-            load_run<IdxT>(gsa + base, gv);
-            const uint2 b8 = *reinterpret_cast<const uint2*>(bint + base);
+    //    a run cost more than the passes).  Sparse new rows (the 256-thread
+    //    form) skip the runs.
+    if constexpr (kT == kInsertThreadsSparse) {
+        // sparse new rows (the CTA size the launcher picks for them): one
+        // symbol per thread and step, its bits ORed into shared memory
+        // directly (new rows rarely share a part, so the atomics rarely meet)
+        for (uint64_t i = i_begin + tid; i < i_end; i += kT) {
+            const IdxT local = gsa[i] + (IdxT)i - (IdxT)O;
+            if (local >= (IdxT)(1u << kSuperShift)) {  // not in this superblock: the plan is inconsistent
+                atomicOr(d_err, 1024u);
+                continue;
+            }
+            const uint32_t l = (uint32_t)local, j = l >> kOccShift, h = (l >> 5) & 1u, bit = 1u << (l & 31u);
+            const uint32_t x = bint[i];
+            atomicOr(&sF[h][j], bit);
+            if (x == kBintDollar) {
+                atomicOr(&sD[h][j], bit);
+            } else {
+                if (x & 1u) atomicOr(&sC[h][j], bit);
+                if (x & 2u) atomicOr(&sC[2 + h][j], bit);
+            }
+        }
+    } else {
+        uint32_t cj = 0xFFFFFFFFu;  // the part being gathered
+        uint32_t f0 = 0, f1 = 0, d0 = 0, d1 = 0, l0 = 0, l1 = 0, h0 = 0, h1 = 0;
+        auto flush = [&]() {
+            if (cj == 0xFFFFFFFFu) return;
+            if (f0) atomicOr(&sF[0][cj], f0);
+            if (f1) atomicOr(&sF[1][cj], f1);
+            if (d0) atomicOr(&sD[0][cj], d0);
+            if (d1) atomicOr(&sD[1][cj], d1);
+            if (l0) atomicOr(&sC[0][cj], l0);
+            if (l1) atomicOr(&sC[1][cj], l1);
+            if (h0) atomicOr(&sC[2][cj], h0);
+            if (h1) atomicOr(&sC[3][cj], h1);
+            f0 = f1 = d0 = d1 = l0 = l1 = h0 = h1 = 0;
+        };
+        // row q of the current part with code x (a terminator when x is kBintDollar)
+        auto mark = [&](uint32_t q, uint32_t x, uint32_t on) {
+            const uint32_t b = on << (q & 31u);
+            const uint32_t blo = q < 32u ? b : 0u, bhi = q < 32u ? 0u : b;
+            const uint32_t isd = x == kBintDollar ? 0xFFFFFFFFu : 0u;
+            const uint32_t m1 = (x & 1u) ? ~isd : 0u, m2 = (x & 2u) ? ~isd : 0u;
+            f0 |= blo;
+            f1 |= bhi;
+            d0 |= blo & isd;
+            d1 |= bhi & isd;
+            l0 |= blo & m1;
+            l1 |= bhi & m1;
+            h0 |= blo & m2;
+            h1 |= bhi & m2;
+        };
+        for (uint64_t base = (i_begin & ~(uint64_t)(kRun - 1)) + (uint64_t)tid * kRun; base < i_end;
+             base += (uint64_t)kT * kRun) {
+            IdxT gv[kRun];
+            uint32_t xs[kRun];
+            uint32_t valid;
+            if (base >= i_begin && base + kRun <= i_end) {
+                load_run<IdxT>(gsa + base, gv);
+                const uint2 b8 = *reinterpret_cast<const uint2*>(bint + base);
 #pragma unroll
-            for (int u = 0; u < kRun; ++u) xs[u] = ((u < 4 ? b8.x : b8.y) >> (8 * (u & 3))) & 0xFFu;
-            valid = (1u << kRun) - 1u;
-        } else {
-            valid = 0;
+                for (int u = 0; u < kRun; ++u) xs[u] = ((u < 4 ? b8.x : b8.y) >> (8 * (u & 3))) & 0xFFu;
+                valid = (1u << kRun) - 1u;
+            } else {
+                valid = 0;
+#pragma unroll
+                for (int u = 0; u < kRun; ++u) {
+                    const uint64_t i = base + u;
+                    const bool in = i >= i_begin && i < i_end;
+                    gv[u] = in ? gsa[i] : (IdxT)0;
+                    xs[u] = in ? bint[i] : 0u;
+                    valid |= (uint32_t)in << u;
+                }
+            }
+            // rows inside the superblock (row arithmetic in the index type: a
+            // 32-bit index has fewer than 2^32 rows)
+            uint32_t loc[kRun], j_lo = 0xFFFFFFFFu, j_hi = 0;
+            const IdxT rel = (IdxT)base - (IdxT)O;
 #pragma unroll
             for (int u = 0; u < kRun; ++u) {
-                const uint64_t i = base + u;
-                const bool in = i >= i_begin && i < i_end;
-                gv[u] = in ? gsa[i] : (IdxT)0;
-                xs[u] = in ? bint[i] : 0u;
-                valid |= (uint32_t)in << u;
-            }
-        }
-        // rows inside the superblock (row arithmetic in the index type: a
-        // 32-bit index has fewer than 2^32 rows)
-        uint32_t loc[kRun], j_lo = 0xFFFFFFFFu, j_hi = 0;
-        const IdxT rel = (IdxT)base - (IdxT)O;
-#pragma unroll
-        for (int u = 0; u < kRun; ++u) {
-            const IdxT local = gv[u] + rel + (IdxT)u;
-            loc[u] = (uint32_t)local;
-            if ((valid >> u) & 1u) {
-                if (local >= (IdxT)(1u << kSuperShift)) {  // not in this superblock: the plan is inconsistent
-                    atomicOr(d_err, 1024u);
-                    valid &= ~(1u << u);
-                } else {
-                    j_lo = min(j_lo, loc[u] >> kOccShift);
-                    j_hi = max(j_hi, loc[u] >> kOccShift);
+                const IdxT local = gv[u] + rel + (IdxT)u;
+                loc[u] = (uint32_t)local;
+                if ((valid >> u) & 1u) {
+                    if (local >= (IdxT)(1u << kSuperShift)) {  // not in this superblock: the plan is inconsistent
+                        atomicOr(d_err, 1024u);
+                        valid &= ~(1u << u);
+                    } else {
+                        j_lo = min(j_lo, loc[u] >> kOccShift);
+                        j_hi = max(j_hi, loc[u] >> kOccShift);
+                    }
                 }
             }
-        }
-        if (!valid) continue;
-        if (j_hi - j_lo < 2) {
-            // one or two parts (dense new rows): a pass over the run per
-            // part, every pass the same for all lanes, so a warp does not
-            // split at each part change
-            for (uint32_t jj = j_lo; jj <= j_hi; ++jj) {
-                if (jj != cj) {
+            if (!valid) continue;
+            if (j_hi - j_lo < 2) {
+                // one or two parts (dense new rows): a pass over the run per
+                // part, every pass the same for all lanes, so a warp does not
+                // split at each part change
+                for (uint32_t jj = j_lo; jj <= j_hi; ++jj) {
+                    if (jj != cj) {
+                        flush();
+                        cj = jj;
+                    }
+#pragma unroll
+                    for (int u = 0; u < kRun; ++u)
+                        mark(loc[u] & 63u, xs[u], ((valid >> u) & 1u) & (uint32_t)((loc[u] >> kOccShift) == jj));
+                }
+                continue;
+            }
+#pragma unroll
+            for (int u = 0; u < kRun; ++u) {
+                if (!((valid >> u) & 1u)) continue;
+                const uint32_t j = loc[u] >> kOccShift;
+                if (j != cj) {
                     flush();
-                    cj = jj;
+                    cj = j;
                 }
-#pragma unroll
-                for (int u = 0; u < kRun; ++u)
-                    mark(loc[u] & 63u, xs[u], ((valid >> u) & 1u) & (uint32_t)((loc[u] >> kOccShift) == jj));
+                mark(loc[u] & 63u, xs[u], 1u);
             }
-            continue;
         }
-#pragma unroll
-        for (int u = 0; u < kRun; ++u) {
-            if (!((valid >> u) & 1u)) continue;
-            const uint32_t j = loc[u] >> kOccShift;
-            if (j != cj) {
-                flush();
-                cj = j;
-            }
-            mark(loc[u] & 63u, xs[u], 1u);
-        }
+        flush();
     }
-    flush();
     __syncthreads();
 
     // 2. new symbols before each part (parts kPer * tid .. in order)
