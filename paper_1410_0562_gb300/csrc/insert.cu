@@ -33,6 +33,7 @@ constexpr uint64_t kStageSupers = 512;      // superblocks per chunk of an in-pl
 constexpr unsigned kStageGrid = 1216;       // CTAs of the staging copy (8 per SM)
 constexpr uint64_t kStageBlocksW = 1ull << 19;  // output blocks per chunk of an in-place 4-bit Insert
 constexpr int kRun = 8;              // consecutive new symbols a thread places at once
+constexpr uint64_t kSparseSymbols = 4096;  // new symbols of a superblock (of 65536 rows) placed one by one
 
 // 64 rows of the 2-bit dictionary as its three bit planes (bit p: row p).
 struct Window {
@@ -271,12 +272,12 @@ __global__ void __launch_bounds__(kT, kT == 256 ? 4 : 2) insert_kernel(const uns
     //    them into shared memory once per part.  A run over one or two
     //    parts takes one pass per part over all of its symbols, so the lanes
     //    of a warp stay together (a divergent part change in the middle of
-    //    a run cost more than the passes).  Sparse new rows (the 256-thread
-    //    form) skip the runs.
-    if constexpr (kT == kInsertThreadsSparse) {
-        // sparse new rows (the CTA size the launcher picks for them): one
-        // symbol per thread and step, its bits ORed into shared memory
-        // directly (new rows rarely share a part, so the atomics rarely meet)
+    //    a run cost more than the passes).  A superblock with few new rows
+    //    skips the runs.
+    if (i_end - i_begin <= kSparseSymbols) {
+        // few new rows: one symbol per thread and step, its bits ORed into
+        // shared memory directly (new rows rarely share a part, so the
+        // atomics rarely meet)
         for (uint64_t i = i_begin + tid; i < i_end; i += kT) {
             const IdxT local = gsa[i] + (IdxT)i - (IdxT)O;
             if (local >= (IdxT)(1u << kSuperShift)) {  // not in this superblock: the plan is inconsistent
