@@ -277,21 +277,34 @@ __global__ void __launch_bounds__(kT, kT == 256 ? 4 : 2) insert_kernel(const uns
     if (i_end - i_begin <= kSparseSymbols) {
         // few new rows: one symbol per thread and step, its bits ORed into
         // shared memory directly (new rows rarely share a part, so the
-        // atomics rarely meet)
-        for (uint64_t i = i_begin + tid; i < i_end; i += kT) {
-            const IdxT local = gsa[i] + (IdxT)i - (IdxT)O;
-            if (local >= (IdxT)(1u << kSuperShift)) {  // not in this superblock: the plan is inconsistent
-                atomicOr(d_err, 1024u);
-                continue;
+        // atomics rarely meet); the loads of four steps go out together
+        for (uint64_t i0 = i_begin + tid; i0 < i_end; i0 += 4 * (uint64_t)kT) {
+            IdxT gv[4];
+            uint32_t xv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const uint64_t i = i0 + (uint64_t)u * kT;
+                gv[u] = i < i_end ? gsa[i] : (IdxT)0;
+                xv[u] = i < i_end ? bint[i] : 0u;
             }
-            const uint32_t l = (uint32_t)local, j = l >> kOccShift, h = (l >> 5) & 1u, bit = 1u << (l & 31u);
-            const uint32_t x = bint[i];
-            atomicOr(&sF[h][j], bit);
-            if (x == kBintDollar) {
-                atomicOr(&sD[h][j], bit);
-            } else {
-                if (x & 1u) atomicOr(&sC[h][j], bit);
-                if (x & 2u) atomicOr(&sC[2 + h][j], bit);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const uint64_t i = i0 + (uint64_t)u * kT;
+                if (i >= i_end) break;
+                const IdxT local = gv[u] + (IdxT)i - (IdxT)O;
+                if (local >= (IdxT)(1u << kSuperShift)) {  // not in this superblock: the plan is inconsistent
+                    atomicOr(d_err, 1024u);
+                    continue;
+                }
+                const uint32_t l = (uint32_t)local, j = l >> kOccShift, h = (l >> 5) & 1u, bit = 1u << (l & 31u);
+                const uint32_t x = xv[u];
+                atomicOr(&sF[h][j], bit);
+                if (x == kBintDollar) {
+                    atomicOr(&sD[h][j], bit);
+                } else {
+                    if (x & 1u) atomicOr(&sC[h][j], bit);
+                    if (x & 2u) atomicOr(&sC[2 + h][j], bit);
+                }
             }
         }
     } else {
