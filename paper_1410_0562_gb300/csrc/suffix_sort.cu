@@ -1090,7 +1090,8 @@ template <int kB>
 __global__ void __launch_bounds__(kThreads) sa_large_gather_kernel(
     const uint32_t* __restrict__ text, unsigned long long base, uint32_t n,
     const unsigned long long* __restrict__ elems, Units u, uint32_t nwin, unsigned long long* __restrict__ lkeys,
-    uint32_t* __restrict__ lvals, uint32_t* __restrict__ lpos) {
+    uint32_t* __restrict__ lvals, uint32_t* __restrict__ lpos, const uint32_t* __restrict__ d_large) {
+    if (*d_large == 0) return;  // no unit takes the device-wide path (the usual case)
     for (uint32_t w = blockIdx.x; w < nwin; w += gridDim.x) {
         const uint32_t lo = w * kWindow, hi = min(n, lo + kWindow);
         const uint32_t beg = u.beg[w];
@@ -1661,7 +1662,7 @@ void suffix_sort_block(Launcher& L, const uint32_t* text, const uint32_t* term, 
     // rows' keys are dead once the local sort has run)
     SBWT_LAUNCH(L, "sa_large_gather", 32.0 * nwin, 24, d_large, large_gather, grid_of(g_local_ctas[dev], nwin),
                 kThreads, 0, text, (unsigned long long)base, n, elems, units, nwin, other, b.vals,
-                b.act_pos[0]);
+                b.act_pos[0], d_large);
     unsigned long long* spare = da ? b.keys_alt : b.keys;  // the elements are dead now
     const bool la = radix_sort_pairs_fused(L, other, b.vals, spare, b.vals_alt, d_large, n, 0, 63, b.radix_temp,
                                            b.err);
