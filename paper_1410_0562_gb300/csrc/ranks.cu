@@ -108,13 +108,17 @@ __global__ void __launch_bounds__(kThreads) compute_ranks_kernel(const uint32_t*
 
     I i = (I)m_ext;
     push(rs + len, i);
-    I wcur = ~(I)0;
-    uint32_t word = 0;
+    // the text word of the current position and the one below it, fetched
+    // a word ahead so the walk never waits for the text
+    I wcur = len > 0 ? (P + len - 1) / kPer : (I)0;
+    uint32_t word = len > 0 ? __ldg(text + wcur) : 0u;
+    uint32_t below = (len > 0 && wcur > 0) ? __ldg(text + wcur - 1) : 0u;
     for (I k = len; k > 0; --k) {
         const I t = P + k - 1;
-        if (t / kPer != wcur) {
+        if (t / kPer != wcur) {  // one word down
             wcur = t / kPer;
-            word = __ldg(text + wcur);
+            word = below;
+            below = wcur > 0 ? __ldg(text + wcur - 1) : 0u;
         }
         const uint32_t c = (word >> (32u - kB - kB * (uint32_t)(t % kPer))) & ((1u << kB) - 1u);
         I Cc, in;
