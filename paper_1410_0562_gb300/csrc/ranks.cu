@@ -200,9 +200,15 @@ __global__ void __launch_bounds__(kThreads) compute_ranks_seg_kernel(const uint3
         const I tt = P + k;
         return (__ldg(text + tt / kPer) >> (32u - kB - kB * (uint32_t)(tt % kPer))) & ((1u << kB) - 1u);
     };
+    const I C0 = (I)d_C[0], C1 = (I)d_C[1], C2 = (I)d_C[2], C3 = (I)d_C[3];
     // Lemma 1: rank of c P[k..] among the old suffixes from the rank i of P[k..]
     auto step = [&](uint32_t c, I i) -> I {
-        const I Cc = (I)__ldg(d_C + c);
+        I Cc;
+        if constexpr (kB == 2) {
+            Cc = (c & 2) ? ((c & 1) ? C3 : C2) : ((c & 1) ? C1 : C0);
+        } else {
+            Cc = (I)__ldg(d_C + c);
+        }
         const I sup = kStage ? s_super[(i >> kSS) * kCodes + c] : (I)__ldg(super + (i >> kSS) * kCodes + c);
         I r = Cc + sup + (I)D::in_super(blocks, c, i);
         if (r > nx) {
@@ -244,9 +250,21 @@ __global__ void __launch_bounds__(kThreads) compute_ranks_seg_kernel(const uint3
             }
         }
     }
-    for (I k = top; k > a; --k) {
-        i = step(code_at(k - 1), i);
-        g[rs + k - 1] = i;
+    // the segment's own walk, the text word below fetched a word ahead
+    if (top > a) {
+        I wcur = (P + top - 1) / kPer;
+        uint32_t word = __ldg(text + wcur);
+        uint32_t below = wcur > 0 ? __ldg(text + wcur - 1) : 0u;
+        for (I k = top; k > a; --k) {
+            const I tt = P + k - 1;
+            if (tt / kPer != wcur) {
+                wcur = tt / kPer;
+                word = below;
+                below = wcur > 0 ? __ldg(text + wcur - 1) : 0u;
+            }
+            i = step((word >> (32u - kB - kB * (uint32_t)(tt % kPer))) & ((1u << kB) - 1u), i);
+            g[rs + k - 1] = i;
+        }
     }
 }
 
