@@ -9,8 +9,10 @@
 alignas(16) static unsigned long long g_dyn_smem[48 * 1024 / 8];  // the superblock counters' stage
 
 namespace sbwt {
+#include "text.inc"
 #include "dict.inc"
 #include "ranks.inc"
+#include "gather.inc"
 }  // namespace sbwt
 using namespace sbwt;
 
@@ -56,5 +58,31 @@ extern "C" int emu_compute_ranks(int k, int seg, uint32_t segs, uint32_t seg_row
         run_k<2>(seg, segs, seg_rows, text, text_words, offsets, nreads, words, super, C, n_ext, m_start, g, n_int, d_err);
     else
         run_k<1>(seg, segs, seg_rows, text, text_words, offsets, nreads, words, super, C, n_ext, m_start, g, n_int, d_err);
+    return 0;
+}
+
+// One gather of B_int, g_sa and Insert's plan over a block's SA_int (2-bit
+// text, 32-bit index), as the library launches it: kGather elements per
+// thread, CTAs of kThreads threads.
+extern "C" int emu_bint_gather(const uint32_t* text, uint64_t text_words, const uint32_t* term, uint64_t term_words,
+                               unsigned long long base, const uint32_t* sa, const uint32_t* g, uint64_t g_len,
+                               uint32_t n, uint8_t* bint, uint32_t* gsa, uint32_t* ins_i0, unsigned long long nsb,
+                               int super_shift) {
+    std::vector<std::pair<void*, size_t>> maps;
+    const uint32_t* g_text = guarded(text, text_words, maps);
+    const uint32_t* g_term = guarded(term, term_words, maps);
+    const uint32_t* g_sa = guarded(sa, n, maps);
+    const uint32_t* g_g = guarded(g, g_len, maps);
+    uint8_t* g_bint = guarded(bint, n, maps);
+    uint32_t* g_gsa = guarded(gsa, n, maps);
+    uint32_t* g_plan = guarded(ins_i0, nsb + 1, maps);
+    const uint64_t per_cta = (uint64_t)kThreads * kGather;
+    run_grid((unsigned)((n + per_cta - 1) / per_cta), kThreads, [&] {
+        bint_gather_kernel<uint32_t, 2>(g_text, g_term, base, g_sa, g_g, n, g_bint, g_gsa, g_plan, nsb, super_shift);
+    });
+    memcpy(bint, g_bint, n);
+    memcpy(gsa, g_gsa, n * 4ull);
+    memcpy(ins_i0, g_plan, (nsb + 1) * 4);
+    for (auto& m : maps) munmap(m.first, m.second);
     return 0;
 }

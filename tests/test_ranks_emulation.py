@@ -1,5 +1,6 @@
 """ComputeRanks (Algorithm 2 with Lemma 1) run on the CPU: the per-read
-kernel and the segmented kernel for long reads.
+kernel and the segmented kernel for long reads; and the gather that follows
+it (B_int, g_sa = g[SA_int] and Insert's plan).
 
 The text of both kernels and of the dictionary layout is cut out of
 csrc/ranks.cu and csrc/sbwt_internal.cuh and compiled for the host with
@@ -44,6 +45,9 @@ def emu(tmp_path_factory):
     hdr = open(os.path.join(CSRC, "sbwt_internal.cuh")).read()
     (d / "dict.inc").write_text("constexpr int kThreads = 256;\n" + _cut(
         hdr, "constexpr int kOccShift = 6;", "// ---------------------------------------------------------------------------\n// CTA-wide scans"))
+    (d / "text.inc").write_text(_cut(hdr, "constexpr int kTextPadWords = 4;", "// Rank dictionary over B"))
+    (d / "gather.inc").write_text(_cut(src, "// B_int and g_sa in one pass over SA_int",
+                                       "// rank(c, k) queries, codes 0..kCodes-1"))
     kern = _cut(src, "// Algorithm 2, one thread per read:", "// B_int and g_sa in one pass over SA_int")
     kern = kern.replace("extern __shared__ unsigned long long s_raw[];", "unsigned long long* s_raw = g_dyn_smem;")
     (d / "ranks.inc").write_text(kern)
@@ -54,6 +58,8 @@ def emu(tmp_path_factory):
     P, U64, U32, I = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int
     L.emu_compute_ranks.argtypes = [I, I, U32, U32, P, U64, P, U64, P, P, P, U64, U64, P, U64, P]
     L.emu_compute_ranks.restype = I
+    L.emu_bint_gather.argtypes = [P, U64, P, U64, U64, P, P, U64, U32, P, P, P, U64, I]
+    L.emu_bint_gather.restype = I
     return L
 
 
@@ -152,3 +158,57 @@ def test_segmented_kernel_against_an_empty_index(emu):
     new = readgen.ragged_reads(6, 700, 1500, seed=35)
     g, err = run(emu, *empty, *new, seg=True)
     assert err == 0 and not np.any(g)
+
+
+def term_bitmap(off: np.ndarray) -> np.ndarray:
+    """Terminator bitmap of an append (bit t & 31 of word t >> 5 set at read
+    j's terminator position off[j+1] + j), with two zero words of padding."""
+    m = len(off) - 1
+    npos = int(off[-1]) + m
+    words = np.zeros((npos + 31) // 32 + 2, np.uint32)
+    tpos = off[1:].astype(np.int64) + np.arange(m)
+    np.bitwise_or.at(words, tpos >> 5, (np.uint32(1) << (tpos & 31).astype(np.uint32)).astype(np.uint32))
+    return words
+
+
+@pytest.mark.parametrize("n_reads,seed", [(40, 1), (173, 2)])
+def test_gather_writes_bint_gsa_and_the_insert_plan(emu, n_reads, seed):
+    """B_int[i] is the symbol before suffix SA[i] (a terminator where the
+    suffix starts its read), g_sa[i] = g[SA[i]], and the plan entry of
+    superblock S is the number of new symbols whose rows r_i = g_sa[i] + i
+    lie below S 2^shift (here 64-row superblocks, so hundreds of entries),
+    for blocks whose sizes are not multiples of a thread's four elements."""
+    rng = np.random.default_rng(seed)
+    reads, off = readgen.ragged_reads(n_reads, 0, 60, seed=seed + 10, p_empty=0.05)
+    m = len(off) - 1
+    n = int(off[-1]) + m
+    text = append_text(reads, off)
+    term = term_bitmap(off)
+    sa = rng.permutation(n).astype(np.uint32)
+    n_ext = 3 * n + 17
+    gsa_want = np.sort(rng.integers(0, n_ext + 1, size=n)).astype(np.uint32)
+    g = np.zeros(n, np.uint32)
+    g[sa] = gsa_want
+    shift = 6
+    nsb = ((n_ext + n) >> shift) + 1
+    bint = np.zeros(n, np.uint8)
+    gsa = np.zeros(n, np.uint32)
+    plan = np.full(nsb + 1, 0xDEADBEEF, np.uint32)
+    ptr = lambda a: ctypes.c_void_p(a.ctypes.data)  # noqa: E731
+    assert emu.emu_bint_gather(ptr(text), len(text), ptr(term), len(term), 0, ptr(sa), ptr(g), n, n, ptr(bint),
+                               ptr(gsa), ptr(plan), nsb, shift) == 0
+    codes = np.zeros(n, np.int64)
+    lut = np.zeros(256, np.int64)
+    for c, v in CODE.items():
+        lut[c] = v
+    pos = np.arange(int(off[-1])) + np.repeat(np.arange(m), np.diff(off.astype(np.int64)))
+    codes[pos] = lut[reads]
+    is_term = np.zeros(n, bool)
+    is_term[off[1:].astype(np.int64) + np.arange(m)] = True
+    t = sa.astype(np.int64)
+    want = np.where((t == 0) | is_term[np.maximum(t - 1, 0)], 255, codes[np.maximum(t - 1, 0)])
+    assert np.array_equal(bint, want.astype(np.uint8))
+    assert np.array_equal(gsa, gsa_want)
+    r = gsa_want.astype(np.int64) + np.arange(n)
+    plan_want = np.searchsorted(r, np.arange(nsb + 1, dtype=np.int64) << shift, side="left")
+    assert np.array_equal(plan.astype(np.int64), plan_want)
