@@ -62,6 +62,8 @@ template <class T>
 static T __shfl_up_sync(unsigned, T v, int d) { return emu_get(v, emu_lane >= (unsigned)d ? emu_lane - d : emu_lane); }
 template <class T>
 static T __shfl_sync(unsigned, T v, int src) { return emu_get(v, (unsigned)src); }
+template <class T>
+static T __shfl_xor_sync(unsigned, T v, int m) { return emu_get(v, emu_lane ^ (unsigned)m); }
 static inline unsigned __reduce_max_sync(unsigned, unsigned v) {
     g_warp->xch[emu_lane] = v;
     g_warp->bar.arrive_and_wait();

@@ -1,0 +1,93 @@
+"""The counting phases of one radix pass (csrc/radix.cu) run on the CPU.
+
+The upsweep counts the digits of each chunk of whole 2048-key tiles (a
+persistent grid of G CTAs, chunk c holding tiles [c per, (c+1) per) of the
+ceil(n / 2048) tiles) and adds them to the pass's digit totals; the chunk
+scan turns the G x 256 counts into each (chunk, digit)'s first output slot:
+the number of keys with a smaller digit plus the keys of the same digit in
+earlier chunks, which is what a stable counting sort gives.  The kernels'
+text is cut out of the CUDA source and compiled for the host with
+tests/emu/cuda_emu.h (the one inline-PTX load becomes two plain loads).
+Checked against numpy on keys whose count is not a multiple of the tile,
+with grids that leave the last chunks empty.  No GPU is used."""
+import ctypes
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CSRC = os.path.join(ROOT, "paper_1410_0562_gb300", "csrc")
+EMU = os.path.join(os.path.dirname(os.path.abspath(__file__)), "emu", "radix_emulation.cpp")
+TILE = 2048
+
+
+def _cut(text, start, end):
+    i = text.index(start)
+    return text[i:text.index(end, i)]
+
+
+@pytest.fixture(scope="module")
+def emu(tmp_path_factory):
+    if not shutil.which("g++"):
+        pytest.skip("g++ is not available")
+    d = tmp_path_factory.mktemp("radixemu")
+    src = open(os.path.join(CSRC, "radix.cu")).read()
+    hdr = open(os.path.join(CSRC, "sbwt_internal.cuh")).read()
+    (d / "radix_hdr.inc").write_text(_cut(hdr, "constexpr int kRadixBits = 8;", "size_t radix_temp_words(uint64_t cap);"))
+    (d / "scan.inc").write_text(_cut(hdr, "struct SumOp {", "// Launch bookkeeping"))
+    (d / "radix_consts.inc").write_text(_cut(src, "constexpr int kThreads = 256;", "// Chunk c of a grid"))
+    count = _cut(src, "// Chunk c of a grid", "// The scatter of one pass over this CTA's chunk")
+    ptx = 'asm volatile("ld.global.cg.v2.u64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "l"(p));'
+    assert ptx in count
+    (d / "radix_count.inc").write_text(count.replace(ptx, "a = p[0];\n    b = p[1];"))
+    lib = d / "libradixemu.so"
+    subprocess.check_call(["g++", "-O1", "-std=c++20", "-shared", "-fPIC", "-pthread", "-I", str(d), "-o", str(lib),
+                           EMU])
+    L = ctypes.CDLL(str(lib))
+    P, U32, I = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_int
+    L.emu_radix_count.argtypes = [P, U32, I, U32, P, P]
+    L.emu_radix_count.restype = I
+    return L
+
+
+def chunk_of(n: int, grid: int) -> np.ndarray:
+    """Chunk of every key index under the kernels' tiling."""
+    ntiles = (n + TILE - 1) // TILE
+    per = (ntiles + grid - 1) // grid
+    return (np.arange(n) // TILE) // per
+
+
+@pytest.mark.parametrize("n,grid,shift", [(50_001, 7, 0), (50_001, 40, 8), (6_000, 5, 16), (2_048, 3, 0), (0, 4, 0)])
+def test_chunk_offsets_are_those_of_a_stable_counting_sort(emu, n, grid, shift):
+    rng = np.random.default_rng(n + grid + shift)
+    # a skewed digit mix (a few digits take most keys) as in the bucket split
+    digits = np.where(rng.random(n) < 0.5, rng.integers(0, 4, n), rng.integers(0, 256, n)).astype(np.uint64)
+    keys = (digits << np.uint64(shift)) | (rng.integers(0, 1 << 20, n).astype(np.uint64) << np.uint64(40))
+    offsets = np.zeros(grid * 256, np.uint32)
+    next_totals = np.full(256, 99, np.uint32)
+    kp = keys if n else np.zeros(1, np.uint64)
+    assert emu.emu_radix_count(ctypes.c_void_p(kp.ctypes.data), n, shift, grid,
+                               ctypes.c_void_p(offsets.ctypes.data), ctypes.c_void_p(next_totals.ctypes.data)) == 0
+    assert not next_totals.any()
+    if n == 0:
+        return
+    chunks = chunk_of(n, grid)
+    used = int(chunks.max()) + 1
+    start = np.concatenate([[0], np.cumsum(np.bincount(digits.astype(np.int64), minlength=256))[:-1]])
+    counts = np.zeros((grid, 256), np.int64)
+    np.add.at(counts, (chunks, digits.astype(np.int64)), 1)
+    want = start[None, :] + np.cumsum(counts, axis=0) - counts
+    got = offsets.reshape(grid, 256).astype(np.int64)
+    # chunks past the last tile hold nothing and are left alone
+    assert np.array_equal(got[:used], want[:used])
+    # the offsets place every key once: a stable counting sort by digit
+    order = np.empty(n, np.int64)
+    nxt = got[:used].copy()
+    for i in range(n):
+        c, dg = chunks[i], int(digits[i])
+        order[nxt[c, dg]] = i
+        nxt[c, dg] += 1
+    assert np.array_equal(order, np.argsort(digits, kind="stable"))
