@@ -370,15 +370,18 @@ __device__ __forceinline__ void store_run(uint32_t* p, uint32_t w0, uint32_t nwi
 // One CTA over all windows, kScanPer consecutive windows per thread: unit
 // ends, long counts, owners, and the offsets of the units that take the
 // global path.  Also zeroes the per-round counts of local unsorted members
-// (zero_slots[k * zero_stride], k < nzero).
+// (zero_slots[k * zero_stride], k < nzero) and the per-round counts of units
+// left to the CTA kernel (left_slots[k], k < nleft).
 constexpr uint32_t kScanSpan = kScanThreads * kScanPer;
 
 __global__ void __launch_bounds__(kScanThreads) sa_unit_scan_kernel(Units u, uint32_t nwin, uint32_t n,
                                                                     uint32_t* __restrict__ d_large_n,
                                                                     uint32_t* __restrict__ zero_slots, int nzero,
-                                                                    int zero_stride) {
+                                                                    int zero_stride,
+                                                                    uint32_t* __restrict__ left_slots, int nleft) {
     __shared__ unsigned long long xch[kScanThreads];
     if ((int)threadIdx.x < nzero) zero_slots[threadIdx.x * zero_stride] = 0;
+    if ((int)threadIdx.x < nleft) left_slots[threadIdx.x] = 0;
     // forward: long suffixes in the block before each unit start (kept in
     // nlong until the backward pass), owner of each window's first row
     uint32_t carry_sum = 0, carry_last = 0;  // carry_last: 1 + index of the last unit so far
@@ -1141,7 +1144,8 @@ __global__ void __launch_bounds__(kThreads) sa_round_gather_local_kernel(
 __global__ void __launch_bounds__(kLThreads, 4) sa_round_local_kernel(
     uint32_t* __restrict__ loc_act, const uint32_t* __restrict__ loc_next, Units u, uint32_t nwin, uint32_t n,
     uint32_t* __restrict__ rank, uint32_t* __restrict__ sa, uint32_t* __restrict__ d_cnt,
-    uint32_t* __restrict__ d_err) {
+    uint32_t* __restrict__ d_err, const uint32_t* __restrict__ d_left) {
+    if (*d_left == 0) return;  // the warp kernel left no unit of more than kWChunk members
     extern __shared__ __align__(16) unsigned char smem[];
     unsigned long long* skey = reinterpret_cast<unsigned long long*>(smem);
     uint32_t* sval = reinterpret_cast<uint32_t*>(skey + kLSlots);
@@ -1256,7 +1260,7 @@ __global__ void __launch_bounds__(kLThreads, 4) sa_round_local_kernel(
 __global__ void __launch_bounds__(kWWarps * 32) sa_round_local_warp_kernel(
     uint32_t* __restrict__ loc_act, const uint32_t* __restrict__ loc_next, Units u, uint32_t nwin, uint32_t n,
     uint32_t* __restrict__ rank, uint32_t* __restrict__ sa, uint32_t* __restrict__ d_cnt,
-    uint32_t* __restrict__ d_err) {
+    uint32_t* __restrict__ d_err, uint32_t* __restrict__ d_left) {
     __shared__ WarpTile tiles[kWWarps];
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t below = (1u << lane) - 1u;
@@ -1266,6 +1270,7 @@ __global__ void __launch_bounds__(kWWarps * 32) sa_round_local_warp_kernel(
         const uint32_t beg = u.beg[w];
         if (beg == kNone || u.lofs[w] != kNone) continue;
         const uint32_t cnt = u.cnt[w];
+        if (cnt > (uint32_t)kWChunk && lane == 0) atomicAdd(d_left, 1u);  // the CTA kernel's unit
         if (cnt == 0 || cnt > (uint32_t)kWChunk) continue;
 #pragma unroll
         for (int j = 0; j < kWStripes; ++j) {
@@ -1561,9 +1566,10 @@ uint32_t suffix_sort_rounds(uint32_t max_len, int code_bits) {
 }
 
 // slot 0: n; 1: size of the global-path list; 2 + 2r: global-path unsorted
-// members after round r (r = 0: the initial sort); 3 + 2r: local ones
+// members after round r (r = 0: the initial sort); 3 + 2r: local ones;
+// 3 + 2R + r (R rounds, r >= 1): units of round r left to the CTA kernel
 size_t suffix_sort_log_slots(uint32_t max_len, int code_bits) {
-    return 4 + 2 * (size_t)suffix_sort_rounds(max_len, code_bits);
+    return 4 + 3 * (size_t)suffix_sort_rounds(max_len, code_bits);
 }
 
 size_t suffix_sort_chunk_words(uint64_t cap) {
@@ -1648,7 +1654,7 @@ void suffix_sort_block(Launcher& L, const uint32_t* text, const uint32_t* term, 
                 warp_grid, kThreads, 0, text, (unsigned long long)base, elems, n, nwin, units, b.sa, b.rank,
                 ll_t, ll_row, ll_key, b.err);
     SBWT_LAUNCH(L, "sa_unit_scan", 96.0 * nwin, 0, nullptr, sa_unit_scan_kernel, 1, kScanThreads, 0, units, nwin, n,
-                d_large, b.count_log + 3, (int)rounds + 1, 2);
+                d_large, b.count_log + 3, (int)rounds + 1, 2, b.count_log + 4 + 2 * rounds, (int)rounds);
     // per long row: its list entry (t, row, key), SA and rank writes; per
     // unsorted member the compacted entry
     SBWT_LAUNCH(L, "sa_local_sort", (double)n * 24, 4, b.count_log + 3, sa_local_sort_warp_kernel,
@@ -1676,6 +1682,7 @@ void suffix_sort_block(Launcher& L, const uint32_t* text, const uint32_t* term, 
         const uint32_t* cnt = b.count_log + 2 + 2 * (r - 1);
         uint32_t* next_cnt = b.count_log + 2 + 2 * r;
         const uint32_t* loc_cnt = b.count_log + 3 + 2 * (r - 1);
+        uint32_t* left = b.count_log + 3 + 2 * rounds + r;
         SBWT_LAUNCH(L, "sa_round_gather", 0, 12, loc_cnt, sa_round_gather_local_kernel, warp_grid, kThreads, 0,
                     b.loc_act, units, nwin, b.rank, h, n, b.loc_next, b.err);
         SBWT_LAUNCH(L, "sa_round_keys", 0, 24, cnt, sa_round_keys_kernel,
@@ -1683,10 +1690,10 @@ void suffix_sort_block(Launcher& L, const uint32_t* text, const uint32_t* term, 
                     b.rank, h, n, bits, b.keys, b.vals, b.err);
         SBWT_LAUNCH(L, "sa_round_local", 0, 24, loc_cnt, sa_round_local_warp_kernel,
                     grid_of(g_round_warp_ctas[dev], (uint64_t)nwin / kWWarps + 1), kWWarps * 32, 0, b.loc_act,
-                    b.loc_next, units, nwin, n, b.rank, b.sa, b.count_log + 3 + 2 * r, b.err);
+                    b.loc_next, units, nwin, n, b.rank, b.sa, b.count_log + 3 + 2 * r, b.err, left);
         SBWT_LAUNCH(L, "sa_round_local_cta", 0, 0, nullptr, sa_round_local_kernel,
                     grid_of(g_round_local_ctas[dev], nwin), kLThreads, kRoundLocalSmem, b.loc_act, b.loc_next,
-                    units, nwin, n, b.rank, b.sa, b.count_log + 3 + 2 * r, b.err);
+                    units, nwin, n, b.rank, b.sa, b.count_log + 3 + 2 * r, b.err, left);
         const bool a = radix_sort_pairs_fused(L, b.keys, b.vals, b.keys_alt, b.vals_alt, cnt, n, 0, 2 * bits,
                                               b.radix_temp, b.err);
         run_groups<false>(L, b, a ? b.keys_alt : b.keys, a ? b.vals_alt : b.vals, b.act_pos[cur], cnt, n,

@@ -55,10 +55,11 @@ extern "C" int emu_local_sort(uint32_t n, const uint32_t* ll_t, const uint32_t* 
     return 0;
 }
 
-// One unit-local round: the warp kernel, then the CTA kernel.
+// One unit-local round: the warp kernel, then the CTA kernel.  *d_left
+// (zero on entry) counts the units the warp kernel left to the CTA kernel.
 extern "C" int emu_round(uint32_t* loc_act, const uint32_t* loc_next, uint32_t* beg, uint32_t* lofs, uint32_t* cnt,
                          uint32_t nwin, uint32_t n, uint32_t* rank, uint32_t* sa, uint32_t* d_cnt, uint32_t* d_err,
-                         unsigned warp_grid, unsigned cta_grid) {
+                         uint32_t* d_left, unsigned warp_grid, unsigned cta_grid) {
     std::vector<std::pair<void*, size_t>> maps;
     uint32_t* g_loc = guarded(loc_act, n, maps);
     const uint32_t* g_next = guarded(loc_next, n, maps);
@@ -67,10 +68,10 @@ extern "C" int emu_round(uint32_t* loc_act, const uint32_t* loc_next, uint32_t* 
     uint32_t* g_cnt = guarded(cnt, nwin, maps);
     Units u{guarded(beg, nwin, maps), nullptr, nullptr, nullptr, nullptr, guarded(lofs, nwin, maps), g_cnt, nullptr};
     run_grid(warp_grid, kWWarps * 32, [&] {
-        sa_round_local_warp_kernel(g_loc, g_next, u, nwin, n, g_rank, g_sa, d_cnt, d_err);
+        sa_round_local_warp_kernel(g_loc, g_next, u, nwin, n, g_rank, g_sa, d_cnt, d_err, d_left);
     });
     run_grid(cta_grid, kLThreads, [&] {
-        sa_round_local_kernel(g_loc, g_next, u, nwin, n, g_rank, g_sa, d_cnt, d_err);
+        sa_round_local_kernel(g_loc, g_next, u, nwin, n, g_rank, g_sa, d_cnt, d_err, d_left);
     });
     memcpy(loc_act, g_loc, n * 4ull);
     memcpy(rank, g_rank, n * 4ull);
@@ -84,15 +85,19 @@ extern "C" int emu_round(uint32_t* loc_act, const uint32_t* loc_next, uint32_t* 
 // global-path offsets, zeroed counts and round counters.  Unit fields are
 // laid out as on the device (one stride of words per field).
 extern "C" int emu_unit_scan(uint32_t* fields, uint64_t stride, uint32_t nwin, uint32_t n, uint32_t* d_large_n,
-                             uint32_t* zero_slots, int nzero, int zero_stride) {
+                             uint32_t* zero_slots, int nzero, int zero_stride, uint32_t* left_slots, int nleft) {
     std::vector<std::pair<void*, size_t>> maps;
     uint32_t* g = guarded(fields, stride * 8, maps);
     uint32_t* gz = guarded(zero_slots, (size_t)nzero * zero_stride, maps);
     Units u{g, g + stride, g + 2 * stride, g + 3 * stride, g + 4 * stride, g + 5 * stride, g + 6 * stride,
             g + 7 * stride};
-    run_grid(1, kScanThreads, [&] { sa_unit_scan_kernel(u, nwin, n, d_large_n, gz, nzero, zero_stride); });
+    uint32_t* gl = guarded(left_slots, (size_t)nleft, maps);
+    run_grid(1, kScanThreads, [&] {
+        sa_unit_scan_kernel(u, nwin, n, d_large_n, gz, nzero, zero_stride, gl, nleft);
+    });
     memcpy(fields, g, stride * 8 * 4);
     memcpy(zero_slots, gz, (size_t)nzero * zero_stride * 4);
+    memcpy(left_slots, gl, (size_t)nleft * 4);
     for (auto& m : maps) munmap(m.first, m.second);
     return 0;
 }

@@ -295,10 +295,14 @@ def test_round(emu, case):
     sa = np.full(n, kNone, np.uint32)
     d_cnt = np.zeros(1, np.uint32)
     d_err = np.zeros(1, np.uint32)
+    d_left = np.zeros(1, np.uint32)
     nwin = len(beg)
+    left = sum(1 for w in range(nwin) if beg[w] != kNone and lofs[w] == kNone and cnt[w] > kWChunk)
     emu.emu_round(_p(loc_act), _p(loc_next), _p(beg), _p(lofs), _p(cnt), ctypes.c_uint32(nwin), ctypes.c_uint32(n),
-                  _p(rank), _p(sa), _p(d_cnt), _p(d_err), ctypes.c_uint(2), ctypes.c_uint(3))
+                  _p(rank), _p(sa), _p(d_cnt), _p(d_err), _p(d_left), ctypes.c_uint(2), ctypes.c_uint(3))
     assert d_err[0] == 0
+    # the count the CTA kernel returns early on when it is zero
+    assert int(d_left[0]) == left
     assert all(sa[r] == t for r, t in e_sa.items())
     assert all(rank[t] == r for t, r in e_rank.items())
     for w, act in e_loc.items():
@@ -342,9 +346,10 @@ def test_unit_scan(emu, case):
     fields[2 * stride:2 * stride + nwin] = lct
     fields[6 * stride:6 * stride + nwin] = 7  # counts to be zeroed
     zero_slots = np.full(3 * 2, 9, np.uint32)
+    left_slots = np.full(4, 9, np.uint32)
     d_large = np.zeros(1, np.uint32)
     emu.emu_unit_scan(_p(fields), ctypes.c_uint64(stride), ctypes.c_uint32(nwin), ctypes.c_uint32(n), _p(d_large),
-                      _p(zero_slots), ctypes.c_int(3), ctypes.c_int(2))
+                      _p(zero_slots), ctypes.c_int(3), ctypes.c_int(2), _p(left_slots), ctypes.c_int(3))
     end = fields[3 * stride:3 * stride + nwin]
     nlong = fields[4 * stride:4 * stride + nwin]
     lofs = fields[5 * stride:5 * stride + nwin]
@@ -373,3 +378,4 @@ def test_unit_scan(emu, case):
     assert int(d_large[0]) == off
     assert np.all(cnt == 0)
     assert list(zero_slots) == [0, 9, 0, 9, 0, 9]
+    assert list(left_slots) == [0, 0, 0, 9]
