@@ -493,7 +493,7 @@ def measure_served(sb, torch, w_res, requests, local, stream, peak):
     # pinned host memory under a 512 MB budget, rewritten in place by Insert;
     # its kernels against the host link measured on the same device
     bw = bw_all
-    h2d, rnd = bw["h2d_GBps"], bw["host_random_32B_GBps"]
+    h2d, d2h, rnd = bw["h2d_GBps"], bw["d2h_GBps"], bw["host_random_32B_GBps"]
     m2 = 2_000_000
     small_reads = w_res.reads[: int(w_res.offsets[m2])]
     small_off = w_res.offsets[: m2 + 1]
@@ -516,12 +516,26 @@ def measure_served(sb, torch, w_res, requests, local, stream, peak):
     ix2.close()
     link = bw
     tiered = {}
-    for name in ("compute_ranks", "insert_merge", "insert_stage"):
-        k = tier_k.get(name)
-        if k and k["GBps"]:
-            tiered[name] = {"GBps": k["GBps"], "ms": k["ms_per_step"],
-                            "frac_of_link": round(k["GBps"] / (rnd if name == "compute_ranks" else h2d), 3),
-                            "link_roofline": "random 32-byte reads" if name == "compute_ranks" else "H2D copy"}
+    k = tier_k.get("compute_ranks")
+    if k and k["GBps"]:
+        # every rank query's block read crosses the link
+        tiered["compute_ranks"] = {"GBps": k["GBps"], "ms": k["ms_per_step"], "link_GBps": k["GBps"],
+                                   "frac_of_link": round(k["GBps"] / rnd, 3), "link_roofline": "random 32-byte reads"}
+    st, mg = tier_k.get("insert_stage"), tier_k.get("insert_merge")
+    if st and st["GBps"]:
+        # the staging kernel reads each old block of a chunk over the link and
+        # writes it to HBM (its counted bytes are both); Insert then writes
+        # the chunk's output blocks back over the link.  So the link carries
+        # the output dictionary once in each direction: half the staging
+        # kernel's counted bytes.
+        link_bytes = st["GBps"] * 1e9 * st["ms_per_step"] / 1e3 / 2
+        tiered["link_bytes_per_direction"] = int(link_bytes)
+        for name, k, rate, roof in (("insert_stage", st, h2d, "H2D copy (old blocks read over the link)"),
+                                    ("insert_merge", mg, d2h, "D2H copy (output blocks written over the link)")):
+            if k and k["ms_per_step"] > 0:
+                lg = link_bytes / (k["ms_per_step"] / 1e3) / 1e9
+                tiered[name] = {"GBps": k["GBps"], "ms": k["ms_per_step"], "link_GBps": round(lg, 1),
+                                "frac_of_link": round(lg / rate, 3), "link_roofline": roof}
     out["host_tier"] = {"resident_reads": m2, "hbm_budget": 512 << 20, "build_s": build2,
                         "build_Mbps": int(small_off[-1]) / build2 / 1e6, "memory": {"hbm": hbm2, "host": host2},
                         "host_bits_per_row": 8.0 * host2 / n2, "host_link": link, "tiered_kernels": tiered,
