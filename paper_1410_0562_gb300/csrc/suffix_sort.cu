@@ -988,6 +988,7 @@ __global__ void __launch_bounds__(kWWarps * 32) sa_local_sort_warp_kernel(
             uint32_t r = 0;
 #pragma unroll
             for (int j = 0; j < kWStripes; ++j) {
+                if ((uint32_t)j * 32 >= c) break;  // past the last stripe (warp-uniform)
                 const uint32_t q = j * 32 + lane;
                 if (q < c) {
                     const uint32_t src = warp_list_index(T, nruns, s + q, r);
@@ -1010,6 +1011,7 @@ __global__ void __launch_bounds__(kWWarps * 32) sa_local_sort_warp_kernel(
                 uint32_t last = 0;
 #pragma unroll
                 for (int j = 0; j < kWStripes; ++j) {
+                    if ((uint32_t)j * 32 >= c) break;  // past the last stripe (warp-uniform)
                     const uint32_t q = j * 32 + lane;
                     if (q >= 1 && q < c && (T.key[q] >> seg_shift) != (T.key[q - 1] >> seg_shift)) last = q;
                 }
@@ -1023,6 +1025,7 @@ __global__ void __launch_bounds__(kWWarps * 32) sa_local_sort_warp_kernel(
             uint32_t bs_carry = 0;
 #pragma unroll
             for (int j = 0; j < kWStripes; ++j) {
+                if ((uint32_t)j * 32 >= cut) break;  // past the last stripe (warp-uniform)
                 const uint32_t q = j * 32 + lane;
                 const bool in = q < cut;
                 const unsigned long long K = in ? T.key[q] : 0ull;
@@ -1065,6 +1068,7 @@ __global__ void __launch_bounds__(kWWarps * 32) sa_local_sort_warp_kernel(
             // the chunk's unsorted members, in sorted order
 #pragma unroll
             for (int j = 0; j < kWStripes; ++j) {
+                if ((uint32_t)j * 32 >= cut) break;  // past the last stripe (warp-uniform)
                 const uint32_t q = j * 32 + lane;
                 const bool a = q < cut && T.act[q];
                 const uint32_t bal = __ballot_sync(0xffffffffu, a);
@@ -1122,18 +1126,31 @@ __global__ void __launch_bounds__(kThreads) sa_large_gather_kernel(
 __global__ void __launch_bounds__(kThreads) sa_round_gather_local_kernel(
     const uint32_t* __restrict__ loc_act, Units u, uint32_t nwin, const uint32_t* __restrict__ rank, uint32_t h,
     uint32_t n, uint32_t* __restrict__ loc_next, uint32_t* __restrict__ d_err) {
-    const int lane = threadIdx.x & 31;
+    constexpr int kG = 4;  // 32-member steps whose loads are in flight together
+    const uint32_t lane = threadIdx.x & 31;
     const uint32_t warps = gridDim.x * (kThreads / 32);
     for (uint32_t w = (blockIdx.x * kThreads + threadIdx.x) >> 5; w < nwin; w += warps) {
-        const uint32_t beg = u.beg[w];
-        if (beg == kNone || u.lofs[w] != kNone) continue;
-        const uint32_t cnt = u.cnt[w];
-        for (uint32_t k = lane; k < cnt; k += 32) {
-            const uint32_t t = loc_act[beg + k];
-            uint32_t nx = 0;
-            if ((uint64_t)t + h < n) nx = rank[t + h];
-            else atomicOr(d_err, 128u);
-            loc_next[beg + k] = nx;
+        const uint32_t beg = u.beg[w], lofs = u.lofs[w], cnt = u.cnt[w];
+        if (beg == kNone || lofs != kNone) continue;
+        for (uint32_t k0 = 0; k0 < cnt; k0 += 32 * kG) {
+            uint32_t t[kG], nx[kG];
+#pragma unroll
+            for (int i = 0; i < kG; ++i) {
+                const uint32_t k = k0 + i * 32 + lane;
+                t[i] = k < cnt ? loc_act[beg + k] : kNone;
+            }
+#pragma unroll
+            for (int i = 0; i < kG; ++i) {
+                const bool in = k0 + i * 32 + lane < cnt;
+                const bool ok = (uint64_t)t[i] + h < n;
+                if (in && !ok) atomicOr(d_err, 128u);
+                nx[i] = in && ok ? rank[t[i] + h] : 0u;
+            }
+#pragma unroll
+            for (int i = 0; i < kG; ++i) {
+                const uint32_t k = k0 + i * 32 + lane;
+                if (k < cnt) loc_next[beg + k] = nx[i];
+            }
         }
     }
 }
@@ -1191,25 +1208,33 @@ __global__ void __launch_bounds__(kLThreads, 4) sa_round_local_kernel(
             w += k;
             continue;
         }
-        // key (rank[t], rank[t + h]) of each slot, loaded blocked; a
-        // thread's loads are independent
+        // key (rank[t], rank[t + h]) of each slot, loaded blocked: every
+        // item's member and next rank first, then the members' ranks, so a
+        // thread's loads are in flight together
         const uint32_t g0 = threadIdx.x * kLItems;
         unsigned long long kk[kLItems];
-        uint32_t v[kLItems];
+        uint32_t v[kLItems], nx[kLItems], src[kLItems];
         uint32_t wi = g0 < total ? batch_window(b, k, g0) : 0u;
 #pragma unroll
         for (int j = 0; j < kLItems; ++j) {
             const uint32_t g = g0 + j;
-            kk[j] = ~0ull;
-            v[j] = 0;
+            src[j] = 0;
             if (g < total) {
                 while (wi + 1 < k && b.pref[wi + 1] <= g) ++wi;
-                const uint32_t src = b.beg[wi] + (g - b.pref[wi]);
-                const uint32_t t = loc_act[src];
-                const uint32_t here = t < n ? rank[t] : 0u;
-                v[j] = t;
-                kk[j] = ((unsigned long long)here << 32) | loc_next[src];
+                src[j] = b.beg[wi] + (g - b.pref[wi]);
             }
+        }
+#pragma unroll
+        for (int j = 0; j < kLItems; ++j) {
+            const bool in = g0 + j < total;
+            v[j] = in ? loc_act[src[j]] : 0u;
+            nx[j] = in ? loc_next[src[j]] : 0u;
+        }
+#pragma unroll
+        for (int j = 0; j < kLItems; ++j) {
+            const bool in = g0 + j < total;
+            const uint32_t here = in && v[j] < n ? rank[v[j]] : 0u;
+            kk[j] = in ? (((unsigned long long)here << 32) | nx[j]) : ~0ull;
         }
         block_sort(kk, v, total, skey, sval, sseg, 32);  // segments: the old groups (equal rank[t])
 
@@ -1266,26 +1291,55 @@ __global__ void __launch_bounds__(kWWarps * 32) sa_round_local_warp_kernel(
     const uint32_t below = (1u << lane) - 1u;
     WarpTile& T = tiles[threadIdx.x >> 5];
     const uint32_t warps = gridDim.x * kWWarps;
-    for (uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nwin; w += warps) {
-        const uint32_t beg = u.beg[w];
-        if (beg == kNone || u.lofs[w] != kNone) continue;
-        const uint32_t cnt = u.cnt[w];
+    // the (start, global-path offset, count) of the warp's next window is
+    // fetched while the current one is sorted (the counts this kernel writes
+    // are its own windows' only)
+    uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    uint32_t nbeg = kNone, nlofs = kNone, ncnt = 0;
+    if (w < nwin) {
+        nbeg = u.beg[w];
+        nlofs = u.lofs[w];
+        ncnt = u.cnt[w];
+    }
+    for (; w < nwin; w += warps) {
+        const uint32_t beg = nbeg, lofs = nlofs, cnt = ncnt;
+        if (w + warps < nwin) {
+            nbeg = u.beg[w + warps];
+            nlofs = u.lofs[w + warps];
+            ncnt = u.cnt[w + warps];
+        }
+        if (beg == kNone || lofs != kNone) continue;
         if (cnt > (uint32_t)kWChunk && lane == 0) atomicAdd(d_left, 1u);  // the CTA kernel's unit
         if (cnt == 0 || cnt > (uint32_t)kWChunk) continue;
+        // the loads of four stripes issued before any is used: members and
+        // next ranks, then the members' ranks
+        constexpr int kHalf = kWStripes / 2;
 #pragma unroll
-        for (int j = 0; j < kWStripes; ++j) {
-            const uint32_t q = j * 32 + lane;
-            if (q < cnt) {
-                const uint32_t t = loc_act[beg + q];
-                const uint32_t here = t < n ? rank[t] : 0u;
-                T.key[q] = ((unsigned long long)here << 32) | loc_next[beg + q];
-                T.t[q] = t;
+        for (int hf = 0; hf < 2; ++hf) {
+            if ((uint32_t)hf * 32 * kHalf >= cnt) break;  // warp-uniform
+            uint32_t mt[kHalf], nx[kHalf], hr[kHalf];
+#pragma unroll
+            for (int i = 0; i < kHalf; ++i) {
+                const uint32_t q = (hf * kHalf + i) * 32 + lane;
+                mt[i] = q < cnt ? loc_act[beg + q] : kNone;
+                nx[i] = q < cnt ? loc_next[beg + q] : 0u;
+            }
+#pragma unroll
+            for (int i = 0; i < kHalf; ++i) hr[i] = mt[i] < n ? rank[mt[i]] : 0u;
+#pragma unroll
+            for (int i = 0; i < kHalf; ++i) {
+                const uint32_t q = (hf * kHalf + i) * 32 + lane;
+                if (q < cnt) {
+                    T.key[q] = ((unsigned long long)hr[i] << 32) | nx[i];
+                    T.t[q] = mt[i];
+                }
             }
         }
         __syncwarp();
         uint32_t bs_carry = 0;
 #pragma unroll
         for (int j = 0; j < kWStripes; ++j) {
+            if ((uint32_t)j * 32 >= cnt) break;  // past the last stripe (warp-uniform)
             const uint32_t q = j * 32 + lane;
             const bool in = q < cnt;
             const unsigned long long K = in ? T.key[q] : 0ull;
@@ -1327,6 +1381,7 @@ __global__ void __launch_bounds__(kWWarps * 32) sa_round_local_warp_kernel(
         uint32_t acnt = 0;
 #pragma unroll
         for (int j = 0; j < kWStripes; ++j) {
+            if ((uint32_t)j * 32 >= cnt) break;  // past the last stripe (warp-uniform)
             const uint32_t q = j * 32 + lane;
             const bool a = q < cnt && T.act[q];
             const uint32_t bal = __ballot_sync(0xffffffffu, a);

@@ -16,6 +16,7 @@ alignas(16) static unsigned char g_dyn_smem[(size_t)kLSlots * 20];  // the large
 #include "unit_scan.inc"
 #include "cta_local.inc"
 #include "warp_local.inc"
+#include "round_gather.inc"
 #include "cta_round.inc"
 #include "warp_round.inc"
 
@@ -51,6 +52,23 @@ extern "C" int emu_local_sort(uint32_t n, const uint32_t* ll_t, const uint32_t* 
     memcpy(rank, g_rank, n * 4ull);
     memcpy(loc_act, g_loc, n * 4ull);
     memcpy(cnt, g_cnt, nwin * 4ull);
+    for (auto& m : maps) munmap(m.first, m.second);
+    return 0;
+}
+
+// The next-rank gather of one round: loc_next[beg + k] = rank[loc_act[beg
+// + k] + h] for the first cnt members of every local unit.
+extern "C" int emu_round_gather(const uint32_t* loc_act, uint32_t* beg, uint32_t* lofs, uint32_t* cnt, uint32_t nwin,
+                                const uint32_t* rank, uint32_t h, uint32_t n, uint32_t* loc_next, uint32_t* d_err,
+                                unsigned grid) {
+    std::vector<std::pair<void*, size_t>> maps;
+    const uint32_t* g_loc = guarded(loc_act, n, maps);
+    const uint32_t* g_rank = guarded(rank, n, maps);
+    uint32_t* g_next = guarded(loc_next, n, maps);
+    Units u{guarded(beg, nwin, maps), nullptr, nullptr, nullptr, nullptr, guarded(lofs, nwin, maps),
+            guarded(cnt, nwin, maps), nullptr};
+    run_grid(grid, kThreads, [&] { sa_round_gather_local_kernel(g_loc, u, nwin, g_rank, h, n, g_next, d_err); });
+    memcpy(loc_next, g_next, n * 4ull);
     for (auto& m : maps) munmap(m.first, m.second);
     return 0;
 }

@@ -65,6 +65,8 @@ def emu(tmp_path_factory):
         "unit_scan.inc": _cut(src, "// kScanPer consecutive windows of one field", "// one spare slot per kLItems"),
         "cta_local.inc": _cut(src, "// one spare slot per kLItems", "// Warp-per-unit local sort."),
         "warp_local.inc": _cut(src, "// Warp-per-unit local sort.", "// The global-path list:"),
+        "round_gather.inc": _cut(src, "// next-ranks of the local unsorted members",
+                                 "// One round for the local units, a batch of units per CTA step"),
         "cta_round.inc": _cut(src, "// One round for the local units, a batch of units per CTA step",
                               "// One round for the local units of at most kWChunk"),
         "warp_round.inc": _cut(src, "// One round for the local units of at most kWChunk",
@@ -309,6 +311,39 @@ def test_round(emu, case):
         assert cnt[w] == len(act)
         assert list(loc_act[beg[w]:beg[w] + len(act)]) == act
     assert int(d_cnt[0]) == sum(len(a) for a in e_loc.values())
+
+
+@pytest.mark.timeout(600)
+@pytest.mark.parametrize("seed,grid", [(31, 1), (32, 3), (33, 7)])
+def test_round_gather(emu, seed, grid):
+    """Each local unit's members get the rank of the suffix h further on,
+    in member order; other rows of loc_next stay as they were; a member
+    whose t + h is past the block is flagged (bit 7 of the error word)."""
+    rng = np.random.default_rng(seed)
+    n, beg, lofs, cnt, loc_act, _, rank, _ = make_round(rng, nwin=40, big_units=0.2)
+    h = 3
+    if seed == 33:  # a member near the block end: no suffix h further on
+        w0 = next(w for w in range(len(beg)) if beg[w] != kNone and lofs[w] == kNone and cnt[w] > 40)
+        loc_act[beg[w0] + 37] = n - 2
+    loc_next = np.full(n, 0xABCDEF, np.uint32)
+    want = loc_next.copy()
+    bad = False
+    for w in range(len(beg)):
+        if beg[w] == kNone or lofs[w] != kNone:
+            continue
+        for k in range(int(cnt[w])):
+            t = int(loc_act[beg[w] + k])
+            if t + h < n:
+                want[beg[w] + k] = rank[t + h]
+            else:
+                want[beg[w] + k] = 0
+                bad = True
+    d_err = np.zeros(1, np.uint32)
+    emu.emu_round_gather(_p(loc_act), _p(beg), _p(lofs), _p(cnt), ctypes.c_uint32(len(beg)), _p(rank),
+                         ctypes.c_uint32(h), ctypes.c_uint32(n), _p(loc_next), _p(d_err), ctypes.c_uint(grid))
+    assert np.array_equal(loc_next, want)
+    assert bool(d_err[0] & 128) == bad and (d_err[0] & ~np.uint32(128)) == 0
+    assert bad or seed != 33
 
 
 # ---- the unit scan ------------------------------------------------------------
