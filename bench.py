@@ -433,6 +433,33 @@ def measure_forms(sb, torch, timer, w, local, args, peak, plain_M, candidates, s
     return out
 
 
+def host_link_table(tier_k, h2d, d2h, rnd):
+    """The host tier's kernels against the host link (GB/s rates measured on
+    the same device): ComputeRanks' block reads all cross the link as random
+    32-byte reads.  The staging kernel reads each old block of a chunk over
+    the link and writes it to HBM (its counted bytes are both); Insert then
+    writes the chunk's output blocks back over the link.  So the link
+    carries the output dictionary once in each direction, half the staging
+    kernel's counted bytes: staging is held against the H2D rate, Insert's
+    write-back against the D2H rate."""
+    tiered = {}
+    k = tier_k.get("compute_ranks")
+    if k and k["GBps"]:
+        tiered["compute_ranks"] = {"GBps": k["GBps"], "ms": k["ms_per_step"], "link_GBps": k["GBps"],
+                                   "frac_of_link": round(k["GBps"] / rnd, 3), "link_roofline": "random 32-byte reads"}
+    st, mg = tier_k.get("insert_stage"), tier_k.get("insert_merge")
+    if st and st["GBps"]:
+        link_bytes = st["GBps"] * 1e9 * st["ms_per_step"] / 1e3 / 2
+        tiered["link_bytes_per_direction"] = int(link_bytes)
+        for name, k, rate, roof in (("insert_stage", st, h2d, "H2D copy (old blocks read over the link)"),
+                                    ("insert_merge", mg, d2h, "D2H copy (output blocks written over the link)")):
+            if k and k["ms_per_step"] > 0:
+                lg = link_bytes / (k["ms_per_step"] / 1e3) / 1e9
+                tiered[name] = {"GBps": k["GBps"], "ms": k["ms_per_step"], "link_GBps": round(lg, 1),
+                                "frac_of_link": round(lg / rate, 3), "link_roofline": roof}
+    return tiered
+
+
 def measure_served(sb, torch, w_res, requests, local, stream, peak):
     """The serving workload: a resident index of the 20M x 100 bp reads
     under an 8 GB HBM budget, then the append requests served closed-loop
@@ -515,27 +542,7 @@ def measure_served(sb, torch, w_res, requests, local, stream, peak):
     rep2 = measure_serving(sb, ix2, small_reqs[1:])
     ix2.close()
     link = bw
-    tiered = {}
-    k = tier_k.get("compute_ranks")
-    if k and k["GBps"]:
-        # every rank query's block read crosses the link
-        tiered["compute_ranks"] = {"GBps": k["GBps"], "ms": k["ms_per_step"], "link_GBps": k["GBps"],
-                                   "frac_of_link": round(k["GBps"] / rnd, 3), "link_roofline": "random 32-byte reads"}
-    st, mg = tier_k.get("insert_stage"), tier_k.get("insert_merge")
-    if st and st["GBps"]:
-        # the staging kernel reads each old block of a chunk over the link and
-        # writes it to HBM (its counted bytes are both); Insert then writes
-        # the chunk's output blocks back over the link.  So the link carries
-        # the output dictionary once in each direction: half the staging
-        # kernel's counted bytes.
-        link_bytes = st["GBps"] * 1e9 * st["ms_per_step"] / 1e3 / 2
-        tiered["link_bytes_per_direction"] = int(link_bytes)
-        for name, k, rate, roof in (("insert_stage", st, h2d, "H2D copy (old blocks read over the link)"),
-                                    ("insert_merge", mg, d2h, "D2H copy (output blocks written over the link)")):
-            if k and k["ms_per_step"] > 0:
-                lg = link_bytes / (k["ms_per_step"] / 1e3) / 1e9
-                tiered[name] = {"GBps": k["GBps"], "ms": k["ms_per_step"], "link_GBps": round(lg, 1),
-                                "frac_of_link": round(lg / rate, 3), "link_roofline": roof}
+    tiered = host_link_table(tier_k, h2d, d2h, rnd)
     out["host_tier"] = {"resident_reads": m2, "hbm_budget": 512 << 20, "build_s": build2,
                         "build_Mbps": int(small_off[-1]) / build2 / 1e6, "memory": {"hbm": hbm2, "host": host2},
                         "host_bits_per_row": 8.0 * host2 / n2, "host_link": link, "tiered_kernels": tiered,

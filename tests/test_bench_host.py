@@ -90,3 +90,22 @@ def test_reference_arm_is_silent_on_other_ranks(monkeypatch):
     with redirect_stdout(buf):
         assert bench.run_reference(args) == 0
     assert buf.getvalue() == ""
+
+
+def test_host_link_table_counts_the_bytes_that_cross_the_link():
+    # kernel rows as kernel_table gives them (one tiered append)
+    tier_k = {"compute_ranks": {"GBps": 90.0, "ms_per_step": 1.0},
+              "insert_stage": {"GBps": 400.0, "ms_per_step": 1.0},  # 400 MB counted: 200 MB read + 200 MB written
+              "insert_merge": {"GBps": 150.0, "ms_per_step": 2.0}}
+    t = bench.host_link_table(tier_k, h2d=200.0, d2h=100.0, rnd=90.0)
+    assert t["link_bytes_per_direction"] == 200_000_000
+    assert t["compute_ranks"]["frac_of_link"] == pytest.approx(1.0)
+    # staging: 200 MB over the link in 1 ms = 200 GB/s, all of the H2D rate
+    assert t["insert_stage"]["link_GBps"] == pytest.approx(200.0)
+    assert t["insert_stage"]["frac_of_link"] == pytest.approx(1.0)
+    # Insert: the same 200 MB written back in 2 ms = 100 GB/s, all of D2H
+    assert t["insert_merge"]["link_GBps"] == pytest.approx(100.0)
+    assert t["insert_merge"]["frac_of_link"] == pytest.approx(1.0)
+    # no staging kernel (the dictionary fits HBM): no link rows for Insert
+    assert set(bench.host_link_table({"compute_ranks": tier_k["compute_ranks"]}, 200.0, 100.0, 90.0)) == \
+        {"compute_ranks"}
