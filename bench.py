@@ -240,11 +240,13 @@ def measure_serving(sb, idx, requests, rate_rps=None, seed=7):
             "offered_rps": rate_rps}
 
 
-def serving_report(sb, fresh, requests):
+def serving_report(sb, fresh, requests, check=None):
     """Closed loop for the sustained rate, then Poisson arrivals at 0.5x and
     0.9x of it (in requests/s).  Each run serves a freshly built resident
     index (fresh() builds one), so every run starts from the same index
-    size; each run reports the index's memory when it ends."""
+    size; each run reports the index's memory when it ends.  check(idx), if
+    given, runs on the closed loop's index after its timing (its result is
+    reported under "result_checks")."""
     out = {}
     rates = [None, 0.5, 0.9]
     sustained_rps = None
@@ -254,6 +256,8 @@ def serving_report(sb, fresh, requests):
         r = measure_serving(sb, idx, requests, rate_rps=rate, seed=7 if f is None else int(f * 100))
         hbm, host = sb.sbwt_memory(idx.handle)
         r["memory_after"] = {"hbm": hbm, "host": host}
+        if f is None and check is not None:
+            r["result_checks"] = check(idx)
         idx.close()
         if f is None:
             sustained_rps = r["requests"] / (r["bases"] / r["Mbps"] / 1e6)
@@ -360,18 +364,86 @@ def host_counts(stats):
     return {s["name"][5:]: s["launches"] for s in stats if s["name"].startswith("host:graph")}
 
 
+def symbol_counts(B, chunk: int = 1 << 26):
+    """Occurrences of each byte value in B, counted a chunk at a time (a
+    bincount of the whole array would widen it to 8-byte integers)."""
+    counts = np.zeros(256, np.int64)
+    for a in range(0, B.size, chunk):
+        counts += np.bincount(B[a:a + chunk], minlength=256)
+    return counts
+
+
+def lf_walks(B, parts, k: int = 32, seed: int = 11, block: int = 4096):
+    """Walks k sampled reads backwards through B by the LF mapping and
+    counts those that spell their read.  Row r (r < m) is read r's
+    terminator suffix; from there LF(i) = C[c] + rank(c, i), c = B[i], gives
+    the row of the suffix one symbol longer, and the walk ends at the row
+    whose B symbol is a terminator (the whole read).  rank comes from symbol
+    counts at every `block` rows.  parts: (reads, offsets) pairs in read-id
+    order.  Returns (walks that spelled their read, walks)."""
+    n = B.size
+    counts = symbol_counts(B)
+    C = np.concatenate([[0], np.cumsum(counts)[:-1]])
+    nb = n // block
+    occ = {}
+    step = (1 << 26) // block * block  # rows per chunk (whole blocks)
+    for c in np.nonzero(counts)[0]:
+        per = np.empty(nb, np.int64)
+        for a in range(0, nb * block, step):
+            z = min(nb * block, a + step)
+            per[a // block:z // block] = (B[a:z].reshape(-1, block) == c).sum(axis=1, dtype=np.int64)
+        occ[int(c)] = np.concatenate([[0], np.cumsum(per)])
+    sizes = [len(o) - 1 for _, o in parts]
+    starts = np.cumsum([0] + sizes)
+    m = int(starts[-1])
+    picks = np.random.default_rng(seed).choice(m, size=min(k, m), replace=False)
+    good = 0
+    for r in picks:
+        pi = int(np.searchsorted(starts, r, side="right")) - 1
+        reads, offs = parts[pi]
+        j = int(r - starts[pi])
+        want = reads[int(offs[j]):int(offs[j + 1])]
+        i, out = int(r), []
+        for _ in range(want.size + 1):
+            c = int(B[i])
+            if c == ord("$"):
+                break
+            out.append(c)
+            b = i // block
+            i = int(C[c] + occ[c][b] + np.count_nonzero(B[b * block:i] == c))
+        good += bytes(out[::-1]) == want.tobytes()
+    return good, len(picks)
+
+
+def result_checks(B, parts):
+    """Whole-B checks of an index built from `parts` ((reads, offsets) in
+    read-id order): its length, the symbol multiset, the terminator rows
+    (row r holds the last symbol of read r) and LF walks of sampled reads."""
+    m = sum(len(o) - 1 for _, o in parts)
+    bases = sum(int(o[-1]) for _, o in parts)
+    expect = np.zeros(256, np.int64)
+    lasts = []
+    for reads, offs in parts:
+        expect += symbol_counts(reads)
+        lens = np.diff(offs.astype(np.int64))
+        lasts.append(np.where(lens > 0, reads[np.maximum(offs[1:].astype(np.int64) - 1, 0)], ord("$")))
+    expect[ord("$")] += m
+    good, walks = lf_walks(B, parts)
+    return {"length_ok": bool(B.size == bases + m),
+            "multiset_ok": bool(np.array_equal(symbol_counts(B), expect)),
+            "terminator_rows_ok": bool(np.array_equal(B[:m], np.concatenate(lasts).astype(np.uint8))),
+            "lf_walks_ok": f"{good}/{walks}"}
+
+
 def check_b(B, w):
     """Cheap checks of a benchmarked B that tie the number to a correct
-    result: its length, the terminator count, the symbol multiset and the
-    terminator rows (row r holds the last symbol of read r)."""
-    assert len(B) == w.bases + w.m
-    counts = np.bincount(B, minlength=256)
-    expect = np.bincount(w.reads, minlength=256)
-    expect[ord("$")] += w.m
-    assert np.array_equal(counts, expect), "symbol multiset differs from the reads"
-    lens = np.diff(w.offsets.astype(np.int64))
-    last = np.where(lens > 0, w.reads[np.maximum(w.offsets[1:].astype(np.int64) - 1, 0)], ord("$"))
-    assert np.array_equal(B[: w.m], last.astype(np.uint8)), "terminator rows differ"
+    result (result_checks); any failure stops the run."""
+    r = result_checks(B, [(w.reads, w.offsets)])
+    assert r["length_ok"], "length differs"
+    assert r["multiset_ok"], "symbol multiset differs from the reads"
+    assert r["terminator_rows_ok"], "terminator rows differ"
+    good, walks = map(int, r["lf_walks_ok"].split("/"))
+    assert good == walks, f"LF walks of sampled reads: {r['lf_walks_ok']} spell their read"
 
 
 def measure_forms(sb, torch, timer, w, local, args, peak, plain_M, candidates, stream, dist=None):
@@ -498,7 +570,15 @@ def measure_served(sb, torch, w_res, requests, local, stream, peak):
     ix.append(*big)
     kern = kernel_table(sb.sbwt_get_kernel_stats(ix.handle), peak)
     ix.close()
-    report = serving_report(sb, fresh, requests)
+    def served_check(ix):
+        # the index holds the resident reads, then the requests' reads in
+        # arrival order (one submitting thread); reported, not asserted
+        try:
+            return result_checks(ix.bwt(), [(w_res.reads, w_res.offsets)] + list(requests))
+        except Exception as e:
+            return {"error": f"{type(e).__name__}: {e}"}
+
+    report = serving_report(sb, fresh, requests, check=served_check)
     out = {"workload": w_res.name, "resident_rows": n_rows, "resident_build_ms": build_ms,
            "resident_build_Mbps": w_res.bases / build_ms / 1e3, "memory_after_build": {"hbm": hbm, "host": host},
            "requests": len(requests), "request_bases": sum(int(o[-1]) for _, o in requests),

@@ -109,3 +109,58 @@ def test_host_link_table_counts_the_bytes_that_cross_the_link():
     # no staging kernel (the dictionary fits HBM): no link rows for Insert
     assert set(bench.host_link_table({"compute_ranks": tier_k["compute_ranks"]}, 200.0, 100.0, 90.0)) == \
         {"compute_ranks"}
+
+
+def _parts_and_oracle_bwt():
+    """A resident set and two requests (reads of mixed lengths, one empty),
+    and B of their concatenation in that order, by the oracle."""
+    import numpy as np
+
+    import oracle
+    import readgen
+    rng = np.random.default_rng(3)
+    parts = []
+    for n_reads, seed in ((40, 1), (15, 2), (9, 3)):
+        reads, off = readgen.uniform_reads(n_reads, 30, seed)
+        lens = rng.integers(0, 31, size=n_reads)
+        lens[0] = 0
+        keep = np.concatenate([reads[int(off[j]):int(off[j]) + int(lens[j])] for j in range(n_reads)])
+        parts.append((keep.astype(np.uint8), np.concatenate([[0], np.cumsum(lens)]).astype(np.uint64)))
+    reads = np.concatenate([r for r, _ in parts])
+    offs, base = [np.uint64(0)], 0
+    for r, o in parts:
+        offs.extend((o[1:] + np.uint64(base)).tolist())
+        base += int(o[-1])
+    oracle.build()
+    return parts, oracle.bwt(reads, np.array(offs, np.uint64))
+
+
+def test_result_checks_pass_on_the_oracle_bwt_and_lf_walks_catch_a_swap():
+    import numpy as np
+    parts, B = _parts_and_oracle_bwt()
+    m = sum(len(o) - 1 for _, o in parts)
+    r = bench.result_checks(B, parts)
+    assert r["length_ok"] and r["multiset_ok"] and r["terminator_rows_ok"]
+    assert r["lf_walks_ok"] == "32/32"
+    assert bench.lf_walks(B, parts, k=m, block=16) == (m, m)  # several checkpoints
+    # two rows past the terminator rows with different symbols swapped: the
+    # multiset and the terminator rows still agree, the walks through them do not
+    i = m + 5
+    j = next(x for x in range(B.size - 1, m, -1) if B[x] != B[i])
+    bad = B.copy()
+    bad[i], bad[j] = B[j], B[i]
+    r = bench.result_checks(bad, parts)
+    assert r["multiset_ok"] and r["terminator_rows_ok"]
+    good, walks = bench.lf_walks(bad, parts, k=m, block=16)
+    assert walks == m and good < m
+    # check_b stops the run on it (one part: the whole set as one workload)
+    reads = np.concatenate([p[0] for p in parts])
+    w = type("W", (), {})()
+    w.reads, w.m, w.bases = reads, m, int(reads.size)
+    offs = [0]
+    for _, o in parts:
+        offs.extend((o[1:].astype(np.int64) + offs[-1]).tolist())
+    w.offsets = np.array(offs, np.uint64)
+    bench.check_b(B, w)
+    with pytest.raises(AssertionError):
+        bench.check_b(np.concatenate([bad[:m], np.roll(bad[m:], 1)]), w)
