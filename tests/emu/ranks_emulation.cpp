@@ -9,10 +9,13 @@
 alignas(16) static unsigned long long g_dyn_smem[48 * 1024 / 8];  // the superblock counters' stage
 
 namespace sbwt {
+#include "alphabet.inc"
 #include "text.inc"
 #include "dict.inc"
 #include "ranks.inc"
 #include "gather.inc"
+#include "queries.inc"
+#include "unpack.inc"
 }  // namespace sbwt
 using namespace sbwt;
 
@@ -84,5 +87,60 @@ extern "C" int emu_bint_gather(const uint32_t* text, uint64_t text_words, const 
     memcpy(gsa, g_gsa, n * 4ull);
     memcpy(ins_i0, g_plan, (nsb + 1) * 4);
     for (auto& m : maps) munmap(m.first, m.second);
+    return 0;
+}
+
+// rank(c, k) queries (c = 4: the terminator) and FM-index counts of
+// patterns over the 2-bit dictionary of sampling 64 K rows (n rows), and
+// the read-back of rows [r0, r1) (r0 a multiple of 64) as bytes.
+template <int K>
+static void run_queries(const unsigned long long* words, const unsigned long long* super, const unsigned long long* C,
+                        unsigned long long n, const uint8_t* codes, const unsigned long long* ks, uint64_t q,
+                        unsigned long long* rank_out, const uint8_t* pats, uint64_t pat_bytes,
+                        const unsigned long long* offs, uint64_t npat, unsigned long long* count_out,
+                        unsigned long long r0, unsigned long long r1, uint8_t* bytes) {
+    std::vector<std::pair<void*, size_t>> maps;
+    const uint64_t nw = (n / (64ull * K) + 1) * Occ<K>::kWords, nsb = (n >> 16) + 1;
+    const unsigned long long* g_words = guarded(words, nw, maps);
+    const unsigned long long* g_super = guarded(super, 4 * nsb, maps);
+    const unsigned long long* g_C = guarded(C, 4, maps);
+    const uint8_t* g_codes = guarded(codes, q ? q : 1, maps);
+    const unsigned long long* g_ks = guarded(ks, q ? q : 1, maps);
+    unsigned long long* g_rank = guarded(rank_out, q ? q : 1, maps);
+    const uint8_t* g_pats = guarded(pats, pat_bytes ? pat_bytes : 1, maps);
+    const unsigned long long* g_offs = guarded(offs, npat + 1, maps);
+    unsigned long long* g_count = guarded(count_out, npat ? npat : 1, maps);
+    // the read-back's output: whole 16-byte rows of the parts it writes
+    const size_t out_bytes = (size_t)((n + 63) / 64 * 64);
+    uint8_t* g_bytes = guarded(bytes, out_bytes, maps);
+    Alphabet16 alpha{};
+    const char* acgt = "ACGT";
+    for (int a = 0; a < 4; ++a) alpha.a[a] = (uint8_t)acgt[a];
+    const uint32_t alpha4 = 'A' | ('C' << 8) | ('G' << 16) | ((uint32_t)'T' << 24);
+    run_grid((unsigned)((q + kThreads - 1) / kThreads), kThreads,
+             [&] { rank_batch_kernel<2, K>(g_words, g_super, g_codes, g_ks, q, g_rank); });
+    run_grid((unsigned)((npat + kThreads - 1) / kThreads), kThreads,
+             [&] { count_kernel<2, K>(g_words, g_super, g_C, n, alpha, 4, g_pats, g_offs, npat, g_count); });
+    const uint64_t parts = (r1 + 63) / 64 - r0 / 64;
+    run_grid((unsigned)((parts + kThreads - 1) / kThreads), kThreads,
+             [&] { unpack_kernel<K>(g_words, r0, r1, alpha4, g_bytes); });
+    memcpy(rank_out, g_rank, q * 8);
+    memcpy(count_out, g_count, npat * 8);
+    memcpy(bytes, g_bytes, out_bytes);
+    for (auto& m : maps) munmap(m.first, m.second);
+}
+
+extern "C" int emu_queries(int k, const unsigned long long* words, const unsigned long long* super,
+                           const unsigned long long* C, unsigned long long n, const uint8_t* codes,
+                           const unsigned long long* ks, uint64_t q, unsigned long long* rank_out, const uint8_t* pats,
+                           uint64_t pat_bytes, const unsigned long long* offs, uint64_t npat,
+                           unsigned long long* count_out, unsigned long long r0, unsigned long long r1,
+                           uint8_t* bytes) {
+    if (k == 4)
+        run_queries<4>(words, super, C, n, codes, ks, q, rank_out, pats, pat_bytes, offs, npat, count_out, r0, r1, bytes);
+    else if (k == 2)
+        run_queries<2>(words, super, C, n, codes, ks, q, rank_out, pats, pat_bytes, offs, npat, count_out, r0, r1, bytes);
+    else
+        run_queries<1>(words, super, C, n, codes, ks, q, rank_out, pats, pat_bytes, offs, npat, count_out, r0, r1, bytes);
     return 0;
 }

@@ -48,6 +48,12 @@ def emu(tmp_path_factory):
     (d / "text.inc").write_text(_cut(hdr, "constexpr int kTextPadWords = 4;", "// Rank dictionary over B"))
     (d / "gather.inc").write_text(_cut(src, "// B_int and g_sa in one pass over SA_int",
                                        "// rank(c, k) queries, codes 0..kCodes-1"))
+    (d / "queries.inc").write_text(_cut(src, "// rank(c, k) queries, codes 0..kCodes-1",
+                                        "// The read-back of the 2-bit dictionary"))
+    (d / "unpack.inc").write_text(_cut(src, "// The read-back of the 2-bit dictionary",
+                                       "// The read-back for the 4-bit dictionary"))
+    kh = open(os.path.join(CSRC, "sbwt_kernels.cuh")).read()
+    (d / "alphabet.inc").write_text(_cut(kh, "struct Alphabet16 {", "// pack.cu:"))
     kern = _cut(src, "// Algorithm 2, one thread per read:", "// B_int and g_sa in one pass over SA_int")
     kern = kern.replace("extern __shared__ unsigned long long s_raw[];", "unsigned long long* s_raw = g_dyn_smem;")
     (d / "ranks.inc").write_text(kern)
@@ -60,6 +66,8 @@ def emu(tmp_path_factory):
     L.emu_compute_ranks.restype = I
     L.emu_bint_gather.argtypes = [P, U64, P, U64, U64, P, P, U64, U32, P, P, P, U64, I]
     L.emu_bint_gather.restype = I
+    L.emu_queries.argtypes = [I, P, P, P, U64, P, P, U64, P, P, U64, P, U64, P, U64, U64, P]
+    L.emu_queries.restype = I
     return L
 
 
@@ -212,3 +220,72 @@ def test_gather_writes_bint_gsa_and_the_insert_plan(emu, n_reads, seed):
     r = gsa_want.astype(np.int64) + np.arange(n)
     plan_want = np.searchsorted(r, np.arange(nsb + 1, dtype=np.int64) << shift, side="left")
     assert np.array_equal(plan.astype(np.int64), plan_want)
+
+
+# ---- queries and read-back over a finished dictionary ----------------------
+
+def _occurrences(reads, off, pat: bytes) -> int:
+    """Occurrences of pat inside the reads (overlapping, none across a read
+    end); the empty pattern occurs at every row."""
+    if not pat:
+        return int(off[-1]) + len(off) - 1
+    total = 0
+    for j in range(len(off) - 1):
+        s = reads[int(off[j]):int(off[j + 1])].tobytes()
+        i = s.find(pat)
+        while i >= 0:
+            total += 1
+            i = s.find(pat, i + 1)
+    return total
+
+
+@pytest.mark.timeout(600)
+@pytest.mark.parametrize("k", [1, 2, 4])
+def test_rank_queries_counts_and_read_back(emu, k):
+    """rank(c, k) for the four codes and the terminator, FM-index counts of
+    patterns (backward search with Lemma 1's C) and the read-back of row
+    ranges, over the dictionary of the oracle's B (two superblocks)."""
+    rng = np.random.default_rng(70 + k)
+    g = readgen.genome(5_000, 9)
+    reads, off = readgen.sampled_reads(g, 1_400, 90, 0.01, 10 + k)
+    m = len(off) - 1
+    B = oracle.bwt(reads, off)
+    n = len(B)
+    assert n > 1 << 16
+    words, sup, C = dictionary(B, m, k)
+    # rank queries: random rows plus the edges (row 0, the end, block and
+    # superblock boundaries)
+    edges = np.array([0, 1, 63, 64, 65, 64 * k, (1 << 16) - 1, 1 << 16, (1 << 16) + 1, n - 1, n], np.uint64)
+    ks = np.concatenate([rng.integers(0, n + 1, size=3000).astype(np.uint64), np.repeat(edges, 5)])
+    codes = np.concatenate([rng.integers(0, 5, size=3000), np.tile(np.arange(5), edges.size)]).astype(np.uint8)
+    sym = np.frombuffer(b"ACGT$", np.uint8)
+    cum = {c: np.concatenate([[0], np.cumsum(B == sym[c])]) for c in range(5)}
+    want_rank = np.array([cum[int(c)][int(x)] for c, x in zip(codes, ks)], np.uint64)
+    # patterns: substrings of the reads, random strings, a foreign byte, empty
+    pats = []
+    for _ in range(150):
+        j = int(rng.integers(0, m))
+        r = reads[int(off[j]):int(off[j + 1])]
+        a = int(rng.integers(0, max(1, r.size - 1)))
+        pats.append(r[a:a + int(rng.integers(1, 25))].tobytes())
+    pats += [bytes(rng.choice(np.frombuffer(b"ACGT", np.uint8), size=int(L))) for L in (1, 2, 3, 6, 12)]
+    pats += [b"ACGNT", b"", b"A" * 40]
+    pbytes = np.frombuffer(b"".join(pats) or b"\0", np.uint8).copy()
+    poffs = np.concatenate([[0], np.cumsum([len(p) for p in pats])]).astype(np.uint64)
+    want_count = np.array([_occurrences(reads, off, p) for p in pats], np.uint64)
+    # read-back of rows [r0, r1): a range from a part start to a ragged end
+    r0, r1 = 64 * 37, n - 5
+    rank_out = np.zeros(ks.size, np.uint64)
+    count_out = np.zeros(len(pats), np.uint64)
+    out = np.full((n + 63) // 64 * 64, 0xEE, np.uint8)
+    assert emu.emu_queries(k, ctypes.c_void_p(words.ctypes.data), ctypes.c_void_p(sup.ctypes.data),
+                           ctypes.c_void_p(C.ctypes.data), n, ctypes.c_void_p(codes.ctypes.data),
+                           ctypes.c_void_p(ks.ctypes.data), ks.size, ctypes.c_void_p(rank_out.ctypes.data),
+                           ctypes.c_void_p(pbytes.ctypes.data), pbytes.size, ctypes.c_void_p(poffs.ctypes.data),
+                           len(pats), ctypes.c_void_p(count_out.ctypes.data), r0, r1,
+                           ctypes.c_void_p(out.ctypes.data)) == 0
+    assert np.array_equal(rank_out, want_rank)
+    assert np.array_equal(count_out, want_count)
+    assert want_count[:150].min() >= 1 and want_count[-3] == 0 and want_count[-2] == n
+    assert np.array_equal(out[r0:r1], B[r0:r1])
+    assert np.all(out[:r0] == 0xEE) and np.all(out[r1:] == 0xEE)
