@@ -87,6 +87,13 @@ static inline int __ffs(unsigned x) { return __builtin_ffs((int)x); }
 static inline int __clz(unsigned x) { return x ? __builtin_clz(x) : 32; }
 static inline unsigned atomicAdd(uint32_t* p, uint32_t v) { return std::atomic_ref<uint32_t>(*p).fetch_add(v); }
 static inline unsigned atomicOr(uint32_t* p, uint32_t v) { return std::atomic_ref<uint32_t>(*p).fetch_or(v); }
+static inline unsigned long long atomicMax(unsigned long long* p, unsigned long long v) {
+    std::atomic_ref<unsigned long long> r(*p);
+    unsigned long long cur = r.load();
+    while (cur < v && !r.compare_exchange_weak(cur, v)) {
+    }
+    return cur;
+}
 static inline unsigned atomicMin(uint32_t* p, uint32_t v) {
     std::atomic_ref<uint32_t> a(*p);
     uint32_t cur = a.load();
@@ -162,7 +169,7 @@ static void run_grid(unsigned grid, unsigned threads, F body) {
     for (unsigned b = 0; b < grid; ++b) {
         g_cta.bar = std::make_unique<std::barrier<>>(threads);
         g_cta.xch.assign(threads, 0);
-        std::vector<EmuWarp> warps(threads / 32);
+        std::vector<EmuWarp> warps((threads + 31) / 32);  // a one-thread grid still gets its (unused) warp
         std::vector<std::thread> th;
         for (unsigned i = 0; i < threads; ++i)
             th.emplace_back([&, b, i] {
