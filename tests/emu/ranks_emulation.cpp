@@ -16,6 +16,7 @@ namespace sbwt {
 #include "gather.inc"
 #include "queries.inc"
 #include "unpack.inc"
+#include "unpack_w.inc"
 }  // namespace sbwt
 using namespace sbwt;
 
@@ -142,5 +143,42 @@ extern "C" int emu_queries(int k, const unsigned long long* words, const unsigne
         run_queries<2>(words, super, C, n, codes, ks, q, rank_out, pats, pat_bytes, offs, npat, count_out, r0, r1, bytes);
     else
         run_queries<1>(words, super, C, n, codes, ks, q, rank_out, pats, pat_bytes, offs, npat, count_out, r0, r1, bytes);
+    return 0;
+}
+
+// The same over the 4-bit dictionary (blocks of 64 rows, superblocks of
+// 4096 rows, 16 codes; c = 16: the terminator), alphabet of sigma symbols.
+extern "C" int emu_queries_w(const OccBlockW* blocks, const unsigned long long* super, const unsigned long long* C,
+                             unsigned long long n, const uint8_t* alpha_bytes, int sigma, const uint8_t* codes,
+                             const unsigned long long* ks, uint64_t q, unsigned long long* rank_out,
+                             const uint8_t* pats, uint64_t pat_bytes, const unsigned long long* offs, uint64_t npat,
+                             unsigned long long* count_out, unsigned long long r0, unsigned long long r1,
+                             uint8_t* bytes) {
+    std::vector<std::pair<void*, size_t>> maps;
+    const uint64_t nb = (n >> kOccShift) + 1, nsb = (nb + kBlocksPerSuperW - 1) / kBlocksPerSuperW;
+    const OccBlockW* g_blocks = guarded(blocks, nb, maps);
+    const unsigned long long* g_super = guarded(super, (size_t)kSigmaW * nsb, maps);
+    const unsigned long long* g_C = guarded(C, kSigmaW, maps);
+    const uint8_t* g_codes = guarded(codes, q ? q : 1, maps);
+    const unsigned long long* g_ks = guarded(ks, q ? q : 1, maps);
+    unsigned long long* g_rank = guarded(rank_out, q ? q : 1, maps);
+    const uint8_t* g_pats = guarded(pats, pat_bytes ? pat_bytes : 1, maps);
+    const unsigned long long* g_offs = guarded(offs, npat + 1, maps);
+    unsigned long long* g_count = guarded(count_out, npat ? npat : 1, maps);
+    const size_t out_bytes = (size_t)((n + 63) / 64 * 64);
+    uint8_t* g_bytes = guarded(bytes, out_bytes, maps);
+    Alphabet16 alpha{};
+    for (int a = 0; a < sigma && a < 16; ++a) alpha.a[a] = alpha_bytes[a];
+    run_grid((unsigned)((q + kThreads - 1) / kThreads), kThreads,
+             [&] { rank_batch_kernel<4, 1>(g_blocks, g_super, g_codes, g_ks, q, g_rank); });
+    run_grid((unsigned)((npat + kThreads - 1) / kThreads), kThreads,
+             [&] { count_kernel<4, 1>(g_blocks, g_super, g_C, n, alpha, sigma, g_pats, g_offs, npat, g_count); });
+    const uint64_t parts = (r1 + 63) / 64 - r0 / 64;
+    run_grid((unsigned)((parts + kThreads - 1) / kThreads), kThreads,
+             [&] { unpack_w_kernel(g_blocks, r0, r1, alpha, g_bytes); });
+    memcpy(rank_out, g_rank, q * 8);
+    memcpy(count_out, g_count, npat * 8);
+    memcpy(bytes, g_bytes, out_bytes);
+    for (auto& m : maps) munmap(m.first, m.second);
     return 0;
 }

@@ -27,7 +27,7 @@ import oracle
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 CSRC = os.path.join(ROOT, "paper_1410_0562_gb300", "csrc")
 EMU = os.path.join(os.path.dirname(os.path.abspath(__file__)), "emu", "insert_w_emulation.cpp")
-ALPHA = b"ACGTNRYKMSWB"  # 12 symbols
+ALPHA = b"ABCGKMNRSTWY"  # 12 symbols, in increasing byte order
 SUPER_ROWS_W = 4096
 
 

@@ -52,6 +52,7 @@ def emu(tmp_path_factory):
                                         "// The read-back of the 2-bit dictionary"))
     (d / "unpack.inc").write_text(_cut(src, "// The read-back of the 2-bit dictionary",
                                        "// The read-back for the 4-bit dictionary"))
+    (d / "unpack_w.inc").write_text(_cut(src, "// The read-back for the 4-bit dictionary", "uint32_t alpha4_of("))
     kh = open(os.path.join(CSRC, "sbwt_kernels.cuh")).read()
     (d / "alphabet.inc").write_text(_cut(kh, "struct Alphabet16 {", "// pack.cu:"))
     kern = _cut(src, "// Algorithm 2, one thread per read:", "// B_int and g_sa in one pass over SA_int")
@@ -68,6 +69,8 @@ def emu(tmp_path_factory):
     L.emu_bint_gather.restype = I
     L.emu_queries.argtypes = [I, P, P, P, U64, P, P, U64, P, P, U64, P, U64, P, U64, U64, P]
     L.emu_queries.restype = I
+    L.emu_queries_w.argtypes = [P, P, P, U64, P, I, P, P, U64, P, P, U64, P, U64, P, U64, U64, P]
+    L.emu_queries_w.restype = I
     return L
 
 
@@ -287,5 +290,60 @@ def test_rank_queries_counts_and_read_back(emu, k):
     assert np.array_equal(rank_out, want_rank)
     assert np.array_equal(count_out, want_count)
     assert want_count[:150].min() >= 1 and want_count[-3] == 0 and want_count[-2] == n
+    assert np.array_equal(out[r0:r1], B[r0:r1])
+    assert np.all(out[:r0] == 0xEE) and np.all(out[r1:] == 0xEE)
+
+
+@pytest.mark.timeout(600)
+def test_rank_queries_counts_and_read_back_4bit(emu):
+    """The same over the 4-bit dictionary of a 12-symbol alphabet: rank for
+    every code (unused codes count zero) and the terminator, counts, and the
+    read-back, over the oracle's B packed into the 4-bit layout."""
+    from test_insert_w_emulation import ALPHA, codes_of, pack_dict_w
+    rng = np.random.default_rng(91)
+    sigma = len(ALPHA)
+    g = readgen.genome_alpha(3_000, 5, np.full(sigma, 1.0 / sigma))
+    reads, off = readgen.sampled_reads_alpha(g, 250, 60, 0.01, 6, ALPHA)
+    m = len(off) - 1
+    B = oracle.bwt(reads, off, ALPHA)
+    n = len(B)
+    assert n > 3 * 4096
+    blocks = pack_dict_w(B)
+    nb = (n >> 6) + 1
+    nsb = (nb + 63) // 64
+    code = np.where(B == ord("$"), -1, codes_of(B))
+    sup = np.zeros((nsb, 16), np.uint64)
+    for s in range(1, nsb):
+        head = code[: s * 4096]
+        sup[s] = [np.count_nonzero(head == c) for c in range(16)]
+    tot = np.array([np.count_nonzero(code == c) for c in range(16)], np.uint64)
+    C = (np.uint64(m) + np.concatenate([[0], np.cumsum(tot)[:-1]])).astype(np.uint64)
+    edges = np.array([0, 1, 63, 64, 4095, 4096, 4097, n - 1, n], np.uint64)
+    ks = np.concatenate([rng.integers(0, n + 1, size=2000).astype(np.uint64), np.repeat(edges, 17)])
+    codes = np.concatenate([rng.integers(0, 17, size=2000), np.tile(np.arange(17), edges.size)]).astype(np.uint8)
+    cum = {c: np.concatenate([[0], np.cumsum(code == c)]) for c in range(16)}
+    cum[16] = np.concatenate([[0], np.cumsum(B == ord("$"))])
+    want_rank = np.array([cum[int(c)][int(x)] for c, x in zip(codes, ks)], np.uint64)
+    pats = []
+    for _ in range(80):
+        j = int(rng.integers(0, m))
+        r = reads[int(off[j]):int(off[j + 1])]
+        a = int(rng.integers(0, max(1, r.size - 1)))
+        pats.append(r[a:a + int(rng.integers(1, 15))].tobytes())
+    pats += [b"ABCZ", b"", bytes(ALPHA[:3])]
+    pbytes = np.frombuffer(b"".join(pats), np.uint8).copy()
+    poffs = np.concatenate([[0], np.cumsum([len(p) for p in pats])]).astype(np.uint64)
+    want_count = np.array([_occurrences(reads, off, p) for p in pats], np.uint64)
+    r0, r1 = 64 * 11, n - 3
+    rank_out = np.zeros(ks.size, np.uint64)
+    count_out = np.zeros(len(pats), np.uint64)
+    out = np.full((n + 63) // 64 * 64, 0xEE, np.uint8)
+    alpha = np.frombuffer(ALPHA, np.uint8).copy()
+    p = lambda a: ctypes.c_void_p(a.ctypes.data)  # noqa: E731
+    assert emu.emu_queries_w(p(blocks), p(sup), p(C), n, p(alpha), sigma, p(codes), p(ks), ks.size, p(rank_out),
+                             p(pbytes), pbytes.size, p(poffs), len(pats), p(count_out), r0, r1, p(out)) == 0
+    assert np.array_equal(rank_out, want_rank)
+    assert np.array_equal(count_out, want_count)
+    assert want_count[:80].min() >= 1 and want_count[-3] == 0 and want_count[-2] == n
     assert np.array_equal(out[r0:r1], B[r0:r1])
     assert np.all(out[:r0] == 0xEE) and np.all(out[r1:] == 0xEE)
