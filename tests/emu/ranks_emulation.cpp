@@ -182,3 +182,46 @@ extern "C" int emu_queries_w(const OccBlockW* blocks, const unsigned long long* 
     for (auto& m : maps) munmap(m.first, m.second);
     return 0;
 }
+
+// ComputeRanks over the 4-bit dictionary (text of 4-bit codes, 8 per word),
+// the per-read (seg = 0) or segmented kernel, with the superblock counters
+// staged in shared memory or read from global memory.
+template <bool kStage>
+static void run_w(int seg, uint32_t segs, uint32_t seg_rows, const uint32_t* text, uint64_t text_words,
+                  const unsigned long long* offsets, unsigned long long nreads, const OccBlockW* blocks,
+                  const unsigned long long* super, const unsigned long long* C, unsigned long long n_ext,
+                  unsigned long long m_start, uint32_t* g, uint64_t n_int, uint32_t* d_err) {
+    std::vector<std::pair<void*, size_t>> maps;
+    const uint64_t nb = (n_ext >> kOccShift) + 1, nsb = (n_ext >> kSuperShiftW) + 1;
+    const uint32_t* g_text = guarded(text, text_words, maps);
+    const unsigned long long* g_off = guarded(offsets, nreads + 1, maps);
+    const OccBlockW* g_blocks = guarded(blocks, nb, maps);
+    const unsigned long long* g_super = guarded(super, (size_t)kSigmaW * nsb, maps);
+    const unsigned long long* g_C = guarded(C, kSigmaW, maps);
+    uint32_t* g_g = guarded(g, n_int, maps);
+    const uint64_t threads = seg ? nreads * segs : nreads;
+    run_grid((unsigned)((threads + kThreads - 1) / kThreads), kThreads, [&] {
+        if (seg)
+            compute_ranks_seg_kernel<uint32_t, kStage, 4, 1>(g_text, g_off, 0, nreads, segs, seg_rows, g_blocks,
+                                                            g_super, g_C, n_ext, m_start, g_g, d_err);
+        else
+            compute_ranks_kernel<uint32_t, kStage, 4, 1>(g_text, g_off, 0, nreads, g_blocks, g_super, g_C, n_ext,
+                                                        m_start, g_g, d_err);
+    });
+    memcpy(g, g_g, n_int * 4);
+    for (auto& m : maps) munmap(m.first, m.second);
+}
+
+extern "C" int emu_compute_ranks_w(int staged, int seg, uint32_t segs, uint32_t seg_rows, const uint32_t* text,
+                                   uint64_t text_words, const unsigned long long* offsets, unsigned long long nreads,
+                                   const OccBlockW* blocks, const unsigned long long* super,
+                                   const unsigned long long* C, unsigned long long n_ext, unsigned long long m_start,
+                                   uint32_t* g, uint64_t n_int, uint32_t* d_err) {
+    if (staged)
+        run_w<true>(seg, segs, seg_rows, text, text_words, offsets, nreads, blocks, super, C, n_ext, m_start, g,
+                    n_int, d_err);
+    else
+        run_w<false>(seg, segs, seg_rows, text, text_words, offsets, nreads, blocks, super, C, n_ext, m_start, g,
+                     n_int, d_err);
+    return 0;
+}

@@ -71,6 +71,8 @@ def emu(tmp_path_factory):
     L.emu_queries.restype = I
     L.emu_queries_w.argtypes = [P, P, P, U64, P, I, P, P, U64, P, P, U64, P, U64, P, U64, U64, P]
     L.emu_queries_w.restype = I
+    L.emu_compute_ranks_w.argtypes = [I, I, U32, U32, P, U64, P, U64, P, P, P, U64, U64, P, U64, P]
+    L.emu_compute_ranks_w.restype = I
     return L
 
 
@@ -294,6 +296,22 @@ def test_rank_queries_counts_and_read_back(emu, k):
     assert np.all(out[:r0] == 0xEE) and np.all(out[r1:] == 0xEE)
 
 
+def dictionary_w(B: np.ndarray, m: int):
+    """Blocks, superblock counters (16 per 4096 rows) and C[] of B in the
+    4-bit layout of the 12-symbol alphabet (m terminators)."""
+    from test_insert_w_emulation import codes_of, pack_dict_w
+    n = len(B)
+    nsb = (((n >> 6) + 1) + 63) // 64
+    code = np.where(B == ord("$"), -1, codes_of(B))
+    sup = np.zeros((nsb, 16), np.uint64)
+    for s in range(1, nsb):
+        head = code[: s * 4096]
+        sup[s] = [np.count_nonzero(head == c) for c in range(16)]
+    tot = np.array([np.count_nonzero(code == c) for c in range(16)], np.uint64)
+    C = (np.uint64(m) + np.concatenate([[0], np.cumsum(tot)[:-1]])).astype(np.uint64)
+    return pack_dict_w(B), sup.ravel(), C
+
+
 @pytest.mark.timeout(600)
 def test_rank_queries_counts_and_read_back_4bit(emu):
     """The same over the 4-bit dictionary of a 12-symbol alphabet: rank for
@@ -308,16 +326,8 @@ def test_rank_queries_counts_and_read_back_4bit(emu):
     B = oracle.bwt(reads, off, ALPHA)
     n = len(B)
     assert n > 3 * 4096
-    blocks = pack_dict_w(B)
-    nb = (n >> 6) + 1
-    nsb = (nb + 63) // 64
+    blocks, sup, C = dictionary_w(B, m)
     code = np.where(B == ord("$"), -1, codes_of(B))
-    sup = np.zeros((nsb, 16), np.uint64)
-    for s in range(1, nsb):
-        head = code[: s * 4096]
-        sup[s] = [np.count_nonzero(head == c) for c in range(16)]
-    tot = np.array([np.count_nonzero(code == c) for c in range(16)], np.uint64)
-    C = (np.uint64(m) + np.concatenate([[0], np.cumsum(tot)[:-1]])).astype(np.uint64)
     edges = np.array([0, 1, 63, 64, 4095, 4096, 4097, n - 1, n], np.uint64)
     ks = np.concatenate([rng.integers(0, n + 1, size=2000).astype(np.uint64), np.repeat(edges, 17)])
     codes = np.concatenate([rng.integers(0, 17, size=2000), np.tile(np.arange(17), edges.size)]).astype(np.uint8)
@@ -347,3 +357,64 @@ def test_rank_queries_counts_and_read_back_4bit(emu):
     assert want_count[:80].min() >= 1 and want_count[-3] == 0 and want_count[-2] == n
     assert np.array_equal(out[r0:r1], B[r0:r1])
     assert np.all(out[:r0] == 0xEE) and np.all(out[r1:] == 0xEE)
+
+
+def append_text_w(reads: np.ndarray, off: np.ndarray) -> np.ndarray:
+    """4-bit codes (index in the 12-symbol alphabet) of an append's positions,
+    8 per word, MSB first, terminators as code 0, four zero words of padding."""
+    from test_insert_w_emulation import codes_of
+    m = len(off) - 1
+    npos = int(off[-1]) + m
+    codes = np.zeros(npos, np.uint32)
+    pos = np.arange(int(off[-1])) + np.repeat(np.arange(m), np.diff(off.astype(np.int64)))
+    codes[pos] = codes_of(reads).astype(np.uint32)
+    nw = (npos + 7) // 8
+    padded = np.zeros(nw * 8, np.uint32)
+    padded[:npos] = codes
+    sh = (28 - 4 * np.arange(8)).astype(np.uint32)
+    words = np.bitwise_or.reduce(padded.reshape(nw, 8) << sh, axis=1).astype(np.uint32)
+    return np.concatenate([words, np.zeros(4, np.uint32)])
+
+
+def ragged_alpha(g, n, lo, hi, seed):
+    """Reads of lengths lo..hi (some empty) sampled from genome g over the
+    12-symbol alphabet."""
+    from test_insert_w_emulation import ALPHA
+    rng = np.random.default_rng(seed)
+    full, _ = readgen.sampled_reads_alpha(g, n, hi, 0.02, seed, ALPHA)
+    lens = rng.integers(lo, hi + 1, size=n)
+    lens[::37] = 0
+    rows = full.reshape(n, hi)
+    reads = np.concatenate([rows[j, :lens[j]] for j in range(n)]).astype(np.uint8)
+    return reads, readgen.offsets_from_lengths(lens)
+
+
+@pytest.mark.timeout(600)
+@pytest.mark.parametrize("seg", [False, True])
+@pytest.mark.parametrize("staged", [True, False])
+def test_compute_ranks_4bit_matches_direct_counts(emu, seg, staged):
+    """ComputeRanks over the 4-bit dictionary (both kernels, the superblock
+    counters staged in shared memory or read from global memory) against the
+    oracle's direct count of smaller old suffixes."""
+    from test_insert_w_emulation import ALPHA
+    sigma = len(ALPHA)
+    g_ = readgen.genome_alpha(4_000, 17, np.full(sigma, 1.0 / sigma))
+    hi = 1500 if seg else 90
+    old = ragged_alpha(g_, 120 if seg else 300, 0, hi, 21)
+    new = ragged_alpha(g_, 10 if seg else 120, 513 if seg else 0, hi, 22)
+    B = oracle.bwt(old[0], old[1], ALPHA)
+    m_ext = len(old[1]) - 1
+    blocks, sup, C = dictionary_w(B, m_ext)
+    text = append_text_w(*new)
+    nreads = len(new[1]) - 1
+    n_int = int(new[1][-1]) + nreads
+    max_len = int(np.diff(new[1].astype(np.int64)).max())
+    segs = max_len // SEG_ROWS + 1
+    g = np.zeros(max(n_int, 1), np.uint32)
+    err = ctypes.c_uint32(0)
+    p = lambda a: ctypes.c_void_p(a.ctypes.data)  # noqa: E731
+    off = np.ascontiguousarray(new[1], np.uint64)
+    assert emu.emu_compute_ranks_w(int(staged), int(seg), segs, SEG_ROWS, p(text), len(text), p(off), nreads,
+                                   p(blocks), p(sup), p(C), len(B), m_ext, p(g), n_int, ctypes.byref(err)) == 0
+    assert err.value == 0
+    assert np.array_equal(g[:n_int], expected_g(old, new))
