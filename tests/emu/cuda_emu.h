@@ -82,6 +82,7 @@ static inline int __syncthreads_count(int pred) {
     return c;
 }
 static inline int __syncthreads_or(int pred) { return __syncthreads_count(pred) > 0; }
+static inline int __syncthreads_and(int pred) { return __syncthreads_count(pred) == (int)blockDim.x; }
 static inline int __popc(unsigned x) { return __builtin_popcount(x); }
 static inline int __ffs(unsigned x) { return __builtin_ffs((int)x); }
 static inline int __clz(unsigned x) { return x ? __builtin_clz(x) : 32; }

@@ -1,4 +1,4 @@
-"""The counting phases of one radix pass (csrc/radix.cu) run on the CPU.
+"""One radix pass (csrc/radix.cu) run on the CPU: its counting phases and its scatter.
 
 The upsweep counts the digits of each chunk of whole 2048-key tiles (a
 persistent grid of G CTAs, chunk c holding tiles [c per, (c+1) per) of the
@@ -8,6 +8,11 @@ the number of keys with a smaller digit plus the keys of the same digit in
 earlier chunks, which is what a stable counting sort gives.  The kernels'
 text is cut out of the CUDA source and compiled for the host with
 tests/emu/cuda_emu.h (the one inline-PTX load becomes two plain loads).
+The downsweep's tile copies and their mbarrier are inline PTX in helper
+functions; the harness gives host versions of those helpers (the copy done
+at once, completing its bytes on the barrier's phase) and checks the bulk
+copies' 16-byte rule, so a whole pass runs and is compared with a stable
+counting sort.
 Checked against numpy on keys whose count is not a multiple of the tile,
 with grids that leave the last chunks empty.  No GPU is used."""
 import ctypes
@@ -43,6 +48,11 @@ def emu(tmp_path_factory):
     ptx = 'asm volatile("ld.global.cg.v2.u64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "l"(p));'
     assert ptx in count
     (d / "radix_count.inc").write_text(count.replace(ptx, "a = p[0];\n    b = p[1];"))
+    down = _cut(src, "// The scatter of one pass over this CTA's chunk",
+                "// ---------------------------------------------------------------------------\n// Fused sort")
+    dyn = "extern __shared__ __align__(128) unsigned char smem[];"
+    assert down.count(dyn) == 1
+    (d / "radix_down.inc").write_text(down.replace(dyn, "unsigned char* smem = g_dyn_smem;"))
     lib = d / "libradixemu.so"
     subprocess.check_call(["g++", "-O1", "-std=c++20", "-shared", "-fPIC", "-pthread", "-I", str(d), "-o", str(lib),
                            EMU])
@@ -50,6 +60,8 @@ def emu(tmp_path_factory):
     P, U32, I = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_int
     L.emu_radix_count.argtypes = [P, U32, I, U32, P, P]
     L.emu_radix_count.restype = I
+    L.emu_radix_pass.argtypes = [P, P, U32, I, U32, I, P, P, P]
+    L.emu_radix_pass.restype = I
     return L
 
 
@@ -91,3 +103,31 @@ def test_chunk_offsets_are_those_of_a_stable_counting_sort(emu, n, grid, shift):
         order[nxt[c, dg]] = i
         nxt[c, dg] += 1
     assert np.array_equal(order, np.argsort(digits, kind="stable"))
+
+
+@pytest.mark.timeout(600)
+@pytest.mark.parametrize("n,grid,shift,pairs", [(50_001, 7, 0, 0), (50_001, 40, 8, 1), (6_000, 5, 16, 0),
+                                                (2_048, 3, 0, 1), (3 * TILE, 2, 24, 1), (1, 1, 0, 0), (0, 4, 0, 1)])
+def test_one_pass_is_a_stable_counting_sort(emu, n, grid, shift, pairs):
+    """The whole pass (upsweep, chunk scan, downsweep with its bulk-copied
+    tiles) puts every key, and its value, where a stable counting sort by
+    the pass's digit does."""
+    rng = np.random.default_rng(n + 3 * grid + shift)
+    digits = np.where(rng.random(n) < 0.5, rng.integers(0, 4, n), rng.integers(0, 256, n)).astype(np.uint64)
+    keys = (digits << np.uint64(shift)) | (rng.integers(0, 1 << 20, n).astype(np.uint64) << np.uint64(40))
+    keys |= rng.integers(0, 1 << 8, n).astype(np.uint64) << np.uint64(32 if shift != 32 else 0)
+    vals = rng.permutation(n).astype(np.uint32)
+    out_k = np.zeros(max(n, 1), np.uint64)
+    out_v = np.zeros(max(n, 1), np.uint32)
+    err = np.zeros(1, np.uint32)
+    kp = keys if n else np.zeros(1, np.uint64)
+    vp = vals if n else np.zeros(1, np.uint32)
+    rc = emu.emu_radix_pass(ctypes.c_void_p(kp.ctypes.data), ctypes.c_void_p(vp.ctypes.data), n, shift, grid, pairs,
+                            ctypes.c_void_p(out_k.ctypes.data), ctypes.c_void_p(out_v.ctypes.data),
+                            ctypes.c_void_p(err.ctypes.data))
+    assert rc == 0, "a bulk copy broke the 16-byte rule"
+    assert err[0] == 0
+    order = np.argsort(digits, kind="stable")
+    assert np.array_equal(out_k[:n], keys[order])
+    if pairs:
+        assert np.array_equal(out_v[:n], vals[order])
