@@ -2,7 +2,8 @@
 // tests: sa_digit_keys (each suffix's element and the first radix pass's
 // per-chunk digit counts) and sa_unit_begin (per window of the
 // bucket-sorted elements: the first bucket start and the long-suffix counts;
-// SA and rank of the short suffixes; the list of long rows with their keys).
+// SA and rank of the short suffixes; the list of long rows with their keys),
+// then the unit scan and the global-path gather of units too large for a CTA.
 //
 // The kernel text is compiled here unchanged (the test cuts it out of the
 // CUDA sources into the .inc files below) on the emulation in cuda_emu.h:
@@ -11,10 +12,13 @@
 #include "cuda_emu.h"
 
 #include "radix_hdr.inc"
+#include "scan.inc"
 #include "constants.inc"
 #include "keys.inc"
 #include "digit_keys.inc"
 #include "unit_begin.inc"
+#include "unit_scan.inc"
+#include "large_gather.inc"
 
 namespace {
 // the packed text with the padding the kernels read past its end, its size
@@ -89,6 +93,62 @@ extern "C" int emu_unit_begin(int kb, const uint32_t* text, uint64_t text_words,
     memcpy(ll_t, g_ll_t, slots * 4);
     memcpy(ll_row, g_ll_row, slots * 4);
     memcpy(ll_key, g_ll_key, slots * 8);
+    for (auto& m : maps) munmap(m.first, m.second);
+    return 0;
+}
+
+// The chain after the bucket sort for one block: sa_unit_begin, the unit
+// scan (one CTA) and the global-path gather, over the bucket-sorted
+// elements.  fields: the unit table, 8 fields of `stride` words (the device
+// layout); lkeys/lvals/lpos hold n entries; *d_large the list's size.
+extern "C" int emu_large_chain(int kb, const uint32_t* text, uint64_t text_words, const unsigned long long* elems,
+                               uint32_t n, uint32_t nwin, uint64_t stride, uint32_t* fields, uint32_t* sa,
+                               uint32_t* rank, unsigned long long* lkeys, uint32_t* lvals, uint32_t* lpos,
+                               uint32_t* d_large, uint32_t* d_err) {
+    std::vector<std::pair<void*, size_t>> maps;
+    std::vector<uint32_t> t(text_alloc_words(text_words), 0u);
+    memcpy(t.data(), text, text_words * 4);
+    const uint32_t* g_text = guarded(t.data(), t.size(), maps);
+    const unsigned long long* g_elems = guarded(elems, n, maps);
+    uint32_t* g = guarded(fields, stride * 8, maps);
+    Units u{g, g + stride, g + 2 * stride, g + 3 * stride, g + 4 * stride, g + 5 * stride, g + 6 * stride,
+            g + 7 * stride};
+    uint32_t* g_sa = guarded(sa, n, maps);
+    uint32_t* g_rank = guarded(rank, n, maps);
+    const size_t slots = (size_t)nwin * kWindow;
+    std::vector<uint32_t> ll_t(slots), ll_row(slots);
+    std::vector<unsigned long long> ll_key(slots);
+    uint32_t* g_ll_t = guarded(ll_t.data(), slots, maps);
+    uint32_t* g_ll_row = guarded(ll_row.data(), slots, maps);
+    unsigned long long* g_ll_key = guarded(ll_key.data(), slots, maps);
+    unsigned long long* g_lkeys = guarded(lkeys, n, maps);
+    uint32_t* g_lvals = guarded(lvals, n, maps);
+    uint32_t* g_lpos = guarded(lpos, n, maps);
+    uint32_t* g_large = guarded(d_large, 1, maps);
+    std::vector<uint32_t> zero(4, 0u);
+    uint32_t* g_zero = guarded(zero.data(), zero.size(), maps);
+    run_grid(3, kThreads, [&] {
+        if (kb == 2)
+            sa_unit_begin_kernel<2>(g_text, 0ull, g_elems, n, nwin, u, g_sa, g_rank, g_ll_t, g_ll_row, g_ll_key,
+                                    d_err);
+        else
+            sa_unit_begin_kernel<4>(g_text, 0ull, g_elems, n, nwin, u, g_sa, g_rank, g_ll_t, g_ll_row, g_ll_key,
+                                    d_err);
+    });
+    run_grid(1, kScanThreads, [&] { sa_unit_scan_kernel(u, nwin, n, g_large, g_zero, 1, 1, g_zero + 2, 1); });
+    run_grid(5, kThreads, [&] {
+        if (kb == 2)
+            sa_large_gather_kernel<2>(g_text, 0ull, n, g_elems, u, nwin, g_lkeys, g_lvals, g_lpos, g_large);
+        else
+            sa_large_gather_kernel<4>(g_text, 0ull, n, g_elems, u, nwin, g_lkeys, g_lvals, g_lpos, g_large);
+    });
+    memcpy(fields, g, stride * 8 * 4);
+    memcpy(sa, g_sa, n * 4ull);
+    memcpy(rank, g_rank, n * 4ull);
+    memcpy(lkeys, g_lkeys, n * 8ull);
+    memcpy(lvals, g_lvals, n * 4ull);
+    memcpy(lpos, g_lpos, n * 4ull);
+    *d_large = *g_large;
     for (auto& m : maps) munmap(m.first, m.second);
     return 0;
 }

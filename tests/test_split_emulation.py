@@ -56,6 +56,11 @@ def emu(tmp_path_factory):
                                            "// One warp per window of the digit-sorted array"))
     (d / "unit_begin.inc").write_text(_cut(src, "// One warp per window of the digit-sorted array",
                                            "// kScanPer consecutive windows of one field"))
+    (d / "scan.inc").write_text(_cut(hdr, "struct SumOp {", "// Launch bookkeeping"))
+    (d / "unit_scan.inc").write_text(_cut(src, "// kScanPer consecutive windows of one field",
+                                          "// one spare slot per kLItems"))
+    (d / "large_gather.inc").write_text(_cut(src, "// The global-path list:",
+                                             "// next-ranks of the local unsorted members"))
     lib = d / "libsplitemu.so"
     subprocess.check_call(["g++", "-O1", "-std=c++20", "-shared", "-fPIC", "-pthread", "-I", str(d), "-o", str(lib),
                            EMU])
@@ -65,6 +70,8 @@ def emu(tmp_path_factory):
     L.emu_unit_begin.argtypes = [I, P, U64, P, U32, U32, P, P, P, P, P, P, P, P, P, ctypes.c_uint]
     L.emu_digit_keys.restype = I
     L.emu_unit_begin.restype = I
+    L.emu_large_chain.argtypes = [I, P, U64, P, U32, U32, U64, P, P, P, P, P, P, P, P]
+    L.emu_large_chain.restype = I
     return L
 
 
@@ -238,3 +245,70 @@ def test_digit_keys_and_unit_begin(emu, case):
         assert np.all(ll_t[lo + k:lo + kWindow] == 0xABCD)
     # a real mix: short and long suffixes in the sorted rows
     assert short.any() and (~short).any()
+
+
+@pytest.mark.timeout(900)
+def test_units_too_large_for_a_cta_are_listed_for_the_device_wide_path(emu):
+    """Many copies of one read make units with more than 2048 long
+    suffixes.  After the unit begin and the unit scan, the gather lists every
+    row of each such unit, in row order, at the unit's offset: (key, t,
+    row); the offsets are the units' sizes summed in unit order."""
+    kb, sigma, P = 2, 4, 11
+    rng = np.random.default_rng(8)
+    rep = rng.integers(0, sigma, size=60)
+    reads = [rep.copy() for _ in range(2600)] + [rng.integers(0, sigma, size=int(rng.integers(0, 90)))
+                                                 for _ in range(600)]
+    order = rng.permutation(len(reads))
+    reads = [reads[i] for i in order]
+    lens = np.array([r.size for r in reads])
+    n = int(lens.sum() + lens.size)
+    codes = rng.integers(0, sigma, size=n)
+    term = np.zeros(n, bool)
+    ends = np.cumsum(lens + 1) - 1
+    term[ends] = True
+    for r, s in zip(reads, ends - lens):
+        codes[s:s + r.size] = r
+    text = pack(codes, kb)
+    keys, field, _ = keys_of(codes, term, kb)
+    digits = bucket_numbers(keys, field, kb, sigma, P)
+    elems = (digits.astype(np.uint64) | (field.astype(np.uint64) << np.uint64(24))
+             | (np.arange(n, dtype=np.uint64) << np.uint64(32)))
+    srt = elems[np.argsort(elems & np.uint64(kDigitMask), kind="stable")]
+    d = (srt & np.uint64(0xFFFFFFFF)).astype(np.uint32)
+    t = (srt >> np.uint64(32)).astype(np.uint32)
+    nwin = (n + kWindow - 1) // kWindow
+    stride = (n // kWindow + 2 + 7) & ~7
+    fields = np.zeros(8 * stride, np.uint32)
+    sa = np.zeros(n, np.uint32)
+    rank = np.zeros(n, np.uint32)
+    lkeys = np.full(n, 0xABCD, np.uint64)
+    lvals = np.full(n, 0xABCD, np.uint32)
+    lpos = np.full(n, 0xABCD, np.uint32)
+    d_large = np.zeros(1, np.uint32)
+    d_err = np.zeros(1, np.uint32)
+    p = lambda a: ctypes.c_void_p(a.ctypes.data)  # noqa: E731
+    assert emu.emu_large_chain(kb, p(text), text.size, p(srt), n, nwin, stride, p(fields), p(sa), p(rank),
+                               p(lkeys), p(lvals), p(lpos), p(d_large), p(d_err)) == 0
+    assert d_err[0] == 0
+    # units from the definitions: a unit is the buckets starting in a window
+    bnd = np.ones(n, bool)
+    bnd[1:] = ((d[1:] ^ d[:-1]) & np.uint32(kDigitMask)) != 0
+    long_ = (d & np.uint32(kShortFlag)) == 0
+    starts = [int(w * kWindow + np.nonzero(bnd[w * kWindow:(w + 1) * kWindow])[0][0])
+              for w in range(nwin) if bnd[w * kWindow:(w + 1) * kWindow].any()]
+    ends = starts[1:] + [n]
+    off, want = 0, []
+    for b, e in zip(starts, ends):
+        if np.count_nonzero(long_[b:e]) > 2048:
+            want.append((b, e, off))
+            off += e - b
+    assert want, "the data must hold a unit too large for a CTA"
+    assert int(d_large[0]) == off
+    lofs = fields[5 * stride:5 * stride + nwin]
+    for b, e, o in want:
+        assert lofs[b // kWindow] == o
+        rows = np.arange(b, e)
+        assert np.array_equal(lpos[o:o + e - b], rows.astype(np.uint32))
+        assert np.array_equal(lvals[o:o + e - b], t[rows])
+        assert np.array_equal(lkeys[o:o + e - b], keys[t[rows]])
+    assert np.all(lpos[off:] == 0xABCD)
