@@ -63,6 +63,7 @@ namespace sbwt {
 #include "radix_consts.inc"
 #include "radix_count.inc"
 #include "radix_down.inc"
+#include "radix_fused_scan.inc"
 }  // namespace sbwt
 using namespace sbwt;
 
@@ -132,6 +133,63 @@ extern "C" int emu_radix_pass(const unsigned long long* keys, const uint32_t* va
     });
     memcpy(out_keys, g_out, n * 8ull);
     if (pairs) memcpy(out_vals, g_outv, n * 4ull);
+    for (auto& m : maps) munmap(m.first, m.second);
+    return g_tma_misaligned ? 1 : 0;
+}
+
+// The fused sort's passes (radix_sort_fused_kernel) with its phases run as
+// consecutive grids in the kernel's order: a grid barrier of the kernel is
+// the end of one grid here, since the emulation runs one CTA at a time.
+// Each downsweep grid starts its tile barrier afresh (the kernel carries
+// one across passes).  Keys with values; the result is in out_keys /
+// out_vals.  Returns 0, or 1 when a bulk copy broke its alignment rule.
+extern "C" int emu_fused_sort(const unsigned long long* keys, const uint32_t* vals, uint32_t n, int begin_bit,
+                              int passes, uint32_t grid, unsigned long long* out_keys, uint32_t* out_vals,
+                              uint32_t* d_err) {
+    std::vector<std::pair<void*, size_t>> maps;
+    const size_t words = kChunkOffsets + (size_t)grid * kBins + 64;
+    std::vector<uint32_t> temp(words, 0u);
+    const size_t nk = ((size_t)n + 1) & ~(size_t)1, nv = ((size_t)n + 3) & ~(size_t)3;
+    std::vector<unsigned long long> k0(nk ? nk : 2, 0ull), k1(nk ? nk : 2, 0ull);
+    std::vector<uint32_t> v0(nv ? nv : 4, 0u), v1(nv ? nv : 4, 0u);
+    if (n) {
+        memcpy(k0.data(), keys, n * 8ull);
+        memcpy(v0.data(), vals, n * 4ull);
+    }
+    unsigned long long* g_k[2] = {guarded(k0.data(), k0.size(), maps), guarded(k1.data(), k1.size(), maps)};
+    uint32_t* g_v[2] = {guarded(v0.data(), v0.size(), maps), guarded(v1.data(), v1.size(), maps)};
+    uint32_t* g_temp = guarded(temp.data(), words, maps);
+    g_tma_misaligned = 0;
+    uint32_t ntiles = 0;
+    const uint32_t tpc = tiles_per_chunk(n, grid, ntiles);
+    const uint32_t nchunks = tpc ? (ntiles + tpc - 1) / tpc : 0;
+    uint32_t* chunk = g_temp + kChunkOffsets;
+    uint32_t* partials = g_temp + kPartials;
+    unsigned long long* bar =
+        reinterpret_cast<unsigned long long*>(g_dyn_smem + down_smem<unsigned long long, true>() - 16);
+    for (int p = 0; p < passes && n > 0; ++p) {
+        const int a = p & 1;
+        const int shift = begin_bit + kRadixBits * p;
+        uint32_t* totals = g_temp + kTotals + (size_t)kBins * (p & 1);
+        uint32_t* next_totals = g_temp + kTotals + (size_t)kBins * ((p + 1) & 1);
+        run_grid(grid, kThreads, [&] {
+            up_phase(g_k[a], n, shift, chunk, totals, reinterpret_cast<uint32_t*>(g_dyn_smem));
+        });
+        run_grid(grid, kThreads, [&] {
+            scan_a_phase(chunk, nchunks, partials);
+            if (blockIdx.x == 0) next_totals[threadIdx.x] = 0;
+        });
+        run_grid(grid, kThreads, [&] { scan_b_phase(chunk, nchunks, partials, totals); });
+        run_grid(grid, kThreads, [&] {
+            if (threadIdx.x == 0) mbar_init(bar, 1);
+            uint32_t parity = 0;
+            down_phase<unsigned long long, true>(g_k[a], g_v[a], g_k[a ^ 1], g_v[a ^ 1], n, shift, chunk, d_err,
+                                                 g_dyn_smem, parity);
+        });
+    }
+    const int fin = passes & 1;
+    memcpy(out_keys, g_k[fin], n * 8ull);
+    memcpy(out_vals, g_v[fin], n * 4ull);
     for (auto& m : maps) munmap(m.first, m.second);
     return g_tma_misaligned ? 1 : 0;
 }

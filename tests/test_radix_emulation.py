@@ -53,6 +53,9 @@ def emu(tmp_path_factory):
     dyn = "extern __shared__ __align__(128) unsigned char smem[];"
     assert down.count(dyn) == 1
     (d / "radix_down.inc").write_text(down.replace(dyn, "unsigned char* smem = g_dyn_smem;"))
+    (d / "radix_fused_scan.inc").write_text(_cut(src, "// Output offsets of every (chunk, digit) from the chunk counts",
+                                                 "template <class KeyT>\n__global__ void __launch_bounds__(kThreads, 3) "
+                                                 "radix_sort_fused_kernel("))
     lib = d / "libradixemu.so"
     subprocess.check_call(["g++", "-O1", "-std=c++20", "-shared", "-fPIC", "-pthread", "-I", str(d), "-o", str(lib),
                            EMU])
@@ -62,6 +65,8 @@ def emu(tmp_path_factory):
     L.emu_radix_count.restype = I
     L.emu_radix_pass.argtypes = [P, P, U32, I, U32, I, P, P, P]
     L.emu_radix_pass.restype = I
+    L.emu_fused_sort.argtypes = [P, P, U32, I, I, U32, P, P, P]
+    L.emu_fused_sort.restype = I
     return L
 
 
@@ -131,3 +136,27 @@ def test_one_pass_is_a_stable_counting_sort(emu, n, grid, shift, pairs):
     assert np.array_equal(out_k[:n], keys[order])
     if pairs:
         assert np.array_equal(out_v[:n], vals[order])
+
+
+@pytest.mark.timeout(600)
+@pytest.mark.parametrize("n,grid,begin,passes", [(20_001, 5, 0, 3), (9_000, 20, 8, 2), (2_048, 3, 0, 1),
+                                                 (12_000, 4, 4, 4), (1, 2, 0, 3)])
+def test_fused_sort_passes_sort_stably_by_all_their_bits(emu, n, grid, begin, passes):
+    """The fused sort's phases (upsweep, the two-step chunk scan of chunk
+    groups, downsweep) run pass after pass with keys and values ping-ponging
+    between the two arrays: the result is a stable sort by bits [begin,
+    begin + 8 passes)."""
+    rng = np.random.default_rng(n + grid + passes)
+    width = 8 * passes
+    field = np.where(rng.random(n) < 0.4, rng.integers(0, 16, n), rng.integers(0, 1 << width, n)).astype(np.uint64)
+    keys = (field << np.uint64(begin)) | (rng.integers(0, 1 << 10, n).astype(np.uint64) << np.uint64(begin + width))
+    keys |= rng.integers(0, 1 << begin, n).astype(np.uint64) if begin else np.uint64(0)
+    vals = rng.permutation(n).astype(np.uint32)
+    out_k = np.zeros(n, np.uint64)
+    out_v = np.zeros(n, np.uint32)
+    err = np.zeros(1, np.uint32)
+    p = lambda a: ctypes.c_void_p(a.ctypes.data)  # noqa: E731
+    assert emu.emu_fused_sort(p(keys), p(vals), n, begin, passes, grid, p(out_k), p(out_v), p(err)) == 0
+    assert err[0] == 0
+    order = np.argsort(field, kind="stable")
+    assert np.array_equal(out_k, keys[order]) and np.array_equal(out_v, vals[order])
