@@ -12,6 +12,7 @@ namespace sbwt {
 #include "alphabet.inc"
 #include "text.inc"
 #include "dict.inc"
+#include "bint.inc"
 #include "ranks.inc"
 #include "gather.inc"
 #include "queries.inc"
@@ -223,5 +224,20 @@ extern "C" int emu_compute_ranks_w(int staged, int seg, uint32_t segs, uint32_t 
     else
         run_w<false>(seg, segs, seg_rows, text, text_words, offsets, nreads, blocks, super, C, n_ext, m_start, g,
                      n_int, d_err);
+    return 0;
+}
+
+// B_int by the one-block kernel (a block into an empty index): one thread
+// per suffix, SA of n entries.
+extern "C" int emu_bint_plain(const uint32_t* text, uint64_t text_words, const uint32_t* term, uint64_t term_words,
+                              unsigned long long base, const uint32_t* sa, uint32_t n, uint8_t* bint) {
+    std::vector<std::pair<void*, size_t>> maps;
+    const uint32_t* g_text = guarded(text, text_words, maps);
+    const uint32_t* g_term = guarded(term, term_words, maps);
+    const uint32_t* g_sa = guarded(sa, n ? n : 1, maps);
+    uint8_t* g_bint = guarded(bint, n ? n : 1, maps);
+    run_grid((n + kThreads - 1) / kThreads, kThreads, [&] { bint_kernel(g_text, g_term, base, g_sa, n, g_bint); });
+    memcpy(bint, g_bint, n);
+    for (auto& m : maps) munmap(m.first, m.second);
     return 0;
 }

@@ -46,6 +46,8 @@ def emu(tmp_path_factory):
     (d / "dict.inc").write_text("constexpr int kThreads = 256;\n" + _cut(
         hdr, "constexpr int kOccShift = 6;", "// ---------------------------------------------------------------------------\n// CTA-wide scans"))
     (d / "text.inc").write_text(_cut(hdr, "constexpr int kTextPadWords = 4;", "// Rank dictionary over B"))
+    (d / "bint.inc").write_text(_cut(src, "// B_int[i]: the symbol before block suffix SA[i]",
+                                     "// Algorithm 2, one thread per read:"))
     (d / "gather.inc").write_text(_cut(src, "// B_int and g_sa in one pass over SA_int",
                                        "// rank(c, k) queries, codes 0..kCodes-1"))
     (d / "queries.inc").write_text(_cut(src, "// rank(c, k) queries, codes 0..kCodes-1",
@@ -73,6 +75,8 @@ def emu(tmp_path_factory):
     L.emu_queries_w.restype = I
     L.emu_compute_ranks_w.argtypes = [I, I, U32, U32, P, U64, P, U64, P, P, P, U64, U64, P, U64, P]
     L.emu_compute_ranks_w.restype = I
+    L.emu_bint_plain.argtypes = [P, U64, P, U64, U64, P, U32, P]
+    L.emu_bint_plain.restype = I
     return L
 
 
@@ -221,6 +225,10 @@ def test_gather_writes_bint_gsa_and_the_insert_plan(emu, n_reads, seed):
     t = sa.astype(np.int64)
     want = np.where((t == 0) | is_term[np.maximum(t - 1, 0)], 255, codes[np.maximum(t - 1, 0)])
     assert np.array_equal(bint, want.astype(np.uint8))
+    # the one-block kernel (a block into an empty index) gives the same B_int
+    bint1 = np.zeros(n, np.uint8)
+    assert emu.emu_bint_plain(ptr(text), len(text), ptr(term), len(term), 0, ptr(sa), n, ptr(bint1)) == 0
+    assert np.array_equal(bint1, want.astype(np.uint8))
     assert np.array_equal(gsa, gsa_want)
     r = gsa_want.astype(np.int64) + np.arange(n)
     plan_want = np.searchsorted(r, np.arange(nsb + 1, dtype=np.int64) << shift, side="left")
